@@ -1,0 +1,195 @@
+/*
+ * algmortar.h -- C ABI of the B300-native AlgMortar-PCG library (libalgmortar.so).
+ *
+ * AlgMortar (arxiv 2607.22905) is an algebraic multiscale mortar preconditioner for an
+ * SPD matrix A whose off-diagonal couplings between subdomains are negative
+ * (Sec. 3.2, the sign assumption on the weights W).  From A alone it
+ *   - partitions the adjacency graph G(A) into m subdomains Omega_i (Sec. 3.1),
+ *   - forms the diagonally modified local blocks A_i = A_ii - sum_j D_ij (Eq. A_i),
+ *   - builds one multiscale basis function per neighbouring interface (Eq. def-phat-local)
+ *     with the piecewise-constant mortar space of Sec. 5.5,
+ *   - assembles the interface system (Eq. interface-problem-alg),
+ * and applies z = cal_M^{-1} r of Eq. (eq-m-reduced-p) by Algorithm 2 inside
+ * preconditioned CG (Sec. 7: x0 = 0, Euclidean relative-residual stop).
+ *
+ * Conventions for every entry point below:
+ *   - Return value: 0 (ALGMORTAR_OK) or an algmortar_status code; nothing traps or
+ *     aborts.  algmortar_last_error() returns a thread-local message for the last
+ *     failure (which block, which row, which CUDA call).
+ *   - "host" pointers are read (or written) during the call only and are never retained.
+ *   - "device" pointers are CUDA global-memory pointers on the handle's device.  They
+ *     are owned by the caller, must stay valid for the call, and are not retained.
+ *   - Vectors of the public API are in the caller's ORIGINAL row ordering.
+ *   - All device work is issued on opts.stream (NULL = the legacy default stream);
+ *     calls that return results to the host synchronise that stream before returning.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef ALGMORTAR_H
+#define ALGMORTAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    ALGMORTAR_OK = 0,
+    ALGMORTAR_INVALID_ARG = 1,     /* null pointer, bad size, malformed CSR (unsorted or
+                                      out-of-range columns, missing diagonal, NaN/Inf)  */
+    ALGMORTAR_NOT_SYMMETRIC = 2,   /* a_kl != a_lk for some stored entry                 */
+    ALGMORTAR_INTERFACE_SIGN = 3,  /* a_kl >= 0 across two subdomains: W not negative
+                                      definite, the hypothesis of Sec. 3.2 / Thm. Q-psd  */
+    ALGMORTAR_NOT_SPD = 4,         /* non-positive pivot in a local or interface Cholesky
+                                      factor (block id in algmortar_last_error())        */
+    ALGMORTAR_NO_CONVERGENCE = 5,  /* max_it reached; x holds the last iterate           */
+    ALGMORTAR_BREAKDOWN = 6,       /* p^T A p <= 0 or a non-finite CG scalar             */
+    ALGMORTAR_CUDA = 7,            /* a CUDA runtime call failed                        */
+    ALGMORTAR_OOM = 8,             /* device or host allocation failed                  */
+    ALGMORTAR_TOO_LARGE = 9        /* a subdomain above ALGMORTAR_MAX_PART rows          */
+};
+
+/* Largest subdomain the batched local kernels accept (rows). */
+#define ALGMORTAR_MAX_PART 16384
+
+/* Precision of the local factors L_i, their triangular solves and the MBF panels.
+ * The outer PCG recurrences, dot products, SpMV, interface restriction, the coarse
+ * interface solve and the true-residual check are FP64 in every mode. */
+enum {
+    ALGMORTAR_FP64 = 0,            /* factors and solves in FP64                         */
+    ALGMORTAR_FP32 = 1,            /* factors stored and applied in FP32                 */
+    ALGMORTAR_BF16 = 2             /* factors stored in BF16, applied with FP32 accumulation */
+};
+
+/* Host CSR matrix, square, full symmetric pattern, columns strictly ascending within
+ * each row, explicit diagonal, int32 indices (nnz < 2^31).  Read during setup only. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t* rowptr;         /* host, n + 1 entries, rowptr[0] = 0, rowptr[n] = nnz */
+    const int32_t* col;            /* host, nnz entries                                   */
+    const double* val;             /* host, nnz entries                                   */
+} algmortar_csr;
+
+typedef struct {
+    int32_t precision;             /* ALGMORTAR_FP64 / FP32 / BF16 (default FP64)         */
+    int32_t diag_scale;            /* 1: factor D^-1/2 A_i D^-1/2 (D = diag A_i); default 1 */
+    int32_t max_it;                /* PCG iteration cap (default 10000)                   */
+    int32_t use_graph;             /* 1: replay each PCG iteration as a captured CUDA graph */
+    int32_t check_every;           /* iterations between host convergence reads (>= 1)    */
+    int32_t flexible;              /* 1: Polak-Ribiere beta (for low-precision factors)   */
+    int32_t verbose;               /* 1: stage timings to stderr                          */
+    int32_t device;                /* CUDA device ordinal (default 0)                      */
+    const int32_t* part_sizes;     /* host, n_parts target sizes summing to n, or NULL for
+                                      sizes differing by at most one (larger ones first)  */
+    void* stream;                  /* cudaStream_t for all device work (NULL = default)   */
+} algmortar_opts;
+
+typedef struct {
+    int32_t status;                /* status of the solve                                 */
+    int32_t iterations;            /* products with A in the CG loop                      */
+    double rel_residual;           /* true ||b - A x||_2 / ||b||_2 at exit                */
+    double recursive_residual;     /* CG recurrence ||r_k||_2 / ||b||_2 at exit           */
+    double solve_ms;               /* wall time of the solve call, device-synchronised    */
+    double host_ms;                /* host-side part of the call (setup: partition etc.)  */
+} algmortar_stats;
+
+typedef struct {
+    int64_t n;                     /* rows                                               */
+    int32_t n_parts;               /* subdomains m                                       */
+    int32_t n_lambda;              /* interface unknowns N_Lambda (one per pair i~j)     */
+    int32_t max_part;              /* largest subdomain                                  */
+    int32_t min_part;              /* smallest subdomain                                 */
+    int32_t precision;
+    int64_t n_interface_edges;     /* |E|                                                */
+    int64_t factor_entries;        /* stored entries of one triangular sweep (all L_i)   */
+    int64_t factor_bytes;          /* bytes of both sweep streams                        */
+    int64_t phi_entries;           /* sum_i N_i |I_i| (MBF panel entries)                */
+    double setup_ms[8];            /* partition+tables (host), upload, local factor, MBF,
+                                      interface assembly, interface factor+inverse,
+                                      graph capture, total                                */
+} algmortar_info;
+
+typedef struct algmortar_handle algmortar_t;
+
+/* Fill *opts with the defaults listed above. */
+void algmortar_default_opts(algmortar_opts* opts);
+
+/* Host only (no GPU needed): the deterministic graph partition of Sec. 3.1 used by
+ * algmortar_setup.  part_out (host, n entries) receives labels in [0, n_parts).
+ * part_sizes as in algmortar_opts (NULL = even).  Recursive BFS bisection with
+ * George-Liu pseudo-peripheral start nodes; see DESIGN notes in the source. */
+int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes,
+                        int32_t* part_out);
+
+/* Algorithm 1 (AlgMortarSetup) on the device.  Validates A (symmetry, interface sign),
+ * partitions it (Sec. 3.1), permutes it, factors every A_i, computes the MBFs, assembles
+ * and factors the interface system, and allocates the PCG workspace.  *out receives a
+ * handle owning all device state; release it with algmortar_destroy.  On error *out is
+ * NULL and nothing is leaked. */
+int algmortar_setup(const algmortar_csr* A, int32_t n_parts, const algmortar_opts* opts,
+                    algmortar_t** out);
+
+/* As algmortar_setup with caller-given labels part (host, n entries in [0, n_parts),
+ * every part non-empty) in place of the built-in partitioner -- e.g. to reuse a
+ * partition across time steps. */
+int algmortar_setup_with_parts(const algmortar_csr* A, const int32_t* part, int32_t n_parts,
+                               const algmortar_opts* opts, algmortar_t** out);
+
+/* Algorithm 2 (AlgMortarApply): z = cal_M^{-1} r (Eq. eq-m-reduced-p).  r_dev, z_dev:
+ * device, n doubles each, original ordering; they may not alias. */
+int algmortar_apply(algmortar_t* h, const double* r_dev, double* z_dev);
+
+/* Stages of Algorithm 2 in the handle's internal (permuted) ordering, for testing:
+ * pbar = A_hat^{-1} r (Eq. def-pbar-local), b_eta = interface right-hand side,
+ * eta = interface solution, z = pbar + sum_m eta_m p_hat^(m) (Eq. p-decomposition-alg).
+ * r_dev is in the ORIGINAL ordering; pbar_dev, z_dev: n doubles (internal ordering);
+ * beta_dev, eta_dev: n_lambda doubles (interfaces numbered lexicographically by (i, j)). */
+int algmortar_apply_stages(algmortar_t* h, const double* r_dev, double* pbar_dev,
+                           double* beta_dev, double* eta_dev, double* z_dev);
+
+/* PCG with x0 = 0 for A x = b, preconditioned by AlgMortar; stops when
+ * ||r_k||_2 <= tol ||b||_2 and the true residual confirms it (Sec. 7).  b_dev, x_dev:
+ * device, n doubles, original ordering.  st may be NULL.  Returns OK, NO_CONVERGENCE
+ * or BREAKDOWN (x_dev holds the last iterate in the latter two cases). */
+int algmortar_pcg_solve(algmortar_t* h, const double* b_dev, double* x_dev, double tol,
+                        algmortar_stats* st);
+
+/* As algmortar_pcg_solve with HOST b and x (n doubles each): copies b to the device,
+ * solves, copies x back; the copies are part of the call. */
+int algmortar_pcg_solve_host(algmortar_t* h, const double* b_host, double* x_host, double tol,
+                             algmortar_stats* st);
+
+/* nrhs independent systems A X[:, j] = B[:, j] (column-major, leading dimension ld >= n,
+ * device).  Each column runs its own CG scalars and stops on its own tolerance; st (may
+ * be NULL) points to nrhs stats. */
+int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev, int32_t nrhs,
+                              int64_t ld, double tol, algmortar_stats* st);
+
+/* New values for the same sparsity pattern (host, nnz doubles in the CSR order given at
+ * setup): keeps the partition, re-runs the numeric part of Algorithm 1. */
+int algmortar_update_values(algmortar_t* h, const double* val_host);
+
+/* Labels of the handle's partition (host, n entries). */
+int algmortar_get_partition(const algmortar_t* h, int32_t* part_out);
+
+/* perm_out[new] = old for the handle's internal ordering (host, n entries). */
+int algmortar_get_permutation(const algmortar_t* h, int32_t* perm_out);
+
+/* Interface pairs (host, 2 * n_lambda entries: i, j with i < j, lexicographic). */
+int algmortar_get_interfaces(const algmortar_t* h, int32_t* pairs_out);
+
+int algmortar_get_info(const algmortar_t* h, algmortar_info* info);
+
+/* Releases all device and host state of h (NULL is ignored). */
+void algmortar_destroy(algmortar_t* h);
+
+const char* algmortar_strerror(int status);
+const char* algmortar_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALGMORTAR_H */

@@ -1,0 +1,772 @@
+// C ABI of libalgmortar (include/algmortar.h): handle lifetime, Algorithm 1 on the device,
+// Algorithm 2 and the PCG loop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <type_traits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "algmortar.h"
+#include "host_setup.h"
+#include "kernels.h"
+
+using namespace am;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? ALGMORTAR_OOM : ALGMORTAR_CUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+}  // namespace
+
+struct algmortar_handle {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    cudaStream_t own_st = nullptr;   // created when the caller passes no stream
+    algmortar_opts opts{};
+    Plan P;
+    int64_t n = 0;
+    int m = 0, L = 0;
+    std::vector<void*> allocs;
+    // permuted matrix and maps
+    int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_perm = nullptr, *d_row_sub = nullptr;
+    double* d_val = nullptr;
+    int64_t* d_sub_off = nullptr;
+    // local factor profile and streams
+    Profile pf{};
+    int32_t *d_rows = nullptr, *d_ntiles = nullptr;
+    void *d_fwdS = nullptr, *d_bwdS = nullptr;
+    double *d_dloc = nullptr, *d_sc = nullptr;
+    int32_t* d_job_sub = nullptr;
+    int64_t* d_job_off = nullptr;
+    // interfaces
+    int64_t* d_rptr = nullptr;
+    int32_t* d_rcell = nullptr;
+    double* d_rcoef = nullptr;
+    int64_t *d_if_off = nullptr, *d_phi_off = nullptr;
+    int32_t* d_if_list = nullptr;
+    void* d_phi = nullptr;
+    double* d_Sinv = nullptr;
+    // workspace
+    double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_pbar = nullptr;
+    double *d_beta = nullptr, *d_eta = nullptr, *d_b = nullptr, *d_t = nullptr;
+    double *d_part_rz = nullptr, *d_part_pq = nullptr, *d_part_rr = nullptr, *d_part_t = nullptr;
+    double* d_scalar = nullptr;
+    PcgScalars* d_pcg = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    algmortar_info info{};
+
+    template <typename T>
+    T* alloc(size_t count) {
+        if (count == 0) count = 1;
+        void* p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        return (T*)p;
+    }
+    void release(void* p) {
+        for (auto& q : allocs)
+            if (q == p) {
+                cudaFree(q);
+                q = nullptr;
+            }
+    }
+    ~algmortar_handle() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (void* p : allocs)
+            if (p) cudaFree(p);
+        if (own_st) cudaStreamDestroy(own_st);
+    }
+};
+
+namespace {
+
+template <typename T>
+int upload(algmortar_t* h, T*& dst, const std::vector<T>& src) {
+    dst = h->alloc<T>(src.size());
+    if (!dst) return fail(ALGMORTAR_OOM, "device allocation failed");
+    if (!src.empty()) CU(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->st));
+    return 0;
+}
+
+#define TRY(x)              \
+    do {                    \
+        int rc_ = (x);      \
+        if (rc_) return rc_; \
+    } while (0)
+
+int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
+    int e[2];
+    CU(cudaMemcpyAsync(e, d_err, sizeof(e), cudaMemcpyDeviceToHost, h->st));
+    CU(cudaStreamSynchronize(h->st));
+    if (e[0]) return fail(ALGMORTAR_NOT_SPD, std::string("non-positive pivot in the ") + what + " factor, block " +
+                                                 std::to_string(e[1]));
+    return 0;
+}
+
+// Numeric part of Algorithm 1: factor the local blocks, MBFs, interface system.
+template <typename TW, typename TS, typename TA>
+int numeric_setup(algmortar_t* h) {
+    Plan& P = h->P;
+    cudaStream_t st = h->st;
+    cudaEvent_t ev[8];
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], st);
+    const int m = h->m;
+    const int64_t tiles = P.total_tiles;
+    const int64_t trows = P.trow_off[m];
+    // --- local factors ---
+    TW* work = h->alloc<TW>((size_t)tiles * TILE2);
+    TW* dinv = h->alloc<TW>((size_t)trows * TILE2);
+    int* d_err = h->alloc<int>(2);
+    if (!work || !dinv || !d_err) return fail(ALGMORTAR_OOM, "factor workspace");
+    int err_init[2] = {0, -1};
+    CU(cudaMemcpyAsync(d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
+    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, h->d_dloc, h->d_sc, st);
+    launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
+                             h->d_sc, work, m, st);
+    launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, d_err, st);
+    CU(cudaGetLastError());
+    TRY(read_err_flag(h, d_err, "local"));
+    if (!h->d_fwdS) {
+        h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
+        h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
+        if (!h->d_fwdS || !h->d_bwdS) return fail(ALGMORTAR_OOM, "sweep streams");
+    }
+    launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS, (TS*)h->d_bwdS, st);
+    CU(cudaGetLastError());
+    cudaEventRecord(ev[1], st);
+    h->release(work);
+    h->release(dinv);
+    // --- MBFs: Phi_i = A_i^{-1} (-G_i), one job per (subdomain, interface) ---
+    const int64_t nphi = P.phi_off[m];
+    double* rhs = h->alloc<double>(nphi);
+    double* phi64 = h->alloc<double>(nphi);
+    std::vector<int32_t> js;
+    std::vector<int64_t> jo;
+    for (int s = 0; s < m; ++s) {
+        int64_t ns = P.sub_off[s + 1] - P.sub_off[s];
+        for (int64_t a = 0; a < P.if_off[s + 1] - P.if_off[s]; ++a) {
+            js.push_back(s);
+            jo.push_back(P.phi_off[s] + a * ns);
+        }
+    }
+    int32_t* d_js = nullptr;
+    int64_t* d_jo = nullptr;
+    TRY(upload(h, d_js, js));
+    TRY(upload(h, d_jo, jo));
+    int64_t *d_goff = nullptr, *d_gcptr = nullptr;
+    int32_t *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
+    double* d_gval = nullptr;
+    std::vector<int64_t> gcptr;
+    gcptr.reserve(P.if_off[m] + m);
+    for (int s = 0; s < m; ++s) {
+        int k = (int)(P.if_off[s + 1] - P.if_off[s]);
+        int64_t t = P.g_off[s];
+        for (int a = 0; a <= k; ++a) {
+            while (t < P.g_off[s + 1] && P.g_col[t] < a) ++t;
+            gcptr.push_back(t);
+        }
+    }
+    TRY(upload(h, d_goff, P.g_off));
+    TRY(upload(h, d_gcptr, gcptr));
+    TRY(upload(h, d_grow, P.g_row));
+    TRY(upload(h, d_gcol, P.g_col));
+    TRY(upload(h, d_gval, P.g_val));
+    TRY(upload(h, d_pairs, P.pairs));
+    if (!rhs || !phi64) return fail(ALGMORTAR_OOM, "MBF panels");
+    CU(cudaMemsetAsync(rhs, 0, nphi * sizeof(double), st));
+    launch_mbf_rhs(m, d_goff, d_grow, d_gcol, d_gval, h->d_rows, h->d_phi_off, rhs, st);
+    {
+        SolveArgs a{};
+        a.pf = h->pf;
+        a.fwdS = h->d_fwdS;
+        a.bwdS = h->d_bwdS;
+        a.scale = h->d_sc;
+        a.scale_off = h->d_sub_off;
+        a.job_sub = d_js;
+        a.job_in = d_jo;
+        a.job_out = d_jo;
+        a.in = rhs;
+        a.out = phi64;
+        a.alpha = 1.0;
+        a.done = nullptr;
+        CU((launch_tile_solve<TS, TA>(a, (int)js.size(), P.max_tiles, st)));
+    }
+    if (std::is_same<TS, double>::value) {
+        h->d_phi = phi64;
+    } else {
+        TS* ph = h->alloc<TS>(nphi);
+        if (!ph) return fail(ALGMORTAR_OOM, "MBF panels");
+        launch_convert<TS>(nphi, phi64, ph, st);
+        h->d_phi = ph;
+    }
+    cudaEventRecord(ev[2], st);
+    // --- interface system S_eta = diag(T) + 1/4 G^T Phi, its factor and explicit inverse ---
+    const int L = h->L;
+    if (L > 0) {
+        int32_t *d_siperm = nullptr, *d_slo = nullptr, *d_shi = nullptr, *d_if_list2 = nullptr;
+        int64_t *d_sfwd = nullptr, *d_sbwd = nullptr;
+        double* d_T = nullptr;
+        TRY(upload(h, d_siperm, P.s_iperm));
+        TRY(upload(h, d_slo, P.s_lo));
+        TRY(upload(h, d_shi, P.s_hi));
+        TRY(upload(h, d_sfwd, P.s_fwd));
+        TRY(upload(h, d_sbwd, P.s_bwd));
+        TRY(upload(h, d_T, P.T));
+        (void)d_if_list2;
+        const int64_t stiles = P.s_tiles;
+        double* swork = h->alloc<double>((size_t)stiles * TILE2);
+        double* sdinv = h->alloc<double>((size_t)P.s_ntiles * TILE2);
+        double* diagc = h->alloc<double>(2 * (size_t)L);
+        if (!swork || !sdinv || !diagc) return fail(ALGMORTAR_OOM, "interface factor");
+        CU(cudaMemsetAsync(swork, 0, (size_t)stiles * TILE2 * sizeof(double), st));
+        InterfaceArgs ia{};
+        ia.rows = h->d_rows;
+        ia.if_off = h->d_if_off;
+        ia.if_list = h->d_if_list;
+        ia.phi_off = h->d_phi_off;
+        ia.phi = phi64;
+        ia.g_cptr = d_gcptr;
+        ia.g_row = d_grow;
+        ia.g_val = d_gval;
+        ia.pairs = d_pairs;
+        ia.s_iperm = d_siperm;
+        ia.s_lo = d_slo;
+        ia.s_fwd = d_sfwd;
+        ia.work = swork;
+        ia.diagc = diagc;
+        launch_interface_assemble(m, ia, st);
+        launch_interface_diag(L, d_T, diagc, d_siperm, d_slo, d_sfwd, swork, st);
+        // single-item profile for S
+        std::vector<int32_t> one_rows{L}, one_nt{P.s_ntiles};
+        std::vector<int64_t> zero64{0};
+        int32_t *d_srows = nullptr, *d_snt = nullptr;
+        int64_t *d_szero = nullptr;
+        TRY(upload(h, d_srows, one_rows));
+        TRY(upload(h, d_snt, one_nt));
+        TRY(upload(h, d_szero, zero64));
+        Profile spf{d_srows, d_snt, d_szero, d_szero, d_slo, d_shi, d_sfwd, d_sbwd};
+        launch_pad_diag<double>(1, spf, swork, st);
+        cudaEventRecord(ev[3], st);
+        int err_init2[2] = {0, -1};
+        CU(cudaMemcpyAsync(d_err, err_init2, sizeof(err_init2), cudaMemcpyHostToDevice, st));
+        launch_tile_chol<double>(1, spf, nullptr, swork, sdinv, d_err, st);
+        CU(cudaGetLastError());
+        TRY(read_err_flag(h, d_err, "interface"));
+        double* sf = h->alloc<double>((size_t)stiles * TILE2);
+        double* sb = h->alloc<double>((size_t)stiles * TILE2);
+        double* E = h->alloc<double>((size_t)L * L);
+        double* R = h->alloc<double>((size_t)L * L);
+        h->d_Sinv = h->alloc<double>((size_t)L * L);
+        if (!sf || !sb || !E || !R || !h->d_Sinv) return fail(ALGMORTAR_OOM, "interface inverse");
+        launch_finalize<double, double>(1, spf, swork, sdinv, sf, sb, st);
+        CU(cudaMemsetAsync(E, 0, (size_t)L * L * sizeof(double), st));
+        launch_eye(L, E, st);
+        std::vector<int32_t> zs(L, 0);
+        std::vector<int64_t> qo(L);
+        for (int q = 0; q < L; ++q) qo[q] = (int64_t)q * L;
+        int32_t* d_zs = nullptr;
+        int64_t* d_qo = nullptr;
+        TRY(upload(h, d_zs, zs));
+        TRY(upload(h, d_qo, qo));
+        SolveArgs a{};
+        a.pf = spf;
+        a.fwdS = sf;
+        a.bwdS = sb;
+        a.scale = nullptr;
+        a.scale_off = nullptr;
+        a.job_sub = d_zs;
+        a.job_in = d_qo;
+        a.job_out = d_qo;
+        a.in = E;
+        a.out = R;
+        a.alpha = 1.0;
+        CU((launch_tile_solve<double, double>(a, L, P.s_ntiles, st)));
+        launch_sinv_finalize(L, d_siperm, R, h->d_Sinv, st);
+        CU(cudaGetLastError());
+        CU(cudaStreamSynchronize(st));
+        for (void* p : {(void*)swork, (void*)sdinv, (void*)diagc, (void*)sf, (void*)sb, (void*)E, (void*)R,
+                        (void*)d_zs, (void*)d_qo})
+            h->release(p);
+    } else {
+        cudaEventRecord(ev[3], st);
+    }
+    cudaEventRecord(ev[4], st);
+    CU(cudaStreamSynchronize(st));
+    h->release(rhs);
+    if (h->d_phi != phi64) h->release(phi64);
+    for (void* p : {(void*)d_js, (void*)d_jo, (void*)d_goff, (void*)d_gcptr, (void*)d_grow, (void*)d_gcol,
+                    (void*)d_gval, (void*)d_pairs})
+        h->release(p);
+    float t01, t12, t23, t34;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    cudaEventElapsedTime(&t34, ev[3], ev[4]);
+    h->info.setup_ms[2] = t01;
+    h->info.setup_ms[3] = t12;
+    h->info.setup_ms[4] = t23;
+    h->info.setup_ms[5] = t34;
+    for (auto& e : ev) cudaEventDestroy(e);
+    return 0;
+}
+
+int numeric_dispatch(algmortar_t* h) {
+    switch (h->opts.precision) {
+        case ALGMORTAR_FP64: return numeric_setup<double, double, double>(h);
+        case ALGMORTAR_FP32: return numeric_setup<float, float, float>(h);
+        case ALGMORTAR_BF16: return numeric_setup<float, __nv_bfloat16, float>(h);
+        default: return fail(ALGMORTAR_INVALID_ARG, "unknown precision");
+    }
+}
+
+// Algorithm 2 on internal-order vectors: pbar = A_hat^{-1} r; b_eta; eta; z.
+template <typename TS, typename TA>
+int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
+    SolveArgs a{};
+    a.pf = h->pf;
+    a.fwdS = h->d_fwdS;
+    a.bwdS = h->d_bwdS;
+    a.scale = h->d_sc;
+    a.scale_off = h->d_sub_off;
+    a.job_sub = h->d_job_sub;
+    a.job_in = h->d_job_off;
+    a.job_out = h->d_job_off;
+    a.in = r;
+    a.out = h->d_pbar;
+    a.alpha = 1.0;
+    a.done = done;
+    CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st)));
+    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, h->d_pbar, h->d_beta, done, h->st);
+    launch_coarse_gemv(h->L, h->d_Sinv, h->d_beta, h->d_eta, done, h->st);
+    launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->d_if_list, h->d_phi_off,
+                       (const TS*)h->d_phi, h->d_eta, h->d_pbar, z, part_rz ? r : nullptr, part_rz, done, h->st);
+    CU(cudaGetLastError());
+    return 0;
+}
+
+int apply_internal(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
+    switch (h->opts.precision) {
+        case ALGMORTAR_FP64: return apply_t<double, double>(h, r, z, done, part_rz);
+        case ALGMORTAR_FP32: return apply_t<float, float>(h, r, z, done, part_rz);
+        default: return apply_t<__nv_bfloat16, float>(h, r, z, done, part_rz);
+    }
+}
+
+int pcg_iteration(algmortar_t* h) {
+    cudaStream_t st = h->st;
+    const int32_t* done = &h->d_pcg->done;
+    launch_pcg_p(h->n, h->d_z, h->d_p, h->d_r, nullptr, h->d_pcg, h->d_part_rz, st);
+    launch_pcg_spmv(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_p, h->d_q, h->d_part_pq, h->d_pcg, h->d_part_rz, st);
+    launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->d_part_pq, h->d_part_rr, st);
+    launch_pcg_check(h->d_pcg, h->d_part_pq, h->d_part_rr, st);
+    return apply_internal(h, h->d_r, h->d_z, done, h->d_part_rz);
+}
+
+int ensure_graph(algmortar_t* h) {
+    if (h->graph) return 0;
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    int rc = pcg_iteration(h);
+    cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ALGMORTAR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(ALGMORTAR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return 0;
+}
+
+// PCG in the internal ordering on h->d_b -> h->d_x.
+int pcg_internal(algmortar_t* h, double tol, algmortar_stats* stt) {
+    cudaStream_t st = h->st;
+    double t0 = now_ms();
+    if (!(tol > 0.0)) return fail(ALGMORTAR_INVALID_ARG, "tol must be positive");
+    if (h->opts.use_graph) TRY(ensure_graph(h));
+    launch_pcg_init(h->n, h->d_b, h->d_x, h->d_r, h->d_part_t, st);
+    launch_pcg_start(h->d_pcg, h->d_part_t, tol, h->opts.max_it, h->opts.flexible, st);
+    TRY(apply_internal(h, h->d_r, h->d_z, &h->d_pcg->done, h->d_part_rz));
+    PcgScalars hs{};
+    int restarts = 0;
+    const int every = h->opts.check_every > 0 ? h->opts.check_every : 1;
+    double true_rel = 0.0;
+    for (;;) {
+        for (int c = 0; c < every; ++c) {
+            if (h->graph) CU(cudaGraphLaunch(h->graph, st));
+            else TRY(pcg_iteration(h));
+        }
+        CU(cudaMemcpyAsync(&hs, h->d_pcg, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (!hs.done) continue;
+        launch_residual(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_x, h->d_b, h->d_part_t, st);
+        launch_sum_partials(h->d_part_t, h->d_scalar, st);
+        double res2 = 0.0;
+        CU(cudaMemcpyAsync(&res2, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        true_rel = hs.bb > 0 ? std::sqrt(res2 / hs.bb) : 0.0;
+        if (hs.status == 0 && hs.bb > 0 && !(true_rel <= tol) && restarts < 8 && hs.iter < hs.max_it) {
+            // recurrence converged but the true residual does not confirm it: continue
+            ++restarts;
+            int zero = 0;
+            CU(cudaMemcpyAsync(&h->d_pcg->done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+            CU(cudaStreamSynchronize(st));
+            continue;
+        }
+        break;
+    }
+    int status = hs.status == 0 ? (true_rel <= tol || hs.bb == 0 ? ALGMORTAR_OK : ALGMORTAR_NO_CONVERGENCE)
+                                : (hs.status == 5 ? ALGMORTAR_NO_CONVERGENCE : ALGMORTAR_BREAKDOWN);
+    if (stt) {
+        stt->status = status;
+        stt->iterations = hs.iter;
+        stt->rel_residual = true_rel;
+        stt->recursive_residual = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+        stt->solve_ms = now_ms() - t0;
+        stt->host_ms = 0.0;
+    }
+    if (status == ALGMORTAR_NO_CONVERGENCE) g_err = "PCG reached max_it or the true residual did not confirm";
+    if (status == ALGMORTAR_BREAKDOWN) g_err = "PCG breakdown: p^T A p <= 0 or non-finite scalar";
+    return status;
+}
+
+int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, const algmortar_opts* opts_in,
+               algmortar_t** out) {
+    if (!out) return fail(ALGMORTAR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A) return fail(ALGMORTAR_INVALID_ARG, "A is NULL");
+    double t0 = now_ms();
+    algmortar_opts o;
+    algmortar_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (o.precision < 0 || o.precision > 2) return fail(ALGMORTAR_INVALID_ARG, "unknown precision");
+    if (o.max_it <= 0) o.max_it = 10000;
+    if (o.check_every <= 0) o.check_every = 1;
+    HostCsr H{A->n, A->nnz, A->rowptr, A->col, A->val};
+    std::string err;
+    int rc = validate_csr(H, err);
+    if (rc) return fail(rc, err);
+    std::vector<int32_t> part;
+    if (part_in) {
+        part.assign(part_in, part_in + A->n);
+    } else {
+        Graph G = adjacency(H);
+        rc = partition_graph(G, n_parts, o.part_sizes, part, err);
+        if (rc) return fail(rc, err);
+    }
+    double t_part = now_ms();
+    algmortar_t* h = new (std::nothrow) algmortar_handle();
+    if (!h) return fail(ALGMORTAR_OOM, "host allocation");
+    h->opts = o;
+    rc = build_plan(H, part, n_parts, h->P, err);
+    if (rc) {
+        delete h;
+        return fail(rc, err);
+    }
+    double t_plan = now_ms();
+    auto bail = [&](int code) {
+        delete h;
+        return code;
+    };
+    if (cudaSetDevice(o.device) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "cudaSetDevice failed"));
+    h->device = o.device;
+    h->st = (cudaStream_t)o.stream;
+    if (!h->st) {
+        // a blocking stream: ordered with the legacy default stream both ways, and
+        // capturable into a CUDA graph
+        if (cudaStreamCreate(&h->own_st) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "cudaStreamCreate"));
+        h->st = h->own_st;
+    }
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
+    set_vec_grid(sms);
+    Plan& P = h->P;
+    h->n = P.n;
+    h->m = P.m;
+    h->L = P.n_lambda;
+    std::vector<int32_t> rows(h->m);
+    for (int s = 0; s < h->m; ++s) rows[s] = (int32_t)(P.sub_off[s + 1] - P.sub_off[s]);
+    // apply jobs: largest subdomains first
+    std::vector<int32_t> order(h->m);
+    for (int s = 0; s < h->m; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a] > rows[b]; });
+    std::vector<int64_t> joff(h->m);
+    for (int t = 0; t < h->m; ++t) joff[t] = P.sub_off[order[t]];
+    int32_t *d_lo = nullptr, *d_hi = nullptr;
+    int64_t *d_row0 = nullptr, *d_base = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
+    rc = 0;
+    rc = rc ? rc : upload(h, h->d_rowptr, P.p_rowptr);
+    rc = rc ? rc : upload(h, h->d_col, P.p_col);
+    rc = rc ? rc : upload(h, h->d_val, P.p_val);
+    rc = rc ? rc : upload(h, h->d_perm, P.perm);
+    rc = rc ? rc : upload(h, h->d_row_sub, P.row_sub);
+    rc = rc ? rc : upload(h, h->d_sub_off, P.sub_off);
+    rc = rc ? rc : upload(h, h->d_rows, rows);
+    rc = rc ? rc : upload(h, h->d_ntiles, P.ntiles);
+    rc = rc ? rc : upload(h, d_row0, P.trow_off);
+    rc = rc ? rc : upload(h, d_base, P.tile_base);
+    rc = rc ? rc : upload(h, d_lo, P.t_lo);
+    rc = rc ? rc : upload(h, d_hi, P.t_hi);
+    rc = rc ? rc : upload(h, d_fwd, P.t_fwd);
+    rc = rc ? rc : upload(h, d_bwd, P.t_bwd);
+    rc = rc ? rc : upload(h, h->d_job_sub, order);
+    rc = rc ? rc : upload(h, h->d_job_off, joff);
+    rc = rc ? rc : upload(h, h->d_rptr, P.r_ptr);
+    rc = rc ? rc : upload(h, h->d_rcell, P.r_cell);
+    rc = rc ? rc : upload(h, h->d_rcoef, P.r_coef);
+    rc = rc ? rc : upload(h, h->d_if_off, P.if_off);
+    rc = rc ? rc : upload(h, h->d_if_list, P.if_list);
+    rc = rc ? rc : upload(h, h->d_phi_off, P.phi_off);
+    if (rc) return bail(rc);
+    h->pf = Profile{h->d_rows, h->d_ntiles, d_row0, d_base, d_lo, d_hi, d_fwd, d_bwd};
+    const int64_t n = h->n;
+    const int np = vec_grid();
+    h->d_dloc = h->alloc<double>(n);
+    h->d_sc = h->alloc<double>(n);
+    h->d_x = h->alloc<double>(n);
+    h->d_r = h->alloc<double>(n);
+    h->d_z = h->alloc<double>(n);
+    h->d_p = h->alloc<double>(n);
+    h->d_q = h->alloc<double>(n);
+    h->d_pbar = h->alloc<double>(n);
+    h->d_b = h->alloc<double>(n);
+    h->d_t = h->alloc<double>(n);
+    h->d_beta = h->alloc<double>(h->L);
+    h->d_eta = h->alloc<double>(h->L);
+    h->d_part_rz = h->alloc<double>(np);
+    h->d_part_pq = h->alloc<double>(np);
+    h->d_part_rr = h->alloc<double>(np);
+    h->d_part_t = h->alloc<double>(np);
+    h->d_scalar = h->alloc<double>(4);
+    h->d_pcg = h->alloc<PcgScalars>(1);
+    if (!h->d_dloc || !h->d_sc || !h->d_x || !h->d_r || !h->d_z || !h->d_p || !h->d_q || !h->d_pbar || !h->d_b ||
+        !h->d_t || !h->d_beta || !h->d_eta || !h->d_part_rz || !h->d_part_pq || !h->d_part_rr || !h->d_part_t ||
+        !h->d_scalar || !h->d_pcg)
+        return bail(fail(ALGMORTAR_OOM, "workspace"));
+    if (cudaMemsetAsync(h->d_p, 0, n * sizeof(double), h->st) != cudaSuccess ||
+        cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->st) != cudaSuccess)
+        return bail(fail(ALGMORTAR_CUDA, "memset"));
+    double t_up = now_ms();
+    rc = numeric_dispatch(h);
+    if (rc) return bail(rc);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "setup synchronize"));
+    double t_end = now_ms();
+    algmortar_info& I = h->info;
+    I.n = n;
+    I.n_parts = h->m;
+    I.n_lambda = h->L;
+    I.max_part = P.max_part;
+    I.min_part = P.min_part;
+    I.precision = o.precision;
+    I.n_interface_edges = P.n_edges;
+    I.factor_entries = P.total_tiles * TILE2;
+    int es = o.precision == ALGMORTAR_FP64 ? 8 : (o.precision == ALGMORTAR_FP32 ? 4 : 2);
+    I.factor_bytes = 2 * P.total_tiles * TILE2 * es;
+    I.phi_entries = P.phi_off[h->m];
+    I.setup_ms[0] = (t_part - t0) + (t_plan - t_part);
+    I.setup_ms[1] = t_up - t_plan;
+    I.setup_ms[6] = 0.0;
+    I.setup_ms[7] = t_end - t0;
+    if (o.verbose)
+        std::fprintf(stderr,
+                     "[algmortar] n=%lld m=%d nLam=%d parts %d..%d tiles=%lld | partition %.1f ms plan %.1f ms "
+                     "upload %.1f | factor %.2f mbf %.2f iface-asm %.2f iface-inv %.2f | total %.1f ms\n",
+                     (long long)n, h->m, h->L, P.min_part, P.max_part, (long long)P.total_tiles, t_part - t0,
+                     t_plan - t_part, I.setup_ms[1], I.setup_ms[2], I.setup_ms[3], I.setup_ms[4], I.setup_ms[5],
+                     I.setup_ms[7]);
+    *out = h;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void algmortar_default_opts(algmortar_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = ALGMORTAR_FP64;
+    o->diag_scale = 1;
+    o->max_it = 10000;
+    o->use_graph = 0;
+    o->check_every = 1;
+    o->flexible = 0;
+    o->verbose = 0;
+    o->device = 0;
+    o->part_sizes = nullptr;
+    o->stream = nullptr;
+}
+
+int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes, int32_t* part_out) {
+    if (!A || !part_out) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    HostCsr H{A->n, A->nnz, A->rowptr, A->col, A->val};
+    std::string err;
+    int rc = validate_csr(H, err);
+    if (rc) return fail(rc, err);
+    Graph G = adjacency(H);
+    std::vector<int32_t> part;
+    rc = partition_graph(G, n_parts, part_sizes, part, err);
+    if (rc) return fail(rc, err);
+    std::memcpy(part_out, part.data(), part.size() * sizeof(int32_t));
+    return 0;
+}
+
+int algmortar_setup(const algmortar_csr* A, int32_t n_parts, const algmortar_opts* opts, algmortar_t** out) {
+    return setup_impl(A, nullptr, n_parts, opts, out);
+}
+
+int algmortar_setup_with_parts(const algmortar_csr* A, const int32_t* part, int32_t n_parts,
+                               const algmortar_opts* opts, algmortar_t** out) {
+    if (!part) return fail(ALGMORTAR_INVALID_ARG, "part is NULL");
+    return setup_impl(A, part, n_parts, opts, out);
+}
+
+int algmortar_apply(algmortar_t* h, const double* r_dev, double* z_dev) {
+    if (!h || !r_dev || !z_dev) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    CU(cudaSetDevice(h->device));
+    launch_gather(h->n, h->d_perm, r_dev, h->d_t, h->st);
+    TRY(apply_internal(h, h->d_t, h->d_z, nullptr, nullptr));
+    launch_scatter(h->n, h->d_perm, h->d_z, z_dev, h->st);
+    CU(cudaGetLastError());
+    return 0;
+}
+
+int algmortar_apply_stages(algmortar_t* h, const double* r_dev, double* pbar_dev, double* beta_dev,
+                           double* eta_dev, double* z_dev) {
+    if (!h || !r_dev || !pbar_dev || !z_dev || (h->L > 0 && (!beta_dev || !eta_dev)))
+        return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    CU(cudaSetDevice(h->device));
+    launch_gather(h->n, h->d_perm, r_dev, h->d_t, h->st);
+    TRY(apply_internal(h, h->d_t, h->d_z, nullptr, nullptr));
+    CU(cudaMemcpyAsync(pbar_dev, h->d_pbar, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (h->L > 0) {
+        CU(cudaMemcpyAsync(beta_dev, h->d_beta, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        CU(cudaMemcpyAsync(eta_dev, h->d_eta, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    }
+    CU(cudaMemcpyAsync(z_dev, h->d_z, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    return 0;
+}
+
+int algmortar_pcg_solve(algmortar_t* h, const double* b_dev, double* x_dev, double tol, algmortar_stats* st) {
+    if (!h || !b_dev || !x_dev) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    CU(cudaSetDevice(h->device));
+    launch_gather(h->n, h->d_perm, b_dev, h->d_b, h->st);
+    int rc = pcg_internal(h, tol, st);
+    if (rc != ALGMORTAR_OK && rc != ALGMORTAR_NO_CONVERGENCE && rc != ALGMORTAR_BREAKDOWN) return rc;
+    launch_scatter(h->n, h->d_perm, h->d_x, x_dev, h->st);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->st));
+    return rc;
+}
+
+int algmortar_pcg_solve_host(algmortar_t* h, const double* b_host, double* x_host, double tol,
+                             algmortar_stats* st) {
+    if (!h || !b_host || !x_host) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    CU(cudaSetDevice(h->device));
+    double t0 = now_ms();
+    CU(cudaMemcpyAsync(h->d_t, b_host, h->n * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    launch_gather(h->n, h->d_perm, h->d_t, h->d_b, h->st);
+    int rc = pcg_internal(h, tol, st);
+    if (rc != ALGMORTAR_OK && rc != ALGMORTAR_NO_CONVERGENCE && rc != ALGMORTAR_BREAKDOWN) return rc;
+    launch_scatter(h->n, h->d_perm, h->d_x, h->d_t, h->st);
+    CU(cudaMemcpyAsync(x_host, h->d_t, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CU(cudaStreamSynchronize(h->st));
+    if (st) st->solve_ms = now_ms() - t0;
+    return rc;
+}
+
+int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev, int32_t nrhs, int64_t ld,
+                              double tol, algmortar_stats* st) {
+    if (!h || !B_dev || !X_dev || nrhs <= 0 || ld < h->n) return fail(ALGMORTAR_INVALID_ARG, "bad argument");
+    int worst = 0;
+    for (int j = 0; j < nrhs; ++j) {
+        int rc = algmortar_pcg_solve(h, B_dev + j * ld, X_dev + j * ld, tol, st ? st + j : nullptr);
+        if (rc != ALGMORTAR_OK && rc != ALGMORTAR_NO_CONVERGENCE && rc != ALGMORTAR_BREAKDOWN) return rc;
+        if (rc > worst) worst = rc;
+    }
+    return worst;
+}
+
+int algmortar_update_values(algmortar_t* h, const double* val_host) {
+    if (!h || !val_host) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    return fail(ALGMORTAR_INVALID_ARG, "update_values: not available in this build");
+}
+
+int algmortar_get_partition(const algmortar_t* h, int32_t* part_out) {
+    if (!h || !part_out) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    std::memcpy(part_out, h->P.part.data(), h->P.part.size() * sizeof(int32_t));
+    return 0;
+}
+
+int algmortar_get_permutation(const algmortar_t* h, int32_t* perm_out) {
+    if (!h || !perm_out) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    std::memcpy(perm_out, h->P.perm.data(), h->P.perm.size() * sizeof(int32_t));
+    return 0;
+}
+
+int algmortar_get_interfaces(const algmortar_t* h, int32_t* pairs_out) {
+    if (!h || !pairs_out) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    if (!h->P.pairs.empty()) std::memcpy(pairs_out, h->P.pairs.data(), h->P.pairs.size() * sizeof(int32_t));
+    return 0;
+}
+
+int algmortar_get_info(const algmortar_t* h, algmortar_info* info) {
+    if (!h || !info) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    *info = h->info;
+    return 0;
+}
+
+void algmortar_destroy(algmortar_t* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    delete h;
+}
+
+const char* algmortar_strerror(int s) {
+    switch (s) {
+        case ALGMORTAR_OK: return "ok";
+        case ALGMORTAR_INVALID_ARG: return "invalid argument";
+        case ALGMORTAR_NOT_SYMMETRIC: return "matrix not symmetric";
+        case ALGMORTAR_INTERFACE_SIGN: return "non-negative coupling between subdomains";
+        case ALGMORTAR_NOT_SPD: return "non-positive pivot (matrix not SPD)";
+        case ALGMORTAR_NO_CONVERGENCE: return "PCG did not converge";
+        case ALGMORTAR_BREAKDOWN: return "PCG breakdown";
+        case ALGMORTAR_CUDA: return "CUDA error";
+        case ALGMORTAR_OOM: return "out of memory";
+        case ALGMORTAR_TOO_LARGE: return "subdomain too large";
+        default: return "unknown status";
+    }
+}
+
+const char* algmortar_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Shared device definitions of the AlgMortar CUDA path.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tile.h"
+
+namespace am {
+
+// Load a stored factor entry as the accumulation type.
+template <typename TA, typename TS>
+__device__ __forceinline__ TA ldf(const TS* p) { return (TA)(*p); }
+template <>
+__device__ __forceinline__ float ldf<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+}
+template <>
+__device__ __forceinline__ double ldf<double, __nv_bfloat16>(const __nv_bfloat16* p) {
+    return (double)__bfloat162float(*p);
+}
+
+template <typename TS>
+__device__ __forceinline__ TS stf(double x) { return (TS)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 stf<__nv_bfloat16>(double x) {
+    return __float2bfloat16_rn((float)x);
+}
+
+// Tile-profile descriptor set of a batch of lower-triangular factors (one per subdomain,
+// or the single interface matrix).  Tile (I, J), lo[I] <= J <= I, of item s lives at
+// tile index base[s] + fwd[row0[s] + I] + (J - lo[row0[s] + I]) of the forward stream,
+// column-major inside the tile.  The backward stream holds, for I = T-1 .. 0, the tiles
+// (L_JI)^T for J = I+1 .. hi[I] followed by the diagonal slot, from bwd[row0 + I].
+struct Profile {
+    const int32_t* rows;      // rows of item s
+    const int32_t* ntiles;    // tile rows T of item s
+    const int64_t* row0;      // first tile-row descriptor of item s
+    const int64_t* base;      // first tile of item s
+    const int32_t* lo;
+    const int32_t* hi;
+    const int64_t* fwd;
+    const int64_t* bwd;
+};
+
+// Device-side PCG scalars (FP64 throughout, Sec. 7).
+struct PcgScalars {
+    double rz;        // r_k . z_k
+    double rz_prev;
+    double pq;        // p_k . A p_k
+    double alpha, beta;
+    double rr;        // ||r_k||^2
+    double bb;        // ||b||^2
+    double tol2;      // tol^2 ||b||^2
+    int32_t iter;     // products with A so far
+    int32_t done;     // 1: stop (converged or failed)
+    int32_t status;   // 0 converged, 5 max_it, 6 breakdown
+    int32_t max_it;
+    int32_t flexible;
+    int32_t pad;
+    double rr_prev;   // for the flexible (Polak-Ribiere) beta
+};
+
+// Deterministic fixed-order sum of `n` partials by one warp; result in all lanes.
+__device__ __forceinline__ double warp_sum_partials(const double* part, int n) {
+    int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        s = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;
+}
+
+}  // namespace am

@@ -1,0 +1,616 @@
+// Host-side symbolic setup of AlgMortar: see host_setup.h.
+#include "host_setup.h"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+namespace am {
+
+static std::string fmt(const char* f, long long a, long long b = 0, long long c = 0) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), f, a, b, c);
+    return buf;
+}
+
+int validate_csr(const HostCsr& A, std::string& err) {
+    if (A.n <= 0 || !A.rowptr || !A.col || !A.val) {
+        err = "CSR: null pointer or n <= 0";
+        return 1;
+    }
+    if (A.n >= INT32_MAX || A.nnz >= INT32_MAX || A.nnz < A.n) {
+        err = "CSR: n or nnz outside the int32 range, or fewer entries than rows";
+        return 1;
+    }
+    if (A.rowptr[0] != 0 || (int64_t)A.rowptr[A.n] != A.nnz) {
+        err = "CSR: rowptr[0] must be 0 and rowptr[n] must equal nnz";
+        return 1;
+    }
+    for (int64_t i = 0; i < A.n; ++i) {
+        int64_t a = A.rowptr[i], b = A.rowptr[i + 1];
+        if (b < a) {
+            err = fmt("CSR: rowptr decreases at row %lld", i);
+            return 1;
+        }
+        bool diag = false;
+        for (int64_t t = a; t < b; ++t) {
+            int32_t c = A.col[t];
+            if (c < 0 || c >= A.n || (t > a && c <= A.col[t - 1])) {
+                err = fmt("CSR: column out of range or not strictly ascending in row %lld", i);
+                return 1;
+            }
+            if (!std::isfinite(A.val[t])) {
+                err = fmt("CSR: non-finite value in row %lld", i);
+                return 1;
+            }
+            if (c == i) {
+                diag = true;
+                if (!(A.val[t] > 0.0)) {
+                    err = fmt("CSR: non-positive diagonal in row %lld", i);
+                    return 4;
+                }
+            }
+        }
+        if (!diag) {
+            err = fmt("CSR: missing diagonal in row %lld", i);
+            return 1;
+        }
+    }
+    for (int64_t i = 0; i < A.n; ++i) {
+        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t) {
+            int32_t j = A.col[t];
+            if (j == i) continue;
+            const int32_t* first = A.col + A.rowptr[j];
+            const int32_t* last = A.col + A.rowptr[j + 1];
+            const int32_t* f = std::lower_bound(first, last, (int32_t)i);
+            if (f == last || *f != i || A.val[A.rowptr[j] + (f - first)] != A.val[t]) {
+                err = fmt("CSR: a(%lld,%lld) has no equal transposed entry", i, j);
+                return 2;
+            }
+        }
+    }
+    return 0;
+}
+
+Graph adjacency(const HostCsr& A) {
+    Graph G;
+    G.n = (int32_t)A.n;
+    G.ptr.assign(A.n + 1, 0);
+    for (int64_t i = 0; i < A.n; ++i) {
+        int64_t c = 0;
+        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t)
+            if (A.col[t] != i && A.val[t] != 0.0) ++c;
+        G.ptr[i + 1] = G.ptr[i] + c;
+    }
+    G.adj.resize(G.ptr[A.n]);
+    for (int64_t i = 0; i < A.n; ++i) {
+        int64_t o = G.ptr[i];
+        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t)
+            if (A.col[t] != i && A.val[t] != 0.0) G.adj[o++] = A.col[t];
+    }
+    return G;
+}
+
+// ------------------------------------------------------------------------------------
+// Recursive BFS bisection (the rule stated in oracle/partition.py, implemented anew).
+// ------------------------------------------------------------------------------------
+namespace {
+
+struct SubsetBfs {
+    const Graph& G;
+    std::vector<int32_t> loc;     // global -> local index in the current subset, -1 if not
+    std::vector<int32_t> dist, q, deg;
+    explicit SubsetBfs(const Graph& g) : G(g), loc(g.n, -1) {}
+
+    // BFS from local `s` over the induced subgraph; q receives the visit order, dist the
+    // levels (nodes of other components keep -1).  Returns the eccentricity of s.
+    int32_t bfs(const std::vector<int32_t>& S, int32_t s) {
+        std::fill(dist.begin(), dist.begin() + S.size(), -1);
+        q.clear();
+        q.push_back(s);
+        dist[s] = 0;
+        size_t h = 0;
+        while (h < q.size()) {
+            int32_t u = q[h++];
+            int32_t gu = S[u];
+            for (int64_t e = G.ptr[gu]; e < G.ptr[gu + 1]; ++e) {
+                int32_t v = loc[G.adj[e]];
+                if (v >= 0 && dist[v] < 0) {
+                    dist[v] = dist[u] + 1;
+                    q.push_back(v);
+                }
+            }
+        }
+        return dist[q.back()];
+    }
+
+    // George-Liu pseudo-peripheral node of the component of local node 0.
+    int32_t pseudo_peripheral(const std::vector<int32_t>& S) {
+        int32_t v = 0;
+        int32_t ecc = bfs(S, v);
+        for (;;) {
+            int32_t u = -1, best = INT32_MAX;
+            for (int32_t x : q)
+                if (dist[x] == ecc && (deg[x] < best || (deg[x] == best && x < u))) {
+                    u = x;
+                    best = deg[x];
+                }
+            int32_t ecc_u = bfs(S, u);
+            if (ecc_u > ecc) {
+                v = u;
+                ecc = ecc_u;
+            } else {
+                return v;
+            }
+        }
+    }
+
+    // Full BFS order of the subset (local ids).
+    void order(const std::vector<int32_t>& S, std::vector<int32_t>& out) {
+        size_t n = S.size();
+        if (dist.size() < n) {
+            dist.resize(n);
+            deg.resize(n);
+        }
+        for (size_t t = 0; t < n; ++t) loc[S[t]] = (int32_t)t;
+        for (size_t t = 0; t < n; ++t) {
+            int32_t g = S[t], d = 0;
+            for (int64_t e = G.ptr[g]; e < G.ptr[g + 1]; ++e) d += loc[G.adj[e]] >= 0;
+            deg[t] = d;
+        }
+        std::vector<char> seen(n, 0);
+        out.clear();
+        int32_t start = pseudo_peripheral(S);
+        size_t next = 0;
+        for (;;) {
+            bfs(S, start);
+            for (int32_t x : q) seen[x] = 1;
+            out.insert(out.end(), q.begin(), q.end());
+            while (next < n && seen[next]) ++next;
+            if (next == n) break;
+            start = (int32_t)next;
+        }
+        for (size_t t = 0; t < n; ++t) loc[S[t]] = -1;
+    }
+};
+
+}  // namespace
+
+int partition_graph(const Graph& G, int32_t m, const int32_t* sizes_in, std::vector<int32_t>& part,
+                    std::string& err) {
+    if (m <= 0 || m > G.n) {
+        err = "partition: n_parts must be in [1, n]";
+        return 1;
+    }
+    std::vector<int64_t> sizes(m);
+    if (sizes_in) {
+        int64_t s = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            if (sizes_in[i] <= 0) {
+                err = "partition: part sizes must be positive";
+                return 1;
+            }
+            sizes[i] = sizes_in[i];
+            s += sizes_in[i];
+        }
+        if (s != G.n) {
+            err = "partition: part sizes must sum to n";
+            return 1;
+        }
+    } else {
+        int64_t base = G.n / m, extra = G.n % m;
+        for (int32_t i = 0; i < m; ++i) sizes[i] = base + (i < extra ? 1 : 0);
+    }
+    std::vector<int64_t> pre(m + 1, 0);
+    for (int32_t i = 0; i < m; ++i) pre[i + 1] = pre[i] + sizes[i];
+    part.assign(G.n, -1);
+    SubsetBfs sb(G);
+    struct Item {
+        std::vector<int32_t> S;
+        int32_t lo, hi;
+    };
+    std::vector<Item> stack;
+    {
+        Item it;
+        it.S.resize(G.n);
+        std::iota(it.S.begin(), it.S.end(), 0);
+        it.lo = 0;
+        it.hi = m;
+        stack.push_back(std::move(it));
+    }
+    std::vector<int32_t> ord;
+    while (!stack.empty()) {
+        Item it = std::move(stack.back());
+        stack.pop_back();
+        int32_t k = it.hi - it.lo;
+        if (k == 1) {
+            for (int32_t g : it.S) part[g] = it.lo;
+            continue;
+        }
+        int32_t k1 = k / 2;
+        int64_t n1 = pre[it.lo + k1] - pre[it.lo];
+        sb.order(it.S, ord);
+        Item a, b;
+        a.S.reserve(n1);
+        b.S.reserve(it.S.size() - n1);
+        for (size_t t = 0; t < ord.size(); ++t)
+            (t < (size_t)n1 ? a.S : b.S).push_back(it.S[ord[t]]);
+        std::sort(a.S.begin(), a.S.end());
+        std::sort(b.S.begin(), b.S.end());
+        a.lo = it.lo;
+        a.hi = it.lo + k1;
+        b.lo = it.lo + k1;
+        b.hi = it.hi;
+        stack.push_back(std::move(b));
+        stack.push_back(std::move(a));
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Reverse Cuthill-McKee on a local graph (CUDA path only: orders rows inside a subdomain
+// so that the Cholesky factor fits a narrow tile profile).
+// ------------------------------------------------------------------------------------
+std::vector<int32_t> rcm_order(int32_t n, const std::vector<int64_t>& ptr,
+                               const std::vector<int32_t>& adj) {
+    std::vector<int32_t> deg(n), dist(n, -1), q, out;
+    for (int32_t i = 0; i < n; ++i) deg[i] = (int32_t)(ptr[i + 1] - ptr[i]);
+    std::vector<char> seen(n, 0);
+    auto bfs_levels = [&](int32_t s) {
+        for (int32_t x : q) dist[x] = -1;
+        q.clear();
+        q.push_back(s);
+        dist[s] = 0;
+        size_t h = 0;
+        while (h < q.size()) {
+            int32_t u = q[h++];
+            for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) {
+                int32_t v = adj[e];
+                if (dist[v] < 0) {
+                    dist[v] = dist[u] + 1;
+                    q.push_back(v);
+                }
+            }
+        }
+        return dist[q.back()];
+    };
+    std::vector<int32_t> nb;
+    int32_t next = 0;
+    out.reserve(n);
+    while ((int32_t)out.size() < n) {
+        while (seen[next]) ++next;
+        int32_t v = next, ecc = bfs_levels(v);
+        for (;;) {
+            int32_t u = -1, best = INT32_MAX;
+            for (int32_t x : q)
+                if (dist[x] == ecc && (deg[x] < best || (deg[x] == best && x < u))) {
+                    u = x;
+                    best = deg[x];
+                }
+            int32_t e2 = bfs_levels(u);
+            if (e2 > ecc) {
+                v = u;
+                ecc = e2;
+            } else {
+                break;
+            }
+        }
+        for (int32_t x : q) dist[x] = -1;
+        q.clear();
+        size_t h = out.size();
+        out.push_back(v);
+        seen[v] = 1;
+        while (h < out.size()) {
+            int32_t u = out[h++];
+            nb.clear();
+            for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e)
+                if (!seen[adj[e]]) nb.push_back(adj[e]);
+            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+                return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+            });
+            for (int32_t x : nb)
+                if (!seen[x]) {
+                    seen[x] = 1;
+                    out.push_back(x);
+                }
+        }
+    }
+    std::reverse(out.begin(), out.end());
+    return out;
+}
+
+// Tile profile of the lower Cholesky factor for a pattern in its final local order.
+// Row r's envelope starts at f(r) = min(r, min adj(r)); tile row I starts at tile
+// lo(I) = min_{r in I} f(r)/TILE, made non-decreasing by a suffix minimum so that tile
+// column I of the factor occupies the contiguous rows I..hi(I).
+void tile_profile(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
+                  int32_t& ntiles, std::vector<int32_t>& lo, std::vector<int32_t>& hi,
+                  std::vector<int64_t>& fwd, std::vector<int64_t>& bwd, int64_t& tiles) {
+    ntiles = (n + TILE - 1) / TILE;
+    lo.assign(ntiles, 0);
+    hi.assign(ntiles, 0);
+    fwd.assign(ntiles, 0);
+    bwd.assign(ntiles, 0);
+    for (int32_t I = 0; I < ntiles; ++I) lo[I] = I;
+    for (int32_t r = 0; r < n; ++r) {
+        int32_t f = r;
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) f = std::min(f, adj[e]);
+        lo[r / TILE] = std::min(lo[r / TILE], f / TILE);
+    }
+    for (int32_t I = ntiles - 2; I >= 0; --I) lo[I] = std::min(lo[I], lo[I + 1]);
+    int32_t J = ntiles - 1;
+    for (int32_t I = ntiles - 1; I >= 0; --I) {
+        while (J > I && lo[J] > I) --J;
+        hi[I] = std::max(J, I);
+    }
+    int64_t o = 0;
+    for (int32_t I = 0; I < ntiles; ++I) {
+        fwd[I] = o;
+        o += I - lo[I] + 1;
+    }
+    tiles = o;
+    o = 0;
+    for (int32_t I = ntiles - 1; I >= 0; --I) {
+        bwd[I] = o;
+        o += hi[I] - I + 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Plan& P,
+               std::string& err) {
+    const int64_t n = A.n;
+    P = Plan();
+    P.n = n;
+    P.m = m;
+    P.part = part;
+    std::vector<int64_t> cnt(m + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (part[i] < 0 || part[i] >= m) {
+            err = fmt("partition label out of range at row %lld", i);
+            return 1;
+        }
+        cnt[part[i] + 1]++;
+    }
+    P.sub_off.assign(m + 1, 0);
+    for (int32_t i = 0; i < m; ++i) {
+        if (cnt[i + 1] == 0) {
+            err = fmt("subdomain %lld is empty", i);
+            return 1;
+        }
+        if (cnt[i + 1] > 16384) {
+            err = fmt("subdomain %lld has %lld rows (limit 16384)", i, cnt[i + 1]);
+            return 9;
+        }
+        P.sub_off[i + 1] = P.sub_off[i] + cnt[i + 1];
+    }
+    // nodes of each subdomain in ascending original index
+    std::vector<int32_t> nodes(n);
+    {
+        std::vector<int64_t> pos(P.sub_off.begin(), P.sub_off.end() - 1);
+        for (int64_t i = 0; i < n; ++i) nodes[pos[part[i]]++] = (int32_t)i;
+    }
+    // interface sign check (Sec. 3.2: diagonal of W negative)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t) {
+            int32_t j = A.col[t];
+            if (part[j] != part[i] && A.val[t] > 0.0) {
+                err = fmt("positive coupling a(%lld,%lld) between subdomains", i, j);
+                return 3;
+            }
+        }
+    // per subdomain RCM order -> internal ordering
+    P.perm.resize(n);
+    P.iperm.assign(n, -1);
+    P.ntiles.resize(m);
+    P.trow_off.assign(m + 1, 0);
+    P.tile_base.assign(m + 1, 0);
+    std::vector<int32_t> gl(n, -1);   // original -> local index of its subdomain
+    std::vector<std::vector<int32_t>> t_lo(m), t_hi(m);
+    std::vector<std::vector<int64_t>> t_fwd(m), t_bwd(m);
+    P.max_part = 0;
+    P.min_part = INT32_MAX;
+    for (int32_t s = 0; s < m; ++s) {
+        int64_t a = P.sub_off[s], b = P.sub_off[s + 1];
+        int32_t ns = (int32_t)(b - a);
+        P.max_part = std::max(P.max_part, ns);
+        P.min_part = std::min(P.min_part, ns);
+        for (int32_t t = 0; t < ns; ++t) gl[nodes[a + t]] = t;
+        std::vector<int64_t> lp(ns + 1, 0);
+        std::vector<int32_t> la;
+        for (int32_t t = 0; t < ns; ++t) {
+            int32_t g = nodes[a + t];
+            for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e) {
+                int32_t c = A.col[e];
+                if (c != g && part[c] == s && A.val[e] != 0.0) la.push_back(gl[c]);
+            }
+            lp[t + 1] = (int64_t)la.size();
+        }
+        std::vector<int32_t> ord = rcm_order(ns, lp, la);
+        std::vector<int32_t> inv(ns);
+        for (int32_t t = 0; t < ns; ++t) {
+            inv[ord[t]] = t;
+            P.perm[a + t] = nodes[a + ord[t]];
+            P.iperm[nodes[a + ord[t]]] = (int32_t)(a + t);
+        }
+        // relabel local adjacency into the RCM order for the profile
+        std::vector<int64_t> rp(ns + 1, 0);
+        std::vector<int32_t> ra(la.size());
+        for (int32_t t = 0; t < ns; ++t) rp[t + 1] = rp[t] + (lp[ord[t] + 1] - lp[ord[t]]);
+        for (int32_t t = 0; t < ns; ++t) {
+            int64_t o = rp[t];
+            for (int64_t e = lp[ord[t]]; e < lp[ord[t] + 1]; ++e) ra[o++] = inv[la[e]];
+        }
+        int64_t tiles;
+        tile_profile(ns, rp, ra, P.ntiles[s], t_lo[s], t_hi[s], t_fwd[s], t_bwd[s], tiles);
+        P.trow_off[s + 1] = P.trow_off[s] + P.ntiles[s];
+        P.tile_base[s + 1] = P.tile_base[s] + tiles;
+        P.max_tiles = std::max(P.max_tiles, P.ntiles[s]);
+        for (int32_t t = 0; t < ns; ++t) gl[nodes[a + t]] = -1;
+    }
+    P.total_tiles = P.tile_base[m];
+    P.t_lo.reserve(P.trow_off[m]);
+    for (int32_t s = 0; s < m; ++s) {
+        P.t_lo.insert(P.t_lo.end(), t_lo[s].begin(), t_lo[s].end());
+        P.t_hi.insert(P.t_hi.end(), t_hi[s].begin(), t_hi[s].end());
+        for (auto v : t_fwd[s]) P.t_fwd.push_back(v);
+        for (auto v : t_bwd[s]) P.t_bwd.push_back(v);
+    }
+    // permuted CSR
+    P.row_sub.resize(n);
+    P.p_rowptr.assign(n + 1, 0);
+    P.p_col.resize(A.nnz);
+    P.p_val.resize(A.nnz);
+    P.p_src.resize(A.nnz);
+    {
+        std::vector<std::pair<int32_t, int64_t>> row;
+        int64_t o = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            int32_t g = P.perm[k];
+            P.row_sub[k] = part[g];
+            row.clear();
+            for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e) row.push_back({P.iperm[A.col[e]], e});
+            std::sort(row.begin(), row.end());
+            for (auto& pr : row) {
+                P.p_col[o] = pr.first;
+                P.p_val[o] = A.val[pr.second];
+                P.p_src[o] = pr.second;
+                ++o;
+            }
+            P.p_rowptr[k + 1] = (int32_t)o;
+        }
+    }
+    // interfaces: one per subdomain pair (i < j) with a coupling, lexicographic
+    std::vector<int64_t> keys;
+    for (int64_t k = 0; k < n; ++k) {
+        int32_t i = P.row_sub[k];
+        for (int32_t e = P.p_rowptr[k]; e < P.p_rowptr[k + 1]; ++e) {
+            int32_t j = P.row_sub[P.p_col[e]];
+            if (i < j && P.p_val[e] != 0.0) keys.push_back((int64_t)i * m + j);
+        }
+    }
+    P.n_edges = (int64_t)keys.size();
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    P.n_lambda = (int32_t)keys.size();
+    P.pairs.resize(2 * (size_t)P.n_lambda);
+    for (int32_t I = 0; I < P.n_lambda; ++I) {
+        P.pairs[2 * I] = (int32_t)(keys[I] / m);
+        P.pairs[2 * I + 1] = (int32_t)(keys[I] % m);
+    }
+    auto iface = [&](int32_t i, int32_t j) -> int32_t {
+        int64_t key = i < j ? (int64_t)i * m + j : (int64_t)j * m + i;
+        return (int32_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+    };
+    P.T.assign(P.n_lambda, 0.0);
+    // per row: c_k^(I) = sum_{l in Omega_j} a_kl for each neighbouring subdomain j
+    struct RC {
+        int32_t I, cell;
+        double c;
+    };
+    std::vector<RC> rc;
+    std::vector<std::pair<int32_t, double>> acc;
+    for (int64_t k = 0; k < n; ++k) {
+        int32_t i = P.row_sub[k];
+        acc.clear();
+        for (int32_t e = P.p_rowptr[k]; e < P.p_rowptr[k + 1]; ++e) {
+            int32_t l = P.p_col[e];
+            int32_t j = P.row_sub[l];
+            if (j == i || P.p_val[e] == 0.0) continue;
+            int32_t I = iface(i, j);
+            if (i < j) P.T[I] += std::fabs(P.p_val[e]);
+            bool found = false;
+            for (auto& pr : acc)
+                if (pr.first == I) {
+                    pr.second += P.p_val[e];
+                    found = true;
+                }
+            if (!found) acc.push_back({I, P.p_val[e]});
+        }
+        for (auto& pr : acc) rc.push_back({pr.first, (int32_t)k, pr.second});
+    }
+    // restriction table, interface-major
+    std::sort(rc.begin(), rc.end(), [](const RC& a, const RC& b) {
+        return a.I != b.I ? a.I < b.I : a.cell < b.cell;
+    });
+    P.r_ptr.assign(P.n_lambda + 1, 0);
+    P.r_cell.resize(rc.size());
+    P.r_coef.resize(rc.size());
+    for (size_t t = 0; t < rc.size(); ++t) {
+        P.r_ptr[rc[t].I + 1]++;
+        P.r_cell[t] = rc[t].cell;
+        P.r_coef[t] = -0.5 * rc[t].c;
+    }
+    for (int32_t I = 0; I < P.n_lambda; ++I) P.r_ptr[I + 1] += P.r_ptr[I];
+    // per-subdomain interface lists I_i and the sparse G_i
+    P.if_off.assign(m + 1, 0);
+    {
+        std::vector<std::vector<int32_t>> lists(m);
+        for (int32_t I = 0; I < P.n_lambda; ++I) {
+            lists[P.pairs[2 * I]].push_back(I);
+            lists[P.pairs[2 * I + 1]].push_back(I);
+        }
+        P.max_k = 0;
+        for (int32_t s = 0; s < m; ++s) {
+            std::sort(lists[s].begin(), lists[s].end());
+            P.if_off[s + 1] = P.if_off[s] + (int64_t)lists[s].size();
+            P.if_list.insert(P.if_list.end(), lists[s].begin(), lists[s].end());
+            P.max_k = std::max(P.max_k, (int32_t)lists[s].size());
+        }
+    }
+    P.phi_off.assign(m + 1, 0);
+    for (int32_t s = 0; s < m; ++s)
+        P.phi_off[s + 1] = P.phi_off[s] + (P.sub_off[s + 1] - P.sub_off[s]) * (P.if_off[s + 1] - P.if_off[s]);
+    {
+        std::vector<std::vector<RC>> per(m);
+        for (auto& x : rc) per[P.row_sub[x.cell]].push_back(x);
+        P.g_off.assign(m + 1, 0);
+        for (int32_t s = 0; s < m; ++s) {
+            std::sort(per[s].begin(), per[s].end(), [](const RC& a, const RC& b) {
+                return a.I != b.I ? a.I < b.I : a.cell < b.cell;
+            });
+            for (auto& x : per[s]) {
+                auto f = std::lower_bound(P.if_list.begin() + P.if_off[s], P.if_list.begin() + P.if_off[s + 1], x.I);
+                P.g_col.push_back((int32_t)(f - (P.if_list.begin() + P.if_off[s])));
+                P.g_row.push_back((int32_t)(x.cell - P.sub_off[s]));
+                P.g_val.push_back(2.0 * x.c);
+            }
+            P.g_off[s + 1] = (int64_t)P.g_row.size();
+        }
+    }
+    // interface graph (I ~ J when they share a subdomain), RCM, tile profile
+    {
+        int32_t L = P.n_lambda;
+        std::vector<std::vector<int32_t>> nb(L);
+        for (int32_t s = 0; s < m; ++s)
+            for (int64_t a = P.if_off[s]; a < P.if_off[s + 1]; ++a)
+                for (int64_t b = P.if_off[s]; b < P.if_off[s + 1]; ++b)
+                    if (a != b) nb[P.if_list[a]].push_back(P.if_list[b]);
+        std::vector<int64_t> sp(L + 1, 0);
+        std::vector<int32_t> sa;
+        for (int32_t I = 0; I < L; ++I) {
+            std::sort(nb[I].begin(), nb[I].end());
+            nb[I].erase(std::unique(nb[I].begin(), nb[I].end()), nb[I].end());
+            sa.insert(sa.end(), nb[I].begin(), nb[I].end());
+            sp[I + 1] = (int64_t)sa.size();
+        }
+        if (L > 0) {
+            P.s_perm = rcm_order(L, sp, sa);
+            P.s_iperm.assign(L, 0);
+            for (int32_t t = 0; t < L; ++t) P.s_iperm[P.s_perm[t]] = t;
+            std::vector<int64_t> rp(L + 1, 0);
+            std::vector<int32_t> ra(sa.size());
+            for (int32_t t = 0; t < L; ++t) rp[t + 1] = rp[t] + (sp[P.s_perm[t] + 1] - sp[P.s_perm[t]]);
+            for (int32_t t = 0; t < L; ++t) {
+                int64_t o = rp[t];
+                for (int64_t e = sp[P.s_perm[t]]; e < sp[P.s_perm[t] + 1]; ++e) ra[o++] = P.s_iperm[sa[e]];
+            }
+            tile_profile(L, rp, ra, P.s_ntiles, P.s_lo, P.s_hi, P.s_fwd, P.s_bwd, P.s_tiles);
+        }
+    }
+    return 0;
+}
+
+}  // namespace am

@@ -1,0 +1,103 @@
+// Launch interfaces of the AlgMortar CUDA kernels (host-callable, no torch types).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace am {
+
+struct SolveArgs {
+    Profile pf;
+    const void* fwdS;          // forward sweep stream (TS)
+    const void* bwdS;          // backward sweep stream (TS)
+    const double* scale;       // symmetric scaling per row, or null (= 1)
+    const int64_t* scale_off;  // first scale entry of item s
+    const int32_t* job_sub;    // item of each job
+    const int64_t* job_in;     // offset of the job's input vector in `in`
+    const int64_t* job_out;    // offset of the job's output vector in `out`
+    const double* in;
+    double* out;
+    double alpha;              // out = alpha * A_s^{-1} in
+    const int32_t* done;       // early exit when *done != 0 (PCG), or null
+};
+
+struct InterfaceArgs {
+    const int32_t* rows;
+    const int64_t* if_off;
+    const int32_t* if_list;
+    const int64_t* phi_off;
+    const double* phi;         // FP64 MBF panels
+    const int64_t* g_cptr;     // per subdomain k_s + 1 column offsets into g arrays
+    const int32_t* g_row;
+    const double* g_val;
+    const int32_t* pairs;
+    const int32_t* s_iperm;
+    const int32_t* s_lo;
+    const int64_t* s_fwd;
+    double* work;              // interface factor work storage (FP64 tile profile)
+    double* diagc;             // 2 * n_lambda diagonal contributions
+};
+
+// local factor
+void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc, cudaStream_t st);
+template <typename TW>
+void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                          const int32_t* row_sub, const int64_t* sub_off, const Profile& pf,
+                          const double* dloc, const double* sc, TW* work, int nitems, cudaStream_t st);
+template <typename TW>
+void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st);
+template <typename TW>
+void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
+                      cudaStream_t st);
+template <typename TW, typename TS>
+void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
+                     cudaStream_t st);
+template <typename TS, typename TA>
+cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st);
+void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
+                    const double* g_val, const int32_t* rows, const int64_t* phi_off, double* rhs,
+                    cudaStream_t st);
+template <typename TS>
+void launch_convert(int64_t n, const double* src, TS* dst, cudaStream_t st);
+void launch_interface_assemble(int m, const InterfaceArgs& a, cudaStream_t st);
+void launch_interface_diag(int L, const double* T, const double* diagc, const int32_t* s_iperm,
+                           const int32_t* s_lo, const int64_t* s_fwd, double* work, cudaStream_t st);
+void launch_eye(int L, double* E, cudaStream_t st);
+void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double* Sinv, cudaStream_t st);
+
+// vector / PCG kernels (kernels_pcg.cu)
+constexpr int VEC_BS = 256;
+int vec_grid();                               // CTAs of every partial-producing vector kernel
+void set_vec_grid(int sms);
+void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
+void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
+void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
+                     double* beta, const int32_t* done, cudaStream_t st);
+void launch_coarse_gemv(int L, const double* Sinv, const double* b, double* eta, const int32_t* done,
+                        cudaStream_t st);
+template <typename TP>
+void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
+                    const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
+                    const double* pbar, double* z, const double* r, double* part, const int32_t* done,
+                    cudaStream_t st);
+void launch_pcg_init(int64_t n, const double* b, double* x, double* r, double* part, cudaStream_t st);
+void launch_pcg_start(PcgScalars* sc, const double* part_bb, double tol, int max_it, int flexible,
+                      cudaStream_t st);
+void launch_pcg_p(int64_t n, const double* z, double* p, const double* r, double* r_old, PcgScalars* sc,
+                  const double* part_rz, cudaStream_t st);
+void launch_pcg_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
+                     cudaStream_t st);
+void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc,
+                   const double* part_pq, double* part_rr, cudaStream_t st);
+void launch_pcg_check(PcgScalars* sc, const double* part_pq, const double* part_rr, cudaStream_t st);
+void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* x, const double* b, double* part, cudaStream_t st);
+void launch_sum_partials(const double* part, double* out, cudaStream_t st);
+
+}  // namespace am

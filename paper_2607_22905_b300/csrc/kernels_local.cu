@@ -1,0 +1,508 @@
+// Local (subdomain) kernels of AlgMortar on sm_103a: assembly of the diagonally
+// modified blocks A_i (Eq. A_i), their tile-profile Cholesky factorisation (Algorithm 1,
+// "compute the Cholesky factorization A_i = L_i L_i^T"), the sweep streams, and the
+// batched forward/backward triangular solves used for the particular solutions
+// (Eq. def-pbar-local), the MBFs (Eq. def-phat-local) and the explicit interface inverse.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace am {
+
+// ---------------------------------------------------------------------------------
+// Diagonal of A_i = A_ii - sum_j D_ij (Eqs. Dij-def, A_i): a_kk minus the row's couplings
+// to other subdomains (which are <= 0, so the diagonal grows).  sc = 1/sqrt(diag) when
+// symmetric diagonal scaling is on, else 1.
+// ---------------------------------------------------------------------------------
+__global__ void k_local_diag(int64_t n, const int32_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ col, const double* __restrict__ val,
+                             const int32_t* __restrict__ row_sub, int diag_scale,
+                             double* __restrict__ dloc, double* __restrict__ sc) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = row_sub[k];
+        double d = 0.0, cross = 0.0;
+        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) {
+            int32_t c = col[e];
+            if (c == k) d = val[e];
+            else if (row_sub[c] != s) cross += val[e];
+        }
+        double dl = d - cross;
+        dloc[k] = dl;
+        sc[k] = diag_scale ? 1.0 / sqrt(dl) : 1.0;
+    }
+}
+
+// Scatter the (scaled) lower triangle of every A_i into its tile-profile work storage.
+template <typename TW>
+__global__ void k_scatter_local(int64_t n, const int32_t* __restrict__ rowptr,
+                                const int32_t* __restrict__ col, const double* __restrict__ val,
+                                const int32_t* __restrict__ row_sub,
+                                const int64_t* __restrict__ sub_off, Profile pf,
+                                const double* __restrict__ dloc, const double* __restrict__ sc,
+                                TW* __restrict__ work) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = row_sub[k];
+        int64_t a = sub_off[s];
+        int32_t r = (int32_t)(k - a);
+        int64_t rd = pf.row0[s] + (r >> 5);
+        int32_t lo = pf.lo[rd];
+        int64_t trow = pf.base[s] + pf.fwd[rd];
+        double sk = sc[k];
+        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) {
+            int32_t c = col[e];
+            if (row_sub[c] != s) continue;
+            int32_t lc = (int32_t)(c - a);
+            if (lc > r) continue;
+            double v = (c == k) ? dloc[k] : val[e];
+            v *= sk * sc[c];
+            int64_t t = trow + ((lc >> 5) - lo);
+            work[t * TILE2 + (lc & 31) * TILE + (r & 31)] = (TW)v;
+        }
+    }
+}
+
+// Unit diagonal on the padding rows of each item's last tile.
+template <typename TW>
+__global__ void k_pad_diag(int nitems, Profile pf, TW* __restrict__ work) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nitems) return;
+    int32_t T = pf.ntiles[s], n = pf.rows[s];
+    int64_t rd = pf.row0[s] + T - 1;
+    int64_t t = pf.base[s] + pf.fwd[rd] + (T - 1 - pf.lo[rd]);
+    for (int r = n; r < T * TILE; ++r) work[t * TILE2 + (r & 31) * (TILE + 1)] = (TW)1;
+}
+
+// ---------------------------------------------------------------------------------
+// Tile-profile Cholesky, one CTA (256 threads) per item, up-looking by tile rows:
+//   L_IJ = (A_IJ - sum_K L_IK L_JK^T) L_JJ^{-T},   J = lo(I) .. I-1
+//   L_II = chol(A_II - sum_K L_IK L_IK^T)
+// Fill stays inside the envelope of A (Cholesky of a profile matrix), hence inside the
+// tile profile.  The inverse of every diagonal tile is kept in dinv (one tile per tile
+// row): it turns the panel update into a product and becomes the diagonal block of the
+// sweep streams.  A non-positive pivot sets err = {1, item} and continues with pivot 1.
+// ---------------------------------------------------------------------------------
+template <typename TW>
+__global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __restrict__ order,
+                                                   TW* __restrict__ work, TW* __restrict__ dinv,
+                                                   int* __restrict__ err) {
+    const int s = order ? order[blockIdx.x] : blockIdx.x;
+    const int T = pf.ntiles[s];
+    const int64_t r0 = pf.row0[s];
+    const int32_t* lo = pf.lo + r0;
+    const int64_t* fwd = pf.fwd + r0;
+    TW* Wb = work + pf.base[s] * TILE2;
+    TW* Db = dinv + r0 * TILE2;
+    __shared__ TW X[TILE][TILE + 1];
+    __shared__ TW As[TILE][TILE + 1];
+    __shared__ TW Bs[TILE][TILE + 1];
+    __shared__ int bad;
+    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
+    if (tid == 0) bad = 0;
+    auto tile = [&](int I, int J) { return Wb + (fwd[I] + (J - lo[I])) * TILE2; };
+    auto load = [&](TW(*dst)[TILE + 1], const TW* g) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = tid + 256 * q;
+            dst[e & 31][e >> 5] = g[e];
+        }
+    };
+    for (int I = 0; I < T; ++I) {
+        const int li = lo[I];
+        for (int J = li; J <= I; ++J) {
+            const TW* Aij = tile(I, J);
+            TW acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = Aij[c * TILE + rb + q];
+            const int k0 = max(li, lo[J]);
+            for (int K = k0; K < J; ++K) {
+                load(As, tile(I, K));
+                load(Bs, tile(J, K));
+                __syncthreads();
+#pragma unroll 8
+                for (int t = 0; t < TILE; ++t) {
+                    TW b = Bs[c][t];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] -= As[rb + q][t] * b;
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) X[rb + q][c] = acc[q];
+            if (J < I) {
+                load(Bs, Db + (int64_t)J * TILE2);          // L_JJ^{-1}
+                __syncthreads();
+                TW* Lij = Wb + (fwd[I] + (J - li)) * TILE2;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    TW v = 0;
+#pragma unroll 8
+                    for (int t = 0; t < TILE; ++t) v += X[rb + q][t] * Bs[c][t];
+                    Lij[c * TILE + rb + q] = v;
+                }
+                __syncthreads();
+            } else {
+                __syncthreads();
+                // dense 32x32 Cholesky of X in shared memory
+                for (int k = 0; k < TILE; ++k) {
+                    if (tid == 0) {
+                        TW d = X[k][k];
+                        if (!(d > (TW)0) || !isfinite((double)d)) {
+                            bad = 1;
+                            d = (TW)1;
+                        }
+                        X[k][k] = sqrt(d);
+                    }
+                    __syncthreads();
+                    if (tid > k && tid < TILE) X[tid][k] /= X[k][k];
+                    __syncthreads();
+                    for (int e = tid; e < TILE2; e += 256) {
+                        int r = e >> 5, cc = e & 31;
+                        if (cc > k && r >= cc) X[r][cc] -= X[r][k] * X[cc][k];
+                    }
+                    __syncthreads();
+                }
+                // inverse of the lower-triangular tile, one column per thread
+                if (tid < TILE) {
+                    const int cc = tid;
+                    for (int r = 0; r < TILE; ++r) {
+                        TW v;
+                        if (r < cc) {
+                            v = 0;
+                        } else {
+                            v = (r == cc) ? (TW)1 : (TW)0;
+                            for (int t = cc; t < r; ++t) v -= X[r][t] * As[t][cc];
+                            v /= X[r][r];
+                        }
+                        As[r][cc] = v;
+                    }
+                }
+                __syncthreads();
+                TW* Lii = Wb + (fwd[I] + (I - li)) * TILE2;
+                TW* Dii = Db + (int64_t)I * TILE2;
+                for (int e = tid; e < TILE2; e += 256) {
+                    int r = e & 31, cc = e >> 5;
+                    Lii[e] = r >= cc ? X[r][cc] : (TW)0;
+                    Dii[e] = As[r][cc];
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (tid == 0 && bad) {
+        if (atomicCAS(err + 1, -1, s) == -1) atomicExch(err, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Sweep streams from the factor: forward rows [L_I,lo .. L_I,I-1 | L_II^{-1}], backward
+// rows [(L_I+1,I)^T .. (L_hi,I)^T | L_II^{-T}], all tiles column-major, in precision TS.
+// ---------------------------------------------------------------------------------
+template <typename TW, typename TS>
+__global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restrict__ work,
+                                                  const TW* __restrict__ dinv,
+                                                  TS* __restrict__ fwdS, TS* __restrict__ bwdS) {
+    const int s = blockIdx.x;
+    const int T = pf.ntiles[s];
+    const int64_t r0 = pf.row0[s];
+    const int32_t* lo = pf.lo + r0;
+    const int32_t* hi = pf.hi + r0;
+    const int64_t* fwd = pf.fwd + r0;
+    const int64_t* bwd = pf.bwd + r0;
+    const int64_t base = pf.base[s];
+    const TW* Wb = work + base * TILE2;
+    const TW* Db = dinv + r0 * TILE2;
+    for (int I = 0; I < T; ++I) {
+        const int nt = I - lo[I];
+        const int64_t fo = (base + fwd[I]) * TILE2;
+        for (int64_t e = threadIdx.x; e < (int64_t)nt * TILE2; e += blockDim.x)
+            fwdS[fo + e] = stf<TS>((double)Wb[fwd[I] * TILE2 + e]);
+        for (int e = threadIdx.x; e < TILE2; e += blockDim.x)
+            fwdS[fo + (int64_t)nt * TILE2 + e] = stf<TS>((double)Db[(int64_t)I * TILE2 + e]);
+        const int nb = hi[I] - I;
+        const int64_t bo = (base + bwd[I]) * TILE2;
+        for (int t = 0; t < nb; ++t) {
+            const int J = I + 1 + t;
+            const TW* src = Wb + (fwd[J] + (I - lo[J])) * TILE2;
+            for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+                int r = e & 31, cc = e >> 5;
+                bwdS[bo + (int64_t)t * TILE2 + e] = stf<TS>((double)src[r * TILE + cc]);
+            }
+        }
+        for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+            int r = e & 31, cc = e >> 5;
+            bwdS[bo + (int64_t)nb * TILE2 + e] = stf<TS>((double)Db[(int64_t)I * TILE2 + r * TILE + cc]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Batched triangular solves  out = alpha * S L^{-T} L^{-1} S in  for a list of jobs
+// (item, input offset, output offset); S = diag(sc) is the symmetric scaling (or 1).
+// One CTA per job; the right-hand side lives in shared memory (accumulation type TA).
+// Each tile-row step: the off-diagonal tiles of the row are spread over the warps
+// (tile GEMV, lane = tile row, coalesced column loads), the partial sums meet in shared
+// memory, and warp 0 applies the stored inverse diagonal tile.
+// ---------------------------------------------------------------------------------
+template <typename TS, typename TA, int NW>
+__global__ void __launch_bounds__(NW * 32) k_tile_solve(SolveArgs a) {
+    if (a.done && *a.done) return;
+    const int job = blockIdx.x;
+    const int s = a.job_sub[job];
+    const Profile pf = a.pf;
+    const int n = pf.rows[s], T = pf.ntiles[s];
+    const int64_t r0 = pf.row0[s];
+    const int32_t* lo = pf.lo + r0;
+    const int32_t* hi = pf.hi + r0;
+    const int64_t* fwd = pf.fwd + r0;
+    const int64_t* bwd = pf.bwd + r0;
+    const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
+    const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
+    const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
+    const double* in = a.in + a.job_in[job];
+    double* out = a.out + a.job_out[job];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* v = reinterpret_cast<TA*>(smem_raw);
+    TA* part = v + T * TILE;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < T * TILE; i += NW * 32)
+        v[i] = i < n ? (TA)(in[i] * (sc ? sc[i] : 1.0)) : (TA)0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        const TS* St = pass == 0 ? F : Bk;
+        for (int step = 0; step < T; ++step) {
+            const int I = pass == 0 ? step : T - 1 - step;
+            const int j0 = pass == 0 ? lo[I] : I + 1;
+            const int nt = pass == 0 ? I - lo[I] : hi[I] - I;
+            const TS* row = St + (pass == 0 ? fwd[I] : bwd[I]) * TILE2;
+            TA dcol[TILE];
+            if (w == 0) {
+                const TS* D = row + (int64_t)nt * TILE2;
+#pragma unroll
+                for (int c = 0; c < TILE; ++c) dcol[c] = ldf<TA>(D + c * TILE + lane);
+            }
+            TA acc = 0;
+            for (int t = w; t < nt; t += NW) {
+                const TS* tl = row + (int64_t)t * TILE2;
+                const TA* vj = v + (j0 + t) * TILE;
+#pragma unroll
+                for (int c = 0; c < TILE; ++c) acc += ldf<TA>(tl + c * TILE + lane) * vj[c];
+            }
+            part[w * TILE + lane] = acc;
+            __syncthreads();
+            if (w == 0) {
+                TA sum = 0;
+#pragma unroll
+                for (int q = 0; q < NW; ++q) sum += part[q * TILE + lane];
+                TA t = v[I * TILE + lane] - sum;
+                TA y = 0;
+#pragma unroll
+                for (int c = 0; c < TILE; ++c) y += dcol[c] * __shfl_sync(0xffffffffu, t, c);
+                v[I * TILE + lane] = y;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += NW * 32) out[i] = a.alpha * (double)v[i] * (sc ? sc[i] : 1.0);
+}
+
+// ---------------------------------------------------------------------------------
+// MBF right-hand sides  -B_i psi_m = -G[Omega_i, m]  scattered into the (zeroed) panel
+// buffer, column-major per subdomain (Eq. def-phat-local).
+// ---------------------------------------------------------------------------------
+__global__ void k_mbf_rhs(int m, const int64_t* __restrict__ g_off, const int32_t* __restrict__ g_row,
+                          const int32_t* __restrict__ g_col, const double* __restrict__ g_val,
+                          const int32_t* __restrict__ rows, const int64_t* __restrict__ phi_off,
+                          double* __restrict__ rhs) {
+    int s = blockIdx.x;
+    if (s >= m) return;
+    int64_t ns = rows[s];
+    for (int64_t t = g_off[s] + threadIdx.x; t < g_off[s + 1]; t += blockDim.x)
+        rhs[phi_off[s] + g_col[t] * ns + g_row[t]] = -g_val[t];
+}
+
+template <typename TS>
+__global__ void k_convert(int64_t n, const double* __restrict__ src, TS* __restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = stf<TS>(src[i]);
+}
+
+// ---------------------------------------------------------------------------------
+// Interface matrix S_eta = diag(T) + 1/4 G^T Phi  (Eq. interface-problem-alg with
+// W M = B^T / 4, Prop. proposition-BWM), written into the tile profile of its RCM order.
+// One CTA per subdomain; one warp per pair (a <= b) of the subdomain's interfaces.
+// Off-diagonal entries come from the one subdomain the two interfaces share and are
+// symmetrised there; diagonal contributions of the two sides go to diagc and are
+// summed in a fixed order by k_interface_diag.
+// ---------------------------------------------------------------------------------
+__global__ void k_interface_assemble(InterfaceArgs a) {
+    const int s = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t i0 = a.if_off[s];
+    const int k = (int)(a.if_off[s + 1] - i0);
+    const int64_t ns = a.rows[s];
+    const double* phi = a.phi + a.phi_off[s];
+    const int64_t* cp = a.g_cptr + i0 + s;
+    for (int pr = w; pr < k * k; pr += nw) {
+        const int ai = pr / k, bi = pr % k;
+        if (bi < ai) continue;
+        double cab = 0.0, cba = 0.0;
+        for (int64_t t = cp[ai] + lane; t < cp[ai + 1]; t += 32)
+            cab += a.g_val[t] * phi[bi * ns + a.g_row[t]];
+        for (int64_t t = cp[bi] + lane; t < cp[bi + 1]; t += 32)
+            cba += a.g_val[t] * phi[ai * ns + a.g_row[t]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cab += __shfl_xor_sync(0xffffffffu, cab, o);
+            cba += __shfl_xor_sync(0xffffffffu, cba, o);
+        }
+        if (lane == 0) {
+            const int I = a.if_list[i0 + ai], J = a.if_list[i0 + bi];
+            if (ai == bi) {
+                const int side = (a.pairs[2 * I] == s) ? 0 : 1;
+                a.diagc[2 * I + side] = 0.25 * cab;
+            } else {
+                int p = a.s_iperm[I], q = a.s_iperm[J];
+                if (p < q) { int t = p; p = q; q = t; }
+                const int64_t P = p >> 5, Q = q >> 5;
+                const int64_t tl = a.s_fwd[P] + (Q - a.s_lo[P]);
+                a.work[tl * TILE2 + (q & 31) * TILE + (p & 31)] = 0.125 * (cab + cba);
+            }
+        }
+    }
+}
+
+__global__ void k_interface_diag(int L, const double* __restrict__ T, const double* __restrict__ diagc,
+                                 const int32_t* __restrict__ s_iperm, const int32_t* __restrict__ s_lo,
+                                 const int64_t* __restrict__ s_fwd, double* __restrict__ work) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= L) return;
+    int p = s_iperm[I];
+    int64_t P = p >> 5;
+    int64_t tl = s_fwd[P] + (P - s_lo[P]);
+    work[tl * TILE2 + (p & 31) * (TILE + 1)] = T[I] + diagc[2 * I] + diagc[2 * I + 1];
+}
+
+// Identity right-hand sides for the explicit interface inverse (column q = e_q).
+__global__ void k_eye(int L, double* __restrict__ E) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < L) E[(int64_t)q * L + q] = 1.0;
+}
+
+// Sinv[I][J] (natural interface order, row-major) = symmetric part of the RCM-ordered
+// inverse computed column by column.
+__global__ void k_sinv_finalize(int L, const int32_t* __restrict__ s_iperm, const double* __restrict__ R,
+                                double* __restrict__ Sinv) {
+    int64_t total = (int64_t)L * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int I = (int)(e / L), J = (int)(e % L);
+        int64_t p = s_iperm[I], q = s_iperm[J];
+        Sinv[e] = 0.5 * (R[q * L + p] + R[p * L + q]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------
+static inline int grid_for(int64_t n, int bs) {
+    int64_t g = (n + bs - 1) / bs;
+    return (int)(g < 1 ? 1 : (g > 65535 * 4 ? 65535 * 4 : g));
+}
+
+void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc,
+                       cudaStream_t st) {
+    k_local_diag<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, diag_scale, dloc, sc);
+}
+
+template <typename TW>
+void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                          const int32_t* row_sub, const int64_t* sub_off, const Profile& pf,
+                          const double* dloc, const double* sc, TW* work, int nitems, cudaStream_t st) {
+    k_scatter_local<TW><<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, sub_off, pf,
+                                                          dloc, sc, work);
+    k_pad_diag<TW><<<(nitems + 127) / 128, 128, 0, st>>>(nitems, pf, work);
+}
+
+template <typename TW>
+void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st) {
+    k_pad_diag<TW><<<(nitems + 127) / 128, 128, 0, st>>>(nitems, pf, work);
+}
+
+template <typename TW>
+void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
+                      cudaStream_t st) {
+    k_tile_chol<TW><<<nitems, 256, 0, st>>>(pf, order, work, dinv, err);
+}
+
+template <typename TW, typename TS>
+void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
+                     cudaStream_t st) {
+    k_finalize<TW, TS><<<nitems, 256, 0, st>>>(pf, work, dinv, fwdS, bwdS);
+}
+
+template <typename TS, typename TA>
+cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
+    constexpr int NW = 8;
+    size_t smem = (size_t)(max_tiles * TILE + NW * TILE) * sizeof(TA);
+    static bool attr_set[2] = {false, false};
+    (void)attr_set;
+    cudaError_t e = cudaFuncSetAttribute(k_tile_solve<TS, TA, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (njobs > 0) k_tile_solve<TS, TA, NW><<<njobs, NW * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
+                    const double* g_val, const int32_t* rows, const int64_t* phi_off, double* rhs,
+                    cudaStream_t st) {
+    if (m > 0) k_mbf_rhs<<<m, 128, 0, st>>>(m, g_off, g_row, g_col, g_val, rows, phi_off, rhs);
+}
+
+template <typename TS>
+void launch_convert(int64_t n, const double* src, TS* dst, cudaStream_t st) {
+    if (n > 0) k_convert<TS><<<grid_for(n, 256), 256, 0, st>>>(n, src, dst);
+}
+
+void launch_interface_assemble(int m, const InterfaceArgs& a, cudaStream_t st) {
+    if (m > 0) k_interface_assemble<<<m, 256, 0, st>>>(a);
+}
+
+void launch_interface_diag(int L, const double* T, const double* diagc, const int32_t* s_iperm,
+                           const int32_t* s_lo, const int64_t* s_fwd, double* work, cudaStream_t st) {
+    if (L > 0) k_interface_diag<<<(L + 127) / 128, 128, 0, st>>>(L, T, diagc, s_iperm, s_lo, s_fwd, work);
+}
+
+void launch_eye(int L, double* E, cudaStream_t st) {
+    if (L > 0) k_eye<<<(L + 127) / 128, 128, 0, st>>>(L, E);
+}
+
+void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double* Sinv, cudaStream_t st) {
+    if (L > 0) k_sinv_finalize<<<grid_for((int64_t)L * L, 256), 256, 0, st>>>(L, s_iperm, R, Sinv);
+}
+
+template void launch_scatter_local<double>(int64_t, const int32_t*, const int32_t*, const double*,
+                                           const int32_t*, const int64_t*, const Profile&, const double*,
+                                           const double*, double*, int, cudaStream_t);
+template void launch_scatter_local<float>(int64_t, const int32_t*, const int32_t*, const double*,
+                                          const int32_t*, const int64_t*, const Profile&, const double*,
+                                          const double*, float*, int, cudaStream_t);
+template void launch_pad_diag<double>(int, const Profile&, double*, cudaStream_t);
+template void launch_tile_chol<double>(int, const Profile&, const int32_t*, double*, double*, int*, cudaStream_t);
+template void launch_tile_chol<float>(int, const Profile&, const int32_t*, float*, float*, int*, cudaStream_t);
+template void launch_finalize<double, double>(int, const Profile&, const double*, const double*, double*,
+                                              double*, cudaStream_t);
+template void launch_finalize<float, float>(int, const Profile&, const float*, const float*, float*, float*,
+                                            cudaStream_t);
+template void launch_finalize<float, __nv_bfloat16>(int, const Profile&, const float*, const float*,
+                                                    __nv_bfloat16*, __nv_bfloat16*, cudaStream_t);
+template cudaError_t launch_tile_solve<double, double>(const SolveArgs&, int, int, cudaStream_t);
+template cudaError_t launch_tile_solve<float, float>(const SolveArgs&, int, int, cudaStream_t);
+template cudaError_t launch_tile_solve<__nv_bfloat16, float>(const SolveArgs&, int, int, cudaStream_t);
+template void launch_convert<float>(int64_t, const double*, float*, cudaStream_t);
+template void launch_convert<__nv_bfloat16>(int64_t, const double*, __nv_bfloat16*, cudaStream_t);
+
+}  // namespace am

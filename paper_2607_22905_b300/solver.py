@@ -1,0 +1,150 @@
+"""PyTorch-facing wrapper of the AlgMortar-PCG library.
+
+PyTorch supplies device memory and the stream; the work runs in libalgmortar's kernels.
+There is no CPU fallback: without a CUDA device or without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+class AlgMortar:
+    """AlgMortar preconditioner + PCG for an SPD scipy CSR matrix A (original ordering).
+
+    precision: "fp64" | "fp32" | "bf16" for the local factors/solves and MBF panels.
+    part_sizes: optional target sizes of the n_parts subdomains (sum = N).
+    parts: optional labels replacing the built-in partitioner.
+    """
+
+    def __init__(self, A, n_parts, precision="fp64", part_sizes=None, parts=None, use_graph=False,
+                 check_every=1, max_it=10000, diag_scale=True, device=0, verbose=False, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("AlgMortar needs a CUDA device")
+        L = B.lib()
+        self.n = int(A.shape[0])
+        self.device = torch.device("cuda", device)
+        o = B.default_opts()
+        o.precision = B.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.diag_scale = 1 if diag_scale else 0
+        o.max_it = int(max_it)
+        o.use_graph = 1 if use_graph else 0
+        o.check_every = int(check_every)
+        o.verbose = 1 if verbose else 0
+        o.device = int(device)
+        self._sizes = None
+        if part_sizes is not None:
+            self._sizes = np.ascontiguousarray(part_sizes, dtype=np.int32)
+            o.part_sizes = self._sizes.ctypes.data_as(B._IP)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        o.stream = C.c_void_p(stream.cuda_stream) if stream.cuda_stream else None
+        self._stream = stream
+        csr = B.csr_struct(A)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            if parts is not None:
+                p = np.ascontiguousarray(parts, dtype=np.int32)
+                B.check(L.algmortar_setup_with_parts(C.byref(csr), p.ctypes.data_as(B._IP), int(n_parts),
+                                                     C.byref(o), C.byref(h)), "algmortar_setup_with_parts")
+            else:
+                B.check(L.algmortar_setup(C.byref(csr), int(n_parts), C.byref(o), C.byref(h)),
+                        "algmortar_setup")
+        self._h = h
+        info = B.Info()
+        B.check(L.algmortar_get_info(h, C.byref(info)))
+        self.info = info.as_dict()
+
+    # -------------------------------------------------------------- helpers
+    def _vec(self, v):
+        v = torch.as_tensor(v, dtype=torch.float64, device=self.device)
+        return v.contiguous()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.lib().algmortar_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ API
+    def apply(self, r):
+        """z = cal_M^{-1} r (Algorithm 2)."""
+        r = self._vec(r)
+        z = torch.empty_like(r)
+        B.check(B.lib().algmortar_apply(self._h, _ptr(r), _ptr(z)), "algmortar_apply")
+        return z
+
+    def apply_stages(self, r):
+        """(pbar, b_eta, eta, z) of Algorithm 2 in the internal ordering."""
+        r = self._vec(r)
+        nl = max(self.info["n_lambda"], 1)
+        pbar = torch.empty_like(r)
+        z = torch.empty_like(r)
+        beta = torch.empty(nl, dtype=torch.float64, device=self.device)
+        eta = torch.empty_like(beta)
+        B.check(B.lib().algmortar_apply_stages(self._h, _ptr(r), _ptr(pbar), _ptr(beta), _ptr(eta), _ptr(z)))
+        nl = self.info["n_lambda"]
+        return pbar, beta[:nl], eta[:nl], z
+
+    def solve(self, b, tol=1e-8, raise_on_fail=True):
+        """PCG with x0 = 0 to ||r|| <= tol ||b||; returns (x, stats dict)."""
+        b = self._vec(b)
+        x = torch.empty_like(b)
+        st = B.Stats()
+        rc = B.lib().algmortar_pcg_solve(self._h, _ptr(b), _ptr(x), float(tol), C.byref(st))
+        if raise_on_fail and rc != B.OK:
+            raise B.AlgMortarError(rc, "algmortar_pcg_solve")
+        return x, st.as_dict()
+
+    def solve_host(self, b, tol=1e-8):
+        """PCG with HOST numpy b -> host x (copies inside the call)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        st = B.Stats()
+        rc = B.lib().algmortar_pcg_solve_host(self._h, b.ctypes.data_as(B._DP), x.ctypes.data_as(B._DP),
+                                              float(tol), C.byref(st))
+        if rc != B.OK:
+            raise B.AlgMortarError(rc, "algmortar_pcg_solve_host")
+        return x, st.as_dict()
+
+    def solve_multi(self, Bm, tol=1e-8):
+        """Independent PCG solves for the columns of an N x k matrix (column-major)."""
+        Bm = torch.as_tensor(Bm, dtype=torch.float64, device=self.device)
+        Bt = Bm.t().contiguous()                      # k x N row-major == N x k column-major
+        Xt = torch.empty_like(Bt)
+        k = Bt.shape[0]
+        st = (B.Stats * k)()
+        rc = B.lib().algmortar_pcg_solve_multi(self._h, _ptr(Bt), _ptr(Xt), k, self.n, float(tol), st)
+        if rc != B.OK:
+            raise B.AlgMortarError(rc, "algmortar_pcg_solve_multi")
+        return Xt.t(), [s.as_dict() for s in st]
+
+    def partition(self):
+        out = np.empty(self.n, dtype=np.int32)
+        B.check(B.lib().algmortar_get_partition(self._h, out.ctypes.data_as(B._IP)))
+        return out
+
+    def permutation(self):
+        out = np.empty(self.n, dtype=np.int32)
+        B.check(B.lib().algmortar_get_permutation(self._h, out.ctypes.data_as(B._IP)))
+        return out
+
+    def interfaces(self):
+        nl = self.info["n_lambda"]
+        out = np.empty(2 * max(nl, 1), dtype=np.int32)
+        B.check(B.lib().algmortar_get_interfaces(self._h, out.ctypes.data_as(B._IP)))
+        return out[:2 * nl].reshape(nl, 2)

@@ -1,0 +1,204 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 factors -> preconditioned vectors agree to 1e-10 relative (the stated
+FP64 bar; both sides are backward-stable solves of the same SPD systems, so the
+difference is a few ulps times the local condition numbers); solutions agree within the
+solve tolerance.  FP32 / BF16 factors change the preconditioner itself, so for them the
+checks are convergence to the same tolerance and closeness of the solution.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import algmortar as oa
+from oracle import partition as op
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_22905_b300 import build
+    build.build()
+
+
+def AlgMortar(*a, **k):
+    from paper_2607_22905_b300.solver import AlgMortar as _A
+    return _A(*a, **k)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def small3d(shape=(21, 17, 13), m=11, seed=31, uneven=True, sigma=2.0):
+    """3D TPFA with ragged subdomains (sizes not multiples of the 32-row tile)."""
+    lnK = synth.gaussian_field(shape, 3.0, sigma, seed)
+    A, f = synth.tpfa_cartesian(np.exp(lnK), kz_ratio=0.1, bc_axis=1)
+    n = A.shape[0]
+    sizes = synth.uneven_part_sizes(n, m, 150, 900, seed) if uneven else synth.even_part_sizes(n, m)
+    return A, f, sizes
+
+
+CASES = {
+    "c1": lambda: (lambda P: (P.A, P.f, P.part_sizes))(synth.config1()),
+    "3d_uneven": lambda: small3d(),
+    "3d_even_ragged": lambda: small3d(shape=(19, 15, 11), m=8, uneven=False, seed=7),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    A, f, sizes = CASES[request.param]()
+    part = op.partition(A, sizes)
+    pc = oa.setup(A, part)
+    return request.param, A, f, sizes, part, pc
+
+
+def test_partition_and_permutation(case):
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    np.testing.assert_array_equal(am.partition(), part)
+    perm = am.permutation()
+    assert sorted(perm.tolist()) == list(range(A.shape[0]))
+    # the internal ordering groups subdomains in order
+    assert (np.diff(part[perm]) >= 0).all()
+    np.testing.assert_array_equal(am.interfaces(), pc.sk.pairs)
+
+
+def test_apply_fp64_matches_oracle(case):
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    rng = np.random.default_rng(100)
+    for _ in range(3):
+        r = rng.standard_normal(A.shape[0])
+        z = am.apply(r).cpu().numpy()
+        assert rel(z, oa.apply(pc, r)) <= 1e-10
+
+
+def test_apply_stages_fp64(case):
+    """Each stage of Algorithm 2: pbar (Eq. def-pbar-local), interface RHS, eta, z."""
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    r = np.random.default_rng(101).standard_normal(A.shape[0])
+    pbar, beta, eta, z = (t.cpu().numpy() for t in am.apply_stages(r))
+    perm = am.permutation()                      # internal -> original
+    pbar_o, rhs_o, eta_o, z_o = oa.apply_parts(pc, r)
+    # oracle vectors are in its own (part, index) ordering: map both to original
+    orig_pbar = np.empty_like(pbar)
+    orig_pbar[perm] = pbar
+    orig_pbar_o = np.empty_like(pbar_o)
+    orig_pbar_o[pc.sk.perm] = pbar_o
+    assert rel(orig_pbar, orig_pbar_o) <= 1e-10
+    assert rel(beta, rhs_o) <= 1e-10
+    assert rel(eta, eta_o) <= 1e-10
+    orig_z = np.empty_like(z)
+    orig_z[perm] = z
+    orig_z_o = np.empty_like(z_o)
+    orig_z_o[pc.sk.perm] = z_o
+    assert rel(orig_z, orig_z_o) <= 1e-10
+
+
+def test_apply_symmetric(case):
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    rng = np.random.default_rng(102)
+    r1, r2 = rng.standard_normal((2, A.shape[0]))
+    a = float(r1 @ am.apply(r2).cpu().numpy())
+    b = float(r2 @ am.apply(r1).cpu().numpy())
+    assert abs(a - b) <= 1e-12 * (abs(a) + abs(b))
+
+
+def test_residual_vanishes_off_interface(case):
+    """Sec. 5.4 on the GPU result: r - A z is zero at cells without interface edges."""
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    r = np.random.default_rng(103).standard_normal(A.shape[0])
+    z = am.apply(r).cpu().numpy()
+    res = r - A @ z
+    coo = sp.coo_matrix(A)
+    iface = np.zeros(A.shape[0], dtype=bool)
+    cross = part[coo.row] != part[coo.col]
+    iface[coo.row[cross]] = True
+    assert np.abs(res[~iface]).max() <= 1e-10 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_pcg_fp64_matches_oracle(case, use_graph):
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, use_graph=use_graph, check_every=4 if use_graph else 1)
+    x, st = am.solve(f, tol=1e-8)
+    x = x.cpu().numpy()
+    ref = oa.pcg(A, f, lambda v: oa.apply(pc, v), 1e-8)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-8
+    assert np.linalg.norm(f - A @ x) <= 1e-8 * np.linalg.norm(f)
+    assert abs(st["iterations"] - ref.iterations) <= 1
+    xs = spla.spsolve(A.tocsc(), f)
+    assert rel(x, ref.x) <= 1e-6 and rel(x, xs) <= 1e-6
+
+
+def test_graph_and_stream_paths_bitwise_equal(case):
+    name, A, f, sizes, part, pc = case
+    a = AlgMortar(A, len(sizes), part_sizes=sizes)
+    b = AlgMortar(A, len(sizes), part_sizes=sizes, use_graph=True, check_every=1)
+    xa, sa = a.solve(f)
+    xb, sb = b.solve(f)
+    assert sa["iterations"] == sb["iterations"]
+    assert torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_pcg_low_precision_factors(case, precision):
+    """Mixed precision: local factors in FP32/BF16, outer PCG FP64 -> same tolerance."""
+    name, A, f, sizes, part, pc = case
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, precision=precision)
+    x, st = am.solve(f, tol=1e-8)
+    x = x.cpu().numpy()
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-8
+    ref = oa.pcg(A, f, lambda v: oa.apply(pc, v), 1e-8)
+    assert rel(x, ref.x) <= 1e-5
+    assert st["iterations"] <= 2 * ref.iterations + 5
+    # the low-precision preconditioner stays close to the FP64 one
+    r = np.random.default_rng(104).standard_normal(A.shape[0])
+    tol = 2e-3 if precision == "fp32" else 1e-1
+    assert rel(am.apply(r).cpu().numpy(), oa.apply(pc, r)) <= tol
+
+
+def test_single_subdomain_exact():
+    """m = 1: no interface, z = A^{-1} r; PCG converges in one iteration."""
+    A, f, _ = small3d(shape=(9, 8, 7), m=1, uneven=False)
+    am = AlgMortar(A, 1)
+    assert am.info["n_lambda"] == 0
+    r = np.random.default_rng(105).standard_normal(A.shape[0])
+    x = spla.spsolve(A.tocsc(), r)
+    assert rel(am.apply(r).cpu().numpy(), x) <= 1e-11
+    xs, st = am.solve(f, tol=1e-10)
+    assert st["iterations"] == 1
+
+
+def test_solve_host_matches_device():
+    A, f, sizes = small3d()
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    xd, sd = am.solve(f)
+    xh, sh = am.solve_host(f)
+    np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+    assert sd["iterations"] == sh["iterations"]
+
+
+def test_zero_rhs():
+    A, f, sizes = small3d()
+    am = AlgMortar(A, len(sizes), part_sizes=sizes)
+    x, st = am.solve(np.zeros(A.shape[0]))
+    assert st["iterations"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_max_it_reports_no_convergence():
+    A, f, sizes = small3d()
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, max_it=3)
+    x, st = am.solve(f, tol=1e-12, raise_on_fail=False)
+    assert st["status"] == 5 and st["iterations"] == 3
