@@ -1,0 +1,365 @@
+"""Benchmark: time to a 1e-8 relative residual for AlgMortar-PCG on one B300.
+
+Workload (default): the 1.122M-cell layered channelised 3D TPFA Darcy system
+(60 x 220 x 85, contrast ~2e7, kz/kx = 0.1, 1122 uneven subdomains of ~300-3000 cells),
+synthetic and seeded (see synth.config3).
+
+One timed step = one full time-to-solution on device-resident inputs:
+    numeric part of Algorithm 1 (local factors, MBFs, interface system, from the CSR
+    values already in HBM)  +  PCG (x0 = 0) to ||r|| <= 1e-8 ||b||.
+The host-side symbolic setup (partition of G(A), permutation, tables) depends only on
+the sparsity pattern, is shared by all variants and is reported separately.
+
+Variants differ only in the precision of the local factors / MBF panels (FP64, FP32,
+BF16 with FP32 accumulation); SpMV, CG recurrences, dot products, restriction and the
+interface solve are FP64 in all of them.  `value` is the fastest mixed-precision
+variant; the FP64 variant is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload (weak scaling,
+no data-path collective); rank 0 prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("time-to-1e-8 rel. residual & PCG iters (1.1M cells): mixed/batched vs FP64 AlgMortar; "
+          "HBM GB/s")
+TOL = 1e-8
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def workload(name):
+    import synth
+    if name == "c3":
+        return synth.config3(), "C3 3D TPFA 60x220x85 (1.122M cells) layered channelised, contrast ~2e7, " \
+                                "kz/kx=0.1, 1122 uneven parts"
+    if name == "c3s":
+        return synth.config3(ny=110, n_parts=561), "C3-small 60x110x85 (561k cells), same field recipe, 561 parts " \
+                                                   "(profiling-sized case)"
+    if name == "c2":
+        return synth.config2(), "C2 3D TPFA 128^3 (2.1M cells), lnK~N(0,9), 512 parts"
+    if name == "c1":
+        return synth.config1(), "C1 2D TPFA 64x64, 16 parts"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile(prefix="clk_", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.f.name):
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist, dist.get_rank(), world
+    return None, 0, 1
+
+
+def run_ours(args):
+    import torch
+    from paper_2607_22905_b300 import binding as B
+    from paper_2607_22905_b300 import build as _build
+    from paper_2607_22905_b300.solver import AlgMortar
+
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    _build.build()
+    dev = torch.device("cuda", local)
+    P, wdesc = workload(args.config)
+    n, nnz = P.n, P.A.nnz
+    vals = torch.as_tensor(P.A.data, dtype=torch.float64, device=dev)
+    b = torch.as_tensor(P.f, dtype=torch.float64, device=dev)
+    peak, peak_kind = load_peaks()
+    variants = [v for v in args.variants.split(",") if v]
+    res = {}
+    handles = {}
+    t0 = time.perf_counter()
+    for prec in variants:
+        am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
+                       check_every=args.check_every, device=local)
+        handles[prec] = am
+    host_setup_ms = {k: v.info["setup_ms"]["partition_and_tables"] for k, v in handles.items()}
+
+    def step(am):
+        am.update_values(vals)
+        x, st = am.solve(b, tol=TOL)
+        return x, st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    clocks_all = {}
+    for prec in variants:
+        am = handles[prec]
+        for _ in range(args.warmup):
+            step(am)
+        l0 = am.info["kernel_launches"] if "kernel_launches" in am.info else 0
+        info0 = B.Info()
+        B.check(B.lib().algmortar_get_info(am._h, C.byref(info0)))
+        barrier()
+        with Clocks() as clk:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            its = []
+            for _ in range(args.steps):
+                x, st = step(am)
+                its.append(st["iterations"])
+            e1.record()
+            barrier()
+        info1 = B.Info()
+        B.check(B.lib().algmortar_get_info(am._h, C.byref(info1)))
+        ms = e0.elapsed_time(e1) / args.steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        xr = x.cpu().numpy()
+        true_rel = float(np.linalg.norm(P.f - P.A @ xr) / np.linalg.norm(P.f))
+        stages = am.time_stages(args.stage_reps)
+        info = am.info
+        res[prec] = {"ms": ms, "iterations": int(np.median(its)), "rel_residual": true_rel,
+                     "setup_ms": {k: round(v, 3) for k, v in info["setup_ms"].items()},
+                     "stages_ms": {k: round(v, 5) for k, v in stages.items()},
+                     "launches_per_step": (info1.kernel_launches - info0.kernel_launches) / args.steps,
+                     "factor_bytes": info["factor_bytes"], "n_lambda": info["n_lambda"],
+                     "x_host": xr}
+        clocks_all[prec] = clk.summary()
+
+    # e2e: the same step through the C ABI with HOST buffers (pinned), copies inside
+    mixed = [v for v in variants if v != "fp64"] or variants
+    best = min(mixed, key=lambda v: res[v]["ms"])
+    am = handles[best]
+    vh = torch.as_tensor(P.A.data, dtype=torch.float64).pin_memory()
+    bh = torch.as_tensor(P.f, dtype=torch.float64).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    L = B.lib()
+    st = B.Stats()
+
+    def e2e_step():
+        B.check(L.algmortar_update_values(am._h, C.cast(C.c_void_p(vh.data_ptr()), B._DP)))
+        rc = L.algmortar_pcg_solve_host(am._h, C.cast(C.c_void_p(bh.data_ptr()), B._DP),
+                                        C.cast(C.c_void_p(xh.data_ptr()), B._DP), TOL, C.byref(st))
+        B.check(rc, "algmortar_pcg_solve_host")
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
+
+    # roofline of the dominant kernel: the batched local triangular solves
+    r = res[best]
+    isz = {"fp64": 8, "fp32": 4, "bf16": 2}[best]
+    local_bytes = r["factor_bytes"] + 8 * n * 4          # both sweep streams + rhs, scale x2, out
+    local_ms = r["stages_ms"]["local_solve"]
+    achieved = local_bytes / (local_ms * 1e-3) / 1e9
+    spmv_bytes = 12 * nnz + 4 * (n + 1) + 8 * n * 3       # values+cols, rowptr, p gather+p.q read, q write
+    spmv_ms = r["stages_ms"]["spmv"]
+    out = {
+        "metric": METRIC,
+        "value": round(r["ms"], 3),
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(r["ms"], 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": f"{best}+f64",
+        "data": "synthetic",
+        "config": {"workload": wdesc, "n": n, "nnz": nnz, "n_parts": P.n_parts, "n_lambda": r["n_lambda"],
+                   "tol": TOL, "variant": best, "step": "numeric setup (Algorithm 1) + PCG to tol",
+                   "l2": "inputs larger than L2 (factor streams %.2f GB, matrix %.0f MB)"
+                         % (r["factor_bytes"] / 1e9, (12 * nnz) / 1e6),
+                   "host_symbolic_setup_ms": round(host_setup_ms[best], 1)},
+        "iterations": r["iterations"],
+        "variants": {k: {kk: vv for kk, vv in v.items() if kk != "x_host"} for k, v in res.items()},
+        "roofline": {"bound": "hbm", "kernel": "k_chain_solve (batched local triangular solves)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "algorithmic_bytes": int(local_bytes), "traffic": None,
+                     "spmv_achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1)},
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(8 * nnz + 8 * n),
+                "d2h_bytes_per_step": int(8 * n)},
+        "gpu_launches": int(r["launches_per_step"] * args.steps),
+        "clocks": clocks_all.get(best),
+    }
+    if "fp64" in res:
+        out["fp64_ms"] = round(res["fp64"]["ms"], 3)
+        out["speedup_vs_fp64"] = round(res["fp64"]["ms"] / r["ms"], 3)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(P, args)
+    if rank == 0:
+        print(json.dumps(out))
+    for am in handles.values():
+        am.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(P, args, n_iter_sample=3):
+    """The FP64 CPU oracle, as it stands, on the host cores: its full setup (Algorithm 1)
+    on the workload plus a few timed PCG iterations, extrapolated to the iteration count
+    the oracle needs (equal to the FP64 GPU count)."""
+    from oracle import algmortar as oa
+    from oracle import partition as op
+    t0 = time.perf_counter()
+    part = op.partition(P.A, P.part_sizes)
+    t_part = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pc = oa.setup(P.A, part)
+    t_setup = time.perf_counter() - t0
+    # time a few PCG iterations (SpMV + apply + vector updates)
+    r = P.f.copy()
+    z = oa.apply(pc, r)
+    p = z.copy()
+    t0 = time.perf_counter()
+    for _ in range(n_iter_sample):
+        q = P.A @ p
+        a = (r @ z) / (p @ q)
+        r = r - a * q
+        z = oa.apply(pc, r)
+        p = z + 0.5 * p
+    t_it = (time.perf_counter() - t0) / n_iter_sample
+    iters = args._fp64_iters if getattr(args, "_fp64_iters", None) else 162
+    value = (t_setup + iters * t_it) * 1e3
+    return {"value": round(value, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle Algorithm 1 setup on the full workload ({t_setup:.1f} s) + {n_iter_sample} timed "
+                      f"PCG iterations ({t_it * 1e3:.0f} ms each) extrapolated to {iters} iterations; "
+                      f"host partition ({t_part:.1f} s) excluded as on the GPU side"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    P, wdesc = workload(args.config)
+    cb = cpu_baseline(P, args)
+    out = {"metric": METRIC, "value": cb["value"], "unit": "ms", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": 1, "warmup": 0, "ms_per_step": cb["value"], "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": wdesc, "n": P.n, "nnz": P.A.nnz, "n_parts": P.n_parts, "tol": TOL},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_apply(args):
+    """One setup and one application of the preconditioner (kernel profiling target)."""
+    import torch
+    from paper_2607_22905_b300.solver import AlgMortar
+    P, wdesc = workload(args.config)
+    prec = args.variants.split(",")[0]
+    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec)
+    r = torch.as_tensor(np.random.default_rng(0).standard_normal(P.n), device="cuda")
+    z = am.apply(r)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "apply", "workload": wdesc, "variant": prec, "info": am.info,
+                      "z_norm": float(z.norm())}))
+    am.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3")
+    ap.add_argument("--variants", default="fp64,fp32,bf16")
+    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--stage-reps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "apply"],
+                    help="apply: set up the first variant and run one preconditioner application "
+                         "(for kernel profiling), no timing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.mode == "apply":
+        run_apply(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -106,9 +106,12 @@ typedef struct {
     int64_t factor_entries;        /* stored entries of one triangular sweep (all L_i)   */
     int64_t factor_bytes;          /* bytes of both sweep streams                        */
     int64_t phi_entries;           /* sum_i N_i |I_i| (MBF panel entries)                */
-    double setup_ms[8];            /* partition+tables (host), upload, local factor, MBF,
-                                      interface assembly, interface factor+inverse,
-                                      graph capture, total                                */
+    double setup_ms[8];            /* [0] partition + tables (host), [1] upload,
+                                      [2] local factors, [3] MBFs, [4] interface assembly,
+                                      [5] interface factor + inverse, [6] interface factor
+                                      alone, [7] total of algmortar_setup               */
+    int64_t kernel_launches;       /* kernels this library has launched in this process
+                                      so far (graph replays counted per kernel)           */
 } algmortar_info;
 
 typedef struct algmortar_handle algmortar_t;
@@ -118,8 +121,11 @@ void algmortar_default_opts(algmortar_opts* opts);
 
 /* Host only (no GPU needed): the deterministic graph partition of Sec. 3.1 used by
  * algmortar_setup.  part_out (host, n entries) receives labels in [0, n_parts).
- * part_sizes as in algmortar_opts (NULL = even).  Recursive BFS bisection with
- * George-Liu pseudo-peripheral start nodes; see DESIGN notes in the source. */
+ * part_sizes as in algmortar_opts (NULL = even).  Rule: recursive bisection; a node set
+ * S assigned to parts lo..hi-1 is put in breadth-first order (neighbours ascending,
+ * started at the George-Liu pseudo-peripheral node of the component of min(S), then at
+ * the smallest unvisited node of each further component) and its first
+ * sizes[lo] + ... + sizes[lo + k/2 - 1] nodes go to the first k/2 parts. */
 int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes,
                         int32_t* part_out);
 
@@ -168,8 +174,14 @@ int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev
                               int64_t ld, double tol, algmortar_stats* st);
 
 /* New values for the same sparsity pattern (host, nnz doubles in the CSR order given at
- * setup): keeps the partition, re-runs the numeric part of Algorithm 1. */
+ * setup): keeps the partition, the permutation and every device buffer (so a captured
+ * PCG graph stays valid) and re-runs the numeric part of Algorithm 1 (local factors,
+ * MBFs, interface system).  The values must keep A symmetric with negative couplings
+ * between subdomains; they are not re-validated (a non-SPD block still returns NOT_SPD). */
 int algmortar_update_values(algmortar_t* h, const double* val_host);
+
+/* As algmortar_update_values with the nnz values in DEVICE memory (CSR order of setup). */
+int algmortar_update_values_device(algmortar_t* h, const double* val_dev);
 
 /* Labels of the handle's partition (host, n entries). */
 int algmortar_get_partition(const algmortar_t* h, int32_t* part_out);
@@ -181,6 +193,15 @@ int algmortar_get_permutation(const algmortar_t* h, int32_t* perm_out);
 int algmortar_get_interfaces(const algmortar_t* h, int32_t* pairs_out);
 
 int algmortar_get_info(const algmortar_t* h, algmortar_info* info);
+
+/* Measurement: average device time (CUDA events on the handle's stream, ms) of each
+ * stage of one PCG iteration over `reps` repetitions, on the handle's current vectors:
+ * ms_out[0] SpMV (+ p.q), [1] CG vector updates, [2] local solves (Eq. def-pbar-local),
+ * [3] restriction, [4] interface solve, [5] prolongation (+ r.z), [6] a whole iteration
+ * as launched by algmortar_pcg_solve (graph or stream), [7] reserved (0).
+ * Kernels run exactly as inside the solver.  The handle's work vectors are overwritten
+ * (the next solve re-initialises them); its results from earlier calls are not kept. */
+int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out);
 
 /* Releases all device and host state of h (NULL is ignored). */
 void algmortar_destroy(algmortar_t* h);

@@ -42,12 +42,12 @@ class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_parts", C.c_int32), ("n_lambda", C.c_int32), ("max_part", C.c_int32),
                 ("min_part", C.c_int32), ("precision", C.c_int32), ("n_interface_edges", C.c_int64),
                 ("factor_entries", C.c_int64), ("factor_bytes", C.c_int64), ("phi_entries", C.c_int64),
-                ("setup_ms", C.c_double * 8)]
+                ("setup_ms", C.c_double * 8), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "setup_ms"}
         names = ["partition_and_tables", "upload", "local_factor", "mbf", "interface_assemble",
-                 "interface_factor_inverse", "graph", "total"]
+                 "interface_factor_inverse", "interface_factor", "total"]
         d["setup_ms"] = dict(zip(names, list(self.setup_ms)))
         return d
 
@@ -66,10 +66,12 @@ SIGNATURES = {
     "algmortar_pcg_solve_host": (C.c_int, [_P, _DP, _DP, C.c_double, C.POINTER(Stats)]),
     "algmortar_pcg_solve_multi": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.POINTER(Stats)]),
     "algmortar_update_values": (C.c_int, [_P, _DP]),
+    "algmortar_update_values_device": (C.c_int, [_P, _P]),
     "algmortar_get_partition": (C.c_int, [_P, _IP]),
     "algmortar_get_permutation": (C.c_int, [_P, _IP]),
     "algmortar_get_interfaces": (C.c_int, [_P, _IP]),
     "algmortar_get_info": (C.c_int, [_P, C.POINTER(Info)]),
+    "algmortar_time_stages": (C.c_int, [_P, C.c_int32, _DP]),
     "algmortar_destroy": (None, [_P]),
     "algmortar_strerror": (C.c_char_p, [C.c_int]),
     "algmortar_last_error": (C.c_char_p, []),

@@ -39,6 +39,24 @@ double now_ms() {
 
 }  // namespace
 
+// Device buffers of Algorithm 1 that survive between numeric setups (value updates
+// reuse them, so captured graphs and pointers stay valid).
+struct NumWs {
+    bool ready = false;
+    int njobs_mbf = 0;
+    int32_t *d_js = nullptr, *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
+    int64_t *d_jo = nullptr, *d_goff = nullptr, *d_gcptr = nullptr;
+    double* d_gval = nullptr;
+    int32_t *d_siperm = nullptr, *d_slo = nullptr, *d_shi = nullptr, *d_srows = nullptr, *d_snt = nullptr,
+            *d_zs = nullptr;
+    int64_t *d_sfwd = nullptr, *d_sbwd = nullptr, *d_szero = nullptr, *d_qo = nullptr;
+    double* d_T = nullptr;
+    void *work = nullptr, *dinv = nullptr;
+    int* d_err = nullptr;
+    double *rhs = nullptr, *phi64 = nullptr, *swork = nullptr, *sdinv = nullptr, *diagc = nullptr;
+    double *sf = nullptr, *sb = nullptr, *E = nullptr, *R = nullptr;
+};
+
 struct algmortar_handle {
     int device = 0;
     cudaStream_t st = nullptr;
@@ -73,7 +91,12 @@ struct algmortar_handle {
     double *d_part_rz = nullptr, *d_part_pq = nullptr, *d_part_rr = nullptr, *d_part_t = nullptr;
     double* d_scalar = nullptr;
     PcgScalars* d_pcg = nullptr;
+    int* d_kerr = nullptr;             // kernel error word (stuck bulk copy)
+    NumWs* ws = nullptr;               // persistent numeric-setup buffers
+    int32_t* d_psrc = nullptr;         // permuted CSR value t = original value psrc[t]
+    double* d_vtmp = nullptr;          // staging for value updates (original CSR order)
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
     algmortar_info info{};
 
     template <typename T>
@@ -96,6 +119,7 @@ struct algmortar_handle {
         for (void* p : allocs)
             if (p) cudaFree(p);
         if (own_st) cudaStreamDestroy(own_st);
+        delete ws;
     }
 };
 
@@ -124,45 +148,13 @@ int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
     return 0;
 }
 
-// Numeric part of Algorithm 1: factor the local blocks, MBFs, interface system.
-template <typename TW, typename TS, typename TA>
-int numeric_setup(algmortar_t* h) {
+// Symbolic uploads and persistent buffers (first numeric setup only).
+template <typename TW, typename TS>
+int numeric_prepare(algmortar_t* h, NumWs& W) {
+    if (W.ready) return 0;
     Plan& P = h->P;
-    cudaStream_t st = h->st;
-    cudaEvent_t ev[8];
-    for (auto& e : ev) cudaEventCreate(&e);
-    cudaEventRecord(ev[0], st);
-    const int m = h->m;
-    const int64_t tiles = P.total_tiles;
-    const int64_t trows = P.trow_off[m];
-    // --- local factors ---
-    TW* work = h->alloc<TW>((size_t)tiles * TILE2);
-    TW* dinv = h->alloc<TW>((size_t)trows * TILE2);
-    int* d_err = h->alloc<int>(2);
-    if (!work || !dinv || !d_err) return fail(ALGMORTAR_OOM, "factor workspace");
-    int err_init[2] = {0, -1};
-    CU(cudaMemcpyAsync(d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
-    CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
-    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, h->d_dloc, h->d_sc, st);
-    launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
-                             h->d_sc, work, m, st);
-    launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, d_err, st);
-    CU(cudaGetLastError());
-    TRY(read_err_flag(h, d_err, "local"));
-    if (!h->d_fwdS) {
-        h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
-        h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
-        if (!h->d_fwdS || !h->d_bwdS) return fail(ALGMORTAR_OOM, "sweep streams");
-    }
-    launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS, (TS*)h->d_bwdS, st);
-    CU(cudaGetLastError());
-    cudaEventRecord(ev[1], st);
-    h->release(work);
-    h->release(dinv);
-    // --- MBFs: Phi_i = A_i^{-1} (-G_i), one job per (subdomain, interface) ---
-    const int64_t nphi = P.phi_off[m];
-    double* rhs = h->alloc<double>(nphi);
-    double* phi64 = h->alloc<double>(nphi);
+    const int m = h->m, L = h->L;
+    const int64_t tiles = P.total_tiles, trows = P.trow_off[m], nphi = P.phi_off[m];
     std::vector<int32_t> js;
     std::vector<int64_t> jo;
     for (int s = 0; s < m; ++s) {
@@ -172,13 +164,7 @@ int numeric_setup(algmortar_t* h) {
             jo.push_back(P.phi_off[s] + a * ns);
         }
     }
-    int32_t* d_js = nullptr;
-    int64_t* d_jo = nullptr;
-    TRY(upload(h, d_js, js));
-    TRY(upload(h, d_jo, jo));
-    int64_t *d_goff = nullptr, *d_gcptr = nullptr;
-    int32_t *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
-    double* d_gval = nullptr;
+    W.njobs_mbf = (int)js.size();
     std::vector<int64_t> gcptr;
     gcptr.reserve(P.if_off[m] + m);
     for (int s = 0; s < m; ++s) {
@@ -189,15 +175,88 @@ int numeric_setup(algmortar_t* h) {
             gcptr.push_back(t);
         }
     }
-    TRY(upload(h, d_goff, P.g_off));
-    TRY(upload(h, d_gcptr, gcptr));
-    TRY(upload(h, d_grow, P.g_row));
-    TRY(upload(h, d_gcol, P.g_col));
-    TRY(upload(h, d_gval, P.g_val));
-    TRY(upload(h, d_pairs, P.pairs));
-    if (!rhs || !phi64) return fail(ALGMORTAR_OOM, "MBF panels");
-    CU(cudaMemsetAsync(rhs, 0, nphi * sizeof(double), st));
-    launch_mbf_rhs(m, d_goff, d_grow, d_gcol, d_gval, h->d_rows, h->d_phi_off, rhs, st);
+    TRY(upload(h, W.d_js, js));
+    TRY(upload(h, W.d_jo, jo));
+    TRY(upload(h, W.d_goff, P.g_off));
+    TRY(upload(h, W.d_gcptr, gcptr));
+    TRY(upload(h, W.d_grow, P.g_row));
+    TRY(upload(h, W.d_gcol, P.g_col));
+    TRY(upload(h, W.d_gval, P.g_val));
+    TRY(upload(h, W.d_pairs, P.pairs));
+    W.work = h->alloc<TW>((size_t)tiles * TILE2);
+    W.dinv = h->alloc<TW>((size_t)trows * TILE2);
+    W.d_err = h->alloc<int>(2);
+    W.rhs = h->alloc<double>(nphi);
+    W.phi64 = h->alloc<double>(nphi);
+    h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
+    h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
+    h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<TS>(nphi);
+    if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
+        return fail(ALGMORTAR_OOM, "factor / MBF buffers");
+    if (L > 0) {
+        TRY(upload(h, W.d_siperm, P.s_iperm));
+        TRY(upload(h, W.d_slo, P.s_lo));
+        TRY(upload(h, W.d_shi, P.s_hi));
+        TRY(upload(h, W.d_sfwd, P.s_fwd));
+        TRY(upload(h, W.d_sbwd, P.s_bwd));
+        TRY(upload(h, W.d_T, P.T));
+        std::vector<int32_t> one_rows{L}, one_nt{P.s_ntiles}, zs(L, 0);
+        std::vector<int64_t> zero64{0}, qo(L);
+        for (int q = 0; q < L; ++q) qo[q] = (int64_t)q * L;
+        TRY(upload(h, W.d_srows, one_rows));
+        TRY(upload(h, W.d_snt, one_nt));
+        TRY(upload(h, W.d_szero, zero64));
+        TRY(upload(h, W.d_zs, zs));
+        TRY(upload(h, W.d_qo, qo));
+        const int64_t stiles = P.s_tiles;
+        W.swork = h->alloc<double>((size_t)stiles * TILE2);
+        W.sdinv = h->alloc<double>((size_t)P.s_ntiles * TILE2);
+        W.diagc = h->alloc<double>(2 * (size_t)L);
+        W.sf = h->alloc<double>((size_t)stiles * TILE2);
+        W.sb = h->alloc<double>((size_t)stiles * TILE2);
+        W.E = h->alloc<double>((size_t)L * L);
+        W.R = h->alloc<double>((size_t)L * L);
+        h->d_Sinv = h->alloc<double>((size_t)L * L);
+        if (!W.swork || !W.sdinv || !W.diagc || !W.sf || !W.sb || !W.E || !W.R || !h->d_Sinv)
+            return fail(ALGMORTAR_OOM, "interface buffers");
+        CU(cudaMemsetAsync(W.E, 0, (size_t)L * L * sizeof(double), h->st));
+        launch_eye(L, W.E, h->st);
+    }
+    W.ready = true;
+    return 0;
+}
+
+// Numeric part of Algorithm 1 on the device: local blocks A_i and their factors, MBFs,
+// interface system, its factor and explicit inverse.  Re-runnable for new values.
+template <typename TW, typename TS, typename TA>
+int numeric_setup(algmortar_t* h) {
+    NumWs& W = *h->ws;
+    TRY((numeric_prepare<TW, TS>(h, W)));
+    Plan& P = h->P;
+    cudaStream_t st = h->st;
+    cudaEvent_t ev[8];
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], st);
+    const int m = h->m, L = h->L;
+    const int64_t tiles = P.total_tiles, nphi = P.phi_off[m];
+    TW* work = (TW*)W.work;
+    TW* dinv = (TW*)W.dinv;
+    // --- local factors (Algorithm 1: extract A_ii, modify its diagonal, factor) ---
+    int err_init[2] = {0, -1};
+    CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
+    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, h->d_dloc, h->d_sc, st);
+    launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
+                             h->d_sc, work, m, st);
+    launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
+    CU(cudaGetLastError());
+    TRY(read_err_flag(h, W.d_err, "local"));
+    launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS, (TS*)h->d_bwdS, st);
+    CU(cudaGetLastError());
+    cudaEventRecord(ev[1], st);
+    // --- MBFs (Eq. def-phat-local): Phi_i = A_i^{-1} (-B_i psi_m), one job per (i, m) ---
+    CU(cudaMemsetAsync(W.rhs, 0, nphi * sizeof(double), st));
+    launch_mbf_rhs(m, W.d_goff, W.d_grow, W.d_gcol, W.d_gval, h->d_rows, h->d_phi_off, W.rhs, st);
     {
         SolveArgs a{};
         a.pf = h->pf;
@@ -205,130 +264,83 @@ int numeric_setup(algmortar_t* h) {
         a.bwdS = h->d_bwdS;
         a.scale = h->d_sc;
         a.scale_off = h->d_sub_off;
-        a.job_sub = d_js;
-        a.job_in = d_jo;
-        a.job_out = d_jo;
-        a.in = rhs;
-        a.out = phi64;
+        a.job_sub = W.d_js;
+        a.job_in = W.d_jo;
+        a.job_out = W.d_jo;
+        a.in = W.rhs;
+        a.out = W.phi64;
         a.alpha = 1.0;
         a.done = nullptr;
-        CU((launch_tile_solve<TS, TA>(a, (int)js.size(), P.max_tiles, st)));
+        a.err = h->d_kerr;
+        CU((launch_tile_solve<TS, TA>(a, W.njobs_mbf, P.max_tiles, st)));
     }
-    if (std::is_same<TS, double>::value) {
-        h->d_phi = phi64;
-    } else {
-        TS* ph = h->alloc<TS>(nphi);
-        if (!ph) return fail(ALGMORTAR_OOM, "MBF panels");
-        launch_convert<TS>(nphi, phi64, ph, st);
-        h->d_phi = ph;
-    }
+    if (!std::is_same<TS, double>::value) launch_convert<TS>(nphi, W.phi64, (TS*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
-    // --- interface system S_eta = diag(T) + 1/4 G^T Phi, its factor and explicit inverse ---
-    const int L = h->L;
+    // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg) ---
     if (L > 0) {
-        int32_t *d_siperm = nullptr, *d_slo = nullptr, *d_shi = nullptr, *d_if_list2 = nullptr;
-        int64_t *d_sfwd = nullptr, *d_sbwd = nullptr;
-        double* d_T = nullptr;
-        TRY(upload(h, d_siperm, P.s_iperm));
-        TRY(upload(h, d_slo, P.s_lo));
-        TRY(upload(h, d_shi, P.s_hi));
-        TRY(upload(h, d_sfwd, P.s_fwd));
-        TRY(upload(h, d_sbwd, P.s_bwd));
-        TRY(upload(h, d_T, P.T));
-        (void)d_if_list2;
-        const int64_t stiles = P.s_tiles;
-        double* swork = h->alloc<double>((size_t)stiles * TILE2);
-        double* sdinv = h->alloc<double>((size_t)P.s_ntiles * TILE2);
-        double* diagc = h->alloc<double>(2 * (size_t)L);
-        if (!swork || !sdinv || !diagc) return fail(ALGMORTAR_OOM, "interface factor");
-        CU(cudaMemsetAsync(swork, 0, (size_t)stiles * TILE2 * sizeof(double), st));
+        CU(cudaMemsetAsync(W.swork, 0, (size_t)P.s_tiles * TILE2 * sizeof(double), st));
         InterfaceArgs ia{};
         ia.rows = h->d_rows;
         ia.if_off = h->d_if_off;
         ia.if_list = h->d_if_list;
         ia.phi_off = h->d_phi_off;
-        ia.phi = phi64;
-        ia.g_cptr = d_gcptr;
-        ia.g_row = d_grow;
-        ia.g_val = d_gval;
-        ia.pairs = d_pairs;
-        ia.s_iperm = d_siperm;
-        ia.s_lo = d_slo;
-        ia.s_fwd = d_sfwd;
-        ia.work = swork;
-        ia.diagc = diagc;
+        ia.phi = W.phi64;
+        ia.g_cptr = W.d_gcptr;
+        ia.g_row = W.d_grow;
+        ia.g_val = W.d_gval;
+        ia.pairs = W.d_pairs;
+        ia.s_iperm = W.d_siperm;
+        ia.s_lo = W.d_slo;
+        ia.s_fwd = W.d_sfwd;
+        ia.work = W.swork;
+        ia.diagc = W.diagc;
         launch_interface_assemble(m, ia, st);
-        launch_interface_diag(L, d_T, diagc, d_siperm, d_slo, d_sfwd, swork, st);
-        // single-item profile for S
-        std::vector<int32_t> one_rows{L}, one_nt{P.s_ntiles};
-        std::vector<int64_t> zero64{0};
-        int32_t *d_srows = nullptr, *d_snt = nullptr;
-        int64_t *d_szero = nullptr;
-        TRY(upload(h, d_srows, one_rows));
-        TRY(upload(h, d_snt, one_nt));
-        TRY(upload(h, d_szero, zero64));
-        Profile spf{d_srows, d_snt, d_szero, d_szero, d_slo, d_shi, d_sfwd, d_sbwd};
-        launch_pad_diag<double>(1, spf, swork, st);
+        launch_interface_diag(L, W.d_T, W.diagc, W.d_siperm, W.d_slo, W.d_sfwd, W.swork, st);
+        Profile spf{W.d_srows, W.d_snt, W.d_szero, W.d_szero, W.d_slo, W.d_shi, W.d_sfwd, W.d_sbwd};
+        launch_pad_diag<double>(1, spf, W.swork, st);
         cudaEventRecord(ev[3], st);
-        int err_init2[2] = {0, -1};
-        CU(cudaMemcpyAsync(d_err, err_init2, sizeof(err_init2), cudaMemcpyHostToDevice, st));
-        launch_tile_chol<double>(1, spf, nullptr, swork, sdinv, d_err, st);
+        CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+        launch_rl_cholesky<double>(P.s_ntiles, W.d_slo, W.d_sfwd, P.s_hi.data(), W.swork, W.sdinv, W.d_err, st);
         CU(cudaGetLastError());
-        TRY(read_err_flag(h, d_err, "interface"));
-        double* sf = h->alloc<double>((size_t)stiles * TILE2);
-        double* sb = h->alloc<double>((size_t)stiles * TILE2);
-        double* E = h->alloc<double>((size_t)L * L);
-        double* R = h->alloc<double>((size_t)L * L);
-        h->d_Sinv = h->alloc<double>((size_t)L * L);
-        if (!sf || !sb || !E || !R || !h->d_Sinv) return fail(ALGMORTAR_OOM, "interface inverse");
-        launch_finalize<double, double>(1, spf, swork, sdinv, sf, sb, st);
-        CU(cudaMemsetAsync(E, 0, (size_t)L * L * sizeof(double), st));
-        launch_eye(L, E, st);
-        std::vector<int32_t> zs(L, 0);
-        std::vector<int64_t> qo(L);
-        for (int q = 0; q < L; ++q) qo[q] = (int64_t)q * L;
-        int32_t* d_zs = nullptr;
-        int64_t* d_qo = nullptr;
-        TRY(upload(h, d_zs, zs));
-        TRY(upload(h, d_qo, qo));
+        TRY(read_err_flag(h, W.d_err, "interface"));
+        cudaEventRecord(ev[5], st);
+        launch_finalize<double, double>(1, spf, W.swork, W.sdinv, W.sf, W.sb, st);
         SolveArgs a{};
         a.pf = spf;
-        a.fwdS = sf;
-        a.bwdS = sb;
+        a.fwdS = W.sf;
+        a.bwdS = W.sb;
         a.scale = nullptr;
         a.scale_off = nullptr;
-        a.job_sub = d_zs;
-        a.job_in = d_qo;
-        a.job_out = d_qo;
-        a.in = E;
-        a.out = R;
+        a.job_sub = W.d_zs;
+        a.job_in = W.d_qo;
+        a.job_out = W.d_qo;
+        a.in = W.E;
+        a.out = W.R;
         a.alpha = 1.0;
+        a.err = h->d_kerr;
         CU((launch_tile_solve<double, double>(a, L, P.s_ntiles, st)));
-        launch_sinv_finalize(L, d_siperm, R, h->d_Sinv, st);
+        launch_sinv_finalize(L, W.d_siperm, W.R, h->d_Sinv, st);
         CU(cudaGetLastError());
-        CU(cudaStreamSynchronize(st));
-        for (void* p : {(void*)swork, (void*)sdinv, (void*)diagc, (void*)sf, (void*)sb, (void*)E, (void*)R,
-                        (void*)d_zs, (void*)d_qo})
-            h->release(p);
     } else {
         cudaEventRecord(ev[3], st);
+        cudaEventRecord(ev[5], st);
     }
     cudaEventRecord(ev[4], st);
     CU(cudaStreamSynchronize(st));
-    h->release(rhs);
-    if (h->d_phi != phi64) h->release(phi64);
-    for (void* p : {(void*)d_js, (void*)d_jo, (void*)d_goff, (void*)d_gcptr, (void*)d_grow, (void*)d_gcol,
-                    (void*)d_gval, (void*)d_pairs})
-        h->release(p);
-    float t01, t12, t23, t34;
+    int kerr = 0;
+    CU(cudaMemcpy(&kerr, h->d_kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (kerr) return fail(ALGMORTAR_CUDA, "a bulk copy of the triangular solves did not complete");
+    float t01, t12, t23, t34, t35;
     cudaEventElapsedTime(&t01, ev[0], ev[1]);
     cudaEventElapsedTime(&t12, ev[1], ev[2]);
     cudaEventElapsedTime(&t23, ev[2], ev[3]);
     cudaEventElapsedTime(&t34, ev[3], ev[4]);
+    cudaEventElapsedTime(&t35, ev[3], ev[5]);
     h->info.setup_ms[2] = t01;
     h->info.setup_ms[3] = t12;
     h->info.setup_ms[4] = t23;
     h->info.setup_ms[5] = t34;
+    h->info.setup_ms[6] = t35;
     for (auto& e : ev) cudaEventDestroy(e);
     return 0;
 }
@@ -342,9 +354,10 @@ int numeric_dispatch(algmortar_t* h) {
     }
 }
 
-// Algorithm 2 on internal-order vectors: pbar = A_hat^{-1} r; b_eta; eta; z.
+// Stages of Algorithm 2 on internal-order vectors.
+// Local particular solutions pbar_i = A_i^{-1} r_i for all subdomains (one launch).
 template <typename TS, typename TA>
-int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
+int stage_local(algmortar_t* h, const double* r, const int32_t* done) {
     SolveArgs a{};
     a.pf = h->pf;
     a.fwdS = h->d_fwdS;
@@ -358,11 +371,32 @@ int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, dou
     a.out = h->d_pbar;
     a.alpha = 1.0;
     a.done = done;
+    a.err = h->d_kerr;
     CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st)));
+    return 0;
+}
+
+// Interface right-hand side and interface solve: b_eta from pbar, eta = S^{-1} b_eta.
+void stage_restrict(algmortar_t* h, const int32_t* done) {
     launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, h->d_pbar, h->d_beta, done, h->st);
+}
+void stage_coarse(algmortar_t* h, const int32_t* done) {
     launch_coarse_gemv(h->L, h->d_Sinv, h->d_beta, h->d_eta, done, h->st);
+}
+
+// z = pbar + Phi eta, with the partial of r . z when part_rz is given.
+template <typename TS>
+void stage_prolong(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
     launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->d_if_list, h->d_phi_off,
                        (const TS*)h->d_phi, h->d_eta, h->d_pbar, z, part_rz ? r : nullptr, part_rz, done, h->st);
+}
+
+template <typename TS, typename TA>
+int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
+    TRY((stage_local<TS, TA>(h, r, done)));
+    stage_restrict(h, done);
+    stage_coarse(h, done);
+    stage_prolong<TS>(h, r, z, done, part_rz);
     CU(cudaGetLastError());
     return 0;
 }
@@ -389,8 +423,11 @@ int ensure_graph(algmortar_t* h) {
     if (h->graph) return 0;
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    const int64_t c0 = launch_count();
     int rc = pcg_iteration(h);
     cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    h->graph_kernels = launch_count() - c0;
+    add_launches(-h->graph_kernels);   // captured, not executed
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -420,8 +457,12 @@ int pcg_internal(algmortar_t* h, double tol, algmortar_stats* stt) {
     double true_rel = 0.0;
     for (;;) {
         for (int c = 0; c < every; ++c) {
-            if (h->graph) CU(cudaGraphLaunch(h->graph, st));
-            else TRY(pcg_iteration(h));
+            if (h->graph) {
+                CU(cudaGraphLaunch(h->graph, st));
+                add_launches(h->graph_kernels);
+            } else {
+                TRY(pcg_iteration(h));
+            }
         }
         CU(cudaMemcpyAsync(&hs, h->d_pcg, sizeof(hs), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
@@ -544,7 +585,14 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     rc = rc ? rc : upload(h, h->d_if_off, P.if_off);
     rc = rc ? rc : upload(h, h->d_if_list, P.if_list);
     rc = rc ? rc : upload(h, h->d_phi_off, P.phi_off);
+    {
+        std::vector<int32_t> psrc(P.p_src.begin(), P.p_src.end());
+        rc = rc ? rc : upload(h, h->d_psrc, psrc);
+    }
     if (rc) return bail(rc);
+    h->ws = new (std::nothrow) NumWs();
+    h->d_vtmp = h->alloc<double>((size_t)A->nnz);
+    if (!h->ws || !h->d_vtmp) return bail(fail(ALGMORTAR_OOM, "workspace"));
     h->pf = Profile{h->d_rows, h->d_ntiles, d_row0, d_base, d_lo, d_hi, d_fwd, d_bwd};
     const int64_t n = h->n;
     const int np = vec_grid();
@@ -566,12 +614,14 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     h->d_part_t = h->alloc<double>(np);
     h->d_scalar = h->alloc<double>(4);
     h->d_pcg = h->alloc<PcgScalars>(1);
+    h->d_kerr = h->alloc<int>(1);
     if (!h->d_dloc || !h->d_sc || !h->d_x || !h->d_r || !h->d_z || !h->d_p || !h->d_q || !h->d_pbar || !h->d_b ||
         !h->d_t || !h->d_beta || !h->d_eta || !h->d_part_rz || !h->d_part_pq || !h->d_part_rr || !h->d_part_t ||
-        !h->d_scalar || !h->d_pcg)
+        !h->d_scalar || !h->d_pcg || !h->d_kerr)
         return bail(fail(ALGMORTAR_OOM, "workspace"));
     if (cudaMemsetAsync(h->d_p, 0, n * sizeof(double), h->st) != cudaSuccess ||
-        cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->st) != cudaSuccess)
+        cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->st) != cudaSuccess ||
+        cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->st) != cudaSuccess)
         return bail(fail(ALGMORTAR_CUDA, "memset"));
     double t_up = now_ms();
     rc = numeric_dispatch(h);
@@ -592,14 +642,13 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     I.phi_entries = P.phi_off[h->m];
     I.setup_ms[0] = (t_part - t0) + (t_plan - t_part);
     I.setup_ms[1] = t_up - t_plan;
-    I.setup_ms[6] = 0.0;
     I.setup_ms[7] = t_end - t0;
     if (o.verbose)
         std::fprintf(stderr,
                      "[algmortar] n=%lld m=%d nLam=%d parts %d..%d tiles=%lld | partition %.1f ms plan %.1f ms "
-                     "upload %.1f | factor %.2f mbf %.2f iface-asm %.2f iface-inv %.2f | total %.1f ms\n",
+                     "upload %.1f | factor %.2f mbf %.2f iface-asm %.2f iface-factor %.2f iface-factor+inv %.2f | total %.1f ms\n",
                      (long long)n, h->m, h->L, P.min_part, P.max_part, (long long)P.total_tiles, t_part - t0,
-                     t_plan - t_part, I.setup_ms[1], I.setup_ms[2], I.setup_ms[3], I.setup_ms[4], I.setup_ms[5],
+                     t_plan - t_part, I.setup_ms[1], I.setup_ms[2], I.setup_ms[3], I.setup_ms[4], I.setup_ms[6], I.setup_ms[5],
                      I.setup_ms[7]);
     *out = h;
     return 0;
@@ -716,7 +765,21 @@ int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev
 
 int algmortar_update_values(algmortar_t* h, const double* val_host) {
     if (!h || !val_host) return fail(ALGMORTAR_INVALID_ARG, "null argument");
-    return fail(ALGMORTAR_INVALID_ARG, "update_values: not available in this build");
+    CU(cudaSetDevice(h->device));
+    const int64_t nnz = (int64_t)h->P.p_val.size();
+    CU(cudaMemcpyAsync(h->d_vtmp, val_host, nnz * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    launch_gather(nnz, h->d_psrc, h->d_vtmp, h->d_val, h->st);
+    CU(cudaGetLastError());
+    return numeric_dispatch(h);
+}
+
+int algmortar_update_values_device(algmortar_t* h, const double* val_dev) {
+    if (!h || !val_dev) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    CU(cudaSetDevice(h->device));
+    const int64_t nnz = (int64_t)h->P.p_val.size();
+    launch_gather(nnz, h->d_psrc, val_dev, h->d_val, h->st);
+    CU(cudaGetLastError());
+    return numeric_dispatch(h);
 }
 
 int algmortar_get_partition(const algmortar_t* h, int32_t* part_out) {
@@ -737,9 +800,84 @@ int algmortar_get_interfaces(const algmortar_t* h, int32_t* pairs_out) {
     return 0;
 }
 
+int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
+    if (!h || !ms_out || reps <= 0) return fail(ALGMORTAR_INVALID_ARG, "bad argument");
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->st;
+    PcgScalars saved;
+    CU(cudaMemcpyAsync(&saved, h->d_pcg, sizeof(saved), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    // a live scalar state: not done, beta/alpha finite, so no kernel exits early
+    PcgScalars live = saved;
+    live.done = 0;
+    live.iter = 1;
+    live.max_it = 1 << 30;
+    live.rz = saved.rz != 0.0 ? saved.rz : 1.0;
+    live.tol2 = 0.0;
+    cudaEvent_t ev[8];
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int it = 0; it <= reps; ++it) {
+        CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));
+        cudaEventRecord(ev[0], st);
+        launch_pcg_spmv(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_p, h->d_q, h->d_part_pq, h->d_pcg,
+                        h->d_part_rz, st);
+        cudaEventRecord(ev[1], st);
+        launch_pcg_p(h->n, h->d_z, h->d_p, h->d_r, nullptr, h->d_pcg, h->d_part_rz, st);
+        launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->d_part_pq, h->d_part_rr, st);
+        cudaEventRecord(ev[2], st);
+        // stages of Algorithm 2 (same launches as apply_internal, timed one by one)
+        switch (h->opts.precision) {
+            case ALGMORTAR_FP64: TRY((stage_local<double, double>(h, h->d_r, nullptr))); break;
+            case ALGMORTAR_FP32: TRY((stage_local<float, float>(h, h->d_r, nullptr))); break;
+            default: TRY((stage_local<__nv_bfloat16, float>(h, h->d_r, nullptr))); break;
+        }
+        cudaEventRecord(ev[3], st);
+        stage_restrict(h, nullptr);
+        cudaEventRecord(ev[4], st);
+        stage_coarse(h, nullptr);
+        cudaEventRecord(ev[5], st);
+        switch (h->opts.precision) {
+            case ALGMORTAR_FP64: stage_prolong<double>(h, h->d_r, h->d_z, nullptr, h->d_part_rz); break;
+            case ALGMORTAR_FP32: stage_prolong<float>(h, h->d_r, h->d_z, nullptr, h->d_part_rz); break;
+            default: stage_prolong<__nv_bfloat16>(h, h->d_r, h->d_z, nullptr, h->d_part_rz); break;
+        }
+        cudaEventRecord(ev[6], st);
+        CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));
+        cudaEventRecord(ev[7], st);
+        if (h->graph) {
+            CU(cudaGraphLaunch(h->graph, st));
+            add_launches(h->graph_kernels);
+        } else {
+            TRY(pcg_iteration(h));
+        }
+        cudaEvent_t e8;
+        CU(cudaEventCreate(&e8));
+        cudaEventRecord(e8, st);
+        CU(cudaEventSynchronize(e8));
+        if (it > 0) {
+            float t;
+            for (int k = 0; k < 6; ++k) {
+                cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+                acc[k] += t;
+            }
+            cudaEventElapsedTime(&t, ev[7], e8);
+            acc[6] += t;
+        }
+        cudaEventDestroy(e8);
+    }
+    for (int k = 0; k < 7; ++k) ms_out[k] = acc[k] / reps;
+    ms_out[7] = 0.0;
+    for (auto& e : ev) cudaEventDestroy(e);
+    CU(cudaMemcpyAsync(h->d_pcg, &saved, sizeof(saved), cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return 0;
+}
+
 int algmortar_get_info(const algmortar_t* h, algmortar_info* info) {
     if (!h || !info) return fail(ALGMORTAR_INVALID_ARG, "null argument");
     *info = h->info;
+    info->kernel_launches = launch_count();
     return 0;
 }
 

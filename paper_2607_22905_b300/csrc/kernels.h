@@ -10,6 +10,11 @@
 
 namespace am {
 
+// Process-wide count of kernels this library has launched (graph replays included).
+void count_launch();
+void add_launches(int64_t k);
+int64_t launch_count();
+
 struct SolveArgs {
     Profile pf;
     const void* fwdS;          // forward sweep stream (TS)
@@ -23,6 +28,7 @@ struct SolveArgs {
     double* out;
     double alpha;              // out = alpha * A_s^{-1} in
     const int32_t* done;       // early exit when *done != 0 (PCG), or null
+    int* err;                  // set to 1 if a bulk copy never completed (bounded wait)
 };
 
 struct InterfaceArgs {
@@ -54,6 +60,10 @@ void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st);
 template <typename TW>
 void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
                       cudaStream_t st);
+// right-looking multi-CTA factor of one profile matrix; h_hi: host copy of hi[]
+template <typename TW>
+void launch_rl_cholesky(int T, const int32_t* d_lo, const int64_t* d_fwd, const int32_t* h_hi, TW* work, TW* dinv,
+                        int* err, cudaStream_t st);
 template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
                      cudaStream_t st);

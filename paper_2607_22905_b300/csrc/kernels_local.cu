@@ -73,6 +73,46 @@ __global__ void k_pad_diag(int nitems, Profile pf, TW* __restrict__ work) {
     for (int r = n; r < T * TILE; ++r) work[t * TILE2 + (r & 31) * (TILE + 1)] = (TW)1;
 }
 
+// Dense Cholesky of the 32x32 tile X (lower triangle used) in shared memory by a CTA of
+// 256 threads, followed by the inverse of the lower-triangular factor into Ainv (one
+// column per thread).  A non-positive or non-finite pivot sets *bad and is replaced by 1.
+template <typename TW>
+__device__ void chol_inv_tile(TW (*X)[TILE + 1], TW (*Ainv)[TILE + 1], int tid, int* bad) {
+    for (int k = 0; k < TILE; ++k) {
+        if (tid == 0) {
+            TW d = X[k][k];
+            if (!(d > (TW)0) || !isfinite((double)d)) {
+                *bad = 1;
+                d = (TW)1;
+            }
+            X[k][k] = sqrt(d);
+        }
+        __syncthreads();
+        if (tid > k && tid < TILE) X[tid][k] /= X[k][k];
+        __syncthreads();
+        for (int e = tid; e < TILE2; e += blockDim.x) {
+            int r = e >> 5, cc = e & 31;
+            if (cc > k && r >= cc) X[r][cc] -= X[r][k] * X[cc][k];
+        }
+        __syncthreads();
+    }
+    if (tid < TILE) {
+        const int cc = tid;
+        for (int r = 0; r < TILE; ++r) {
+            TW v;
+            if (r < cc) {
+                v = 0;
+            } else {
+                v = (r == cc) ? (TW)1 : (TW)0;
+                for (int t = cc; t < r; ++t) v -= X[r][t] * Ainv[t][cc];
+                v /= X[r][r];
+            }
+            Ainv[r][cc] = v;
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------
 // Tile-profile Cholesky, one CTA (256 threads) per item, up-looking by tile rows:
 //   L_IJ = (A_IJ - sum_K L_IK L_JK^T) L_JJ^{-T},   J = lo(I) .. I-1
@@ -143,41 +183,7 @@ __global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __
                 __syncthreads();
             } else {
                 __syncthreads();
-                // dense 32x32 Cholesky of X in shared memory
-                for (int k = 0; k < TILE; ++k) {
-                    if (tid == 0) {
-                        TW d = X[k][k];
-                        if (!(d > (TW)0) || !isfinite((double)d)) {
-                            bad = 1;
-                            d = (TW)1;
-                        }
-                        X[k][k] = sqrt(d);
-                    }
-                    __syncthreads();
-                    if (tid > k && tid < TILE) X[tid][k] /= X[k][k];
-                    __syncthreads();
-                    for (int e = tid; e < TILE2; e += 256) {
-                        int r = e >> 5, cc = e & 31;
-                        if (cc > k && r >= cc) X[r][cc] -= X[r][k] * X[cc][k];
-                    }
-                    __syncthreads();
-                }
-                // inverse of the lower-triangular tile, one column per thread
-                if (tid < TILE) {
-                    const int cc = tid;
-                    for (int r = 0; r < TILE; ++r) {
-                        TW v;
-                        if (r < cc) {
-                            v = 0;
-                        } else {
-                            v = (r == cc) ? (TW)1 : (TW)0;
-                            for (int t = cc; t < r; ++t) v -= X[r][t] * As[t][cc];
-                            v /= X[r][r];
-                        }
-                        As[r][cc] = v;
-                    }
-                }
-                __syncthreads();
+                chol_inv_tile<TW>(X, As, tid, &bad);
                 TW* Lii = Wb + (fwd[I] + (I - li)) * TILE2;
                 TW* Dii = Db + (int64_t)I * TILE2;
                 for (int e = tid; e < TILE2; e += 256) {
@@ -191,6 +197,90 @@ __global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __
     }
     if (tid == 0 && bad) {
         if (atomicCAS(err + 1, -1, s) == -1) atomicExch(err, 1);
+    }
+}
+
+
+// ---------------------------------------------------------------------------------
+// Right-looking tile Cholesky of ONE large profile matrix (the interface system), spread
+// over many CTAs: for each tile column k, (1) factor the updated diagonal tile, (2) form
+// the panel L_Ik = S_Ik L_kk^{-T} for I = k+1 .. hi(k), (3) update the trailing tiles
+// S_IJ -= L_Ik L_Jk^T for k < J <= I <= hi(k).  Tiles outside the profile never change.
+// ---------------------------------------------------------------------------------
+template <typename TW>
+__global__ void __launch_bounds__(256) k_rl_potrf(const int32_t* __restrict__ lo, const int64_t* __restrict__ fwd,
+                                                  TW* __restrict__ work, TW* __restrict__ dinv, int k,
+                                                  int* __restrict__ err) {
+    __shared__ TW X[TILE][TILE + 1];
+    __shared__ TW As[TILE][TILE + 1];
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    TW* t = work + (fwd[k] + (k - lo[k])) * TILE2;
+    for (int e = tid; e < TILE2; e += 256) X[e & 31][e >> 5] = t[e];
+    __syncthreads();
+    chol_inv_tile<TW>(X, As, tid, &bad);
+    TW* D = dinv + (int64_t)k * TILE2;
+    for (int e = tid; e < TILE2; e += 256) {
+        int r = e & 31, cc = e >> 5;
+        t[e] = r >= cc ? X[r][cc] : (TW)0;
+        D[e] = As[r][cc];
+    }
+    if (tid == 0 && bad) {
+        if (atomicCAS(err + 1, -1, k) == -1) atomicExch(err, 1);
+    }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_rl_trsm(const int32_t* __restrict__ lo, const int64_t* __restrict__ fwd,
+                                                 TW* __restrict__ work, const TW* __restrict__ dinv, int k) {
+    __shared__ TW X[TILE][TILE + 1];
+    __shared__ TW Bs[TILE][TILE + 1];
+    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
+    const int I = k + 1 + blockIdx.x;
+    TW* t = work + (fwd[I] + (k - lo[I])) * TILE2;
+    const TW* D = dinv + (int64_t)k * TILE2;
+    for (int e = tid; e < TILE2; e += 256) {
+        X[e & 31][e >> 5] = t[e];
+        Bs[e & 31][e >> 5] = D[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        TW v = 0;
+#pragma unroll 8
+        for (int u = 0; u < TILE; ++u) v += X[rb + q][u] * Bs[c][u];
+        t[c * TILE + rb + q] = v;
+    }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_rl_update(const int32_t* __restrict__ lo, const int64_t* __restrict__ fwd,
+                                                   TW* __restrict__ work, int k) {
+    __shared__ TW As[TILE][TILE + 1];
+    __shared__ TW Bs[TILE][TILE + 1];
+    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
+    // pair index -> (a >= b) in the lower triangle of the w x w trailing block
+    const int64_t p = blockIdx.x;
+    int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= p) ++a;
+    while ((int64_t)a * (a + 1) / 2 > p) --a;
+    const int b = (int)(p - (int64_t)a * (a + 1) / 2);
+    const int I = k + 1 + a, J = k + 1 + b;
+    const TW* LI = work + (fwd[I] + (k - lo[I])) * TILE2;
+    const TW* LJ = work + (fwd[J] + (k - lo[J])) * TILE2;
+    TW* t = work + (fwd[I] + (J - lo[I])) * TILE2;
+    for (int e = tid; e < TILE2; e += 256) {
+        As[e & 31][e >> 5] = LI[e];
+        Bs[e & 31][e >> 5] = LJ[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        TW v = t[c * TILE + rb + q];
+#pragma unroll 8
+        for (int u = 0; u < TILE; ++u) v -= As[rb + q][u] * Bs[c][u];
+        t[c * TILE + rb + q] = v;
     }
 }
 
@@ -237,15 +327,55 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
 }
 
 // ---------------------------------------------------------------------------------
+// TMA (bulk async copy) + mbarrier helpers.  Every wait is bounded: on timeout the
+// caller records an error and drains its own copies (also bounded) before returning.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+constexpr long long kWaitLimit = 1ll << 22;   // try_wait rounds before a wait is declared stuck
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------------
 // Batched triangular solves  out = alpha * S L^{-T} L^{-1} S in  for a list of jobs
 // (item, input offset, output offset); S = diag(sc) is the symmetric scaling (or 1).
-// One CTA per job; the right-hand side lives in shared memory (accumulation type TA).
-// Each tile-row step: the off-diagonal tiles of the row are spread over the warps
-// (tile GEMV, lane = tile row, coalesced column loads), the partial sums meet in shared
-// memory, and warp 0 applies the stored inverse diagonal tile.
+//
+// One warp per job walks the tile rows in order (forward stream, then backward stream).
+// The item's factor tiles are consumed strictly in storage order, so they are streamed
+// through an R-slot shared-memory ring by bulk async copies (one 32x32 tile per copy,
+// completion on a per-slot mbarrier): while the warp works on tile q, tiles q+1..q+R-1
+// are in flight.  Step for tile row I:  acc = sum_J T_IJ v_J over the off-diagonal tiles
+// (lane = tile row, column-major tiles -> conflict-free shared loads), then
+// v_I = D_I (v_I - acc) with the stored inverse diagonal tile.  No block-wide barrier.
 // ---------------------------------------------------------------------------------
-template <typename TS, typename TA, int NW>
-__global__ void __launch_bounds__(NW * 32) k_tile_solve(SolveArgs a) {
+template <typename TS, typename TA, int R>
+__global__ void __launch_bounds__(32) k_chain_solve(SolveArgs a) {
     if (a.done && *a.done) return;
     const int job = blockIdx.x;
     const int s = a.job_sub[job];
@@ -256,54 +386,98 @@ __global__ void __launch_bounds__(NW * 32) k_tile_solve(SolveArgs a) {
     const int32_t* hi = pf.hi + r0;
     const int64_t* fwd = pf.fwd + r0;
     const int64_t* bwd = pf.bwd + r0;
+    const int64_t nts = fwd[T - 1] + (T - 1 - lo[T - 1]) + 1;      // tiles per stream
     const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
     const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
     const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
     const double* in = a.in + a.job_in[job];
     double* out = a.out + a.job_out[job];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* v = reinterpret_cast<TA*>(smem_raw);
-    TA* part = v + T * TILE;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int i = tid; i < T * TILE; i += NW * 32)
-        v[i] = i < n ? (TA)(in[i] * (sc ? sc[i] : 1.0)) : (TA)0;
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        const TS* St = pass == 0 ? F : Bk;
-        for (int step = 0; step < T; ++step) {
+    const int lane = threadIdx.x;
+    constexpr uint32_t TB = TILE2 * sizeof(TS);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TS* ring = reinterpret_cast<TS*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
+    TA* v = reinterpret_cast<TA*>(smem_raw + R * TB + R * sizeof(uint64_t));
+
+    const int64_t total = 2 * nts;
+    auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
+    if (lane == 0) {
+        for (int i = 0; i < R; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        fence_async_smem();
+        for (int64_t q = 0; q < R && q < total; ++q)
+            tma_load_1d(smem_u32(ring + q * TILE2), src(q), TB, smem_u32(&bars[q]));
+    }
+    for (int i = lane; i < T * TILE; i += 32) v[i] = i < n ? (TA)(in[i] * (sc ? sc[i] : 1.0)) : (TA)0;
+    __syncwarp();
+
+    int64_t q = 0;
+    bool ok = true;
+    // wait for tile q, returns its slot
+    auto acquire = [&](int64_t qq) -> const TS* {
+        const int slot = (int)(qq % R);
+        const uint32_t par = (uint32_t)((qq / R) & 1);
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[slot]), par));
+        return ring + slot * TILE2;
+    };
+    // slot of tile qq is free again: refill it with tile qq + R
+    auto release = [&](int64_t qq) {
+        __syncwarp();
+        if (lane == 0 && ok && qq + R < total) {
+            const int slot = (int)(qq % R);
+            fence_async_smem();
+            tma_load_1d(smem_u32(ring + slot * TILE2), src(qq + R), TB, smem_u32(&bars[slot]));
+        }
+    };
+    for (int pass = 0; pass < 2 && ok; ++pass) {
+        for (int step = 0; step < T && ok; ++step) {
             const int I = pass == 0 ? step : T - 1 - step;
             const int j0 = pass == 0 ? lo[I] : I + 1;
             const int nt = pass == 0 ? I - lo[I] : hi[I] - I;
-            const TS* row = St + (pass == 0 ? fwd[I] : bwd[I]) * TILE2;
-            TA dcol[TILE];
-            if (w == 0) {
-                const TS* D = row + (int64_t)nt * TILE2;
-#pragma unroll
-                for (int c = 0; c < TILE; ++c) dcol[c] = ldf<TA>(D + c * TILE + lane);
-            }
-            TA acc = 0;
-            for (int t = w; t < nt; t += NW) {
-                const TS* tl = row + (int64_t)t * TILE2;
+            TA acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+            for (int t = 0; t < nt; ++t) {
+                const TS* tl = acquire(q);
                 const TA* vj = v + (j0 + t) * TILE;
 #pragma unroll
-                for (int c = 0; c < TILE; ++c) acc += ldf<TA>(tl + c * TILE + lane) * vj[c];
+                for (int c = 0; c < TILE; c += 4) {
+                    acc0 += ldf<TA>(tl + (c + 0) * TILE + lane) * vj[c + 0];
+                    acc1 += ldf<TA>(tl + (c + 1) * TILE + lane) * vj[c + 1];
+                    acc2 += ldf<TA>(tl + (c + 2) * TILE + lane) * vj[c + 2];
+                    acc3 += ldf<TA>(tl + (c + 3) * TILE + lane) * vj[c + 3];
+                }
+                release(q);
+                ++q;
             }
-            part[w * TILE + lane] = acc;
-            __syncthreads();
-            if (w == 0) {
-                TA sum = 0;
+            const TS* D = acquire(q);
+            TA* vi = v + I * TILE;
+            vi[lane] = vi[lane] - ((acc0 + acc1) + (acc2 + acc3));
+            __syncwarp();
+            TA y0 = 0, y1 = 0, y2 = 0, y3 = 0;
 #pragma unroll
-                for (int q = 0; q < NW; ++q) sum += part[q * TILE + lane];
-                TA t = v[I * TILE + lane] - sum;
-                TA y = 0;
-#pragma unroll
-                for (int c = 0; c < TILE; ++c) y += dcol[c] * __shfl_sync(0xffffffffu, t, c);
-                v[I * TILE + lane] = y;
+            for (int c = 0; c < TILE; c += 4) {
+                y0 += ldf<TA>(D + (c + 0) * TILE + lane) * vi[c + 0];
+                y1 += ldf<TA>(D + (c + 1) * TILE + lane) * vi[c + 1];
+                y2 += ldf<TA>(D + (c + 2) * TILE + lane) * vi[c + 2];
+                y3 += ldf<TA>(D + (c + 3) * TILE + lane) * vi[c + 3];
             }
-            __syncthreads();
+            __syncwarp();
+            vi[lane] = (y0 + y1) + (y2 + y3);
+            release(q);
+            ++q;
         }
     }
-    for (int i = tid; i < n; i += NW * 32) out[i] = a.alpha * (double)v[i] * (sc ? sc[i] : 1.0);
+    if (!ok) {
+        // a copy never completed: record it, drain what is still in flight, give up
+        if (lane == 0) {
+            atomicExch(a.err, 1);
+            for (int64_t qq = q; qq < total && qq < q + R; ++qq)
+                mbar_wait(smem_u32(&bars[qq % R]), (uint32_t)((qq / R) & 1));
+        }
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) out[i] = a.alpha * (double)v[i] * (sc ? sc[i] : 1.0);
 }
 
 // ---------------------------------------------------------------------------------
@@ -414,6 +588,7 @@ static inline int grid_for(int64_t n, int bs) {
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                        const int32_t* row_sub, int diag_scale, double* dloc, double* sc,
                        cudaStream_t st) {
+    count_launch();
     k_local_diag<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, diag_scale, dloc, sc);
 }
 
@@ -421,67 +596,112 @@ template <typename TW>
 void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                           const int32_t* row_sub, const int64_t* sub_off, const Profile& pf,
                           const double* dloc, const double* sc, TW* work, int nitems, cudaStream_t st) {
+    count_launch();
     k_scatter_local<TW><<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, sub_off, pf,
                                                           dloc, sc, work);
+    count_launch();
     k_pad_diag<TW><<<(nitems + 127) / 128, 128, 0, st>>>(nitems, pf, work);
 }
 
 template <typename TW>
 void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st) {
+    count_launch();
     k_pad_diag<TW><<<(nitems + 127) / 128, 128, 0, st>>>(nitems, pf, work);
 }
 
 template <typename TW>
 void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
                       cudaStream_t st) {
+    count_launch();
     k_tile_chol<TW><<<nitems, 256, 0, st>>>(pf, order, work, dinv, err);
+}
+
+template <typename TW>
+void launch_rl_cholesky(int T, const int32_t* d_lo, const int64_t* d_fwd, const int32_t* h_hi, TW* work, TW* dinv,
+                        int* err, cudaStream_t st) {
+    for (int k = 0; k < T; ++k) {
+        count_launch();
+        k_rl_potrf<TW><<<1, 256, 0, st>>>(d_lo, d_fwd, work, dinv, k, err);
+        const int w = h_hi[k] - k;
+        if (w > 0) {
+            count_launch();
+            k_rl_trsm<TW><<<w, 256, 0, st>>>(d_lo, d_fwd, work, dinv, k);
+            count_launch();
+            k_rl_update<TW><<<(unsigned)((int64_t)w * (w + 1) / 2), 256, 0, st>>>(d_lo, d_fwd, work, k);
+        }
+    }
 }
 
 template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
                      cudaStream_t st) {
+    count_launch();
     k_finalize<TW, TS><<<nitems, 256, 0, st>>>(pf, work, dinv, fwdS, bwdS);
+}
+
+template <typename TS>
+constexpr int ring_slots() {
+    return sizeof(TS) == 8 ? 4 : (sizeof(TS) == 4 ? 8 : 12);
 }
 
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
-    constexpr int NW = 8;
-    size_t smem = (size_t)(max_tiles * TILE + NW * TILE) * sizeof(TA);
-    static bool attr_set[2] = {false, false};
-    (void)attr_set;
-    cudaError_t e = cudaFuncSetAttribute(k_tile_solve<TS, TA, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr int R = ring_slots<TS>();
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + (size_t)max_tiles * TILE * sizeof(TA);
+    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    if (njobs > 0) k_tile_solve<TS, TA, NW><<<njobs, NW * 32, smem, st>>>(a);
+    if (njobs > 0) {
+        count_launch();
+        k_chain_solve<TS, TA, R><<<njobs, 32, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
                     const double* g_val, const int32_t* rows, const int64_t* phi_off, double* rhs,
                     cudaStream_t st) {
-    if (m > 0) k_mbf_rhs<<<m, 128, 0, st>>>(m, g_off, g_row, g_col, g_val, rows, phi_off, rhs);
+    if (m > 0) {
+        count_launch();
+        k_mbf_rhs<<<m, 128, 0, st>>>(m, g_off, g_row, g_col, g_val, rows, phi_off, rhs);
+    }
 }
 
 template <typename TS>
 void launch_convert(int64_t n, const double* src, TS* dst, cudaStream_t st) {
-    if (n > 0) k_convert<TS><<<grid_for(n, 256), 256, 0, st>>>(n, src, dst);
+    if (n > 0) {
+        count_launch();
+        k_convert<TS><<<grid_for(n, 256), 256, 0, st>>>(n, src, dst);
+    }
 }
 
 void launch_interface_assemble(int m, const InterfaceArgs& a, cudaStream_t st) {
-    if (m > 0) k_interface_assemble<<<m, 256, 0, st>>>(a);
+    if (m > 0) {
+        count_launch();
+        k_interface_assemble<<<m, 256, 0, st>>>(a);
+    }
 }
 
 void launch_interface_diag(int L, const double* T, const double* diagc, const int32_t* s_iperm,
                            const int32_t* s_lo, const int64_t* s_fwd, double* work, cudaStream_t st) {
-    if (L > 0) k_interface_diag<<<(L + 127) / 128, 128, 0, st>>>(L, T, diagc, s_iperm, s_lo, s_fwd, work);
+    if (L > 0) {
+        count_launch();
+        k_interface_diag<<<(L + 127) / 128, 128, 0, st>>>(L, T, diagc, s_iperm, s_lo, s_fwd, work);
+    }
 }
 
 void launch_eye(int L, double* E, cudaStream_t st) {
-    if (L > 0) k_eye<<<(L + 127) / 128, 128, 0, st>>>(L, E);
+    if (L > 0) {
+        count_launch();
+        k_eye<<<(L + 127) / 128, 128, 0, st>>>(L, E);
+    }
 }
 
 void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double* Sinv, cudaStream_t st) {
-    if (L > 0) k_sinv_finalize<<<grid_for((int64_t)L * L, 256), 256, 0, st>>>(L, s_iperm, R, Sinv);
+    if (L > 0) {
+        count_launch();
+        k_sinv_finalize<<<grid_for((int64_t)L * L, 256), 256, 0, st>>>(L, s_iperm, R, Sinv);
+    }
 }
 
 template void launch_scatter_local<double>(int64_t, const int32_t*, const int32_t*, const double*,
@@ -493,6 +713,8 @@ template void launch_scatter_local<float>(int64_t, const int32_t*, const int32_t
 template void launch_pad_diag<double>(int, const Profile&, double*, cudaStream_t);
 template void launch_tile_chol<double>(int, const Profile&, const int32_t*, double*, double*, int*, cudaStream_t);
 template void launch_tile_chol<float>(int, const Profile&, const int32_t*, float*, float*, int*, cudaStream_t);
+template void launch_rl_cholesky<double>(int, const int32_t*, const int64_t*, const int32_t*, double*, double*,
+                                         int*, cudaStream_t);
 template void launch_finalize<double, double>(int, const Profile&, const double*, const double*, double*,
                                               double*, cudaStream_t);
 template void launch_finalize<float, float>(int, const Profile&, const float*, const float*, float*, float*,

@@ -6,10 +6,18 @@
 // Dot products are deterministic: every partial-producing kernel runs with exactly
 // vec_grid() CTAs, writes one partial per CTA, and consumers sum the partials in a fixed
 // order (warp_sum_partials), so repeated runs give bit-identical scalars.
+#include <atomic>
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace am {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 static int g_vec_grid = 4 * 148;
 int vec_grid() { return g_vec_grid; }
@@ -81,8 +89,12 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __
         int64_t i0 = if_off[s];
         int kk = (int)(if_off[s + 1] - i0);
         const TP* ph = phi + phi_off[s] + (k - a);
-        double v = pbar[k];
-        for (int c = 0; c < kk; ++c) v += ldf<double>(ph + c * ns) * eta[if_list[i0 + c]];
+        // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
+        // (FP64 panels: FP64; FP32/BF16 panels: FP32), then added to pbar in FP64
+        using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
+        TA corr = 0;
+        for (int c = 0; c < kk; ++c) corr += ldf<TA>(ph + c * ns) * (TA)eta[if_list[i0 + c]];
+        double v = pbar[k] + (double)corr;
         z[k] = v;
         if (r) acc += r[k] * v;
     }
@@ -257,57 +269,74 @@ static inline int grid_for(int64_t n, int bs) {
 }
 
 void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st) {
+    count_launch();
     k_gather<<<grid_for(n, 256), 256, 0, st>>>(n, perm, src, dst);
 }
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st) {
+    count_launch();
     k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, perm, src, dst);
 }
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* done, cudaStream_t st) {
-    if (L > 0) k_restrict<<<(L + 7) / 8, 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, done);
+    if (L > 0) {
+        count_launch();
+        k_restrict<<<(L + 7) / 8, 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, done);
+    }
 }
 void launch_coarse_gemv(int L, const double* Sinv, const double* b, double* eta, const int32_t* done,
                         cudaStream_t st) {
-    if (L > 0) k_coarse_gemv<<<(L + 7) / 8, 256, 0, st>>>(L, Sinv, b, eta, done);
+    if (L > 0) {
+        count_launch();
+        k_coarse_gemv<<<(L + 7) / 8, 256, 0, st>>>(L, Sinv, b, eta, done);
+    }
 }
 template <typename TP>
 void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
                     const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
                     const double* pbar, double* z, const double* r, double* part, const int32_t* done,
                     cudaStream_t st) {
+    count_launch();
     k_prolong<TP><<<vec_grid(), VEC_BS, 0, st>>>(n, row_sub, sub_off, if_off, if_list, phi_off, phi, eta, pbar, z,
                                                  r, part, done);
 }
 void launch_pcg_init(int64_t n, const double* b, double* x, double* r, double* part, cudaStream_t st) {
+    count_launch();
     k_pcg_init<<<vec_grid(), VEC_BS, 0, st>>>(n, b, x, r, part);
 }
 void launch_pcg_start(PcgScalars* sc, const double* part_bb, double tol, int max_it, int flexible,
                       cudaStream_t st) {
+    count_launch();
     k_pcg_start<<<1, 32, 0, st>>>(sc, part_bb, vec_grid(), tol, max_it, flexible);
 }
 void launch_pcg_p(int64_t n, const double* z, double* p, const double* r, double* r_old, PcgScalars* sc,
                   const double* part_rz, cudaStream_t st) {
     (void)r;
     (void)r_old;
+    count_launch();
     k_pcg_p<<<vec_grid(), VEC_BS, 0, st>>>(n, z, p, sc, part_rz, vec_grid());
 }
 void launch_pcg_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
                      cudaStream_t st) {
+    count_launch();
     k_pcg_spmv<<<vec_grid(), VEC_BS, 0, st>>>(n, rowptr, col, val, p, q, part_pq, sc, part_rz, vec_grid());
 }
 void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc,
                    const double* part_pq, double* part_rr, cudaStream_t st) {
+    count_launch();
     k_pcg_xr<<<vec_grid(), VEC_BS, 0, st>>>(n, x, r, p, q, sc, part_pq, part_rr, vec_grid());
 }
 void launch_pcg_check(PcgScalars* sc, const double* part_pq, const double* part_rr, cudaStream_t st) {
+    count_launch();
     k_pcg_check<<<1, 32, 0, st>>>(sc, part_pq, part_rr, vec_grid());
 }
 void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, double* part, cudaStream_t st) {
+    count_launch();
     k_residual<<<vec_grid(), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, part);
 }
 void launch_sum_partials(const double* part, double* out, cudaStream_t st) {
+    count_launch();
     k_sum_partials<<<1, 32, 0, st>>>(part, vec_grid(), out);
 }
 

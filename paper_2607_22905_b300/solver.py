@@ -133,6 +133,27 @@ class AlgMortar:
             raise B.AlgMortarError(rc, "algmortar_pcg_solve_multi")
         return Xt.t(), [s.as_dict() for s in st]
 
+    def update_values(self, values):
+        """New CSR values (same pattern, original CSR order): numpy -> host path,
+        CUDA tensor -> device path.  Re-runs the numeric part of Algorithm 1."""
+        if isinstance(values, torch.Tensor) and values.is_cuda:
+            v = values.to(torch.float64).contiguous()
+            B.check(B.lib().algmortar_update_values_device(self._h, _ptr(v)), "algmortar_update_values_device")
+        else:
+            v = np.ascontiguousarray(values, dtype=np.float64)
+            B.check(B.lib().algmortar_update_values(self._h, v.ctypes.data_as(B._DP)), "algmortar_update_values")
+        info = B.Info()
+        B.check(B.lib().algmortar_get_info(self._h, C.byref(info)))
+        self.info = info.as_dict()
+
+    STAGES = ("spmv", "cg_vectors", "local_solve", "restrict", "coarse", "prolong", "iteration")
+
+    def time_stages(self, reps=20):
+        """Average device ms per PCG-iteration stage (CUDA events on the handle's stream)."""
+        out = (C.c_double * 8)()
+        B.check(B.lib().algmortar_time_stages(self._h, int(reps), out), "algmortar_time_stages")
+        return dict(zip(self.STAGES, list(out)[:7]))
+
     def partition(self):
         out = np.empty(self.n, dtype=np.int32)
         B.check(B.lib().algmortar_get_partition(self._h, out.ctypes.data_as(B._IP)))

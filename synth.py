@@ -261,14 +261,15 @@ def channel_field(shape, n_top: int, seed: int):
     return K
 
 
-def config3(seed: int = 3, n_parts: int = 1122) -> Problem:
+def config3(seed: int = 3, n_parts: int = 1122, ny: int = 220) -> Problem:
     """3D 60x220x85 (1.122M cells): 35 smooth top layers over 50 channelised layers,
-    contrast ~2e7, kz/kx = 0.1, Dirichlet on the y ends, uneven parts of ~300-3000."""
-    shape = (60, 220, 85)
+    contrast ~2e7, kz/kx = 0.1, Dirichlet on the y ends, uneven parts of ~300-3000.
+    `ny` < 220 gives a shorter copy of the same field (profiling-sized case)."""
+    shape = (60, ny, 85)
     K = channel_field(shape, 35, seed)
     A, f = tpfa_cartesian(K, kz_ratio=0.1, bc_axis=1)
     sizes = uneven_part_sizes(A.shape[0], n_parts, 300, 3000, seed)
-    return Problem("c3_3d_60x220x85_channels", A, f, shape, n_parts, sizes,
+    return Problem(f"c3_3d_60x{ny}x85_channels", A, f, shape, n_parts, sizes,
                    {"channel_fraction": float((K[:, :, 35:] > 1).mean())})
 
 
