@@ -84,6 +84,9 @@ typedef struct {
     const int32_t* part_sizes;     /* host, n_parts target sizes summing to n, or NULL for
                                       sizes differing by at most one (larger ones first)  */
     void* stream;                  /* cudaStream_t for all device work (NULL = default)   */
+    int32_t nd_depth;              /* interface solve: depth of the nested-dissection split
+                                      (2^depth groups from the partition's bisection tree);
+                                      -1 (default) picks ~1000-unknown interior blocks    */
 } algmortar_opts;
 
 typedef struct {
@@ -182,6 +185,18 @@ int algmortar_update_values(algmortar_t* h, const double* val_host);
 
 /* As algmortar_update_values with the nnz values in DEVICE memory (CSR order of setup). */
 int algmortar_update_values_device(algmortar_t* h, const double* val_dev);
+
+/* Adjoint gradient for TPFA matrices (not in the paper).  With the handle's current
+ * matrix A (values from setup or the last update) read as a two-point flux system --
+ * off-diagonal a_kl = -T_kl, T_kl = c 2 K_k K_l / (K_k + K_l) for any face factor c --
+ * plus Dirichlet half-faces summarised per cell (tb_k = sum_b T_b, tbp_k = sum_b T_b
+ * p_bc, so f_k = tbp_k), the state p (A p = f) and the adjoint lambda (A lambda = dL/dp),
+ * writes grad_k = dL/d ln K_k:
+ *   sum_l -(lambda_k - lambda_l)(p_k - p_l) T_kl K_l / (K_k + K_l) + lambda_k (tbp_k - p_k tb_k).
+ * All pointers: device, n doubles, original ordering.  Uses the handle's work vectors
+ * (do not call it between the stages of another call on the same handle). */
+int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* tb_dev, const double* tbp_dev,
+                            const double* p_dev, const double* lam_dev, double* grad_dev);
 
 /* Labels of the handle's partition (host, n entries). */
 int algmortar_get_partition(const algmortar_t* h, int32_t* part_out);

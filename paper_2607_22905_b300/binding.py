@@ -27,7 +27,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("diag_scale", C.c_int32), ("max_it", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("flexible", C.c_int32),
                 ("verbose", C.c_int32), ("device", C.c_int32), ("part_sizes", C.POINTER(C.c_int32)),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("nd_depth", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -67,6 +67,7 @@ SIGNATURES = {
     "algmortar_pcg_solve_multi": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.POINTER(Stats)]),
     "algmortar_update_values": (C.c_int, [_P, _DP]),
     "algmortar_update_values_device": (C.c_int, [_P, _P]),
+    "algmortar_tpfa_grad_lnK": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "algmortar_get_partition": (C.c_int, [_P, _IP]),
     "algmortar_get_permutation": (C.c_int, [_P, _IP]),
     "algmortar_get_interfaces": (C.c_int, [_P, _IP]),

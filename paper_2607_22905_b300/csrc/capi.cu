@@ -47,14 +47,39 @@ struct NumWs {
     int32_t *d_js = nullptr, *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
     int64_t *d_jo = nullptr, *d_goff = nullptr, *d_gcptr = nullptr;
     double* d_gval = nullptr;
-    int32_t *d_siperm = nullptr, *d_slo = nullptr, *d_shi = nullptr, *d_srows = nullptr, *d_snt = nullptr,
-            *d_zs = nullptr;
-    int64_t *d_sfwd = nullptr, *d_sbwd = nullptr, *d_szero = nullptr, *d_qo = nullptr;
     double* d_T = nullptr;
     void *work = nullptr, *dinv = nullptr;
     int* d_err = nullptr;
-    double *rhs = nullptr, *phi64 = nullptr, *swork = nullptr, *sdinv = nullptr, *diagc = nullptr;
-    double *sf = nullptr, *sb = nullptr, *E = nullptr, *R = nullptr;
+    double *rhs = nullptr, *phi64 = nullptr, *diagc = nullptr, *Sd = nullptr;
+    // interface groups as factor items (non-empty groups only)
+    int nitems = 0;
+    std::vector<int32_t> item_group;           // item -> group
+    std::vector<int64_t> item_row0, item_base; // host copies
+    std::vector<std::vector<int32_t>> item_hi; // host hi[] per item (right-looking launcher)
+    int32_t *d_irows = nullptr, *d_int = nullptr, *d_ilo = nullptr, *d_ihi = nullptr;
+    int64_t *d_irow0 = nullptr, *d_ibase = nullptr, *d_ifwd = nullptr, *d_ibwd = nullptr, *d_isrc = nullptr;
+    int32_t *d_titem = nullptr, *d_tI = nullptr, *d_tJ = nullptr;
+    int64_t ntiles_items = 0, trows_items = 0;
+    int max_tiles_items = 0;
+    double *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr, *gE = nullptr, *RHS = nullptr;
+    int32_t* d_gjob = nullptr;
+    int64_t *d_gjin = nullptr, *d_wjin = nullptr;
+    int32_t* d_wjob = nullptr;
+    int njobs_g = 0, njobs_w = 0;
+    int32_t *d_colitem = nullptr, *d_cola = nullptr;
+    int64_t ncols_w = 0;
+    int64_t *d_doff = nullptr, *d_entbase = nullptr;
+    int32_t* d_entg = nullptr;
+    int64_t nent = 0;
+    double* D = nullptr;
+    // separator Schur complement as a single dense item
+    int cT = 0;
+    std::vector<int32_t> c_hi;
+    int32_t *d_crows = nullptr, *d_cnt = nullptr, *d_clo = nullptr, *d_chi = nullptr, *d_cjob = nullptr;
+    int64_t *d_czero = nullptr, *d_cfwd = nullptr, *d_cbwd = nullptr, *d_cjin = nullptr;
+    double *cwork = nullptr, *cdinv = nullptr, *cf = nullptr, *cb = nullptr, *cE = nullptr;
+    int32_t* d_crowsq = nullptr;
+    int64_t* d_czerooff = nullptr;
 };
 
 struct algmortar_handle {
@@ -84,7 +109,13 @@ struct algmortar_handle {
     int64_t *d_if_off = nullptr, *d_phi_off = nullptr;
     int32_t* d_if_list = nullptr;
     void* d_phi = nullptr;
-    double* d_Sinv = nullptr;
+    // interface solve by nested dissection (ND order inside the handle)
+    NdSolveArgs nd{};
+    int32_t* nd_grows = nullptr;       // rows of each interface group (symmetrisation)
+    int32_t* d_ndpos = nullptr;        // interface id -> ND position
+    int32_t* d_ifpos = nullptr;        // if_list entries as ND positions (prolongation)
+    double* d_P = nullptr;             // sum_g a_g partial products
+    double* d_nat = nullptr;           // natural-order staging (stage outputs)
     // workspace
     double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_pbar = nullptr;
     double *d_beta = nullptr, *d_eta = nullptr, *d_b = nullptr, *d_t = nullptr;
@@ -94,6 +125,10 @@ struct algmortar_handle {
     int* d_kerr = nullptr;             // kernel error word (stuck bulk copy)
     NumWs* ws = nullptr;               // persistent numeric-setup buffers
     int32_t* d_psrc = nullptr;         // permuted CSR value t = original value psrc[t]
+    int64_t* d_ell_ptr = nullptr;      // sliced-ELL copy of the matrix (SpMV)
+    int32_t *d_ell_col = nullptr, *d_ell_src = nullptr;
+    double* d_ell_val = nullptr;
+    int64_t n_ell = 0;
     double* d_vtmp = nullptr;          // staging for value updates (original CSR order)
     cudaGraphExec_t graph = nullptr;
     int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
@@ -194,33 +229,222 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
     if (L > 0) {
-        TRY(upload(h, W.d_siperm, P.s_iperm));
-        TRY(upload(h, W.d_slo, P.s_lo));
-        TRY(upload(h, W.d_shi, P.s_hi));
-        TRY(upload(h, W.d_sfwd, P.s_fwd));
-        TRY(upload(h, W.d_sbwd, P.s_bwd));
         TRY(upload(h, W.d_T, P.T));
-        std::vector<int32_t> one_rows{L}, one_nt{P.s_ntiles}, zs(L, 0);
-        std::vector<int64_t> zero64{0}, qo(L);
-        for (int q = 0; q < L; ++q) qo[q] = (int64_t)q * L;
-        TRY(upload(h, W.d_srows, one_rows));
-        TRY(upload(h, W.d_snt, one_nt));
-        TRY(upload(h, W.d_szero, zero64));
-        TRY(upload(h, W.d_zs, zs));
-        TRY(upload(h, W.d_qo, qo));
-        const int64_t stiles = P.s_tiles;
-        W.swork = h->alloc<double>((size_t)stiles * TILE2);
-        W.sdinv = h->alloc<double>((size_t)P.s_ntiles * TILE2);
         W.diagc = h->alloc<double>(2 * (size_t)L);
-        W.sf = h->alloc<double>((size_t)stiles * TILE2);
-        W.sb = h->alloc<double>((size_t)stiles * TILE2);
-        W.E = h->alloc<double>((size_t)L * L);
-        W.R = h->alloc<double>((size_t)L * L);
-        h->d_Sinv = h->alloc<double>((size_t)L * L);
-        if (!W.swork || !W.sdinv || !W.diagc || !W.sf || !W.sb || !W.E || !W.R || !h->d_Sinv)
-            return fail(ALGMORTAR_OOM, "interface buffers");
-        CU(cudaMemsetAsync(W.E, 0, (size_t)L * L * sizeof(double), h->st));
-        launch_eye(L, W.E, h->st);
+        W.Sd = h->alloc<double>((size_t)L * L);
+        if (!W.diagc || !W.Sd) return fail(ALGMORTAR_OOM, "interface matrix");
+        // ---- groups (interior blocks) as dense factor items ----
+        const int G = P.nd_G;
+        const int64_t nin = P.nd_goff[G];
+        const int nsep = P.nd_nsep;
+        std::vector<int32_t> irows, int_, ilo, ihi, titem, tI, tJ, gjob, wjob, colitem, cola, entg, row_g, prow_g;
+        std::vector<int64_t> irow0, ibase, ifwd, ibwd, isrc, gjin, wjin, gioff(G, 0), woff(G, 0), doff(G, 0),
+            entbase(G, 0);
+        int64_t trow = 0, tb = 0, gi = 0, wo = 0, dof = 0, ent = 0;
+        for (int g = 0; g < G; ++g) {
+            const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
+            gioff[g] = gi;
+            woff[g] = wo;
+            doff[g] = dof;
+            entbase[g] = ent;
+            for (int64_t t = 0; t < ng; ++t) row_g.push_back(g);
+            for (int64_t t = 0; t < ag; ++t) prow_g.push_back(g);
+            if (ng > 0) {
+                const int it = (int)irows.size();
+                const int T = (int)((ng + TILE - 1) / TILE);
+                W.item_group.push_back(g);
+                W.item_row0.push_back(trow);
+                W.item_base.push_back(tb);
+                irows.push_back((int32_t)ng);
+                int_.push_back(T);
+                irow0.push_back(trow);
+                ibase.push_back(tb);
+                isrc.push_back(P.nd_goff[g] * L + P.nd_goff[g]);
+                std::vector<int32_t> hi(T, T - 1);
+                W.item_hi.push_back(hi);
+                for (int I = 0; I < T; ++I) {
+                    ilo.push_back(0);
+                    ihi.push_back(T - 1);
+                    ifwd.push_back((int64_t)I * (I + 1) / 2);
+                    ibwd.push_back((int64_t)(T - 1 - I) * (T - I) / 2);
+                    for (int J = 0; J <= I; ++J) {
+                        titem.push_back(it);
+                        tI.push_back(I);
+                        tJ.push_back(J);
+                    }
+                }
+                W.max_tiles_items = std::max(W.max_tiles_items, T);
+                trow += T;
+                tb += (int64_t)T * (T + 1) / 2;
+                for (int64_t c = 0; c < ng; ++c) {
+                    gjob.push_back(it);
+                    gjin.push_back(gi + c * ng);
+                }
+                for (int64_t c = 0; c < ag; ++c) {
+                    wjob.push_back(it);
+                    wjin.push_back(wo + c * ng);
+                    colitem.push_back(g);
+                    cola.push_back((int32_t)c);
+                }
+                for (int64_t e = 0; e < ag * ag; ++e) entg.push_back(g);
+            }
+            gi += ng * ng;
+            wo += ng * ag;
+            dof += ag * ag;
+            ent += (ng > 0) ? ag * ag : 0;
+        }
+        W.nitems = (int)irows.size();
+        W.ntiles_items = tb;
+        W.trows_items = trow;
+        W.njobs_g = (int)gjob.size();
+        W.njobs_w = (int)wjob.size();
+        W.ncols_w = (int64_t)colitem.size();
+        W.nent = (int64_t)entg.size();
+        // entries of groups without interior rows contribute nothing: rebase ent indices
+        TRY(upload(h, W.d_irows, irows));
+        TRY(upload(h, W.d_int, int_));
+        TRY(upload(h, W.d_irow0, irow0));
+        TRY(upload(h, W.d_ibase, ibase));
+        TRY(upload(h, W.d_ilo, ilo));
+        TRY(upload(h, W.d_ihi, ihi));
+        TRY(upload(h, W.d_ifwd, ifwd));
+        TRY(upload(h, W.d_ibwd, ibwd));
+        TRY(upload(h, W.d_isrc, isrc));
+        TRY(upload(h, W.d_titem, titem));
+        TRY(upload(h, W.d_tI, tI));
+        TRY(upload(h, W.d_tJ, tJ));
+        TRY(upload(h, W.d_gjob, gjob));
+        TRY(upload(h, W.d_gjin, gjin));
+        TRY(upload(h, W.d_wjob, wjob));
+        TRY(upload(h, W.d_wjin, wjin));
+        TRY(upload(h, W.d_colitem, colitem));
+        TRY(upload(h, W.d_cola, cola));
+        TRY(upload(h, W.d_entg, entg));
+        // ent_base must index the compacted entry list: recompute from entg
+        {
+            std::vector<int64_t> eb(G, 0);
+            int64_t o = 0;
+            for (int g = 0; g < G; ++g) {
+                eb[g] = o;
+                const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
+                if (ng > 0) o += ag * ag;
+            }
+            TRY(upload(h, W.d_entbase, eb));
+        }
+        TRY(upload(h, W.d_doff, doff));
+        W.gwork = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
+        W.gdinv = h->alloc<double>((size_t)std::max<int64_t>(trow, 1) * TILE2);
+        W.gf = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
+        W.gb = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
+        W.gE = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
+        W.RHS = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
+        W.D = h->alloc<double>((size_t)std::max<int64_t>(dof, 1));
+        double* Ginv = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
+        double* Wcm = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
+        double* Wrm = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
+        if (!W.gwork || !W.gdinv || !W.gf || !W.gb || !W.gE || !W.RHS || !W.D || !Ginv || !Wcm || !Wrm)
+            return fail(ALGMORTAR_OOM, "interface group buffers");
+        // blocks of groups without interior unknowns are never written: keep them zero
+        CU(cudaMemsetAsync(W.D, 0, (size_t)std::max<int64_t>(dof, 1) * sizeof(double), h->st));
+        // identity right-hand sides of each group (column-major n_g x n_g)
+        {
+            std::vector<double> eye;
+            CU(cudaMemsetAsync(W.gE, 0, (size_t)std::max<int64_t>(gi, 1) * sizeof(double), h->st));
+            std::vector<int64_t> diag_idx;
+            for (int g = 0; g < G; ++g) {
+                const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g];
+                for (int64_t c = 0; c < ng; ++c) diag_idx.push_back(gioff[g] + c * ng + c);
+            }
+            std::vector<double> ones(diag_idx.size(), 1.0);
+            double* d_ones = nullptr;
+            int64_t* d_didx = nullptr;
+            TRY(upload(h, d_ones, ones));
+            TRY(upload(h, d_didx, diag_idx));
+            launch_scatter_values((int64_t)diag_idx.size(), d_didx, d_ones, W.gE, h->st);
+        }
+        // per-iteration ND solve arguments
+        int64_t *d_goff = nullptr, *d_aoff = nullptr, *d_gioff = nullptr, *d_woff = nullptr;
+        int32_t *d_alist = nullptr, *d_sg = nullptr, *d_sidx = nullptr, *d_rowg = nullptr, *d_prowg = nullptr;
+        TRY(upload(h, d_goff, P.nd_goff));
+        TRY(upload(h, d_aoff, P.nd_aoff));
+        TRY(upload(h, d_gioff, gioff));
+        TRY(upload(h, d_woff, woff));
+        TRY(upload(h, d_alist, P.nd_alist));
+        TRY(upload(h, d_sg, P.nd_sg));
+        TRY(upload(h, d_sidx, P.nd_sidx));
+        TRY(upload(h, d_rowg, row_g));
+        TRY(upload(h, d_prowg, prow_g));
+        TRY(upload(h, h->d_ndpos, P.nd_pos));
+        {
+            std::vector<int32_t> gr(G);
+            for (int g = 0; g < G; ++g) gr[g] = (int32_t)(P.nd_goff[g + 1] - P.nd_goff[g]);
+            TRY(upload(h, h->nd_grows, gr));
+        }
+        {
+            std::vector<int32_t> ifpos(P.if_list.size());
+            for (size_t t = 0; t < ifpos.size(); ++t) ifpos[t] = P.nd_pos[P.if_list[t]];
+            TRY(upload(h, h->d_ifpos, ifpos));
+        }
+        h->d_P = h->alloc<double>((size_t)std::max<int64_t>(P.nd_aoff[G], 1));
+        h->d_nat = h->alloc<double>((size_t)L);
+        if (!h->d_P || !h->d_nat) return fail(ALGMORTAR_OOM, "interface vectors");
+        NdSolveArgs& a = h->nd;
+        a.G = G;
+        a.nsep = nsep;
+        a.nin = nin;
+        a.np = P.nd_aoff[G];
+        a.goff = d_goff;
+        a.aoff = d_aoff;
+        a.alist = d_alist;
+        a.sg = d_sg;
+        a.sidx = d_sidx;
+        a.row_g = d_rowg;
+        a.prow_g = d_prowg;
+        a.Ginv = Ginv;
+        a.gioff = d_gioff;
+        a.Wcm = Wcm;
+        a.Wrm = Wrm;
+        a.woff = d_woff;
+        // ---- separator Schur complement C as one dense item ----
+        if (nsep > 0) {
+            const int T = (nsep + TILE - 1) / TILE;
+            W.cT = T;
+            W.c_hi.assign(T, T - 1);
+            std::vector<int32_t> clo(T, 0), chi(T, T - 1), cj(nsep, 0);
+            std::vector<int64_t> cfwd(T), cbwd(T), cjin(nsep), czero{0};
+            for (int I = 0; I < T; ++I) {
+                cfwd[I] = (int64_t)I * (I + 1) / 2;
+                cbwd[I] = (int64_t)(T - 1 - I) * (T - I) / 2;
+            }
+            for (int q = 0; q < nsep; ++q) cjin[q] = (int64_t)q * nsep;
+            std::vector<int32_t> crows{nsep}, cnt{T};
+            TRY(upload(h, W.d_crows, crows));
+            TRY(upload(h, W.d_cnt, cnt));
+            TRY(upload(h, W.d_czero, czero));
+            TRY(upload(h, W.d_clo, clo));
+            TRY(upload(h, W.d_chi, chi));
+            TRY(upload(h, W.d_cfwd, cfwd));
+            TRY(upload(h, W.d_cbwd, cbwd));
+            TRY(upload(h, W.d_cjob, cj));
+            TRY(upload(h, W.d_cjin, cjin));
+            const int64_t ct = (int64_t)T * (T + 1) / 2;
+            W.cwork = h->alloc<double>((size_t)ct * TILE2);
+            W.cdinv = h->alloc<double>((size_t)T * TILE2);
+            W.cf = h->alloc<double>((size_t)ct * TILE2);
+            W.cb = h->alloc<double>((size_t)ct * TILE2);
+            W.cE = h->alloc<double>((size_t)nsep * nsep);
+            double* Cinv = h->alloc<double>((size_t)nsep * nsep);
+            if (!W.cwork || !W.cdinv || !W.cf || !W.cb || !W.cE || !Cinv)
+                return fail(ALGMORTAR_OOM, "separator buffers");
+            CU(cudaMemsetAsync(W.cE, 0, (size_t)nsep * nsep * sizeof(double), h->st));
+            launch_eye(nsep, W.cE, h->st);
+            std::vector<int32_t> sq{nsep};
+            std::vector<int64_t> z0{0};
+            TRY(upload(h, W.d_crowsq, sq));
+            TRY(upload(h, W.d_czerooff, z0));
+            a.Cinv = Cinv;
+            CU(prepare_nd_solve(nsep));
+        }
     }
     W.ready = true;
     return 0;
@@ -276,10 +500,13 @@ int numeric_setup(algmortar_t* h) {
     }
     if (!std::is_same<TS, double>::value) launch_convert<TS>(nphi, W.phi64, (TS*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
-    // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg) ---
+    // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg),
+    //     solved exactly by one level of nested dissection (kernels_coarse.cu) ---
     if (L > 0) {
-        CU(cudaMemsetAsync(W.swork, 0, (size_t)P.s_tiles * TILE2 * sizeof(double), st));
-        InterfaceArgs ia{};
+        const int G = P.nd_G, nsep = P.nd_nsep;
+        const int64_t sep0 = P.nd_goff[G];
+        CU(cudaMemsetAsync(W.Sd, 0, (size_t)L * L * sizeof(double), st));
+        NdAssembleArgs ia{};
         ia.rows = h->d_rows;
         ia.if_off = h->d_if_off;
         ia.if_list = h->d_if_list;
@@ -289,38 +516,76 @@ int numeric_setup(algmortar_t* h) {
         ia.g_row = W.d_grow;
         ia.g_val = W.d_gval;
         ia.pairs = W.d_pairs;
-        ia.s_iperm = W.d_siperm;
-        ia.s_lo = W.d_slo;
-        ia.s_fwd = W.d_sfwd;
-        ia.work = W.swork;
+        ia.nd_pos = h->d_ndpos;
+        ia.Sd = W.Sd;
         ia.diagc = W.diagc;
-        launch_interface_assemble(m, ia, st);
-        launch_interface_diag(L, W.d_T, W.diagc, W.d_siperm, W.d_slo, W.d_sfwd, W.swork, st);
-        Profile spf{W.d_srows, W.d_snt, W.d_szero, W.d_szero, W.d_slo, W.d_shi, W.d_sfwd, W.d_sbwd};
-        launch_pad_diag<double>(1, spf, W.swork, st);
+        ia.L = L;
+        launch_nd_assemble(m, ia, st);
+        launch_nd_diag(L, W.d_T, W.diagc, h->d_ndpos, W.Sd, st);
         cudaEventRecord(ev[3], st);
+        // interior blocks: dense tiles, right-looking factor per group, sweep streams
+        Profile gpf{W.d_irows, W.d_int, W.d_irow0, W.d_ibase, W.d_ilo, W.d_ihi, W.d_ifwd, W.d_ibwd};
+        launch_dense_to_tiles(W.ntiles_items, W.Sd, L, W.d_isrc, W.d_irows, W.d_ibase, W.d_titem, W.d_tI, W.d_tJ,
+                              W.gwork, st);
         CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
-        launch_rl_cholesky<double>(P.s_ntiles, W.d_slo, W.d_sfwd, P.s_hi.data(), W.swork, W.sdinv, W.d_err, st);
+        for (int it = 0; it < W.nitems; ++it) {
+            const int64_t r0 = W.item_row0[it], b0 = W.item_base[it];
+            launch_rl_cholesky<double>((int)W.item_hi[it].size(), W.d_ilo + r0, W.d_ifwd + r0, W.item_hi[it].data(),
+                                       W.gwork + b0 * TILE2, W.gdinv + r0 * TILE2, W.d_err, st);
+        }
         CU(cudaGetLastError());
-        TRY(read_err_flag(h, W.d_err, "interface"));
+        TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
+        launch_finalize<double, double>(W.nitems, gpf, W.gwork, W.gdinv, W.gf, W.gb, st);
+        // S_gg^{-1} (identity columns) and W_g = S_gg^{-1} S_{g,A_g}
+        launch_nd_rhs(W.ncols_w, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.woff, W.d_colitem,
+                      W.d_cola, W.RHS, st);
+        SolveArgs sa{};
+        sa.pf = gpf;
+        sa.fwdS = W.gf;
+        sa.bwdS = W.gb;
+        sa.alpha = 1.0;
+        sa.err = h->d_kerr;
+        sa.job_sub = W.d_gjob;
+        sa.job_in = W.d_gjin;
+        sa.job_out = W.d_gjin;
+        sa.in = W.gE;
+        sa.out = (double*)h->nd.Ginv;
+        CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
+        sa.job_sub = W.d_wjob;
+        sa.job_in = W.d_wjin;
+        sa.job_out = W.d_wjin;
+        sa.in = W.RHS;
+        sa.out = (double*)h->nd.Wcm;
+        CU((launch_tile_solve<double, double>(sa, W.njobs_w, W.max_tiles_items, st)));
+        launch_symmetrise(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
+        launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
+        if (nsep > 0) {
+            launch_nd_schur_blocks(W.nent, h->nd.goff, h->nd.aoff, h->nd.woff, W.d_doff, W.d_entg, W.d_entbase, W.RHS,
+                                   h->nd.Wcm, W.D, st);
+            const int64_t ct = (int64_t)W.cT * (W.cT + 1) / 2;
+            launch_nd_schur_tiles(ct, L, nsep, sep0, W.Sd, h->nd.sg, h->nd.sidx, h->nd.aoff, W.d_doff, W.D, W.cwork, st);
+            CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+            launch_rl_cholesky<double>(W.cT, W.d_clo, W.d_cfwd, W.c_hi.data(), W.cwork, W.cdinv, W.d_err, st);
+            CU(cudaGetLastError());
+            TRY(read_err_flag(h, W.d_err, "interface (separator)"));
+            Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};
+            launch_finalize<double, double>(1, cpf, W.cwork, W.cdinv, W.cf, W.cb, st);
+            SolveArgs ca{};
+            ca.pf = cpf;
+            ca.fwdS = W.cf;
+            ca.bwdS = W.cb;
+            ca.alpha = 1.0;
+            ca.err = h->d_kerr;
+            ca.job_sub = W.d_cjob;
+            ca.job_in = W.d_cjin;
+            ca.job_out = W.d_cjin;
+            ca.in = W.cE;
+            ca.out = (double*)h->nd.Cinv;
+            CU((launch_tile_solve<double, double>(ca, nsep, W.cT, st)));
+            launch_symmetrise(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
+        }
+        CU(cudaGetLastError());
         cudaEventRecord(ev[5], st);
-        launch_finalize<double, double>(1, spf, W.swork, W.sdinv, W.sf, W.sb, st);
-        SolveArgs a{};
-        a.pf = spf;
-        a.fwdS = W.sf;
-        a.bwdS = W.sb;
-        a.scale = nullptr;
-        a.scale_off = nullptr;
-        a.job_sub = W.d_zs;
-        a.job_in = W.d_qo;
-        a.job_out = W.d_qo;
-        a.in = W.E;
-        a.out = W.R;
-        a.alpha = 1.0;
-        a.err = h->d_kerr;
-        CU((launch_tile_solve<double, double>(a, L, P.s_ntiles, st)));
-        launch_sinv_finalize(L, W.d_siperm, W.R, h->d_Sinv, st);
-        CU(cudaGetLastError());
     } else {
         cudaEventRecord(ev[3], st);
         cudaEventRecord(ev[5], st);
@@ -378,16 +643,16 @@ int stage_local(algmortar_t* h, const double* r, const int32_t* done) {
 
 // Interface right-hand side and interface solve: b_eta from pbar, eta = S^{-1} b_eta.
 void stage_restrict(algmortar_t* h, const int32_t* done) {
-    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, h->d_pbar, h->d_beta, done, h->st);
+    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, h->d_pbar, h->d_beta, h->d_ndpos, done, h->st);
 }
 void stage_coarse(algmortar_t* h, const int32_t* done) {
-    launch_coarse_gemv(h->L, h->d_Sinv, h->d_beta, h->d_eta, done, h->st);
+    if (h->L > 0) launch_nd_solve(h->nd, h->d_beta, h->d_eta, h->d_P, done, h->st);
 }
 
 // z = pbar + Phi eta, with the partial of r . z when part_rz is given.
 template <typename TS>
 void stage_prolong(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
-    launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->d_if_list, h->d_phi_off,
+    launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list, h->d_phi_off,
                        (const TS*)h->d_phi, h->d_eta, h->d_pbar, z, part_rz ? r : nullptr, part_rz, done, h->st);
 }
 
@@ -413,7 +678,8 @@ int pcg_iteration(algmortar_t* h) {
     cudaStream_t st = h->st;
     const int32_t* done = &h->d_pcg->done;
     launch_pcg_p(h->n, h->d_z, h->d_p, h->d_r, nullptr, h->d_pcg, h->d_part_rz, st);
-    launch_pcg_spmv(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_p, h->d_q, h->d_part_pq, h->d_pcg, h->d_part_rz, st);
+    launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_part_pq, h->d_pcg,
+                        h->d_part_rz, st);
     launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->d_part_pq, h->d_part_rr, st);
     launch_pcg_check(h->d_pcg, h->d_part_pq, h->d_part_rr, st);
     return apply_internal(h, h->d_r, h->d_z, done, h->d_part_rz);
@@ -531,6 +797,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         delete h;
         return fail(rc, err);
     }
+    if (o.nd_depth >= 0) plan_interface_nd(h->P, o.nd_depth);
     double t_plan = now_ms();
     auto bail = [&](int code) {
         delete h;
@@ -590,9 +857,18 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         rc = rc ? rc : upload(h, h->d_psrc, psrc);
     }
     if (rc) return bail(rc);
+    rc = rc ? rc : upload(h, h->d_ell_ptr, P.ell_ptr);
+    rc = rc ? rc : upload(h, h->d_ell_col, P.ell_col);
+    rc = rc ? rc : upload(h, h->d_ell_src, P.ell_src);
+    if (rc) return bail(rc);
+    h->n_ell = (int64_t)P.ell_col.size();
     h->ws = new (std::nothrow) NumWs();
     h->d_vtmp = h->alloc<double>((size_t)A->nnz);
-    if (!h->ws || !h->d_vtmp) return bail(fail(ALGMORTAR_OOM, "workspace"));
+    h->d_ell_val = h->alloc<double>((size_t)h->n_ell);
+    if (!h->ws || !h->d_vtmp || !h->d_ell_val) return bail(fail(ALGMORTAR_OOM, "workspace"));
+    if (cudaMemcpyAsync(h->d_vtmp, A->val, A->nnz * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+        return bail(fail(ALGMORTAR_CUDA, "upload values"));
+    launch_ell_values(h->n_ell, h->d_ell_src, h->d_vtmp, h->d_ell_val, h->st);
     h->pf = Profile{h->d_rows, h->d_ntiles, d_row0, d_base, d_lo, d_hi, d_fwd, d_bwd};
     const int64_t n = h->n;
     const int np = vec_grid();
@@ -671,6 +947,7 @@ void algmortar_default_opts(algmortar_opts* o) {
     o->device = 0;
     o->part_sizes = nullptr;
     o->stream = nullptr;
+    o->nd_depth = -1;
 }
 
 int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes, int32_t* part_out) {
@@ -716,8 +993,9 @@ int algmortar_apply_stages(algmortar_t* h, const double* r_dev, double* pbar_dev
     TRY(apply_internal(h, h->d_t, h->d_z, nullptr, nullptr));
     CU(cudaMemcpyAsync(pbar_dev, h->d_pbar, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     if (h->L > 0) {
-        CU(cudaMemcpyAsync(beta_dev, h->d_beta, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-        CU(cudaMemcpyAsync(eta_dev, h->d_eta, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        // ND order inside the handle -> natural interface order
+        launch_gather(h->L, h->d_ndpos, h->d_beta, beta_dev, h->st);
+        launch_gather(h->L, h->d_ndpos, h->d_eta, eta_dev, h->st);
     }
     CU(cudaMemcpyAsync(z_dev, h->d_z, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return 0;
@@ -769,6 +1047,7 @@ int algmortar_update_values(algmortar_t* h, const double* val_host) {
     const int64_t nnz = (int64_t)h->P.p_val.size();
     CU(cudaMemcpyAsync(h->d_vtmp, val_host, nnz * sizeof(double), cudaMemcpyHostToDevice, h->st));
     launch_gather(nnz, h->d_psrc, h->d_vtmp, h->d_val, h->st);
+    launch_ell_values(h->n_ell, h->d_ell_src, h->d_vtmp, h->d_ell_val, h->st);
     CU(cudaGetLastError());
     return numeric_dispatch(h);
 }
@@ -778,8 +1057,25 @@ int algmortar_update_values_device(algmortar_t* h, const double* val_dev) {
     CU(cudaSetDevice(h->device));
     const int64_t nnz = (int64_t)h->P.p_val.size();
     launch_gather(nnz, h->d_psrc, val_dev, h->d_val, h->st);
+    launch_ell_values(h->n_ell, h->d_ell_src, val_dev, h->d_ell_val, h->st);
     CU(cudaGetLastError());
     return numeric_dispatch(h);
+}
+
+int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* tb_dev, const double* tbp_dev,
+                            const double* p_dev, const double* lam_dev, double* grad_dev) {
+    if (!h || !K_dev || !tb_dev || !tbp_dev || !p_dev || !lam_dev || !grad_dev)
+        return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    CU(cudaSetDevice(h->device));
+    const int64_t n = h->n;
+    // internal ordering: gather the per-cell inputs, run the row gather, scatter back
+    double* buf[5] = {h->d_x, h->d_r, h->d_z, h->d_p, h->d_q};
+    const double* src[5] = {K_dev, tb_dev, tbp_dev, p_dev, lam_dev};
+    for (int i = 0; i < 5; ++i) launch_gather(n, h->d_perm, src[i], buf[i], h->st);
+    launch_tpfa_grad(n, h->d_rowptr, h->d_col, h->d_val, buf[0], buf[1], buf[2], buf[3], buf[4], h->d_t, h->st);
+    launch_scatter(n, h->d_perm, h->d_t, grad_dev, h->st);
+    CU(cudaGetLastError());
+    return 0;
 }
 
 int algmortar_get_partition(const algmortar_t* h, int32_t* part_out) {
@@ -820,8 +1116,8 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     for (int it = 0; it <= reps; ++it) {
         CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));
         cudaEventRecord(ev[0], st);
-        launch_pcg_spmv(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_p, h->d_q, h->d_part_pq, h->d_pcg,
-                        h->d_part_rz, st);
+        launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_part_pq,
+                            h->d_pcg, h->d_part_rz, st);
         cudaEventRecord(ev[1], st);
         launch_pcg_p(h->n, h->d_z, h->d_p, h->d_r, nullptr, h->d_pcg, h->d_part_rz, st);
         launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->d_part_pq, h->d_part_rr, st);

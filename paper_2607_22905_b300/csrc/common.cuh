@@ -29,6 +29,19 @@ __device__ __forceinline__ __nv_bfloat16 stf<__nv_bfloat16>(double x) {
     return __float2bfloat16_rn((float)x);
 }
 
+// Storage of a 32x32 tile in the sweep streams: row-major, 16-byte chunks of row r
+// XOR-swizzled by a per-row key so that 32 lanes reading their own rows with 128-bit
+// shared loads hit distinct banks within each quarter-warp.
+template <typename TS>
+__host__ __device__ __forceinline__ int swz_row_key(int r) {
+    return sizeof(TS) == 2 ? ((r >> 1) & 3) : (r & 7);
+}
+template <typename TS>
+__host__ __device__ __forceinline__ int swz_index(int r, int c) {
+    constexpr int E = 16 / sizeof(TS);          // elements per 16-byte chunk
+    return r * TILE + (((c / E) ^ swz_row_key<TS>(r)) * E) + (c % E);
+}
+
 // Tile-profile descriptor set of a batch of lower-triangular factors (one per subdomain,
 // or the single interface matrix).  Tile (I, J), lo[I] <= J <= I, of item s lives at
 // tile index base[s] + fwd[row0[s] + I] + (J - lo[row0[s] + I]) of the forward stream,

@@ -482,6 +482,34 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             P.p_rowptr[k + 1] = (int32_t)o;
         }
     }
+    // sliced ELL (32-row slices) of the permuted matrix
+    {
+        const int64_t ns = (n + 31) / 32;
+        P.ell_ptr.assign(ns + 1, 0);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            int32_t w = 0;
+            for (int64_t k = sl * 32; k < std::min<int64_t>(n, sl * 32 + 32); ++k)
+                w = std::max(w, P.p_rowptr[k + 1] - P.p_rowptr[k]);
+            P.ell_ptr[sl + 1] = P.ell_ptr[sl] + 32 * (int64_t)w;
+        }
+        P.ell_col.assign(P.ell_ptr[ns], 0);
+        P.ell_src.assign(P.ell_ptr[ns], -1);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            const int64_t w = (P.ell_ptr[sl + 1] - P.ell_ptr[sl]) / 32;
+            for (int r = 0; r < 32; ++r) {
+                const int64_t k = sl * 32 + r;
+                for (int64_t e = 0; e < w; ++e) {
+                    const int64_t o = P.ell_ptr[sl] + e * 32 + r;
+                    if (k < n && e < P.p_rowptr[k + 1] - P.p_rowptr[k]) {
+                        P.ell_col[o] = P.p_col[P.p_rowptr[k] + e];
+                        P.ell_src[o] = (int32_t)P.p_src[P.p_rowptr[k] + e];
+                    } else {
+                        P.ell_col[o] = (int32_t)std::min<int64_t>(k, n - 1);
+                    }
+                }
+            }
+        }
+    }
     // interfaces: one per subdomain pair (i < j) with a coupling, lexicographic
     std::vector<int64_t> keys;
     for (int64_t k = 0; k < n; ++k) {
@@ -580,37 +608,85 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             P.g_off[s + 1] = (int64_t)P.g_row.size();
         }
     }
-    // interface graph (I ~ J when they share a subdomain), RCM, tile profile
-    {
-        int32_t L = P.n_lambda;
-        std::vector<std::vector<int32_t>> nb(L);
-        for (int32_t s = 0; s < m; ++s)
-            for (int64_t a = P.if_off[s]; a < P.if_off[s + 1]; ++a)
-                for (int64_t b = P.if_off[s]; b < P.if_off[s + 1]; ++b)
-                    if (a != b) nb[P.if_list[a]].push_back(P.if_list[b]);
-        std::vector<int64_t> sp(L + 1, 0);
-        std::vector<int32_t> sa;
-        for (int32_t I = 0; I < L; ++I) {
-            std::sort(nb[I].begin(), nb[I].end());
-            nb[I].erase(std::unique(nb[I].begin(), nb[I].end()), nb[I].end());
-            sa.insert(sa.end(), nb[I].begin(), nb[I].end());
-            sp[I + 1] = (int64_t)sa.size();
+    plan_interface_nd(P, -1);
+    return 0;
+}
+
+// Groups = nodes at depth D of the bisection tree over part ids (the partitioner gives the
+// first k/2 of k parts to one side, so every subtree is a contiguous id range).
+void plan_interface_nd(Plan& P, int depth) {
+    const int32_t L = P.n_lambda, m = P.m;
+    if (depth < 0) {
+        depth = 0;
+        while (depth < 6 && (L >> (depth + 1)) >= 900 && (m >> (depth + 1)) >= 4) ++depth;
+    }
+    std::vector<int32_t> grp(m, 0);
+    int32_t G = 0;
+    std::vector<std::pair<int32_t, int32_t>> stack{{0, m}};
+    std::vector<std::pair<int32_t, int32_t>> leaves;
+    std::vector<int> dep{0};
+    while (!stack.empty()) {
+        auto r = stack.back();
+        int d = dep.back();
+        stack.pop_back();
+        dep.pop_back();
+        if (d == depth || r.second - r.first <= 1) {
+            leaves.push_back(r);
+            continue;
         }
-        if (L > 0) {
-            P.s_perm = rcm_order(L, sp, sa);
-            P.s_iperm.assign(L, 0);
-            for (int32_t t = 0; t < L; ++t) P.s_iperm[P.s_perm[t]] = t;
-            std::vector<int64_t> rp(L + 1, 0);
-            std::vector<int32_t> ra(sa.size());
-            for (int32_t t = 0; t < L; ++t) rp[t + 1] = rp[t] + (sp[P.s_perm[t] + 1] - sp[P.s_perm[t]]);
-            for (int32_t t = 0; t < L; ++t) {
-                int64_t o = rp[t];
-                for (int64_t e = sp[P.s_perm[t]]; e < sp[P.s_perm[t] + 1]; ++e) ra[o++] = P.s_iperm[sa[e]];
-            }
-            tile_profile(L, rp, ra, P.s_ntiles, P.s_lo, P.s_hi, P.s_fwd, P.s_bwd, P.s_tiles);
+        int32_t k1 = (r.second - r.first) / 2;
+        stack.push_back({r.first + k1, r.second});
+        dep.push_back(d + 1);
+        stack.push_back({r.first, r.first + k1});
+        dep.push_back(d + 1);
+    }
+    std::sort(leaves.begin(), leaves.end());
+    G = (int32_t)leaves.size();
+    for (int32_t g = 0; g < G; ++g)
+        for (int32_t i = leaves[g].first; i < leaves[g].second; ++i) grp[i] = g;
+    P.nd_G = G;
+    P.nd_pos.assign(L, -1);
+    P.nd_id.clear();
+    P.nd_goff.assign(G + 1, 0);
+    std::vector<std::vector<int32_t>> inner(G);
+    std::vector<int32_t> sep;
+    for (int32_t I = 0; I < L; ++I) {
+        int32_t gi = grp[P.pairs[2 * I]], gj = grp[P.pairs[2 * I + 1]];
+        if (gi == gj) inner[gi].push_back(I);
+        else sep.push_back(I);
+    }
+    for (int32_t g = 0; g < G; ++g) {
+        P.nd_goff[g + 1] = P.nd_goff[g] + (int64_t)inner[g].size();
+        for (int32_t I : inner[g]) {
+            P.nd_pos[I] = (int32_t)P.nd_id.size();
+            P.nd_id.push_back(I);
         }
     }
-    return 0;
+    P.nd_nsep = (int32_t)sep.size();
+    std::vector<std::vector<int32_t>> adj(G);
+    P.nd_sg.assign(2 * (size_t)P.nd_nsep, 0);
+    for (int32_t t = 0; t < P.nd_nsep; ++t) {
+        int32_t I = sep[t];
+        P.nd_pos[I] = (int32_t)P.nd_id.size();
+        P.nd_id.push_back(I);
+        int32_t g1 = grp[P.pairs[2 * I]], g2 = grp[P.pairs[2 * I + 1]];
+        if (g1 > g2) std::swap(g1, g2);
+        P.nd_sg[2 * t] = g1;
+        P.nd_sg[2 * t + 1] = g2;
+        adj[g1].push_back(t);
+        adj[g2].push_back(t);
+    }
+    P.nd_aoff.assign(G + 1, 0);
+    P.nd_alist.clear();
+    P.nd_sidx.assign(2 * (size_t)P.nd_nsep, 0);
+    for (int32_t g = 0; g < G; ++g) {
+        P.nd_aoff[g + 1] = P.nd_aoff[g] + (int64_t)adj[g].size();
+        for (size_t a = 0; a < adj[g].size(); ++a) {
+            int32_t t = adj[g][a];
+            P.nd_alist.push_back(t);
+            P.nd_sidx[2 * t + (P.nd_sg[2 * t] == g ? 0 : 1)] = (int32_t)a;
+        }
+    }
 }
 
 }  // namespace am

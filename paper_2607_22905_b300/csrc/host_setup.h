@@ -46,6 +46,11 @@ struct Plan {
     std::vector<double> p_val;
     std::vector<int64_t> p_src;         // p_val[t] = A.val[p_src[t]] (for value updates)
     std::vector<int32_t> row_sub;       // internal row -> subdomain
+    // sliced ELL copy of the permuted matrix for the SpMV: slices of 32 rows, width =
+    // longest row of the slice, column-major inside the slice; padding has src = -1
+    std::vector<int64_t> ell_ptr;       // nslices + 1 element offsets
+    std::vector<int32_t> ell_col;       // column (internal), padding -> the row itself
+    std::vector<int32_t> ell_src;       // index into the ORIGINAL CSR values, or -1
     // tile profile of each local factor
     std::vector<int32_t> ntiles;        // per subdomain
     std::vector<int64_t> trow_off;      // m + 1: tile-row descriptors of subdomain i start here
@@ -83,10 +88,27 @@ struct Plan {
     std::vector<int64_t> s_fwd, s_bwd;
     int64_t s_tiles = 0;
     int32_t max_part = 0, min_part = 0, max_k = 0;
+    // one-level nested dissection of the interface system: interfaces whose two
+    // subdomains lie in the same group g (a subtree of the partition's bisection tree)
+    // are interior to g; the rest form the separator.  ND position order: interiors of
+    // group 0..G-1, then the separator.
+    int32_t nd_G = 1;
+    std::vector<int32_t> nd_pos;        // interface id -> ND position
+    std::vector<int32_t> nd_id;         // ND position -> interface id
+    std::vector<int64_t> nd_goff;       // G + 1: interior of g = positions [goff[g], goff[g+1])
+    int32_t nd_nsep = 0;                // separator = positions [goff[G], goff[G] + nsep)
+    std::vector<int64_t> nd_aoff;       // G + 1 into nd_alist
+    std::vector<int32_t> nd_alist;      // separator-local indices adjacent to group g, ascending
+    std::vector<int32_t> nd_sg;         // 2 * nsep: the two groups of separator s (g1 < g2)
+    std::vector<int32_t> nd_sidx;       // 2 * nsep: index of s in A_{g1}, A_{g2}
 };
 
 int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Plan& P,
                std::string& err);
+
+// Nested-dissection layout of the interface system (fills the nd_* fields of P).
+// depth < 0 chooses it from the interface count (interior blocks of ~1000 unknowns).
+void plan_interface_nd(Plan& P, int depth);
 
 // Tile-profile descriptors for a symmetric pattern given as local adjacency lists.
 void tile_profile(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,

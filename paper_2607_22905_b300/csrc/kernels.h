@@ -48,6 +48,64 @@ struct InterfaceArgs {
     double* diagc;             // 2 * n_lambda diagonal contributions
 };
 
+struct NdAssembleArgs {
+    const int32_t* rows;
+    const int64_t* if_off;
+    const int32_t* if_list;
+    const int64_t* phi_off;
+    const double* phi;         // FP64 MBF panels
+    const int64_t* g_cptr;
+    const int32_t* g_row;
+    const double* g_val;
+    const int32_t* pairs;
+    const int32_t* nd_pos;     // interface id -> ND position
+    double* Sd;                // dense ND-ordered interface matrix (row-major)
+    double* diagc;             // 2 * n_lambda
+    int64_t L;
+};
+
+struct NdSolveArgs {
+    int G;                     // groups
+    int nsep;                  // separator unknowns
+    int64_t nin;               // interior unknowns (= goff[G])
+    int64_t np;                // sum_g a_g (= aoff[G])
+    const int64_t* goff;       // G + 1
+    const int64_t* aoff;       // G + 1
+    const int32_t* alist;      // separator-local indices adjacent to each group
+    const int32_t* sg;         // 2 * nsep groups of each separator unknown
+    const int32_t* sidx;       // 2 * nsep index inside A_g
+    const int32_t* row_g;      // interior ND row -> group
+    const int32_t* prow_g;     // row of P -> group
+    const double* Ginv;        // per group n_g x n_g symmetric inverse
+    const int64_t* gioff;      // G offsets into Ginv
+    const double* Wcm;         // per group n_g x a_g, column-major
+    const double* Wrm;         // same, row-major
+    const int64_t* woff;       // G offsets into W
+    const double* Cinv;        // nsep x nsep symmetric inverse of the separator Schur complement
+};
+
+// interface system (kernels_coarse.cu)
+void launch_nd_assemble(int m, const NdAssembleArgs& a, cudaStream_t st);
+void launch_nd_diag(int L, const double* T, const double* diagc, const int32_t* nd_pos, double* Sd, cudaStream_t st);
+void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const int64_t* src_off, const int32_t* rows,
+                           const int64_t* base, const int32_t* tile_item, const int32_t* tile_I,
+                           const int32_t* tile_J, double* work, cudaStream_t st);
+void launch_nd_rhs(int64_t ncols, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
+                   const int32_t* alist, int64_t sep0, const int64_t* woff, const int32_t* col_item,
+                   const int32_t* col_a, double* out, cudaStream_t st);
+void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
+void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
+                             double* Wrm, cudaStream_t st);
+void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* aoff, const int64_t* woff,
+                            const int64_t* doff, const int32_t* ent_g, const int64_t* ent_base, const double* RHS,
+                            const double* Wcm, double* D, cudaStream_t st);
+void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
+                           const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
+                           double* work, cudaStream_t st);
+void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, const int32_t* done,
+                     cudaStream_t st);
+cudaError_t prepare_nd_solve(int nsep);
+
 // local factor
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                        const int32_t* row_sub, int diag_scale, double* dloc, double* sc, cudaStream_t st);
@@ -86,8 +144,9 @@ int vec_grid();                               // CTAs of every partial-producing
 void set_vec_grid(int sms);
 void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
+void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st);
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
-                     double* beta, const int32_t* done, cudaStream_t st);
+                     double* beta, const int32_t* omap, const int32_t* done, cudaStream_t st);
 void launch_coarse_gemv(int L, const double* Sinv, const double* b, double* eta, const int32_t* done,
                         cudaStream_t st);
 template <typename TP>
@@ -103,11 +162,18 @@ void launch_pcg_p(int64_t n, const double* z, double* p, const double* r, double
 void launch_pcg_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
                      cudaStream_t st);
+void launch_pcg_spmv_ell(int64_t n, const int64_t* ell_ptr, const int32_t* ell_col, const double* ell_val,
+                         const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
+                         cudaStream_t st);
+void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
 void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc,
                    const double* part_pq, double* part_rr, cudaStream_t st);
 void launch_pcg_check(PcgScalars* sc, const double* part_pq, const double* part_rr, cudaStream_t st);
 void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, double* part, cudaStream_t st);
 void launch_sum_partials(const double* part, double* out, cudaStream_t st);
+void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,
+                      const double* tb, const double* tbp, const double* p, const double* lam, double* grad,
+                      cudaStream_t st);
 
 }  // namespace am

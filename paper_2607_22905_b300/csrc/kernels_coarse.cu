@@ -1,0 +1,349 @@
+// Interface (coarse) system of AlgMortar on sm_103a: assembly of
+//   S_eta = diag(T) + 1/4 G^T Phi     (Eq. interface-problem-alg with W M = B^T / 4,
+//                                       Prop. proposition-BWM; SPD by Cor. cor-schur-eta)
+// and its exact FP64 solve  eta = S_eta^{-1} b_eta  (Algorithm 2, "solve the interface
+// system") by one level of nested dissection:
+//
+//   S = [ S_11 ..      S_1G  ]      interior blocks S_gg: interfaces whose two subdomains
+//       [       S_GG   S_GG' ]      lie in group g; separator: all other interfaces.
+//       [ S_G'1 ...    S_G'G']
+//
+//   y_g  = S_gg^{-1} b_g,   P_g = W_g^T b_g  with  W_g = S_gg^{-1} S_{g,A_g}
+//   eta_sep = C^{-1} (b_sep - sum_g P_g),   C = S_sep,sep - sum_g S_{A_g,g} W_g
+//   eta_g = y_g - W_g eta_{A_g}
+//
+// (A_g: separator unknowns coupled to group g.)  Every per-iteration product runs as a
+// wide warp-per-row GEMV over all SMs (FP64 ALU-bound on B300), with no sequential
+// triangular sweep on the critical path.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace am {
+
+// ---------------------------------------------------------------------------------
+// Assembly into a dense, ND-ordered, symmetric n_lambda x n_lambda matrix Sd (row-major).
+// One CTA per subdomain; one warp per pair (a <= b) of its interfaces; off-diagonal
+// entries come from the single subdomain the two interfaces share (symmetrised there),
+// diagonal contributions of both sides are summed in a fixed order by k_nd_diag.
+// ---------------------------------------------------------------------------------
+__global__ void k_nd_assemble(NdAssembleArgs a) {
+    const int s = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t i0 = a.if_off[s];
+    const int k = (int)(a.if_off[s + 1] - i0);
+    const int64_t ns = a.rows[s];
+    const double* phi = a.phi + a.phi_off[s];
+    const int64_t* cp = a.g_cptr + i0 + s;
+    const int64_t L = a.L;
+    for (int pr = w; pr < k * k; pr += nw) {
+        const int ai = pr / k, bi = pr % k;
+        if (bi < ai) continue;
+        double cab = 0.0, cba = 0.0;
+        for (int64_t t = cp[ai] + lane; t < cp[ai + 1]; t += 32)
+            cab += a.g_val[t] * phi[bi * ns + a.g_row[t]];
+        for (int64_t t = cp[bi] + lane; t < cp[bi + 1]; t += 32)
+            cba += a.g_val[t] * phi[ai * ns + a.g_row[t]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cab += __shfl_xor_sync(0xffffffffu, cab, o);
+            cba += __shfl_xor_sync(0xffffffffu, cba, o);
+        }
+        if (lane == 0) {
+            const int I = a.if_list[i0 + ai], J = a.if_list[i0 + bi];
+            if (ai == bi) {
+                const int side = (a.pairs[2 * I] == s) ? 0 : 1;
+                a.diagc[2 * I + side] = 0.25 * cab;
+            } else {
+                const int64_t p = a.nd_pos[I], q = a.nd_pos[J];
+                const double v = 0.125 * (cab + cba);
+                a.Sd[p * L + q] = v;
+                a.Sd[q * L + p] = v;
+            }
+        }
+    }
+}
+
+__global__ void k_nd_diag(int L, const double* __restrict__ T, const double* __restrict__ diagc,
+                          const int32_t* __restrict__ nd_pos, double* __restrict__ Sd) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= L) return;
+    int64_t p = nd_pos[I];
+    Sd[p * L + p] = T[I] + diagc[2 * I] + diagc[2 * I + 1];
+}
+
+// Dense lower tile storage of an n x n block (tile (I, J), J <= I, at I(I+1)/2 + J,
+// column-major inside the tile) from a row-major source with leading dimension ld;
+// padding rows get a unit diagonal.  One CTA per tile, items laid out by `base`.
+__global__ void k_dense_to_tiles(const double* __restrict__ src, int64_t ld, const int64_t* __restrict__ src_off,
+                                 const int32_t* __restrict__ rows, const int64_t* __restrict__ base,
+                                 const int32_t* __restrict__ tile_item, const int32_t* __restrict__ tile_I,
+                                 const int32_t* __restrict__ tile_J, double* __restrict__ work) {
+    const int64_t t = blockIdx.x;
+    const int g = tile_item[t], I = tile_I[t], J = tile_J[t];
+    const int n = rows[g];
+    const double* S = src + src_off[g];
+    double* dst = work + (base[g] + (int64_t)I * (I + 1) / 2 + J) * TILE2;
+    for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+        const int r = I * TILE + (e & 31), c = J * TILE + (e >> 5);
+        double v;
+        if (r < n && c < n) v = S[(int64_t)r * ld + c];
+        else v = (r == c) ? 1.0 : 0.0;
+        dst[e] = v;
+    }
+}
+
+// Column-major n_g x a_g right-hand sides S[g rows, A_g columns] from Sd.
+__global__ void k_nd_rhs(int64_t L, const double* __restrict__ Sd, const int64_t* __restrict__ goff,
+                         const int64_t* __restrict__ aoff, const int32_t* __restrict__ alist, int64_t sep0,
+                         const int64_t* __restrict__ woff, const int32_t* __restrict__ col_item,
+                         const int32_t* __restrict__ col_a, double* __restrict__ out) {
+    const int64_t c = blockIdx.x;
+    const int g = col_item[c], aa = col_a[c];
+    const int64_t ng = goff[g + 1] - goff[g];
+    const int64_t q = sep0 + alist[aoff[g] + aa];
+    double* o = out + woff[g] + (int64_t)aa * ng;
+    for (int64_t i = threadIdx.x; i < ng; i += blockDim.x) o[i] = Sd[(goff[g] + i) * L + q];
+}
+
+// In-place symmetrisation of column-major square blocks: M = (M + M^T) / 2.
+__global__ void k_symmetrise(const int32_t* __restrict__ rows, const int64_t* __restrict__ off, int nitems,
+                             double* __restrict__ M) {
+    const int g = blockIdx.y;
+    if (g >= nitems) return;
+    const int64_t n = rows[g];
+    double* A = M + off[g];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        if (i < j) {
+            const double v = 0.5 * (A[i * n + j] + A[j * n + i]);
+            A[i * n + j] = v;
+            A[j * n + i] = v;
+        }
+    }
+}
+
+// Row-major copy of the column-major n_g x a_g blocks W_g.
+__global__ void k_transpose_blocks(const int64_t* __restrict__ goff, const int64_t* __restrict__ aoff,
+                                   const int64_t* __restrict__ woff, int G, const double* __restrict__ Wcm,
+                                   double* __restrict__ Wrm) {
+    const int g = blockIdx.y;
+    if (g >= G) return;
+    const int64_t ng = goff[g + 1] - goff[g], ag = aoff[g + 1] - aoff[g];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ng * ag;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ag, j = e % ag;
+        Wrm[woff[g] + e] = Wcm[woff[g] + j * ng + i];
+    }
+}
+
+// D_g = S_{A_g,g} W_g  (a_g x a_g, row-major), one warp per entry.
+__global__ void k_nd_schur_blocks(int64_t nent, const int64_t* __restrict__ goff, const int64_t* __restrict__ aoff,
+                                  const int64_t* __restrict__ woff, const int64_t* __restrict__ doff,
+                                  const int32_t* __restrict__ ent_g, const int64_t* __restrict__ ent_base,
+                                  const double* __restrict__ RHS, const double* __restrict__ Wcm,
+                                  double* __restrict__ D) {
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= nent) return;
+    const int g = ent_g[wid];
+    const int64_t ng = goff[g + 1] - goff[g], ag = aoff[g + 1] - aoff[g];
+    const int64_t e = wid - ent_base[g];
+    const int64_t i = e / ag, j = e % ag;
+    const double* x = RHS + woff[g] + i * ng;
+    const double* y = Wcm + woff[g] + j * ng;
+    double s = 0.0;
+    for (int64_t t = lane; t < ng; t += 32) s += x[t] * y[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) D[doff[g] + i * ag + j] = s;
+}
+
+// Lower tiles of C = S_sep,sep - sum_g D_g (symmetrised), one CTA per tile.
+__global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double* __restrict__ Sd,
+                                 const int32_t* __restrict__ sg, const int32_t* __restrict__ sidx,
+                                 const int64_t* __restrict__ aoff, const int64_t* __restrict__ doff,
+                                 const double* __restrict__ D, double* __restrict__ work) {
+    const int64_t t = blockIdx.x;
+    int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(I + 1) * (I + 2) / 2 <= t) ++I;
+    while ((int64_t)I * (I + 1) / 2 > t) --I;
+    const int J = (int)(t - (int64_t)I * (I + 1) / 2);
+    double* dst = work + t * TILE2;
+    for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+        const int s = I * TILE + (e & 31), u = J * TILE + (e >> 5);
+        double v;
+        if (s < nsep && u < nsep) {
+            double cs = Sd[(sep0 + s) * L + sep0 + u], ct = Sd[(sep0 + u) * L + sep0 + s];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    if (sg[2 * s + a] == sg[2 * u + b]) {
+                        const int g = sg[2 * s + a];
+                        const int64_t ag = aoff[g + 1] - aoff[g];
+                        cs -= D[doff[g] + sidx[2 * s + a] * ag + sidx[2 * u + b]];
+                        ct -= D[doff[g] + sidx[2 * u + b] * ag + sidx[2 * s + a]];
+                    }
+            v = 0.5 * (cs + ct);
+        } else {
+            v = (s == u) ? 1.0 : 0.0;
+        }
+        dst[e] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Per-iteration solve (ND order in and out).
+// Stage 1: eta_g = Ginv_g b_g  (rows of the symmetric inverse) and P_g = W_g^T b_g.
+// ---------------------------------------------------------------------------------
+__global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
+                            double* __restrict__ P, const int32_t* __restrict__ done) {
+    if (done && *done) return;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nin = a.goff[a.G];
+    if (wid < nin) {
+        const int g = a.row_g[wid];
+        const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
+        const double* row = a.Ginv + a.gioff[g] + i * ng;
+        const double* bg = b + g0;
+        double s = 0.0;
+        for (int64_t j = lane; j < ng; j += 32) s += row[j] * bg[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) eta[wid] = s;
+    } else if (wid < nin + a.aoff[a.G]) {
+        const int64_t r = wid - nin;
+        const int g = a.prow_g[r];
+        const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = r - a.aoff[g];
+        const double* col = a.Wcm + a.woff[g] + j * ng;
+        const double* bg = b + g0;
+        double s = 0.0;
+        for (int64_t t = lane; t < ng; t += 32) s += col[t] * bg[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) P[r] = s;
+    }
+}
+
+// Stage 2: c = b_sep - sum_g P_g (built in shared memory by every CTA), eta_sep = Cinv c.
+__global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
+                            const double* __restrict__ P, const int32_t* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ double cvec[];
+    const int nsep = a.nsep;
+    const int64_t sep0 = a.goff[a.G];
+    for (int s = threadIdx.x; s < nsep; s += blockDim.x) {
+        const int g1 = a.sg[2 * s], g2 = a.sg[2 * s + 1];
+        cvec[s] = b[sep0 + s] - P[a.aoff[g1] + a.sidx[2 * s]] - P[a.aoff[g2] + a.sidx[2 * s + 1]];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= nsep) return;
+    const double* row = a.Cinv + wid * nsep;
+    double s = 0.0;
+    for (int t = lane; t < nsep; t += 32) s += row[t] * cvec[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) eta[sep0 + wid] = s;
+}
+
+// Stage 3: eta_g -= W_g eta_{A_g}.
+__global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, const int32_t* __restrict__ done) {
+    if (done && *done) return;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nin = a.goff[a.G];
+    if (wid >= nin) return;
+    const int g = a.row_g[wid];
+    const int64_t g0 = a.goff[g], ag = a.aoff[g + 1] - a.aoff[g], i = wid - g0;
+    const double* row = a.Wrm + a.woff[g] + i * ag;
+    const int32_t* al = a.alist + a.aoff[g];
+    double s = 0.0;
+    for (int64_t j = lane; j < ag; j += 32) s += row[j] * eta[nin + al[j]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) eta[wid] -= s;
+}
+
+// ------------------------------------------------------------------------ launchers
+void launch_nd_assemble(int m, const NdAssembleArgs& a, cudaStream_t st) {
+    if (m > 0) {
+        count_launch();
+        k_nd_assemble<<<m, 256, 0, st>>>(a);
+    }
+}
+void launch_nd_diag(int L, const double* T, const double* diagc, const int32_t* nd_pos, double* Sd, cudaStream_t st) {
+    if (L > 0) {
+        count_launch();
+        k_nd_diag<<<(L + 127) / 128, 128, 0, st>>>(L, T, diagc, nd_pos, Sd);
+    }
+}
+void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const int64_t* src_off, const int32_t* rows,
+                           const int64_t* base, const int32_t* tile_item, const int32_t* tile_I,
+                           const int32_t* tile_J, double* work, cudaStream_t st) {
+    if (ntiles > 0) {
+        count_launch();
+        k_dense_to_tiles<<<(unsigned)ntiles, 256, 0, st>>>(src, ld, src_off, rows, base, tile_item, tile_I, tile_J,
+                                                           work);
+    }
+}
+void launch_nd_rhs(int64_t ncols, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
+                   const int32_t* alist, int64_t sep0, const int64_t* woff, const int32_t* col_item,
+                   const int32_t* col_a, double* out, cudaStream_t st) {
+    if (ncols > 0) {
+        count_launch();
+        k_nd_rhs<<<(unsigned)ncols, 256, 0, st>>>(L, Sd, goff, aoff, alist, sep0, woff, col_item, col_a, out);
+    }
+}
+void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st) {
+    if (nitems > 0) {
+        count_launch();
+        k_symmetrise<<<dim3(256, nitems), 256, 0, st>>>(rows, off, nitems, M);
+    }
+}
+void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
+                             double* Wrm, cudaStream_t st) {
+    if (G > 0) {
+        count_launch();
+        k_transpose_blocks<<<dim3(256, G), 256, 0, st>>>(goff, aoff, woff, G, Wcm, Wrm);
+    }
+}
+void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* aoff, const int64_t* woff,
+                            const int64_t* doff, const int32_t* ent_g, const int64_t* ent_base, const double* RHS,
+                            const double* Wcm, double* D, cudaStream_t st) {
+    if (nent > 0) {
+        count_launch();
+        k_nd_schur_blocks<<<(unsigned)((nent + 7) / 8), 256, 0, st>>>(nent, goff, aoff, woff, doff, ent_g, ent_base,
+                                                                       RHS, Wcm, D);
+    }
+}
+void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
+                           const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
+                           double* work, cudaStream_t st) {
+    if (ntiles > 0) {
+        count_launch();
+        k_nd_schur_tiles<<<(unsigned)ntiles, 256, 0, st>>>(L, nsep, sep0, Sd, sg, sidx, aoff, doff, D, work);
+    }
+}
+void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, const int32_t* done,
+                     cudaStream_t st) {
+    const int64_t nin = a.nin, np = a.np;
+    if (nin + np > 0) {
+        count_launch();
+        k_nd_stage1<<<(unsigned)((nin + np + 7) / 8), 256, 0, st>>>(a, b, eta, P, done);
+    }
+    if (a.nsep > 0) {
+        count_launch();
+        k_nd_stage2<<<(unsigned)((a.nsep + 7) / 8), 256, (size_t)a.nsep * sizeof(double), st>>>(a, b, eta, P, done);
+        count_launch();
+        k_nd_stage3<<<(unsigned)((nin + 7) / 8), 256, 0, st>>>(a, eta, done);
+    }
+}
+cudaError_t prepare_nd_solve(int nsep) {
+    size_t smem = (size_t)nsep * sizeof(double);
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(k_nd_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+}  // namespace am

@@ -286,7 +286,9 @@ __global__ void __launch_bounds__(256) k_rl_update(const int32_t* __restrict__ l
 
 // ---------------------------------------------------------------------------------
 // Sweep streams from the factor: forward rows [L_I,lo .. L_I,I-1 | L_II^{-1}], backward
-// rows [(L_I+1,I)^T .. (L_hi,I)^T | L_II^{-T}], all tiles column-major, in precision TS.
+// rows [(L_I+1,I)^T .. (L_hi,I)^T | L_II^{-T}], in precision TS.  Every 32x32 tile M is
+// stored row-major with its 16-byte chunks XOR-swizzled (swz_index), so that the solve
+// reads row `lane` of a tile with conflict-free 128-bit shared loads.
 // ---------------------------------------------------------------------------------
 template <typename TW, typename TS>
 __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restrict__ work,
@@ -305,23 +307,23 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
     for (int I = 0; I < T; ++I) {
         const int nt = I - lo[I];
         const int64_t fo = (base + fwd[I]) * TILE2;
-        for (int64_t e = threadIdx.x; e < (int64_t)nt * TILE2; e += blockDim.x)
-            fwdS[fo + e] = stf<TS>((double)Wb[fwd[I] * TILE2 + e]);
-        for (int e = threadIdx.x; e < TILE2; e += blockDim.x)
-            fwdS[fo + (int64_t)nt * TILE2 + e] = stf<TS>((double)Db[(int64_t)I * TILE2 + e]);
-        const int nb = hi[I] - I;
-        const int64_t bo = (base + bwd[I]) * TILE2;
-        for (int t = 0; t < nb; ++t) {
-            const int J = I + 1 + t;
-            const TW* src = Wb + (fwd[J] + (I - lo[J])) * TILE2;
+        // forward: M = L_IJ (column-major source: M[r][c] at c*32 + r), then L_II^{-1}
+        for (int t = 0; t <= nt; ++t) {
+            const TW* src = t < nt ? Wb + (fwd[I] + t) * TILE2 : Db + (int64_t)I * TILE2;
             for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
-                int r = e & 31, cc = e >> 5;
-                bwdS[bo + (int64_t)t * TILE2 + e] = stf<TS>((double)src[r * TILE + cc]);
+                const int r = e >> 5, c = e & 31;
+                fwdS[fo + (int64_t)t * TILE2 + swz_index<TS>(r, c)] = stf<TS>((double)src[c * TILE + r]);
             }
         }
-        for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
-            int r = e & 31, cc = e >> 5;
-            bwdS[bo + (int64_t)nb * TILE2 + e] = stf<TS>((double)Db[(int64_t)I * TILE2 + r * TILE + cc]);
+        // backward: M = (L_JI)^T (M[r][c] = L_JI[c][r] at r*32 + c), then L_II^{-T}
+        const int nb = hi[I] - I;
+        const int64_t bo = (base + bwd[I]) * TILE2;
+        for (int t = 0; t <= nb; ++t) {
+            const TW* src = t < nb ? Wb + (fwd[I + 1 + t] + (I - lo[I + 1 + t])) * TILE2 : Db + (int64_t)I * TILE2;
+            for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
+                const int r = e >> 5, c = e & 31;
+                bwdS[bo + (int64_t)t * TILE2 + swz_index<TS>(r, c)] = stf<TS>((double)src[r * TILE + c]);
+            }
         }
     }
 }
@@ -366,118 +368,210 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // Batched triangular solves  out = alpha * S L^{-T} L^{-1} S in  for a list of jobs
 // (item, input offset, output offset); S = diag(sc) is the symmetric scaling (or 1).
 //
-// One warp per job walks the tile rows in order (forward stream, then backward stream).
-// The item's factor tiles are consumed strictly in storage order, so they are streamed
-// through an R-slot shared-memory ring by bulk async copies (one 32x32 tile per copy,
-// completion on a per-slot mbarrier): while the warp works on tile q, tiles q+1..q+R-1
-// are in flight.  Step for tile row I:  acc = sum_J T_IJ v_J over the off-diagonal tiles
-// (lane = tile row, column-major tiles -> conflict-free shared loads), then
-// v_I = D_I (v_I - acc) with the stored inverse diagonal tile.  No block-wide barrier.
+// One CTA of NW warps per job walks the tile rows in order (forward stream, then
+// backward stream).  The item's tiles are consumed strictly in storage order, so they are
+// streamed through an R-slot shared-memory ring by bulk async copies (one 32x32 tile per
+// copy, completion on a per-slot mbarrier); a slot is refilled as soon as its tile has
+// been read, so R tiles are always in flight.  Step for tile row I:
+//   each warp takes every NW-th off-diagonal tile and forms its partial sum_J T_IJ v_J
+//   (lane = tile row, 128-bit shared loads of the swizzled row and of v_J);
+//   one named barrier; every warp then reduces the partials and applies the stored
+//   inverse diagonal tile itself (identical results, so no second barrier is needed);
+//   the diagonal slot is refilled after the next step's barrier, when all warps are done.
 // ---------------------------------------------------------------------------------
-template <typename TS, typename TA, int R>
-__global__ void __launch_bounds__(32) k_chain_solve(SolveArgs a) {
+template <typename TS, typename TA>
+__device__ __forceinline__ TA row_dot(const TS* tile, int lane, const TA* v);
+
+// FP64 tiles: 16 chunks of 2 doubles per row
+template <>
+__device__ __forceinline__ double row_dot<double, double>(const double* tile, int lane, const double* v) {
+    const double2* row = reinterpret_cast<const double2*>(tile + lane * TILE);
+    const double2* vv = reinterpret_cast<const double2*>(v);
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int sw = lane & 7;
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+        const double2 t0 = row[j ^ sw], t1 = row[(j + 1) ^ sw];
+        const double2 x0 = vv[j], x1 = vv[j + 1];
+        a0 = fma(t0.x, x0.x, a0);
+        a1 = fma(t0.y, x0.y, a1);
+        a2 = fma(t1.x, x1.x, a2);
+        a3 = fma(t1.y, x1.y, a3);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
+// FP32 tiles: 8 chunks of 4 floats per row
+template <>
+__device__ __forceinline__ float row_dot<float, float>(const float* tile, int lane, const float* v) {
+    const float4* row = reinterpret_cast<const float4*>(tile + lane * TILE);
+    const float4* vv = reinterpret_cast<const float4*>(v);
+    float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int sw = lane & 7;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 t = row[j ^ sw];
+        const float4 x = vv[j];
+        a0 = fmaf(t.x, x.x, a0);
+        a1 = fmaf(t.y, x.y, a1);
+        a2 = fmaf(t.z, x.z, a2);
+        a3 = fmaf(t.w, x.w, a3);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
+// BF16 tiles: 4 chunks of 8 bf16 per row, FP32 accumulation
+template <>
+__device__ __forceinline__ float row_dot<__nv_bfloat16, float>(const __nv_bfloat16* tile, int lane, const float* v) {
+    const uint4* row = reinterpret_cast<const uint4*>(tile + lane * TILE);
+    const float4* vv = reinterpret_cast<const float4*>(v);
+    float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const int sw = (lane >> 1) & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint4 t = row[j ^ sw];
+        const float4 x0 = vv[2 * j], x1 = vv[2 * j + 1];
+        const float2 p0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.x));
+        const float2 p1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.y));
+        const float2 p2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.z));
+        const float2 p3 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.w));
+        a0 = fmaf(p0.x, x0.x, a0);
+        a1 = fmaf(p0.y, x0.y, a1);
+        a2 = fmaf(p1.x, x0.z, a2);
+        a3 = fmaf(p1.y, x0.w, a3);
+        a0 = fmaf(p2.x, x1.x, a0);
+        a1 = fmaf(p2.y, x1.y, a1);
+        a2 = fmaf(p3.x, x1.z, a2);
+        a3 = fmaf(p3.y, x1.w, a3);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <typename TS, typename TA, int R, int NW>
+__global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
     if (a.done && *a.done) return;
     const int job = blockIdx.x;
     const int s = a.job_sub[job];
     const Profile pf = a.pf;
     const int n = pf.rows[s], T = pf.ntiles[s];
     const int64_t r0 = pf.row0[s];
-    const int32_t* lo = pf.lo + r0;
-    const int32_t* hi = pf.hi + r0;
-    const int64_t* fwd = pf.fwd + r0;
-    const int64_t* bwd = pf.bwd + r0;
-    const int64_t nts = fwd[T - 1] + (T - 1 - lo[T - 1]) + 1;      // tiles per stream
+    const int64_t nts = pf.fwd[r0 + T - 1] + (T - 1 - pf.lo[r0 + T - 1]) + 1;   // tiles per stream
     const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
     const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
     const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
     const double* in = a.in + a.job_in[job];
     double* out = a.out + a.job_out[job];
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     constexpr uint32_t TB = TILE2 * sizeof(TS);
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TS* ring = reinterpret_cast<TS*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
-    TA* v = reinterpret_cast<TA*>(smem_raw + R * TB + R * sizeof(uint64_t));
-
+    TA* part = reinterpret_cast<TA*>(smem_raw + R * TB + R * sizeof(uint64_t));   // [2][NW][32]
+    int32_t* lo_s = reinterpret_cast<int32_t*>(part + 2 * NW * TILE);
+    int32_t* hi_s = lo_s + T;
+    TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));                        // 16-byte aligned
     const int64_t total = 2 * nts;
     auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
-    if (lane == 0) {
+    if (tid == 0) {
         for (int i = 0; i < R; ++i) mbar_init(smem_u32(&bars[i]), 1);
         fence_async_smem();
         for (int64_t q = 0; q < R && q < total; ++q)
             tma_load_1d(smem_u32(ring + q * TILE2), src(q), TB, smem_u32(&bars[q]));
     }
-    for (int i = lane; i < T * TILE; i += 32) v[i] = i < n ? (TA)(in[i] * (sc ? sc[i] : 1.0)) : (TA)0;
-    __syncwarp();
+    for (int i = tid; i < T; i += NW * 32) {
+        lo_s[i] = pf.lo[r0 + i];
+        hi_s[i] = pf.hi[r0 + i];
+    }
+    for (int i = tid; i < T * TILE; i += NW * 32) v[i] = i < n ? (TA)(in[i] * (sc ? sc[i] : 1.0)) : (TA)0;
+    __syncthreads();
 
-    int64_t q = 0;
     bool ok = true;
-    // wait for tile q, returns its slot
-    auto acquire = [&](int64_t qq) -> const TS* {
+    auto wait_tile = [&](int64_t qq) -> const TS* {
         const int slot = (int)(qq % R);
-        const uint32_t par = (uint32_t)((qq / R) & 1);
-        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[slot]), par));
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[slot]), (uint32_t)((qq / R) & 1)));
         return ring + slot * TILE2;
     };
-    // slot of tile qq is free again: refill it with tile qq + R
-    auto release = [&](int64_t qq) {
-        __syncwarp();
-        if (lane == 0 && ok && qq + R < total) {
+    auto refill = [&](int64_t qq) {   // tile qq has been read by every consumer: load qq + R
+        if (ok && qq + R < total) {
             const int slot = (int)(qq % R);
             fence_async_smem();
             tma_load_1d(smem_u32(ring + slot * TILE2), src(qq + R), TB, smem_u32(&bars[slot]));
         }
     };
-    for (int pass = 0; pass < 2 && ok; ++pass) {
-        for (int step = 0; step < T && ok; ++step) {
+    int64_t q = 0;
+    int64_t pending_diag = -1;      // diagonal tile whose slot is released at the next barrier
+    int par = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int step = 0; step < T; ++step) {
             const int I = pass == 0 ? step : T - 1 - step;
-            const int j0 = pass == 0 ? lo[I] : I + 1;
-            const int nt = pass == 0 ? I - lo[I] : hi[I] - I;
-            TA acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-            for (int t = 0; t < nt; ++t) {
-                const TS* tl = acquire(q);
-                const TA* vj = v + (j0 + t) * TILE;
-#pragma unroll
-                for (int c = 0; c < TILE; c += 4) {
-                    acc0 += ldf<TA>(tl + (c + 0) * TILE + lane) * vj[c + 0];
-                    acc1 += ldf<TA>(tl + (c + 1) * TILE + lane) * vj[c + 1];
-                    acc2 += ldf<TA>(tl + (c + 2) * TILE + lane) * vj[c + 2];
-                    acc3 += ldf<TA>(tl + (c + 3) * TILE + lane) * vj[c + 3];
-                }
-                release(q);
-                ++q;
-            }
-            const TS* D = acquire(q);
+            const int j0 = pass == 0 ? lo_s[I] : I + 1;
+            const int nt = pass == 0 ? I - lo_s[I] : hi_s[I] - I;
+            // off-diagonal tiles of the next step (the first backward step has none)
+            const int nt_next = pass == 0 ? (step + 1 < T ? (I + 1) - lo_s[I + 1] : 0)
+                                          : (step + 1 < T ? hi_s[I - 1] - (I - 1) : 0);
             TA* vi = v + I * TILE;
-            vi[lane] = vi[lane] - ((acc0 + acc1) + (acc2 + acc3));
-            __syncwarp();
-            TA y0 = 0, y1 = 0, y2 = 0, y3 = 0;
-#pragma unroll
-            for (int c = 0; c < TILE; c += 4) {
-                y0 += ldf<TA>(D + (c + 0) * TILE + lane) * vi[c + 0];
-                y1 += ldf<TA>(D + (c + 1) * TILE + lane) * vi[c + 1];
-                y2 += ldf<TA>(D + (c + 2) * TILE + lane) * vi[c + 2];
-                y3 += ldf<TA>(D + (c + 3) * TILE + lane) * vi[c + 3];
+            const TA rhs = vi[lane];    // read before the barrier: vi is overwritten after it
+            TA acc = 0;
+            for (int t = w; t < nt; t += NW) {
+                const TS* tl = wait_tile(q + t);
+                acc += row_dot<TS, TA>(tl, lane, v + (j0 + t) * TILE);
+                __syncwarp();
+                if (lane == 0) refill(q + t);
             }
-            __syncwarp();
-            vi[lane] = (y0 + y1) + (y2 + y3);
-            release(q);
-            ++q;
+            part[(par * NW + w) * TILE + lane] = acc;
+            if (NW > 1) named_barrier(1, NW * 32);
+            else __syncwarp();
+            if (tid == 0 && pending_diag >= 0) refill(pending_diag);
+            const TS* D = wait_tile(q + nt);
+            TA sum = 0;
+#pragma unroll
+            for (int u = 0; u < NW; ++u) sum += part[(par * NW + u) * TILE + lane];
+            const TA t = rhs - sum;
+            // y = D t with t distributed one value per lane (shuffle broadcast)
+            TA y0 = 0, y1 = 0;
+            const int sw = swz_row_key<TS>(lane);
+            constexpr int E = 16 / sizeof(TS);
+            const TS* rowp = D + lane * TILE;
+#pragma unroll
+            for (int c = 0; c < TILE; c += 2) {
+                const TA d0 = ldf<TA>(rowp + (((c) / E) ^ sw) * E + (c) % E);
+                const TA d1 = ldf<TA>(rowp + (((c + 1) / E) ^ sw) * E + (c + 1) % E);
+                y0 += d0 * __shfl_sync(0xffffffffu, t, c);
+                y1 += d1 * __shfl_sync(0xffffffffu, t, c + 1);
+            }
+            vi[lane] = y0 + y1;         // every warp writes the same values
+            // The diagonal slot may only be refilled once every warp has read it.  If the
+            // next row needs R or more tiles before its barrier, the refill cannot wait
+            // for that barrier (a warp could then wait on the refilled tile): release now.
+            if (nt_next >= R) {
+                if (NW > 1) named_barrier(1, NW * 32);
+                else __syncwarp();
+                if (tid == 0) refill(q + nt);
+                pending_diag = -1;
+            } else {
+                __syncwarp();
+                pending_diag = q + nt;
+            }
+            q += nt + 1;
+            par ^= 1;
         }
     }
     if (!ok) {
-        // a copy never completed: record it, drain what is still in flight, give up
-        if (lane == 0) {
+        if (tid == 0) {
             atomicExch(a.err, 1);
             for (int64_t qq = q; qq < total && qq < q + R; ++qq)
                 mbar_wait(smem_u32(&bars[qq % R]), (uint32_t)((qq / R) & 1));
         }
-        __syncwarp();
+        __syncthreads();
         return;
     }
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) out[i] = a.alpha * (double)v[i] * (sc ? sc[i] : 1.0);
+    __syncthreads();
+    for (int i = tid; i < n; i += NW * 32) out[i] = a.alpha * (double)v[i] * (sc ? sc[i] : 1.0);
 }
 
 // ---------------------------------------------------------------------------------
@@ -647,13 +741,15 @@ constexpr int ring_slots() {
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
     constexpr int R = ring_slots<TS>();
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + (size_t)max_tiles * TILE * sizeof(TA);
-    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    constexpr int NW = 4;
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + 2 * NW * TILE * sizeof(TA) +
+                  (size_t)(2 * max_tiles + 4) * sizeof(int32_t) + (size_t)max_tiles * TILE * sizeof(TA) + 16;
+    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
         count_launch();
-        k_chain_solve<TS, TA, R><<<njobs, 32, smem, st>>>(a);
+        k_chain_solve<TS, TA, R, NW><<<njobs, NW * 32, smem, st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -31,6 +31,11 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const doub
     GRID_STRIDE(k, n) dst[k] = src[perm[k]];
 }
 
+__global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, const double* __restrict__ v,
+                                 double* __restrict__ dst) {
+    GRID_STRIDE(k, n) dst[idx[k]] = v[k];
+}
+
 __global__ void k_scatter(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
                           double* __restrict__ dst) {
     GRID_STRIDE(k, n) dst[perm[k]] = src[k];
@@ -40,7 +45,8 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ perm, const dou
 // the interface right-hand side of Eq. (interface-problem-alg), one warp per interface.
 __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_t* __restrict__ rcell,
                            const double* __restrict__ rcoef, const double* __restrict__ pbar,
-                           double* __restrict__ beta, const int32_t* __restrict__ done) {
+                           double* __restrict__ beta, const int32_t* __restrict__ omap,
+                           const int32_t* __restrict__ done) {
     if (done && *done) return;
     int I = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
@@ -49,7 +55,7 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     for (int64_t t = rptr[I] + lane; t < rptr[I + 1]; t += 32) s += rcoef[t] * pbar[rcell[t]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) beta[I] = s;
+    if (lane == 0) beta[omap ? omap[I] : I] = s;
 }
 
 // eta = S_eta^{-1} b_eta, one warp per row of the explicit inverse (FP64).
@@ -180,6 +186,48 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv(int64_t n, const int32_t* _
     if (threadIdx.x == 0) part_pq[blockIdx.x] = s;
 }
 
+// Same product on the sliced-ELL copy: one thread per row, the warp = one 32-row slice,
+// every load of values/columns is one contiguous 256/128-byte segment.
+__global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
+                                                          const int32_t* __restrict__ ell_col,
+                                                          const double* __restrict__ ell_val,
+                                                          const double* __restrict__ p, double* __restrict__ q,
+                                                          double* __restrict__ part_pq, PcgScalars* __restrict__ sc,
+                                                          const double* __restrict__ part_rz, int np) {
+    if (sc->done) return;
+    __shared__ double sh[32];
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        double rz = warp_sum_partials(part_rz, np);
+        if (threadIdx.x == 0) {
+            sc->rz_prev = sc->rz;
+            sc->rz = rz;
+        }
+    }
+    double acc = 0.0;
+    GRID_STRIDE(k, n) {
+        const int64_t sl = k >> 5;
+        const int r = (int)(k & 31);
+        const int64_t b = ell_ptr[sl], w = (ell_ptr[sl + 1] - b) >> 5;
+        const double* v = ell_val + b + r;
+        const int32_t* c = ell_col + b + r;
+        double s = 0.0;
+        for (int64_t e = 0; e < w; ++e) s += __ldg(v + e * 32) * __ldg(p + __ldg(c + e * 32));
+        q[k] = s;
+        acc += p[k] * s;
+    }
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part_pq[blockIdx.x] = s;
+}
+
+// ell_val[t] = val[src[t]] (0 for padding)
+__global__ void k_ell_values(int64_t nell, const int32_t* __restrict__ src, const double* __restrict__ val,
+                             double* __restrict__ ell_val) {
+    GRID_STRIDE(t, nell) {
+        const int32_t s = src[t];
+        ell_val[t] = s >= 0 ? val[s] : 0.0;
+    }
+}
+
 // alpha = rho_k / (p . q);  x += alpha p;  r -= alpha q;  partial of ||r||^2.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
@@ -262,6 +310,34 @@ __global__ void k_sum_partials(const double* __restrict__ part, int np, double* 
     if (threadIdx.x == 0) *out = s;
 }
 
+// ------------------------------------------------------------------------- adjoint
+// dL/d lnK for a TPFA matrix (harmonic-mean transmissibilities T_kl = -a_kl between
+// cells k, l; Dirichlet half-faces folded into per-cell sums tb_k = sum_b T_b,
+// tbp_k = sum_b T_b p_bc), given the state p (A p = f) and the adjoint lambda
+// (A lambda = dL/dp):
+//   dL/dT_kl = -(lambda_k - lambda_l)(p_k - p_l),   dT_kl/dlnK_k = T_kl K_l / (K_k + K_l)
+//   dL/dT_b  =  lambda_k (p_bc - p_k),              dT_b/dlnK_k  = T_b
+// One thread per cell gathers over its row: deterministic, no atomics.  All vectors in
+// the CSR's own ordering.
+__global__ void k_tpfa_grad(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const double* __restrict__ K,
+                            const double* __restrict__ tb, const double* __restrict__ tbp,
+                            const double* __restrict__ p, const double* __restrict__ lam,
+                            double* __restrict__ grad) {
+    GRID_STRIDE(k, n) {
+        const double pk = p[k], lk = lam[k], Kk = K[k];
+        double g = lk * (tbp[k] - pk * tb[k]);
+        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) {
+            const int32_t l = col[e];
+            if (l == k) continue;
+            const double T = -val[e];
+            const double dLdT = -(lk - lam[l]) * (pk - p[l]);
+            g += dLdT * T * K[l] / (Kk + K[l]);
+        }
+        grad[k] = g;
+    }
+}
+
 // ------------------------------------------------------------------------ launchers
 static inline int grid_for(int64_t n, int bs) {
     int64_t g = (n + bs - 1) / bs;
@@ -272,15 +348,21 @@ void launch_gather(int64_t n, const int32_t* perm, const double* src, double* ds
     count_launch();
     k_gather<<<grid_for(n, 256), 256, 0, st>>>(n, perm, src, dst);
 }
+void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st) {
+    if (n > 0) {
+        count_launch();
+        k_scatter_values<<<grid_for(n, 256), 256, 0, st>>>(n, idx, v, dst);
+    }
+}
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st) {
     count_launch();
     k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, perm, src, dst);
 }
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
-                     double* beta, const int32_t* done, cudaStream_t st) {
+                     double* beta, const int32_t* omap, const int32_t* done, cudaStream_t st) {
     if (L > 0) {
         count_launch();
-        k_restrict<<<(L + 7) / 8, 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, done);
+        k_restrict<<<(L + 7) / 8, 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, done);
     }
 }
 void launch_coarse_gemv(int L, const double* Sinv, const double* b, double* eta, const int32_t* done,
@@ -321,6 +403,17 @@ void launch_pcg_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const
     count_launch();
     k_pcg_spmv<<<vec_grid(), VEC_BS, 0, st>>>(n, rowptr, col, val, p, q, part_pq, sc, part_rz, vec_grid());
 }
+void launch_pcg_spmv_ell(int64_t n, const int64_t* ell_ptr, const int32_t* ell_col, const double* ell_val,
+                         const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
+                         cudaStream_t st) {
+    count_launch();
+    k_pcg_spmv_ell<<<vec_grid(), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, part_pq, sc, part_rz,
+                                                  vec_grid());
+}
+void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st) {
+    count_launch();
+    k_ell_values<<<grid_for(nell, 256), 256, 0, st>>>(nell, src, val, ell_val);
+}
 void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc,
                    const double* part_pq, double* part_rr, cudaStream_t st) {
     count_launch();
@@ -334,6 +427,12 @@ void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const
                      const double* x, const double* b, double* part, cudaStream_t st) {
     count_launch();
     k_residual<<<vec_grid(), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, part);
+}
+void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,
+                      const double* tb, const double* tbp, const double* p, const double* lam, double* grad,
+                      cudaStream_t st) {
+    count_launch();
+    k_tpfa_grad<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, K, tb, tbp, p, lam, grad);
 }
 void launch_sum_partials(const double* part, double* out, cudaStream_t st) {
     count_launch();

@@ -27,7 +27,8 @@ class AlgMortar:
     """
 
     def __init__(self, A, n_parts, precision="fp64", part_sizes=None, parts=None, use_graph=False,
-                 check_every=1, max_it=10000, diag_scale=True, device=0, verbose=False, stream=None):
+                 check_every=1, max_it=10000, diag_scale=True, device=0, verbose=False, stream=None,
+                 nd_depth=-1):
         if not torch.cuda.is_available():
             raise RuntimeError("AlgMortar needs a CUDA device")
         L = B.lib()
@@ -41,6 +42,7 @@ class AlgMortar:
         o.check_every = int(check_every)
         o.verbose = 1 if verbose else 0
         o.device = int(device)
+        o.nd_depth = int(nd_depth)
         self._sizes = None
         if part_sizes is not None:
             self._sizes = np.ascontiguousarray(part_sizes, dtype=np.int32)
@@ -60,6 +62,7 @@ class AlgMortar:
                 B.check(L.algmortar_setup(C.byref(csr), int(n_parts), C.byref(o), C.byref(h)),
                         "algmortar_setup")
         self._h = h
+        self.values_token = object()
         info = B.Info()
         B.check(L.algmortar_get_info(h, C.byref(info)))
         self.info = info.as_dict()
@@ -142,9 +145,18 @@ class AlgMortar:
         else:
             v = np.ascontiguousarray(values, dtype=np.float64)
             B.check(B.lib().algmortar_update_values(self._h, v.ctypes.data_as(B._DP)), "algmortar_update_values")
+        self.values_token = object()
         info = B.Info()
         B.check(B.lib().algmortar_get_info(self._h, C.byref(info)))
         self.info = info.as_dict()
+
+    def tpfa_grad_lnK(self, K, tb, tbp, p, lam):
+        """dL/d ln K for TPFA values (see algmortar_tpfa_grad_lnK); device tensors."""
+        K, tb, tbp, p, lam = (self._vec(v) for v in (K, tb, tbp, p, lam))
+        out = torch.empty_like(p)
+        B.check(B.lib().algmortar_tpfa_grad_lnK(self._h, _ptr(K), _ptr(tb), _ptr(tbp), _ptr(p), _ptr(lam),
+                                                _ptr(out)), "algmortar_tpfa_grad_lnK")
+        return out
 
     STAGES = ("spmv", "cg_vectors", "local_solve", "restrict", "coarse", "prolong", "iteration")
 

@@ -341,6 +341,22 @@ def config4(seed: int = 4, shape=(100, 100, 50), n_parts: int = 500, nrhs: int =
                    {"rhs": rhs, "faults": faults.tolist(), "throws": throws.tolist()})
 
 
+def tpfa_cell_bc(n, faces):
+    """Per-cell sums of the Dirichlet half-faces: tb_k = sum_b T_b, tbp_k = sum_b T_b p_bc."""
+    tb = np.zeros(n)
+    tbp = np.zeros(n)
+    np.add.at(tb, faces["bc_cell"], faces["bc_T"])
+    np.add.at(tbp, faces["bc_cell"], faces["bc_T"] * faces["bc_p"])
+    return tb, tbp
+
+
+def observations(n, n_obs, seed, p_ref, noise=0.01):
+    """Seeded observation cells (without replacement) and noisy observed pressures."""
+    rng = np.random.default_rng(seed)
+    obs = np.sort(rng.choice(n, n_obs, replace=False))
+    return obs, p_ref[obs] + noise * rng.standard_normal(n_obs)
+
+
 def tpfa_from_lnK(lnK: np.ndarray, kz_ratio=1.0, bc_axis=0, p_lo=1.0, p_hi=0.0):
     """TPFA system for log-permeability lnK plus the face data the gradient needs.
 

@@ -22,7 +22,7 @@ def built():
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "algmortar.h")).read()
-    decl = r"^\s*(?:int|void|const char\s*\*)\s*(algmortar_[a-z_]+)\s*\("
+    decl = r"^\s*(?:int|void|const char\s*\*)\s*(algmortar_[A-Za-z0-9_]+)\s*\("
     return sorted(set(re.findall(decl, src, flags=re.M)))
 
 

@@ -169,6 +169,42 @@ def test_pcg_low_precision_factors(case, precision):
     assert rel(am.apply(r).cpu().numpy(), oa.apply(pc, r)) <= tol
 
 
+@pytest.mark.parametrize("depth", [0, 1, 2])
+def test_interface_nested_dissection(depth):
+    """The interface solve by nested dissection (2^depth groups + separator) gives the
+    same eta and z as the oracle's dense Cholesky of S_eta."""
+    A, f, sizes = small3d(shape=(23, 19, 15), m=16, seed=41)
+    part = op.partition(A, sizes)
+    pc = oa.setup(A, part)
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, nd_depth=depth)
+    r = np.random.default_rng(106).standard_normal(A.shape[0])
+    pbar, beta, eta, z = (t.cpu().numpy() for t in am.apply_stages(r))
+    _, rhs_o, eta_o, _ = oa.apply_parts(pc, r)
+    assert rel(beta, rhs_o) <= 1e-10
+    assert rel(eta, eta_o) <= 1e-10
+    assert rel(am.apply(r).cpu().numpy(), oa.apply(pc, r)) <= 1e-10
+    x, st = am.solve(f, tol=1e-8)
+    ref = oa.pcg(A, f, lambda v: oa.apply(pc, v), 1e-8)
+    assert st["status"] == 0 and abs(st["iterations"] - ref.iterations) <= 1
+
+
+def test_update_values_matches_fresh_setup():
+    """New values on the same pattern (a second permeability sample) through
+    algmortar_update_values equal a fresh setup, for the host and device paths."""
+    A, f, sizes = small3d(seed=31)
+    A2, f2, _ = small3d(seed=32)
+    assert (A.indices == A2.indices).all() and (A.indptr == A2.indptr).all()
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, use_graph=True)
+    x1, _ = am.solve(f)
+    fresh = AlgMortar(A2, len(sizes), part_sizes=sizes)
+    for vals in (A2.data, torch.as_tensor(A2.data, device="cuda")):
+        am.update_values(vals)
+        xa, sa = am.solve(f2)
+        xb, sb = fresh.solve(f2)
+        assert sa["iterations"] == sb["iterations"]
+        assert torch.equal(xa, xb)
+
+
 def test_single_subdomain_exact():
     """m = 1: no interface, z = A^{-1} r; PCG converges in one iteration."""
     A, f, _ = small3d(shape=(9, 8, 7), m=1, uneven=False)
