@@ -16,6 +16,7 @@
 
 using namespace am;
 
+
 namespace {
 
 thread_local std::string g_err;
@@ -62,7 +63,7 @@ struct NumWs {
     int64_t ntiles_items = 0, trows_items = 0;
     int max_tiles_items = 0;
     double *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr, *gE = nullptr, *RHS = nullptr;
-    int32_t* d_gjob = nullptr;
+    int32_t *d_gjob = nullptr, *d_gjt0 = nullptr, *d_cjt0 = nullptr;
     int64_t *d_gjin = nullptr, *d_wjin = nullptr;
     int32_t* d_wjob = nullptr;
     int njobs_g = 0, njobs_w = 0;
@@ -119,12 +120,15 @@ struct algmortar_handle {
     // workspace
     double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_pbar = nullptr;
     double *d_beta = nullptr, *d_eta = nullptr, *d_b = nullptr, *d_t = nullptr;
-    double *d_part_rz = nullptr, *d_part_pq = nullptr, *d_part_rr = nullptr, *d_part_t = nullptr;
+    GridSum gs{};                      // partials + ticket of the deterministic grid sums
     double* d_scalar = nullptr;
     PcgScalars* d_pcg = nullptr;
     int* d_kerr = nullptr;             // kernel error word (stuck bulk copy)
     NumWs* ws = nullptr;               // persistent numeric-setup buffers
     int32_t* d_psrc = nullptr;         // permuted CSR value t = original value psrc[t]
+    int64_t* d_rp_ptr = nullptr;       // restriction entry -> CSR positions of its couplings
+    int32_t* d_rp_pos = nullptr;
+    int32_t* d_g_from_r = nullptr;     // G entry -> restriction entry
     int64_t* d_ell_ptr = nullptr;      // sliced-ELL copy of the matrix (SpMV)
     int32_t *d_ell_col = nullptr, *d_ell_src = nullptr;
     double* d_ell_val = nullptr;
@@ -237,7 +241,8 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         const int G = P.nd_G;
         const int64_t nin = P.nd_goff[G];
         const int nsep = P.nd_nsep;
-        std::vector<int32_t> irows, int_, ilo, ihi, titem, tI, tJ, gjob, wjob, colitem, cola, entg, row_g, prow_g;
+        std::vector<int32_t> irows, int_, ilo, ihi, titem, tI, tJ, gjob, gjt0, wjob, colitem, cola, entg, row_g,
+            prow_g;
         std::vector<int64_t> irow0, ibase, ifwd, ibwd, isrc, gjin, wjin, gioff(G, 0), woff(G, 0), doff(G, 0),
             entbase(G, 0);
         int64_t trow = 0, tb = 0, gi = 0, wo = 0, dof = 0, ent = 0;
@@ -278,6 +283,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
                 tb += (int64_t)T * (T + 1) / 2;
                 for (int64_t c = 0; c < ng; ++c) {
                     gjob.push_back(it);
+                    gjt0.push_back((int32_t)(c / TILE));
                     gjin.push_back(gi + c * ng);
                 }
                 for (int64_t c = 0; c < ag; ++c) {
@@ -315,6 +321,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         TRY(upload(h, W.d_tJ, tJ));
         TRY(upload(h, W.d_gjob, gjob));
         TRY(upload(h, W.d_gjin, gjin));
+        TRY(upload(h, W.d_gjt0, gjt0));
         TRY(upload(h, W.d_wjob, wjob));
         TRY(upload(h, W.d_wjin, wjin));
         TRY(upload(h, W.d_colitem, colitem));
@@ -412,6 +419,8 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             W.c_hi.assign(T, T - 1);
             std::vector<int32_t> clo(T, 0), chi(T, T - 1), cj(nsep, 0);
             std::vector<int64_t> cfwd(T), cbwd(T), cjin(nsep), czero{0};
+            std::vector<int32_t> cjt0(nsep);
+            for (int q = 0; q < nsep; ++q) cjt0[q] = q / TILE;
             for (int I = 0; I < T; ++I) {
                 cfwd[I] = (int64_t)I * (I + 1) / 2;
                 cbwd[I] = (int64_t)(T - 1 - I) * (T - I) / 2;
@@ -427,6 +436,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             TRY(upload(h, W.d_cbwd, cbwd));
             TRY(upload(h, W.d_cjob, cj));
             TRY(upload(h, W.d_cjin, cjin));
+            TRY(upload(h, W.d_cjt0, cjt0));
             const int64_t ct = (int64_t)T * (T + 1) / 2;
             W.cwork = h->alloc<double>((size_t)ct * TILE2);
             W.cdinv = h->alloc<double>((size_t)T * TILE2);
@@ -465,6 +475,9 @@ int numeric_setup(algmortar_t* h) {
     const int64_t tiles = P.total_tiles, nphi = P.phi_off[m];
     TW* work = (TW*)W.work;
     TW* dinv = (TW*)W.dinv;
+    // value-dependent interface tables (restriction coefficients, T_I, G entries)
+    launch_iface_tables(L, (int64_t)P.r_cell.size(), h->d_rp_ptr, h->d_rp_pos, h->d_val, h->d_rptr, h->d_rcoef,
+                        W.d_T ? W.d_T : h->d_scalar, (int64_t)P.g_val.size(), h->d_g_from_r, W.d_gval, st);
     // --- local factors (Algorithm 1: extract A_ii, modify its diagonal, factor) ---
     int err_init[2] = {0, -1};
     CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
@@ -548,16 +561,18 @@ int numeric_setup(algmortar_t* h) {
         sa.job_sub = W.d_gjob;
         sa.job_in = W.d_gjin;
         sa.job_out = W.d_gjin;
+        sa.job_t0 = W.d_gjt0;          // lower triangle of S_gg^{-1} only
         sa.in = W.gE;
         sa.out = (double*)h->nd.Ginv;
         CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
+        sa.job_t0 = nullptr;
         sa.job_sub = W.d_wjob;
         sa.job_in = W.d_wjin;
         sa.job_out = W.d_wjin;
         sa.in = W.RHS;
         sa.out = (double*)h->nd.Wcm;
         CU((launch_tile_solve<double, double>(sa, W.njobs_w, W.max_tiles_items, st)));
-        launch_symmetrise(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
+        launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
         launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
         if (nsep > 0) {
             launch_nd_schur_blocks(W.nent, h->nd.goff, h->nd.aoff, h->nd.woff, W.d_doff, W.d_entg, W.d_entbase, W.RHS,
@@ -579,10 +594,11 @@ int numeric_setup(algmortar_t* h) {
             ca.job_sub = W.d_cjob;
             ca.job_in = W.d_cjin;
             ca.job_out = W.d_cjin;
+            ca.job_t0 = W.d_cjt0;      // lower triangle of C^{-1} only
             ca.in = W.cE;
             ca.out = (double*)h->nd.Cinv;
             CU((launch_tile_solve<double, double>(ca, nsep, W.cT, st)));
-            launch_symmetrise(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
+            launch_mirror_lower(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
         }
         CU(cudaGetLastError());
         cudaEventRecord(ev[5], st);
@@ -649,40 +665,39 @@ void stage_coarse(algmortar_t* h, const int32_t* done) {
     if (h->L > 0) launch_nd_solve(h->nd, h->d_beta, h->d_eta, h->d_P, done, h->st);
 }
 
-// z = pbar + Phi eta, with the partial of r . z when part_rz is given.
+// z = pbar + Phi eta, and r . z into *rz when rz is given.
 template <typename TS>
-void stage_prolong(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
-    launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list, h->d_phi_off,
-                       (const TS*)h->d_phi, h->d_eta, h->d_pbar, z, part_rz ? r : nullptr, part_rz, done, h->st);
+void stage_prolong(algmortar_t* h, const double* r, double* z, const int32_t* done, double* rz) {
+    launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list,
+                       h->d_phi_off, (const TS*)h->d_phi, h->d_eta, h->d_pbar, z, r, h->gs, rz, done, h->st);
 }
 
 template <typename TS, typename TA>
-int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
+int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, double* rz) {
     TRY((stage_local<TS, TA>(h, r, done)));
     stage_restrict(h, done);
     stage_coarse(h, done);
-    stage_prolong<TS>(h, r, z, done, part_rz);
+    stage_prolong<TS>(h, r, z, done, rz);
     CU(cudaGetLastError());
     return 0;
 }
 
-int apply_internal(algmortar_t* h, const double* r, double* z, const int32_t* done, double* part_rz) {
+int apply_internal(algmortar_t* h, const double* r, double* z, const int32_t* done, double* rz) {
     switch (h->opts.precision) {
-        case ALGMORTAR_FP64: return apply_t<double, double>(h, r, z, done, part_rz);
-        case ALGMORTAR_FP32: return apply_t<float, float>(h, r, z, done, part_rz);
-        default: return apply_t<__nv_bfloat16, float>(h, r, z, done, part_rz);
+        case ALGMORTAR_FP64: return apply_t<double, double>(h, r, z, done, rz);
+        case ALGMORTAR_FP32: return apply_t<float, float>(h, r, z, done, rz);
+        default: return apply_t<__nv_bfloat16, float>(h, r, z, done, rz);
     }
 }
 
 int pcg_iteration(algmortar_t* h) {
     cudaStream_t st = h->st;
     const int32_t* done = &h->d_pcg->done;
-    launch_pcg_p(h->n, h->d_z, h->d_p, h->d_r, nullptr, h->d_pcg, h->d_part_rz, st);
-    launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_part_pq, h->d_pcg,
-                        h->d_part_rz, st);
-    launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->d_part_pq, h->d_part_rr, st);
-    launch_pcg_check(h->d_pcg, h->d_part_pq, h->d_part_rr, st);
-    return apply_internal(h, h->d_r, h->d_z, done, h->d_part_rz);
+    launch_pcg_p(h->n, h->d_z, h->d_p, h->d_pcg, st);
+    launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_pcg, h->gs, st);
+    launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->gs, st);
+    launch_pcg_check(h->d_pcg, st);
+    return apply_internal(h, h->d_r, h->d_z, done, &h->d_pcg->rz_next);
 }
 
 int ensure_graph(algmortar_t* h) {
@@ -714,9 +729,8 @@ int pcg_internal(algmortar_t* h, double tol, algmortar_stats* stt) {
     double t0 = now_ms();
     if (!(tol > 0.0)) return fail(ALGMORTAR_INVALID_ARG, "tol must be positive");
     if (h->opts.use_graph) TRY(ensure_graph(h));
-    launch_pcg_init(h->n, h->d_b, h->d_x, h->d_r, h->d_part_t, st);
-    launch_pcg_start(h->d_pcg, h->d_part_t, tol, h->opts.max_it, h->opts.flexible, st);
-    TRY(apply_internal(h, h->d_r, h->d_z, &h->d_pcg->done, h->d_part_rz));
+    launch_pcg_init(h->n, h->d_b, h->d_x, h->d_r, h->d_pcg, h->gs, tol, h->opts.max_it, st);
+    TRY(apply_internal(h, h->d_r, h->d_z, &h->d_pcg->done, &h->d_pcg->rz_next));
     PcgScalars hs{};
     int restarts = 0;
     const int every = h->opts.check_every > 0 ? h->opts.check_every : 1;
@@ -733,10 +747,9 @@ int pcg_internal(algmortar_t* h, double tol, algmortar_stats* stt) {
         CU(cudaMemcpyAsync(&hs, h->d_pcg, sizeof(hs), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         if (!hs.done) continue;
-        launch_residual(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_x, h->d_b, h->d_part_t, st);
-        launch_sum_partials(h->d_part_t, h->d_scalar, st);
+        launch_residual(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_x, h->d_b, h->d_pcg, h->gs, st);
         double res2 = 0.0;
-        CU(cudaMemcpyAsync(&res2, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(&res2, &h->d_pcg->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         true_rel = hs.bb > 0 ? std::sqrt(res2 / hs.bb) : 0.0;
         if (hs.status == 0 && hs.bb > 0 && !(true_rel <= tol) && restarts < 8 && hs.iter < hs.max_it) {
@@ -812,9 +825,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         if (cudaStreamCreate(&h->own_st) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "cudaStreamCreate"));
         h->st = h->own_st;
     }
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
-    set_vec_grid(sms);
+
     Plan& P = h->P;
     h->n = P.n;
     h->m = P.m;
@@ -857,6 +868,9 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         rc = rc ? rc : upload(h, h->d_psrc, psrc);
     }
     if (rc) return bail(rc);
+    rc = rc ? rc : upload(h, h->d_rp_ptr, P.rp_ptr);
+    rc = rc ? rc : upload(h, h->d_rp_pos, P.rp_pos);
+    rc = rc ? rc : upload(h, h->d_g_from_r, P.g_from_r);
     rc = rc ? rc : upload(h, h->d_ell_ptr, P.ell_ptr);
     rc = rc ? rc : upload(h, h->d_ell_col, P.ell_col);
     rc = rc ? rc : upload(h, h->d_ell_src, P.ell_src);
@@ -871,7 +885,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     launch_ell_values(h->n_ell, h->d_ell_src, h->d_vtmp, h->d_ell_val, h->st);
     h->pf = Profile{h->d_rows, h->d_ntiles, d_row0, d_base, d_lo, d_hi, d_fwd, d_bwd};
     const int64_t n = h->n;
-    const int np = vec_grid();
+    const int np = vec_blocks(P.n);
     h->d_dloc = h->alloc<double>(n);
     h->d_sc = h->alloc<double>(n);
     h->d_x = h->alloc<double>(n);
@@ -884,20 +898,19 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     h->d_t = h->alloc<double>(n);
     h->d_beta = h->alloc<double>(h->L);
     h->d_eta = h->alloc<double>(h->L);
-    h->d_part_rz = h->alloc<double>(np);
-    h->d_part_pq = h->alloc<double>(np);
-    h->d_part_rr = h->alloc<double>(np);
-    h->d_part_t = h->alloc<double>(np);
+    h->gs.part = h->alloc<double>(np);
+    h->gs.ticket = h->alloc<unsigned int>(1);
     h->d_scalar = h->alloc<double>(4);
     h->d_pcg = h->alloc<PcgScalars>(1);
     h->d_kerr = h->alloc<int>(1);
     if (!h->d_dloc || !h->d_sc || !h->d_x || !h->d_r || !h->d_z || !h->d_p || !h->d_q || !h->d_pbar || !h->d_b ||
-        !h->d_t || !h->d_beta || !h->d_eta || !h->d_part_rz || !h->d_part_pq || !h->d_part_rr || !h->d_part_t ||
+        !h->d_t || !h->d_beta || !h->d_eta || !h->gs.part || !h->gs.ticket ||
         !h->d_scalar || !h->d_pcg || !h->d_kerr)
         return bail(fail(ALGMORTAR_OOM, "workspace"));
     if (cudaMemsetAsync(h->d_p, 0, n * sizeof(double), h->st) != cudaSuccess ||
         cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->st) != cudaSuccess ||
-        cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->st) != cudaSuccess)
+        cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->st) != cudaSuccess ||
+        cudaMemsetAsync(h->gs.ticket, 0, sizeof(unsigned int), h->st) != cudaSuccess)
         return bail(fail(ALGMORTAR_CUDA, "memset"));
     double t_up = now_ms();
     rc = numeric_dispatch(h);
@@ -1116,11 +1129,10 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     for (int it = 0; it <= reps; ++it) {
         CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));
         cudaEventRecord(ev[0], st);
-        launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_part_pq,
-                            h->d_pcg, h->d_part_rz, st);
+        launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_pcg, h->gs, st);
         cudaEventRecord(ev[1], st);
-        launch_pcg_p(h->n, h->d_z, h->d_p, h->d_r, nullptr, h->d_pcg, h->d_part_rz, st);
-        launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->d_part_pq, h->d_part_rr, st);
+        launch_pcg_p(h->n, h->d_z, h->d_p, h->d_pcg, st);
+        launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->gs, st);
         cudaEventRecord(ev[2], st);
         // stages of Algorithm 2 (same launches as apply_internal, timed one by one)
         switch (h->opts.precision) {
@@ -1134,9 +1146,9 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
         stage_coarse(h, nullptr);
         cudaEventRecord(ev[5], st);
         switch (h->opts.precision) {
-            case ALGMORTAR_FP64: stage_prolong<double>(h, h->d_r, h->d_z, nullptr, h->d_part_rz); break;
-            case ALGMORTAR_FP32: stage_prolong<float>(h, h->d_r, h->d_z, nullptr, h->d_part_rz); break;
-            default: stage_prolong<__nv_bfloat16>(h, h->d_r, h->d_z, nullptr, h->d_part_rz); break;
+            case ALGMORTAR_FP64: stage_prolong<double>(h, h->d_r, h->d_z, nullptr, &h->d_pcg->rz_next); break;
+            case ALGMORTAR_FP32: stage_prolong<float>(h, h->d_r, h->d_z, nullptr, &h->d_pcg->rz_next); break;
+            default: stage_prolong<__nv_bfloat16>(h, h->d_r, h->d_z, nullptr, &h->d_pcg->rz_next); break;
         }
         cudaEventRecord(ev[6], st);
         CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));

@@ -60,20 +60,27 @@ struct Profile {
 
 // Device-side PCG scalars (FP64 throughout, Sec. 7).
 struct PcgScalars {
-    double rz;        // r_k . z_k
-    double rz_prev;
+    double rz;        // rho_k = r_k . z_k of the current search direction
+    double rz_next;   // r . z of the latest preconditioned residual
     double pq;        // p_k . A p_k
     double alpha, beta;
-    double rr;        // ||r_k||^2
+    double rr;        // ||r_k||^2 (checked)
+    double rr_new;    // ||r||^2 after the latest update
     double bb;        // ||b||^2
     double tol2;      // tol^2 ||b||^2
+    double res2;      // ||b - A x||^2 (true residual, on request)
     int32_t iter;     // products with A so far
     int32_t done;     // 1: stop (converged or failed)
     int32_t status;   // 0 converged, 5 max_it, 6 breakdown
     int32_t max_it;
-    int32_t flexible;
-    int32_t pad;
-    double rr_prev;   // for the flexible (Polak-Ribiere) beta
+};
+
+// Deterministic grid-wide sum: every CTA writes its block sum to part[blockIdx.x]; the
+// CTA that finishes last (atomic ticket) adds the partials in a fixed order, stores the
+// total and re-arms the ticket.  Same inputs -> bit-identical result.
+struct GridSum {
+    double* part;          // >= gridDim.x doubles
+    unsigned int* ticket;  // 0 between launches
 };
 
 // Deterministic fixed-order sum of `n` partials by one warp; result in all lanes.
@@ -81,6 +88,16 @@ __device__ __forceinline__ double warp_sum_partials(const double* part, int n) {
     int lane = threadIdx.x & 31;
     double s = 0.0;
     for (int i = lane; i < n; i += 32) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Same as warp_sum_partials, reading with L1 bypass (partials written by other CTAs).
+__device__ __forceinline__ double warp_sum_partials_cg(const double* part, int n) {
+    int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += __ldcg(part + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
@@ -102,6 +119,30 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     }
     __syncthreads();
     return s;
+}
+
+// Grid-wide deterministic sum of v into *result (see GridSum); returns true in the CTA
+// that wrote the result (its threads may then use *result after a __syncthreads).
+__device__ __forceinline__ bool grid_sum(double v, double* sh, GridSum g, double* result) {
+    __shared__ int last;
+    double s = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        g.part[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(g.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < 32) {
+            double t = warp_sum_partials_cg(g.part, gridDim.x);
+            if (threadIdx.x == 0) {
+                *result = t;
+                *g.ticket = 0;
+            }
+        }
+    }
+    return last != 0;
 }
 
 }  // namespace am

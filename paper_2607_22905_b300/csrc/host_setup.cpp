@@ -537,9 +537,11 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
     struct RC {
         int32_t I, cell;
         double c;
+        int64_t pos0, npos;   // positions of the row's couplings to the other side
     };
     std::vector<RC> rc;
-    std::vector<std::pair<int32_t, double>> acc;
+    std::vector<int32_t> row_pos;     // CSR positions, grouped per (row, interface)
+    std::vector<std::pair<int32_t, std::vector<int32_t>>> acc;
     for (int64_t k = 0; k < n; ++k) {
         int32_t i = P.row_sub[k];
         acc.clear();
@@ -552,24 +554,34 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             bool found = false;
             for (auto& pr : acc)
                 if (pr.first == I) {
-                    pr.second += P.p_val[e];
+                    pr.second.push_back(e);
                     found = true;
                 }
-            if (!found) acc.push_back({I, P.p_val[e]});
+            if (!found) acc.push_back({I, std::vector<int32_t>{e}});
         }
-        for (auto& pr : acc) rc.push_back({pr.first, (int32_t)k, pr.second});
+        for (auto& pr : acc) {
+            double c = 0.0;
+            for (int32_t e : pr.second) c += P.p_val[e];
+            rc.push_back({pr.first, (int32_t)k, c, (int64_t)row_pos.size(), (int64_t)pr.second.size()});
+            row_pos.insert(row_pos.end(), pr.second.begin(), pr.second.end());
+        }
     }
-    // restriction table, interface-major
+    // restriction table, interface-major; rp_* lists each entry's CSR positions so that
+    // the value-dependent coefficients can be recomputed on the device for new values
     std::sort(rc.begin(), rc.end(), [](const RC& a, const RC& b) {
         return a.I != b.I ? a.I < b.I : a.cell < b.cell;
     });
     P.r_ptr.assign(P.n_lambda + 1, 0);
     P.r_cell.resize(rc.size());
     P.r_coef.resize(rc.size());
+    P.rp_ptr.assign(rc.size() + 1, 0);
+    P.rp_pos.clear();
     for (size_t t = 0; t < rc.size(); ++t) {
         P.r_ptr[rc[t].I + 1]++;
         P.r_cell[t] = rc[t].cell;
         P.r_coef[t] = -0.5 * rc[t].c;
+        P.rp_pos.insert(P.rp_pos.end(), row_pos.begin() + rc[t].pos0, row_pos.begin() + rc[t].pos0 + rc[t].npos);
+        P.rp_ptr[t + 1] = (int64_t)P.rp_pos.size();
     }
     for (int32_t I = 0; I < P.n_lambda; ++I) P.r_ptr[I + 1] += P.r_ptr[I];
     // per-subdomain interface lists I_i and the sparse G_i
@@ -592,14 +604,17 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
     for (int32_t s = 0; s < m; ++s)
         P.phi_off[s + 1] = P.phi_off[s] + (P.sub_off[s + 1] - P.sub_off[s]) * (P.if_off[s + 1] - P.if_off[s]);
     {
-        std::vector<std::vector<RC>> per(m);
-        for (auto& x : rc) per[P.row_sub[x.cell]].push_back(x);
+        std::vector<std::vector<std::pair<RC, int32_t>>> per(m);
+        for (size_t t = 0; t < rc.size(); ++t) per[P.row_sub[rc[t].cell]].push_back({rc[t], (int32_t)t});
         P.g_off.assign(m + 1, 0);
+        P.g_from_r.clear();
         for (int32_t s = 0; s < m; ++s) {
-            std::sort(per[s].begin(), per[s].end(), [](const RC& a, const RC& b) {
-                return a.I != b.I ? a.I < b.I : a.cell < b.cell;
+            std::sort(per[s].begin(), per[s].end(), [](const std::pair<RC, int32_t>& a, const std::pair<RC, int32_t>& b) {
+                return a.first.I != b.first.I ? a.first.I < b.first.I : a.first.cell < b.first.cell;
             });
-            for (auto& x : per[s]) {
+            for (auto& xr : per[s]) {
+                const RC& x = xr.first;
+                P.g_from_r.push_back(xr.second);
                 auto f = std::lower_bound(P.if_list.begin() + P.if_off[s], P.if_list.begin() + P.if_off[s + 1], x.I);
                 P.g_col.push_back((int32_t)(f - (P.if_list.begin() + P.if_off[s])));
                 P.g_row.push_back((int32_t)(x.cell - P.sub_off[s]));

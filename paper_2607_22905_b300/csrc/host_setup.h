@@ -70,6 +70,8 @@ struct Plan {
     std::vector<int64_t> r_ptr;
     std::vector<int32_t> r_cell;
     std::vector<double> r_coef;         // = -1/4 G[k, I] = -1/2 c_k^(I)  (> 0)
+    std::vector<int64_t> rp_ptr;        // restriction entry t: its CSR positions
+    std::vector<int32_t> rp_pos;        //   rp_pos[rp_ptr[t] .. rp_ptr[t+1]) (c_k = sum of those values)
     // per subdomain interface lists I_i and MBF panel layout
     std::vector<int64_t> if_off;        // m + 1 into if_list
     std::vector<int32_t> if_list;       // global interface ids, ascending
@@ -80,6 +82,7 @@ struct Plan {
     std::vector<int64_t> g_off;         // m + 1
     std::vector<int32_t> g_row, g_col;
     std::vector<double> g_val;
+    std::vector<int32_t> g_from_r;      // G entry -> restriction entry (g_val = -4 r_coef)
     // interface system layout: RCM order of the interface graph and its tile profile
     std::vector<int32_t> s_perm;        // s_perm[pos] = interface id
     std::vector<int32_t> s_iperm;       // interface id -> pos

@@ -29,6 +29,8 @@ struct SolveArgs {
     double alpha;              // out = alpha * A_s^{-1} in
     const int32_t* done;       // early exit when *done != 0 (PCG), or null
     int* err;                  // set to 1 if a bulk copy never completed (bounded wait)
+    const int32_t* job_t0;     // per job: tile row where the right-hand side starts (rows
+                               // above are zero) and below which no result is needed; or null
 };
 
 struct InterfaceArgs {
@@ -85,6 +87,9 @@ struct NdSolveArgs {
 };
 
 // interface system (kernels_coarse.cu)
+void launch_iface_tables(int L, int64_t nr, const int64_t* rp_ptr, const int32_t* rp_pos, const double* val,
+                         const int64_t* r_ptr, double* rcoef, double* T, int64_t ng, const int32_t* g_from_r,
+                         double* gval, cudaStream_t st);
 void launch_nd_assemble(int m, const NdAssembleArgs& a, cudaStream_t st);
 void launch_nd_diag(int L, const double* T, const double* diagc, const int32_t* nd_pos, double* Sd, cudaStream_t st);
 void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const int64_t* src_off, const int32_t* rows,
@@ -94,6 +99,7 @@ void launch_nd_rhs(int64_t ncols, int64_t L, const double* Sd, const int64_t* go
                    const int32_t* alist, int64_t sep0, const int64_t* woff, const int32_t* col_item,
                    const int32_t* col_a, double* out, cudaStream_t st);
 void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
+void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
                              double* Wrm, cudaStream_t st);
 void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* aoff, const int64_t* woff,
@@ -140,38 +146,28 @@ void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double
 
 // vector / PCG kernels (kernels_pcg.cu)
 constexpr int VEC_BS = 256;
-int vec_grid();                               // CTAs of every partial-producing vector kernel
-void set_vec_grid(int sms);
+int vec_blocks(int64_t n);                    // CTAs of the one-row-per-thread kernels
 void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st);
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* omap, const int32_t* done, cudaStream_t st);
-void launch_coarse_gemv(int L, const double* Sinv, const double* b, double* eta, const int32_t* done,
-                        cudaStream_t st);
 template <typename TP>
 void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
                     const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
-                    const double* pbar, double* z, const double* r, double* part, const int32_t* done,
+                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, const int32_t* done,
                     cudaStream_t st);
-void launch_pcg_init(int64_t n, const double* b, double* x, double* r, double* part, cudaStream_t st);
-void launch_pcg_start(PcgScalars* sc, const double* part_bb, double tol, int max_it, int flexible,
-                      cudaStream_t st);
-void launch_pcg_p(int64_t n, const double* z, double* p, const double* r, double* r_old, PcgScalars* sc,
-                  const double* part_rz, cudaStream_t st);
-void launch_pcg_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                     const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
-                     cudaStream_t st);
+void launch_pcg_init(int64_t n, const double* b, double* x, double* r, PcgScalars* sc, GridSum gs, double tol,
+                     int max_it, cudaStream_t st);
+void launch_pcg_p(int64_t n, const double* z, double* p, const PcgScalars* sc, cudaStream_t st);
 void launch_pcg_spmv_ell(int64_t n, const int64_t* ell_ptr, const int32_t* ell_col, const double* ell_val,
-                         const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
-                         cudaStream_t st);
+                         const double* p, double* q, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
-void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc,
-                   const double* part_pq, double* part_rr, cudaStream_t st);
-void launch_pcg_check(PcgScalars* sc, const double* part_pq, const double* part_rr, cudaStream_t st);
-void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                     const double* x, const double* b, double* part, cudaStream_t st);
-void launch_sum_partials(const double* part, double* out, cudaStream_t st);
+void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc, GridSum gs,
+                   cudaStream_t st);
+void launch_pcg_check(PcgScalars* sc, cudaStream_t st);
+void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* x,
+                     const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,
                       const double* tb, const double* tbp, const double* p, const double* lam, double* grad,
                       cudaStream_t st);

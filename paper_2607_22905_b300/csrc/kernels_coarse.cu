@@ -15,10 +15,40 @@
 // (A_g: separator unknowns coupled to group g.)  Every per-iteration product runs as a
 // wide warp-per-row GEMV over all SMs (FP64 ALU-bound on B300), with no sequential
 // triangular sweep on the critical path.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace am {
+
+// ---------------------------------------------------------------------------------
+// Value-dependent interface tables, recomputed for every numeric setup:
+//   c_k^(I) = sum of row k's couplings a_kl to the other subdomain of interface I
+//   r_coef  = -1/2 c_k^(I)          (restriction, b_eta = -1/4 G^T pbar)
+//   G[k, I] = 2 c_k^(I) = -4 r_coef (coupling B psi_I, Eq. Bij-contrib)
+//   T_I     = sum_{(k,l) in E_I} |a_kl| = sum over both sides of -1/2 c_k^(I)
+// ---------------------------------------------------------------------------------
+__global__ void k_iface_coef(int64_t nr, const int64_t* __restrict__ rp_ptr, const int32_t* __restrict__ rp_pos,
+                             const double* __restrict__ val, double* __restrict__ rcoef) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nr; t += (int64_t)gridDim.x * blockDim.x) {
+        double c = 0.0;
+        for (int64_t e = rp_ptr[t]; e < rp_ptr[t + 1]; ++e) c += val[rp_pos[e]];
+        rcoef[t] = -0.5 * c;
+    }
+}
+
+__global__ void k_iface_T_g(int L, const int64_t* __restrict__ r_ptr, const double* __restrict__ rcoef,
+                            double* __restrict__ T, int64_t ng, const int32_t* __restrict__ g_from_r,
+                            double* __restrict__ gval) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < L) {
+        double s = 0.0;
+        for (int64_t t = r_ptr[i]; t < r_ptr[i + 1]; ++t) s += rcoef[t];
+        T[i] = s;
+    }
+    for (int64_t u = i; u < ng; u += (int64_t)gridDim.x * blockDim.x) gval[u] = -4.0 * rcoef[g_from_r[u]];
+}
 
 // ---------------------------------------------------------------------------------
 // Assembly into a dense, ND-ordered, symmetric n_lambda x n_lambda matrix Sd (row-major).
@@ -119,6 +149,20 @@ __global__ void k_symmetrise(const int32_t* __restrict__ rows, const int64_t* __
             A[i * n + j] = v;
             A[j * n + i] = v;
         }
+    }
+}
+
+// Column-major square blocks whose lower triangle holds a symmetric matrix: copy it to
+// the upper triangle (M[j][i] = M[i][j] for i > j).
+__global__ void k_mirror_lower(const int32_t* __restrict__ rows, const int64_t* __restrict__ off, int nitems,
+                               double* __restrict__ M) {
+    const int g = blockIdx.y;
+    if (g >= nitems) return;
+    const int64_t n = rows[g];
+    double* A = M + off[g];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / n, r = e % n;     // column c, row r (column-major element e)
+        if (r < c) A[e] = A[r * n + c];          // (r, c) above the diagonal <- (c, r) below it
     }
 }
 
@@ -266,6 +310,19 @@ __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, const int32
 }
 
 // ------------------------------------------------------------------------ launchers
+void launch_iface_tables(int L, int64_t nr, const int64_t* rp_ptr, const int32_t* rp_pos, const double* val,
+                         const int64_t* r_ptr, double* rcoef, double* T, int64_t ng, const int32_t* g_from_r,
+                         double* gval, cudaStream_t st) {
+    if (nr > 0) {
+        count_launch();
+        k_iface_coef<<<(unsigned)std::min<int64_t>((nr + 255) / 256, 4096), 256, 0, st>>>(nr, rp_ptr, rp_pos, val,
+                                                                                         rcoef);
+        const int64_t work = std::max<int64_t>(L, 1);
+        count_launch();
+        k_iface_T_g<<<(unsigned)std::min<int64_t>((work + 255) / 256, 4096), 256, 0, st>>>(L, r_ptr, rcoef, T, ng,
+                                                                                          g_from_r, gval);
+    }
+}
 void launch_nd_assemble(int m, const NdAssembleArgs& a, cudaStream_t st) {
     if (m > 0) {
         count_launch();
@@ -299,6 +356,12 @@ void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, doub
     if (nitems > 0) {
         count_launch();
         k_symmetrise<<<dim3(256, nitems), 256, 0, st>>>(rows, off, nitems, M);
+    }
+}
+void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st) {
+    if (nitems > 0) {
+        count_launch();
+        k_mirror_lower<<<dim3(256, nitems), 256, 0, st>>>(rows, off, nitems, M);
     }
 }
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,

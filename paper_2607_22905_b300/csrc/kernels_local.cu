@@ -460,6 +460,13 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
     const int n = pf.rows[s], T = pf.ntiles[s];
     const int64_t r0 = pf.row0[s];
     const int64_t nts = pf.fwd[r0 + T - 1] + (T - 1 - pf.lo[r0 + T - 1]) + 1;   // tiles per stream
+    // Optional start row t0 (identity right-hand side e_j, j in tile row t0): rows above
+    // t0 stay zero in the forward sweep, and only rows >= t0 of the result are wanted, so
+    // the forward sweep starts and the backward sweep stops at t0.  The consumed tiles are
+    // then stream positions [q0, qend), still contiguous.
+    const int t0 = a.job_t0 ? a.job_t0[job] : 0;
+    const int64_t q0 = pf.fwd[r0 + t0];
+    const int64_t qend = nts + pf.bwd[r0 + t0] + (pf.hi[r0 + t0] - t0) + 1;
     const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
     const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
     const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
@@ -472,16 +479,19 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
     TS* ring = reinterpret_cast<TS*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
     TA* part = reinterpret_cast<TA*>(smem_raw + R * TB + R * sizeof(uint64_t));   // [2][NW][32]
-    int32_t* lo_s = reinterpret_cast<int32_t*>(part + 2 * NW * TILE);
+    TA* tbuf = part + 2 * NW * TILE;                                                // [NW][32]
+    int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + NW * TILE);
     int32_t* hi_s = lo_s + T;
     TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));                        // 16-byte aligned
-    const int64_t total = 2 * nts;
     auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
+    // ring slot and mbarrier phase of stream position q (counted from q0)
+    auto slot_of = [&](int64_t q) { return (int)((q - q0) % R); };
+    auto parity_of = [&](int64_t q) { return (uint32_t)(((q - q0) / R) & 1); };
     if (tid == 0) {
         for (int i = 0; i < R; ++i) mbar_init(smem_u32(&bars[i]), 1);
         fence_async_smem();
-        for (int64_t q = 0; q < R && q < total; ++q)
-            tma_load_1d(smem_u32(ring + q * TILE2), src(q), TB, smem_u32(&bars[q]));
+        for (int64_t q = q0; q < q0 + R && q < qend; ++q)
+            tma_load_1d(smem_u32(ring + slot_of(q) * TILE2), src(q), TB, smem_u32(&bars[slot_of(q)]));
     }
     for (int i = tid; i < T; i += NW * 32) {
         lo_s[i] = pf.lo[r0 + i];
@@ -492,23 +502,23 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
 
     bool ok = true;
     auto wait_tile = [&](int64_t qq) -> const TS* {
-        const int slot = (int)(qq % R);
-        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[slot]), (uint32_t)((qq / R) & 1)));
+        const int slot = slot_of(qq);
+        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[slot]), parity_of(qq)));
         return ring + slot * TILE2;
     };
     auto refill = [&](int64_t qq) {   // tile qq has been read by every consumer: load qq + R
-        if (ok && qq + R < total) {
-            const int slot = (int)(qq % R);
+        if (ok && qq + R < qend) {
+            const int slot = slot_of(qq);
             fence_async_smem();
             tma_load_1d(smem_u32(ring + slot * TILE2), src(qq + R), TB, smem_u32(&bars[slot]));
         }
     };
-    int64_t q = 0;
+    int64_t q = q0;
     int64_t pending_diag = -1;      // diagonal tile whose slot is released at the next barrier
     int par = 0;
     for (int pass = 0; pass < 2; ++pass) {
-        for (int step = 0; step < T; ++step) {
-            const int I = pass == 0 ? step : T - 1 - step;
+        for (int step = t0; step < T; ++step) {
+            const int I = pass == 0 ? step : T - 1 - (step - t0);
             const int j0 = pass == 0 ? lo_s[I] : I + 1;
             const int nt = pass == 0 ? I - lo_s[I] : hi_s[I] - I;
             // off-diagonal tiles of the next step (the first backward step has none)
@@ -531,20 +541,13 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
             TA sum = 0;
 #pragma unroll
             for (int u = 0; u < NW; ++u) sum += part[(par * NW + u) * TILE + lane];
-            const TA t = rhs - sum;
-            // y = D t with t distributed one value per lane (shuffle broadcast)
-            TA y0 = 0, y1 = 0;
-            const int sw = swz_row_key<TS>(lane);
-            constexpr int E = 16 / sizeof(TS);
-            const TS* rowp = D + lane * TILE;
-#pragma unroll
-            for (int c = 0; c < TILE; c += 2) {
-                const TA d0 = ldf<TA>(rowp + (((c) / E) ^ sw) * E + (c) % E);
-                const TA d1 = ldf<TA>(rowp + (((c + 1) / E) ^ sw) * E + (c + 1) % E);
-                y0 += d0 * __shfl_sync(0xffffffffu, t, c);
-                y1 += d1 * __shfl_sync(0xffffffffu, t, c + 1);
-            }
-            vi[lane] = y0 + y1;         // every warp writes the same values
+            // y = D t: t goes through this warp's own shared buffer so that row `lane` of
+            // D and t are both read with 128-bit loads (row_dot)
+            TA* tw = tbuf + w * TILE;
+            tw[lane] = rhs - sum;
+            __syncwarp();
+            const TA y = row_dot<TS, TA>(D, lane, tw);
+            vi[lane] = y;               // every warp writes the same values
             // The diagonal slot may only be refilled once every warp has read it.  If the
             // next row needs R or more tiles before its barrier, the refill cannot wait
             // for that barrier (a warp could then wait on the refilled tile): release now.
@@ -564,8 +567,7 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
     if (!ok) {
         if (tid == 0) {
             atomicExch(a.err, 1);
-            for (int64_t qq = q; qq < total && qq < q + R; ++qq)
-                mbar_wait(smem_u32(&bars[qq % R]), (uint32_t)((qq / R) & 1));
+            for (int64_t qq = q; qq < qend && qq < q + R; ++qq) mbar_wait(smem_u32(&bars[slot_of(qq)]), parity_of(qq));
         }
         __syncthreads();
         return;
@@ -742,7 +744,7 @@ template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
     constexpr int R = ring_slots<TS>();
     constexpr int NW = 4;
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + 2 * NW * TILE * sizeof(TA) +
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + 3 * NW * TILE * sizeof(TA) +
                   (size_t)(2 * max_tiles + 4) * sizeof(int32_t) + (size_t)max_tiles * TILE * sizeof(TA) + 16;
     cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -1,11 +1,12 @@
-// Global-vector kernels of AlgMortar-PCG on sm_103a: CSR SpMV, the fused FP64 CG vector
-// updates and dot products (Sec. 7: x0 = 0, Euclidean relative-residual stop), the
-// interface restriction and prolongation of Algorithm 2, and the coarse interface solve
-// as a product with the explicit (symmetrised) inverse.
+// Global-vector kernels of AlgMortar-PCG on sm_103a: SpMV (sliced ELL), the fused FP64
+// CG vector updates and dot products (Sec. 7: x0 = 0, Euclidean relative-residual stop),
+// the interface restriction and prolongation of Algorithm 2, value refreshes, and the
+// adjoint gradient of the TPFA transmissibilities.
 //
-// Dot products are deterministic: every partial-producing kernel runs with exactly
-// vec_grid() CTAs, writes one partial per CTA, and consumers sum the partials in a fixed
-// order (warp_sum_partials), so repeated runs give bit-identical scalars.
+// Vector kernels run one row per thread.  Dot products are deterministic: each CTA
+// writes its block sum, and the CTA that finishes last adds the partials in a fixed
+// order (GridSum) and stores the scalar straight into the device-side PCG state, so
+// repeated runs give bit-identical iterates and no partial arrays cross kernels.
 #include <atomic>
 #include <type_traits>
 
@@ -19,9 +20,11 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-static int g_vec_grid = 4 * 148;
-int vec_grid() { return g_vec_grid; }
-void set_vec_grid(int sms) { g_vec_grid = 4 * (sms > 0 ? sms : 148); }
+// CTAs of a one-row-per-thread vector kernel over n rows (= size of its GridSum partials)
+int vec_blocks(int64_t n) {
+    int64_t g = (n + VEC_BS - 1) / VEC_BS;
+    return (int)(g < 1 ? 1 : (g > (1 << 30) ? (1 << 30) : g));
+}
 
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
@@ -31,18 +34,19 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const doub
     GRID_STRIDE(k, n) dst[k] = src[perm[k]];
 }
 
-__global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, const double* __restrict__ v,
-                                 double* __restrict__ dst) {
-    GRID_STRIDE(k, n) dst[idx[k]] = v[k];
-}
-
 __global__ void k_scatter(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
                           double* __restrict__ dst) {
     GRID_STRIDE(k, n) dst[perm[k]] = src[k];
 }
 
+__global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, const double* __restrict__ v,
+                                 double* __restrict__ dst) {
+    GRID_STRIDE(k, n) dst[idx[k]] = v[k];
+}
+
 // b_eta[I] = -1/4 sum_k G[k, I] pbar_k = sum_{(k,l) in E_I} |a_kl| (pbar_k + pbar_l)/2 --
-// the interface right-hand side of Eq. (interface-problem-alg), one warp per interface.
+// the interface right-hand side of Eq. (interface-problem-alg), one warp per interface,
+// written at position omap[I] (the interface solve's ordering) when omap is given.
 __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_t* __restrict__ rcell,
                            const double* __restrict__ rcoef, const double* __restrict__ pbar,
                            double* __restrict__ beta, const int32_t* __restrict__ omap,
@@ -58,23 +62,8 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     if (lane == 0) beta[omap ? omap[I] : I] = s;
 }
 
-// eta = S_eta^{-1} b_eta, one warp per row of the explicit inverse (FP64).
-__global__ void k_coarse_gemv(int L, const double* __restrict__ Sinv, const double* __restrict__ b,
-                              double* __restrict__ eta, const int32_t* __restrict__ done) {
-    if (done && *done) return;
-    int I = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
-    if (I >= L) return;
-    const double* row = Sinv + (int64_t)I * L;
-    double s = 0.0;
-    for (int J = lane; J < L; J += 32) s += row[J] * __ldg(b + J);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) eta[I] = s;
-}
-
-// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg), fused with
-// the partial of r . z when r is given.
+// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg), one row
+// per thread; with `rz` given, also the grid-wide r . z.
 template <typename TP>
 __global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __restrict__ row_sub,
                                                      const int64_t* __restrict__ sub_off,
@@ -83,171 +72,113 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __
                                                      const int64_t* __restrict__ phi_off,
                                                      const TP* __restrict__ phi, const double* __restrict__ eta,
                                                      const double* __restrict__ pbar, double* __restrict__ z,
-                                                     const double* __restrict__ r, double* __restrict__ part,
+                                                     const double* __restrict__ r, GridSum gs, double* rz,
                                                      const int32_t* __restrict__ done) {
     if (done && *done) return;
     __shared__ double sh[32];
+    // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
+    // (FP64 panels: FP64; FP32/BF16 panels: FP32), then added to pbar in FP64
+    using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     double acc = 0.0;
     GRID_STRIDE(k, n) {
-        int32_t s = row_sub[k];
-        int64_t a = sub_off[s];
-        int64_t ns = sub_off[s + 1] - a;
-        int64_t i0 = if_off[s];
-        int kk = (int)(if_off[s + 1] - i0);
+        const int32_t s = row_sub[k];
+        const int64_t a = sub_off[s];
+        const int64_t ns = sub_off[s + 1] - a;
+        const int64_t i0 = if_off[s];
+        const int kk = (int)(if_off[s + 1] - i0);
         const TP* ph = phi + phi_off[s] + (k - a);
-        // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
-        // (FP64 panels: FP64; FP32/BF16 panels: FP32), then added to pbar in FP64
-        using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
         TA corr = 0;
-        for (int c = 0; c < kk; ++c) corr += ldf<TA>(ph + c * ns) * (TA)eta[if_list[i0 + c]];
-        double v = pbar[k] + (double)corr;
+        for (int c = 0; c < kk; ++c) corr += ldf<TA>(ph + c * ns) * (TA)__ldg(eta + __ldg(if_list + i0 + c));
+        const double v = pbar[k] + (double)corr;
         z[k] = v;
-        if (r) acc += r[k] * v;
+        if (rz) acc += r[k] * v;
     }
-    if (part) {
-        double s = block_sum(acc, sh);
-        if (threadIdx.x == 0) part[blockIdx.x] = s;
-    }
+    if (rz) grid_sum(acc, sh, gs, rz);
 }
 
 // ------------------------------------------------------------------------------ PCG
+// x = 0, r = b, ||b||^2; the CTA that completes the sum initialises the PCG state.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __restrict__ b,
                                                       double* __restrict__ x, double* __restrict__ r,
-                                                      double* __restrict__ part) {
+                                                      PcgScalars* __restrict__ sc, GridSum gs, double tol,
+                                                      int max_it) {
     __shared__ double sh[32];
     double acc = 0.0;
     GRID_STRIDE(k, n) {
-        double v = b[k];
+        const double v = b[k];
         r[k] = v;
         x[k] = 0.0;
         acc += v * v;
     }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void k_pcg_start(PcgScalars* sc, const double* __restrict__ part, int np, double tol, int max_it,
-                            int flexible) {
-    double bb = warp_sum_partials(part, np);
-    if (threadIdx.x == 0) {
-        sc->bb = bb;
+    if (grid_sum(acc, sh, gs, &sc->bb) && threadIdx.x == 0) {
+        const double bb = sc->bb;
         sc->rr = bb;
+        sc->rr_new = bb;
         sc->tol2 = tol * tol * bb;
         sc->iter = 0;
         sc->done = bb == 0.0 ? 1 : 0;
         sc->status = 0;
         sc->max_it = max_it;
-        sc->flexible = flexible;
         sc->rz = 0.0;
-        sc->rz_prev = 0.0;
+        sc->rz_next = 0.0;
         sc->alpha = sc->beta = sc->pq = 0.0;
     }
 }
 
-// p = z + beta p, beta = rho_k / rho_{k-1} (0 on the first iteration).
+// p = z + beta p, beta = rho_new / rho (0 on the first iteration).
 __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
-                                                   PcgScalars* __restrict__ sc, const double* __restrict__ part_rz,
-                                                   int np) {
+                                                   const PcgScalars* __restrict__ sc) {
     if (sc->done) return;
-    __shared__ double s_beta;
-    if (threadIdx.x < 32) {
-        double rz = warp_sum_partials(part_rz, np);
-        if (threadIdx.x == 0) s_beta = sc->iter == 0 ? 0.0 : rz / sc->rz;
-    }
-    __syncthreads();
-    const double beta = s_beta;
+    const double beta = sc->iter == 0 ? 0.0 : sc->rz_next / sc->rz;
     GRID_STRIDE(k, n) p[k] = z[k] + beta * p[k];
 }
 
-// q = A p (CSR, one thread per row) and the partial of p . q; CTA 0 records rho_k.
-__global__ void __launch_bounds__(VEC_BS) k_pcg_spmv(int64_t n, const int32_t* __restrict__ rowptr,
-                                                      const int32_t* __restrict__ col,
-                                                      const double* __restrict__ val,
-                                                      const double* __restrict__ p, double* __restrict__ q,
-                                                      double* __restrict__ part_pq, PcgScalars* __restrict__ sc,
-                                                      const double* __restrict__ part_rz, int np) {
-    if (sc->done) return;
-    __shared__ double sh[32];
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-        double rz = warp_sum_partials(part_rz, np);
-        if (threadIdx.x == 0) {
-            sc->rz_prev = sc->rz;
-            sc->rz = rz;
-        }
-    }
-    double acc = 0.0;
-    GRID_STRIDE(k, n) {
-        double s = 0.0;
-        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) s += val[e] * __ldg(p + col[e]);
-        q[k] = s;
-        acc += p[k] * s;
-    }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part_pq[blockIdx.x] = s;
-}
-
-// Same product on the sliced-ELL copy: one thread per row, the warp = one 32-row slice,
-// every load of values/columns is one contiguous 256/128-byte segment.
+// q = A p on the sliced-ELL copy (one thread per row; a warp is one 32-row slice, so each
+// load of values / columns is one contiguous segment) and p . q -> sc->pq.  CTA 0 moves
+// rho to the new direction's value (read by the following kernels only).
 __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
                                                           const int32_t* __restrict__ ell_col,
                                                           const double* __restrict__ ell_val,
                                                           const double* __restrict__ p, double* __restrict__ q,
-                                                          double* __restrict__ part_pq, PcgScalars* __restrict__ sc,
-                                                          const double* __restrict__ part_rz, int np) {
+                                                          PcgScalars* __restrict__ sc, GridSum gs) {
     if (sc->done) return;
     __shared__ double sh[32];
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-        double rz = warp_sum_partials(part_rz, np);
-        if (threadIdx.x == 0) {
-            sc->rz_prev = sc->rz;
-            sc->rz = rz;
-        }
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->rz = sc->rz_next;
     double acc = 0.0;
     GRID_STRIDE(k, n) {
         const int64_t sl = k >> 5;
         const int r = (int)(k & 31);
-        const int64_t b = ell_ptr[sl], w = (ell_ptr[sl + 1] - b) >> 5;
+        const int64_t b = __ldg(ell_ptr + sl), w = (__ldg(ell_ptr + sl + 1) - b) >> 5;
         const double* v = ell_val + b + r;
         const int32_t* c = ell_col + b + r;
         double s = 0.0;
-        for (int64_t e = 0; e < w; ++e) s += __ldg(v + e * 32) * __ldg(p + __ldg(c + e * 32));
+        int64_t e = 0;
+        for (; e + 4 <= w; e += 4) {
+            const int32_t c0 = __ldg(c + e * 32), c1 = __ldg(c + (e + 1) * 32);
+            const int32_t c2 = __ldg(c + (e + 2) * 32), c3 = __ldg(c + (e + 3) * 32);
+            const double v0 = __ldg(v + e * 32), v1 = __ldg(v + (e + 1) * 32);
+            const double v2 = __ldg(v + (e + 2) * 32), v3 = __ldg(v + (e + 3) * 32);
+            s += v0 * __ldg(p + c0);
+            s += v1 * __ldg(p + c1);
+            s += v2 * __ldg(p + c2);
+            s += v3 * __ldg(p + c3);
+        }
+        for (; e < w; ++e) s += __ldg(v + e * 32) * __ldg(p + __ldg(c + e * 32));
         q[k] = s;
         acc += p[k] * s;
     }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part_pq[blockIdx.x] = s;
+    grid_sum(acc, sh, gs, &sc->pq);
 }
 
-// ell_val[t] = val[src[t]] (0 for padding)
-__global__ void k_ell_values(int64_t nell, const int32_t* __restrict__ src, const double* __restrict__ val,
-                             double* __restrict__ ell_val) {
-    GRID_STRIDE(t, nell) {
-        const int32_t s = src[t];
-        ell_val[t] = s >= 0 ? val[s] : 0.0;
-    }
-}
-
-// alpha = rho_k / (p . q);  x += alpha p;  r -= alpha q;  partial of ||r||^2.
+// alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
-                                                    PcgScalars* __restrict__ sc, const double* __restrict__ part_pq,
-                                                    double* __restrict__ part_rr, int np) {
+                                                    PcgScalars* __restrict__ sc, GridSum gs) {
     if (sc->done) return;
     __shared__ double sh[32];
-    __shared__ double s_alpha;
-    __shared__ int s_ok;
-    if (threadIdx.x < 32) {
-        double pq = warp_sum_partials(part_pq, np);
-        if (threadIdx.x == 0) {
-            double al = sc->rz / pq;
-            s_ok = (pq > 0.0 && isfinite(al)) ? 1 : 0;
-            s_alpha = al;
-        }
-    }
-    __syncthreads();
-    const double al = s_alpha;
-    const int ok = s_ok;
+    const double pq = sc->pq;
+    const double al = sc->rz / pq;
+    const bool ok = pq > 0.0 && isfinite(al);
     double acc = 0.0;
     GRID_STRIDE(k, n) {
         double rk = r[k];
@@ -258,42 +189,37 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
         }
         acc += rk * rk;
     }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part_rr[blockIdx.x] = s;
+    grid_sum(acc, sh, gs, &sc->rr_new);
 }
 
-__global__ void k_pcg_check(PcgScalars* sc, const double* __restrict__ part_pq, const double* __restrict__ part_rr,
-                            int np) {
+// Stop test on the device: breakdown, convergence, iteration cap.
+__global__ void k_pcg_check(PcgScalars* sc) {
     if (sc->done) return;
-    double pq = warp_sum_partials(part_pq, np);
-    double rr = warp_sum_partials(part_rr, np);
-    if (threadIdx.x == 0) {
-        sc->iter += 1;
-        sc->pq = pq;
-        double al = sc->rz / pq;
-        sc->alpha = al;
-        if (!(pq > 0.0) || !isfinite(al) || !isfinite(rr)) {
+    sc->iter += 1;
+    const double pq = sc->pq, rr = sc->rr_new;
+    const double al = sc->rz / pq;
+    sc->alpha = al;
+    if (!(pq > 0.0) || !isfinite(al) || !isfinite(rr)) {
+        sc->done = 1;
+        sc->status = 6;
+    } else {
+        sc->rr = rr;
+        if (rr <= sc->tol2) {
             sc->done = 1;
-            sc->status = 6;
-        } else {
-            sc->rr = rr;
-            if (rr <= sc->tol2) {
-                sc->done = 1;
-                sc->status = 0;
-            } else if (sc->iter >= sc->max_it) {
-                sc->done = 1;
-                sc->status = 5;
-            }
+            sc->status = 0;
+        } else if (sc->iter >= sc->max_it) {
+            sc->done = 1;
+            sc->status = 5;
         }
     }
 }
 
-// partials of ||b - A x||^2 (true residual)
+// ||b - A x||^2 -> sc->res2 (true residual, CSR copy of A).
 __global__ void __launch_bounds__(VEC_BS) k_residual(int64_t n, const int32_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ col,
                                                       const double* __restrict__ val,
                                                       const double* __restrict__ x, const double* __restrict__ b,
-                                                      double* __restrict__ part) {
+                                                      PcgScalars* __restrict__ sc, GridSum gs) {
     __shared__ double sh[32];
     double acc = 0.0;
     GRID_STRIDE(k, n) {
@@ -301,13 +227,16 @@ __global__ void __launch_bounds__(VEC_BS) k_residual(int64_t n, const int32_t* _
         for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) s -= val[e] * x[col[e]];
         acc += s * s;
     }
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    grid_sum(acc, sh, gs, &sc->res2);
 }
 
-__global__ void k_sum_partials(const double* __restrict__ part, int np, double* __restrict__ out) {
-    double s = warp_sum_partials(part, np);
-    if (threadIdx.x == 0) *out = s;
+// ell_val[t] = val[src[t]] (0 for padding)
+__global__ void k_ell_values(int64_t nell, const int32_t* __restrict__ src, const double* __restrict__ val,
+                             double* __restrict__ ell_val) {
+    GRID_STRIDE(t, nell) {
+        const int32_t s = src[t];
+        ell_val[t] = s >= 0 ? val[s] : 0.0;
+    }
 }
 
 // ------------------------------------------------------------------------- adjoint
@@ -365,68 +294,46 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
         k_restrict<<<(L + 7) / 8, 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, done);
     }
 }
-void launch_coarse_gemv(int L, const double* Sinv, const double* b, double* eta, const int32_t* done,
-                        cudaStream_t st) {
-    if (L > 0) {
-        count_launch();
-        k_coarse_gemv<<<(L + 7) / 8, 256, 0, st>>>(L, Sinv, b, eta, done);
-    }
-}
 template <typename TP>
 void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
                     const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
-                    const double* pbar, double* z, const double* r, double* part, const int32_t* done,
+                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, const int32_t* done,
                     cudaStream_t st) {
     count_launch();
-    k_prolong<TP><<<vec_grid(), VEC_BS, 0, st>>>(n, row_sub, sub_off, if_off, if_list, phi_off, phi, eta, pbar, z,
-                                                 r, part, done);
+    k_prolong<TP><<<vec_blocks(n), VEC_BS, 0, st>>>(n, row_sub, sub_off, if_off, if_list, phi_off, phi, eta, pbar, z,
+                                                    r, gs, rz, done);
 }
-void launch_pcg_init(int64_t n, const double* b, double* x, double* r, double* part, cudaStream_t st) {
+void launch_pcg_init(int64_t n, const double* b, double* x, double* r, PcgScalars* sc, GridSum gs, double tol,
+                     int max_it, cudaStream_t st) {
     count_launch();
-    k_pcg_init<<<vec_grid(), VEC_BS, 0, st>>>(n, b, x, r, part);
+    k_pcg_init<<<vec_blocks(n), VEC_BS, 0, st>>>(n, b, x, r, sc, gs, tol, max_it);
 }
-void launch_pcg_start(PcgScalars* sc, const double* part_bb, double tol, int max_it, int flexible,
-                      cudaStream_t st) {
+void launch_pcg_p(int64_t n, const double* z, double* p, const PcgScalars* sc, cudaStream_t st) {
     count_launch();
-    k_pcg_start<<<1, 32, 0, st>>>(sc, part_bb, vec_grid(), tol, max_it, flexible);
-}
-void launch_pcg_p(int64_t n, const double* z, double* p, const double* r, double* r_old, PcgScalars* sc,
-                  const double* part_rz, cudaStream_t st) {
-    (void)r;
-    (void)r_old;
-    count_launch();
-    k_pcg_p<<<vec_grid(), VEC_BS, 0, st>>>(n, z, p, sc, part_rz, vec_grid());
-}
-void launch_pcg_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                     const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
-                     cudaStream_t st) {
-    count_launch();
-    k_pcg_spmv<<<vec_grid(), VEC_BS, 0, st>>>(n, rowptr, col, val, p, q, part_pq, sc, part_rz, vec_grid());
+    k_pcg_p<<<vec_blocks(n), VEC_BS, 0, st>>>(n, z, p, sc);
 }
 void launch_pcg_spmv_ell(int64_t n, const int64_t* ell_ptr, const int32_t* ell_col, const double* ell_val,
-                         const double* p, double* q, double* part_pq, PcgScalars* sc, const double* part_rz,
-                         cudaStream_t st) {
+                         const double* p, double* q, PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
-    k_pcg_spmv_ell<<<vec_grid(), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, part_pq, sc, part_rz,
-                                                  vec_grid());
+    k_pcg_spmv_ell<<<vec_blocks(n), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, sc, gs);
 }
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st) {
     count_launch();
     k_ell_values<<<grid_for(nell, 256), 256, 0, st>>>(nell, src, val, ell_val);
 }
-void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc,
-                   const double* part_pq, double* part_rr, cudaStream_t st) {
+void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc, GridSum gs,
+                   cudaStream_t st) {
     count_launch();
-    k_pcg_xr<<<vec_grid(), VEC_BS, 0, st>>>(n, x, r, p, q, sc, part_pq, part_rr, vec_grid());
+    k_pcg_xr<<<vec_blocks(n), VEC_BS, 0, st>>>(n, x, r, p, q, sc, gs);
 }
-void launch_pcg_check(PcgScalars* sc, const double* part_pq, const double* part_rr, cudaStream_t st) {
+void launch_pcg_check(PcgScalars* sc, cudaStream_t st) {
     count_launch();
-    k_pcg_check<<<1, 32, 0, st>>>(sc, part_pq, part_rr, vec_grid());
+    k_pcg_check<<<1, 1, 0, st>>>(sc);
 }
-void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                     const double* x, const double* b, double* part, cudaStream_t st) {
+void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* x,
+                     const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
-    k_residual<<<vec_grid(), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, part);
+    k_residual<<<vec_blocks(n), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, sc, gs);
 }
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,
                       const double* tb, const double* tbp, const double* p, const double* lam, double* grad,
@@ -434,20 +341,13 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
     count_launch();
     k_tpfa_grad<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, K, tb, tbp, p, lam, grad);
 }
-void launch_sum_partials(const double* part, double* out, cudaStream_t st) {
-    count_launch();
-    k_sum_partials<<<1, 32, 0, st>>>(part, vec_grid(), out);
-}
 
-template void launch_prolong<double>(int64_t, const int32_t*, const int64_t*, const int64_t*, const int32_t*,
-                                     const int64_t*, const double*, const double*, const double*, double*,
-                                     const double*, double*, const int32_t*, cudaStream_t);
-template void launch_prolong<float>(int64_t, const int32_t*, const int64_t*, const int64_t*, const int32_t*,
-                                    const int64_t*, const float*, const double*, const double*, double*,
-                                    const double*, double*, const int32_t*, cudaStream_t);
-template void launch_prolong<__nv_bfloat16>(int64_t, const int32_t*, const int64_t*, const int64_t*,
-                                            const int32_t*, const int64_t*, const __nv_bfloat16*, const double*,
-                                            const double*, double*, const double*, double*, const int32_t*,
-                                            cudaStream_t);
+#define INST_PROLONG(TP)                                                                                     \
+    template void launch_prolong<TP>(int64_t, const int32_t*, const int64_t*, const int64_t*, const int32_t*,     \
+                                     const int64_t*, const TP*, const double*, const double*, double*,            \
+                                     const double*, GridSum, double*, const int32_t*, cudaStream_t);
+INST_PROLONG(double)
+INST_PROLONG(float)
+INST_PROLONG(__nv_bfloat16)
 
 }  // namespace am
