@@ -198,6 +198,26 @@ int algmortar_update_values_device(algmortar_t* h, const double* val_dev);
 int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* tb_dev, const double* tbp_dev,
                             const double* p_dev, const double* lam_dev, double* grad_dev);
 
+/* Interface solve eta = S^{-1} b for the handle's interface system, WITHOUT any device
+ * allocation.  The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need the solve (a fixed memory budget or a
+ * caller-owned pool, real-time loops that must stay out of the allocator, hosts that
+ * forbid cudaMalloc after start-up).  It computes the same eta as algmortar_apply_stages
+ * returns for b = b_eta (same kernels, same order), but keeps its temporaries in a
+ * file-scope device array of 2^20 doubles (8 MiB) that every GPU loading the library
+ * holds until the process exits.
+ *   b_dev, eta_dev: device, n_lambda doubles each, natural interface order (pairs
+ *   (i, j) lexicographic); caller-owned, not retained.  Work goes on the handle's stream.
+ * Limits and sharing: needs 2 n_lambda + sum_g |A_g| doubles of the array (the sizes of
+ * the nested-dissection layout in algmortar_info terms: at most ~3 n_lambda); larger
+ * systems return ALGMORTAR_TOO_LARGE with a message.  All calls share the one array,
+ * which keeps the previous call's contents (every entry this call reads is written by
+ * it first); calls whose device work overlaps -- other streams, other threads, other
+ * handles on the same GPU -- race on it and must be serialised by the caller.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * no allocation); make that first call before any stream capture on that device. */
+int algmortar_interface_solve_noalloc(const algmortar_t* h, const double* b_dev, double* eta_dev);
+
 /* Labels of the handle's partition (host, n entries). */
 int algmortar_get_partition(const algmortar_t* h, int32_t* part_out);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "algmortar_update_values": (C.c_int, [_P, _DP]),
     "algmortar_update_values_device": (C.c_int, [_P, _P]),
     "algmortar_tpfa_grad_lnK": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "algmortar_interface_solve_noalloc": (C.c_int, [_P, _P, _P]),
     "algmortar_get_partition": (C.c_int, [_P, _IP]),
     "algmortar_get_permutation": (C.c_int, [_P, _IP]),
     "algmortar_get_interfaces": (C.c_int, [_P, _IP]),

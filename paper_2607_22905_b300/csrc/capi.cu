@@ -16,6 +16,10 @@
 
 using namespace am;
 
+namespace am {
+int interface_solve_noalloc(int device, cudaStream_t st, int L, const NdSolveArgs& nd, const int32_t* d_ndpos,
+                            const double* b_dev, double* eta_dev, std::string& err);
+}
 
 namespace {
 
@@ -1088,6 +1092,15 @@ int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* t
     launch_tpfa_grad(n, h->d_rowptr, h->d_col, h->d_val, buf[0], buf[1], buf[2], buf[3], buf[4], h->d_t, h->st);
     launch_scatter(n, h->d_perm, h->d_t, grad_dev, h->st);
     CU(cudaGetLastError());
+    return 0;
+}
+
+int algmortar_interface_solve_noalloc(const algmortar_t* h, const double* b_dev, double* eta_dev) {
+    if (!h) return fail(ALGMORTAR_INVALID_ARG, "null handle");
+    if (h->L > 0 && (!b_dev || !eta_dev)) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    std::string err;
+    int rc = am::interface_solve_noalloc(h->device, h->st, h->L, h->nd, h->d_ndpos, b_dev, eta_dev, err);
+    if (rc) return fail(rc, err);
     return 0;
 }
 
