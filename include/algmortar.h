@@ -53,6 +53,10 @@ enum {
 /* Largest subdomain the batched local kernels accept (rows). */
 #define ALGMORTAR_MAX_PART 16384
 
+/* Right-hand sides one batched PCG iteration carries (algmortar_pcg_solve_multi splits
+ * larger requests into batches of this many columns). */
+#define ALGMORTAR_MAX_BATCH 32
+
 /* Precision of the local factors L_i, their triangular solves and the MBF panels.
  * The outer PCG recurrences, dot products, SpMV, interface restriction, the coarse
  * interface solve and the true-residual check are FP64 in every mode. */
@@ -171,8 +175,14 @@ int algmortar_pcg_solve_host(algmortar_t* h, const double* b_host, double* x_hos
                              algmortar_stats* st);
 
 /* nrhs independent systems A X[:, j] = B[:, j] (column-major, leading dimension ld >= n,
- * device).  Each column runs its own CG scalars and stops on its own tolerance; st (may
- * be NULL) points to nrhs stats. */
+ * device), solved as batches of up to ALGMORTAR_MAX_BATCH columns: every kernel of a
+ * PCG iteration (SpMV, vector updates, the stages of Algorithm 2) covers all columns of
+ * the batch in one launch, so the local factors and MBF panels stream once per
+ * iteration for the whole batch.  Each column runs its own CG scalars and stops on its
+ * own tolerance (stopped columns are skipped); its iterates are bit-identical to
+ * algmortar_pcg_solve on that column.  st (may be NULL) points to nrhs stats.  The
+ * batch workspace (8 n + 2 L doubles per column) is allocated on first use and kept.
+ * Returns OK, NO_CONVERGENCE or BREAKDOWN (the worst column). */
 int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev, int32_t nrhs,
                               int64_t ld, double tol, algmortar_stats* st);
 

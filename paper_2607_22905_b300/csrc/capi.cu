@@ -87,6 +87,22 @@ struct NumWs {
     int64_t* d_czerooff = nullptr;
 };
 
+// PCG / apply vectors of k right-hand sides, column-major: cell vectors with leading
+// dimension n, interface vectors with leading dimension max(L, 1), and per column one PCG
+// state, one grid-sum ticket and its block partials.  The captured iteration graph
+// belongs to the batch (its launches carry the column count).
+struct Vecs {
+    int k = 0, cap = 0;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *pbar = nullptr;
+    double *b = nullptr, *t = nullptr;
+    double *beta = nullptr, *eta = nullptr, *P = nullptr;
+    PcgScalars* sc = nullptr;
+    GridSum gs{};
+    cudaGraphExec_t graph = nullptr;
+    int graph_k = 0;                   // column count the graph was captured with
+    int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
+};
+
 struct algmortar_handle {
     int device = 0;
     cudaStream_t st = nullptr;
@@ -119,14 +135,9 @@ struct algmortar_handle {
     int32_t* nd_grows = nullptr;       // rows of each interface group (symmetrisation)
     int32_t* d_ndpos = nullptr;        // interface id -> ND position
     int32_t* d_ifpos = nullptr;        // if_list entries as ND positions (prolongation)
-    double* d_P = nullptr;             // sum_g a_g partial products
-    double* d_nat = nullptr;           // natural-order staging (stage outputs)
-    // workspace
-    double *d_x = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_pbar = nullptr;
-    double *d_beta = nullptr, *d_eta = nullptr, *d_b = nullptr, *d_t = nullptr;
-    GridSum gs{};                      // partials + ticket of the deterministic grid sums
+    // workspace: single right-hand side (v1) and the batched solves' columns (vk)
+    Vecs v1, vk;
     double* d_scalar = nullptr;
-    PcgScalars* d_pcg = nullptr;
     int* d_kerr = nullptr;             // kernel error word (stuck bulk copy)
     NumWs* ws = nullptr;               // persistent numeric-setup buffers
     int32_t* d_psrc = nullptr;         // permuted CSR value t = original value psrc[t]
@@ -138,8 +149,6 @@ struct algmortar_handle {
     double* d_ell_val = nullptr;
     int64_t n_ell = 0;
     double* d_vtmp = nullptr;          // staging for value updates (original CSR order)
-    cudaGraphExec_t graph = nullptr;
-    int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
     algmortar_info info{};
 
     template <typename T>
@@ -158,7 +167,8 @@ struct algmortar_handle {
             }
     }
     ~algmortar_handle() {
-        if (graph) cudaGraphExecDestroy(graph);
+        if (v1.graph) cudaGraphExecDestroy(v1.graph);
+        if (vk.graph) cudaGraphExecDestroy(vk.graph);
         for (void* p : allocs)
             if (p) cudaFree(p);
         if (own_st) cudaStreamDestroy(own_st);
@@ -396,9 +406,6 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             for (size_t t = 0; t < ifpos.size(); ++t) ifpos[t] = P.nd_pos[P.if_list[t]];
             TRY(upload(h, h->d_ifpos, ifpos));
         }
-        h->d_P = h->alloc<double>((size_t)std::max<int64_t>(P.nd_aoff[G], 1));
-        h->d_nat = h->alloc<double>((size_t)L);
-        if (!h->d_P || !h->d_nat) return fail(ALGMORTAR_OOM, "interface vectors");
         NdSolveArgs& a = h->nd;
         a.G = G;
         a.nsep = nsep;
@@ -545,10 +552,10 @@ int numeric_setup(algmortar_t* h) {
         launch_dense_to_tiles(W.ntiles_items, W.Sd, L, W.d_isrc, W.d_irows, W.d_ibase, W.d_titem, W.d_tI, W.d_tJ,
                               W.gwork, st);
         CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
-        for (int it = 0; it < W.nitems; ++it) {
-            const int64_t r0 = W.item_row0[it], b0 = W.item_base[it];
-            launch_rl_cholesky<double>((int)W.item_hi[it].size(), W.d_ilo + r0, W.d_ifwd + r0, W.item_hi[it].data(),
-                                       W.gwork + b0 * TILE2, W.gdinv + r0 * TILE2, W.d_err, st);
+        {
+            std::vector<int32_t> Th(W.nitems);
+            for (int it = 0; it < W.nitems; ++it) Th[it] = (int32_t)W.item_hi[it].size();
+            launch_dense_cholesky(W.nitems, Th, W.d_int, W.d_ibase, W.d_irow0, W.gwork, W.gdinv, W.d_err, st);
         }
         CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
@@ -584,7 +591,8 @@ int numeric_setup(algmortar_t* h) {
             const int64_t ct = (int64_t)W.cT * (W.cT + 1) / 2;
             launch_nd_schur_tiles(ct, L, nsep, sep0, W.Sd, h->nd.sg, h->nd.sidx, h->nd.aoff, W.d_doff, W.D, W.cwork, st);
             CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
-            launch_rl_cholesky<double>(W.cT, W.d_clo, W.d_cfwd, W.c_hi.data(), W.cwork, W.cdinv, W.d_err, st);
+            launch_dense_cholesky(1, std::vector<int32_t>{W.cT}, W.d_cnt, W.d_czero, W.d_czero, W.cwork, W.cdinv,
+                                  W.d_err, st);
             CU(cudaGetLastError());
             TRY(read_err_flag(h, W.d_err, "interface (separator)"));
             Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};
@@ -639,10 +647,21 @@ int numeric_dispatch(algmortar_t* h) {
     }
 }
 
-// Stages of Algorithm 2 on internal-order vectors.
+// Column strides of a batch; `pcg` makes the kernels skip columns whose PCG has stopped.
+ColStrides col_strides(const algmortar_t* h, const Vecs& v, bool pcg) {
+    ColStrides cs{};
+    cs.v = h->n;
+    cs.l = h->L > 0 ? h->L : 1;
+    cs.done = pcg ? &v.sc->done : nullptr;
+    cs.done_stride = (int)(sizeof(PcgScalars) / sizeof(int32_t));
+    cs.sc_stride = (int)(sizeof(PcgScalars) / sizeof(double));
+    return cs;
+}
+
+// Stages of Algorithm 2 on internal-order vectors, all columns of the batch per launch.
 // Local particular solutions pbar_i = A_i^{-1} r_i for all subdomains (one launch).
 template <typename TS, typename TA>
-int stage_local(algmortar_t* h, const double* r, const int32_t* done) {
+int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs) {
     SolveArgs a{};
     a.pf = h->pf;
     a.fwdS = h->d_fwdS;
@@ -653,132 +672,201 @@ int stage_local(algmortar_t* h, const double* r, const int32_t* done) {
     a.job_in = h->d_job_off;
     a.job_out = h->d_job_off;
     a.in = r;
-    a.out = h->d_pbar;
+    a.out = v.pbar;
     a.alpha = 1.0;
-    a.done = done;
+    a.done = cs.done;
+    a.done_stride = cs.done_stride;
+    a.ldin = a.ldout = h->n;
     a.err = h->d_kerr;
-    CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st)));
+    CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st, v.k)));
     return 0;
 }
 
 // Interface right-hand side and interface solve: b_eta from pbar, eta = S^{-1} b_eta.
-void stage_restrict(algmortar_t* h, const int32_t* done) {
-    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, h->d_pbar, h->d_beta, h->d_ndpos, done, h->st);
+void stage_restrict(algmortar_t* h, Vecs& v, const ColStrides& cs) {
+    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, v.pbar, v.beta, h->d_ndpos, cs, v.k, h->st);
 }
-void stage_coarse(algmortar_t* h, const int32_t* done) {
-    if (h->L > 0) launch_nd_solve(h->nd, h->d_beta, h->d_eta, h->d_P, done, h->st);
+void stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
+    if (h->L > 0) launch_nd_solve(h->nd, v.beta, v.eta, v.P, cs, v.k, h->st);
 }
 
-// z = pbar + Phi eta, and r . z into *rz when rz is given.
+// z = pbar + Phi eta, and r . z into rz[column] when rz is given.
 template <typename TS>
-void stage_prolong(algmortar_t* h, const double* r, double* z, const int32_t* done, double* rz) {
+void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, double* rz) {
     launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list,
-                       h->d_phi_off, (const TS*)h->d_phi, h->d_eta, h->d_pbar, z, r, h->gs, rz, done, h->st);
+                       h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, z, r, v.gs, rz, cs, v.k, h->st);
 }
 
 template <typename TS, typename TA>
-int apply_t(algmortar_t* h, const double* r, double* z, const int32_t* done, double* rz) {
-    TRY((stage_local<TS, TA>(h, r, done)));
-    stage_restrict(h, done);
-    stage_coarse(h, done);
-    stage_prolong<TS>(h, r, z, done, rz);
+int apply_t(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
+    const ColStrides cs = col_strides(h, v, pcg);
+    TRY((stage_local<TS, TA>(h, v, r, cs)));
+    stage_restrict(h, v, cs);
+    stage_coarse(h, v, cs);
+    stage_prolong<TS>(h, v, r, z, cs, pcg ? &v.sc->rz_next : nullptr);
     CU(cudaGetLastError());
     return 0;
 }
 
-int apply_internal(algmortar_t* h, const double* r, double* z, const int32_t* done, double* rz) {
+// z = M^{-1} r for the batch's columns; with `pcg`, stopped columns are skipped and
+// r . z goes to each column's rz_next.
+int apply_internal(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
     switch (h->opts.precision) {
-        case ALGMORTAR_FP64: return apply_t<double, double>(h, r, z, done, rz);
-        case ALGMORTAR_FP32: return apply_t<float, float>(h, r, z, done, rz);
-        default: return apply_t<__nv_bfloat16, float>(h, r, z, done, rz);
+        case ALGMORTAR_FP64: return apply_t<double, double>(h, v, r, z, pcg);
+        case ALGMORTAR_FP32: return apply_t<float, float>(h, v, r, z, pcg);
+        default: return apply_t<__nv_bfloat16, float>(h, v, r, z, pcg);
     }
 }
 
-int pcg_iteration(algmortar_t* h) {
+int pcg_iteration(algmortar_t* h, Vecs& v) {
     cudaStream_t st = h->st;
-    const int32_t* done = &h->d_pcg->done;
-    launch_pcg_p(h->n, h->d_z, h->d_p, h->d_pcg, st);
-    launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_pcg, h->gs, st);
-    launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->gs, st);
-    launch_pcg_check(h->d_pcg, st);
-    return apply_internal(h, h->d_r, h->d_z, done, &h->d_pcg->rz_next);
+    const int64_t n = h->n;
+    launch_pcg_p(n, v.k, n, v.z, v.p, v.sc, st);
+    launch_pcg_spmv_ell(n, v.k, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
+    launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.sc, v.gs, st);
+    launch_pcg_check(v.sc, v.k, st);
+    return apply_internal(h, v, v.r, v.z, true);
 }
 
-int ensure_graph(algmortar_t* h) {
-    if (h->graph) return 0;
+int ensure_graph(algmortar_t* h, Vecs& v) {
+    if (v.graph && v.graph_k == v.k) return 0;
+    if (v.graph) {
+        cudaGraphExecDestroy(v.graph);
+        v.graph = nullptr;
+    }
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
     const int64_t c0 = launch_count();
-    int rc = pcg_iteration(h);
+    int rc = pcg_iteration(h, v);
     cudaError_t e = cudaStreamEndCapture(h->st, &g);
-    h->graph_kernels = launch_count() - c0;
-    add_launches(-h->graph_kernels);   // captured, not executed
+    v.graph_kernels = launch_count() - c0;
+    add_launches(-v.graph_kernels);   // captured, not executed
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     if (e != cudaSuccess) return fail(ALGMORTAR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(&v.graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->graph = nullptr;
+        v.graph = nullptr;
         return fail(ALGMORTAR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
+    v.graph_k = v.k;
     return 0;
 }
 
-// PCG in the internal ordering on h->d_b -> h->d_x.
-int pcg_internal(algmortar_t* h, double tol, algmortar_stats* stt) {
+// Workspace of a batch with room for `cap` columns (first use, or growth).
+int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
+    if (v.cap >= cap) return 0;
+    void* old[] = {v.x, v.r, v.z, v.p, v.q, v.pbar, v.b, v.t, v.beta, v.eta, v.P, v.sc, v.gs.part, v.gs.ticket};
+    for (void* p : old)
+        if (p) h->release(p);
+    if (v.graph) {
+        cudaGraphExecDestroy(v.graph);
+        v.graph = nullptr;
+    }
+    const size_t n = (size_t)h->n * cap;
+    const size_t l = (size_t)std::max(h->L, 1) * cap;
+    const int64_t np = h->P.nd_aoff.empty() ? 1 : std::max<int64_t>(h->P.nd_aoff.back(), 1);
+    const size_t nb = (size_t)vec_blocks(h->n) * cap;
+    v.x = h->alloc<double>(n);
+    v.r = h->alloc<double>(n);
+    v.z = h->alloc<double>(n);
+    v.p = h->alloc<double>(n);
+    v.q = h->alloc<double>(n);
+    v.pbar = h->alloc<double>(n);
+    v.b = h->alloc<double>(n);
+    v.t = h->alloc<double>(n);
+    v.beta = h->alloc<double>(l);
+    v.eta = h->alloc<double>(l);
+    v.P = h->alloc<double>((size_t)np * cap);
+    v.sc = h->alloc<PcgScalars>(cap);
+    v.gs.part = h->alloc<double>(nb);
+    v.gs.ticket = h->alloc<unsigned int>(cap);
+    if (!v.x || !v.r || !v.z || !v.p || !v.q || !v.pbar || !v.b || !v.t || !v.beta || !v.eta || !v.P || !v.sc ||
+        !v.gs.part || !v.gs.ticket) {
+        v.cap = 0;
+        return fail(ALGMORTAR_OOM, "vector workspace");
+    }
+    CU(cudaMemsetAsync(v.p, 0, n * sizeof(double), h->st));
+    CU(cudaMemsetAsync(v.sc, 0, cap * sizeof(PcgScalars), h->st));
+    CU(cudaMemsetAsync(v.gs.ticket, 0, cap * sizeof(unsigned int), h->st));
+    v.cap = cap;
+    v.k = cap;
+    return 0;
+}
+
+// PCG in the internal ordering on v.b -> v.x for the batch's k columns; stats[j] per column.
+// Returns the worst column status.
+int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     cudaStream_t st = h->st;
     double t0 = now_ms();
     if (!(tol > 0.0)) return fail(ALGMORTAR_INVALID_ARG, "tol must be positive");
-    if (h->opts.use_graph) TRY(ensure_graph(h));
-    launch_pcg_init(h->n, h->d_b, h->d_x, h->d_r, h->d_pcg, h->gs, tol, h->opts.max_it, st);
-    TRY(apply_internal(h, h->d_r, h->d_z, &h->d_pcg->done, &h->d_pcg->rz_next));
-    PcgScalars hs{};
-    int restarts = 0;
+    const int k = v.k;
+    const int64_t n = h->n;
+    if (h->opts.use_graph) TRY(ensure_graph(h, v));
+    launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, st);
+    TRY(apply_internal(h, v, v.r, v.z, true));
+    std::vector<PcgScalars> hs(k);
+    std::vector<int> restarts(k, 0);
+    std::vector<double> true_rel(k, 0.0);
+    std::vector<char> fin(k, 0);
     const int every = h->opts.check_every > 0 ? h->opts.check_every : 1;
-    double true_rel = 0.0;
+    static const int zero = 0;
     for (;;) {
         for (int c = 0; c < every; ++c) {
-            if (h->graph) {
-                CU(cudaGraphLaunch(h->graph, st));
-                add_launches(h->graph_kernels);
+            if (v.graph) {
+                CU(cudaGraphLaunch(v.graph, st));
+                add_launches(v.graph_kernels);
             } else {
-                TRY(pcg_iteration(h));
+                TRY(pcg_iteration(h, v));
             }
         }
-        CU(cudaMemcpyAsync(&hs, h->d_pcg, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(hs.data(), v.sc, k * sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        if (!hs.done) continue;
-        launch_residual(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_x, h->d_b, h->d_pcg, h->gs, st);
-        double res2 = 0.0;
-        CU(cudaMemcpyAsync(&res2, &h->d_pcg->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        bool all = true;
+        for (int j = 0; j < k; ++j) all = all && hs[j].done;
+        if (!all) continue;
+        launch_residual(n, k, n, h->d_rowptr, h->d_col, h->d_val, v.x, v.b, v.sc, v.gs, st);
+        CU(cudaMemcpyAsync(hs.data(), v.sc, k * sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        true_rel = hs.bb > 0 ? std::sqrt(res2 / hs.bb) : 0.0;
-        if (hs.status == 0 && hs.bb > 0 && !(true_rel <= tol) && restarts < 8 && hs.iter < hs.max_it) {
-            // recurrence converged but the true residual does not confirm it: continue
-            ++restarts;
-            int zero = 0;
-            CU(cudaMemcpyAsync(&h->d_pcg->done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-            CU(cudaStreamSynchronize(st));
-            continue;
+        bool again = false;
+        for (int j = 0; j < k; ++j) {
+            if (fin[j]) continue;
+            true_rel[j] = hs[j].bb > 0 ? std::sqrt(hs[j].res2 / hs[j].bb) : 0.0;
+            if (hs[j].status == 0 && hs[j].bb > 0 && !(true_rel[j] <= tol) && restarts[j] < 8 &&
+                hs[j].iter < hs[j].max_it) {
+                // recurrence converged but the true residual does not confirm it: continue
+                ++restarts[j];
+                CU(cudaMemcpyAsync(&v.sc[j].done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+                again = true;
+            } else {
+                fin[j] = 1;
+            }
         }
-        break;
+        if (!again) break;
+        CU(cudaStreamSynchronize(st));
     }
-    int status = hs.status == 0 ? (true_rel <= tol || hs.bb == 0 ? ALGMORTAR_OK : ALGMORTAR_NO_CONVERGENCE)
-                                : (hs.status == 5 ? ALGMORTAR_NO_CONVERGENCE : ALGMORTAR_BREAKDOWN);
-    if (stt) {
-        stt->status = status;
-        stt->iterations = hs.iter;
-        stt->rel_residual = true_rel;
-        stt->recursive_residual = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
-        stt->solve_ms = now_ms() - t0;
-        stt->host_ms = 0.0;
+    int worst = ALGMORTAR_OK;
+    for (int j = 0; j < k; ++j) {
+        const PcgScalars& s = hs[j];
+        int status = s.status == 0 ? (true_rel[j] <= tol || s.bb == 0 ? ALGMORTAR_OK : ALGMORTAR_NO_CONVERGENCE)
+                                   : (s.status == 5 ? ALGMORTAR_NO_CONVERGENCE : ALGMORTAR_BREAKDOWN);
+        if (stt) {
+            stt[j].status = status;
+            stt[j].iterations = s.iter;
+            stt[j].rel_residual = true_rel[j];
+            stt[j].recursive_residual = s.bb > 0 ? std::sqrt(s.rr / s.bb) : 0.0;
+            stt[j].solve_ms = now_ms() - t0;
+            stt[j].host_ms = 0.0;
+        }
+        if (status == ALGMORTAR_BREAKDOWN || (status == ALGMORTAR_NO_CONVERGENCE && worst == ALGMORTAR_OK))
+            worst = status;
     }
-    if (status == ALGMORTAR_NO_CONVERGENCE) g_err = "PCG reached max_it or the true residual did not confirm";
-    if (status == ALGMORTAR_BREAKDOWN) g_err = "PCG breakdown: p^T A p <= 0 or non-finite scalar";
-    return status;
+    if (worst == ALGMORTAR_NO_CONVERGENCE) g_err = "PCG reached max_it or the true residual did not confirm";
+    if (worst == ALGMORTAR_BREAKDOWN) g_err = "PCG breakdown: p^T A p <= 0 or non-finite scalar";
+    return worst;
 }
 
 int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, const algmortar_opts* opts_in,
@@ -822,6 +910,11 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     };
     if (cudaSetDevice(o.device) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "cudaSetDevice failed"));
     h->device = o.device;
+    {
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
+        set_vec_sms(sms);
+    }
     h->st = (cudaStream_t)o.stream;
     if (!h->st) {
         // a blocking stream: ordered with the legacy default stream both ways, and
@@ -889,33 +982,14 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     launch_ell_values(h->n_ell, h->d_ell_src, h->d_vtmp, h->d_ell_val, h->st);
     h->pf = Profile{h->d_rows, h->d_ntiles, d_row0, d_base, d_lo, d_hi, d_fwd, d_bwd};
     const int64_t n = h->n;
-    const int np = vec_blocks(P.n);
     h->d_dloc = h->alloc<double>(n);
     h->d_sc = h->alloc<double>(n);
-    h->d_x = h->alloc<double>(n);
-    h->d_r = h->alloc<double>(n);
-    h->d_z = h->alloc<double>(n);
-    h->d_p = h->alloc<double>(n);
-    h->d_q = h->alloc<double>(n);
-    h->d_pbar = h->alloc<double>(n);
-    h->d_b = h->alloc<double>(n);
-    h->d_t = h->alloc<double>(n);
-    h->d_beta = h->alloc<double>(h->L);
-    h->d_eta = h->alloc<double>(h->L);
-    h->gs.part = h->alloc<double>(np);
-    h->gs.ticket = h->alloc<unsigned int>(1);
     h->d_scalar = h->alloc<double>(4);
-    h->d_pcg = h->alloc<PcgScalars>(1);
     h->d_kerr = h->alloc<int>(1);
-    if (!h->d_dloc || !h->d_sc || !h->d_x || !h->d_r || !h->d_z || !h->d_p || !h->d_q || !h->d_pbar || !h->d_b ||
-        !h->d_t || !h->d_beta || !h->d_eta || !h->gs.part || !h->gs.ticket ||
-        !h->d_scalar || !h->d_pcg || !h->d_kerr)
-        return bail(fail(ALGMORTAR_OOM, "workspace"));
-    if (cudaMemsetAsync(h->d_p, 0, n * sizeof(double), h->st) != cudaSuccess ||
-        cudaMemsetAsync(h->d_pcg, 0, sizeof(PcgScalars), h->st) != cudaSuccess ||
-        cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->st) != cudaSuccess ||
-        cudaMemsetAsync(h->gs.ticket, 0, sizeof(unsigned int), h->st) != cudaSuccess)
-        return bail(fail(ALGMORTAR_CUDA, "memset"));
+    if (!h->d_dloc || !h->d_sc || !h->d_scalar || !h->d_kerr) return bail(fail(ALGMORTAR_OOM, "workspace"));
+    rc = alloc_vecs(h, h->v1, 1);
+    if (rc) return bail(rc);
+    if (cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->st) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "memset"));
     double t_up = now_ms();
     rc = numeric_dispatch(h);
     if (rc) return bail(rc);
@@ -994,9 +1068,10 @@ int algmortar_setup_with_parts(const algmortar_csr* A, const int32_t* part, int3
 int algmortar_apply(algmortar_t* h, const double* r_dev, double* z_dev) {
     if (!h || !r_dev || !z_dev) return fail(ALGMORTAR_INVALID_ARG, "null argument");
     CU(cudaSetDevice(h->device));
-    launch_gather(h->n, h->d_perm, r_dev, h->d_t, h->st);
-    TRY(apply_internal(h, h->d_t, h->d_z, nullptr, nullptr));
-    launch_scatter(h->n, h->d_perm, h->d_z, z_dev, h->st);
+    Vecs& v = h->v1;
+    launch_gather(h->n, h->d_perm, r_dev, v.t, h->st);
+    TRY(apply_internal(h, v, v.t, v.z, false));
+    launch_scatter(h->n, h->d_perm, v.z, z_dev, h->st);
     CU(cudaGetLastError());
     return 0;
 }
@@ -1006,25 +1081,27 @@ int algmortar_apply_stages(algmortar_t* h, const double* r_dev, double* pbar_dev
     if (!h || !r_dev || !pbar_dev || !z_dev || (h->L > 0 && (!beta_dev || !eta_dev)))
         return fail(ALGMORTAR_INVALID_ARG, "null argument");
     CU(cudaSetDevice(h->device));
-    launch_gather(h->n, h->d_perm, r_dev, h->d_t, h->st);
-    TRY(apply_internal(h, h->d_t, h->d_z, nullptr, nullptr));
-    CU(cudaMemcpyAsync(pbar_dev, h->d_pbar, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    Vecs& v = h->v1;
+    launch_gather(h->n, h->d_perm, r_dev, v.t, h->st);
+    TRY(apply_internal(h, v, v.t, v.z, false));
+    CU(cudaMemcpyAsync(pbar_dev, v.pbar, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     if (h->L > 0) {
         // ND order inside the handle -> natural interface order
-        launch_gather(h->L, h->d_ndpos, h->d_beta, beta_dev, h->st);
-        launch_gather(h->L, h->d_ndpos, h->d_eta, eta_dev, h->st);
+        launch_gather(h->L, h->d_ndpos, v.beta, beta_dev, h->st);
+        launch_gather(h->L, h->d_ndpos, v.eta, eta_dev, h->st);
     }
-    CU(cudaMemcpyAsync(z_dev, h->d_z, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    CU(cudaMemcpyAsync(z_dev, v.z, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     return 0;
 }
 
 int algmortar_pcg_solve(algmortar_t* h, const double* b_dev, double* x_dev, double tol, algmortar_stats* st) {
     if (!h || !b_dev || !x_dev) return fail(ALGMORTAR_INVALID_ARG, "null argument");
     CU(cudaSetDevice(h->device));
-    launch_gather(h->n, h->d_perm, b_dev, h->d_b, h->st);
-    int rc = pcg_internal(h, tol, st);
+    Vecs& v = h->v1;
+    launch_gather(h->n, h->d_perm, b_dev, v.b, h->st);
+    int rc = pcg_internal(h, v, tol, st);
     if (rc != ALGMORTAR_OK && rc != ALGMORTAR_NO_CONVERGENCE && rc != ALGMORTAR_BREAKDOWN) return rc;
-    launch_scatter(h->n, h->d_perm, h->d_x, x_dev, h->st);
+    launch_scatter(h->n, h->d_perm, v.x, x_dev, h->st);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(h->st));
     return rc;
@@ -1035,12 +1112,13 @@ int algmortar_pcg_solve_host(algmortar_t* h, const double* b_host, double* x_hos
     if (!h || !b_host || !x_host) return fail(ALGMORTAR_INVALID_ARG, "null argument");
     CU(cudaSetDevice(h->device));
     double t0 = now_ms();
-    CU(cudaMemcpyAsync(h->d_t, b_host, h->n * sizeof(double), cudaMemcpyHostToDevice, h->st));
-    launch_gather(h->n, h->d_perm, h->d_t, h->d_b, h->st);
-    int rc = pcg_internal(h, tol, st);
+    Vecs& v = h->v1;
+    CU(cudaMemcpyAsync(v.t, b_host, h->n * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    launch_gather(h->n, h->d_perm, v.t, v.b, h->st);
+    int rc = pcg_internal(h, v, tol, st);
     if (rc != ALGMORTAR_OK && rc != ALGMORTAR_NO_CONVERGENCE && rc != ALGMORTAR_BREAKDOWN) return rc;
-    launch_scatter(h->n, h->d_perm, h->d_x, h->d_t, h->st);
-    CU(cudaMemcpyAsync(x_host, h->d_t, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    launch_scatter(h->n, h->d_perm, v.x, v.t, h->st);
+    CU(cudaMemcpyAsync(x_host, v.t, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     CU(cudaStreamSynchronize(h->st));
     if (st) st->solve_ms = now_ms() - t0;
     return rc;
@@ -1049,12 +1127,23 @@ int algmortar_pcg_solve_host(algmortar_t* h, const double* b_host, double* x_hos
 int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev, int32_t nrhs, int64_t ld,
                               double tol, algmortar_stats* st) {
     if (!h || !B_dev || !X_dev || nrhs <= 0 || ld < h->n) return fail(ALGMORTAR_INVALID_ARG, "bad argument");
-    int worst = 0;
-    for (int j = 0; j < nrhs; ++j) {
-        int rc = algmortar_pcg_solve(h, B_dev + j * ld, X_dev + j * ld, tol, st ? st + j : nullptr);
+    CU(cudaSetDevice(h->device));
+    // batches of up to ALGMORTAR_MAX_BATCH columns: every launch of the iteration covers
+    // all columns of the batch (gridDim.y), each column with its own PCG state
+    const int kmax = nrhs < ALGMORTAR_MAX_BATCH ? nrhs : ALGMORTAR_MAX_BATCH;
+    TRY(alloc_vecs(h, h->vk, kmax));
+    Vecs& v = h->vk;
+    int worst = ALGMORTAR_OK;
+    for (int j0 = 0; j0 < nrhs; j0 += kmax) {
+        v.k = nrhs - j0 < kmax ? nrhs - j0 : kmax;
+        launch_gather_cols(h->n, v.k, h->d_perm, B_dev + j0 * ld, ld, v.b, h->n, h->st);
+        int rc = pcg_internal(h, v, tol, st ? st + j0 : nullptr);
         if (rc != ALGMORTAR_OK && rc != ALGMORTAR_NO_CONVERGENCE && rc != ALGMORTAR_BREAKDOWN) return rc;
-        if (rc > worst) worst = rc;
+        launch_scatter_cols(h->n, v.k, h->d_perm, v.x, h->n, X_dev + j0 * ld, ld, h->st);
+        CU(cudaGetLastError());
+        if (rc == ALGMORTAR_BREAKDOWN || (rc == ALGMORTAR_NO_CONVERGENCE && worst == ALGMORTAR_OK)) worst = rc;
     }
+    CU(cudaStreamSynchronize(h->st));
     return worst;
 }
 
@@ -1086,11 +1175,12 @@ int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* t
     CU(cudaSetDevice(h->device));
     const int64_t n = h->n;
     // internal ordering: gather the per-cell inputs, run the row gather, scatter back
-    double* buf[5] = {h->d_x, h->d_r, h->d_z, h->d_p, h->d_q};
+    Vecs& v = h->v1;
+    double* buf[5] = {v.x, v.r, v.z, v.p, v.q};
     const double* src[5] = {K_dev, tb_dev, tbp_dev, p_dev, lam_dev};
     for (int i = 0; i < 5; ++i) launch_gather(n, h->d_perm, src[i], buf[i], h->st);
-    launch_tpfa_grad(n, h->d_rowptr, h->d_col, h->d_val, buf[0], buf[1], buf[2], buf[3], buf[4], h->d_t, h->st);
-    launch_scatter(n, h->d_perm, h->d_t, grad_dev, h->st);
+    launch_tpfa_grad(n, h->d_rowptr, h->d_col, h->d_val, buf[0], buf[1], buf[2], buf[3], buf[4], v.t, h->st);
+    launch_scatter(n, h->d_perm, v.t, grad_dev, h->st);
     CU(cudaGetLastError());
     return 0;
 }
@@ -1126,8 +1216,10 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     if (!h || !ms_out || reps <= 0) return fail(ALGMORTAR_INVALID_ARG, "bad argument");
     CU(cudaSetDevice(h->device));
     cudaStream_t st = h->st;
+    Vecs& v = h->v1;
+    const int64_t n = h->n;
     PcgScalars saved;
-    CU(cudaMemcpyAsync(&saved, h->d_pcg, sizeof(saved), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&saved, v.sc, sizeof(saved), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     // a live scalar state: not done, beta/alpha finite, so no kernel exits early
     PcgScalars live = saved;
@@ -1136,41 +1228,44 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     live.max_it = 1 << 30;
     live.rz = saved.rz != 0.0 ? saved.rz : 1.0;
     live.tol2 = 0.0;
+    const ColStrides cs = col_strides(h, v, false);
+    double* rz = &v.sc->rz_next;
+    if (h->opts.use_graph) TRY(ensure_graph(h, v));
     cudaEvent_t ev[8];
     for (auto& e : ev) CU(cudaEventCreate(&e));
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int it = 0; it <= reps; ++it) {
-        CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(v.sc, &live, sizeof(live), cudaMemcpyHostToDevice, st));
         cudaEventRecord(ev[0], st);
-        launch_pcg_spmv_ell(h->n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, h->d_p, h->d_q, h->d_pcg, h->gs, st);
+        launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
         cudaEventRecord(ev[1], st);
-        launch_pcg_p(h->n, h->d_z, h->d_p, h->d_pcg, st);
-        launch_pcg_xr(h->n, h->d_x, h->d_r, h->d_p, h->d_q, h->d_pcg, h->gs, st);
+        launch_pcg_p(n, 1, n, v.z, v.p, v.sc, st);
+        launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.sc, v.gs, st);
         cudaEventRecord(ev[2], st);
         // stages of Algorithm 2 (same launches as apply_internal, timed one by one)
         switch (h->opts.precision) {
-            case ALGMORTAR_FP64: TRY((stage_local<double, double>(h, h->d_r, nullptr))); break;
-            case ALGMORTAR_FP32: TRY((stage_local<float, float>(h, h->d_r, nullptr))); break;
-            default: TRY((stage_local<__nv_bfloat16, float>(h, h->d_r, nullptr))); break;
+            case ALGMORTAR_FP64: TRY((stage_local<double, double>(h, v, v.r, cs))); break;
+            case ALGMORTAR_FP32: TRY((stage_local<float, float>(h, v, v.r, cs))); break;
+            default: TRY((stage_local<__nv_bfloat16, float>(h, v, v.r, cs))); break;
         }
         cudaEventRecord(ev[3], st);
-        stage_restrict(h, nullptr);
+        stage_restrict(h, v, cs);
         cudaEventRecord(ev[4], st);
-        stage_coarse(h, nullptr);
+        stage_coarse(h, v, cs);
         cudaEventRecord(ev[5], st);
         switch (h->opts.precision) {
-            case ALGMORTAR_FP64: stage_prolong<double>(h, h->d_r, h->d_z, nullptr, &h->d_pcg->rz_next); break;
-            case ALGMORTAR_FP32: stage_prolong<float>(h, h->d_r, h->d_z, nullptr, &h->d_pcg->rz_next); break;
-            default: stage_prolong<__nv_bfloat16>(h, h->d_r, h->d_z, nullptr, &h->d_pcg->rz_next); break;
+            case ALGMORTAR_FP64: stage_prolong<double>(h, v, v.r, v.z, cs, rz); break;
+            case ALGMORTAR_FP32: stage_prolong<float>(h, v, v.r, v.z, cs, rz); break;
+            default: stage_prolong<__nv_bfloat16>(h, v, v.r, v.z, cs, rz); break;
         }
         cudaEventRecord(ev[6], st);
-        CU(cudaMemcpyAsync(h->d_pcg, &live, sizeof(live), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(v.sc, &live, sizeof(live), cudaMemcpyHostToDevice, st));
         cudaEventRecord(ev[7], st);
-        if (h->graph) {
-            CU(cudaGraphLaunch(h->graph, st));
-            add_launches(h->graph_kernels);
+        if (v.graph) {
+            CU(cudaGraphLaunch(v.graph, st));
+            add_launches(v.graph_kernels);
         } else {
-            TRY(pcg_iteration(h));
+            TRY(pcg_iteration(h, v));
         }
         cudaEvent_t e8;
         CU(cudaEventCreate(&e8));
@@ -1190,7 +1285,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     for (int k = 0; k < 7; ++k) ms_out[k] = acc[k] / reps;
     ms_out[7] = 0.0;
     for (auto& e : ev) cudaEventDestroy(e);
-    CU(cudaMemcpyAsync(h->d_pcg, &saved, sizeof(saved), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(v.sc, &saved, sizeof(saved), cudaMemcpyHostToDevice, st));
     CU(cudaStreamSynchronize(st));
     return 0;
 }

@@ -75,6 +75,17 @@ struct PcgScalars {
     int32_t max_it;
 };
 
+// Column layout of a batch of right-hand sides processed by one launch (gridDim.y =
+// columns): N-vectors of column j start j * v doubles after column 0, interface vectors
+// j * l after, and column j's stop flag is done[j * done_stride] (null: never stop).
+struct ColStrides {
+    int64_t v;
+    int64_t l;
+    const int32_t* done;
+    int done_stride;
+    int sc_stride;        // doubles between consecutive columns' PCG states
+};
+
 // Deterministic grid-wide sum: every CTA writes its block sum to part[blockIdx.x]; the
 // CTA that finishes last (atomic ticket) adds the partials in a fixed order, stores the
 // total and re-arms the ticket.  Same inputs -> bit-identical result.
@@ -122,7 +133,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Grid-wide deterministic sum of v into *result (see GridSum); returns true in the CTA
-// that wrote the result (its threads may then use *result after a __syncthreads).
+// that wrote the result (its threads may then use *result after a __syncthreads).  The
+// last CTA adds the partials with all its threads (fixed strided assignment, then a
+// fixed-order block reduction), so the tail stays short.
 __device__ __forceinline__ bool grid_sum(double v, double* sh, GridSum g, double* result) {
     __shared__ int last;
     double s = block_sum(v, sh);
@@ -134,12 +147,12 @@ __device__ __forceinline__ bool grid_sum(double v, double* sh, GridSum g, double
     __syncthreads();
     if (last) {
         __threadfence();
-        if (threadIdx.x < 32) {
-            double t = warp_sum_partials_cg(g.part, gridDim.x);
-            if (threadIdx.x == 0) {
-                *result = t;
-                *g.ticket = 0;
-            }
+        double t = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(g.part + i);
+        t = block_sum(t, sh);
+        if (threadIdx.x == 0) {
+            *result = t;
+            *g.ticket = 0;
         }
     }
     return last != 0;

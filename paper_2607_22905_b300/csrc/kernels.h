@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "common.cuh"
 
@@ -31,6 +32,8 @@ struct SolveArgs {
     int* err;                  // set to 1 if a bulk copy never completed (bounded wait)
     const int32_t* job_t0;     // per job: tile row where the right-hand side starts (rows
                                // above are zero) and below which no result is needed; or null
+    int64_t ldin, ldout;       // column strides of in / out (gridDim.y = columns)
+    int done_stride;           // int32 stride between columns' stop flags
 };
 
 struct InterfaceArgs {
@@ -99,6 +102,9 @@ void launch_nd_rhs(int64_t ncols, int64_t L, const double* Sd, const int64_t* go
                    const int32_t* alist, int64_t sep0, const int64_t* woff, const int32_t* col_item,
                    const int32_t* col_a, double* out, cudaStream_t st);
 void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
+// right-looking Cholesky of dense items advancing together (T_host: host copy of T)
+void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
+                           const int64_t* row0, double* work, double* dinv, int* err, cudaStream_t st);
 void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
                              double* Wrm, cudaStream_t st);
@@ -108,7 +114,7 @@ void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* ao
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
                            const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
                            double* work, cudaStream_t st);
-void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, const int32_t* done,
+void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
                      cudaStream_t st);
 cudaError_t prepare_nd_solve(int nsep);
 
@@ -132,7 +138,7 @@ template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
                      cudaStream_t st);
 template <typename TS, typename TA>
-cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st);
+cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols = 1);
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
                     const double* g_val, const int32_t* rows, const int64_t* phi_off, double* rhs,
                     cudaStream_t st);
@@ -146,28 +152,35 @@ void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double
 
 // vector / PCG kernels (kernels_pcg.cu)
 constexpr int VEC_BS = 256;
-int vec_blocks(int64_t n);                    // CTAs of the one-row-per-thread kernels
+int vec_blocks(int64_t n);                    // CTAs of the grid-strided vector kernels
+void set_vec_sms(int sms);
 void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
+void launch_gather_cols(int64_t n, int ncols, const int32_t* perm, const double* src, int64_t lds, double* dst,
+                        int64_t ldd, cudaStream_t st);
+void launch_scatter_cols(int64_t n, int ncols, const int32_t* perm, const double* src, int64_t lds, double* dst,
+                         int64_t ldd, cudaStream_t st);
 void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st);
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
-                     double* beta, const int32_t* omap, const int32_t* done, cudaStream_t st);
+                     double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st);
 template <typename TP>
 void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
                     const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
-                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, const int32_t* done,
-                    cudaStream_t st);
-void launch_pcg_init(int64_t n, const double* b, double* x, double* r, PcgScalars* sc, GridSum gs, double tol,
-                     int max_it, cudaStream_t st);
-void launch_pcg_p(int64_t n, const double* z, double* p, const PcgScalars* sc, cudaStream_t st);
-void launch_pcg_spmv_ell(int64_t n, const int64_t* ell_ptr, const int32_t* ell_col, const double* ell_val,
-                         const double* p, double* q, PcgScalars* sc, GridSum gs, cudaStream_t st);
+                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, ColStrides cs,
+                    int ncols, cudaStream_t st);
+void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
+                     GridSum gs, double tol, int max_it, cudaStream_t st);
+void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
+                  cudaStream_t st);
+void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
+                         const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
+                         cudaStream_t st);
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
-void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc, GridSum gs,
-                   cudaStream_t st);
-void launch_pcg_check(PcgScalars* sc, cudaStream_t st);
-void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* x,
-                     const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st);
+void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
+                   PcgScalars* sc, GridSum gs, cudaStream_t st);
+void launch_pcg_check(PcgScalars* sc, int ncols, cudaStream_t st);
+void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,
                       const double* tb, const double* tbp, const double* p, const double* lam, double* grad,
                       cudaStream_t st);

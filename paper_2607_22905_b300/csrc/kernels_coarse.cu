@@ -16,6 +16,7 @@
 // wide warp-per-row GEMV over all SMs (FP64 ALU-bound on B300), with no sequential
 // triangular sweep on the critical path.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -235,12 +236,152 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
 }
 
 // ---------------------------------------------------------------------------------
+// Right-looking Cholesky of a batch of DENSE items (the interface blocks), all items
+// advancing tile column k together: tile (I, J) of item g at base[g] + I(I+1)/2 + J,
+// column-major inside the tile; inverse diagonal tiles at dinv + (row0[g] + I) tiles.
+// ---------------------------------------------------------------------------------
+// One warp factors the 32x32 tile A_kk (row `lane` in registers, shuffles only) and
+// inverts the factor by forward substitution L X = I, one row of X per lane.
+__global__ void __launch_bounds__(32) k_dpotrf_b(int nitems, const int32_t* __restrict__ T,
+                                                 const int64_t* __restrict__ base,
+                                                 const int64_t* __restrict__ row0, double* __restrict__ work,
+                                                 double* __restrict__ dinv, int k, int* __restrict__ err) {
+    const int g = blockIdx.x;
+    if (g >= nitems || k >= T[g]) return;
+    const int lane = threadIdx.x;
+    double* t = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
+    double a[TILE];
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) a[c] = t[c * TILE + lane];
+    bool bad = false;
+#pragma unroll
+    for (int kk = 0; kk < TILE; ++kk) {
+        double piv = __shfl_sync(0xffffffffu, a[kk], kk);
+        if (!(piv > 0.0) || !isfinite(piv)) {
+            bad = true;
+            piv = 1.0;
+        }
+        const double d = sqrt(piv);
+        const double lk = lane > kk ? a[kk] / d : (lane == kk ? d : 0.0);
+        a[kk] = lk;
+#pragma unroll
+        for (int c = kk + 1; c < TILE; ++c) {
+            const double lck = __shfl_sync(0xffffffffu, lk, c);
+            if (lane >= c) a[c] -= lk * lck;
+        }
+    }
+    double x[TILE];
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) x[c] = (c == lane) ? 1.0 : 0.0;
+#pragma unroll
+    for (int r = 0; r < TILE; ++r) {
+        if (lane == r) {
+#pragma unroll
+            for (int c = 0; c < TILE; ++c) x[c] /= a[r];
+        }
+        const double lr = a[r];   // L[lane][r]
+#pragma unroll
+        for (int c = 0; c <= r; ++c) {
+            const double xrc = __shfl_sync(0xffffffffu, x[c], r);
+            if (lane > r) x[c] -= lr * xrc;
+        }
+    }
+    double* D = dinv + (row0[g] + k) * TILE2;
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) {
+        t[c * TILE + lane] = c <= lane ? a[c] : 0.0;
+        D[c * TILE + lane] = x[c];
+    }
+    if (lane == 0 && bad) {
+        if (atomicCAS(err + 1, -1, g) == -1) atomicExch(err, 1);
+    }
+}
+
+// block -> (item, local index) over per-item counts cnt_g(k)
+__device__ __forceinline__ int item_of_block(int nitems, const int32_t* T, int k, int64_t b, bool pairs,
+                                             int64_t* local) {
+    for (int g = 0; g < nitems; ++g) {
+        const int64_t w = T[g] - 1 - k;
+        const int64_t c = w <= 0 ? 0 : (pairs ? w * (w + 1) / 2 : w);
+        if (b < c) {
+            *local = b;
+            return g;
+        }
+        b -= c;
+    }
+    return -1;
+}
+
+// L_Ik = A_Ik L_kk^{-T} for I = k+1 .. T_g-1 of every item
+__global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __restrict__ T,
+                                                 const int64_t* __restrict__ base,
+                                                 const int64_t* __restrict__ row0, double* __restrict__ work,
+                                                 const double* __restrict__ dinv, int k) {
+    __shared__ double X[TILE][TILE + 1];
+    __shared__ double Bs[TILE][TILE + 1];
+    int64_t li;
+    const int g = item_of_block(nitems, T, k, blockIdx.x, false, &li);
+    if (g < 0) return;
+    const int I = k + 1 + (int)li;
+    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
+    double* t = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
+    const double* D = dinv + (row0[g] + k) * TILE2;
+    for (int e = tid; e < TILE2; e += 256) {
+        X[e & 31][e >> 5] = t[e];
+        Bs[e & 31][e >> 5] = D[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = 0;
+#pragma unroll 8
+        for (int u = 0; u < TILE; ++u) v += X[rb + q][u] * Bs[c][u];
+        t[c * TILE + rb + q] = v;
+    }
+}
+
+// A_IJ -= L_Ik L_Jk^T for k < J <= I < T_g of every item
+__global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __restrict__ T,
+                                                   const int64_t* __restrict__ base, double* __restrict__ work, int k) {
+    __shared__ double As[TILE][TILE + 1];
+    __shared__ double Bs[TILE][TILE + 1];
+    int64_t p;
+    const int g = item_of_block(nitems, T, k, blockIdx.x, true, &p);
+    if (g < 0) return;
+    int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= p) ++a;
+    while ((int64_t)a * (a + 1) / 2 > p) --a;
+    const int b = (int)(p - (int64_t)a * (a + 1) / 2);
+    const int I = k + 1 + a, J = k + 1 + b;
+    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
+    const double* LI = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
+    const double* LJ = work + (base[g] + (int64_t)J * (J + 1) / 2 + k) * TILE2;
+    double* t = work + (base[g] + (int64_t)I * (I + 1) / 2 + J) * TILE2;
+    for (int e = tid; e < TILE2; e += 256) {
+        As[e & 31][e >> 5] = LI[e];
+        Bs[e & 31][e >> 5] = LJ[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = t[c * TILE + rb + q];
+#pragma unroll 8
+        for (int u = 0; u < TILE; ++u) v -= As[rb + q][u] * Bs[c][u];
+        t[c * TILE + rb + q] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Per-iteration solve (ND order in and out).
 // Stage 1: eta_g = Ginv_g b_g  (rows of the symmetric inverse) and P_g = W_g^T b_g.
 // ---------------------------------------------------------------------------------
 __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
-                            double* __restrict__ P, const int32_t* __restrict__ done) {
-    if (done && *done) return;
+                            double* __restrict__ P, ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
+    b += col * cs.l;
+    eta += col * cs.l;
+    P += col * a.np;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t nin = a.goff[a.G];
@@ -270,8 +411,12 @@ __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double*
 
 // Stage 2: c = b_sep - sum_g P_g (built in shared memory by every CTA), eta_sep = Cinv c.
 __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
-                            const double* __restrict__ P, const int32_t* __restrict__ done) {
-    if (done && *done) return;
+                            const double* __restrict__ P, ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
+    b += col * cs.l;
+    eta += col * cs.l;
+    P += col * a.np;
     extern __shared__ double cvec[];
     const int nsep = a.nsep;
     const int64_t sep0 = a.goff[a.G];
@@ -292,8 +437,10 @@ __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double*
 }
 
 // Stage 3: eta_g -= W_g eta_{A_g}.
-__global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, const int32_t* __restrict__ done) {
-    if (done && *done) return;
+__global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
+    eta += col * cs.l;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t nin = a.goff[a.G];
@@ -358,6 +505,29 @@ void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, doub
         k_symmetrise<<<dim3(256, nitems), 256, 0, st>>>(rows, off, nitems, M);
     }
 }
+void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
+                           const int64_t* row0, double* work, double* dinv, int* err, cudaStream_t st) {
+    int maxT = 0;
+    for (int t : T_host) maxT = std::max(maxT, t);
+    for (int k = 0; k < maxT; ++k) {
+        int64_t nt = 0, np = 0;
+        for (int t : T_host) {
+            const int64_t w = t - 1 - k;
+            if (w > 0) {
+                nt += w;
+                np += w * (w + 1) / 2;
+            }
+        }
+        count_launch();
+        k_dpotrf_b<<<nitems, 32, 0, st>>>(nitems, T, base, row0, work, dinv, k, err);
+        if (nt > 0) {
+            count_launch();
+            k_dtrsm_b<<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, k);
+            count_launch();
+            k_dupdate_b<<<(unsigned)np, 256, 0, st>>>(nitems, T, base, work, k);
+        }
+    }
+}
 void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st) {
     if (nitems > 0) {
         count_launch();
@@ -388,18 +558,19 @@ void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, co
         k_nd_schur_tiles<<<(unsigned)ntiles, 256, 0, st>>>(L, nsep, sep0, Sd, sg, sidx, aoff, doff, D, work);
     }
 }
-void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, const int32_t* done,
+void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
                      cudaStream_t st) {
     const int64_t nin = a.nin, np = a.np;
     if (nin + np > 0) {
         count_launch();
-        k_nd_stage1<<<(unsigned)((nin + np + 7) / 8), 256, 0, st>>>(a, b, eta, P, done);
+        k_nd_stage1<<<dim3((unsigned)((nin + np + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
     }
     if (a.nsep > 0) {
         count_launch();
-        k_nd_stage2<<<(unsigned)((a.nsep + 7) / 8), 256, (size_t)a.nsep * sizeof(double), st>>>(a, b, eta, P, done);
+        k_nd_stage2<<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, (size_t)a.nsep * sizeof(double), st>>>(
+            a, b, eta, P, cs);
         count_launch();
-        k_nd_stage3<<<(unsigned)((nin + 7) / 8), 256, 0, st>>>(a, eta, done);
+        k_nd_stage3<<<dim3((unsigned)((nin + 7) / 8), ncols), 256, 0, st>>>(a, eta, cs);
     }
 }
 cudaError_t prepare_nd_solve(int nsep) {

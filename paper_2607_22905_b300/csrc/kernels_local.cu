@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
     const int64_t base = pf.base[s];
     const TW* Wb = work + base * TILE2;
     const TW* Db = dinv + r0 * TILE2;
-    for (int I = 0; I < T; ++I) {
+    for (int I = blockIdx.y; I < T; I += gridDim.y) {
         const int nt = I - lo[I];
         const int64_t fo = (base + fwd[I]) * TILE2;
         // forward: M = L_IJ (column-major source: M[r][c] at c*32 + r), then L_II^{-1}
@@ -453,7 +453,8 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 
 template <typename TS, typename TA, int R, int NW>
 __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
-    if (a.done && *a.done) return;
+    const int col = blockIdx.y;   // right-hand-side column of a batched solve
+    if (a.done && a.done[col * a.done_stride]) return;
     const int job = blockIdx.x;
     const int s = a.job_sub[job];
     const Profile pf = a.pf;
@@ -470,8 +471,8 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
     const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
     const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
     const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
-    const double* in = a.in + a.job_in[job];
-    double* out = a.out + a.job_out[job];
+    const double* in = a.in + a.job_in[job] + col * a.ldin;
+    double* out = a.out + a.job_out[job] + col * a.ldout;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     constexpr uint32_t TB = TILE2 * sizeof(TS);
 
@@ -732,7 +733,7 @@ template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
                      cudaStream_t st) {
     count_launch();
-    k_finalize<TW, TS><<<nitems, 256, 0, st>>>(pf, work, dinv, fwdS, bwdS);
+    k_finalize<TW, TS><<<dim3(nitems, 32), 256, 0, st>>>(pf, work, dinv, fwdS, bwdS);
 }
 
 template <typename TS>
@@ -741,7 +742,7 @@ constexpr int ring_slots() {
 }
 
 template <typename TS, typename TA>
-cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
+cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int R = ring_slots<TS>();
     constexpr int NW = 4;
     size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + 3 * NW * TILE * sizeof(TA) +
@@ -751,7 +752,7 @@ cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cuda
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
         count_launch();
-        k_chain_solve<TS, TA, R, NW><<<njobs, NW * 32, smem, st>>>(a);
+        k_chain_solve<TS, TA, R, NW><<<dim3(njobs, ncols), NW * 32, smem, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -819,9 +820,9 @@ template void launch_finalize<float, float>(int, const Profile&, const float*, c
                                             cudaStream_t);
 template void launch_finalize<float, __nv_bfloat16>(int, const Profile&, const float*, const float*,
                                                     __nv_bfloat16*, __nv_bfloat16*, cudaStream_t);
-template cudaError_t launch_tile_solve<double, double>(const SolveArgs&, int, int, cudaStream_t);
-template cudaError_t launch_tile_solve<float, float>(const SolveArgs&, int, int, cudaStream_t);
-template cudaError_t launch_tile_solve<__nv_bfloat16, float>(const SolveArgs&, int, int, cudaStream_t);
+template cudaError_t launch_tile_solve<double, double>(const SolveArgs&, int, int, cudaStream_t, int);
+template cudaError_t launch_tile_solve<float, float>(const SolveArgs&, int, int, cudaStream_t, int);
+template cudaError_t launch_tile_solve<__nv_bfloat16, float>(const SolveArgs&, int, int, cudaStream_t, int);
 template void launch_convert<float>(int64_t, const double*, float*, cudaStream_t);
 template void launch_convert<__nv_bfloat16>(int64_t, const double*, __nv_bfloat16*, cudaStream_t);
 

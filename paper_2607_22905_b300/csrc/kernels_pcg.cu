@@ -3,7 +3,7 @@
 // the interface restriction and prolongation of Algorithm 2, value refreshes, and the
 // adjoint gradient of the TPFA transmissibilities.
 //
-// Vector kernels run one row per thread.  Dot products are deterministic: each CTA
+// Vector kernels are grid-strided over rows.  Dot products are deterministic: each CTA
 // writes its block sum, and the CTA that finishes last adds the partials in a fixed
 // order (GridSum) and stores the scalar straight into the device-side PCG state, so
 // repeated runs give bit-identical iterates and no partial arrays cross kernels.
@@ -20,22 +20,30 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-// CTAs of a one-row-per-thread vector kernel over n rows (= size of its GridSum partials)
+// CTAs of the grid-strided vector kernels over n rows (= size of their GridSum partials):
+// at most 8 resident CTAs of 256 threads on each of the device's SMs
+static int g_max_vec_blocks = 8 * 148;
+void set_vec_sms(int sms) { g_max_vec_blocks = 8 * (sms > 0 ? sms : 148); }
 int vec_blocks(int64_t n) {
     int64_t g = (n + VEC_BS - 1) / VEC_BS;
-    return (int)(g < 1 ? 1 : (g > (1 << 30) ? (1 << 30) : g));
+    return (int)(g < 1 ? 1 : (g > g_max_vec_blocks ? g_max_vec_blocks : g));
 }
 
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// dst[k] = src[perm[k]] / dst[perm[k]] = src[k], column blockIdx.y at the given strides
 __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
-                         double* __restrict__ dst) {
+                         int64_t lds, double* __restrict__ dst, int64_t ldd) {
+    src += blockIdx.y * lds;
+    dst += blockIdx.y * ldd;
     GRID_STRIDE(k, n) dst[k] = src[perm[k]];
 }
 
 __global__ void k_scatter(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ src,
-                          double* __restrict__ dst) {
+                          int64_t lds, double* __restrict__ dst, int64_t ldd) {
+    src += blockIdx.y * lds;
+    dst += blockIdx.y * ldd;
     GRID_STRIDE(k, n) dst[perm[k]] = src[k];
 }
 
@@ -49,9 +57,11 @@ __global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, con
 // written at position omap[I] (the interface solve's ordering) when omap is given.
 __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_t* __restrict__ rcell,
                            const double* __restrict__ rcoef, const double* __restrict__ pbar,
-                           double* __restrict__ beta, const int32_t* __restrict__ omap,
-                           const int32_t* __restrict__ done) {
-    if (done && *done) return;
+                           double* __restrict__ beta, const int32_t* __restrict__ omap, ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
+    pbar += col * cs.v;
+    beta += col * cs.l;
     int I = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (I >= L) return;
@@ -73,9 +83,17 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __
                                                      const TP* __restrict__ phi, const double* __restrict__ eta,
                                                      const double* __restrict__ pbar, double* __restrict__ z,
                                                      const double* __restrict__ r, GridSum gs, double* rz,
-                                                     const int32_t* __restrict__ done) {
-    if (done && *done) return;
+                                                     ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
     __shared__ double sh[32];
+    eta += col * cs.l;
+    pbar += col * cs.v;
+    z += col * cs.v;
+    if (r) r += col * cs.v;
+    if (rz) rz += col * cs.sc_stride;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
     // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
     // (FP64 panels: FP64; FP32/BF16 panels: FP32), then added to pbar in FP64
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
@@ -99,10 +117,17 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __
 // ------------------------------------------------------------------------------ PCG
 // x = 0, r = b, ||b||^2; the CTA that completes the sum initialises the PCG state.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __restrict__ b,
-                                                      double* __restrict__ x, double* __restrict__ r,
+                                                      double* __restrict__ x, double* __restrict__ r, int64_t ld,
                                                       PcgScalars* __restrict__ sc, GridSum gs, double tol,
                                                       int max_it) {
     __shared__ double sh[32];
+    const int col = blockIdx.y;
+    b += col * ld;
+    x += col * ld;
+    r += col * ld;
+    sc += col;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
     double acc = 0.0;
     GRID_STRIDE(k, n) {
         const double v = b[k];
@@ -127,8 +152,12 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
 
 // p = z + beta p, beta = rho_new / rho (0 on the first iteration).
 __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
-                                                   const PcgScalars* __restrict__ sc) {
+                                                   int64_t ld, const PcgScalars* __restrict__ sc) {
+    const int col = blockIdx.y;
+    sc += col;
     if (sc->done) return;
+    z += col * ld;
+    p += col * ld;
     const double beta = sc->iter == 0 ? 0.0 : sc->rz_next / sc->rz;
     GRID_STRIDE(k, n) p[k] = z[k] + beta * p[k];
 }
@@ -140,9 +169,15 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
                                                           const int32_t* __restrict__ ell_col,
                                                           const double* __restrict__ ell_val,
                                                           const double* __restrict__ p, double* __restrict__ q,
-                                                          PcgScalars* __restrict__ sc, GridSum gs) {
+                                                          int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
+    const int col = blockIdx.y;
+    sc += col;
     if (sc->done) return;
     __shared__ double sh[32];
+    p += col * ld;
+    q += col * ld;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->rz = sc->rz_next;
     double acc = 0.0;
     GRID_STRIDE(k, n) {
@@ -173,9 +208,17 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
 // alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
-                                                    PcgScalars* __restrict__ sc, GridSum gs) {
+                                                    int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
+    const int col = blockIdx.y;
+    sc += col;
     if (sc->done) return;
     __shared__ double sh[32];
+    x += col * ld;
+    r += col * ld;
+    p += col * ld;
+    q += col * ld;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
     const double pq = sc->pq;
     const double al = sc->rz / pq;
     const bool ok = pq > 0.0 && isfinite(al);
@@ -193,7 +236,9 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
 }
 
 // Stop test on the device: breakdown, convergence, iteration cap.
-__global__ void k_pcg_check(PcgScalars* sc) {
+__global__ void k_pcg_check(PcgScalars* sc, int ncols) {
+    if ((int)threadIdx.x >= ncols) return;
+    sc += threadIdx.x;
     if (sc->done) return;
     sc->iter += 1;
     const double pq = sc->pq, rr = sc->rr_new;
@@ -216,15 +261,21 @@ __global__ void k_pcg_check(PcgScalars* sc) {
 
 // ||b - A x||^2 -> sc->res2 (true residual, CSR copy of A).
 __global__ void __launch_bounds__(VEC_BS) k_residual(int64_t n, const int32_t* __restrict__ rowptr,
-                                                      const int32_t* __restrict__ col,
+                                                      const int32_t* __restrict__ cidx,
                                                       const double* __restrict__ val,
                                                       const double* __restrict__ x, const double* __restrict__ b,
-                                                      PcgScalars* __restrict__ sc, GridSum gs) {
+                                                      int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
     __shared__ double sh[32];
+    const int col = blockIdx.y;
+    x += col * ld;
+    b += col * ld;
+    sc += col;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
     double acc = 0.0;
     GRID_STRIDE(k, n) {
         double s = b[k];
-        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) s -= val[e] * x[col[e]];
+        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) s -= val[e] * x[cidx[e]];
         acc += s * s;
     }
     grid_sum(acc, sh, gs, &sc->res2);
@@ -274,8 +325,12 @@ static inline int grid_for(int64_t n, int bs) {
 }
 
 void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st) {
+    launch_gather_cols(n, 1, perm, src, n, dst, n, st);
+}
+void launch_gather_cols(int64_t n, int ncols, const int32_t* perm, const double* src, int64_t lds, double* dst,
+                        int64_t ldd, cudaStream_t st) {
     count_launch();
-    k_gather<<<grid_for(n, 256), 256, 0, st>>>(n, perm, src, dst);
+    k_gather<<<dim3(grid_for(n, 256), ncols), 256, 0, st>>>(n, perm, src, lds, dst, ldd);
 }
 void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st) {
     if (n > 0) {
@@ -284,56 +339,62 @@ void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, doubl
     }
 }
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st) {
+    launch_scatter_cols(n, 1, perm, src, n, dst, n, st);
+}
+void launch_scatter_cols(int64_t n, int ncols, const int32_t* perm, const double* src, int64_t lds, double* dst,
+                         int64_t ldd, cudaStream_t st) {
     count_launch();
-    k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, perm, src, dst);
+    k_scatter<<<dim3(grid_for(n, 256), ncols), 256, 0, st>>>(n, perm, src, lds, dst, ldd);
 }
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
-                     double* beta, const int32_t* omap, const int32_t* done, cudaStream_t st) {
+                     double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st) {
     if (L > 0) {
         count_launch();
-        k_restrict<<<(L + 7) / 8, 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, done);
+        k_restrict<<<dim3((L + 7) / 8, ncols), 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, cs);
     }
 }
 template <typename TP>
 void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
                     const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
-                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, const int32_t* done,
-                    cudaStream_t st) {
+                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, ColStrides cs,
+                    int ncols, cudaStream_t st) {
     count_launch();
-    k_prolong<TP><<<vec_blocks(n), VEC_BS, 0, st>>>(n, row_sub, sub_off, if_off, if_list, phi_off, phi, eta, pbar, z,
-                                                    r, gs, rz, done);
+    k_prolong<TP><<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, row_sub, sub_off, if_off, if_list, phi_off, phi,
+                                                                 eta, pbar, z, r, gs, rz, cs);
 }
-void launch_pcg_init(int64_t n, const double* b, double* x, double* r, PcgScalars* sc, GridSum gs, double tol,
-                     int max_it, cudaStream_t st) {
+void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
+                     GridSum gs, double tol, int max_it, cudaStream_t st) {
     count_launch();
-    k_pcg_init<<<vec_blocks(n), VEC_BS, 0, st>>>(n, b, x, r, sc, gs, tol, max_it);
+    k_pcg_init<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, b, x, r, ld, sc, gs, tol, max_it);
 }
-void launch_pcg_p(int64_t n, const double* z, double* p, const PcgScalars* sc, cudaStream_t st) {
+void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
+                  cudaStream_t st) {
     count_launch();
-    k_pcg_p<<<vec_blocks(n), VEC_BS, 0, st>>>(n, z, p, sc);
+    k_pcg_p<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, z, p, ld, sc);
 }
-void launch_pcg_spmv_ell(int64_t n, const int64_t* ell_ptr, const int32_t* ell_col, const double* ell_val,
-                         const double* p, double* q, PcgScalars* sc, GridSum gs, cudaStream_t st) {
+void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
+                         const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
+                         cudaStream_t st) {
     count_launch();
-    k_pcg_spmv_ell<<<vec_blocks(n), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, sc, gs);
+    k_pcg_spmv_ell<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, ld, sc, gs);
 }
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st) {
     count_launch();
     k_ell_values<<<grid_for(nell, 256), 256, 0, st>>>(nell, src, val, ell_val);
 }
-void launch_pcg_xr(int64_t n, double* x, double* r, const double* p, const double* q, PcgScalars* sc, GridSum gs,
-                   cudaStream_t st) {
+void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
+                   PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
-    k_pcg_xr<<<vec_blocks(n), VEC_BS, 0, st>>>(n, x, r, p, q, sc, gs);
+    k_pcg_xr<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, ld, sc, gs);
 }
-void launch_pcg_check(PcgScalars* sc, cudaStream_t st) {
+void launch_pcg_check(PcgScalars* sc, int ncols, cudaStream_t st) {
     count_launch();
-    k_pcg_check<<<1, 1, 0, st>>>(sc);
+    k_pcg_check<<<1, ((ncols + 31) / 32) * 32, 0, st>>>(sc, ncols);
 }
-void launch_residual(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* x,
-                     const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {
+void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
-    k_residual<<<vec_blocks(n), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, sc, gs);
+    k_residual<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, ld, sc, gs);
 }
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,
                       const double* tb, const double* tbp, const double* p, const double* lam, double* grad,
@@ -345,7 +406,7 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
 #define INST_PROLONG(TP)                                                                                     \
     template void launch_prolong<TP>(int64_t, const int32_t*, const int64_t*, const int64_t*, const int32_t*,     \
                                      const int64_t*, const TP*, const double*, const double*, double*,            \
-                                     const double*, GridSum, double*, const int32_t*, cudaStream_t);
+                                     const double*, GridSum, double*, ColStrides, int, cudaStream_t);
 INST_PROLONG(double)
 INST_PROLONG(float)
 INST_PROLONG(__nv_bfloat16)

@@ -66,7 +66,7 @@ int interface_solve_noalloc(int device, cudaStream_t st, int L, const NdSolveArg
     double* eta_nd = scratch + L;      // written by stages 1 (interior) and 2 (separator)
     double* P = scratch + 2 * (int64_t)L;   // written by stage 1 before stage 2 reads it
     launch_scatter(L, d_ndpos, b_dev, b_nd, st);
-    launch_nd_solve(nd, b_nd, eta_nd, P, nullptr, st);
+    launch_nd_solve(nd, b_nd, eta_nd, P, ColStrides{}, 1, st);
     launch_gather(L, d_ndpos, eta_nd, eta_dev, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

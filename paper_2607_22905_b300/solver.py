@@ -124,15 +124,16 @@ class AlgMortar:
             raise B.AlgMortarError(rc, "algmortar_pcg_solve_host")
         return x, st.as_dict()
 
-    def solve_multi(self, Bm, tol=1e-8):
-        """Independent PCG solves for the columns of an N x k matrix (column-major)."""
+    def solve_multi(self, Bm, tol=1e-8, raise_on_fail=True):
+        """Independent PCG solves for the columns of an N x k matrix, batched: each
+        iteration's kernels cover all columns of a batch in one launch."""
         Bm = torch.as_tensor(Bm, dtype=torch.float64, device=self.device)
         Bt = Bm.t().contiguous()                      # k x N row-major == N x k column-major
         Xt = torch.empty_like(Bt)
         k = Bt.shape[0]
         st = (B.Stats * k)()
         rc = B.lib().algmortar_pcg_solve_multi(self._h, _ptr(Bt), _ptr(Xt), k, self.n, float(tol), st)
-        if rc != B.OK:
+        if rc != B.OK and (raise_on_fail or rc not in (B.NO_CONVERGENCE, B.BREAKDOWN)):
             raise B.AlgMortarError(rc, "algmortar_pcg_solve_multi")
         return Xt.t(), [s.as_dict() for s in st]
 

@@ -238,3 +238,45 @@ def test_max_it_reports_no_convergence():
     am = AlgMortar(A, len(sizes), part_sizes=sizes, max_it=3)
     x, st = am.solve(f, tol=1e-12, raise_on_fail=False)
     assert st["status"] == 5 and st["iterations"] == 3
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_multi_rhs_batches_bitwise_equal_single(use_graph):
+    """35 right-hand sides (a batch of 32 and a ragged batch of 3): every column equals the
+    single-RHS solve bit for bit, with its own iteration count and stop; a zero column
+    stops at once, a column scaled by 1e6 takes its own path."""
+    A, f, sizes = small3d()
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, precision="fp32", use_graph=use_graph, check_every=3)
+    rng = np.random.default_rng(12)
+    k = 35
+    Bm = rng.standard_normal((A.shape[0], k))
+    Bm[:, 3] = 0.0
+    Bm[:, 4] *= 1e6
+    Bm[:, 5] = f
+    X, stats = am.solve_multi(Bm, tol=1e-9)
+    its = set()
+    for j in range(k):
+        x, st = am.solve(Bm[:, j], tol=1e-9)
+        assert torch.equal(X[:, j], x), j
+        assert stats[j]["iterations"] == st["iterations"]
+        assert stats[j]["status"] == 0
+        its.add(st["iterations"])
+        if j != 3:
+            xj = X[:, j].cpu().numpy()
+            assert np.linalg.norm(Bm[:, j] - A @ xj) <= 1e-9 * np.linalg.norm(Bm[:, j])
+    assert stats[3]["iterations"] == 0 and float(X[:, 3].abs().max()) == 0.0
+    assert len(its) > 1
+
+
+def test_multi_rhs_matches_oracle_pcg():
+    """Batched FP64 solves against the oracle's PCG on the same seeded columns."""
+    A, f, sizes = small3d(shape=(19, 15, 11), m=8, uneven=False, seed=7)
+    part = op.partition(A, sizes)
+    pc = oa.setup(A, part)
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, precision="fp64")
+    Bm = np.random.default_rng(13).standard_normal((A.shape[0], 4))
+    X, stats = am.solve_multi(Bm, tol=1e-10)
+    for j in range(4):
+        ref = oa.pcg(A, Bm[:, j], lambda v: oa.apply(pc, v), 1e-10)
+        assert abs(stats[j]["iterations"] - ref.iterations) <= 1
+        assert rel(X[:, j].cpu().numpy(), ref.x) <= 1e-7
