@@ -91,6 +91,9 @@ typedef struct {
     int32_t nd_depth;              /* interface solve: depth of the nested-dissection split
                                       (2^depth groups from the partition's bisection tree);
                                       -1 (default) picks ~1000-unknown interior blocks    */
+    int32_t l2_prefetch;           /* local triangular solves: factor tiles prefetched into
+                                      L2 ahead of each CTA's shared-memory ring; -1
+                                      (default) = 32, 0 = off                             */
 } algmortar_opts;
 
 typedef struct {

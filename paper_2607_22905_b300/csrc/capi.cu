@@ -178,6 +178,15 @@ struct algmortar_handle {
 
 namespace {
 
+// Storage type of the MBF panels Phi: FP64 with FP64 factors, else FP32.  BF16 panels
+// would round Phi apart from the A_i^{-1} that the interface matrix was built with, and
+// that mismatch makes M^{-1} visibly non-symmetric (~1e-4 relative); FP32 keeps it at
+// rounding level for 32 MB more per iteration at config 3.
+inline int l2_ahead(const algmortar_t* h) { return h->opts.l2_prefetch < 0 ? 32 : h->opts.l2_prefetch; }
+
+template <typename TS>
+using PanelT = typename std::conditional<std::is_same<TS, double>::value, double, float>::type;
+
 template <typename T>
 int upload(algmortar_t* h, T*& dst, const std::vector<T>& src) {
     dst = h->alloc<T>(src.size());
@@ -243,7 +252,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     W.phi64 = h->alloc<double>(nphi);
     h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
     h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
-    h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<TS>(nphi);
+    h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<PanelT<TS>>(nphi);
     if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
     if (L > 0) {
@@ -520,9 +529,10 @@ int numeric_setup(algmortar_t* h) {
         a.alpha = 1.0;
         a.done = nullptr;
         a.err = h->d_kerr;
+        a.l2_ahead = l2_ahead(h);
         CU((launch_tile_solve<TS, TA>(a, W.njobs_mbf, P.max_tiles, st)));
     }
-    if (!std::is_same<TS, double>::value) launch_convert<TS>(nphi, W.phi64, (TS*)h->d_phi, st);
+    if (!std::is_same<TS, double>::value) launch_convert<PanelT<TS>>(nphi, W.phi64, (PanelT<TS>*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
     // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg),
     //     solved exactly by one level of nested dissection (kernels_coarse.cu) ---
@@ -569,6 +579,7 @@ int numeric_setup(algmortar_t* h) {
         sa.bwdS = W.gb;
         sa.alpha = 1.0;
         sa.err = h->d_kerr;
+        sa.l2_ahead = l2_ahead(h);
         sa.job_sub = W.d_gjob;
         sa.job_in = W.d_gjin;
         sa.job_out = W.d_gjin;
@@ -603,6 +614,7 @@ int numeric_setup(algmortar_t* h) {
             ca.bwdS = W.cb;
             ca.alpha = 1.0;
             ca.err = h->d_kerr;
+            ca.l2_ahead = l2_ahead(h);
             ca.job_sub = W.d_cjob;
             ca.job_in = W.d_cjin;
             ca.job_out = W.d_cjin;
@@ -677,6 +689,7 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs) 
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
+    a.l2_ahead = l2_ahead(h);
     a.err = h->d_kerr;
     CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st, v.k)));
     return 0;
@@ -703,7 +716,7 @@ int apply_t(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
     TRY((stage_local<TS, TA>(h, v, r, cs)));
     stage_restrict(h, v, cs);
     stage_coarse(h, v, cs);
-    stage_prolong<TS>(h, v, r, z, cs, pcg ? &v.sc->rz_next : nullptr);
+    stage_prolong<PanelT<TS>>(h, v, r, z, cs, pcg ? &v.sc->rz_next : nullptr);
     CU(cudaGetLastError());
     return 0;
 }
@@ -724,7 +737,6 @@ int pcg_iteration(algmortar_t* h, Vecs& v) {
     launch_pcg_p(n, v.k, n, v.z, v.p, v.sc, st);
     launch_pcg_spmv_ell(n, v.k, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
     launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.sc, v.gs, st);
-    launch_pcg_check(v.sc, v.k, st);
     return apply_internal(h, v, v.r, v.z, true);
 }
 
@@ -1039,6 +1051,7 @@ void algmortar_default_opts(algmortar_opts* o) {
     o->part_sizes = nullptr;
     o->stream = nullptr;
     o->nd_depth = -1;
+    o->l2_prefetch = -1;
 }
 
 int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes, int32_t* part_out) {
@@ -1256,7 +1269,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
         switch (h->opts.precision) {
             case ALGMORTAR_FP64: stage_prolong<double>(h, v, v.r, v.z, cs, rz); break;
             case ALGMORTAR_FP32: stage_prolong<float>(h, v, v.r, v.z, cs, rz); break;
-            default: stage_prolong<__nv_bfloat16>(h, v, v.r, v.z, cs, rz); break;
+            default: stage_prolong<float>(h, v, v.r, v.z, cs, rz); break;
         }
         cudaEventRecord(ev[6], st);
         CU(cudaMemcpyAsync(v.sc, &live, sizeof(live), cudaMemcpyHostToDevice, st));

@@ -34,6 +34,8 @@ struct SolveArgs {
                                // above are zero) and below which no result is needed; or null
     int64_t ldin, ldout;       // column strides of in / out (gridDim.y = columns)
     int done_stride;           // int32 stride between columns' stop flags
+    int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
+    int l2_ahead;              // tiles prefetched into L2 beyond the shared-memory ring (0: off)
 };
 
 struct InterfaceArgs {
@@ -178,7 +180,6 @@ void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_pt
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
                    PcgScalars* sc, GridSum gs, cudaStream_t st);
-void launch_pcg_check(PcgScalars* sc, int ncols, cudaStream_t st);
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,

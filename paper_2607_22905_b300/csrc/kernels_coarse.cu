@@ -241,7 +241,11 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
 // column-major inside the tile; inverse diagonal tiles at dinv + (row0[g] + I) tiles.
 // ---------------------------------------------------------------------------------
 // One warp factors the 32x32 tile A_kk (row `lane` in registers, shuffles only) and
-// inverts the factor by forward substitution L X = I, one row of X per lane.
+// inverts the factor.  B300's FP64 rate is ~1/64 of FP32 and a divide is a long
+// sequence of FP64 operations, so the tile takes one square root and one reciprocal per
+// column step (warp-uniform) and no other divides: with D = diag(L) and the unit lower
+// N = D^{-1} L (row scaling), L^{-1} = N^{-1} D^{-1}, i.e. forward substitution with
+// unit pivots followed by a column scaling.
 __global__ void __launch_bounds__(32) k_dpotrf_b(int nitems, const int32_t* __restrict__ T,
                                                  const int64_t* __restrict__ base,
                                                  const int64_t* __restrict__ row0, double* __restrict__ work,
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(32) k_dpotrf_b(int nitems, const int32_t* __re
 #pragma unroll
     for (int c = 0; c < TILE; ++c) a[c] = t[c * TILE + lane];
     bool bad = false;
+    double rdl = 1.0;   // 1 / L[lane][lane]
 #pragma unroll
     for (int kk = 0; kk < TILE; ++kk) {
         double piv = __shfl_sync(0xffffffffu, a[kk], kk);
@@ -262,7 +267,9 @@ __global__ void __launch_bounds__(32) k_dpotrf_b(int nitems, const int32_t* __re
             piv = 1.0;
         }
         const double d = sqrt(piv);
-        const double lk = lane > kk ? a[kk] / d : (lane == kk ? d : 0.0);
+        const double rd = 1.0 / d;
+        const double lk = lane > kk ? a[kk] * rd : (lane == kk ? d : 0.0);
+        if (lane == kk) rdl = rd;
         a[kk] = lk;
 #pragma unroll
         for (int c = kk + 1; c < TILE; ++c) {
@@ -270,27 +277,26 @@ __global__ void __launch_bounds__(32) k_dpotrf_b(int nitems, const int32_t* __re
             if (lane >= c) a[c] -= lk * lck;
         }
     }
+    // Y = N^{-1}: rows final in order; row r is broadcast and eliminated from rows > r
     double x[TILE];
 #pragma unroll
     for (int c = 0; c < TILE; ++c) x[c] = (c == lane) ? 1.0 : 0.0;
 #pragma unroll
     for (int r = 0; r < TILE; ++r) {
-        if (lane == r) {
+        const double nr = a[r] * rdl;   // N[lane][r]
 #pragma unroll
-            for (int c = 0; c < TILE; ++c) x[c] /= a[r];
+        for (int c = 0; c < r; ++c) {
+            const double yrc = __shfl_sync(0xffffffffu, x[c], r);
+            if (lane > r) x[c] -= nr * yrc;
         }
-        const double lr = a[r];   // L[lane][r]
-#pragma unroll
-        for (int c = 0; c <= r; ++c) {
-            const double xrc = __shfl_sync(0xffffffffu, x[c], r);
-            if (lane > r) x[c] -= lr * xrc;
-        }
+        if (lane > r) x[r] -= nr;   // Y[r][r] = 1
     }
     double* D = dinv + (row0[g] + k) * TILE2;
 #pragma unroll
     for (int c = 0; c < TILE; ++c) {
+        const double sc = __shfl_sync(0xffffffffu, rdl, c);
         t[c * TILE + lane] = c <= lane ? a[c] : 0.0;
-        D[c * TILE + lane] = x[c];
+        D[c * TILE + lane] = x[c] * sc;
     }
     if (lane == 0 && bad) {
         if (atomicCAS(err + 1, -1, g) == -1) atomicExch(err, 1);

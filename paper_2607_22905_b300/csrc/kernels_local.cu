@@ -348,6 +348,12 @@ __device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint3
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+// Asynchronous prefetch of a global range into L2 (no completion tracking): the chain
+// solves run it ahead of their shared-memory ring, so the ring's bulk copies are served
+// from L2 and the ring depth no longer caps a CTA's bytes in flight at HBM latency.
+__device__ __forceinline__ void l2_prefetch(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -453,9 +459,11 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 
 template <typename TS, typename TA, int R, int NW>
 __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
-    const int col = blockIdx.y;   // right-hand-side column of a batched solve
+    // batched solves put the column in blockIdx.x, so the CTAs of one subdomain's columns
+    // run side by side and share its factor stream through L2
+    const int col = a.col_fast ? blockIdx.x : 0;
+    const int job = a.col_fast ? blockIdx.y : blockIdx.x;
     if (a.done && a.done[col * a.done_stride]) return;
-    const int job = blockIdx.x;
     const int s = a.job_sub[job];
     const Profile pf = a.pf;
     const int n = pf.rows[s], T = pf.ntiles[s];
@@ -493,6 +501,14 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
         fence_async_smem();
         for (int64_t q = q0; q < q0 + R && q < qend; ++q)
             tma_load_1d(smem_u32(ring + slot_of(q) * TILE2), src(q), TB, smem_u32(&bars[slot_of(q)]));
+        // L2 prefetch window [q0 + R, q0 + R + ahead): contiguous within each stream
+        const int64_t p0 = q0 + R, p1 = min(q0 + R + (int64_t)a.l2_ahead, qend);
+        if (p0 < p1) {
+            const int64_t f1 = min(p1, nts);
+            if (p0 < f1) l2_prefetch(src(p0), (uint32_t)((f1 - p0) * TB));
+            const int64_t b0 = max(p0, nts);
+            if (b0 < p1) l2_prefetch(src(b0), (uint32_t)((p1 - b0) * TB));
+        }
     }
     for (int i = tid; i < T; i += NW * 32) {
         lo_s[i] = pf.lo[r0 + i];
@@ -512,6 +528,8 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
             const int slot = slot_of(qq);
             fence_async_smem();
             tma_load_1d(smem_u32(ring + slot * TILE2), src(qq + R), TB, smem_u32(&bars[slot]));
+            const int64_t qp = qq + R + a.l2_ahead;   // keep the L2 window `l2_ahead` tiles deep
+            if (a.l2_ahead > 0 && qp < qend) l2_prefetch(src(qp), TB);
         }
     };
     int64_t q = q0;
@@ -752,7 +770,10 @@ cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cuda
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
         count_launch();
-        k_chain_solve<TS, TA, R, NW><<<dim3(njobs, ncols), NW * 32, smem, st>>>(a);
+        SolveArgs b = a;
+        b.col_fast = ncols > 1;
+        const dim3 grid = ncols > 1 ? dim3(ncols, njobs) : dim3(njobs);
+        k_chain_solve<TS, TA, R, NW><<<grid, NW * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
 }

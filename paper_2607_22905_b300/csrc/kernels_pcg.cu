@@ -205,7 +205,30 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
     grid_sum(acc, sh, gs, &sc->pq);
 }
 
-// alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new.
+// Stop test on the device (breakdown, convergence, iteration cap), run by the thread that
+// completes ||r||^2.
+__device__ __forceinline__ void pcg_stop_test(PcgScalars* sc) {
+    sc->iter += 1;
+    const double pq = sc->pq, rr = sc->rr_new;
+    const double al = sc->rz / pq;
+    sc->alpha = al;
+    if (!(pq > 0.0) || !isfinite(al) || !isfinite(rr)) {
+        sc->done = 1;
+        sc->status = 6;
+    } else {
+        sc->rr = rr;
+        if (rr <= sc->tol2) {
+            sc->done = 1;
+            sc->status = 0;
+        } else if (sc->iter >= sc->max_it) {
+            sc->done = 1;
+            sc->status = 5;
+        }
+    }
+}
+
+// alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new, then the
+// stop test.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
@@ -232,31 +255,7 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
         }
         acc += rk * rk;
     }
-    grid_sum(acc, sh, gs, &sc->rr_new);
-}
-
-// Stop test on the device: breakdown, convergence, iteration cap.
-__global__ void k_pcg_check(PcgScalars* sc, int ncols) {
-    if ((int)threadIdx.x >= ncols) return;
-    sc += threadIdx.x;
-    if (sc->done) return;
-    sc->iter += 1;
-    const double pq = sc->pq, rr = sc->rr_new;
-    const double al = sc->rz / pq;
-    sc->alpha = al;
-    if (!(pq > 0.0) || !isfinite(al) || !isfinite(rr)) {
-        sc->done = 1;
-        sc->status = 6;
-    } else {
-        sc->rr = rr;
-        if (rr <= sc->tol2) {
-            sc->done = 1;
-            sc->status = 0;
-        } else if (sc->iter >= sc->max_it) {
-            sc->done = 1;
-            sc->status = 5;
-        }
-    }
+    if (grid_sum(acc, sh, gs, &sc->rr_new) && threadIdx.x == 0) pcg_stop_test(sc);
 }
 
 // ||b - A x||^2 -> sc->res2 (true residual, CSR copy of A).
@@ -386,10 +385,6 @@ void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const
                    PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
     k_pcg_xr<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, ld, sc, gs);
-}
-void launch_pcg_check(PcgScalars* sc, int ncols, cudaStream_t st) {
-    count_launch();
-    k_pcg_check<<<1, ((ncols + 31) / 32) * 32, 0, st>>>(sc, ncols);
 }
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {
