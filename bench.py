@@ -336,6 +336,20 @@ def run_apply(args):
     am.close()
 
 
+def run_solve(args):
+    """One setup and one PCG solve to the tolerance on the stream path (profiling target
+    for the per-iteration kernels)."""
+    import torch
+    from paper_2607_22905_b300.solver import AlgMortar
+    P, wdesc = workload(args.config)
+    prec = args.variants.split(",")[0]
+    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec)
+    x, st = am.solve(torch.as_tensor(P.f, device="cuda"), tol=TOL)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "solve", "workload": wdesc, "variant": prec, "stats": st}))
+    am.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,9 +361,9 @@ def main():
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--stage-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "apply"],
-                    help="apply: set up the first variant and run one preconditioner application "
-                         "(for kernel profiling), no timing")
+    ap.add_argument("--mode", default="bench", choices=["bench", "apply", "solve"],
+                    help="apply / solve: set up the first variant and run one preconditioner "
+                         "application / one PCG solve (kernel profiling targets), no timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -357,6 +371,8 @@ def main():
         run_reference(args)
     elif args.mode == "apply":
         run_apply(args)
+    elif args.mode == "solve":
+        run_solve(args)
     else:
         run_ours(args)
 

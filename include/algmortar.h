@@ -82,7 +82,8 @@ typedef struct {
     int32_t max_it;                /* PCG iteration cap (default 10000)                   */
     int32_t use_graph;             /* 1: replay each PCG iteration as a captured CUDA graph */
     int32_t check_every;           /* iterations between host convergence reads (>= 1)    */
-    int32_t flexible;              /* 1: Polak-Ribiere beta (for low-precision factors)   */
+    int32_t flexible;              /* 1: Polak-Ribiere beta (r_{k+1}.(z_{k+1} - z_k) / rho_k,
+                                      for slightly non-symmetric low-precision M^{-1})    */
     int32_t verbose;               /* 1: stage timings to stderr                          */
     int32_t device;                /* CUDA device ordinal (default 0)                      */
     const int32_t* part_sizes;     /* host, n_parts target sizes summing to n, or NULL for
@@ -93,7 +94,10 @@ typedef struct {
                                       -1 (default) picks ~1000-unknown interior blocks    */
     int32_t l2_prefetch;           /* local triangular solves: factor tiles prefetched into
                                       L2 ahead of each CTA's shared-memory ring; -1
-                                      (default) = 32, 0 = off                             */
+                                      (default) = 0 = off                                 */
+    int32_t deep_ring;             /* local triangular solves: 1 doubles each CTA's ring of
+                                      factor tiles (64 KB instead of 32 KB of shared
+                                      memory, fewer CTAs per SM); default 0               */
 } algmortar_opts;
 
 typedef struct {
@@ -166,7 +170,9 @@ int algmortar_apply_stages(algmortar_t* h, const double* r_dev, double* pbar_dev
                            double* beta_dev, double* eta_dev, double* z_dev);
 
 /* PCG with x0 = 0 for A x = b, preconditioned by AlgMortar; stops when
- * ||r_k||_2 <= tol ||b||_2 and the true residual confirms it (Sec. 7).  b_dev, x_dev:
+ * ||r_k||_2 <= tol ||b||_2 and the true residual confirms it (Sec. 7).  When it does
+ * not, the recursive residual is replaced by b - A x and the search directions restart
+ * (at most 8 times).  opts.flexible selects the Polak-Ribiere beta.  b_dev, x_dev:
  * device, n doubles, original ordering.  st may be NULL.  Returns OK, NO_CONVERGENCE
  * or BREAKDOWN (x_dev holds the last iterate in the latter two cases). */
 int algmortar_pcg_solve(algmortar_t* h, const double* b_dev, double* x_dev, double tol,

@@ -182,7 +182,7 @@ namespace {
 // would round Phi apart from the A_i^{-1} that the interface matrix was built with, and
 // that mismatch makes M^{-1} visibly non-symmetric (~1e-4 relative); FP32 keeps it at
 // rounding level for 32 MB more per iteration at config 3.
-inline int l2_ahead(const algmortar_t* h) { return h->opts.l2_prefetch < 0 ? 32 : h->opts.l2_prefetch; }
+inline int l2_ahead(const algmortar_t* h) { return h->opts.l2_prefetch < 0 ? 0 : h->opts.l2_prefetch; }
 
 template <typename TS>
 using PanelT = typename std::conditional<std::is_same<TS, double>::value, double, float>::type;
@@ -530,6 +530,7 @@ int numeric_setup(algmortar_t* h) {
         a.done = nullptr;
         a.err = h->d_kerr;
         a.l2_ahead = l2_ahead(h);
+        a.deep_ring = h->opts.deep_ring;
         CU((launch_tile_solve<TS, TA>(a, W.njobs_mbf, P.max_tiles, st)));
     }
     if (!std::is_same<TS, double>::value) launch_convert<PanelT<TS>>(nphi, W.phi64, (PanelT<TS>*)h->d_phi, st);
@@ -580,6 +581,7 @@ int numeric_setup(algmortar_t* h) {
         sa.alpha = 1.0;
         sa.err = h->d_kerr;
         sa.l2_ahead = l2_ahead(h);
+        sa.deep_ring = h->opts.deep_ring;
         sa.job_sub = W.d_gjob;
         sa.job_in = W.d_gjin;
         sa.job_out = W.d_gjin;
@@ -615,6 +617,7 @@ int numeric_setup(algmortar_t* h) {
             ca.alpha = 1.0;
             ca.err = h->d_kerr;
             ca.l2_ahead = l2_ahead(h);
+            ca.deep_ring = h->opts.deep_ring;
             ca.job_sub = W.d_cjob;
             ca.job_in = W.d_cjin;
             ca.job_out = W.d_cjin;
@@ -690,6 +693,7 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs) 
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
     a.l2_ahead = l2_ahead(h);
+    a.deep_ring = h->opts.deep_ring;
     a.err = h->d_kerr;
     CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st, v.k)));
     return 0;
@@ -736,7 +740,7 @@ int pcg_iteration(algmortar_t* h, Vecs& v) {
     const int64_t n = h->n;
     launch_pcg_p(n, v.k, n, v.z, v.p, v.sc, st);
     launch_pcg_spmv_ell(n, v.k, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
-    launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.sc, v.gs, st);
+    launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, st);
     return apply_internal(h, v, v.r, v.z, true);
 }
 
@@ -781,7 +785,7 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     const size_t n = (size_t)h->n * cap;
     const size_t l = (size_t)std::max(h->L, 1) * cap;
     const int64_t np = h->P.nd_aoff.empty() ? 1 : std::max<int64_t>(h->P.nd_aoff.back(), 1);
-    const size_t nb = (size_t)vec_blocks(h->n) * cap;
+    const size_t nb = 2 * (size_t)vec_blocks(h->n) * cap;   // two sums per CTA (flexible beta)
     v.x = h->alloc<double>(n);
     v.r = h->alloc<double>(n);
     v.z = h->alloc<double>(n);
@@ -818,7 +822,7 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     const int k = v.k;
     const int64_t n = h->n;
     if (h->opts.use_graph) TRY(ensure_graph(h, v));
-    launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, st);
+    launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, h->opts.flexible ? 1 : 0, st);
     TRY(apply_internal(h, v, v.r, v.z, true));
     std::vector<PcgScalars> hs(k);
     std::vector<int> restarts(k, 0);
@@ -849,7 +853,8 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
             true_rel[j] = hs[j].bb > 0 ? std::sqrt(hs[j].res2 / hs[j].bb) : 0.0;
             if (hs[j].status == 0 && hs[j].bb > 0 && !(true_rel[j] <= tol) && restarts[j] < 8 &&
                 hs[j].iter < hs[j].max_it) {
-                // recurrence converged but the true residual does not confirm it: continue
+                // the recurrence converged but the true residual does not confirm it:
+                // replace r by b - A x and restart the directions (below)
                 ++restarts[j];
                 CU(cudaMemcpyAsync(&v.sc[j].done, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
                 again = true;
@@ -858,6 +863,8 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
             }
         }
         if (!again) break;
+        launch_pcg_replace(n, k, n, h->d_rowptr, h->d_col, h->d_val, v.x, v.b, v.r, v.sc, v.gs, st);
+        TRY(apply_internal(h, v, v.r, v.z, true));
         CU(cudaStreamSynchronize(st));
     }
     int worst = ALGMORTAR_OK;
@@ -1052,6 +1059,7 @@ void algmortar_default_opts(algmortar_opts* o) {
     o->stream = nullptr;
     o->nd_depth = -1;
     o->l2_prefetch = -1;
+    o->deep_ring = 0;
 }
 
 int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes, int32_t* part_out) {
@@ -1253,7 +1261,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
         launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
         cudaEventRecord(ev[1], st);
         launch_pcg_p(n, 1, n, v.z, v.p, v.sc, st);
-        launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.sc, v.gs, st);
+        launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, st);
         cudaEventRecord(ev[2], st);
         // stages of Algorithm 2 (same launches as apply_internal, timed one by one)
         switch (h->opts.precision) {

@@ -69,10 +69,13 @@ struct PcgScalars {
     double bb;        // ||b||^2
     double tol2;      // tol^2 ||b||^2
     double res2;      // ||b - A x||^2 (true residual, on request)
+    double rz_mix;    // r_{k+1} . z_k (flexible beta only)
     int32_t iter;     // products with A so far
     int32_t done;     // 1: stop (converged or failed)
     int32_t status;   // 0 converged, 5 max_it, 6 breakdown
     int32_t max_it;
+    int32_t flexible; // 1: Polak-Ribiere beta
+    int32_t restart;  // 1: the residual was just replaced by b - A x; next beta = 0
 };
 
 // Column layout of a batch of right-hand sides processed by one launch (gridDim.y =
@@ -130,6 +133,36 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     }
     __syncthreads();
     return s;
+}
+
+// Two grid-wide sums at once (partials interleaved, 2 per CTA); same contract as grid_sum.
+__device__ __forceinline__ bool grid_sum2(double v0, double v1, double* sh, GridSum g, double* r0, double* r1) {
+    __shared__ int last2;
+    const double s0 = block_sum(v0, sh);
+    const double s1 = block_sum(v1, sh);
+    if (threadIdx.x == 0) {
+        g.part[2 * blockIdx.x] = s0;
+        g.part[2 * blockIdx.x + 1] = s1;
+        __threadfence();
+        last2 = atomicAdd(g.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last2) {
+        __threadfence();
+        double t0 = 0.0, t1 = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            t0 += __ldcg(g.part + 2 * i);
+            t1 += __ldcg(g.part + 2 * i + 1);
+        }
+        t0 = block_sum(t0, sh);
+        t1 = block_sum(t1, sh);
+        if (threadIdx.x == 0) {
+            *r0 = t0;
+            *r1 = t1;
+            *g.ticket = 0;
+        }
+    }
+    return last2 != 0;
 }
 
 // Grid-wide deterministic sum of v into *result (see GridSum); returns true in the CTA

@@ -36,6 +36,7 @@ struct SolveArgs {
     int done_stride;           // int32 stride between columns' stop flags
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
     int l2_ahead;              // tiles prefetched into L2 beyond the shared-memory ring (0: off)
+    int deep_ring;             // 1: twice the default ring depth (64 KB of tiles per CTA)
 };
 
 struct InterfaceArgs {
@@ -171,7 +172,10 @@ void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, c
                     const double* pbar, double* z, const double* r, GridSum gs, double* rz, ColStrides cs,
                     int ncols, cudaStream_t st);
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
-                     GridSum gs, double tol, int max_it, cudaStream_t st);
+                     GridSum gs, double tol, int max_it, int flexible, cudaStream_t st);
+void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,
+                        const double* val, const double* x, const double* b, double* r, PcgScalars* sc, GridSum gs,
+                        cudaStream_t st);
 void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
                   cudaStream_t st);
 void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
@@ -179,7 +183,7 @@ void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_pt
                          cudaStream_t st);
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
-                   PcgScalars* sc, GridSum gs, cudaStream_t st);
+                   const double* z, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,

@@ -759,9 +759,8 @@ constexpr int ring_slots() {
     return sizeof(TS) == 8 ? 4 : (sizeof(TS) == 4 ? 8 : 12);
 }
 
-template <typename TS, typename TA>
-cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
-    constexpr int R = ring_slots<TS>();
+template <typename TS, typename TA, int R>
+static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int NW = 4;
     size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + 3 * NW * TILE * sizeof(TA) +
                   (size_t)(2 * max_tiles + 4) * sizeof(int32_t) + (size_t)max_tiles * TILE * sizeof(TA) + 16;
@@ -776,6 +775,13 @@ cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cuda
         k_chain_solve<TS, TA, R, NW><<<grid, NW * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
+}
+
+template <typename TS, typename TA>
+cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
+    constexpr int R = ring_slots<TS>();
+    return a.deep_ring ? launch_ring<TS, TA, 2 * R>(a, njobs, max_tiles, st, ncols)
+                       : launch_ring<TS, TA, R>(a, njobs, max_tiles, st, ncols);
 }
 
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __
 __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __restrict__ b,
                                                       double* __restrict__ x, double* __restrict__ r, int64_t ld,
                                                       PcgScalars* __restrict__ sc, GridSum gs, double tol,
-                                                      int max_it) {
+                                                      int max_it, int flexible) {
     __shared__ double sh[32];
     const int col = blockIdx.y;
     b += col * ld;
@@ -146,11 +146,17 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
         sc->max_it = max_it;
         sc->rz = 0.0;
         sc->rz_next = 0.0;
+        sc->rz_mix = 0.0;
         sc->alpha = sc->beta = sc->pq = 0.0;
+        sc->flexible = flexible;
+        sc->restart = 0;
     }
 }
 
-// p = z + beta p, beta = rho_new / rho (0 on the first iteration).
+// p = z + beta p with beta = rho_new / rho (Fletcher-Reeves form of CG), or with the
+// flexible (Polak-Ribiere) beta = (rho_new - r_new . z_old) / rho, which tolerates a
+// slightly non-symmetric preconditioner; beta = 0 on the first iteration and right after
+// a residual replacement.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                                                    int64_t ld, const PcgScalars* __restrict__ sc) {
     const int col = blockIdx.y;
@@ -158,7 +164,9 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __res
     if (sc->done) return;
     z += col * ld;
     p += col * ld;
-    const double beta = sc->iter == 0 ? 0.0 : sc->rz_next / sc->rz;
+    const double beta = (sc->iter == 0 || sc->restart)
+                            ? 0.0
+                            : (sc->flexible ? (sc->rz_next - sc->rz_mix) / sc->rz : sc->rz_next / sc->rz);
     GRID_STRIDE(k, n) p[k] = z[k] + beta * p[k];
 }
 
@@ -178,7 +186,10 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
     q += col * ld;
     gs.part += col * gridDim.x;
     gs.ticket += col;
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->rz = sc->rz_next;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->rz = sc->rz_next;
+        sc->restart = 0;
+    }
     double acc = 0.0;
     GRID_STRIDE(k, n) {
         const int64_t sl = k >> 5;
@@ -227,11 +238,13 @@ __device__ __forceinline__ void pcg_stop_test(PcgScalars* sc) {
     }
 }
 
-// alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new, then the
-// stop test.
+// alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new (and, for
+// the flexible beta, r_new . z_old -> sc->rz_mix, z still holding z_old), then the stop
+// test.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
-                                                    int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
+                                                    const double* __restrict__ z, int64_t ld,
+                                                    PcgScalars* __restrict__ sc, GridSum gs) {
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
@@ -240,12 +253,14 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
     r += col * ld;
     p += col * ld;
     q += col * ld;
-    gs.part += col * gridDim.x;
+    z += col * ld;
+    const bool flex = sc->flexible != 0;
+    gs.part += col * (flex ? 2 : 1) * gridDim.x;
     gs.ticket += col;
     const double pq = sc->pq;
     const double al = sc->rz / pq;
     const bool ok = pq > 0.0 && isfinite(al);
-    double acc = 0.0;
+    double acc = 0.0, acc2 = 0.0;
     GRID_STRIDE(k, n) {
         double rk = r[k];
         if (ok) {
@@ -254,8 +269,41 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
             r[k] = rk;
         }
         acc += rk * rk;
+        if (flex) acc2 += rk * z[k];
     }
-    if (grid_sum(acc, sh, gs, &sc->rr_new) && threadIdx.x == 0) pcg_stop_test(sc);
+    const bool last = flex ? grid_sum2(acc, acc2, sh, gs, &sc->rr_new, &sc->rz_mix)
+                           : grid_sum(acc, sh, gs, &sc->rr_new);
+    if (last && threadIdx.x == 0) pcg_stop_test(sc);
+}
+
+// Residual replacement for columns that restart (done == 0): r = b - A x, ||r||^2 ->
+// rr and rr_new, and the next beta is 0 (CSR copy of A).
+__global__ void __launch_bounds__(VEC_BS) k_pcg_replace(int64_t n, const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ cidx,
+                                                         const double* __restrict__ val,
+                                                         const double* __restrict__ x, const double* __restrict__ b,
+                                                         double* __restrict__ r, int64_t ld,
+                                                         PcgScalars* __restrict__ sc, GridSum gs) {
+    const int col = blockIdx.y;
+    sc += col;
+    if (sc->done) return;
+    __shared__ double sh[32];
+    x += col * ld;
+    b += col * ld;
+    r += col * ld;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
+    double acc = 0.0;
+    GRID_STRIDE(k, n) {
+        double s = b[k];
+        for (int32_t e = rowptr[k]; e < rowptr[k + 1]; ++e) s -= val[e] * x[cidx[e]];
+        r[k] = s;
+        acc += s * s;
+    }
+    if (grid_sum(acc, sh, gs, &sc->rr_new) && threadIdx.x == 0) {
+        sc->rr = sc->rr_new;
+        sc->restart = 1;
+    }
 }
 
 // ||b - A x||^2 -> sc->res2 (true residual, CSR copy of A).
@@ -362,9 +410,15 @@ void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, c
                                                                  eta, pbar, z, r, gs, rz, cs);
 }
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
-                     GridSum gs, double tol, int max_it, cudaStream_t st) {
+                     GridSum gs, double tol, int max_it, int flexible, cudaStream_t st) {
     count_launch();
-    k_pcg_init<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, b, x, r, ld, sc, gs, tol, max_it);
+    k_pcg_init<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, b, x, r, ld, sc, gs, tol, max_it, flexible);
+}
+void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,
+                        const double* val, const double* x, const double* b, double* r, PcgScalars* sc, GridSum gs,
+                        cudaStream_t st) {
+    count_launch();
+    k_pcg_replace<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, r, ld, sc, gs);
 }
 void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
                   cudaStream_t st) {
@@ -382,9 +436,9 @@ void launch_ell_values(int64_t nell, const int32_t* src, const double* val, doub
     k_ell_values<<<grid_for(nell, 256), 256, 0, st>>>(nell, src, val, ell_val);
 }
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
-                   PcgScalars* sc, GridSum gs, cudaStream_t st) {
+                   const double* z, PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
-    k_pcg_xr<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, ld, sc, gs);
+    k_pcg_xr<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, z, ld, sc, gs);
 }
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {

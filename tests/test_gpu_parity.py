@@ -280,3 +280,34 @@ def test_multi_rhs_matches_oracle_pcg():
         ref = oa.pcg(A, Bm[:, j], lambda v: oa.apply(pc, v), 1e-10)
         assert abs(stats[j]["iterations"] - ref.iterations) <= 1
         assert rel(X[:, j].cpu().numpy(), ref.x) <= 1e-7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_flexible_beta(precision):
+    """Polak-Ribiere beta: with the FP64 (symmetric) preconditioner r_{k+1}.z_k = 0 in
+    exact arithmetic, so the iteration count matches the standard beta to +-1; with
+    low-precision factors it converges to the same tolerance."""
+    A, f, sizes = small3d()
+    std = AlgMortar(A, len(sizes), part_sizes=sizes, precision=precision)
+    flx = AlgMortar(A, len(sizes), part_sizes=sizes, precision=precision, flexible=True, use_graph=True,
+                    check_every=4)
+    xs, ss = std.solve(f, tol=1e-10)
+    xf, sf = flx.solve(f, tol=1e-10)
+    assert sf["status"] == 0
+    assert np.linalg.norm(f - A @ xf.cpu().numpy()) <= 1e-10 * np.linalg.norm(f)
+    if precision == "fp64":
+        assert abs(sf["iterations"] - ss["iterations"]) <= 1
+    else:
+        assert sf["iterations"] <= ss["iterations"] + 3
+
+
+def test_tight_tolerance_reports_true_residual():
+    """A tolerance near the FP64 floor with BF16 factors: the solver either confirms it on
+    the true residual (after residual replacements) or reports NO_CONVERGENCE; it never
+    breaks down, and the reported residual is the true one."""
+    A, f, sizes = small3d()
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, precision="bf16", use_graph=True, check_every=4)
+    x, st = am.solve(f, tol=1e-14, raise_on_fail=False)
+    assert st["status"] in (0, 5)
+    true = np.linalg.norm(f - A @ x.cpu().numpy()) / np.linalg.norm(f)
+    assert abs(true - st["rel_residual"]) <= 1e-3 * true + 1e-16
