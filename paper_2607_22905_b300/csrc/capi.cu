@@ -121,6 +121,7 @@ struct algmortar_handle {
     int32_t *d_rows = nullptr, *d_ntiles = nullptr;
     void *d_fwdS = nullptr, *d_bwdS = nullptr;
     double *d_dloc = nullptr, *d_sc = nullptr;
+    float* d_sc32 = nullptr;
     int32_t* d_job_sub = nullptr;
     int64_t* d_job_off = nullptr;
     // interfaces
@@ -502,7 +503,8 @@ int numeric_setup(algmortar_t* h) {
     int err_init[2] = {0, -1};
     CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
-    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, h->d_dloc, h->d_sc, st);
+    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, h->d_dloc, h->d_sc,
+                      h->d_sc32, st);
     launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
                              h->d_sc, work, m, st);
     launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
@@ -520,13 +522,13 @@ int numeric_setup(algmortar_t* h) {
         a.fwdS = h->d_fwdS;
         a.bwdS = h->d_bwdS;
         a.scale = h->d_sc;
+        a.scale32 = h->d_sc32;
         a.scale_off = h->d_sub_off;
         a.job_sub = W.d_js;
         a.job_in = W.d_jo;
         a.job_out = W.d_jo;
         a.in = W.rhs;
         a.out = W.phi64;
-        a.alpha = 1.0;
         a.done = nullptr;
         a.err = h->d_kerr;
         a.l2_ahead = l2_ahead(h);
@@ -578,7 +580,6 @@ int numeric_setup(algmortar_t* h) {
         sa.pf = gpf;
         sa.fwdS = W.gf;
         sa.bwdS = W.gb;
-        sa.alpha = 1.0;
         sa.err = h->d_kerr;
         sa.l2_ahead = l2_ahead(h);
         sa.deep_ring = h->opts.deep_ring;
@@ -614,7 +615,6 @@ int numeric_setup(algmortar_t* h) {
             ca.pf = cpf;
             ca.fwdS = W.cf;
             ca.bwdS = W.cb;
-            ca.alpha = 1.0;
             ca.err = h->d_kerr;
             ca.l2_ahead = l2_ahead(h);
             ca.deep_ring = h->opts.deep_ring;
@@ -682,13 +682,13 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs) 
     a.fwdS = h->d_fwdS;
     a.bwdS = h->d_bwdS;
     a.scale = h->d_sc;
+    a.scale32 = h->d_sc32;
     a.scale_off = h->d_sub_off;
     a.job_sub = h->d_job_sub;
     a.job_in = h->d_job_off;
     a.job_out = h->d_job_off;
     a.in = r;
     a.out = v.pbar;
-    a.alpha = 1.0;
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
@@ -707,11 +707,11 @@ void stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
     if (h->L > 0) launch_nd_solve(h->nd, v.beta, v.eta, v.P, cs, v.k, h->st);
 }
 
-// z = pbar + Phi eta, and r . z into rz[column] when rz is given.
+// z = pbar + Phi eta; inside PCG (sc given) also r . z and the next beta per column.
 template <typename TS>
-void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, double* rz) {
-    launch_prolong<TS>(h->n, h->d_row_sub, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list,
-                       h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, z, r, v.gs, rz, cs, v.k, h->st);
+void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, PcgScalars* sc) {
+    launch_prolong<TS>(h->m, h->P.max_k, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list,
+                       h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, z, r, v.gs, sc, cs, v.k, h->st);
 }
 
 template <typename TS, typename TA>
@@ -720,7 +720,7 @@ int apply_t(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
     TRY((stage_local<TS, TA>(h, v, r, cs)));
     stage_restrict(h, v, cs);
     stage_coarse(h, v, cs);
-    stage_prolong<PanelT<TS>>(h, v, r, z, cs, pcg ? &v.sc->rz_next : nullptr);
+    stage_prolong<PanelT<TS>>(h, v, r, z, cs, pcg ? v.sc : nullptr);
     CU(cudaGetLastError());
     return 0;
 }
@@ -785,7 +785,9 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     const size_t n = (size_t)h->n * cap;
     const size_t l = (size_t)std::max(h->L, 1) * cap;
     const int64_t np = h->P.nd_aoff.empty() ? 1 : std::max<int64_t>(h->P.nd_aoff.back(), 1);
-    const size_t nb = 2 * (size_t)vec_blocks(h->n) * cap;   // two sums per CTA (flexible beta)
+    // grid-sum partials: two per CTA (flexible beta) of the widest grid (vector kernels or
+    // one CTA per subdomain)
+    const size_t nb = 2 * (size_t)std::max(vec_blocks(h->n), h->m) * cap;
     v.x = h->alloc<double>(n);
     v.r = h->alloc<double>(n);
     v.z = h->alloc<double>(n);
@@ -1003,9 +1005,10 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     const int64_t n = h->n;
     h->d_dloc = h->alloc<double>(n);
     h->d_sc = h->alloc<double>(n);
+    h->d_sc32 = h->alloc<float>(n);
     h->d_scalar = h->alloc<double>(4);
     h->d_kerr = h->alloc<int>(1);
-    if (!h->d_dloc || !h->d_sc || !h->d_scalar || !h->d_kerr) return bail(fail(ALGMORTAR_OOM, "workspace"));
+    if (!h->d_dloc || !h->d_sc || !h->d_sc32 || !h->d_scalar || !h->d_kerr) return bail(fail(ALGMORTAR_OOM, "workspace"));
     rc = alloc_vecs(h, h->v1, 1);
     if (rc) return bail(rc);
     if (cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->st) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "memset"));
@@ -1250,7 +1253,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     live.rz = saved.rz != 0.0 ? saved.rz : 1.0;
     live.tol2 = 0.0;
     const ColStrides cs = col_strides(h, v, false);
-    double* rz = &v.sc->rz_next;
+    PcgScalars* rz = v.sc;
     if (h->opts.use_graph) TRY(ensure_graph(h, v));
     cudaEvent_t ev[8];
     for (auto& e : ev) CU(cudaEventCreate(&e));

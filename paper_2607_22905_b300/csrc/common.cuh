@@ -76,6 +76,8 @@ struct PcgScalars {
     int32_t max_it;
     int32_t flexible; // 1: Polak-Ribiere beta
     int32_t restart;  // 1: the residual was just replaced by b - A x; next beta = 0
+    int32_t step_ok;  // p . A p > 0 and alpha finite (set with alpha)
+    int32_t pad_;
 };
 
 // Column layout of a batch of right-hand sides processed by one launch (gridDim.y =

@@ -20,14 +20,14 @@ struct SolveArgs {
     Profile pf;
     const void* fwdS;          // forward sweep stream (TS)
     const void* bwdS;          // backward sweep stream (TS)
-    const double* scale;       // symmetric scaling per row, or null (= 1)
+    const double* scale;       // symmetric scaling per row, or null (= 1); FP64 solves
+    const float* scale32;      // the same scaling rounded to FP32 (FP32 / BF16 solves)
     const int64_t* scale_off;  // first scale entry of item s
     const int32_t* job_sub;    // item of each job
     const int64_t* job_in;     // offset of the job's input vector in `in`
     const int64_t* job_out;    // offset of the job's output vector in `out`
     const double* in;
     double* out;
-    double alpha;              // out = alpha * A_s^{-1} in
     const int32_t* done;       // early exit when *done != 0 (PCG), or null
     int* err;                  // set to 1 if a bulk copy never completed (bounded wait)
     const int32_t* job_t0;     // per job: tile row where the right-hand side starts (rows
@@ -123,7 +123,7 @@ cudaError_t prepare_nd_solve(int nsep);
 
 // local factor
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc, cudaStream_t st);
+                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc, float* sc32, cudaStream_t st);
 template <typename TW>
 void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                           const int32_t* row_sub, const int64_t* sub_off, const Profile& pf,
@@ -167,10 +167,9 @@ void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, doubl
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st);
 template <typename TP>
-void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
-                    const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
-                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, ColStrides cs,
-                    int ncols, cudaStream_t st);
+void launch_prolong(int m, int max_k, const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list,
+                    const int64_t* phi_off, const TP* phi, const double* eta, const double* pbar, double* z,
+                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st);
 void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,

@@ -16,7 +16,7 @@ namespace am {
 __global__ void k_local_diag(int64_t n, const int32_t* __restrict__ rowptr,
                              const int32_t* __restrict__ col, const double* __restrict__ val,
                              const int32_t* __restrict__ row_sub, int diag_scale,
-                             double* __restrict__ dloc, double* __restrict__ sc) {
+                             double* __restrict__ dloc, double* __restrict__ sc, float* __restrict__ sc32) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int32_t s = row_sub[k];
@@ -28,7 +28,9 @@ __global__ void k_local_diag(int64_t n, const int32_t* __restrict__ rowptr,
         }
         double dl = d - cross;
         dloc[k] = dl;
-        sc[k] = diag_scale ? 1.0 / sqrt(dl) : 1.0;
+        const double f = diag_scale ? 1.0 / sqrt(dl) : 1.0;
+        sc[k] = f;
+        sc32[k] = (float)f;
     }
 }
 
@@ -371,7 +373,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 // ---------------------------------------------------------------------------------
-// Batched triangular solves  out = alpha * S L^{-T} L^{-1} S in  for a list of jobs
+// Batched triangular solves  out = S L^{-T} L^{-1} S in  for a list of jobs
 // (item, input offset, output offset); S = diag(sc) is the symmetric scaling (or 1).
 //
 // One CTA of NW warps per job walks the tile rows in order (forward stream, then
@@ -479,6 +481,7 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
     const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
     const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
     const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
+    const float* sc32 = a.scale32 ? a.scale32 + a.scale_off[s] : nullptr;
     const double* in = a.in + a.job_in[job] + col * a.ldin;
     double* out = a.out + a.job_out[job] + col * a.ldout;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -514,7 +517,13 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
         lo_s[i] = pf.lo[r0 + i];
         hi_s[i] = pf.hi[r0 + i];
     }
-    for (int i = tid; i < T * TILE; i += NW * 32) v[i] = i < n ? (TA)(in[i] * (sc ? sc[i] : 1.0)) : (TA)0;
+    // scaling in the solve's arithmetic: FP32 solves scale in FP32 (B300's FP64 pipe is
+    // ~1/64 of FP32, so FP64 work per row is kept off the chain's prologue/epilogue)
+    if constexpr (sizeof(TA) == 4) {
+        for (int i = tid; i < T * TILE; i += NW * 32) v[i] = i < n ? (float)in[i] * (sc32 ? sc32[i] : 1.0f) : 0.0f;
+    } else {
+        for (int i = tid; i < T * TILE; i += NW * 32) v[i] = i < n ? in[i] * (sc ? sc[i] : 1.0) : 0.0;
+    }
     __syncthreads();
 
     bool ok = true;
@@ -592,7 +601,11 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
         return;
     }
     __syncthreads();
-    for (int i = tid; i < n; i += NW * 32) out[i] = a.alpha * (double)v[i] * (sc ? sc[i] : 1.0);
+    if constexpr (sizeof(TA) == 4) {
+        for (int i = tid; i < n; i += NW * 32) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
+    } else {
+        for (int i = tid; i < n; i += NW * 32) out[i] = v[i] * (sc ? sc[i] : 1.0);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -701,10 +714,10 @@ static inline int grid_for(int64_t n, int bs) {
 }
 
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc,
+                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc, float* sc32,
                        cudaStream_t st) {
     count_launch();
-    k_local_diag<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, diag_scale, dloc, sc);
+    k_local_diag<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, diag_scale, dloc, sc, sc32);
 }
 
 template <typename TW>

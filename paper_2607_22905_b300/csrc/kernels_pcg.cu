@@ -72,46 +72,66 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     if (lane == 0) beta[omap ? omap[I] : I] = s;
 }
 
-// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg), one row
-// per thread; with `rz` given, also the grid-wide r . z.
+// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg) for the
+// rows k of subdomain i = blockIdx.x; inside PCG (`psc` given) also rho = r . z and, in
+// the CTA that completes it, the next beta (one thread: scalar FP64 division stays off
+// the per-row path, B300's FP64 pipe being ~1/64 of its FP32 rate).  The CTA
+// stages the subdomain's k_i interface values eta_m in shared memory once, then each
+// thread walks its rows with k_i independent, coalesced panel loads (column-major panel:
+// a warp reads 32 consecutive rows of one column).
 template <typename TP>
-__global__ void __launch_bounds__(VEC_BS) k_prolong(int64_t n, const int32_t* __restrict__ row_sub,
-                                                     const int64_t* __restrict__ sub_off,
+__global__ void __launch_bounds__(VEC_BS) k_prolong(const int64_t* __restrict__ sub_off,
                                                      const int64_t* __restrict__ if_off,
                                                      const int32_t* __restrict__ if_list,
                                                      const int64_t* __restrict__ phi_off,
                                                      const TP* __restrict__ phi, const double* __restrict__ eta,
                                                      const double* __restrict__ pbar, double* __restrict__ z,
-                                                     const double* __restrict__ r, GridSum gs, double* rz,
-                                                     ColStrides cs) {
+                                                     const double* __restrict__ r, GridSum gs,
+                                                     PcgScalars* psc, ColStrides cs) {
+    // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
+    // (FP64 panels: FP64; FP32 panels: FP32), then added to pbar in FP64
+    using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     __shared__ double sh[32];
+    extern __shared__ unsigned char e_raw[];
+    TA* e = reinterpret_cast<TA*>(e_raw);
     eta += col * cs.l;
     pbar += col * cs.v;
     z += col * cs.v;
     if (r) r += col * cs.v;
-    if (rz) rz += col * cs.sc_stride;
+    if (psc) psc += col;
     gs.part += col * gridDim.x;
     gs.ticket += col;
-    // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
-    // (FP64 panels: FP64; FP32/BF16 panels: FP32), then added to pbar in FP64
-    using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
+    const int s = blockIdx.x;
+    const int64_t a0 = sub_off[s];
+    const int ns = (int)(sub_off[s + 1] - a0);
+    const int64_t i0 = if_off[s];
+    const int kk = (int)(if_off[s + 1] - i0);
+    for (int c = threadIdx.x; c < kk; c += blockDim.x) e[c] = (TA)eta[if_list[i0 + c]];
+    __syncthreads();
+    const TP* ph = phi + phi_off[s];
     double acc = 0.0;
-    GRID_STRIDE(k, n) {
-        const int32_t s = row_sub[k];
-        const int64_t a = sub_off[s];
-        const int64_t ns = sub_off[s + 1] - a;
-        const int64_t i0 = if_off[s];
-        const int kk = (int)(if_off[s + 1] - i0);
-        const TP* ph = phi + phi_off[s] + (k - a);
-        TA corr = 0;
-        for (int c = 0; c < kk; ++c) corr += ldf<TA>(ph + c * ns) * (TA)__ldg(eta + __ldg(if_list + i0 + c));
-        const double v = pbar[k] + (double)corr;
-        z[k] = v;
-        if (rz) acc += r[k] * v;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        TA c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        int c = 0;
+        for (; c + 4 <= kk; c += 4) {
+            c0 += ldf<TA>(ph + (int64_t)c * ns + i) * e[c];
+            c1 += ldf<TA>(ph + (int64_t)(c + 1) * ns + i) * e[c + 1];
+            c2 += ldf<TA>(ph + (int64_t)(c + 2) * ns + i) * e[c + 2];
+            c3 += ldf<TA>(ph + (int64_t)(c + 3) * ns + i) * e[c + 3];
+        }
+        for (; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns + i) * e[c];
+        const double v = pbar[a0 + i] + (double)((c0 + c1) + (c2 + c3));
+        z[a0 + i] = v;
+        if (psc) acc += r[a0 + i] * v;
     }
-    if (rz) grid_sum(acc, sh, gs, rz);
+    if (psc && grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
+        const double rn = psc->rz_next;
+        psc->beta = (psc->iter == 0 || psc->restart)
+                        ? 0.0
+                        : (psc->flexible ? (rn - psc->rz_mix) / psc->rz : rn / psc->rz);
+    }
 }
 
 // ------------------------------------------------------------------------------ PCG
@@ -153,10 +173,10 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
     }
 }
 
-// p = z + beta p with beta = rho_new / rho (Fletcher-Reeves form of CG), or with the
-// flexible (Polak-Ribiere) beta = (rho_new - r_new . z_old) / rho, which tolerates a
-// slightly non-symmetric preconditioner; beta = 0 on the first iteration and right after
-// a residual replacement.
+// p = z + beta p; beta (set where rho_new is completed, in the prolongation) is
+// rho_new / rho (Fletcher-Reeves form of CG) or the flexible (Polak-Ribiere)
+// (rho_new - r_new . z_old) / rho, which tolerates a slightly non-symmetric
+// preconditioner; 0 on the first iteration and right after a residual replacement.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                                                    int64_t ld, const PcgScalars* __restrict__ sc) {
     const int col = blockIdx.y;
@@ -164,15 +184,14 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __res
     if (sc->done) return;
     z += col * ld;
     p += col * ld;
-    const double beta = (sc->iter == 0 || sc->restart)
-                            ? 0.0
-                            : (sc->flexible ? (sc->rz_next - sc->rz_mix) / sc->rz : sc->rz_next / sc->rz);
+    const double beta = sc->beta;
     GRID_STRIDE(k, n) p[k] = z[k] + beta * p[k];
 }
 
 // q = A p on the sliced-ELL copy (one thread per row; a warp is one 32-row slice, so each
-// load of values / columns is one contiguous segment) and p . q -> sc->pq.  CTA 0 moves
-// rho to the new direction's value (read by the following kernels only).
+// load of values / columns is one contiguous segment) and p . q -> sc->pq; the CTA that
+// completes p . q sets alpha = rho / p . q once.  CTA 0 moves rho to the new direction's
+// value (read by the following kernels only).
 __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
                                                           const int32_t* __restrict__ ell_col,
                                                           const double* __restrict__ ell_val,
@@ -213,17 +232,19 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
         q[k] = s;
         acc += p[k] * s;
     }
-    grid_sum(acc, sh, gs, &sc->pq);
+    if (grid_sum(acc, sh, gs, &sc->pq) && threadIdx.x == 0) {
+        const double pq = sc->pq, al = sc->rz_next / pq;
+        sc->alpha = al;
+        sc->step_ok = (pq > 0.0 && isfinite(al)) ? 1 : 0;
+    }
 }
 
 // Stop test on the device (breakdown, convergence, iteration cap), run by the thread that
 // completes ||r||^2.
 __device__ __forceinline__ void pcg_stop_test(PcgScalars* sc) {
     sc->iter += 1;
-    const double pq = sc->pq, rr = sc->rr_new;
-    const double al = sc->rz / pq;
-    sc->alpha = al;
-    if (!(pq > 0.0) || !isfinite(al) || !isfinite(rr)) {
+    const double rr = sc->rr_new;
+    if (!sc->step_ok || !isfinite(rr)) {
         sc->done = 1;
         sc->status = 6;
     } else {
@@ -238,7 +259,7 @@ __device__ __forceinline__ void pcg_stop_test(PcgScalars* sc) {
     }
 }
 
-// alpha = rho / (p . q);  x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new (and, for
+// x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new (and, for
 // the flexible beta, r_new . z_old -> sc->rz_mix, z still holding z_old), then the stop
 // test.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
@@ -257,9 +278,8 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
     const bool flex = sc->flexible != 0;
     gs.part += col * (flex ? 2 : 1) * gridDim.x;
     gs.ticket += col;
-    const double pq = sc->pq;
-    const double al = sc->rz / pq;
-    const bool ok = pq > 0.0 && isfinite(al);
+    const double al = sc->alpha;
+    const bool ok = sc->step_ok != 0;
     double acc = 0.0, acc2 = 0.0;
     GRID_STRIDE(k, n) {
         double rk = r[k];
@@ -401,13 +421,13 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
     }
 }
 template <typename TP>
-void launch_prolong(int64_t n, const int32_t* row_sub, const int64_t* sub_off, const int64_t* if_off,
-                    const int32_t* if_list, const int64_t* phi_off, const TP* phi, const double* eta,
-                    const double* pbar, double* z, const double* r, GridSum gs, double* rz, ColStrides cs,
-                    int ncols, cudaStream_t st) {
+void launch_prolong(int m, int max_k, const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list,
+                    const int64_t* phi_off, const TP* phi, const double* eta, const double* pbar, double* z,
+                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
+    using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     count_launch();
-    k_prolong<TP><<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, row_sub, sub_off, if_off, if_list, phi_off, phi,
-                                                                 eta, pbar, z, r, gs, rz, cs);
+    k_prolong<TP><<<dim3(m, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
+        sub_off, if_off, if_list, phi_off, phi, eta, pbar, z, r, gs, sc, cs);
 }
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st) {
@@ -453,11 +473,10 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
 }
 
 #define INST_PROLONG(TP)                                                                                     \
-    template void launch_prolong<TP>(int64_t, const int32_t*, const int64_t*, const int64_t*, const int32_t*,     \
-                                     const int64_t*, const TP*, const double*, const double*, double*,            \
-                                     const double*, GridSum, double*, ColStrides, int, cudaStream_t);
+    template void launch_prolong<TP>(int, int, const int64_t*, const int64_t*, const int32_t*, const int64_t*,   \
+                                     const TP*, const double*, const double*, double*, const double*, GridSum,    \
+                                     PcgScalars*, ColStrides, int, cudaStream_t);
 INST_PROLONG(double)
 INST_PROLONG(float)
-INST_PROLONG(__nv_bfloat16)
 
 }  // namespace am
