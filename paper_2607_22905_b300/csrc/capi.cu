@@ -116,6 +116,8 @@ struct algmortar_handle {
     int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_perm = nullptr, *d_row_sub = nullptr;
     double* d_val = nullptr;
     int64_t* d_sub_off = nullptr;
+    int nchunks = 0;                   // prolongation: row chunks (<= VEC_BS rows of one subdomain)
+    int32_t *d_chunk_sub = nullptr, *d_chunk_off = nullptr;
     // local factor profile and streams
     Profile pf{};
     int32_t *d_rows = nullptr, *d_ntiles = nullptr;
@@ -710,8 +712,9 @@ void stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
 // z = pbar + Phi eta; inside PCG (sc given) also r . z and the next beta per column.
 template <typename TS>
 void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, PcgScalars* sc) {
-    launch_prolong<TS>(h->m, h->P.max_k, h->d_sub_off, h->d_if_off, h->L > 0 ? h->d_ifpos : h->d_if_list,
-                       h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, z, r, v.gs, sc, cs, v.k, h->st);
+    launch_prolong<TS>(h->nchunks, h->d_chunk_sub, h->d_chunk_off, h->P.max_k, h->d_sub_off, h->d_if_off,
+                       h->L > 0 ? h->d_ifpos : h->d_if_list, h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, z, r,
+                       v.gs, sc, cs, v.k, h->st);
 }
 
 template <typename TS, typename TA>
@@ -786,8 +789,8 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     const size_t l = (size_t)std::max(h->L, 1) * cap;
     const int64_t np = h->P.nd_aoff.empty() ? 1 : std::max<int64_t>(h->P.nd_aoff.back(), 1);
     // grid-sum partials: two per CTA (flexible beta) of the widest grid (vector kernels or
-    // one CTA per subdomain)
-    const size_t nb = 2 * (size_t)std::max(vec_blocks(h->n), h->m) * cap;
+    // one CTA per row chunk of a subdomain)
+    const size_t nb = 2 * (size_t)std::max(vec_blocks(h->n), h->nchunks) * cap;
     v.x = h->alloc<double>(n);
     v.r = h->alloc<double>(n);
     v.z = h->alloc<double>(n);
@@ -965,6 +968,17 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     rc = rc ? rc : upload(h, h->d_perm, P.perm);
     rc = rc ? rc : upload(h, h->d_row_sub, P.row_sub);
     rc = rc ? rc : upload(h, h->d_sub_off, P.sub_off);
+    {
+        std::vector<int32_t> cs, co;
+        for (int s = 0; s < P.m; ++s)
+            for (int64_t o = 0; o < P.sub_off[s + 1] - P.sub_off[s]; o += VEC_BS) {
+                cs.push_back(s);
+                co.push_back((int32_t)o);
+            }
+        h->nchunks = (int)cs.size();
+        rc = rc ? rc : upload(h, h->d_chunk_sub, cs);
+        rc = rc ? rc : upload(h, h->d_chunk_off, co);
+    }
     rc = rc ? rc : upload(h, h->d_rows, rows);
     rc = rc ? rc : upload(h, h->d_ntiles, P.ntiles);
     rc = rc ? rc : upload(h, d_row0, P.trow_off);

@@ -167,9 +167,10 @@ void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, doubl
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st);
 template <typename TP>
-void launch_prolong(int m, int max_k, const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list,
-                    const int64_t* phi_off, const TP* phi, const double* eta, const double* pbar, double* z,
-                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
+void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
+                    const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,
+                    const TP* phi, const double* eta, const double* pbar, double* z, const double* r, GridSum gs,
+                    PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st);
 void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,

@@ -72,15 +72,18 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     if (lane == 0) beta[omap ? omap[I] : I] = s;
 }
 
-// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg) for the
-// rows k of subdomain i = blockIdx.x; inside PCG (`psc` given) also rho = r . z and, in
-// the CTA that completes it, the next beta (one thread: scalar FP64 division stays off
-// the per-row path, B300's FP64 pipe being ~1/64 of its FP32 rate).  The CTA
-// stages the subdomain's k_i interface values eta_m in shared memory once, then each
-// thread walks its rows with k_i independent, coalesced panel loads (column-major panel:
-// a warp reads 32 consecutive rows of one column).
+// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg), one CTA
+// per chunk of up to VEC_BS rows of one subdomain i (chunk_sub / chunk_off), one row per
+// thread.  The CTA stages the subdomain's k_i interface values eta_m in shared memory;
+// each thread then issues its k_i panel loads (column-major panel: a warp reads 32
+// consecutive rows of one column) with no dependent index loads.  Inside PCG (`psc`
+// given) also rho = r . z and, in the CTA that completes it, the next beta (one thread:
+// scalar FP64 divisions stay off the per-row path, B300's FP64 pipe being ~1/64 of its
+// FP32 rate).
 template <typename TP>
-__global__ void __launch_bounds__(VEC_BS) k_prolong(const int64_t* __restrict__ sub_off,
+__global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ chunk_sub,
+                                                     const int32_t* __restrict__ chunk_off,
+                                                     const int64_t* __restrict__ sub_off,
                                                      const int64_t* __restrict__ if_off,
                                                      const int32_t* __restrict__ if_list,
                                                      const int64_t* __restrict__ phi_off,
@@ -103,28 +106,29 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int64_t* __restrict__ 
     if (psc) psc += col;
     gs.part += col * gridDim.x;
     gs.ticket += col;
-    const int s = blockIdx.x;
+    const int s = chunk_sub[blockIdx.x];
     const int64_t a0 = sub_off[s];
     const int ns = (int)(sub_off[s + 1] - a0);
     const int64_t i0 = if_off[s];
     const int kk = (int)(if_off[s + 1] - i0);
     for (int c = threadIdx.x; c < kk; c += blockDim.x) e[c] = (TA)eta[if_list[i0 + c]];
     __syncthreads();
-    const TP* ph = phi + phi_off[s];
+    const int i = chunk_off[blockIdx.x] + threadIdx.x;
     double acc = 0.0;
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    if (i < ns) {
+        const TP* ph = phi + phi_off[s] + i;
         TA c0 = 0, c1 = 0, c2 = 0, c3 = 0;
         int c = 0;
         for (; c + 4 <= kk; c += 4) {
-            c0 += ldf<TA>(ph + (int64_t)c * ns + i) * e[c];
-            c1 += ldf<TA>(ph + (int64_t)(c + 1) * ns + i) * e[c + 1];
-            c2 += ldf<TA>(ph + (int64_t)(c + 2) * ns + i) * e[c + 2];
-            c3 += ldf<TA>(ph + (int64_t)(c + 3) * ns + i) * e[c + 3];
+            c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
+            c1 += ldf<TA>(ph + (int64_t)(c + 1) * ns) * e[c + 1];
+            c2 += ldf<TA>(ph + (int64_t)(c + 2) * ns) * e[c + 2];
+            c3 += ldf<TA>(ph + (int64_t)(c + 3) * ns) * e[c + 3];
         }
-        for (; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns + i) * e[c];
+        for (; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
         const double v = pbar[a0 + i] + (double)((c0 + c1) + (c2 + c3));
         z[a0 + i] = v;
-        if (psc) acc += r[a0 + i] * v;
+        if (psc) acc = r[a0 + i] * v;
     }
     if (psc && grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
         const double rn = psc->rz_next;
@@ -421,13 +425,14 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
     }
 }
 template <typename TP>
-void launch_prolong(int m, int max_k, const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list,
-                    const int64_t* phi_off, const TP* phi, const double* eta, const double* pbar, double* z,
-                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
+void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
+                    const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,
+                    const TP* phi, const double* eta, const double* pbar, double* z, const double* r, GridSum gs,
+                    PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     count_launch();
-    k_prolong<TP><<<dim3(m, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
-        sub_off, if_off, if_list, phi_off, phi, eta, pbar, z, r, gs, sc, cs);
+    k_prolong<TP><<<dim3(nchunks, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
+        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, z, r, gs, sc, cs);
 }
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st) {
@@ -473,9 +478,9 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
 }
 
 #define INST_PROLONG(TP)                                                                                     \
-    template void launch_prolong<TP>(int, int, const int64_t*, const int64_t*, const int32_t*, const int64_t*,   \
-                                     const TP*, const double*, const double*, double*, const double*, GridSum,    \
-                                     PcgScalars*, ColStrides, int, cudaStream_t);
+    template void launch_prolong<TP>(int, const int32_t*, const int32_t*, int, const int64_t*, const int64_t*,    \
+                                     const int32_t*, const int64_t*, const TP*, const double*, const double*,     \
+                                     double*, const double*, GridSum, PcgScalars*, ColStrides, int, cudaStream_t);
 INST_PROLONG(double)
 INST_PROLONG(float)
 
