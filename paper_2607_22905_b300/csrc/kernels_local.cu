@@ -365,6 +365,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 constexpr long long kWaitLimit = 1ll << 22;   // try_wait rounds before a wait is declared stuck
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     for (long long i = 0; i < kWaitLimit; ++i)
@@ -376,16 +379,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // Batched triangular solves  out = S L^{-T} L^{-1} S in  for a list of jobs
 // (item, input offset, output offset); S = diag(sc) is the symmetric scaling (or 1).
 //
-// One CTA of NW warps per job walks the tile rows in order (forward stream, then
-// backward stream).  The item's tiles are consumed strictly in storage order, so they are
-// streamed through an R-slot shared-memory ring by bulk async copies (one 32x32 tile per
-// copy, completion on a per-slot mbarrier); a slot is refilled as soon as its tile has
-// been read, so R tiles are always in flight.  Step for tile row I:
-//   each warp takes every NW-th off-diagonal tile and forms its partial sum_J T_IJ v_J
-//   (lane = tile row, 128-bit shared loads of the swizzled row and of v_J);
-//   one named barrier; every warp then reduces the partials and applies the stored
-//   inverse diagonal tile itself (identical results, so no second barrier is needed);
-//   the diagonal slot is refilled after the next step's barrier, when all warps are done.
+// One CTA per job walks the tile rows in order (forward stream, then backward stream).
+// The item's tiles are consumed strictly in storage order, so a producer warp streams
+// them through an R-slot shared-memory ring by bulk async copies (one 32x32 tile per
+// copy, completion on full[slot]) and reloads a slot as soon as the consumer warp that
+// read its tile releases it (empty[slot]).  NW consumer warps form, per tile row I, the
+// partial sums sum_J T_IJ v_J (lane = tile row, 128-bit shared loads of the swizzled row
+// and of v_J), meet at one named barrier, and warp 0 applies the stored inverse diagonal
+// tile.  Measured on B300 (clock64 probes): with every warp issuing its own refills and
+// every warp repeating the diagonal product, a step took ~2300-3600 cycles, a quarter
+// of it in the refill path.
 // ---------------------------------------------------------------------------------
 template <typename TS, typename TA>
 __device__ __forceinline__ TA row_dot(const TS* tile, int lane, const TA* v);
@@ -460,7 +463,7 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 }
 
 template <typename TS, typename TA, int R, int NW>
-__global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
+__global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
     // batched solves put the column in blockIdx.x, so the CTAs of one subdomain's columns
     // run side by side and share its factor stream through L2
     const int col = a.col_fast ? blockIdx.x : 0;
@@ -489,122 +492,142 @@ __global__ void __launch_bounds__(NW * 32) k_chain_solve(SolveArgs a) {
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TS* ring = reinterpret_cast<TS*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
-    TA* part = reinterpret_cast<TA*>(smem_raw + R * TB + R * sizeof(uint64_t));   // [2][NW][32]
-    TA* tbuf = part + 2 * NW * TILE;                                                // [NW][32]
-    int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + NW * TILE);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
+    uint64_t* empty = full + R;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + R);
+    int64_t* issued = reinterpret_cast<int64_t*>(empty + R + 1);
+    TA* part = reinterpret_cast<TA*>(empty + R + 2);   // [2][NW][32]
+    TA* tbuf = part + 2 * NW * TILE;                    // [32] (warp 0)
+    int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + TILE);
     int32_t* hi_s = lo_s + T;
-    TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));                        // 16-byte aligned
+    TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));   // 16-byte aligned
     auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
-    // ring slot and mbarrier phase of stream position q (counted from q0)
-    auto slot_of = [&](int64_t q) { return (int)((q - q0) % R); };
-    auto parity_of = [&](int64_t q) { return (uint32_t)(((q - q0) / R) & 1); };
     if (tid == 0) {
-        for (int i = 0; i < R; ++i) mbar_init(smem_u32(&bars[i]), 1);
-        fence_async_smem();
-        for (int64_t q = q0; q < q0 + R && q < qend; ++q)
-            tma_load_1d(smem_u32(ring + slot_of(q) * TILE2), src(q), TB, smem_u32(&bars[slot_of(q)]));
-        // L2 prefetch window [q0 + R, q0 + R + ahead): contiguous within each stream
-        const int64_t p0 = q0 + R, p1 = min(q0 + R + (int64_t)a.l2_ahead, qend);
-        if (p0 < p1) {
-            const int64_t f1 = min(p1, nts);
-            if (p0 < f1) l2_prefetch(src(p0), (uint32_t)((f1 - p0) * TB));
-            const int64_t b0 = max(p0, nts);
-            if (b0 < p1) l2_prefetch(src(b0), (uint32_t)((p1 - b0) * TB));
+        for (int i = 0; i < R; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
         }
+        *abort_flag = 0;
+        *issued = q0;
+        fence_async_smem();
     }
-    for (int i = tid; i < T; i += NW * 32) {
+    for (int i = tid; i < T; i += (NW + 1) * 32) {
         lo_s[i] = pf.lo[r0 + i];
         hi_s[i] = pf.hi[r0 + i];
     }
     // scaling in the solve's arithmetic: FP32 solves scale in FP32 (B300's FP64 pipe is
     // ~1/64 of FP32, so FP64 work per row is kept off the chain's prologue/epilogue)
     if constexpr (sizeof(TA) == 4) {
-        for (int i = tid; i < T * TILE; i += NW * 32) v[i] = i < n ? (float)in[i] * (sc32 ? sc32[i] : 1.0f) : 0.0f;
+        for (int i = tid; i < T * TILE; i += (NW + 1) * 32)
+            v[i] = i < n ? (float)in[i] * (sc32 ? sc32[i] : 1.0f) : 0.0f;
     } else {
-        for (int i = tid; i < T * TILE; i += NW * 32) v[i] = i < n ? in[i] * (sc ? sc[i] : 1.0) : 0.0;
+        for (int i = tid; i < T * TILE; i += (NW + 1) * 32) v[i] = i < n ? in[i] * (sc ? sc[i] : 1.0) : 0.0;
     }
     __syncthreads();
 
-    bool ok = true;
-    auto wait_tile = [&](int64_t qq) -> const TS* {
-        const int slot = slot_of(qq);
-        if (ok) ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[slot]), parity_of(qq)));
-        return ring + slot * TILE2;
-    };
-    auto refill = [&](int64_t qq) {   // tile qq has been read by every consumer: load qq + R
-        if (ok && qq + R < qend) {
-            const int slot = slot_of(qq);
-            fence_async_smem();
-            tma_load_1d(smem_u32(ring + slot * TILE2), src(qq + R), TB, smem_u32(&bars[slot]));
-            const int64_t qp = qq + R + a.l2_ahead;   // keep the L2 window `l2_ahead` tiles deep
-            if (a.l2_ahead > 0 && qp < qend) l2_prefetch(src(qp), TB);
+    if (w == NW) {
+        // Producer warp: one lane streams the tiles through the ring in storage order.  A
+        // slot is reloaded once its previous tile has been released by the warp that read
+        // it (one arrival per use on empty[slot]).
+        if (lane == 0) {
+            int64_t q = q0;
+            for (; q < qend; ++q) {
+                const int slot = (int)((q - q0) % R);
+                const int64_t u = (q - q0) / R;
+                if (u > 0 && (*abort_flag || !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((u - 1) & 1)))) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tma_load_1d(smem_u32(ring + slot * TILE2), src(q), TB, smem_u32(&full[slot]));
+                const int64_t qp = q + a.l2_ahead;   // optional L2 window ahead of the ring
+                if (a.l2_ahead > 0 && qp < qend) l2_prefetch(src(qp), TB);
+            }
+            *issued = q;
         }
-    };
-    int64_t q = q0;
-    int64_t pending_diag = -1;      // diagonal tile whose slot is released at the next barrier
-    int par = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int step = t0; step < T; ++step) {
-            const int I = pass == 0 ? step : T - 1 - (step - t0);
-            const int j0 = pass == 0 ? lo_s[I] : I + 1;
-            const int nt = pass == 0 ? I - lo_s[I] : hi_s[I] - I;
-            // off-diagonal tiles of the next step (the first backward step has none)
-            const int nt_next = pass == 0 ? (step + 1 < T ? (I + 1) - lo_s[I + 1] : 0)
-                                          : (step + 1 < T ? hi_s[I - 1] - (I - 1) : 0);
-            TA* vi = v + I * TILE;
-            const TA rhs = vi[lane];    // read before the barrier: vi is overwritten after it
-            TA acc = 0;
-            for (int t = w; t < nt; t += NW) {
-                const TS* tl = wait_tile(q + t);
-                acc += row_dot<TS, TA>(tl, lane, v + (j0 + t) * TILE);
-                __syncwarp();
-                if (lane == 0) refill(q + t);
+    } else {
+        // Consumer warps.  Step for tile row I: warp 0 takes the off-diagonal tile nearest
+        // the diagonal (it needs the row solved in the previous step, which warp 0 itself
+        // produced), warps 1..NW-1 share the others (they need only rows solved at least
+        // two steps back, ordered by the previous step's barrier), one named barrier, then
+        // warp 0 alone reduces the partial sums and applies the stored inverse diagonal
+        // tile.  Every tile is read by exactly one warp, which releases it at once.
+        auto wait_full = [&](int64_t qq) -> const TS* {
+            const int slot = (int)((qq - q0) % R);
+            if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
+                const bool r = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full[slot]), (uint32_t)(((qq - q0) / R) & 1)));
+                if (!r && lane == 0) *abort_flag = 1;
             }
-            part[(par * NW + w) * TILE + lane] = acc;
-            if (NW > 1) named_barrier(1, NW * 32);
-            else __syncwarp();
-            if (tid == 0 && pending_diag >= 0) refill(pending_diag);
-            const TS* D = wait_tile(q + nt);
-            TA sum = 0;
-#pragma unroll
-            for (int u = 0; u < NW; ++u) sum += part[(par * NW + u) * TILE + lane];
-            // y = D t: t goes through this warp's own shared buffer so that row `lane` of
-            // D and t are both read with 128-bit loads (row_dot)
-            TA* tw = tbuf + w * TILE;
-            tw[lane] = rhs - sum;
+            return ring + slot * TILE2;
+        };
+        auto release = [&](int64_t qq) {
             __syncwarp();
-            const TA y = row_dot<TS, TA>(D, lane, tw);
-            vi[lane] = y;               // every warp writes the same values
-            // The diagonal slot may only be refilled once every warp has read it.  If the
-            // next row needs R or more tiles before its barrier, the refill cannot wait
-            // for that barrier (a warp could then wait on the refilled tile): release now.
-            if (nt_next >= R) {
-                if (NW > 1) named_barrier(1, NW * 32);
-                else __syncwarp();
-                if (tid == 0) refill(q + nt);
-                pending_diag = -1;
-            } else {
-                __syncwarp();
-                pending_diag = q + nt;
+            if (lane == 0) mbar_arrive(smem_u32(&empty[(qq - q0) % R]));
+        };
+        int64_t q = q0;
+        int par = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int step = t0; step < T; ++step) {
+                const int I = pass == 0 ? step : T - 1 - (step - t0);
+                const int j0 = pass == 0 ? lo_s[I] : I + 1;
+                const int nt = pass == 0 ? I - lo_s[I] : hi_s[I] - I;
+                TA acc = 0;
+                if (w == 0) {
+                    if (nt > 0) {
+                        const int tn = pass == 0 ? nt - 1 : 0;   // J = I - 1 / J = I + 1
+                        const TS* tl = wait_full(q + tn);
+                        acc = row_dot<TS, TA>(tl, lane, v + (j0 + tn) * TILE);
+                        release(q + tn);
+                    }
+                } else {
+                    for (int k = w - 1; k < nt - 1; k += NW - 1) {
+                        const int t = pass == 0 ? k : k + 1;
+                        const TS* tl = wait_full(q + t);
+                        acc += row_dot<TS, TA>(tl, lane, v + (j0 + t) * TILE);
+                        release(q + t);
+                    }
+                }
+                part[(par * NW + w) * TILE + lane] = acc;
+                named_barrier(1, NW * 32);
+                if (w == 0) {
+                    TA* vi = v + I * TILE;
+                    TA sum = 0;
+#pragma unroll
+                    for (int u = 0; u < NW; ++u) sum += part[(par * NW + u) * TILE + lane];
+                    // y = D t: t goes through shared memory so that row `lane` of D and t
+                    // are both read with 128-bit loads (row_dot)
+                    tbuf[lane] = vi[lane] - sum;
+                    __syncwarp();
+                    const TS* D = wait_full(q + nt);
+                    const TA y = row_dot<TS, TA>(D, lane, tbuf);
+                    release(q + nt);
+                    vi[lane] = y;
+                    __syncwarp();
+                }
+                q += nt + 1;
+                par ^= 1;
             }
-            q += nt + 1;
-            par ^= 1;
         }
     }
-    if (!ok) {
+    __syncthreads();
+    if (*abort_flag) {
         if (tid == 0) {
             atomicExch(a.err, 1);
-            for (int64_t qq = q; qq < qend && qq < q + R; ++qq) mbar_wait(smem_u32(&bars[slot_of(qq)]), parity_of(qq));
+            // only the last use of a slot can still be in flight (a reload waits for the
+            // release of the previous use, which follows its arrival): drain those
+            const int64_t last = *issued - 1;
+            for (int sl = 0; sl < R; ++sl) {
+                if (last - q0 < sl) continue;
+                const int64_t u = (last - q0 - sl) / R;
+                mbar_wait(smem_u32(&full[sl]), (uint32_t)(u & 1));
+            }
         }
         __syncthreads();
         return;
     }
-    __syncthreads();
     if constexpr (sizeof(TA) == 4) {
-        for (int i = tid; i < n; i += NW * 32) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
+        for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
     } else {
-        for (int i = tid; i < n; i += NW * 32) out[i] = v[i] * (sc ? sc[i] : 1.0);
+        for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = v[i] * (sc ? sc[i] : 1.0);
     }
 }
 
@@ -774,9 +797,10 @@ constexpr int ring_slots() {
 
 template <typename TS, typename TA, int R>
 static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
-    constexpr int NW = 4;
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + R * sizeof(uint64_t) + 3 * NW * TILE * sizeof(TA) +
-                  (size_t)(2 * max_tiles + 4) * sizeof(int32_t) + (size_t)max_tiles * TILE * sizeof(TA) + 16;
+    constexpr int NW = 4;   // consumer warps (+ 1 producer warp)
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (2 * R + 2) * sizeof(uint64_t) +
+                  (2 * NW + 1) * TILE * sizeof(TA) + (size_t)(2 * max_tiles + 4) * sizeof(int32_t) +
+                  (size_t)max_tiles * TILE * sizeof(TA) + 16;
     cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -785,7 +809,7 @@ static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cud
         SolveArgs b = a;
         b.col_fast = ncols > 1;
         const dim3 grid = ncols > 1 ? dim3(ncols, njobs) : dim3(njobs);
-        k_chain_solve<TS, TA, R, NW><<<grid, NW * 32, smem, st>>>(b);
+        k_chain_solve<TS, TA, R, NW><<<grid, (NW + 1) * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
 }
