@@ -496,7 +496,12 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
     uint64_t* empty = full + R;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + R);
     int64_t* issued = reinterpret_cast<int64_t*>(empty + R + 1);
-    TA* part = reinterpret_cast<TA*>(empty + R + 2);   // [2][NW][32]
+    // stream position whose copy was last issued into each slot: a consumer waits for its
+    // own position here before the mbarrier, because tiles are released out of order (by
+    // different warps) and a parity wait cannot tell "use u + 1 landed" from "use u not
+    // landed yet"
+    volatile int64_t* slot_q = reinterpret_cast<volatile int64_t*>(empty + R + 2);
+    TA* part = reinterpret_cast<TA*>(empty + 2 * R + 2);   // [2][NW][32]
     TA* tbuf = part + 2 * NW * TILE;                    // [32] (warp 0)
     int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + TILE);
     int32_t* hi_s = lo_s + T;
@@ -509,6 +514,7 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
         }
         *abort_flag = 0;
         *issued = q0;
+        for (int i = 0; i < R; ++i) slot_q[i] = -1;
         fence_async_smem();
     }
     for (int i = tid; i < T; i += (NW + 1) * 32) {
@@ -538,6 +544,7 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
                     *abort_flag = 1;
                     break;
                 }
+                slot_q[slot] = q;
                 tma_load_1d(smem_u32(ring + slot * TILE2), src(q), TB, smem_u32(&full[slot]));
                 const int64_t qp = q + a.l2_ahead;   // optional L2 window ahead of the ring
                 if (a.l2_ahead > 0 && qp < qend) l2_prefetch(src(qp), TB);
@@ -554,7 +561,14 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
         auto wait_full = [&](int64_t qq) -> const TS* {
             const int slot = (int)((qq - q0) % R);
             if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
-                const bool r = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full[slot]), (uint32_t)(((qq - q0) / R) & 1)));
+                bool r = false;
+                for (long long i = 0; i < kWaitLimit; ++i)
+                    if (slot_q[slot] == qq) {
+                        r = true;
+                        break;
+                    }
+                r = r && mbar_wait(smem_u32(&full[slot]), (uint32_t)(((qq - q0) / R) & 1));
+                r = __all_sync(0xffffffffu, r);
                 if (!r && lane == 0) *abort_flag = 1;
             }
             return ring + slot * TILE2;
@@ -798,7 +812,7 @@ constexpr int ring_slots() {
 template <typename TS, typename TA, int R>
 static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int NW = 4;   // consumer warps (+ 1 producer warp)
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (2 * R + 2) * sizeof(uint64_t) +
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * R + 2) * sizeof(uint64_t) +
                   (2 * NW + 1) * TILE * sizeof(TA) + (size_t)(2 * max_tiles + 4) * sizeof(int32_t) +
                   (size_t)max_tiles * TILE * sizeof(TA) + 16;
     cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
