@@ -350,6 +350,15 @@ __device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint3
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
 // Asynchronous prefetch of a global range into L2 (no completion tracking): the chain
 // solves run it ahead of their shared-memory ring, so the ring's bulk copies are served
 // from L2 and the ring depth no longer caps a CTA's bytes in flight at HBM latency.
@@ -364,6 +373,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+// Non-blocking probe of a phase (no suspension of the thread, unlike try_wait).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded busy poll: reacts to a phase completion at once (the producer warp of the
+// chain solves, whose reload latency is on every consumer's path).
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity) {
+    for (long long i = 0; i < (1ll << 24); ++i)
+        if (mbar_test_wait(bar, parity)) return true;
+    return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -462,8 +488,11 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <typename TS, typename TA, int R, int NW>
+template <typename TS, typename TA, int G, int NW>
 __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
+    // ring of R = 4G tile slots filled by bulk copies of G consecutive tiles (RG = 4
+    // groups): fewer, larger copies keep more bytes in flight per copy issued
+    constexpr int RG = 4, R = RG * G;
     // batched solves put the column in blockIdx.x, so the CTAs of one subdomain's columns
     // run side by side and share its factor stream through L2
     const int col = a.col_fast ? blockIdx.x : 0;
@@ -492,29 +521,29 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TS* ring = reinterpret_cast<TS*>(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
-    uint64_t* empty = full + R;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + R);
-    int64_t* issued = reinterpret_cast<int64_t*>(empty + R + 1);
-    // stream position whose copy was last issued into each slot: a consumer waits for its
-    // own position here before the mbarrier, because tiles are released out of order (by
-    // different warps) and a parity wait cannot tell "use u + 1 landed" from "use u not
-    // landed yet"
-    volatile int64_t* slot_q = reinterpret_cast<volatile int64_t*>(empty + R + 2);
-    TA* part = reinterpret_cast<TA*>(empty + 2 * R + 2);   // [2][NW][32]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + R * TB);   // per group slot
+    uint64_t* empty = full + RG;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + RG);
+    int64_t* issued = reinterpret_cast<int64_t*>(empty + RG + 1);
+    // first stream position of the group last issued into each group slot: a consumer
+    // waits for its own group here before the mbarrier, because tiles are released out of
+    // order (by different warps) and a parity wait cannot tell "use u + 1 landed" from
+    // "use u not landed yet"
+    volatile int64_t* slot_q = reinterpret_cast<volatile int64_t*>(empty + RG + 2);
+    TA* part = reinterpret_cast<TA*>(empty + 2 * RG + 2);   // [2][NW][32]
     TA* tbuf = part + 2 * NW * TILE;                    // [32] (warp 0)
     int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + TILE);
     int32_t* hi_s = lo_s + T;
     TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));   // 16-byte aligned
     auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
     if (tid == 0) {
-        for (int i = 0; i < R; ++i) {
+        for (int i = 0; i < RG; ++i) {
             mbar_init(smem_u32(&full[i]), 1);
-            mbar_init(smem_u32(&empty[i]), 1);
+            mbar_init(smem_u32(&empty[i]), G);   // one release per tile of the group
+            slot_q[i] = -1;
         }
         *abort_flag = 0;
         *issued = q0;
-        for (int i = 0; i < R; ++i) slot_q[i] = -1;
         fence_async_smem();
     }
     for (int i = tid; i < T; i += (NW + 1) * 32) {
@@ -532,24 +561,35 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
     __syncthreads();
 
     if (w == NW) {
-        // Producer warp: one lane streams the tiles through the ring in storage order.  A
-        // slot is reloaded once its previous tile has been released by the warp that read
-        // it (one arrival per use on empty[slot]).
+        // Producer warp: one lane streams the tiles through the ring in storage order, G
+        // tiles per group.  A group slot is reloaded once every tile of its previous group
+        // has been released by the warp that read it (G arrivals on empty[slot]).
         if (lane == 0) {
-            int64_t q = q0;
-            for (; q < qend; ++q) {
-                const int slot = (int)((q - q0) % R);
-                const int64_t u = (q - q0) / R;
-                if (u > 0 && (*abort_flag || !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((u - 1) & 1)))) {
+            int64_t g0 = q0;
+            for (; g0 < qend; g0 += G) {
+                const int64_t gi = (g0 - q0) / G;
+                const int gs = (int)(gi % RG);
+                const int64_t u = gi / RG;
+                if (u > 0 && (*abort_flag || !mbar_poll(smem_u32(&empty[gs]), (uint32_t)((u - 1) & 1)))) {
                     *abort_flag = 1;
                     break;
                 }
-                slot_q[slot] = q;
-                tma_load_1d(smem_u32(ring + slot * TILE2), src(q), TB, smem_u32(&full[slot]));
-                const int64_t qp = q + a.l2_ahead;   // optional L2 window ahead of the ring
-                if (a.l2_ahead > 0 && qp < qend) l2_prefetch(src(qp), TB);
+                const int cnt = (int)min((int64_t)G, qend - g0);
+                slot_q[gs] = g0;
+                const uint32_t bar = smem_u32(&full[gs]);
+                mbar_expect_tx(bar, (uint32_t)cnt * TB);
+                TS* dst = ring + (int64_t)(gs * G) * TILE2;
+                // a group may straddle the end of the forward stream: split the copy there
+                const int c1 = g0 < nts ? (int)min((int64_t)cnt, nts - g0) : 0;
+                if (c1 > 0) bulk_copy(smem_u32(dst), src(g0), (uint32_t)c1 * TB, bar);
+                if (cnt > c1) bulk_copy(smem_u32(dst + (int64_t)c1 * TILE2), src(g0 + c1), (uint32_t)(cnt - c1) * TB, bar);
+                const int64_t qp = g0 + G + a.l2_ahead;   // optional L2 window ahead of the ring
+                if (a.l2_ahead > 0 && qp < qend) {
+                    const int64_t qe = min(qp + G, qp < nts ? min(nts, qend) : qend);   // one stream
+                    l2_prefetch(src(qp), (uint32_t)(qe - qp) * TB);
+                }
             }
-            *issued = q;
+            *issued = g0;
         }
     } else {
         // Consumer warps.  Step for tile row I: warp 0 takes the off-diagonal tile nearest
@@ -559,23 +599,25 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
         // warp 0 alone reduces the partial sums and applies the stored inverse diagonal
         // tile.  Every tile is read by exactly one warp, which releases it at once.
         auto wait_full = [&](int64_t qq) -> const TS* {
-            const int slot = (int)((qq - q0) % R);
+            const int64_t gi = (qq - q0) / G;
+            const int gs = (int)(gi % RG);
             if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
+                const int64_t gq = q0 + gi * G;
                 bool r = false;
                 for (long long i = 0; i < kWaitLimit; ++i)
-                    if (slot_q[slot] == qq) {
+                    if (slot_q[gs] == gq) {
                         r = true;
                         break;
                     }
-                r = r && mbar_wait(smem_u32(&full[slot]), (uint32_t)(((qq - q0) / R) & 1));
+                r = r && mbar_poll(smem_u32(&full[gs]), (uint32_t)((gi / RG) & 1));
                 r = __all_sync(0xffffffffu, r);
                 if (!r && lane == 0) *abort_flag = 1;
             }
-            return ring + slot * TILE2;
+            return ring + ((qq - q0) % R) * TILE2;
         };
         auto release = [&](int64_t qq) {
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&empty[(qq - q0) % R]));
+            if (lane == 0) mbar_arrive(smem_u32(&empty[((qq - q0) / G) % RG]));
         };
         int64_t q = q0;
         int par = 0;
@@ -626,12 +668,12 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
     if (*abort_flag) {
         if (tid == 0) {
             atomicExch(a.err, 1);
-            // only the last use of a slot can still be in flight (a reload waits for the
-            // release of the previous use, which follows its arrival): drain those
-            const int64_t last = *issued - 1;
-            for (int sl = 0; sl < R; ++sl) {
-                if (last - q0 < sl) continue;
-                const int64_t u = (last - q0 - sl) / R;
+            // only the last use of a group slot can still be in flight (a reload waits for
+            // the release of the previous use, which follows its arrival): drain those
+            const int64_t ng = (*issued - q0 + G - 1) / G;   // groups issued
+            for (int sl = 0; sl < RG; ++sl) {
+                if (ng <= sl) continue;
+                const int64_t u = (ng - 1 - sl) / RG;
                 mbar_wait(smem_u32(&full[sl]), (uint32_t)(u & 1));
             }
         }
@@ -804,18 +846,21 @@ void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* di
     k_finalize<TW, TS><<<dim3(nitems, 32), 256, 0, st>>>(pf, work, dinv, fwdS, bwdS);
 }
 
+// tiles per bulk copy (the ring holds 4 groups): 8 KB copies for FP32 / BF16, one 8 KB
+// tile for FP64 (32 KB rings; twice that with deep_ring)
 template <typename TS>
-constexpr int ring_slots() {
-    return sizeof(TS) == 8 ? 4 : (sizeof(TS) == 4 ? 8 : 12);
+constexpr int group_tiles() {
+    return sizeof(TS) == 8 ? 1 : (sizeof(TS) == 4 ? 2 : 4);
 }
 
-template <typename TS, typename TA, int R>
+template <typename TS, typename TA, int G>
 static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int NW = 4;   // consumer warps (+ 1 producer warp)
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * R + 2) * sizeof(uint64_t) +
+    constexpr int R = 4 * G;
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * 4 + 2) * sizeof(uint64_t) +
                   (2 * NW + 1) * TILE * sizeof(TA) + (size_t)(2 * max_tiles + 4) * sizeof(int32_t) +
                   (size_t)max_tiles * TILE * sizeof(TA) + 16;
-    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
@@ -823,16 +868,16 @@ static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cud
         SolveArgs b = a;
         b.col_fast = ncols > 1;
         const dim3 grid = ncols > 1 ? dim3(ncols, njobs) : dim3(njobs);
-        k_chain_solve<TS, TA, R, NW><<<grid, (NW + 1) * 32, smem, st>>>(b);
+        k_chain_solve<TS, TA, G, NW><<<grid, (NW + 1) * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
 }
 
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
-    constexpr int R = ring_slots<TS>();
-    return a.deep_ring ? launch_ring<TS, TA, 2 * R>(a, njobs, max_tiles, st, ncols)
-                       : launch_ring<TS, TA, R>(a, njobs, max_tiles, st, ncols);
+    constexpr int G = group_tiles<TS>();
+    return a.deep_ring ? launch_ring<TS, TA, 2 * G>(a, njobs, max_tiles, st, ncols)
+                       : launch_ring<TS, TA, G>(a, njobs, max_tiles, st, ncols);
 }
 
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
