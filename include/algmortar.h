@@ -95,9 +95,16 @@ typedef struct {
     int32_t l2_prefetch;           /* local triangular solves: factor tiles prefetched into
                                       L2 ahead of each CTA's shared-memory ring; -1
                                       (default) = 0 = off                                 */
-    int32_t deep_ring;             /* local triangular solves: 1 doubles each CTA's ring of
-                                      factor tiles (64 KB instead of 32 KB of shared
-                                      memory, fewer CTAs per SM); default 0               */
+    int32_t deep_ring;             /* local triangular solves, ring of factor tiles per CTA:
+                                      0 (default) 4 groups of 8 KB bulk copies (FP64: 4
+                                      single tiles), 1 twice the group size (64 KB ring,
+                                      fewer CTAs per SM), 2 twice the group size in 2
+                                      groups (same ring size as 0)                        */
+    int32_t smooth_steps;          /* nu >= 0 block-Jacobi smoothing steps before and after
+                                      the AlgMortar correction (Sec. 5.4), composed
+                                      multiplicatively; blocks = the subdomains, each
+                                      solved with an exact factor of the unmodified
+                                      A_ii in the factor precision; default 0            */
 } algmortar_opts;
 
 typedef struct {

@@ -28,7 +28,7 @@ class Opts(C.Structure):
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("flexible", C.c_int32),
                 ("verbose", C.c_int32), ("device", C.c_int32), ("part_sizes", C.POINTER(C.c_int32)),
                 ("stream", C.c_void_p), ("nd_depth", C.c_int32), ("l2_prefetch", C.c_int32),
-                ("deep_ring", C.c_int32)]
+                ("deep_ring", C.c_int32), ("smooth_steps", C.c_int32)]
 
 
 class Stats(C.Structure):

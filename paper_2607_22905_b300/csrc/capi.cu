@@ -94,7 +94,7 @@ struct NumWs {
 struct Vecs {
     int k = 0, cap = 0;
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *pbar = nullptr;
-    double *b = nullptr, *t = nullptr;
+    double *b = nullptr, *t = nullptr, *w = nullptr;   // w: smoother residuals
     double *beta = nullptr, *eta = nullptr, *P = nullptr;
     PcgScalars* sc = nullptr;
     GridSum gs{};
@@ -122,6 +122,11 @@ struct algmortar_handle {
     Profile pf{};
     int32_t *d_rows = nullptr, *d_ntiles = nullptr;
     void *d_fwdS = nullptr, *d_bwdS = nullptr;
+    // block-Jacobi smoother (Sec. 5.4): factors of the unmodified blocks A_ii on the same
+    // tile profiles, and their symmetric scaling
+    void *d_fwdS2 = nullptr, *d_bwdS2 = nullptr;
+    double *d_dloc2 = nullptr, *d_sc2 = nullptr;
+    float* d_sc2_32 = nullptr;
     double *d_dloc = nullptr, *d_sc = nullptr;
     float* d_sc32 = nullptr;
     int32_t* d_job_sub = nullptr;
@@ -255,6 +260,11 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     W.phi64 = h->alloc<double>(nphi);
     h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
     h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
+    if (h->opts.smooth_steps > 0) {
+        h->d_fwdS2 = h->alloc<TS>((size_t)tiles * TILE2);
+        h->d_bwdS2 = h->alloc<TS>((size_t)tiles * TILE2);
+        if (!h->d_fwdS2 || !h->d_bwdS2) return fail(ALGMORTAR_OOM, "smoother factor buffers");
+    }
     h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<PanelT<TS>>(nphi);
     if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
@@ -505,8 +515,8 @@ int numeric_setup(algmortar_t* h) {
     int err_init[2] = {0, -1};
     CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
-    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, h->d_dloc, h->d_sc,
-                      h->d_sc32, st);
+    launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, 1, h->d_dloc,
+                      h->d_sc, h->d_sc32, st);
     launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
                              h->d_sc, work, m, st);
     launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
@@ -514,6 +524,20 @@ int numeric_setup(algmortar_t* h) {
     TRY(read_err_flag(h, W.d_err, "local"));
     launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS, (TS*)h->d_bwdS, st);
     CU(cudaGetLastError());
+    if (h->opts.smooth_steps > 0) {
+        // smoother blocks = the subdomains, unmodified A_ii (same sparsity, same profile)
+        CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
+        launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, 0, h->d_dloc2,
+                          h->d_sc2, h->d_sc2_32, st);
+        launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf,
+                                 h->d_dloc2, h->d_sc2, work, m, st);
+        launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
+        CU(cudaGetLastError());
+        TRY(read_err_flag(h, W.d_err, "smoother block"));
+        launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS2, (TS*)h->d_bwdS2, st);
+        CU(cudaGetLastError());
+    }
     cudaEventRecord(ev[1], st);
     // --- MBFs (Eq. def-phat-local): Phi_i = A_i^{-1} (-B_i psi_m), one job per (i, m) ---
     CU(cudaMemsetAsync(W.rhs, 0, nphi * sizeof(double), st));
@@ -677,20 +701,24 @@ ColStrides col_strides(const algmortar_t* h, const Vecs& v, bool pcg) {
 
 // Stages of Algorithm 2 on internal-order vectors, all columns of the batch per launch.
 // Local particular solutions pbar_i = A_i^{-1} r_i for all subdomains (one launch).
+// With `smoother`, the same batched solve with the block-Jacobi factors of the
+// unmodified A_ii into `out` (accumulating when asked): out (+)= B^{-1} r.
 template <typename TS, typename TA>
-int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs) {
+int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, bool smoother = false,
+                double* out = nullptr, bool accumulate = false) {
     SolveArgs a{};
     a.pf = h->pf;
-    a.fwdS = h->d_fwdS;
-    a.bwdS = h->d_bwdS;
-    a.scale = h->d_sc;
-    a.scale32 = h->d_sc32;
+    a.fwdS = smoother ? h->d_fwdS2 : h->d_fwdS;
+    a.bwdS = smoother ? h->d_bwdS2 : h->d_bwdS;
+    a.scale = smoother ? h->d_sc2 : h->d_sc;
+    a.scale32 = smoother ? h->d_sc2_32 : h->d_sc32;
     a.scale_off = h->d_sub_off;
     a.job_sub = h->d_job_sub;
     a.job_in = h->d_job_off;
     a.job_out = h->d_job_off;
     a.in = r;
-    a.out = v.pbar;
+    a.out = out ? out : v.pbar;
+    a.accumulate = accumulate ? 1 : 0;
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
@@ -709,21 +737,49 @@ void stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
     if (h->L > 0) launch_nd_solve(h->nd, v.beta, v.eta, v.P, cs, v.k, h->st);
 }
 
-// z = pbar + Phi eta; inside PCG (sc given) also r . z and the next beta per column.
+// z = base + pbar + Phi eta (base may be null); inside PCG (sc given) also r . z and the
+// next beta per column.
 template <typename TS>
-void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, PcgScalars* sc) {
+void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, PcgScalars* sc,
+                   const double* base = nullptr) {
     launch_prolong<TS>(h->nchunks, h->d_chunk_sub, h->d_chunk_off, h->P.max_k, h->d_sub_off, h->d_if_off,
-                       h->L > 0 ? h->d_ifpos : h->d_if_list, h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, z, r,
-                       v.gs, sc, cs, v.k, h->st);
+                       h->L > 0 ? h->d_ifpos : h->d_if_list, h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, base,
+                       z, r, v.gs, sc, cs, v.k, h->st);
 }
 
 template <typename TS, typename TA>
 int apply_t(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
     const ColStrides cs = col_strides(h, v, pcg);
-    TRY((stage_local<TS, TA>(h, v, r, cs)));
+    const int nu = h->opts.smooth_steps;
+    if (nu <= 0) {
+        TRY((stage_local<TS, TA>(h, v, r, cs)));
+        stage_restrict(h, v, cs);
+        stage_coarse(h, v, cs);
+        stage_prolong<PanelT<TS>>(h, v, r, z, cs, pcg ? v.sc : nullptr);
+        CU(cudaGetLastError());
+        return 0;
+    }
+    // Sec. 5.4: nu block-Jacobi steps, the AlgMortar correction, nu block-Jacobi steps,
+    // composed multiplicatively on x (= z): x = B^{-1} r first, then x += B^{-1} (r - A x)
+    const int64_t n = h->n;
+    auto resid = [&]() {
+        launch_smooth_residual(n, v.k, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, z, r, v.w, cs, h->st);
+    };
+    TRY((stage_local<TS, TA>(h, v, r, cs, true, z, false)));
+    for (int k = 1; k < nu; ++k) {
+        resid();
+        TRY((stage_local<TS, TA>(h, v, v.w, cs, true, z, true)));
+    }
+    resid();
+    TRY((stage_local<TS, TA>(h, v, v.w, cs)));
     stage_restrict(h, v, cs);
     stage_coarse(h, v, cs);
-    stage_prolong<PanelT<TS>>(h, v, r, z, cs, pcg ? v.sc : nullptr);
+    stage_prolong<PanelT<TS>>(h, v, nullptr, z, cs, nullptr, z);
+    for (int k = 0; k < nu; ++k) {
+        resid();
+        TRY((stage_local<TS, TA>(h, v, v.w, cs, true, z, true)));
+    }
+    if (pcg) launch_pcg_rho(n, v.k, r, z, v.sc, v.gs, cs, h->st);
     CU(cudaGetLastError());
     return 0;
 }
@@ -778,7 +834,7 @@ int ensure_graph(algmortar_t* h, Vecs& v) {
 // Workspace of a batch with room for `cap` columns (first use, or growth).
 int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     if (v.cap >= cap) return 0;
-    void* old[] = {v.x, v.r, v.z, v.p, v.q, v.pbar, v.b, v.t, v.beta, v.eta, v.P, v.sc, v.gs.part, v.gs.ticket};
+    void* old[] = {v.x, v.r, v.z, v.p, v.q, v.pbar, v.b, v.t, v.w, v.beta, v.eta, v.P, v.sc, v.gs.part, v.gs.ticket};
     for (void* p : old)
         if (p) h->release(p);
     if (v.graph) {
@@ -799,13 +855,15 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     v.pbar = h->alloc<double>(n);
     v.b = h->alloc<double>(n);
     v.t = h->alloc<double>(n);
+    v.w = h->opts.smooth_steps > 0 ? h->alloc<double>(n) : nullptr;
     v.beta = h->alloc<double>(l);
     v.eta = h->alloc<double>(l);
     v.P = h->alloc<double>((size_t)np * cap);
     v.sc = h->alloc<PcgScalars>(cap);
     v.gs.part = h->alloc<double>(nb);
     v.gs.ticket = h->alloc<unsigned int>(cap);
-    if (!v.x || !v.r || !v.z || !v.p || !v.q || !v.pbar || !v.b || !v.t || !v.beta || !v.eta || !v.P || !v.sc ||
+    if (!v.x || !v.r || !v.z || !v.p || !v.q || !v.pbar || !v.b || !v.t || (h->opts.smooth_steps > 0 && !v.w) ||
+        !v.beta || !v.eta || !v.P || !v.sc ||
         !v.gs.part || !v.gs.ticket) {
         v.cap = 0;
         return fail(ALGMORTAR_OOM, "vector workspace");
@@ -904,6 +962,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     if (opts_in) o = *opts_in;
     if (o.precision < 0 || o.precision > 2) return fail(ALGMORTAR_INVALID_ARG, "unknown precision");
     if (o.max_it <= 0) o.max_it = 10000;
+    if (o.smooth_steps < 0 || o.smooth_steps > 64) return fail(ALGMORTAR_INVALID_ARG, "smooth_steps out of [0, 64]");
     if (o.check_every <= 0) o.check_every = 1;
     HostCsr H{A->n, A->nnz, A->rowptr, A->col, A->val};
     std::string err;
@@ -1020,6 +1079,12 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     h->d_dloc = h->alloc<double>(n);
     h->d_sc = h->alloc<double>(n);
     h->d_sc32 = h->alloc<float>(n);
+    if (o.smooth_steps > 0) {
+        h->d_dloc2 = h->alloc<double>(n);
+        h->d_sc2 = h->alloc<double>(n);
+        h->d_sc2_32 = h->alloc<float>(n);
+        if (!h->d_dloc2 || !h->d_sc2 || !h->d_sc2_32) return bail(fail(ALGMORTAR_OOM, "smoother workspace"));
+    }
     h->d_scalar = h->alloc<double>(4);
     h->d_kerr = h->alloc<int>(1);
     if (!h->d_dloc || !h->d_sc || !h->d_sc32 || !h->d_scalar || !h->d_kerr) return bail(fail(ALGMORTAR_OOM, "workspace"));
@@ -1077,6 +1142,7 @@ void algmortar_default_opts(algmortar_opts* o) {
     o->nd_depth = -1;
     o->l2_prefetch = -1;
     o->deep_ring = 0;
+    o->smooth_steps = 0;
 }
 
 int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes, int32_t* part_out) {

@@ -37,6 +37,7 @@ struct SolveArgs {
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
     int l2_ahead;              // tiles prefetched into L2 beyond the shared-memory ring (0: off)
     int deep_ring;             // 1: twice the default ring depth (64 KB of tiles per CTA)
+    int accumulate;            // 1: out += result instead of out = result
 };
 
 struct InterfaceArgs {
@@ -123,7 +124,8 @@ cudaError_t prepare_nd_solve(int nsep);
 
 // local factor
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc, float* sc32, cudaStream_t st);
+                       const int32_t* row_sub, int diag_scale, int modified, double* dloc, double* sc, float* sc32,
+                       cudaStream_t st);
 template <typename TW>
 void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                           const int32_t* row_sub, const int64_t* sub_off, const Profile& pf,
@@ -169,8 +171,13 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
 template <typename TP>
 void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
                     const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,
-                    const TP* phi, const double* eta, const double* pbar, double* z, const double* r, GridSum gs,
-                    PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
+                    const TP* phi, const double* eta, const double* pbar, const double* base, double* z,
+                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
+void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
+                            const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
+                            cudaStream_t st);
+void launch_pcg_rho(int64_t n, int ncols, const double* r, const double* z, PcgScalars* sc, GridSum gs,
+                    ColStrides cs, cudaStream_t st);
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st);
 void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,

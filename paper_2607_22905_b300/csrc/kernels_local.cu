@@ -15,7 +15,7 @@ namespace am {
 // ---------------------------------------------------------------------------------
 __global__ void k_local_diag(int64_t n, const int32_t* __restrict__ rowptr,
                              const int32_t* __restrict__ col, const double* __restrict__ val,
-                             const int32_t* __restrict__ row_sub, int diag_scale,
+                             const int32_t* __restrict__ row_sub, int diag_scale, int modified,
                              double* __restrict__ dloc, double* __restrict__ sc, float* __restrict__ sc32) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -26,7 +26,8 @@ __global__ void k_local_diag(int64_t n, const int32_t* __restrict__ rowptr,
             if (c == k) d = val[e];
             else if (row_sub[c] != s) cross += val[e];
         }
-        double dl = d - cross;
+        // A_i = A_ii - sum_j D_ij (Eq. A_i); the block-Jacobi smoother factors A_ii itself
+        double dl = modified ? d - cross : d;
         dloc[k] = dl;
         const double f = diag_scale ? 1.0 / sqrt(dl) : 1.0;
         sc[k] = f;
@@ -488,11 +489,12 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <typename TS, typename TA, int G, int NW>
+template <typename TS, typename TA, int G, int RG, int NW>
 __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
-    // ring of R = 4G tile slots filled by bulk copies of G consecutive tiles (RG = 4
-    // groups): fewer, larger copies keep more bytes in flight per copy issued
-    constexpr int RG = 4, R = RG * G;
+    // ring of R = RG * G tile slots filled by bulk copies of G consecutive tiles: fewer,
+    // larger copies keep more bytes in flight per copy issued
+    static_assert(RG % 2 == 0, "the barrier block keeps 16-byte alignment for even RG");
+    constexpr int R = RG * G;
     // batched solves put the column in blockIdx.x, so the CTAs of one subdomain's columns
     // run side by side and share its factor stream through L2
     const int col = a.col_fast ? blockIdx.x : 0;
@@ -681,9 +683,15 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
         return;
     }
     if constexpr (sizeof(TA) == 4) {
-        for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
+        if (a.accumulate)
+            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] += (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
+        else
+            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
     } else {
-        for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = v[i] * (sc ? sc[i] : 1.0);
+        if (a.accumulate)
+            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] += v[i] * (sc ? sc[i] : 1.0);
+        else
+            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = v[i] * (sc ? sc[i] : 1.0);
     }
 }
 
@@ -793,10 +801,11 @@ static inline int grid_for(int64_t n, int bs) {
 }
 
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
-                       const int32_t* row_sub, int diag_scale, double* dloc, double* sc, float* sc32,
+                       const int32_t* row_sub, int diag_scale, int modified, double* dloc, double* sc, float* sc32,
                        cudaStream_t st) {
     count_launch();
-    k_local_diag<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, diag_scale, dloc, sc, sc32);
+    k_local_diag<<<grid_for(n, 256), 256, 0, st>>>(n, rowptr, col, val, row_sub, diag_scale, modified, dloc, sc,
+                                                    sc32);
 }
 
 template <typename TW>
@@ -853,14 +862,14 @@ constexpr int group_tiles() {
     return sizeof(TS) == 8 ? 1 : (sizeof(TS) == 4 ? 2 : 4);
 }
 
-template <typename TS, typename TA, int G>
+template <typename TS, typename TA, int G, int RG>
 static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int NW = 4;   // consumer warps (+ 1 producer warp)
-    constexpr int R = 4 * G;
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * 4 + 2) * sizeof(uint64_t) +
+    constexpr int R = RG * G;
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * RG + 2) * sizeof(uint64_t) +
                   (2 * NW + 1) * TILE * sizeof(TA) + (size_t)(2 * max_tiles + 4) * sizeof(int32_t) +
                   (size_t)max_tiles * TILE * sizeof(TA) + 16;
-    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, G, RG, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
@@ -868,7 +877,7 @@ static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cud
         SolveArgs b = a;
         b.col_fast = ncols > 1;
         const dim3 grid = ncols > 1 ? dim3(ncols, njobs) : dim3(njobs);
-        k_chain_solve<TS, TA, G, NW><<<grid, (NW + 1) * 32, smem, st>>>(b);
+        k_chain_solve<TS, TA, G, RG, NW><<<grid, (NW + 1) * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
 }
@@ -876,8 +885,11 @@ static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cud
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int G = group_tiles<TS>();
-    return a.deep_ring ? launch_ring<TS, TA, 2 * G>(a, njobs, max_tiles, st, ncols)
-                       : launch_ring<TS, TA, G>(a, njobs, max_tiles, st, ncols);
+    switch (a.deep_ring) {
+        case 1: return launch_ring<TS, TA, 2 * G, 4>(a, njobs, max_tiles, st, ncols);   // 2x ring
+        case 2: return launch_ring<TS, TA, 2 * G, 2>(a, njobs, max_tiles, st, ncols);   // 2x copies
+        default: return launch_ring<TS, TA, G, 4>(a, njobs, max_tiles, st, ncols);
+    }
 }
 
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,

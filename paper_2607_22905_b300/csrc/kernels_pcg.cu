@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
                                                      const int32_t* __restrict__ if_list,
                                                      const int64_t* __restrict__ phi_off,
                                                      const TP* __restrict__ phi, const double* __restrict__ eta,
-                                                     const double* __restrict__ pbar, double* __restrict__ z,
+                                                     const double* __restrict__ pbar,
+                                                     const double* base, double* z,   // may alias
                                                      const double* __restrict__ r, GridSum gs,
                                                      PcgScalars* psc, ColStrides cs) {
     // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
     eta += col * cs.l;
     pbar += col * cs.v;
     z += col * cs.v;
+    if (base) base += col * cs.v;
     if (r) r += col * cs.v;
     if (psc) psc += col;
     gs.part += col * gridDim.x;
@@ -126,11 +128,58 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
             c3 += ldf<TA>(ph + (int64_t)(c + 3) * ns) * e[c + 3];
         }
         for (; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
-        const double v = pbar[a0 + i] + (double)((c0 + c1) + (c2 + c3));
+        double v = pbar[a0 + i] + (double)((c0 + c1) + (c2 + c3));
+        if (base) v += base[a0 + i];   // smoothed application: x + M^{-1} (r - A x)
         z[a0 + i] = v;
         if (psc) acc = r[a0 + i] * v;
     }
     if (psc && grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
+        const double rn = psc->rz_next;
+        psc->beta = (psc->iter == 0 || psc->restart)
+                        ? 0.0
+                        : (psc->flexible ? (rn - psc->rz_mix) / psc->rz : rn / psc->rz);
+    }
+}
+
+// s = r - A x (sliced ELL) for the block-Jacobi smoothing steps (Sec. 5.4).
+__global__ void __launch_bounds__(VEC_BS) k_smooth_residual(int64_t n, const int64_t* __restrict__ ell_ptr,
+                                                             const int32_t* __restrict__ ell_col,
+                                                             const double* __restrict__ ell_val,
+                                                             const double* __restrict__ x, const double* __restrict__ r,
+                                                             double* __restrict__ s, ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
+    x += col * cs.v;
+    r += col * cs.v;
+    s += col * cs.v;
+    GRID_STRIDE(k, n) {
+        const int64_t sl = k >> 5;
+        const int rr = (int)(k & 31);
+        const int64_t b = __ldg(ell_ptr + sl), w = (__ldg(ell_ptr + sl + 1) - b) >> 5;
+        const double* v = ell_val + b + rr;
+        const int32_t* c = ell_col + b + rr;
+        double acc = r[k];
+        for (int64_t e = 0; e < w; ++e) acc -= __ldg(v + e * 32) * __ldg(x + __ldg(c + e * 32));
+        s[k] = acc;
+    }
+}
+
+// Completion of the preconditioned residual (smoothed path): rho = r . z and the next
+// beta (as in k_prolong's tail).
+__global__ void __launch_bounds__(VEC_BS) k_pcg_rho(int64_t n, const double* __restrict__ r,
+                                                     const double* __restrict__ z, PcgScalars* psc, GridSum gs,
+                                                     ColStrides cs) {
+    const int col = blockIdx.y;
+    if (cs.done && cs.done[col * cs.done_stride]) return;
+    __shared__ double sh[32];
+    r += col * cs.v;
+    z += col * cs.v;
+    psc += col;
+    gs.part += col * gridDim.x;
+    gs.ticket += col;
+    double acc = 0.0;
+    GRID_STRIDE(k, n) acc += r[k] * z[k];
+    if (grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
         const double rn = psc->rz_next;
         psc->beta = (psc->iter == 0 || psc->restart)
                         ? 0.0
@@ -427,12 +476,23 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
 template <typename TP>
 void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
                     const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,
-                    const TP* phi, const double* eta, const double* pbar, double* z, const double* r, GridSum gs,
-                    PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
+                    const TP* phi, const double* eta, const double* pbar, const double* base, double* z,
+                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     count_launch();
     k_prolong<TP><<<dim3(nchunks, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
-        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, z, r, gs, sc, cs);
+        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, base, z, r, gs, sc, cs);
+}
+void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
+                            const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
+                            cudaStream_t st) {
+    count_launch();
+    k_smooth_residual<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, x, r, s, cs);
+}
+void launch_pcg_rho(int64_t n, int ncols, const double* r, const double* z, PcgScalars* sc, GridSum gs,
+                    ColStrides cs, cudaStream_t st) {
+    count_launch();
+    k_pcg_rho<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, r, z, sc, gs, cs);
 }
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st) {
@@ -480,7 +540,8 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
 #define INST_PROLONG(TP)                                                                                     \
     template void launch_prolong<TP>(int, const int32_t*, const int32_t*, int, const int64_t*, const int64_t*,    \
                                      const int32_t*, const int64_t*, const TP*, const double*, const double*,     \
-                                     double*, const double*, GridSum, PcgScalars*, ColStrides, int, cudaStream_t);
+                                     const double*, double*, const double*, GridSum, PcgScalars*, ColStrides,     \
+                                     int, cudaStream_t);
 INST_PROLONG(double)
 INST_PROLONG(float)
 
