@@ -96,10 +96,10 @@ typedef struct {
                                       L2 ahead of each CTA's shared-memory ring; -1
                                       (default) = 0 = off                                 */
     int32_t deep_ring;             /* local triangular solves, ring of factor tiles per CTA:
-                                      0 (default) 4 groups of 8 KB bulk copies (FP64: 4
-                                      single tiles), 1 twice the group size (64 KB ring,
-                                      fewer CTAs per SM), 2 twice the group size in 2
-                                      groups (same ring size as 0)                        */
+                                      0 (default) 4 groups of G tiles per bulk copy (FP32
+                                      16 KB, BF16 8 KB, FP64 one 8 KB tile), 1 twice the
+                                      group size (twice the shared memory, fewer CTAs per
+                                      SM), 2 twice the group size in 2 groups            */
     int32_t smooth_steps;          /* nu >= 0 block-Jacobi smoothing steps before and after
                                       the AlgMortar correction (Sec. 5.4), composed
                                       multiplicatively; blocks = the subdomains, each

@@ -855,11 +855,12 @@ void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* di
     k_finalize<TW, TS><<<dim3(nitems, 32), 256, 0, st>>>(pf, work, dinv, fwdS, bwdS);
 }
 
-// tiles per bulk copy (the ring holds 4 groups): 8 KB copies for FP32 / BF16, one 8 KB
-// tile for FP64 (32 KB rings; twice that with deep_ring)
+// Tiles per bulk copy (the ring holds 4 groups), chosen by measurement at config 3 on
+// B300: FP32 16 KB copies (64 KB ring), BF16 8 KB copies (32 KB ring), FP64 one 8 KB tile
+// per copy (32 KB ring; FP64 solves are bound by the FP64 pipe, not by the copies).
 template <typename TS>
 constexpr int group_tiles() {
-    return sizeof(TS) == 8 ? 1 : (sizeof(TS) == 4 ? 2 : 4);
+    return sizeof(TS) == 8 ? 1 : 4;
 }
 
 template <typename TS, typename TA, int G, int RG>
