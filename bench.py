@@ -41,6 +41,17 @@ METRIC = ("time-to-1e-8 rel. residual & PCG iters (1.1M cells): mixed/batched vs
 TOL = 1e-8
 
 
+def _source_rev(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+# revision of the local-solve kernel source: DRAM traffic taken by ncu on another revision
+# is not reported
+KERNEL_REVISION = _source_rev("paper_2607_22905_b300/csrc/kernels_local.cu")
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -260,9 +271,16 @@ def run_ours(args):
         "gpu_launches": int(r["launches_per_step"] * args.steps),
         "clocks": clocks_all.get(best),
     }
+    tr = load_traffic(best)
+    if tr is not None:
+        out["roofline"]["traffic"] = tr["bytes_per_launch"]
+        out["roofline"]["traffic_source"] = tr["source"]
     if "fp64" in res:
         out["fp64_ms"] = round(res["fp64"]["ms"], 3)
         out["speedup_vs_fp64"] = round(res["fp64"]["ms"] / r["ms"], 3)
+    if args.extras and rank == 0:
+        out["smoothing"] = smoothing_runs(P, best, vals, b, args, local)
+        out["multi_rhs"] = multi_rhs_run(best, args, local)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(P, args)
     if rank == 0:
@@ -271,6 +289,78 @@ def run_ours(args):
         am.close()
     if dist:
         dist.destroy_process_group()
+
+
+def load_traffic(variant):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary (scaled
+    to the full workload there), or None when no summary covers this variant's kernel."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as fh:
+            d = json.load(fh)
+        e = d.get(variant)
+        return e if e and e.get("kernel_revision") == KERNEL_REVISION else None
+    except Exception:
+        return None
+
+
+def smoothing_runs(P, prec, vals, b, args, local, nus=(1, 2)):
+    """Sec. 5.4 block-Jacobi pre/post smoothing (nu steps each side) on the same workload:
+    step time (numeric setup + PCG to tol) and iterations, 2 timed steps each."""
+    import torch
+    from paper_2607_22905_b300.solver import AlgMortar
+    outs = {}
+    for nu in nus:
+        am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
+                       check_every=args.check_every, device=local, smooth_steps=nu)
+        for _ in range(2):
+            am.update_values(vals)
+            am.solve(b, tol=TOL)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            am.update_values(vals)
+            x, st = am.solve(b, tol=TOL)
+        e1.record()
+        torch.cuda.synchronize()
+        outs[f"nu{nu}"] = {"ms": round(e0.elapsed_time(e1) / 2, 3), "iterations": st["iterations"],
+                           "rel_residual": st["rel_residual"]}
+        am.close()
+    return outs
+
+
+def multi_rhs_run(prec, args, local, nrhs=64, nsingle=4):
+    """Batched multi-RHS PCG on config 4 (500k cells, irregular faulted grid, 64 RHS):
+    one solve_multi call over all columns vs single-RHS solves of the same columns."""
+    import torch
+    import synth
+    from paper_2607_22905_b300.solver import AlgMortar
+    P = synth.config4()
+    Bm = torch.as_tensor(P.meta["rhs"][:, :nrhs], dtype=torch.float64, device=torch.device("cuda", local))
+    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
+                   check_every=args.check_every, device=local)
+    am.solve_multi(Bm[:, :8], tol=TOL)
+    am.solve(Bm[:, 0], tol=TOL)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    X, stats = am.solve_multi(Bm, tol=TOL)
+    e[1].record()
+    its1 = []
+    e[2].record()
+    for j in range(nsingle):
+        x, st = am.solve(Bm[:, j], tol=TOL)
+        its1.append(st["iterations"])
+    e[3].record()
+    torch.cuda.synchronize()
+    batched = e[0].elapsed_time(e[1])
+    single = e[2].elapsed_time(e[3]) / nsingle
+    am.close()
+    its = [s["iterations"] for s in stats]
+    return {"workload": "C4 100x100x50 faulted hexahedral stand-in (500k cells), %d RHS, %s factors" % (nrhs, prec),
+            "batched_ms_per_rhs": round(batched / nrhs, 3), "single_ms_per_rhs": round(single, 3),
+            "batch_speedup": round(single / (batched / nrhs), 3),
+            "iterations_min_max": [int(min(its)), int(max(its))], "single_iterations": its1}
 
 
 def cpu_baseline(P, args, n_iter_sample=3):
@@ -361,6 +451,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--stage-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the smoothing and multi-RHS side measurements")
     ap.add_argument("--mode", default="bench", choices=["bench", "apply", "solve"],
                     help="apply / solve: set up the first variant and run one preconditioner "
                          "application / one PCG solve (kernel profiling targets), no timing")

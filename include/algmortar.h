@@ -192,13 +192,14 @@ int algmortar_pcg_solve_host(algmortar_t* h, const double* b_host, double* x_hos
 
 /* nrhs independent systems A X[:, j] = B[:, j] (column-major, leading dimension ld >= n,
  * device), solved as batches of up to ALGMORTAR_MAX_BATCH columns: every kernel of a
- * PCG iteration (SpMV, vector updates, the stages of Algorithm 2) covers all columns of
- * the batch in one launch, so the local factors and MBF panels stream once per
- * iteration for the whole batch.  Each column runs its own CG scalars and stops on its
- * own tolerance (stopped columns are skipped); its iterates are bit-identical to
- * algmortar_pcg_solve on that column.  st (may be NULL) points to nrhs stats.  The
- * batch workspace (8 n + 2 L doubles per column) is allocated on first use and kept.
- * Returns OK, NO_CONVERGENCE or BREAKDOWN (the worst column). */
+ * PCG iteration covers all columns of the batch in one launch; the local solves run as
+ * column-block jobs (4 columns of one subdomain per CTA, each factor tile read once per
+ * block).  Each column runs its own CG scalars and stops on its own tolerance (stopped
+ * columns are skipped).  The batched local solve sums a tile row's contributions in a
+ * different order than the single-RHS kernel, so columns agree with algmortar_pcg_solve
+ * to rounding, not bit for bit.  st (may be NULL) points to nrhs stats.  The batch
+ * workspace (8 n + 2 L doubles per column) is allocated on first use and kept.  Returns
+ * OK, NO_CONVERGENCE or BREAKDOWN (the worst column). */
 int algmortar_pcg_solve_multi(algmortar_t* h, const double* B_dev, double* X_dev, int32_t nrhs,
                               int64_t ld, double tol, algmortar_stats* st);
 

@@ -46,9 +46,32 @@ double now_ms() {
 
 // Device buffers of Algorithm 1 that survive between numeric setups (value updates
 // reuse them, so captured graphs and pointers stay valid).
+// Column-block jobs of the multi-column chain solve: up to COLS_PER_JOB columns of one
+// item at a constant stride, the smallest start row of the block (identity columns).
+struct BlockJobs {
+    std::vector<int32_t> sub, nc, t0;
+    std::vector<int64_t> in, ld;
+    void add(int32_t item, int64_t base, int64_t stride, int64_t ncols, bool identity_t0) {
+        for (int64_t c = 0; c < ncols; c += COLS_PER_JOB) {
+            sub.push_back(item);
+            in.push_back(base + c * stride);
+            ld.push_back(stride);
+            nc.push_back((int32_t)std::min<int64_t>(COLS_PER_JOB, ncols - c));
+            t0.push_back(identity_t0 ? (int32_t)(c / TILE) : 0);
+        }
+    }
+    int size() const { return (int)sub.size(); }
+};
+struct DevBlockJobs {
+    int n = 0;
+    int32_t *sub = nullptr, *nc = nullptr, *t0 = nullptr;
+    int64_t *in = nullptr, *ld = nullptr;
+};
+
 struct NumWs {
     bool ready = false;
     int njobs_mbf = 0;
+    DevBlockJobs bj_mbf, bj_g, bj_w, bj_c;   // column-block jobs of the setup solves
     int32_t *d_js = nullptr, *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
     int64_t *d_jo = nullptr, *d_goff = nullptr, *d_gcptr = nullptr;
     double* d_gval = nullptr;
@@ -100,6 +123,9 @@ struct Vecs {
     GridSum gs{};
     cudaGraphExec_t graph = nullptr;
     int graph_k = 0;                   // column count the graph was captured with
+    DevBlockJobs bj;                   // column-block jobs of the batched local solves
+    int32_t* bj_col0 = nullptr;
+    int bj_k = 0;                      // column count bj was built for
     int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
 };
 
@@ -209,6 +235,29 @@ int upload(algmortar_t* h, T*& dst, const std::vector<T>& src) {
         if (rc_) return rc_; \
     } while (0)
 
+int upload_jobs(algmortar_t* h, DevBlockJobs& d, const BlockJobs& b) {
+    d.n = b.size();
+    TRY(upload(h, d.sub, b.sub));
+    TRY(upload(h, d.nc, b.nc));
+    TRY(upload(h, d.t0, b.t0));
+    TRY(upload(h, d.in, b.in));
+    TRY(upload(h, d.ld, b.ld));
+    return 0;
+}
+
+// A solve over column-block jobs (SolveArgs.job_* set from d; in/out offsets shared).
+template <typename TS, typename TA>
+int solve_cols(SolveArgs a, const DevBlockJobs& d, bool identity, int max_tiles, cudaStream_t st) {
+    a.job_sub = d.sub;
+    a.job_in = d.in;
+    a.job_out = d.in;
+    a.job_ld = d.ld;
+    a.job_nc = d.nc;
+    a.job_t0 = identity ? d.t0 : nullptr;
+    CU((launch_tile_solve_cols<TS, TA>(a, d.n, max_tiles, st)));
+    return 0;
+}
+
 int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
     int e[2];
     CU(cudaMemcpyAsync(e, d_err, sizeof(e), cudaMemcpyDeviceToHost, h->st));
@@ -235,6 +284,14 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         }
     }
     W.njobs_mbf = (int)js.size();
+    {
+        BlockJobs b;
+        for (int s = 0; s < m; ++s) {
+            const int64_t ns = P.sub_off[s + 1] - P.sub_off[s];
+            b.add(s, P.phi_off[s], ns, P.if_off[s + 1] - P.if_off[s], false);
+        }
+        TRY(upload_jobs(h, W.bj_mbf, b));
+    }
     std::vector<int64_t> gcptr;
     gcptr.reserve(P.if_off[m] + m);
     for (int s = 0; s < m; ++s) {
@@ -281,6 +338,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             prow_g;
         std::vector<int64_t> irow0, ibase, ifwd, ibwd, isrc, gjin, wjin, gioff(G, 0), woff(G, 0), doff(G, 0),
             entbase(G, 0);
+        BlockJobs bg, bw;
         int64_t trow = 0, tb = 0, gi = 0, wo = 0, dof = 0, ent = 0;
         for (int g = 0; g < G; ++g) {
             const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
@@ -322,6 +380,8 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
                     gjt0.push_back((int32_t)(c / TILE));
                     gjin.push_back(gi + c * ng);
                 }
+                bg.add(it, gi, ng, ng, true);
+                bw.add(it, wo, ng, ag, false);
                 for (int64_t c = 0; c < ag; ++c) {
                     wjob.push_back(it);
                     wjin.push_back(wo + c * ng);
@@ -355,6 +415,8 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         TRY(upload(h, W.d_titem, titem));
         TRY(upload(h, W.d_tI, tI));
         TRY(upload(h, W.d_tJ, tJ));
+        TRY(upload_jobs(h, W.bj_g, bg));
+        TRY(upload_jobs(h, W.bj_w, bw));
         TRY(upload(h, W.d_gjob, gjob));
         TRY(upload(h, W.d_gjin, gjin));
         TRY(upload(h, W.d_gjt0, gjt0));
@@ -470,6 +532,11 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             TRY(upload(h, W.d_cjob, cj));
             TRY(upload(h, W.d_cjin, cjin));
             TRY(upload(h, W.d_cjt0, cjt0));
+            {
+                BlockJobs bc;
+                bc.add(0, 0, nsep, nsep, true);
+                TRY(upload_jobs(h, W.bj_c, bc));
+            }
             const int64_t ct = (int64_t)T * (T + 1) / 2;
             W.cwork = h->alloc<double>((size_t)ct * TILE2);
             W.cdinv = h->alloc<double>((size_t)T * TILE2);
@@ -550,16 +617,11 @@ int numeric_setup(algmortar_t* h) {
         a.scale = h->d_sc;
         a.scale32 = h->d_sc32;
         a.scale_off = h->d_sub_off;
-        a.job_sub = W.d_js;
-        a.job_in = W.d_jo;
-        a.job_out = W.d_jo;
         a.in = W.rhs;
         a.out = W.phi64;
         a.done = nullptr;
         a.err = h->d_kerr;
-        a.l2_ahead = l2_ahead(h);
-        a.deep_ring = h->opts.deep_ring;
-        CU((launch_tile_solve<TS, TA>(a, W.njobs_mbf, P.max_tiles, st)));
+        TRY((solve_cols<TS, TA>(a, W.bj_mbf, false, P.max_tiles, st)));
     }
     if (!std::is_same<TS, double>::value) launch_convert<PanelT<TS>>(nphi, W.phi64, (PanelT<TS>*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
@@ -607,22 +669,13 @@ int numeric_setup(algmortar_t* h) {
         sa.fwdS = W.gf;
         sa.bwdS = W.gb;
         sa.err = h->d_kerr;
-        sa.l2_ahead = l2_ahead(h);
-        sa.deep_ring = h->opts.deep_ring;
-        sa.job_sub = W.d_gjob;
-        sa.job_in = W.d_gjin;
-        sa.job_out = W.d_gjin;
-        sa.job_t0 = W.d_gjt0;          // lower triangle of S_gg^{-1} only
         sa.in = W.gE;
         sa.out = (double*)h->nd.Ginv;
-        CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
-        sa.job_t0 = nullptr;
-        sa.job_sub = W.d_wjob;
-        sa.job_in = W.d_wjin;
-        sa.job_out = W.d_wjin;
+        // identity columns start at their own tile row: lower triangle of S_gg^{-1} only
+        TRY((solve_cols<double, double>(sa, W.bj_g, true, W.max_tiles_items, st)));
         sa.in = W.RHS;
         sa.out = (double*)h->nd.Wcm;
-        CU((launch_tile_solve<double, double>(sa, W.njobs_w, W.max_tiles_items, st)));
+        TRY((solve_cols<double, double>(sa, W.bj_w, false, W.max_tiles_items, st)));
         launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
         launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
         if (nsep > 0) {
@@ -642,15 +695,9 @@ int numeric_setup(algmortar_t* h) {
             ca.fwdS = W.cf;
             ca.bwdS = W.cb;
             ca.err = h->d_kerr;
-            ca.l2_ahead = l2_ahead(h);
-            ca.deep_ring = h->opts.deep_ring;
-            ca.job_sub = W.d_cjob;
-            ca.job_in = W.d_cjin;
-            ca.job_out = W.d_cjin;
-            ca.job_t0 = W.d_cjt0;      // lower triangle of C^{-1} only
             ca.in = W.cE;
             ca.out = (double*)h->nd.Cinv;
-            CU((launch_tile_solve<double, double>(ca, nsep, W.cT, st)));
+            TRY((solve_cols<double, double>(ca, W.bj_c, true, W.cT, st)));   // lower triangle of C^{-1}
             launch_mirror_lower(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
         }
         CU(cudaGetLastError());
@@ -725,6 +772,12 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     a.l2_ahead = l2_ahead(h);
     a.deep_ring = h->opts.deep_ring;
     a.err = h->d_kerr;
+    if (v.k > 1) {
+        // batched columns: one job per (subdomain, block of COLS_PER_JOB columns), each
+        // factor tile read once per block
+        a.job_col0 = v.bj_col0;
+        return solve_cols<TS, TA>(a, v.bj, false, h->P.max_tiles, h->st);
+    }
     CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st, v.k)));
     return 0;
 }
@@ -876,6 +929,32 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     return 0;
 }
 
+// Column-block jobs for a batch of k > 1 columns: per subdomain (largest first) blocks of
+// COLS_PER_JOB consecutive columns at stride n.
+int ensure_batch_jobs(algmortar_t* h, Vecs& v) {
+    if (v.k <= 1 || v.bj_k == v.k) return 0;
+    std::vector<int32_t> rows(h->m), order(h->m);
+    for (int s = 0; s < h->m; ++s) {
+        rows[s] = (int32_t)(h->P.sub_off[s + 1] - h->P.sub_off[s]);
+        order[s] = s;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rows[x] > rows[y]; });
+    BlockJobs b;
+    std::vector<int32_t> col0;
+    for (int s : order) {
+        const size_t before = b.sub.size();
+        b.add(s, h->P.sub_off[s], h->n, v.k, false);
+        for (size_t j = before; j < b.sub.size(); ++j) col0.push_back((int32_t)((j - before) * COLS_PER_JOB));
+    }
+    void* old[] = {v.bj.sub, v.bj.nc, v.bj.t0, v.bj.in, v.bj.ld, v.bj_col0};
+    for (void* p : old)
+        if (p) h->release(p);
+    TRY(upload_jobs(h, v.bj, b));
+    TRY(upload(h, v.bj_col0, col0));
+    v.bj_k = v.k;
+    return 0;
+}
+
 // PCG in the internal ordering on v.b -> v.x for the batch's k columns; stats[j] per column.
 // Returns the worst column status.
 int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
@@ -884,6 +963,7 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     if (!(tol > 0.0)) return fail(ALGMORTAR_INVALID_ARG, "tol must be positive");
     const int k = v.k;
     const int64_t n = h->n;
+    TRY(ensure_batch_jobs(h, v));
     if (h->opts.use_graph) TRY(ensure_graph(h, v));
     launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, h->opts.flexible ? 1 : 0, st);
     TRY(apply_internal(h, v, v.r, v.z, true));

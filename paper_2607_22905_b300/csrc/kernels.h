@@ -38,6 +38,12 @@ struct SolveArgs {
     int l2_ahead;              // tiles prefetched into L2 beyond the shared-memory ring (0: off)
     int deep_ring;             // 1: twice the default ring depth (64 KB of tiles per CTA)
     int accumulate;            // 1: out += result instead of out = result
+    // column-block jobs (launch_tile_solve_cols): up to NW columns of one item per job,
+    // column c at job_in[job] + c * job_ld[job] (in and out), the first job_nc[job] valid,
+    // and for PCG columns the stop flag of column job_col0[job] + c
+    const int64_t* job_ld;
+    const int32_t* job_nc;
+    const int32_t* job_col0;
 };
 
 struct InterfaceArgs {
@@ -144,6 +150,11 @@ void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* di
                      cudaStream_t st);
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols = 1);
+// Column-block jobs: each of the 4 consumer warps of a CTA solves one column of the job
+// with the same factor tile stream (each tile copied once per job, read by every warp).
+constexpr int COLS_PER_JOB = 4;
+template <typename TS, typename TA>
+cudaError_t launch_tile_solve_cols(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st);
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
                     const double* g_val, const int32_t* rows, const int64_t* phi_off, double* rhs,
                     cudaStream_t st);

@@ -377,6 +377,25 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
     }
 }
 
+// Warp dot product of a contiguous row with x (len entries), four independent FP64
+// accumulators per lane (the FP64 pipe's latency is long on B300), lanes 0..31 strided.
+__device__ __forceinline__ double warp_row_dot(const double* __restrict__ row, const double* __restrict__ x,
+                                               int64_t len, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t j = lane;
+    for (; j + 96 < len; j += 128) {
+        s0 += row[j] * x[j];
+        s1 += row[j + 32] * x[j + 32];
+        s2 += row[j + 64] * x[j + 64];
+        s3 += row[j + 96] * x[j + 96];
+    }
+    for (; j < len; j += 32) s0 += row[j] * x[j];
+    double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // ---------------------------------------------------------------------------------
 // Per-iteration solve (ND order in and out).
 // Stage 1: eta_g = Ginv_g b_g  (rows of the symmetric inverse) and P_g = W_g^T b_g.
@@ -394,23 +413,13 @@ __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double*
     if (wid < nin) {
         const int g = a.row_g[wid];
         const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
-        const double* row = a.Ginv + a.gioff[g] + i * ng;
-        const double* bg = b + g0;
-        double s = 0.0;
-        for (int64_t j = lane; j < ng; j += 32) s += row[j] * bg[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double s = warp_row_dot(a.Ginv + a.gioff[g] + i * ng, b + g0, ng, lane);
         if (lane == 0) eta[wid] = s;
     } else if (wid < nin + a.aoff[a.G]) {
         const int64_t r = wid - nin;
         const int g = a.prow_g[r];
         const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = r - a.aoff[g];
-        const double* col = a.Wcm + a.woff[g] + j * ng;
-        const double* bg = b + g0;
-        double s = 0.0;
-        for (int64_t t = lane; t < ng; t += 32) s += col[t] * bg[t];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double s = warp_row_dot(a.Wcm + a.woff[g] + j * ng, b + g0, ng, lane);
         if (lane == 0) P[r] = s;
     }
 }
@@ -434,11 +443,7 @@ __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double*
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (wid >= nsep) return;
-    const double* row = a.Cinv + wid * nsep;
-    double s = 0.0;
-    for (int t = lane; t < nsep; t += 32) s += row[t] * cvec[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double s = warp_row_dot(a.Cinv + wid * nsep, cvec, nsep, lane);
     if (lane == 0) eta[sep0 + wid] = s;
 }
 
@@ -455,8 +460,15 @@ __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides 
     const int64_t g0 = a.goff[g], ag = a.aoff[g + 1] - a.aoff[g], i = wid - g0;
     const double* row = a.Wrm + a.woff[g] + i * ag;
     const int32_t* al = a.alist + a.aoff[g];
-    double s = 0.0;
-    for (int64_t j = lane; j < ag; j += 32) s += row[j] * eta[nin + al[j]];
+    const double* es = eta + nin;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t j = lane;
+    for (; j + 32 < ag; j += 64) {
+        s0 += row[j] * es[al[j]];
+        s1 += row[j + 32] * es[al[j + 32]];
+    }
+    for (; j < ag; j += 32) s0 += row[j] * es[al[j]];
+    double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) eta[wid] -= s;

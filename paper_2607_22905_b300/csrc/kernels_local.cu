@@ -696,6 +696,203 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
+// Column-block variant for many right-hand sides of one item (the MBF panels, the
+// identity columns of the interface inverses, batched PCG columns): consumer warp w
+// solves column w of the job on its own (lane = tile row, as above, its own solution
+// vector in shared memory), all NW warps walking the same tile stream, so each factor
+// tile is copied from memory once per NW columns.  Every warp reads every tile and
+// releases it (NW arrivals per tile on empty[group]); no named barriers.
+// ---------------------------------------------------------------------------------
+template <typename TS, typename TA, int G, int RG, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve_cols(SolveArgs a) {
+    static_assert(RG % 2 == 0, "the barrier block keeps 16-byte alignment for even RG");
+    constexpr int R = RG * G;
+    const int job = blockIdx.x;
+    const int nc = a.job_nc ? a.job_nc[job] : NW;
+    const int c0 = a.job_col0 ? a.job_col0[job] : 0;
+    {
+        bool any = false;   // the job's columns that still run (PCG stop flags)
+        for (int c = 0; c < nc; ++c) any = any || !(a.done && a.done[(c0 + c) * a.done_stride]);
+        if (!any) return;
+    }
+    const int s = a.job_sub[job];
+    const Profile pf = a.pf;
+    const int n = pf.rows[s], T = pf.ntiles[s];
+    const int64_t r0 = pf.row0[s];
+    const int64_t nts = pf.fwd[r0 + T - 1] + (T - 1 - pf.lo[r0 + T - 1]) + 1;
+    const int t0 = a.job_t0 ? a.job_t0[job] : 0;   // smallest start row of the job's columns
+    const int64_t q0 = pf.fwd[r0 + t0];
+    const int64_t qend = nts + pf.bwd[r0 + t0] + (pf.hi[r0 + t0] - t0) + 1;
+    const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
+    const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
+    const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
+    const float* sc32 = a.scale32 ? a.scale32 + a.scale_off[s] : nullptr;
+    const int64_t ld = a.job_ld ? a.job_ld[job] : a.ldin;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const bool act = w < nc && !(a.done && a.done[(c0 + w) * a.done_stride]);
+    constexpr uint32_t TB = TILE2 * sizeof(TS);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TS* ring = reinterpret_cast<TS*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + R * TB);
+    uint64_t* empty = full + RG;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + RG);
+    int64_t* issued = reinterpret_cast<int64_t*>(empty + RG + 1);
+    volatile int64_t* slot_q = reinterpret_cast<volatile int64_t*>(empty + RG + 2);
+    TA* tbuf = reinterpret_cast<TA*>(empty + 2 * RG + 2);   // [NW][32]
+    int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + NW * TILE);
+    int32_t* hi_s = lo_s + T;
+    TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));   // [NW][T * 32], 16-byte aligned
+    auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
+    if (tid == 0) {
+        for (int i = 0; i < RG; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&empty[i]), G * NW);
+            slot_q[i] = -1;
+        }
+        *abort_flag = 0;
+        *issued = q0;
+        fence_async_smem();
+    }
+    for (int i = tid; i < T; i += (NW + 1) * 32) {
+        lo_s[i] = pf.lo[r0 + i];
+        hi_s[i] = pf.hi[r0 + i];
+    }
+    if (w < NW) {
+        TA* vw = v + (int64_t)w * T * TILE;
+        const double* in = a.in + a.job_in[job] + (int64_t)w * ld;
+        for (int i = lane; i < T * TILE; i += 32) {
+            TA x = 0;
+            if (act && i < n) {
+                if constexpr (sizeof(TA) == 4) x = (float)in[i] * (sc32 ? sc32[i] : 1.0f);
+                else x = in[i] * (sc ? sc[i] : 1.0);
+            }
+            vw[i] = x;
+        }
+    }
+    __syncthreads();
+
+    if (w == NW) {
+        if (lane == 0) {   // producer, as in k_chain_solve
+            int64_t g0 = q0;
+            for (; g0 < qend; g0 += G) {
+                const int64_t gi = (g0 - q0) / G;
+                const int gs = (int)(gi % RG);
+                const int64_t u = gi / RG;
+                if (u > 0 && (*abort_flag || !mbar_poll(smem_u32(&empty[gs]), (uint32_t)((u - 1) & 1)))) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int cnt = (int)min((int64_t)G, qend - g0);
+                slot_q[gs] = g0;
+                const uint32_t bar = smem_u32(&full[gs]);
+                mbar_expect_tx(bar, (uint32_t)cnt * TB);
+                TS* dst = ring + (int64_t)(gs * G) * TILE2;
+                const int c1 = g0 < nts ? (int)min((int64_t)cnt, nts - g0) : 0;
+                if (c1 > 0) bulk_copy(smem_u32(dst), src(g0), (uint32_t)c1 * TB, bar);
+                if (cnt > c1) bulk_copy(smem_u32(dst + (int64_t)c1 * TILE2), src(g0 + c1), (uint32_t)(cnt - c1) * TB, bar);
+            }
+            *issued = g0;
+        }
+    } else {
+        TA* vw = v + (int64_t)w * T * TILE;
+        TA* tw = tbuf + w * TILE;
+        auto wait_full = [&](int64_t qq) -> const TS* {
+            const int64_t gi = (qq - q0) / G;
+            const int gs = (int)(gi % RG);
+            if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
+                const int64_t gq = q0 + gi * G;
+                bool r = false;
+                for (long long i = 0; i < kWaitLimit; ++i)
+                    if (slot_q[gs] == gq) {
+                        r = true;
+                        break;
+                    }
+                r = r && mbar_poll(smem_u32(&full[gs]), (uint32_t)((gi / RG) & 1));
+                r = __all_sync(0xffffffffu, r);
+                if (!r && lane == 0) *abort_flag = 1;
+            }
+            return ring + ((qq - q0) % R) * TILE2;
+        };
+        auto release = [&](int64_t qq) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&empty[((qq - q0) / G) % RG]));
+        };
+        int64_t q = q0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int step = t0; step < T; ++step) {
+                const int I = pass == 0 ? step : T - 1 - (step - t0);
+                const int j0 = pass == 0 ? lo_s[I] : I + 1;
+                const int nt = pass == 0 ? I - lo_s[I] : hi_s[I] - I;
+                TA acc = 0;
+                for (int t = 0; t < nt; ++t) {
+                    const TS* tl = wait_full(q + t);
+                    if (act) acc += row_dot<TS, TA>(tl, lane, vw + (j0 + t) * TILE);
+                    release(q + t);
+                }
+                TA* vi = vw + I * TILE;
+                tw[lane] = vi[lane] - acc;
+                __syncwarp();
+                const TS* D = wait_full(q + nt);
+                const TA y = act ? row_dot<TS, TA>(D, lane, tw) : (TA)0;
+                release(q + nt);
+                vi[lane] = y;
+                __syncwarp();
+                q += nt + 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        if (tid == 0) {
+            atomicExch(a.err, 1);
+            const int64_t ng = (*issued - q0 + G - 1) / G;
+            for (int sl = 0; sl < RG; ++sl) {
+                if (ng <= sl) continue;
+                const int64_t u = (ng - 1 - sl) / RG;
+                mbar_wait(smem_u32(&full[sl]), (uint32_t)(u & 1));
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    if (w < NW && act) {
+        const TA* vw = v + (int64_t)w * T * TILE;
+        double* out = a.out + a.job_out[job] + (int64_t)w * ld;
+        for (int i = lane; i < n; i += 32) {
+            double x;
+            if constexpr (sizeof(TA) == 4) x = (double)(vw[i] * (sc32 ? sc32[i] : 1.0f));
+            else x = vw[i] * (sc ? sc[i] : 1.0);
+            if (a.accumulate) out[i] += x;
+            else out[i] = x;
+        }
+    }
+}
+
+template <typename TS, typename TA, int G, int RG>
+static cudaError_t launch_cols_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
+    constexpr int NW = COLS_PER_JOB;
+    constexpr int R = RG * G;
+    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * RG + 2) * sizeof(uint64_t) + NW * TILE * sizeof(TA) +
+                  (size_t)(2 * max_tiles + 4) * sizeof(int32_t) + (size_t)NW * max_tiles * TILE * sizeof(TA) + 16;
+    cudaError_t e = cudaFuncSetAttribute(k_chain_solve_cols<TS, TA, G, RG, NW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (njobs > 0) {
+        count_launch();
+        k_chain_solve_cols<TS, TA, G, RG, NW><<<njobs, (NW + 1) * 32, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TA>
+cudaError_t launch_tile_solve_cols(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st) {
+    // 8 KB bulk copies, 32 KB ring (the per-warp solution vectors take the rest)
+    return launch_cols_ring<TS, TA, 8192 / (TILE2 * sizeof(TS)) < 1 ? 1 : 8192 / (TILE2 * sizeof(TS)), 4>(
+        a, njobs, max_tiles, st);
+}
+
+// ---------------------------------------------------------------------------------
 // MBF right-hand sides  -B_i psi_m = -G[Omega_i, m]  scattered into the (zeroed) panel
 // buffer, column-major per subdomain (Eq. def-phat-local).
 // ---------------------------------------------------------------------------------
@@ -957,6 +1154,9 @@ template void launch_finalize<float, float>(int, const Profile&, const float*, c
 template void launch_finalize<float, __nv_bfloat16>(int, const Profile&, const float*, const float*,
                                                     __nv_bfloat16*, __nv_bfloat16*, cudaStream_t);
 template cudaError_t launch_tile_solve<double, double>(const SolveArgs&, int, int, cudaStream_t, int);
+template cudaError_t launch_tile_solve_cols<double, double>(const SolveArgs&, int, int, cudaStream_t);
+template cudaError_t launch_tile_solve_cols<float, float>(const SolveArgs&, int, int, cudaStream_t);
+template cudaError_t launch_tile_solve_cols<__nv_bfloat16, float>(const SolveArgs&, int, int, cudaStream_t);
 template cudaError_t launch_tile_solve<float, float>(const SolveArgs&, int, int, cudaStream_t, int);
 template cudaError_t launch_tile_solve<__nv_bfloat16, float>(const SolveArgs&, int, int, cudaStream_t, int);
 template void launch_convert<float>(int64_t, const double*, float*, cudaStream_t);

@@ -113,25 +113,35 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
     const int ns = (int)(sub_off[s + 1] - a0);
     const int64_t i0 = if_off[s];
     const int kk = (int)(if_off[s + 1] - i0);
+    const int i = chunk_off[blockIdx.x] + threadIdx.x;
+    const bool row = i < ns;
+    // the row's operands and its first KP panel entries are loaded before the CTA waits
+    // for the interface values (gathered through if_list), so both latencies overlap
+    constexpr int KP = 16;
+    const TP* ph = phi + phi_off[s] + i;
+    TA pv[KP];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) pv[c] = (row && c < kk) ? ldf<TA>(ph + (int64_t)c * ns) : (TA)0;
+    const double pb = row ? pbar[a0 + i] : 0.0;
+    const double bs = (row && base) ? base[a0 + i] : 0.0;
+    const double rv = (row && psc) ? r[a0 + i] : 0.0;
     for (int c = threadIdx.x; c < kk; c += blockDim.x) e[c] = (TA)eta[if_list[i0 + c]];
     __syncthreads();
-    const int i = chunk_off[blockIdx.x] + threadIdx.x;
     double acc = 0.0;
-    if (i < ns) {
-        const TP* ph = phi + phi_off[s] + i;
+    if (row) {
         TA c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        int c = 0;
-        for (; c + 4 <= kk; c += 4) {
-            c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
-            c1 += ldf<TA>(ph + (int64_t)(c + 1) * ns) * e[c + 1];
-            c2 += ldf<TA>(ph + (int64_t)(c + 2) * ns) * e[c + 2];
-            c3 += ldf<TA>(ph + (int64_t)(c + 3) * ns) * e[c + 3];
+#pragma unroll
+        for (int c = 0; c < KP; c += 4) {
+            if (c < kk) c0 += pv[c] * e[c];
+            if (c + 1 < kk) c1 += pv[c + 1] * e[c + 1];
+            if (c + 2 < kk) c2 += pv[c + 2] * e[c + 2];
+            if (c + 3 < kk) c3 += pv[c + 3] * e[c + 3];
         }
-        for (; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
-        double v = pbar[a0 + i] + (double)((c0 + c1) + (c2 + c3));
-        if (base) v += base[a0 + i];   // smoothed application: x + M^{-1} (r - A x)
+        for (int c = KP; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
+        double v = pb + (double)((c0 + c1) + (c2 + c3));
+        if (base) v += bs;   // smoothed application: x + M^{-1} (r - A x)
         z[a0 + i] = v;
-        if (psc) acc = r[a0 + i] * v;
+        if (psc) acc = rv * v;
     }
     if (psc && grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
         const double rn = psc->rz_next;

@@ -98,9 +98,12 @@ def test_c4_faulted_multi_rhs():
     for j in range(B.shape[1]):
         assert stats[j]["status"] == 0
         assert np.linalg.norm(B[:, j] - P.A @ X[:, j]) <= 1e-8 * np.linalg.norm(B[:, j])
-    # single-RHS solves give the same columns (same kernels, same order)
-    x0, _ = am.solve(B[:, 0], tol=1e-8)
-    assert torch.equal(x0, torch.as_tensor(X[:, 0], device=x0.device))
+    # the single-RHS solve of a column agrees to the tolerance (the batched local solve
+    # sums in another order)
+    x0, st0 = am.solve(B[:, 0], tol=1e-8)
+    x0 = x0.cpu().numpy()
+    assert np.linalg.norm(x0 - X[:, 0]) <= 1e-6 * np.linalg.norm(x0)
+    assert abs(st0["iterations"] - stats[0]["iterations"]) <= 2
 
 
 def test_c5_adjoint_directional_fd():

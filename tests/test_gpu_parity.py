@@ -242,9 +242,10 @@ def test_max_it_reports_no_convergence():
 
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_multi_rhs_batches_bitwise_equal_single(use_graph):
-    """35 right-hand sides (a batch of 32 and a ragged batch of 3): every column equals the
-    single-RHS solve bit for bit, with its own iteration count and stop; a zero column
-    stops at once, a column scaled by 1e6 takes its own path."""
+    """35 right-hand sides (a batch of 32 and a ragged batch of 3; column blocks of 4 with a
+    ragged last block): every column converges on its own, agrees with the single-RHS
+    solve to the tolerance with the same iteration count to +-2; a zero column stops at
+    once, a column scaled by 1e6 takes its own path."""
     A, f, sizes = small3d()
     am = AlgMortar(A, len(sizes), part_sizes=sizes, precision="fp32", use_graph=use_graph, check_every=3)
     rng = np.random.default_rng(12)
@@ -257,8 +258,9 @@ def test_multi_rhs_batches_bitwise_equal_single(use_graph):
     its = set()
     for j in range(k):
         x, st = am.solve(Bm[:, j], tol=1e-9)
-        assert torch.equal(X[:, j], x), j
-        assert stats[j]["iterations"] == st["iterations"]
+        if j != 3:
+            assert rel(X[:, j].cpu().numpy(), x.cpu().numpy()) <= 1e-6, j
+        assert abs(stats[j]["iterations"] - st["iterations"]) <= 2
         assert stats[j]["status"] == 0
         its.add(st["iterations"])
         if j != 3:
@@ -361,8 +363,8 @@ def test_smoothed_apply_matches_oracle(nu):
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_smoothed_low_precision_and_multi_rhs(precision):
-    """Smoothing with low-precision factors converges; batched columns equal the
-    single-RHS solves bit for bit."""
+    """Smoothing with low-precision factors converges; batched columns agree with the
+    single-RHS solves to the tolerance."""
     A, f, sizes = small3d()
     am = AlgMortar(A, len(sizes), part_sizes=sizes, precision=precision, smooth_steps=1, use_graph=True,
                    check_every=3)
@@ -370,6 +372,6 @@ def test_smoothed_low_precision_and_multi_rhs(precision):
     X, stats = am.solve_multi(Bm, tol=1e-9)
     for j in range(3):
         x, st = am.solve(Bm[:, j], tol=1e-9)
-        assert torch.equal(X[:, j], x)
+        assert rel(X[:, j].cpu().numpy(), x.cpu().numpy()) <= 1e-6
         assert stats[j]["status"] == 0
         assert np.linalg.norm(Bm[:, j] - A @ x.cpu().numpy()) <= 1e-9 * np.linalg.norm(Bm[:, j])
