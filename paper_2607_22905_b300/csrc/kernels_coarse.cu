@@ -240,65 +240,78 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
 // advancing tile column k together: tile (I, J) of item g at base[g] + I(I+1)/2 + J,
 // column-major inside the tile; inverse diagonal tiles at dinv + (row0[g] + I) tiles.
 // ---------------------------------------------------------------------------------
-// One warp factors the 32x32 tile A_kk (row `lane` in registers, shuffles only) and
-// inverts the factor.  B300's FP64 rate is ~1/64 of FP32 and a divide is a long
-// sequence of FP64 operations, so the tile takes one square root and one reciprocal per
-// column step (warp-uniform) and no other divides: with D = diag(L) and the unit lower
-// N = D^{-1} L (row scaling), L^{-1} = N^{-1} D^{-1}, i.e. forward substitution with
-// unit pivots followed by a column scaling.
-__global__ void __launch_bounds__(32) k_dpotrf_b(int nitems, const int32_t* __restrict__ T,
-                                                 const int64_t* __restrict__ base,
-                                                 const int64_t* __restrict__ row0, double* __restrict__ work,
-                                                 double* __restrict__ dinv, int k, int* __restrict__ err) {
+// Four warps factor the 32x32 tile A_kk and invert the factor.  B300's FP64 rate is
+// ~1.9 FMA per clock per SM, i.e. a single warp's FP64 instruction occupies its SM
+// sub-partition for ~68 cycles, so the tile's FP64 work is spread over the four
+// sub-partitions: warp w owns columns 8w..8w+7 (row `lane` of them in registers).
+//   factor: for column kk the owner scales it by 1/sqrt(pivot) (one square root and one
+//     reciprocal per column, no other divisions) and publishes it in shared memory; after
+//     a barrier every warp applies the rank-1 update to its own columns right of kk;
+//   inverse: with D = diag(L) and the unit lower N = D^{-1} L, L^{-1} = N^{-1} D^{-1};
+//     the columns of N^{-1} are independent, so each warp forward-substitutes its own 8
+//     columns (rows final in order, row r broadcast by shuffle) and scales them.
+__global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __restrict__ T,
+                                                  const int64_t* __restrict__ base,
+                                                  const int64_t* __restrict__ row0, double* __restrict__ work,
+                                                  double* __restrict__ dinv, int k, int* __restrict__ err) {
+    __shared__ double Ls[TILE][TILE + 1];   // L (column kk published at step kk)
+    __shared__ double rd_s[TILE];           // 1 / L[c][c]
+    __shared__ int bad_s;
     const int g = blockIdx.x;
     if (g >= nitems || k >= T[g]) return;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cb = 8 * w;   // first owned column
     double* t = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
-    double a[TILE];
+    double a[8];
 #pragma unroll
-    for (int c = 0; c < TILE; ++c) a[c] = t[c * TILE + lane];
-    bool bad = false;
-    double rdl = 1.0;   // 1 / L[lane][lane]
-#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = t[(cb + j) * TILE + lane];
+    if (threadIdx.x == 0) bad_s = 0;
+    __syncthreads();
     for (int kk = 0; kk < TILE; ++kk) {
-        double piv = __shfl_sync(0xffffffffu, a[kk], kk);
-        if (!(piv > 0.0) || !isfinite(piv)) {
-            bad = true;
-            piv = 1.0;
+        if (w == (kk >> 3)) {
+            const int j = kk & 7;
+            double piv = __shfl_sync(0xffffffffu, a[j], kk);
+            if (!(piv > 0.0) || !isfinite(piv)) {
+                if (lane == 0) bad_s = 1;
+                piv = 1.0;
+            }
+            const double d = sqrt(piv);
+            const double rdv = 1.0 / d;
+            const double lk = lane > kk ? a[j] * rdv : (lane == kk ? d : 0.0);
+            a[j] = lk;
+            Ls[lane][kk] = lk;
+            if (lane == 0) rd_s[kk] = rdv;
         }
-        const double d = sqrt(piv);
-        const double rd = 1.0 / d;
-        const double lk = lane > kk ? a[kk] * rd : (lane == kk ? d : 0.0);
-        if (lane == kk) rdl = rd;
-        a[kk] = lk;
+        __syncthreads();
+        const double lk = Ls[lane][kk];
 #pragma unroll
-        for (int c = kk + 1; c < TILE; ++c) {
-            const double lck = __shfl_sync(0xffffffffu, lk, c);
-            if (lane >= c) a[c] -= lk * lck;
+        for (int j = 0; j < 8; ++j) {
+            const int c = cb + j;
+            if (c > kk && lane >= c) a[j] -= lk * Ls[c][kk];
         }
     }
-    // Y = N^{-1}: rows final in order; row r is broadcast and eliminated from rows > r
-    double x[TILE];
+    // every column of L is in Ls now (the last step's barrier ordered the writes)
+    double x[8];
 #pragma unroll
-    for (int c = 0; c < TILE; ++c) x[c] = (c == lane) ? 1.0 : 0.0;
-#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = (cb + j == lane) ? 1.0 : 0.0;
+    const double rdl = rd_s[lane];
     for (int r = 0; r < TILE; ++r) {
-        const double nr = a[r] * rdl;   // N[lane][r]
+        const double nr = lane > r ? Ls[lane][r] * rdl : 0.0;   // N[lane][r]
 #pragma unroll
-        for (int c = 0; c < r; ++c) {
-            const double yrc = __shfl_sync(0xffffffffu, x[c], r);
-            if (lane > r) x[c] -= nr * yrc;
+        for (int j = 0; j < 8; ++j) {
+            if (cb + j > r) continue;                            // N^{-1} is lower triangular
+            const double yrc = __shfl_sync(0xffffffffu, x[j], r);
+            x[j] -= nr * yrc;
         }
-        if (lane > r) x[r] -= nr;   // Y[r][r] = 1
     }
     double* D = dinv + (row0[g] + k) * TILE2;
 #pragma unroll
-    for (int c = 0; c < TILE; ++c) {
-        const double sc = __shfl_sync(0xffffffffu, rdl, c);
-        t[c * TILE + lane] = c <= lane ? a[c] : 0.0;
-        D[c * TILE + lane] = x[c] * sc;
+    for (int j = 0; j < 8; ++j) {
+        const int c = cb + j;
+        t[c * TILE + lane] = c <= lane ? Ls[lane][c] : 0.0;
+        D[c * TILE + lane] = x[j] * rd_s[c];
     }
-    if (lane == 0 && bad) {
+    if (threadIdx.x == 0 && bad_s) {
         if (atomicCAS(err + 1, -1, g) == -1) atomicExch(err, 1);
     }
 }
@@ -537,7 +550,7 @@ void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const
             }
         }
         count_launch();
-        k_dpotrf_b<<<nitems, 32, 0, st>>>(nitems, T, base, row0, work, dinv, k, err);
+        k_dpotrf_b<<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, k, err);
         if (nt > 0) {
             count_launch();
             k_dtrsm_b<<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, k);
