@@ -236,7 +236,7 @@ def run_ours(args):
     # roofline of the dominant kernel: the batched local triangular solves
     r = res[best]
     isz = {"fp64": 8, "fp32": 4, "bf16": 2}[best]
-    local_bytes = r["factor_bytes"] + 8 * n * 4          # both sweep streams + rhs, scale x2, out
+    local_bytes = r["factor_bytes"] + 24 * n             # both sweep streams + rhs, out, FP32 scale x2
     local_ms = r["stages_ms"]["local_solve"]
     achieved = local_bytes / (local_ms * 1e-3) / 1e9
     spmv_bytes = 12 * nnz + 4 * (n + 1) + 8 * n * 3       # values+cols, rowptr, p gather+p.q read, q write
