@@ -669,13 +669,22 @@ int numeric_setup(algmortar_t* h) {
         sa.fwdS = W.gf;
         sa.bwdS = W.gb;
         sa.err = h->d_kerr;
+        // one job per column (measured faster than column blocks here: the FP64 work of a
+        // job is spread over four warps and the grids are larger)
+        sa.job_sub = W.d_gjob;
+        sa.job_in = W.d_gjin;
+        sa.job_out = W.d_gjin;
+        sa.job_t0 = W.d_gjt0;          // identity columns: lower triangle of S_gg^{-1} only
         sa.in = W.gE;
         sa.out = (double*)h->nd.Ginv;
-        // identity columns start at their own tile row: lower triangle of S_gg^{-1} only
-        TRY((solve_cols<double, double>(sa, W.bj_g, true, W.max_tiles_items, st)));
+        CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
+        sa.job_t0 = nullptr;
+        sa.job_sub = W.d_wjob;
+        sa.job_in = W.d_wjin;
+        sa.job_out = W.d_wjin;
         sa.in = W.RHS;
         sa.out = (double*)h->nd.Wcm;
-        TRY((solve_cols<double, double>(sa, W.bj_w, false, W.max_tiles_items, st)));
+        CU((launch_tile_solve<double, double>(sa, W.njobs_w, W.max_tiles_items, st)));
         launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
         launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
         if (nsep > 0) {
@@ -695,9 +704,13 @@ int numeric_setup(algmortar_t* h) {
             ca.fwdS = W.cf;
             ca.bwdS = W.cb;
             ca.err = h->d_kerr;
+            ca.job_sub = W.d_cjob;
+            ca.job_in = W.d_cjin;
+            ca.job_out = W.d_cjin;
+            ca.job_t0 = W.d_cjt0;      // lower triangle of C^{-1} only
             ca.in = W.cE;
             ca.out = (double*)h->nd.Cinv;
-            TRY((solve_cols<double, double>(ca, W.bj_c, true, W.cT, st)));   // lower triangle of C^{-1}
+            CU((launch_tile_solve<double, double>(ca, nsep, W.cT, st)));
             launch_mirror_lower(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
         }
         CU(cudaGetLastError());
