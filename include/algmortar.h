@@ -99,7 +99,8 @@ typedef struct {
                                       0 (default) 4 groups of G tiles per bulk copy (FP32
                                       16 KB, BF16 8 KB, FP64 one 8 KB tile), 1 twice the
                                       group size (twice the shared memory, fewer CTAs per
-                                      SM), 2 twice the group size in 2 groups            */
+                                      SM), 2 twice the group size in 2 groups, 3 six
+                                      groups, 4 eight groups                              */
     int32_t smooth_steps;          /* nu >= 0 block-Jacobi smoothing steps before and after
                                       the AlgMortar correction (Sec. 5.4), composed
                                       multiplicatively; blocks = the subdomains, each

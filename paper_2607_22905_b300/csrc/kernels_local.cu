@@ -1086,6 +1086,8 @@ cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cuda
     switch (a.deep_ring) {
         case 1: return launch_ring<TS, TA, 2 * G, 4>(a, njobs, max_tiles, st, ncols);   // 2x ring
         case 2: return launch_ring<TS, TA, 2 * G, 2>(a, njobs, max_tiles, st, ncols);   // 2x copies
+        case 3: return launch_ring<TS, TA, G, 6>(a, njobs, max_tiles, st, ncols);       // 1.5x groups
+        case 4: return launch_ring<TS, TA, G, 8>(a, njobs, max_tiles, st, ncols);       // 2x groups
         default: return launch_ring<TS, TA, G, 4>(a, njobs, max_tiles, st, ncols);
     }
 }
