@@ -97,6 +97,8 @@ struct NumWs {
     int32_t *d_colitem = nullptr, *d_cola = nullptr;
     int64_t ncols_w = 0;
     int64_t *d_doff = nullptr, *d_entbase = nullptr;
+    int64_t* d_wc_ptr = nullptr;   // coupling pattern of S_{g,A_g}: per W column, interior rows
+    int32_t* d_wc_row = nullptr;
     int32_t* d_entg = nullptr;
     int64_t nent = 0;
     double* D = nullptr;
@@ -479,6 +481,32 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         TRY(upload(h, d_sidx, P.nd_sidx));
         TRY(upload(h, d_rowg, row_g));
         TRY(upload(h, d_prowg, prow_g));
+        {
+            // nonzeros of S_{g,A_g}: interior interface i couples to separator interface a
+            // exactly when they share a subdomain (Eq. interface-problem-alg)
+            std::vector<int64_t> wc_ptr{0};
+            std::vector<int32_t> wc_row, tmp;
+            for (int g = 0; g < G; ++g) {
+                const int64_t g0 = P.nd_goff[g], g1 = P.nd_goff[g + 1];
+                for (int64_t j = P.nd_aoff[g]; j < P.nd_aoff[g + 1]; ++j) {
+                    const int32_t I = P.nd_id[P.nd_goff[G] + P.nd_alist[j]];
+                    tmp.clear();
+                    for (int e = 0; e < 2; ++e) {
+                        const int32_t sb = P.pairs[2 * (size_t)I + e];
+                        for (int64_t t = P.if_off[sb]; t < P.if_off[sb + 1]; ++t) {
+                            const int32_t pos = P.nd_pos[P.if_list[t]];
+                            if (pos >= g0 && pos < g1) tmp.push_back((int32_t)(pos - g0));
+                        }
+                    }
+                    std::sort(tmp.begin(), tmp.end());
+                    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+                    wc_row.insert(wc_row.end(), tmp.begin(), tmp.end());
+                    wc_ptr.push_back((int64_t)wc_row.size());
+                }
+            }
+            TRY(upload(h, W.d_wc_ptr, wc_ptr));
+            TRY(upload(h, W.d_wc_row, wc_row));
+        }
         TRY(upload(h, h->d_ndpos, P.nd_pos));
         {
             std::vector<int32_t> gr(G);
@@ -661,9 +689,7 @@ int numeric_setup(algmortar_t* h) {
         CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
         launch_finalize<double, double>(W.nitems, gpf, W.gwork, W.gdinv, W.gf, W.gb, st);
-        // S_gg^{-1} (identity columns) and W_g = S_gg^{-1} S_{g,A_g}
-        launch_nd_rhs(W.ncols_w, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.woff, W.d_colitem,
-                      W.d_cola, W.RHS, st);
+        // S_gg^{-1} (identity columns), then W_g = S_gg^{-1} S_{g,A_g} from its sparse pattern
         SolveArgs sa{};
         sa.pf = gpf;
         sa.fwdS = W.gf;
@@ -678,18 +704,13 @@ int numeric_setup(algmortar_t* h) {
         sa.in = W.gE;
         sa.out = (double*)h->nd.Ginv;
         CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
-        sa.job_t0 = nullptr;
-        sa.job_sub = W.d_wjob;
-        sa.job_in = W.d_wjin;
-        sa.job_out = W.d_wjin;
-        sa.in = W.RHS;
-        sa.out = (double*)h->nd.Wcm;
-        CU((launch_tile_solve<double, double>(sa, W.njobs_w, W.max_tiles_items, st)));
         launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
+        launch_nd_w_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g, W.d_wc_ptr,
+                           W.d_wc_row, h->nd.gioff, h->nd.Ginv, h->nd.woff, (double*)h->nd.Wcm, st);
         launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
         if (nsep > 0) {
-            launch_nd_schur_blocks(W.nent, h->nd.goff, h->nd.aoff, h->nd.woff, W.d_doff, W.d_entg, W.d_entbase, W.RHS,
-                                   h->nd.Wcm, W.D, st);
+            launch_nd_schur_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g,
+                                   W.d_wc_ptr, W.d_wc_row, h->nd.woff, h->nd.Wrm, W.d_doff, W.D, st);
             const int64_t ct = (int64_t)W.cT * (W.cT + 1) / 2;
             launch_nd_schur_tiles(ct, L, nsep, sep0, W.Sd, h->nd.sg, h->nd.sidx, h->nd.aoff, W.d_doff, W.D, W.cwork, st);
             CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));

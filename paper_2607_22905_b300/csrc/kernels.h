@@ -121,6 +121,14 @@ void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int
 void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* aoff, const int64_t* woff,
                             const int64_t* doff, const int32_t* ent_g, const int64_t* ent_base, const double* RHS,
                             const double* Wcm, double* D, cudaStream_t st);
+void launch_nd_w_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
+                        const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
+                        const int32_t* wc_row, const int64_t* gioff, const double* Ginv, const int64_t* woff,
+                        double* Wcm, cudaStream_t st);
+void launch_nd_schur_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
+                            const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
+                            const int32_t* wc_row, const int64_t* woff, const double* Wrm, const int64_t* doff,
+                            double* D, cudaStream_t st);
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
                            const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
                            double* work, cudaStream_t st);

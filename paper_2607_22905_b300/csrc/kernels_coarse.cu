@@ -203,6 +203,78 @@ __global__ void k_nd_schur_blocks(int64_t nent, const int64_t* __restrict__ goff
     if (lane == 0) D[doff[g] + i * ag + j] = s;
 }
 
+// W_g = S_gg^{-1} S_{g,A_g} from the explicit symmetric inverse and the sparse coupling
+// block: S_{g,A_g} has a nonzero (i, a) only where interior interface i and separator
+// interface a share a subdomain, so column a of W_g is a short combination of columns
+// of S_gg^{-1} (n_g * nnz FMAs instead of the n_g^2 * |A_g| of triangular solves).
+// One CTA per column r (group prow_g[r], local column r - aoff[g]); the coupling rows
+// wc_row[wc_ptr[r] .. wc_ptr[r+1]) are local interior indices, values read from Sd.
+__global__ void k_nd_w_sparse(int64_t L, const double* __restrict__ Sd, const int64_t* __restrict__ goff,
+                              const int64_t* __restrict__ aoff, const int32_t* __restrict__ alist, int64_t sep0,
+                              const int32_t* __restrict__ prow_g, const int64_t* __restrict__ wc_ptr,
+                              const int32_t* __restrict__ wc_row, const int64_t* __restrict__ gioff,
+                              const double* __restrict__ Ginv, const int64_t* __restrict__ woff,
+                              double* __restrict__ Wcm) {
+    constexpr int MAXNZ = 256;
+    __shared__ double sv[MAXNZ];
+    __shared__ int32_t si[MAXNZ];
+    const int64_t r = blockIdx.x;
+    const int g = prow_g[r];
+    const int64_t g0 = goff[g], ng = goff[g + 1] - g0, j = r - aoff[g];
+    const int64_t q = sep0 + alist[aoff[g] + j];
+    const double* Gi = Ginv + gioff[g];
+    double* out = Wcm + woff[g] + j * ng;
+    for (int64_t t0 = wc_ptr[r]; t0 < wc_ptr[r + 1]; t0 += MAXNZ) {
+        const int cnt = (int)min((int64_t)MAXNZ, wc_ptr[r + 1] - t0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int32_t i = wc_row[t0 + t];
+            si[t] = i;
+            sv[t] = Sd[(g0 + i) * L + q];
+        }
+        __syncthreads();
+        for (int64_t k = threadIdx.x; k < ng; k += blockDim.x) {
+            double a0 = 0.0, a1 = 0.0;
+            int t = 0;
+            for (; t + 1 < cnt; t += 2) {
+                a0 += Gi[(int64_t)si[t] * ng + k] * sv[t];
+                a1 += Gi[(int64_t)si[t + 1] * ng + k] * sv[t + 1];
+            }
+            if (t < cnt) a0 += Gi[(int64_t)si[t] * ng + k] * sv[t];
+            if (t0 == wc_ptr[r]) out[k] = a0 + a1;
+            else out[k] += a0 + a1;
+        }
+    }
+    if (wc_ptr[r] == wc_ptr[r + 1])
+        for (int64_t k = threadIdx.x; k < ng; k += blockDim.x) out[k] = 0.0;
+}
+
+// D_g = S_{A_g,g} W_g with the same sparse pattern: row j of D_g is sum over the coupling
+// rows i of S(i, a_j) W_g[i, :] (row-major copy of W_g).  One warp per (g, j).
+__global__ void k_nd_schur_sparse(int64_t L, int64_t np, const double* __restrict__ Sd,
+                                  const int64_t* __restrict__ goff, const int64_t* __restrict__ aoff,
+                                  const int32_t* __restrict__ alist, int64_t sep0, const int32_t* __restrict__ prow_g,
+                                  const int64_t* __restrict__ wc_ptr, const int32_t* __restrict__ wc_row,
+                                  const int64_t* __restrict__ woff, const double* __restrict__ Wrm,
+                                  const int64_t* __restrict__ doff, double* __restrict__ D) {
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= np) return;
+    const int g = prow_g[r];
+    const int64_t g0 = goff[g], ag = aoff[g + 1] - aoff[g], j = r - aoff[g];
+    const int64_t q = sep0 + alist[aoff[g] + j];
+    const double* Wg = Wrm + woff[g];
+    double* out = D + doff[g] + j * ag;
+    for (int64_t k = lane; k < ag; k += 32) {
+        double acc = 0.0;
+        for (int64_t t = wc_ptr[r]; t < wc_ptr[r + 1]; ++t) {
+            const int32_t i = wc_row[t];
+            acc += Sd[(g0 + i) * L + q] * Wg[(int64_t)i * ag + k];
+        }
+        out[k] = acc;
+    }
+}
+
 // Lower tiles of C = S_sep,sep - sum_g D_g (symmetrised), one CTA per tile.
 __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double* __restrict__ Sd,
                                  const int32_t* __restrict__ sg, const int32_t* __restrict__ sidx,
@@ -579,6 +651,26 @@ void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* ao
         count_launch();
         k_nd_schur_blocks<<<(unsigned)((nent + 7) / 8), 256, 0, st>>>(nent, goff, aoff, woff, doff, ent_g, ent_base,
                                                                        RHS, Wcm, D);
+    }
+}
+void launch_nd_w_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
+                        const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
+                        const int32_t* wc_row, const int64_t* gioff, const double* Ginv, const int64_t* woff,
+                        double* Wcm, cudaStream_t st) {
+    if (np > 0) {
+        count_launch();
+        k_nd_w_sparse<<<(unsigned)np, 256, 0, st>>>(L, Sd, goff, aoff, alist, sep0, prow_g, wc_ptr, wc_row, gioff,
+                                                    Ginv, woff, Wcm);
+    }
+}
+void launch_nd_schur_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
+                            const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
+                            const int32_t* wc_row, const int64_t* woff, const double* Wrm, const int64_t* doff,
+                            double* D, cudaStream_t st) {
+    if (np > 0) {
+        count_launch();
+        k_nd_schur_sparse<<<(unsigned)((np + 7) / 8), 256, 0, st>>>(L, np, Sd, goff, aoff, alist, sep0, prow_g, wc_ptr,
+                                                                    wc_row, woff, Wrm, doff, D);
     }
 }
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
