@@ -71,7 +71,7 @@ struct DevBlockJobs {
 struct NumWs {
     bool ready = false;
     int njobs_mbf = 0;
-    DevBlockJobs bj_mbf, bj_g, bj_w, bj_c;   // column-block jobs of the setup solves
+    DevBlockJobs bj_mbf;                      // column-block jobs of the MBF solves
     int32_t *d_js = nullptr, *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
     int64_t *d_jo = nullptr, *d_goff = nullptr, *d_gcptr = nullptr;
     double* d_gval = nullptr;
@@ -89,18 +89,13 @@ struct NumWs {
     int32_t *d_titem = nullptr, *d_tI = nullptr, *d_tJ = nullptr;
     int64_t ntiles_items = 0, trows_items = 0;
     int max_tiles_items = 0;
-    double *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr, *gE = nullptr, *RHS = nullptr;
+    double *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr, *gE = nullptr;
     int32_t *d_gjob = nullptr, *d_gjt0 = nullptr, *d_cjt0 = nullptr;
-    int64_t *d_gjin = nullptr, *d_wjin = nullptr;
-    int32_t* d_wjob = nullptr;
-    int njobs_g = 0, njobs_w = 0;
-    int32_t *d_colitem = nullptr, *d_cola = nullptr;
-    int64_t ncols_w = 0;
-    int64_t *d_doff = nullptr, *d_entbase = nullptr;
+    int64_t* d_gjin = nullptr;
+    int njobs_g = 0;
+    int64_t* d_doff = nullptr;
     int64_t* d_wc_ptr = nullptr;   // coupling pattern of S_{g,A_g}: per W column, interior rows
     int32_t* d_wc_row = nullptr;
-    int32_t* d_entg = nullptr;
-    int64_t nent = 0;
     double* D = nullptr;
     // separator Schur complement as a single dense item
     int cT = 0;
@@ -336,18 +331,14 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         const int G = P.nd_G;
         const int64_t nin = P.nd_goff[G];
         const int nsep = P.nd_nsep;
-        std::vector<int32_t> irows, int_, ilo, ihi, titem, tI, tJ, gjob, gjt0, wjob, colitem, cola, entg, row_g,
-            prow_g;
-        std::vector<int64_t> irow0, ibase, ifwd, ibwd, isrc, gjin, wjin, gioff(G, 0), woff(G, 0), doff(G, 0),
-            entbase(G, 0);
-        BlockJobs bg, bw;
-        int64_t trow = 0, tb = 0, gi = 0, wo = 0, dof = 0, ent = 0;
+        std::vector<int32_t> irows, int_, ilo, ihi, titem, tI, tJ, gjob, gjt0, row_g, prow_g;
+        std::vector<int64_t> irow0, ibase, ifwd, ibwd, isrc, gjin, gioff(G, 0), woff(G, 0), doff(G, 0);
+        int64_t trow = 0, tb = 0, gi = 0, wo = 0, dof = 0;
         for (int g = 0; g < G; ++g) {
             const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
             gioff[g] = gi;
             woff[g] = wo;
             doff[g] = dof;
-            entbase[g] = ent;
             for (int64_t t = 0; t < ng; ++t) row_g.push_back(g);
             for (int64_t t = 0; t < ag; ++t) prow_g.push_back(g);
             if (ng > 0) {
@@ -382,29 +373,15 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
                     gjt0.push_back((int32_t)(c / TILE));
                     gjin.push_back(gi + c * ng);
                 }
-                bg.add(it, gi, ng, ng, true);
-                bw.add(it, wo, ng, ag, false);
-                for (int64_t c = 0; c < ag; ++c) {
-                    wjob.push_back(it);
-                    wjin.push_back(wo + c * ng);
-                    colitem.push_back(g);
-                    cola.push_back((int32_t)c);
-                }
-                for (int64_t e = 0; e < ag * ag; ++e) entg.push_back(g);
             }
             gi += ng * ng;
             wo += ng * ag;
             dof += ag * ag;
-            ent += (ng > 0) ? ag * ag : 0;
         }
         W.nitems = (int)irows.size();
         W.ntiles_items = tb;
         W.trows_items = trow;
         W.njobs_g = (int)gjob.size();
-        W.njobs_w = (int)wjob.size();
-        W.ncols_w = (int64_t)colitem.size();
-        W.nent = (int64_t)entg.size();
-        // entries of groups without interior rows contribute nothing: rebase ent indices
         TRY(upload(h, W.d_irows, irows));
         TRY(upload(h, W.d_int, int_));
         TRY(upload(h, W.d_irow0, irow0));
@@ -417,39 +394,20 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         TRY(upload(h, W.d_titem, titem));
         TRY(upload(h, W.d_tI, tI));
         TRY(upload(h, W.d_tJ, tJ));
-        TRY(upload_jobs(h, W.bj_g, bg));
-        TRY(upload_jobs(h, W.bj_w, bw));
         TRY(upload(h, W.d_gjob, gjob));
         TRY(upload(h, W.d_gjin, gjin));
         TRY(upload(h, W.d_gjt0, gjt0));
-        TRY(upload(h, W.d_wjob, wjob));
-        TRY(upload(h, W.d_wjin, wjin));
-        TRY(upload(h, W.d_colitem, colitem));
-        TRY(upload(h, W.d_cola, cola));
-        TRY(upload(h, W.d_entg, entg));
-        // ent_base must index the compacted entry list: recompute from entg
-        {
-            std::vector<int64_t> eb(G, 0);
-            int64_t o = 0;
-            for (int g = 0; g < G; ++g) {
-                eb[g] = o;
-                const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
-                if (ng > 0) o += ag * ag;
-            }
-            TRY(upload(h, W.d_entbase, eb));
-        }
         TRY(upload(h, W.d_doff, doff));
         W.gwork = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
         W.gdinv = h->alloc<double>((size_t)std::max<int64_t>(trow, 1) * TILE2);
         W.gf = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
         W.gb = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
         W.gE = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
-        W.RHS = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
         W.D = h->alloc<double>((size_t)std::max<int64_t>(dof, 1));
         double* Ginv = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
         double* Wcm = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
         double* Wrm = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
-        if (!W.gwork || !W.gdinv || !W.gf || !W.gb || !W.gE || !W.RHS || !W.D || !Ginv || !Wcm || !Wrm)
+        if (!W.gwork || !W.gdinv || !W.gf || !W.gb || !W.gE || !W.D || !Ginv || !Wcm || !Wrm)
             return fail(ALGMORTAR_OOM, "interface group buffers");
         // blocks of groups without interior unknowns are never written: keep them zero
         CU(cudaMemsetAsync(W.D, 0, (size_t)std::max<int64_t>(dof, 1) * sizeof(double), h->st));
@@ -560,11 +518,6 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             TRY(upload(h, W.d_cjob, cj));
             TRY(upload(h, W.d_cjin, cjin));
             TRY(upload(h, W.d_cjt0, cjt0));
-            {
-                BlockJobs bc;
-                bc.add(0, 0, nsep, nsep, true);
-                TRY(upload_jobs(h, W.bj_c, bc));
-            }
             const int64_t ct = (int64_t)T * (T + 1) / 2;
             W.cwork = h->alloc<double>((size_t)ct * TILE2);
             W.cdinv = h->alloc<double>((size_t)T * TILE2);

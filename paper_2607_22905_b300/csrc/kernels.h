@@ -46,23 +46,6 @@ struct SolveArgs {
     const int32_t* job_col0;
 };
 
-struct InterfaceArgs {
-    const int32_t* rows;
-    const int64_t* if_off;
-    const int32_t* if_list;
-    const int64_t* phi_off;
-    const double* phi;         // FP64 MBF panels
-    const int64_t* g_cptr;     // per subdomain k_s + 1 column offsets into g arrays
-    const int32_t* g_row;
-    const double* g_val;
-    const int32_t* pairs;
-    const int32_t* s_iperm;
-    const int32_t* s_lo;
-    const int64_t* s_fwd;
-    double* work;              // interface factor work storage (FP64 tile profile)
-    double* diagc;             // 2 * n_lambda diagonal contributions
-};
-
 struct NdAssembleArgs {
     const int32_t* rows;
     const int64_t* if_off;
@@ -108,19 +91,12 @@ void launch_nd_diag(int L, const double* T, const double* diagc, const int32_t* 
 void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const int64_t* src_off, const int32_t* rows,
                            const int64_t* base, const int32_t* tile_item, const int32_t* tile_I,
                            const int32_t* tile_J, double* work, cudaStream_t st);
-void launch_nd_rhs(int64_t ncols, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
-                   const int32_t* alist, int64_t sep0, const int64_t* woff, const int32_t* col_item,
-                   const int32_t* col_a, double* out, cudaStream_t st);
-void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 // right-looking Cholesky of dense items advancing together (T_host: host copy of T)
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
                            const int64_t* row0, double* work, double* dinv, int* err, cudaStream_t st);
 void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
                              double* Wrm, cudaStream_t st);
-void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* aoff, const int64_t* woff,
-                            const int64_t* doff, const int32_t* ent_g, const int64_t* ent_base, const double* RHS,
-                            const double* Wcm, double* D, cudaStream_t st);
 void launch_nd_w_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
                         const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
                         const int32_t* wc_row, const int64_t* gioff, const double* Ginv, const int64_t* woff,
@@ -149,10 +125,6 @@ void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st);
 template <typename TW>
 void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
                       cudaStream_t st);
-// right-looking multi-CTA factor of one profile matrix; h_hi: host copy of hi[]
-template <typename TW>
-void launch_rl_cholesky(int T, const int32_t* d_lo, const int64_t* d_fwd, const int32_t* h_hi, TW* work, TW* dinv,
-                        int* err, cudaStream_t st);
 template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
                      cudaStream_t st);
@@ -168,11 +140,7 @@ void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int
                     cudaStream_t st);
 template <typename TS>
 void launch_convert(int64_t n, const double* src, TS* dst, cudaStream_t st);
-void launch_interface_assemble(int m, const InterfaceArgs& a, cudaStream_t st);
-void launch_interface_diag(int L, const double* T, const double* diagc, const int32_t* s_iperm,
-                           const int32_t* s_lo, const int64_t* s_fwd, double* work, cudaStream_t st);
 void launch_eye(int L, double* E, cudaStream_t st);
-void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double* Sinv, cudaStream_t st);
 
 // vector / PCG kernels (kernels_pcg.cu)
 constexpr int VEC_BS = 256;

@@ -123,36 +123,6 @@ __global__ void k_dense_to_tiles(const double* __restrict__ src, int64_t ld, con
     }
 }
 
-// Column-major n_g x a_g right-hand sides S[g rows, A_g columns] from Sd.
-__global__ void k_nd_rhs(int64_t L, const double* __restrict__ Sd, const int64_t* __restrict__ goff,
-                         const int64_t* __restrict__ aoff, const int32_t* __restrict__ alist, int64_t sep0,
-                         const int64_t* __restrict__ woff, const int32_t* __restrict__ col_item,
-                         const int32_t* __restrict__ col_a, double* __restrict__ out) {
-    const int64_t c = blockIdx.x;
-    const int g = col_item[c], aa = col_a[c];
-    const int64_t ng = goff[g + 1] - goff[g];
-    const int64_t q = sep0 + alist[aoff[g] + aa];
-    double* o = out + woff[g] + (int64_t)aa * ng;
-    for (int64_t i = threadIdx.x; i < ng; i += blockDim.x) o[i] = Sd[(goff[g] + i) * L + q];
-}
-
-// In-place symmetrisation of column-major square blocks: M = (M + M^T) / 2.
-__global__ void k_symmetrise(const int32_t* __restrict__ rows, const int64_t* __restrict__ off, int nitems,
-                             double* __restrict__ M) {
-    const int g = blockIdx.y;
-    if (g >= nitems) return;
-    const int64_t n = rows[g];
-    double* A = M + off[g];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / n, j = e % n;
-        if (i < j) {
-            const double v = 0.5 * (A[i * n + j] + A[j * n + i]);
-            A[i * n + j] = v;
-            A[j * n + i] = v;
-        }
-    }
-}
-
 // Column-major square blocks whose lower triangle holds a symmetric matrix: copy it to
 // the upper triangle (M[j][i] = M[i][j] for i > j).
 __global__ void k_mirror_lower(const int32_t* __restrict__ rows, const int64_t* __restrict__ off, int nitems,
@@ -179,28 +149,6 @@ __global__ void k_transpose_blocks(const int64_t* __restrict__ goff, const int64
         const int64_t i = e / ag, j = e % ag;
         Wrm[woff[g] + e] = Wcm[woff[g] + j * ng + i];
     }
-}
-
-// D_g = S_{A_g,g} W_g  (a_g x a_g, row-major), one warp per entry.
-__global__ void k_nd_schur_blocks(int64_t nent, const int64_t* __restrict__ goff, const int64_t* __restrict__ aoff,
-                                  const int64_t* __restrict__ woff, const int64_t* __restrict__ doff,
-                                  const int32_t* __restrict__ ent_g, const int64_t* __restrict__ ent_base,
-                                  const double* __restrict__ RHS, const double* __restrict__ Wcm,
-                                  double* __restrict__ D) {
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= nent) return;
-    const int g = ent_g[wid];
-    const int64_t ng = goff[g + 1] - goff[g], ag = aoff[g + 1] - aoff[g];
-    const int64_t e = wid - ent_base[g];
-    const int64_t i = e / ag, j = e % ag;
-    const double* x = RHS + woff[g] + i * ng;
-    const double* y = Wcm + woff[g] + j * ng;
-    double s = 0.0;
-    for (int64_t t = lane; t < ng; t += 32) s += x[t] * y[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) D[doff[g] + i * ag + j] = s;
 }
 
 // W_g = S_gg^{-1} S_{g,A_g} from the explicit symmetric inverse and the sparse coupling
@@ -594,20 +542,6 @@ void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const 
                                                            work);
     }
 }
-void launch_nd_rhs(int64_t ncols, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
-                   const int32_t* alist, int64_t sep0, const int64_t* woff, const int32_t* col_item,
-                   const int32_t* col_a, double* out, cudaStream_t st) {
-    if (ncols > 0) {
-        count_launch();
-        k_nd_rhs<<<(unsigned)ncols, 256, 0, st>>>(L, Sd, goff, aoff, alist, sep0, woff, col_item, col_a, out);
-    }
-}
-void launch_symmetrise(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st) {
-    if (nitems > 0) {
-        count_launch();
-        k_symmetrise<<<dim3(256, nitems), 256, 0, st>>>(rows, off, nitems, M);
-    }
-}
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
                            const int64_t* row0, double* work, double* dinv, int* err, cudaStream_t st) {
     int maxT = 0;
@@ -642,15 +576,6 @@ void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int
     if (G > 0) {
         count_launch();
         k_transpose_blocks<<<dim3(256, G), 256, 0, st>>>(goff, aoff, woff, G, Wcm, Wrm);
-    }
-}
-void launch_nd_schur_blocks(int64_t nent, const int64_t* goff, const int64_t* aoff, const int64_t* woff,
-                            const int64_t* doff, const int32_t* ent_g, const int64_t* ent_base, const double* RHS,
-                            const double* Wcm, double* D, cudaStream_t st) {
-    if (nent > 0) {
-        count_launch();
-        k_nd_schur_blocks<<<(unsigned)((nent + 7) / 8), 256, 0, st>>>(nent, goff, aoff, woff, doff, ent_g, ent_base,
-                                                                       RHS, Wcm, D);
     }
 }
 void launch_nd_w_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,

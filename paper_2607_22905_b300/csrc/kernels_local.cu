@@ -205,89 +205,6 @@ __global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __
 
 
 // ---------------------------------------------------------------------------------
-// Right-looking tile Cholesky of ONE large profile matrix (the interface system), spread
-// over many CTAs: for each tile column k, (1) factor the updated diagonal tile, (2) form
-// the panel L_Ik = S_Ik L_kk^{-T} for I = k+1 .. hi(k), (3) update the trailing tiles
-// S_IJ -= L_Ik L_Jk^T for k < J <= I <= hi(k).  Tiles outside the profile never change.
-// ---------------------------------------------------------------------------------
-template <typename TW>
-__global__ void __launch_bounds__(256) k_rl_potrf(const int32_t* __restrict__ lo, const int64_t* __restrict__ fwd,
-                                                  TW* __restrict__ work, TW* __restrict__ dinv, int k,
-                                                  int* __restrict__ err) {
-    __shared__ TW X[TILE][TILE + 1];
-    __shared__ TW As[TILE][TILE + 1];
-    __shared__ int bad;
-    const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
-    TW* t = work + (fwd[k] + (k - lo[k])) * TILE2;
-    for (int e = tid; e < TILE2; e += 256) X[e & 31][e >> 5] = t[e];
-    __syncthreads();
-    chol_inv_tile<TW>(X, As, tid, &bad);
-    TW* D = dinv + (int64_t)k * TILE2;
-    for (int e = tid; e < TILE2; e += 256) {
-        int r = e & 31, cc = e >> 5;
-        t[e] = r >= cc ? X[r][cc] : (TW)0;
-        D[e] = As[r][cc];
-    }
-    if (tid == 0 && bad) {
-        if (atomicCAS(err + 1, -1, k) == -1) atomicExch(err, 1);
-    }
-}
-
-template <typename TW>
-__global__ void __launch_bounds__(256) k_rl_trsm(const int32_t* __restrict__ lo, const int64_t* __restrict__ fwd,
-                                                 TW* __restrict__ work, const TW* __restrict__ dinv, int k) {
-    __shared__ TW X[TILE][TILE + 1];
-    __shared__ TW Bs[TILE][TILE + 1];
-    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
-    const int I = k + 1 + blockIdx.x;
-    TW* t = work + (fwd[I] + (k - lo[I])) * TILE2;
-    const TW* D = dinv + (int64_t)k * TILE2;
-    for (int e = tid; e < TILE2; e += 256) {
-        X[e & 31][e >> 5] = t[e];
-        Bs[e & 31][e >> 5] = D[e];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        TW v = 0;
-#pragma unroll 8
-        for (int u = 0; u < TILE; ++u) v += X[rb + q][u] * Bs[c][u];
-        t[c * TILE + rb + q] = v;
-    }
-}
-
-template <typename TW>
-__global__ void __launch_bounds__(256) k_rl_update(const int32_t* __restrict__ lo, const int64_t* __restrict__ fwd,
-                                                   TW* __restrict__ work, int k) {
-    __shared__ TW As[TILE][TILE + 1];
-    __shared__ TW Bs[TILE][TILE + 1];
-    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
-    // pair index -> (a >= b) in the lower triangle of the w x w trailing block
-    const int64_t p = blockIdx.x;
-    int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= p) ++a;
-    while ((int64_t)a * (a + 1) / 2 > p) --a;
-    const int b = (int)(p - (int64_t)a * (a + 1) / 2);
-    const int I = k + 1 + a, J = k + 1 + b;
-    const TW* LI = work + (fwd[I] + (k - lo[I])) * TILE2;
-    const TW* LJ = work + (fwd[J] + (k - lo[J])) * TILE2;
-    TW* t = work + (fwd[I] + (J - lo[I])) * TILE2;
-    for (int e = tid; e < TILE2; e += 256) {
-        As[e & 31][e >> 5] = LI[e];
-        Bs[e & 31][e >> 5] = LJ[e];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        TW v = t[c * TILE + rb + q];
-#pragma unroll 8
-        for (int u = 0; u < TILE; ++u) v -= As[rb + q][u] * Bs[c][u];
-        t[c * TILE + rb + q] = v;
-    }
-}
-
-// ---------------------------------------------------------------------------------
 // Sweep streams from the factor: forward rows [L_I,lo .. L_I,I-1 | L_II^{-1}], backward
 // rows [(L_I+1,I)^T .. (L_hi,I)^T | L_II^{-T}], in precision TS.  Every 32x32 tile M is
 // stored row-major with its 16-byte chunks XOR-swizzled (swz_index), so that the solve
@@ -914,79 +831,10 @@ __global__ void k_convert(int64_t n, const double* __restrict__ src, TS* __restr
         dst[i] = stf<TS>(src[i]);
 }
 
-// ---------------------------------------------------------------------------------
-// Interface matrix S_eta = diag(T) + 1/4 G^T Phi  (Eq. interface-problem-alg with
-// W M = B^T / 4, Prop. proposition-BWM), written into the tile profile of its RCM order.
-// One CTA per subdomain; one warp per pair (a <= b) of the subdomain's interfaces.
-// Off-diagonal entries come from the one subdomain the two interfaces share and are
-// symmetrised there; diagonal contributions of the two sides go to diagc and are
-// summed in a fixed order by k_interface_diag.
-// ---------------------------------------------------------------------------------
-__global__ void k_interface_assemble(InterfaceArgs a) {
-    const int s = blockIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t i0 = a.if_off[s];
-    const int k = (int)(a.if_off[s + 1] - i0);
-    const int64_t ns = a.rows[s];
-    const double* phi = a.phi + a.phi_off[s];
-    const int64_t* cp = a.g_cptr + i0 + s;
-    for (int pr = w; pr < k * k; pr += nw) {
-        const int ai = pr / k, bi = pr % k;
-        if (bi < ai) continue;
-        double cab = 0.0, cba = 0.0;
-        for (int64_t t = cp[ai] + lane; t < cp[ai + 1]; t += 32)
-            cab += a.g_val[t] * phi[bi * ns + a.g_row[t]];
-        for (int64_t t = cp[bi] + lane; t < cp[bi + 1]; t += 32)
-            cba += a.g_val[t] * phi[ai * ns + a.g_row[t]];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            cab += __shfl_xor_sync(0xffffffffu, cab, o);
-            cba += __shfl_xor_sync(0xffffffffu, cba, o);
-        }
-        if (lane == 0) {
-            const int I = a.if_list[i0 + ai], J = a.if_list[i0 + bi];
-            if (ai == bi) {
-                const int side = (a.pairs[2 * I] == s) ? 0 : 1;
-                a.diagc[2 * I + side] = 0.25 * cab;
-            } else {
-                int p = a.s_iperm[I], q = a.s_iperm[J];
-                if (p < q) { int t = p; p = q; q = t; }
-                const int64_t P = p >> 5, Q = q >> 5;
-                const int64_t tl = a.s_fwd[P] + (Q - a.s_lo[P]);
-                a.work[tl * TILE2 + (q & 31) * TILE + (p & 31)] = 0.125 * (cab + cba);
-            }
-        }
-    }
-}
-
-__global__ void k_interface_diag(int L, const double* __restrict__ T, const double* __restrict__ diagc,
-                                 const int32_t* __restrict__ s_iperm, const int32_t* __restrict__ s_lo,
-                                 const int64_t* __restrict__ s_fwd, double* __restrict__ work) {
-    int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= L) return;
-    int p = s_iperm[I];
-    int64_t P = p >> 5;
-    int64_t tl = s_fwd[P] + (P - s_lo[P]);
-    work[tl * TILE2 + (p & 31) * (TILE + 1)] = T[I] + diagc[2 * I] + diagc[2 * I + 1];
-}
-
 // Identity right-hand sides for the explicit interface inverse (column q = e_q).
 __global__ void k_eye(int L, double* __restrict__ E) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < L) E[(int64_t)q * L + q] = 1.0;
-}
-
-// Sinv[I][J] (natural interface order, row-major) = symmetric part of the RCM-ordered
-// inverse computed column by column.
-__global__ void k_sinv_finalize(int L, const int32_t* __restrict__ s_iperm, const double* __restrict__ R,
-                                double* __restrict__ Sinv) {
-    int64_t total = (int64_t)L * L;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int I = (int)(e / L), J = (int)(e % L);
-        int64_t p = s_iperm[I], q = s_iperm[J];
-        Sinv[e] = 0.5 * (R[q * L + p] + R[p * L + q]);
-    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -1027,22 +875,6 @@ void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* w
                       cudaStream_t st) {
     count_launch();
     k_tile_chol<TW><<<nitems, 256, 0, st>>>(pf, order, work, dinv, err);
-}
-
-template <typename TW>
-void launch_rl_cholesky(int T, const int32_t* d_lo, const int64_t* d_fwd, const int32_t* h_hi, TW* work, TW* dinv,
-                        int* err, cudaStream_t st) {
-    for (int k = 0; k < T; ++k) {
-        count_launch();
-        k_rl_potrf<TW><<<1, 256, 0, st>>>(d_lo, d_fwd, work, dinv, k, err);
-        const int w = h_hi[k] - k;
-        if (w > 0) {
-            count_launch();
-            k_rl_trsm<TW><<<w, 256, 0, st>>>(d_lo, d_fwd, work, dinv, k);
-            count_launch();
-            k_rl_update<TW><<<(unsigned)((int64_t)w * (w + 1) / 2), 256, 0, st>>>(d_lo, d_fwd, work, k);
-        }
-    }
 }
 
 template <typename TW, typename TS>
@@ -1109,32 +941,10 @@ void launch_convert(int64_t n, const double* src, TS* dst, cudaStream_t st) {
     }
 }
 
-void launch_interface_assemble(int m, const InterfaceArgs& a, cudaStream_t st) {
-    if (m > 0) {
-        count_launch();
-        k_interface_assemble<<<m, 256, 0, st>>>(a);
-    }
-}
-
-void launch_interface_diag(int L, const double* T, const double* diagc, const int32_t* s_iperm,
-                           const int32_t* s_lo, const int64_t* s_fwd, double* work, cudaStream_t st) {
-    if (L > 0) {
-        count_launch();
-        k_interface_diag<<<(L + 127) / 128, 128, 0, st>>>(L, T, diagc, s_iperm, s_lo, s_fwd, work);
-    }
-}
-
 void launch_eye(int L, double* E, cudaStream_t st) {
     if (L > 0) {
         count_launch();
         k_eye<<<(L + 127) / 128, 128, 0, st>>>(L, E);
-    }
-}
-
-void launch_sinv_finalize(int L, const int32_t* s_iperm, const double* R, double* Sinv, cudaStream_t st) {
-    if (L > 0) {
-        count_launch();
-        k_sinv_finalize<<<grid_for((int64_t)L * L, 256), 256, 0, st>>>(L, s_iperm, R, Sinv);
     }
 }
 
@@ -1147,8 +957,6 @@ template void launch_scatter_local<float>(int64_t, const int32_t*, const int32_t
 template void launch_pad_diag<double>(int, const Profile&, double*, cudaStream_t);
 template void launch_tile_chol<double>(int, const Profile&, const int32_t*, double*, double*, int*, cudaStream_t);
 template void launch_tile_chol<float>(int, const Profile&, const int32_t*, float*, float*, int*, cudaStream_t);
-template void launch_rl_cholesky<double>(int, const int32_t*, const int64_t*, const int32_t*, double*, double*,
-                                         int*, cudaStream_t);
 template void launch_finalize<double, double>(int, const Profile&, const double*, const double*, double*,
                                               double*, cudaStream_t);
 template void launch_finalize<float, float>(int, const Profile&, const float*, const float*, float*, float*,
