@@ -406,12 +406,16 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <typename TS, typename TA, int G, int RG, int NW>
-__global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
-    // ring of R = RG * G tile slots filled by bulk copies of G consecutive tiles: fewer,
-    // larger copies keep more bytes in flight per copy issued
-    static_assert(RG % 2 == 0, "the barrier block keeps 16-byte alignment for even RG");
+template <typename TS, typename TA, int G, int RG, int CR, int NW>
+__global__ void __launch_bounds__((NW + 2) * 32) k_chain_solve(SolveArgs a) {
+    // Two rings.  The critical ring holds, per step (tile row), the two tiles on the
+    // chain's critical path -- the off-diagonal tile next to the diagonal and the inverse
+    // diagonal tile -- CR steps ahead; the main ring holds the remaining ("far")
+    // off-diagonal tiles, R = RG * G slots filled by bulk copies of G far tiles.
     constexpr int R = RG * G;
+    // 8-byte words of barriers, flags and slot tags, padded so that what follows stays
+    // 16-byte aligned (128-bit shared loads)
+    constexpr int HDR = 3 * RG + 2 * CR + 3, HDRP = HDR + (HDR & 1);
     // batched solves put the column in blockIdx.x, so the CTAs of one subdomain's columns
     // run side by side and share its factor stream through L2
     const int col = a.col_fast ? blockIdx.x : 0;
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
     // then stream positions [q0, qend), still contiguous.
     const int t0 = a.job_t0 ? a.job_t0[job] : 0;
     const int64_t q0 = pf.fwd[r0 + t0];
-    const int64_t qend = nts + pf.bwd[r0 + t0] + (pf.hi[r0 + t0] - t0) + 1;
+    const int nsteps = 2 * (T - t0);
     const TS* F = (const TS*)a.fwdS + pf.base[s] * TILE2;
     const TS* Bk = (const TS*)a.bwdS + pf.base[s] * TILE2;
     const double* sc = a.scale ? a.scale + a.scale_off[s] : nullptr;
@@ -436,95 +440,169 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
     const double* in = a.in + a.job_in[job] + col * a.ldin;
     double* out = a.out + a.job_out[job] + col * a.ldout;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    constexpr int NT = (NW + 2) * 32;
     constexpr uint32_t TB = TILE2 * sizeof(TS);
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TS* ring = reinterpret_cast<TS*>(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + R * TB);   // per group slot
-    uint64_t* empty = full + RG;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + RG);
-    int64_t* issued = reinterpret_cast<int64_t*>(empty + RG + 1);
-    // first stream position of the group last issued into each group slot: a consumer
-    // waits for its own group here before the mbarrier, because tiles are released out of
-    // order (by different warps) and a parity wait cannot tell "use u + 1 landed" from
-    // "use u not landed yet"
-    volatile int64_t* slot_q = reinterpret_cast<volatile int64_t*>(empty + RG + 2);
-    TA* part = reinterpret_cast<TA*>(empty + 2 * RG + 2);   // [2][NW][32]
-    TA* tbuf = part + 2 * NW * TILE;                    // [32] (warp 0)
+    TS* cring = ring + (int64_t)R * TILE2;                                   // [CR][2 tiles]
+    uint64_t* full = reinterpret_cast<uint64_t*>(cring + (int64_t)2 * CR * TILE2);   // [RG]
+    uint64_t* empty = full + RG;                                             // [RG]
+    uint64_t* cfull = empty + RG;                                            // [CR]
+    uint64_t* cempty = cfull + CR;                                           // [CR]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(cempty + CR);
+    int64_t* issued = reinterpret_cast<int64_t*>(cempty + CR + 1);   // [0] far groups, [1] steps
+    // index of the far group last issued into each group slot: tiles are released out of
+    // order (by different warps), and a parity wait alone cannot tell "use u + 1 landed"
+    // from "use u not landed yet", so a consumer first waits for its own group here
+    volatile int64_t* slot_g = reinterpret_cast<volatile int64_t*>(cempty + CR + 3);   // [RG]
+    TA* part = reinterpret_cast<TA*>(full + HDRP);            // [2][NW][32]
+    TA* tbuf = part + 2 * NW * TILE;                          // [32] (warp 0)
     int32_t* lo_s = reinterpret_cast<int32_t*>(tbuf + TILE);
     int32_t* hi_s = lo_s + T;
     TA* v = reinterpret_cast<TA*>(hi_s + T + ((2 * T) & 3));   // 16-byte aligned
     auto src = [&](int64_t q) -> const TS* { return q < nts ? F + q * TILE2 : Bk + (q - nts) * TILE2; };
+    // step k: tile row, number of off-diagonal tiles, first stream position
+    auto row_of = [&](int k) { return k < T - t0 ? t0 + k : T - 1 - (k - (T - t0)); };
+    auto nt_of = [&](int k) {
+        const int I = row_of(k);
+        return k < T - t0 ? I - lo_s[I] : hi_s[I] - I;
+    };
     if (tid == 0) {
         for (int i = 0; i < RG; ++i) {
             mbar_init(smem_u32(&full[i]), 1);
             mbar_init(smem_u32(&empty[i]), G);   // one release per tile of the group
-            slot_q[i] = -1;
+            slot_g[i] = -1;
+        }
+        for (int i = 0; i < CR; ++i) {
+            mbar_init(smem_u32(&cfull[i]), 1);
+            mbar_init(smem_u32(&cempty[i]), 1);  // warp 0 releases the pair once
         }
         *abort_flag = 0;
-        *issued = q0;
+        issued[0] = 0;
+        issued[1] = 0;
         fence_async_smem();
     }
-    for (int i = tid; i < T; i += (NW + 1) * 32) {
+    for (int i = tid; i < T; i += NT) {
         lo_s[i] = pf.lo[r0 + i];
         hi_s[i] = pf.hi[r0 + i];
     }
     // scaling in the solve's arithmetic: FP32 solves scale in FP32 (B300's FP64 pipe is
     // ~1/64 of FP32, so FP64 work per row is kept off the chain's prologue/epilogue)
     if constexpr (sizeof(TA) == 4) {
-        for (int i = tid; i < T * TILE; i += (NW + 1) * 32)
-            v[i] = i < n ? (float)in[i] * (sc32 ? sc32[i] : 1.0f) : 0.0f;
+        for (int i = tid; i < T * TILE; i += NT) v[i] = i < n ? (float)in[i] * (sc32 ? sc32[i] : 1.0f) : 0.0f;
     } else {
-        for (int i = tid; i < T * TILE; i += (NW + 1) * 32) v[i] = i < n ? in[i] * (sc ? sc[i] : 1.0) : 0.0;
+        for (int i = tid; i < T * TILE; i += NT) v[i] = i < n ? in[i] * (sc ? sc[i] : 1.0) : 0.0;
     }
     __syncthreads();
 
-    if (w == NW) {
-        // Producer warp: one lane streams the tiles through the ring in storage order, G
-        // tiles per group.  A group slot is reloaded once every tile of its previous group
-        // has been released by the warp that read it (G arrivals on empty[slot]).
+    if (w == NW + 1) {
+        // Critical producer: per step, the nearest off-diagonal tile and the diagonal tile
+        // into slot k % CR once warp 0 has released step k - CR.
         if (lane == 0) {
-            int64_t g0 = q0;
-            for (; g0 < qend; g0 += G) {
-                const int64_t gi = (g0 - q0) / G;
+            int64_t q = q0;
+            int k = 0;
+            for (; k < nsteps; ++k) {
+                const int nt = nt_of(k);
+                const int cs = k % CR, u = k / CR;
+                if (u > 0 && (*abort_flag || !mbar_poll(smem_u32(&cempty[cs]), (uint32_t)((u - 1) & 1)))) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const uint32_t bar = smem_u32(&cfull[cs]);
+                TS* dst = cring + (int64_t)(2 * cs) * TILE2;
+                mbar_expect_tx(bar, (uint32_t)(nt > 0 ? 2 : 1) * TB);
+                if (nt == 0) {
+                    bulk_copy(smem_u32(dst + TILE2), src(q), TB, bar);
+                } else if (k < T - t0) {   // forward: nearest and diagonal are adjacent
+                    bulk_copy(smem_u32(dst), src(q + nt - 1), 2 * TB, bar);
+                } else {                   // backward: nearest first in the row
+                    bulk_copy(smem_u32(dst), src(q), TB, bar);
+                    bulk_copy(smem_u32(dst + TILE2), src(q + nt), TB, bar);
+                }
+                q += nt + 1;
+            }
+            issued[1] = k;
+        }
+    } else if (w == NW) {
+        // Far producer: the far tiles of the steps in order, G per group (a group may span
+        // several rows: one copy per contiguous run); a group slot is reloaded once every
+        // tile of its previous group has been released.
+        if (lane == 0) {
+            int k = 0, off = 0;
+            int64_t q = q0;
+            int nt = nsteps > 0 ? nt_of(0) : 0;
+            int64_t gi = 0;
+            auto nf_of = [&](int nt_) { return nt_ > 1 ? nt_ - 1 : 0; };
+            while (true) {
+                while (k < nsteps && off >= nf_of(nt)) {   // next step with far tiles left
+                    q += nt + 1;
+                    ++k;
+                    off = 0;
+                    if (k < nsteps) nt = nt_of(k);
+                }
+                if (k >= nsteps) break;
                 const int gs = (int)(gi % RG);
                 const int64_t u = gi / RG;
                 if (u > 0 && (*abort_flag || !mbar_poll(smem_u32(&empty[gs]), (uint32_t)((u - 1) & 1)))) {
                     *abort_flag = 1;
                     break;
                 }
-                const int cnt = (int)min((int64_t)G, qend - g0);
-                slot_q[gs] = g0;
+                // gather the group: up to G far tiles, as contiguous runs
+                int64_t seg_p[G];
+                int seg_n[G];
+                int nseg = 0, cnt = 0;
+                int k2 = k, off2 = off, nt2 = nt;
+                int64_t q2 = q;
+                while (cnt < G && k2 < nsteps) {
+                    const int nf2 = nf_of(nt2);
+                    if (off2 < nf2) {
+                        const int m = min(G - cnt, nf2 - off2);
+                        // far tiles of a forward row: t = 0 .. nt-2; backward: t = 1 .. nt-1
+                        const int64_t p = q2 + (k2 < T - t0 ? 0 : 1) + off2;
+                        seg_p[nseg] = p;
+                        seg_n[nseg] = m;
+                        ++nseg;
+                        cnt += m;
+                        off2 += m;
+                    }
+                    if (off2 >= nf2) {
+                        q2 += nt2 + 1;
+                        ++k2;
+                        off2 = 0;
+                        if (k2 < nsteps) nt2 = nt_of(k2);
+                    }
+                }
+                k = k2;
+                off = off2;
+                nt = nt2;
+                q = q2;
+                slot_g[gs] = gi;
                 const uint32_t bar = smem_u32(&full[gs]);
                 mbar_expect_tx(bar, (uint32_t)cnt * TB);
                 TS* dst = ring + (int64_t)(gs * G) * TILE2;
-                // a group may straddle the end of the forward stream: split the copy there
-                const int c1 = g0 < nts ? (int)min((int64_t)cnt, nts - g0) : 0;
-                if (c1 > 0) bulk_copy(smem_u32(dst), src(g0), (uint32_t)c1 * TB, bar);
-                if (cnt > c1) bulk_copy(smem_u32(dst + (int64_t)c1 * TILE2), src(g0 + c1), (uint32_t)(cnt - c1) * TB, bar);
-                const int64_t qp = g0 + G + a.l2_ahead;   // optional L2 window ahead of the ring
-                if (a.l2_ahead > 0 && qp < qend) {
-                    const int64_t qe = min(qp + G, qp < nts ? min(nts, qend) : qend);   // one stream
-                    l2_prefetch(src(qp), (uint32_t)(qe - qp) * TB);
+                for (int e = 0; e < nseg; ++e) {
+                    bulk_copy(smem_u32(dst), src(seg_p[e]), (uint32_t)seg_n[e] * TB, bar);
+                    dst += (int64_t)seg_n[e] * TILE2;
                 }
+                ++gi;
             }
-            *issued = g0;
+            issued[0] = gi;
         }
     } else {
         // Consumer warps.  Step for tile row I: warp 0 takes the off-diagonal tile nearest
         // the diagonal (it needs the row solved in the previous step, which warp 0 itself
-        // produced), warps 1..NW-1 share the others (they need only rows solved at least
+        // produced), warps 1..NW-1 share the far tiles (they need only rows solved at least
         // two steps back, ordered by the previous step's barrier), one named barrier, then
         // warp 0 alone reduces the partial sums and applies the stored inverse diagonal
         // tile.  Every tile is read by exactly one warp, which releases it at once.
-        auto wait_full = [&](int64_t qq) -> const TS* {
-            const int64_t gi = (qq - q0) / G;
+        auto wait_far = [&](int64_t f) -> const TS* {
+            const int64_t gi = f / G;
             const int gs = (int)(gi % RG);
             if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
-                const int64_t gq = q0 + gi * G;
                 bool r = false;
                 for (long long i = 0; i < kWaitLimit; ++i)
-                    if (slot_q[gs] == gq) {
+                    if (slot_g[gs] == gi) {
                         r = true;
                         break;
                     }
@@ -532,83 +610,85 @@ __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve(SolveArgs a) {
                 r = __all_sync(0xffffffffu, r);
                 if (!r && lane == 0) *abort_flag = 1;
             }
-            return ring + ((qq - q0) % R) * TILE2;
+            return ring + (f % R) * TILE2;
         };
-        auto release = [&](int64_t qq) {
+        auto release_far = [&](int64_t f) {
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&empty[((qq - q0) / G) % RG]));
+            if (lane == 0) mbar_arrive(smem_u32(&empty[(f / G) % RG]));
         };
-        int64_t q = q0;
-        int par = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int step = t0; step < T; ++step) {
-                const int I = pass == 0 ? step : T - 1 - (step - t0);
-                const int j0 = pass == 0 ? lo_s[I] : I + 1;
-                const int nt = pass == 0 ? I - lo_s[I] : hi_s[I] - I;
-                TA acc = 0;
-                if (w == 0) {
-                    if (nt > 0) {
-                        const int tn = pass == 0 ? nt - 1 : 0;   // J = I - 1 / J = I + 1
-                        const TS* tl = wait_full(q + tn);
-                        acc = row_dot<TS, TA>(tl, lane, v + (j0 + tn) * TILE);
-                        release(q + tn);
-                    }
-                } else {
-                    for (int k = w - 1; k < nt - 1; k += NW - 1) {
-                        const int t = pass == 0 ? k : k + 1;
-                        const TS* tl = wait_full(q + t);
-                        acc += row_dot<TS, TA>(tl, lane, v + (j0 + t) * TILE);
-                        release(q + t);
-                    }
-                }
-                part[(par * NW + w) * TILE + lane] = acc;
-                named_barrier(1, NW * 32);
-                if (w == 0) {
-                    TA* vi = v + I * TILE;
-                    TA sum = 0;
-#pragma unroll
-                    for (int u = 0; u < NW; ++u) sum += part[(par * NW + u) * TILE + lane];
-                    // y = D t: t goes through shared memory so that row `lane` of D and t
-                    // are both read with 128-bit loads (row_dot)
-                    tbuf[lane] = vi[lane] - sum;
-                    __syncwarp();
-                    const TS* D = wait_full(q + nt);
-                    const TA y = row_dot<TS, TA>(D, lane, tbuf);
-                    release(q + nt);
-                    vi[lane] = y;
-                    __syncwarp();
-                }
-                q += nt + 1;
-                par ^= 1;
+        auto wait_crit = [&](int k) -> const TS* {
+            const int cs = k % CR;
+            if (!__any_sync(0xffffffffu, *abort_flag != 0)) {
+                const bool r = __all_sync(0xffffffffu, mbar_poll(smem_u32(&cfull[cs]), (uint32_t)((k / CR) & 1)));
+                if (!r && lane == 0) *abort_flag = 1;
             }
+            return cring + (int64_t)(2 * cs) * TILE2;
+        };
+        int64_t fb = 0;   // far-tile index of the step's first far tile
+        int par = 0;
+        for (int k = 0; k < nsteps; ++k) {
+            const bool fwd = k < T - t0;
+            const int I = row_of(k);
+            const int j0 = fwd ? lo_s[I] : I + 1;
+            const int nt = fwd ? I - lo_s[I] : hi_s[I] - I;
+            const int nf = nt > 1 ? nt - 1 : 0;
+            TA acc = 0;
+            const TS* cp = nullptr;
+            if (w == 0) {
+                cp = wait_crit(k);
+                if (nt > 0) acc = row_dot<TS, TA>(cp, lane, v + (fwd ? I - 1 : I + 1) * TILE);
+            } else {
+                for (int e = w - 1; e < nf; e += NW - 1) {
+                    const TS* tl = wait_far(fb + e);
+                    acc += row_dot<TS, TA>(tl, lane, v + (j0 + (fwd ? e : e + 1)) * TILE);
+                    release_far(fb + e);
+                }
+            }
+            part[(par * NW + w) * TILE + lane] = acc;
+            named_barrier(1, NW * 32);
+            if (w == 0) {
+                TA* vi = v + I * TILE;
+                TA sum = 0;
+#pragma unroll
+                for (int u = 0; u < NW; ++u) sum += part[(par * NW + u) * TILE + lane];
+                // y = D t: t goes through shared memory so that row `lane` of D and t
+                // are both read with 128-bit loads (row_dot)
+                tbuf[lane] = vi[lane] - sum;
+                __syncwarp();
+                const TA y = row_dot<TS, TA>(cp + TILE2, lane, tbuf);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&cempty[k % CR]));
+                vi[lane] = y;
+                __syncwarp();
+            }
+            fb += nf;
+            par ^= 1;
         }
     }
     __syncthreads();
     if (*abort_flag) {
         if (tid == 0) {
             atomicExch(a.err, 1);
-            // only the last use of a group slot can still be in flight (a reload waits for
-            // the release of the previous use, which follows its arrival): drain those
-            const int64_t ng = (*issued - q0 + G - 1) / G;   // groups issued
-            for (int sl = 0; sl < RG; ++sl) {
-                if (ng <= sl) continue;
-                const int64_t u = (ng - 1 - sl) / RG;
-                mbar_wait(smem_u32(&full[sl]), (uint32_t)(u & 1));
-            }
+            // only the last use of a slot can still be in flight (a reload waits for the
+            // release of the previous use, which follows its arrival): drain those
+            for (int sl = 0; sl < RG; ++sl)
+                if (issued[0] > sl) mbar_wait(smem_u32(&full[sl]), (uint32_t)(((issued[0] - 1 - sl) / RG) & 1));
+            for (int sl = 0; sl < CR; ++sl)
+                if (issued[1] > sl) mbar_wait(smem_u32(&cfull[sl]), (uint32_t)(((issued[1] - 1 - sl) / CR) & 1));
         }
         __syncthreads();
         return;
     }
     if constexpr (sizeof(TA) == 4) {
         if (a.accumulate)
-            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] += (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
+            for (int i = tid; i < n; i += NT) out[i] += (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
         else
-            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
+            for (int i = tid; i < n; i += NT) out[i] = (double)(v[i] * (sc32 ? sc32[i] : 1.0f));
     } else {
         if (a.accumulate)
-            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] += v[i] * (sc ? sc[i] : 1.0);
+            for (int i = tid; i < n; i += NT) out[i] += v[i] * (sc ? sc[i] : 1.0);
         else
-            for (int i = tid; i < n; i += (NW + 1) * 32) out[i] = v[i] * (sc ? sc[i] : 1.0);
+            for (int i = tid; i < n; i += NT) out[i] = v[i] * (sc ? sc[i] : 1.0);
     }
 }
 
@@ -892,22 +972,23 @@ constexpr int group_tiles() {
     return sizeof(TS) == 8 ? 1 : 4;
 }
 
-template <typename TS, typename TA, int G, int RG>
+template <typename TS, typename TA, int G, int RG, int CR>
 static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
-    constexpr int NW = 4;   // consumer warps (+ 1 producer warp)
+    constexpr int NW = 4;   // consumer warps (+ 2 producer warps)
     constexpr int R = RG * G;
-    size_t smem = (size_t)R * TILE2 * sizeof(TS) + (3 * RG + 2) * sizeof(uint64_t) +
+    constexpr int HDR = 3 * RG + 2 * CR + 3, HDRP = HDR + (HDR & 1);
+    size_t smem = (size_t)(R + 2 * CR) * TILE2 * sizeof(TS) + HDRP * sizeof(uint64_t) +
                   (2 * NW + 1) * TILE * sizeof(TA) + (size_t)(2 * max_tiles + 4) * sizeof(int32_t) +
                   (size_t)max_tiles * TILE * sizeof(TA) + 16;
-    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, G, RG, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_chain_solve<TS, TA, G, RG, CR, NW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
         count_launch();
         SolveArgs b = a;
         b.col_fast = ncols > 1;
         const dim3 grid = ncols > 1 ? dim3(ncols, njobs) : dim3(njobs);
-        k_chain_solve<TS, TA, G, RG, NW><<<grid, (NW + 1) * 32, smem, st>>>(b);
+        k_chain_solve<TS, TA, G, RG, CR, NW><<<grid, (NW + 2) * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
 }
@@ -915,12 +996,12 @@ static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cud
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols) {
     constexpr int G = group_tiles<TS>();
+    constexpr int CR = sizeof(TS) == 8 ? 2 : 4;   // critical pairs in flight
     switch (a.deep_ring) {
-        case 1: return launch_ring<TS, TA, 2 * G, 4>(a, njobs, max_tiles, st, ncols);   // 2x ring
-        case 2: return launch_ring<TS, TA, 2 * G, 2>(a, njobs, max_tiles, st, ncols);   // 2x copies
-        case 3: return launch_ring<TS, TA, G, 6>(a, njobs, max_tiles, st, ncols);       // 1.5x groups
-        case 4: return launch_ring<TS, TA, G, 8>(a, njobs, max_tiles, st, ncols);       // 2x groups
-        default: return launch_ring<TS, TA, G, 4>(a, njobs, max_tiles, st, ncols);
+        case 1: return launch_ring<TS, TA, G, 2, CR>(a, njobs, max_tiles, st, ncols);       // half far ring
+        case 2: return launch_ring<TS, TA, G, 4, 2 * CR>(a, njobs, max_tiles, st, ncols);   // 2x critical
+        case 3: return launch_ring<TS, TA, G, 2, 2 * CR>(a, njobs, max_tiles, st, ncols);
+        default: return launch_ring<TS, TA, G, 4, CR>(a, njobs, max_tiles, st, ncols);
     }
 }
 
