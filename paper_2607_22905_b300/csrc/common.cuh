@@ -10,17 +10,6 @@
 
 namespace am {
 
-// Programmatic dependent launch (sm_90 and later).  The per-iteration kernels are
-// launched with cudaLaunchAttributeProgrammaticStreamSerialization, so a kernel's CTAs
-// may be scheduled while its predecessor in the stream is still finishing; they wait
-// here (for the predecessor's completion and the visibility of its writes) before
-// touching any of its results, and let their own successor be scheduled at once.  For
-// a launch without the attribute both instructions do nothing.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Load a stored factor entry as the accumulation type.
 template <typename TA, typename TS>
 __device__ __forceinline__ TA ldf(const TS* p) { return (TA)(*p); }

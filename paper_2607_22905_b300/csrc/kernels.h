@@ -9,27 +9,7 @@
 
 #include "common.cuh"
 
-#include <utility>
-
 namespace am {
-
-// Launch with programmatic stream serialization (the kernel calls pdl_enter() first).
-template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                       Args&&... args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 
 // Process-wide count of kernels this library has launched (graph replays included).
 void count_launch();

@@ -435,7 +435,6 @@ __device__ __forceinline__ double warp_row_dot(const double* __restrict__ row, c
 // ---------------------------------------------------------------------------------
 __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
                             double* __restrict__ P, ColStrides cs) {
-    pdl_enter();
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     b += col * cs.l;
@@ -461,7 +460,6 @@ __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double*
 // Stage 2: c = b_sep - sum_g P_g (built in shared memory by every CTA), eta_sep = Cinv c.
 __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
                             const double* __restrict__ P, ColStrides cs) {
-    pdl_enter();
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     b += col * cs.l;
@@ -484,7 +482,6 @@ __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double*
 
 // Stage 3: eta_g -= W_g eta_{A_g}.
 __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides cs) {
-    pdl_enter();
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     eta += col * cs.l;
@@ -614,14 +611,14 @@ void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double*
     const int64_t nin = a.nin, np = a.np;
     if (nin + np > 0) {
         count_launch();
-        launch_pdl(k_nd_stage1, dim3((unsigned)((nin + np + 7) / 8), ncols), dim3(256), 0, st, a, b, eta, P, cs);
+        k_nd_stage1<<<dim3((unsigned)((nin + np + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
     }
     if (a.nsep > 0) {
         count_launch();
-        launch_pdl(k_nd_stage2, dim3((unsigned)((a.nsep + 7) / 8), ncols), dim3(256), (size_t)a.nsep * sizeof(double),
-                   st, a, b, eta, P, cs);
+        k_nd_stage2<<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, (size_t)a.nsep * sizeof(double), st>>>(
+            a, b, eta, P, cs);
         count_launch();
-        launch_pdl(k_nd_stage3, dim3((unsigned)((nin + 7) / 8), ncols), dim3(256), 0, st, a, eta, cs);
+        k_nd_stage3<<<dim3((unsigned)((nin + 7) / 8), ncols), 256, 0, st>>>(a, eta, cs);
     }
 }
 cudaError_t prepare_nd_solve(int nsep) {

@@ -408,7 +408,6 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 
 template <typename TS, typename TA, int G, int RG, int CR, int NW>
 __global__ void __launch_bounds__((NW + 2) * 32) k_chain_solve(SolveArgs a) {
-    pdl_enter();
     // Two rings.  The critical ring holds, per step (tile row), the two tiles on the
     // chain's critical path -- the off-diagonal tile next to the diagonal and the inverse
     // diagonal tile -- CR steps ahead; the main ring holds the remaining ("far")
@@ -703,7 +702,6 @@ __global__ void __launch_bounds__((NW + 2) * 32) k_chain_solve(SolveArgs a) {
 // ---------------------------------------------------------------------------------
 template <typename TS, typename TA, int G, int RG, int NW>
 __global__ void __launch_bounds__((NW + 1) * 32) k_chain_solve_cols(SolveArgs a) {
-    pdl_enter();
     static_assert(RG % 2 == 0, "the barrier block keeps 16-byte alignment for even RG");
     constexpr int R = RG * G;
     const int job = blockIdx.x;
@@ -879,7 +877,7 @@ static cudaError_t launch_cols_ring(const SolveArgs& a, int njobs, int max_tiles
     if (e != cudaSuccess) return e;
     if (njobs > 0) {
         count_launch();
-        launch_pdl(k_chain_solve_cols<TS, TA, G, RG, NW>, dim3(njobs), dim3((NW + 1) * 32), smem, st, a);
+        k_chain_solve_cols<TS, TA, G, RG, NW><<<njobs, (NW + 1) * 32, smem, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -990,7 +988,7 @@ static cudaError_t launch_ring(const SolveArgs& a, int njobs, int max_tiles, cud
         SolveArgs b = a;
         b.col_fast = ncols > 1;
         const dim3 grid = ncols > 1 ? dim3(ncols, njobs) : dim3(njobs);
-        launch_pdl(k_chain_solve<TS, TA, G, RG, CR, NW>, grid, dim3((NW + 2) * 32), smem, st, b);
+        k_chain_solve<TS, TA, G, RG, CR, NW><<<grid, (NW + 2) * 32, smem, st>>>(b);
     }
     return cudaGetLastError();
 }

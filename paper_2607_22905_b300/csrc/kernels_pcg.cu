@@ -58,7 +58,6 @@ __global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, con
 __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_t* __restrict__ rcell,
                            const double* __restrict__ rcoef, const double* __restrict__ pbar,
                            double* __restrict__ beta, const int32_t* __restrict__ omap, ColStrides cs) {
-    pdl_enter();
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     pbar += col * cs.v;
@@ -93,7 +92,6 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
                                                      const double* base, double* z,   // may alias
                                                      const double* __restrict__ r, GridSum gs,
                                                      PcgScalars* psc, ColStrides cs) {
-    pdl_enter();
     // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
     // (FP64 panels: FP64; FP32 panels: FP32), then added to pbar in FP64
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
@@ -159,7 +157,6 @@ __global__ void __launch_bounds__(VEC_BS) k_smooth_residual(int64_t n, const int
                                                              const double* __restrict__ ell_val,
                                                              const double* __restrict__ x, const double* __restrict__ r,
                                                              double* __restrict__ s, ColStrides cs) {
-    pdl_enter();
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     x += col * cs.v;
@@ -182,7 +179,6 @@ __global__ void __launch_bounds__(VEC_BS) k_smooth_residual(int64_t n, const int
 __global__ void __launch_bounds__(VEC_BS) k_pcg_rho(int64_t n, const double* __restrict__ r,
                                                      const double* __restrict__ z, PcgScalars* psc, GridSum gs,
                                                      ColStrides cs) {
-    pdl_enter();
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     __shared__ double sh[32];
@@ -246,7 +242,6 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
 // preconditioner; 0 on the first iteration and right after a residual replacement.
 __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                                                    int64_t ld, const PcgScalars* __restrict__ sc) {
-    pdl_enter();
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
@@ -265,7 +260,6 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
                                                           const double* __restrict__ ell_val,
                                                           const double* __restrict__ p, double* __restrict__ q,
                                                           int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
-    pdl_enter();
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
@@ -335,7 +329,6 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ z, int64_t ld,
                                                     PcgScalars* __restrict__ sc, GridSum gs) {
-    pdl_enter();
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
@@ -487,7 +480,7 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
                      double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st) {
     if (L > 0) {
         count_launch();
-        launch_pdl(k_restrict, dim3((L + 7) / 8, ncols), dim3(256), 0, st, L, rptr, rcell, rcoef, pbar, beta, omap, cs);
+        k_restrict<<<dim3((L + 7) / 8, ncols), 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, cs);
     }
 }
 template <typename TP>
@@ -497,20 +490,19 @@ void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_
                     const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     count_launch();
-    launch_pdl(k_prolong<TP>, dim3(nchunks, ncols), dim3(VEC_BS), (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st,
-               chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, base, z, r, gs, sc, cs);
+    k_prolong<TP><<<dim3(nchunks, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
+        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, base, z, r, gs, sc, cs);
 }
 void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
                             const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
                             cudaStream_t st) {
     count_launch();
-    launch_pdl(k_smooth_residual, dim3(vec_blocks(n), ncols), dim3(VEC_BS), 0, st, n, ell_ptr, ell_col, ell_val, x, r, s,
-               cs);
+    k_smooth_residual<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, x, r, s, cs);
 }
 void launch_pcg_rho(int64_t n, int ncols, const double* r, const double* z, PcgScalars* sc, GridSum gs,
                     ColStrides cs, cudaStream_t st) {
     count_launch();
-    launch_pdl(k_pcg_rho, dim3(vec_blocks(n), ncols), dim3(VEC_BS), 0, st, n, r, z, sc, gs, cs);
+    k_pcg_rho<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, r, z, sc, gs, cs);
 }
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
                      GridSum gs, double tol, int max_it, int flexible, cudaStream_t st) {
@@ -526,14 +518,13 @@ void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr,
 void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
                   cudaStream_t st) {
     count_launch();
-    launch_pdl(k_pcg_p, dim3(vec_blocks(n), ncols), dim3(VEC_BS), 0, st, n, z, p, ld, sc);
+    k_pcg_p<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, z, p, ld, sc);
 }
 void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
                          const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
                          cudaStream_t st) {
     count_launch();
-    launch_pdl(k_pcg_spmv_ell, dim3(vec_blocks(n), ncols), dim3(VEC_BS), 0, st, n, ell_ptr, ell_col, ell_val, p, q, ld,
-               sc, gs);
+    k_pcg_spmv_ell<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, ld, sc, gs);
 }
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st) {
     count_launch();
@@ -542,7 +533,7 @@ void launch_ell_values(int64_t nell, const int32_t* src, const double* val, doub
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
                    const double* z, PcgScalars* sc, GridSum gs, cudaStream_t st) {
     count_launch();
-    launch_pdl(k_pcg_xr, dim3(vec_blocks(n), ncols), dim3(VEC_BS), 0, st, n, x, r, p, q, z, ld, sc, gs);
+    k_pcg_xr<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, z, ld, sc, gs);
 }
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {
