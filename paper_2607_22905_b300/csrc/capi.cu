@@ -96,7 +96,6 @@ struct NumWs {
     int64_t* d_doff = nullptr;
     int64_t* d_wc_ptr = nullptr;   // coupling pattern of S_{g,A_g}: per W column, interior rows
     int32_t* d_wc_row = nullptr;
-    double* d_wc_val = nullptr;    // and its values (refreshed by every numeric setup)
     double* D = nullptr;
     // separator Schur complement as a single dense item
     int cT = 0;
@@ -465,8 +464,6 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             }
             TRY(upload(h, W.d_wc_ptr, wc_ptr));
             TRY(upload(h, W.d_wc_row, wc_row));
-            W.d_wc_val = h->alloc<double>(std::max<size_t>(wc_row.size(), 1));
-            if (!W.d_wc_val) return fail(ALGMORTAR_OOM, "interface coupling values");
         }
         TRY(upload(h, h->d_ndpos, P.nd_pos));
         {
@@ -496,9 +493,6 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         a.Wcm = Wcm;
         a.Wrm = Wrm;
         a.woff = d_woff;
-        a.wc_ptr = W.d_wc_ptr;
-        a.wc_row = W.d_wc_row;
-        a.wc_val = W.d_wc_val;
         // ---- separator Schur complement C as one dense item ----
         if (nsep > 0) {
             const int T = (nsep + TILE - 1) / TILE;
@@ -665,7 +659,7 @@ int numeric_setup(algmortar_t* h) {
         CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
         launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
         launch_nd_w_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g, W.d_wc_ptr,
-                           W.d_wc_row, h->nd.gioff, h->nd.Ginv, h->nd.woff, (double*)h->nd.Wcm, W.d_wc_val, st);
+                           W.d_wc_row, h->nd.gioff, h->nd.Ginv, h->nd.woff, (double*)h->nd.Wcm, st);
         launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
         if (nsep > 0) {
             launch_nd_schur_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g,

@@ -80,11 +80,6 @@ struct NdSolveArgs {
     const double* Wrm;         // same, row-major
     const int64_t* woff;       // G offsets into W
     const double* Cinv;        // nsep x nsep symmetric inverse of the separator Schur complement
-    // sparse coupling S_{g,A_g}: per row r of P (separator unknown of group g), the
-    // interior rows wc_row[wc_ptr[r] .. wc_ptr[r+1]) of g and the values S(i, a)
-    const int64_t* wc_ptr;
-    const int32_t* wc_row;
-    const double* wc_val;
 };
 
 // interface system (kernels_coarse.cu)
@@ -105,7 +100,7 @@ void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int
 void launch_nd_w_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
                         const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
                         const int32_t* wc_row, const int64_t* gioff, const double* Ginv, const int64_t* woff,
-                        double* Wcm, double* wc_val, cudaStream_t st);
+                        double* Wcm, cudaStream_t st);
 void launch_nd_schur_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
                             const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
                             const int32_t* wc_row, const int64_t* woff, const double* Wrm, const int64_t* doff,

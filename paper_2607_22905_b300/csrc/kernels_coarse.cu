@@ -162,7 +162,7 @@ __global__ void k_nd_w_sparse(int64_t L, const double* __restrict__ Sd, const in
                               const int32_t* __restrict__ prow_g, const int64_t* __restrict__ wc_ptr,
                               const int32_t* __restrict__ wc_row, const int64_t* __restrict__ gioff,
                               const double* __restrict__ Ginv, const int64_t* __restrict__ woff,
-                              double* __restrict__ Wcm, double* __restrict__ wc_val) {
+                              double* __restrict__ Wcm) {
     constexpr int MAXNZ = 256;
     __shared__ double sv[MAXNZ];
     __shared__ int32_t si[MAXNZ];
@@ -179,7 +179,6 @@ __global__ void k_nd_w_sparse(int64_t L, const double* __restrict__ Sd, const in
             const int32_t i = wc_row[t0 + t];
             si[t] = i;
             sv[t] = Sd[(g0 + i) * L + q];
-            wc_val[t0 + t] = sv[t];   // kept for the per-iteration P = S_{A,g} y_g
         }
         __syncthreads();
         for (int64_t k = threadIdx.x; k < ng; k += blockDim.x) {
@@ -432,7 +431,7 @@ __device__ __forceinline__ double warp_row_dot(const double* __restrict__ row, c
 
 // ---------------------------------------------------------------------------------
 // Per-iteration solve (ND order in and out).
-// Stage 1: y_g = Ginv_g b_g (rows of the symmetric inverse), written to eta_g.
+// Stage 1: eta_g = Ginv_g b_g  (rows of the symmetric inverse) and P_g = W_g^T b_g.
 // ---------------------------------------------------------------------------------
 __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
                             double* __restrict__ P, ColStrides cs) {
@@ -449,23 +448,13 @@ __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double*
         const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
         const double s = warp_row_dot(a.Ginv + a.gioff[g] + i * ng, b + g0, ng, lane);
         if (lane == 0) eta[wid] = s;
+    } else if (wid < nin + a.aoff[a.G]) {
+        const int64_t r = wid - nin;
+        const int g = a.prow_g[r];
+        const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = r - a.aoff[g];
+        const double s = warp_row_dot(a.Wcm + a.woff[g] + j * ng, b + g0, ng, lane);
+        if (lane == 0) P[r] = s;
     }
-}
-
-// Stage 1b: P_g = W_g^T b_g = S_{A_g,g} S_gg^{-1} b_g = S_{A_g,g} y_g with y_g from stage
-// 1 -- a sparse product (the coupling pattern) instead of a dense n_g x |A_g| one.  One
-// thread per row of P.
-__global__ void k_nd_stage1p(NdSolveArgs a, const double* __restrict__ eta, double* __restrict__ P, ColStrides cs) {
-    const int col = blockIdx.y;
-    if (cs.done && cs.done[col * cs.done_stride]) return;
-    eta += col * cs.l;
-    P += col * a.np;
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= a.np) return;
-    const double* y = eta + a.goff[a.prow_g[r]];
-    double s = 0.0;
-    for (int64_t t = a.wc_ptr[r]; t < a.wc_ptr[r + 1]; ++t) s += a.wc_val[t] * y[a.wc_row[t]];
-    P[r] = s;
 }
 
 // Stage 2: c = b_sep - sum_g P_g (built in shared memory by every CTA), eta_sep = Cinv c.
@@ -592,11 +581,11 @@ void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int
 void launch_nd_w_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
                         const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
                         const int32_t* wc_row, const int64_t* gioff, const double* Ginv, const int64_t* woff,
-                        double* Wcm, double* wc_val, cudaStream_t st) {
+                        double* Wcm, cudaStream_t st) {
     if (np > 0) {
         count_launch();
         k_nd_w_sparse<<<(unsigned)np, 256, 0, st>>>(L, Sd, goff, aoff, alist, sep0, prow_g, wc_ptr, wc_row, gioff,
-                                                    Ginv, woff, Wcm, wc_val);
+                                                    Ginv, woff, Wcm);
     }
 }
 void launch_nd_schur_sparse(int64_t np, int64_t L, const double* Sd, const int64_t* goff, const int64_t* aoff,
@@ -620,13 +609,9 @@ void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, co
 void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
                      cudaStream_t st) {
     const int64_t nin = a.nin, np = a.np;
-    if (nin > 0) {
+    if (nin + np > 0) {
         count_launch();
-        k_nd_stage1<<<dim3((unsigned)((nin + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
-    }
-    if (np > 0) {
-        count_launch();
-        k_nd_stage1p<<<dim3((unsigned)((np + 255) / 256), ncols), 256, 0, st>>>(a, eta, P, cs);
+        k_nd_stage1<<<dim3((unsigned)((nin + np + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
     }
     if (a.nsep > 0) {
         count_launch();
