@@ -363,48 +363,78 @@ def multi_rhs_run(prec, args, local, nrhs=64, nsingle=4):
             "iterations_min_max": [int(min(its)), int(max(its))], "single_iterations": its1}
 
 
-def cpu_baseline(P, args, n_iter_sample=3):
-    """The FP64 CPU oracle, as it stands, on the host cores: its full setup (Algorithm 1)
-    on the workload plus a few timed PCG iterations, extrapolated to the iteration count
-    the oracle needs (equal to the FP64 GPU count)."""
+def _oracle_iterations(P, pc, n):
+    """Seconds per PCG iteration of the oracle (SpMV, Algorithm 2, vector updates)."""
     from oracle import algmortar as oa
-    from oracle import partition as op
-    t0 = time.perf_counter()
-    part = op.partition(P.A, P.part_sizes)
-    t_part = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    pc = oa.setup(P.A, part)
-    t_setup = time.perf_counter() - t0
-    # time a few PCG iterations (SpMV + apply + vector updates)
     r = P.f.copy()
     z = oa.apply(pc, r)
     p = z.copy()
     t0 = time.perf_counter()
-    for _ in range(n_iter_sample):
+    for _ in range(n):
         q = P.A @ p
         a = (r @ z) / (p @ q)
         r = r - a * q
         z = oa.apply(pc, r)
         p = z + 0.5 * p
-    t_it = (time.perf_counter() - t0) / n_iter_sample
+    return (time.perf_counter() - t0) / n
+
+
+def _oracle_step(P, part, iters, n_iter_sample):
+    """One step of the CPU oracle on the workload as a bounded sample: its full setup
+    (Algorithm 1) timed, plus n_iter_sample timed PCG iterations extrapolated to iters."""
+    from oracle import algmortar as oa
+    t0 = time.perf_counter()
+    pc = oa.setup(P.A, part)
+    t_setup = time.perf_counter() - t0
+    t_it = _oracle_iterations(P, pc, n_iter_sample)
+    return t_setup + iters * t_it, t_setup, t_it, pc
+
+
+def cpu_baseline(P, args, n_iter_sample=3):
+    """The FP64 CPU oracle, as it stands, on the host cores: its full setup (Algorithm 1)
+    on the workload plus a few timed PCG iterations, extrapolated to the iteration count
+    the oracle needs (equal to the FP64 GPU count)."""
+    from oracle import partition as op
+    t0 = time.perf_counter()
+    part = op.partition(P.A, P.part_sizes)
+    t_part = time.perf_counter() - t0
     iters = args._fp64_iters if getattr(args, "_fp64_iters", None) else 162
-    value = (t_setup + iters * t_it) * 1e3
-    return {"value": round(value, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+    value, t_setup, t_it, _ = _oracle_step(P, part, iters, n_iter_sample)
+    return {"value": round(value * 1e3, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"oracle Algorithm 1 setup on the full workload ({t_setup:.1f} s) + {n_iter_sample} timed "
                       f"PCG iterations ({t_it * 1e3:.0f} ms each) extrapolated to {iters} iterations; "
                       f"host partition ({t_part:.1f} s) excluded as on the GPU side"}
 
 
-def run_reference(args):
-    """Reference arm: the FP64 CPU oracle timed on the host (rank 0 only)."""
+def run_reference(args, n_iter_sample=3, iters=162):
+    """Reference arm: the FP64 CPU oracle timed on the host (rank 0 only).  W untimed
+    warm-up iterations after one untimed setup, then K timed steps, each a bounded sample
+    of the workload (full setup + n_iter_sample PCG iterations extrapolated to the FP64
+    iteration count)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import algmortar as oa
+    from oracle import partition as op
     P, wdesc = workload(args.config)
-    cb = cpu_baseline(P, args)
+    part = op.partition(P.A, P.part_sizes)
+    pc = oa.setup(P.A, part)
+    for _ in range(args.warmup):
+        _oracle_iterations(P, pc, 1)
+    steps = []
+    for _ in range(args.steps):
+        value, t_setup, t_it, _ = _oracle_step(P, part, iters, n_iter_sample)
+        steps.append((value, t_setup, t_it))
+    ms = 1e3 * sum(v for v, _, _ in steps) / len(steps)
+    t_setup = sum(s for _, s, _ in steps) / len(steps)
+    t_it = sum(t for _, _, t in steps) / len(steps)
+    cb = {"value": round(ms, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"per step: oracle Algorithm 1 setup on the full workload (mean {t_setup:.1f} s) + "
+                    f"{n_iter_sample} timed PCG iterations (mean {t_it * 1e3:.0f} ms each) extrapolated to "
+                    f"{iters} iterations; host partition excluded as on the GPU side"}
     out = {"metric": METRIC, "value": cb["value"], "unit": "ms", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-           "steps": 1, "warmup": 0, "ms_per_step": cb["value"], "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"], "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": wdesc, "n": P.n, "nnz": P.A.nnz, "n_parts": P.n_parts, "tol": TOL},
            "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
