@@ -134,6 +134,17 @@ def dist_init():
     return None, 0, 1
 
 
+def max_over_ranks(value, dist, device="cpu"):
+    """Replica runs (one independent copy of the workload per rank, no data-path
+    collective): the step time of the job is the slowest rank's."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     from paper_2607_22905_b300 import binding as B
@@ -192,10 +203,7 @@ def run_ours(args):
         info1 = B.Info()
         B.check(B.lib().algmortar_get_info(am._h, C.byref(info1)))
         ms = e0.elapsed_time(e1) / args.steps
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         xr = x.cpu().numpy()
         true_rel = float(np.linalg.norm(P.f - P.A @ xr) / np.linalg.norm(P.f))
         stages = am.time_stages(args.stage_reps)
