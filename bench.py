@@ -269,7 +269,7 @@ def run_ours(args):
                    "host_symbolic_setup_ms": round(host_setup_ms[best], 1)},
         "iterations": r["iterations"],
         "variants": {k: {kk: vv for kk, vv in v.items() if kk != "x_host"} for k, v in res.items()},
-        "roofline": {"bound": "hbm", "kernel": "k_chain_solve (batched local triangular solves)",
+        "roofline": {"bound": "hbm", "kernel": "k_chain_solve_pairs (batched local triangular solves, tile rows in pairs)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "algorithmic_bytes": int(local_bytes), "traffic": None,

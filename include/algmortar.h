@@ -95,12 +95,16 @@ typedef struct {
     int32_t l2_prefetch;           /* local triangular solves: factor tiles prefetched into
                                       L2 ahead of each CTA's shared-memory ring; -1
                                       (default) = 0 = off                                 */
-    int32_t deep_ring;             /* local triangular solves, ring of factor tiles per CTA:
-                                      0 (default) 4 groups of G tiles per bulk copy (FP32
-                                      16 KB, BF16 8 KB, FP64 one 8 KB tile), 1 twice the
-                                      group size (twice the shared memory, fewer CTAs per
-                                      SM), 2 twice the group size in 2 groups, 3 six
-                                      groups, 4 eight groups                              */
+    int32_t deep_ring;             /* local triangular solves, shared-memory rings per CTA
+                                      (a tuning switch; every value computes the same
+                                      solve).  FP32/BF16 factors (tile rows solved in
+                                      pairs): 0 (default) far-tile ring of 4 (BF16) or 2
+                                      (FP32) groups of 4 tiles, 2 critical slots, 6
+                                      consumer warps; 1 4 consumer warps; 2 3 critical
+                                      slots; 3 one more far-ring group.  FP64 factors: 0
+                                      (default) 4 groups of one tile, 2 critical slots;
+                                      1 2 groups; 2 4 critical slots; 3 2 groups and 4
+                                      critical slots.  Other values act as 0.              */
     int32_t smooth_steps;          /* nu >= 0 block-Jacobi smoothing steps before and after
                                       the AlgMortar correction (Sec. 5.4), composed
                                       multiplicatively; blocks = the subdomains, each
