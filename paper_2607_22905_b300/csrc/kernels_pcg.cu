@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
                                                      const double* __restrict__ pbar,
                                                      const double* base, double* z,   // may alias
                                                      const double* __restrict__ r, GridSum gs,
-                                                     PcgScalars* psc, ColStrides cs) {
+                                                     PcgScalars* psc, ColStrides cs, int nchunks) {
     // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
     // (FP64 panels: FP64; FP32 panels: FP32), then added to pbar in FP64
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
@@ -108,12 +108,18 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
     if (psc) psc += col;
     gs.part += col * gridDim.x;
     gs.ticket += col;
-    const int s = chunk_sub[blockIdx.x];
+    // CTAs loop over the row chunks: the grid is capped at the vector kernels' size (one
+    // wave), since every CTA's arrival at the grid-wide sum below (partial, fence, atomic)
+    // delays its retirement -- with one CTA per chunk (~5000 at config 3, four waves) the
+    // stage took 53 us instead of 43 us on B300
+    double acc = 0.0;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int s = chunk_sub[ch];
     const int64_t a0 = sub_off[s];
     const int ns = (int)(sub_off[s + 1] - a0);
     const int64_t i0 = if_off[s];
     const int kk = (int)(if_off[s + 1] - i0);
-    const int i = chunk_off[blockIdx.x] + threadIdx.x;
+    const int i = chunk_off[ch] + threadIdx.x;
     const bool row = i < ns;
     // the row's operands and its first KP panel entries are loaded before the CTA waits
     // for the interface values (gathered through if_list), so both latencies overlap
@@ -127,7 +133,6 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
     const double rv = (row && psc) ? r[a0 + i] : 0.0;
     for (int c = threadIdx.x; c < kk; c += blockDim.x) e[c] = (TA)eta[if_list[i0 + c]];
     __syncthreads();
-    double acc = 0.0;
     if (row) {
         TA c0 = 0, c1 = 0, c2 = 0, c3 = 0;
 #pragma unroll
@@ -141,7 +146,9 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
         double v = pb + (double)((c0 + c1) + (c2 + c3));
         if (base) v += bs;   // smoothed application: x + M^{-1} (r - A x)
         z[a0 + i] = v;
-        if (psc) acc = rv * v;
+        if (psc) acc += rv * v;
+    }
+    __syncthreads();   // e is refilled by the next chunk
     }
     if (psc && grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
         const double rn = psc->rz_next;
@@ -490,8 +497,9 @@ void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_
                     const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
     using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
     count_launch();
-    k_prolong<TP><<<dim3(nchunks, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
-        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, base, z, r, gs, sc, cs);
+    const int g = nchunks < g_max_vec_blocks ? nchunks : g_max_vec_blocks;
+    k_prolong<TP><<<dim3(g > 0 ? g : 1, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
+        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, base, z, r, gs, sc, cs, nchunks);
 }
 void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
                             const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
