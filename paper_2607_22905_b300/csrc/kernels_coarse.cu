@@ -263,10 +263,12 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
 // Four warps factor the 32x32 tile A_kk and invert the factor.  B300's FP64 rate is
 // ~1.9 FMA per clock per SM, i.e. a single warp's FP64 instruction occupies its SM
 // sub-partition for ~68 cycles, so the tile's FP64 work is spread over the four
-// sub-partitions: warp w owns columns 8w..8w+7 (row `lane` of them in registers).
-//   factor: for column kk the owner scales it by 1/sqrt(pivot) (one square root and one
-//     reciprocal per column, no other divisions) and publishes it in shared memory; after
-//     a barrier every warp applies the rank-1 update to its own columns right of kk;
+// sub-partitions: warp w owns columns w, w + 4, ... (row `lane` of them in registers).
+//   factor: at step kk every warp applies column kk to its columns right of kk; the
+//     owner of column kk + 1 updates that column first, then scales it by 1/sqrt(pivot)
+//     (one reciprocal square root, L_cc = pivot * rsqrt(pivot)) and publishes it, so the
+//     pivot's dependent FP64 chain overlaps the other warps' updates (one-column
+//     lookahead; one barrier per column);
 //   inverse: with D = diag(L) and the unit lower N = D^{-1} L, L^{-1} = N^{-1} D^{-1};
 //     the columns of N^{-1} are independent, so each warp forward-substitutes its own 8
 //     columns (rows final in order, row r broadcast by shuffle) and scales them.
@@ -274,52 +276,60 @@ __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __r
                                                   const int64_t* __restrict__ base,
                                                   const int64_t* __restrict__ row0, double* __restrict__ work,
                                                   double* __restrict__ dinv, int k, int* __restrict__ err) {
-    __shared__ double Ls[TILE][TILE + 1];   // L (column kk published at step kk)
+    __shared__ double Ls[TILE][TILE + 1];   // L (column c published at step c - 1)
     __shared__ double rd_s[TILE];           // 1 / L[c][c]
     __shared__ int bad_s;
     const int g = blockIdx.x;
     if (g >= nitems || k >= T[g]) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int cb = 8 * w;   // first owned column
     double* t = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
-    double a[8];
+    double a[8];   // a[j]: row `lane` of column w + 4 j
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = t[(cb + j) * TILE + lane];
+    for (int j = 0; j < 8; ++j) a[j] = t[(w + 4 * j) * TILE + lane];
     if (threadIdx.x == 0) bad_s = 0;
     __syncthreads();
-    for (int kk = 0; kk < TILE; ++kk) {
-        if (w == (kk >> 3)) {
-            const int j = kk & 7;
-            double piv = __shfl_sync(0xffffffffu, a[j], kk);
-            if (!(piv > 0.0) || !isfinite(piv)) {
-                if (lane == 0) bad_s = 1;
-                piv = 1.0;
-            }
-            const double d = sqrt(piv);
-            const double rdv = 1.0 / d;
-            const double lk = lane > kk ? a[j] * rdv : (lane == kk ? d : 0.0);
-            a[j] = lk;
-            Ls[lane][kk] = lk;
-            if (lane == 0) rd_s[kk] = rdv;
+    // owner warp of column c = w + 4 j: scale it by 1 / sqrt(pivot) and publish it
+    auto pivot = [&](int c, double& aj) {
+        double piv = __shfl_sync(0xffffffffu, aj, c);
+        if (!(piv > 0.0) || !isfinite(piv)) {
+            if (lane == 0) bad_s = 1;
+            piv = 1.0;
         }
-        __syncthreads();
+        const double rs = rsqrt(piv);
+        const double lk = lane > c ? aj * rs : (lane == c ? piv * rs : 0.0);
+        aj = lk;
+        Ls[lane][c] = lk;
+        if (lane == 0) rd_s[c] = rs;
+    };
+    if (w == 0) pivot(0, a[0]);
+    for (int kk = 0; kk < TILE; ++kk) {
+        __syncthreads();   // column kk published
         const double lk = Ls[lane][kk];
+        const int nx = kk + 1;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int c = cb + j;
-            if (c > kk && lane >= c) a[j] -= lk * Ls[c][kk];
+            const int c = w + 4 * j;
+            if (c == nx) {   // lookahead: column kk + 1 first, then its pivot
+                if (lane >= c) a[j] -= lk * Ls[c][kk];
+                pivot(c, a[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = w + 4 * j;
+            if (c > nx && lane >= c) a[j] -= lk * Ls[c][kk];
         }
     }
-    // every column of L is in Ls now (the last step's barrier ordered the writes)
+    // every column of L is in Ls now (published before the last step's barrier)
     double x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (cb + j == lane) ? 1.0 : 0.0;
+    for (int j = 0; j < 8; ++j) x[j] = (w + 4 * j == lane) ? 1.0 : 0.0;
     const double rdl = rd_s[lane];
     for (int r = 0; r < TILE; ++r) {
         const double nr = lane > r ? Ls[lane][r] * rdl : 0.0;   // N[lane][r]
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            if (cb + j > r) continue;                            // N^{-1} is lower triangular
+            if (w + 4 * j > r) continue;                         // N^{-1} is lower triangular
             const double yrc = __shfl_sync(0xffffffffu, x[j], r);
             x[j] -= nr * yrc;
         }
@@ -327,7 +337,7 @@ __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __r
     double* D = dinv + (row0[g] + k) * TILE2;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const int c = cb + j;
+        const int c = w + 4 * j;
         t[c * TILE + lane] = c <= lane ? Ls[lane][c] : 0.0;
         D[c * TILE + lane] = x[j] * rd_s[c];
     }
