@@ -316,10 +316,12 @@ def test_tight_tolerance_reports_true_residual():
 
 
 def test_wide_profile_many_tiles_per_row():
-    """Two subdomains of ~2300 cells: ~12 tiles per tile row, more than the shared-memory
-    ring holds (4 FP64 / 8 FP32 slots), so tiles are released out of order by different
-    warps while later ones are loaded.  FP64 apply matches the oracle; the deep ring gives
-    bit-identical results; FP32 / BF16 PCG converge."""
+    """Two subdomains of ~2300 cells (73 tile rows, ~3 off-diagonal tiles per row): each
+    chain streams ~8 times its ring's capacity, so ring slots are reused while tiles are
+    released out of order by different warps.  FP64 apply matches the oracle; the
+    alternative ring configuration gives bit-identical results (every tile row has at most
+    two far tiles, so both configurations sum the same partials in the same order);
+    FP32 / BF16 PCG converge."""
     A, f, sizes = small3d(m=2, uneven=False)
     part = op.partition(A, sizes)
     pc = oa.setup(A, part)
@@ -375,3 +377,49 @@ def test_smoothed_low_precision_and_multi_rhs(precision):
         assert rel(X[:, j].cpu().numpy(), x.cpu().numpy()) <= 1e-6
         assert stats[j]["status"] == 0
         assert np.linalg.norm(Bm[:, j] - A @ x.cpu().numpy()) <= 1e-9 * np.linalg.norm(Bm[:, j])
+
+
+def _pair_edge_cases():
+    # checkerboard colouring: no coupling inside a subdomain, so every local block is
+    # diagonal (no off-diagonal tiles at all) and each chain has 25 tile rows (odd)
+    A1, f1 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((40, 40, 1), 3.0, 1.0, 3)), bc_axis=0)
+    ii, jj = np.meshgrid(np.arange(40), np.arange(40), indexing="ij")
+    chk = ((ii + jj) % 2).ravel(order="F").astype(np.int32)
+    # parts of 1, 2, 3 and 5 tile rows (20, 45, 90, 150 cells) on a 61 x 5 strip
+    A2, f2 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((61, 5, 1), 3.0, 1.0, 4)), bc_axis=0)
+    return {"checkerboard": (A1, f1, chk, None), "tiny_parts": (A2, f2, None, [20, 45, 90, 150])}
+
+
+@pytest.mark.parametrize("name", ["checkerboard", "tiny_parts"])
+def test_pair_chain_edge_profiles(name):
+    """Edge cases of the paired tile rows (FP32/BF16): chains of 1-5 tile rows (odd counts
+    end on a single row), and diagonal local blocks (no near, far or coupling tiles).
+    FP64 apply matches the oracle; FP32/BF16 applies stay close to it and are symmetric
+    to rounding (the backward stream is the exact transpose of the forward one); PCG
+    converges for all three."""
+    A, f, labels, sizes = _pair_edge_cases()[name]
+    if labels is None:
+        part = op.partition(A, sizes)
+        m = len(sizes)
+    else:
+        part = labels
+        m = int(labels.max()) + 1
+    pc = oa.setup(A, part)
+    rng = np.random.default_rng(77)
+    r, s2 = rng.standard_normal((2, A.shape[0]))
+    z_ref = oa.apply(pc, r)
+    for prec in ("fp64", "fp32", "bf16"):
+        am = AlgMortar(A, m, parts=part, precision=prec)
+        z = am.apply(r).cpu().numpy()
+        if prec == "fp64":
+            assert rel(z, z_ref) <= 1e-10
+        else:
+            # low-precision factors perturb the preconditioner by ~cond(A_i) * unit
+            # roundoff (BF16: 2^-9), the bounds of test_pcg_low_precision_factors
+            assert rel(z, z_ref) <= (2e-3 if prec == "fp32" else 1e-1)
+            a_ = float(s2 @ z)
+            b_ = float(r @ am.apply(s2).cpu().numpy())
+            assert abs(a_ - b_) <= 1e-6 * (abs(a_) + abs(b_))
+        x, st = am.solve(f, tol=1e-9)
+        assert st["status"] == 0
+        assert np.linalg.norm(f - A @ x.cpu().numpy()) <= 1e-9 * np.linalg.norm(f)
