@@ -471,6 +471,72 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Row `lane` of two tiles times one vector, sharing the vector's shared-memory loads;
+// each result is accumulated exactly as row_dot does (bitwise the same values).
+template <typename TS, typename TA>
+__device__ __forceinline__ void row_dot2(const TS* A, const TS* B, int lane, const TA* v, TA& oa, TA& ob);
+
+template <>
+__device__ __forceinline__ void row_dot2<float, float>(const float* A, const float* B, int lane, const float* v,
+                                                       float& oa, float& ob) {
+    const float4* ra = reinterpret_cast<const float4*>(A + lane * TILE);
+    const float4* rb = reinterpret_cast<const float4*>(B + lane * TILE);
+    const float4* vv = reinterpret_cast<const float4*>(v);
+    float a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    const int sw = lane & 7;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 x = vv[j];
+        const float4 ta = ra[j ^ sw], tb = rb[j ^ sw];
+        a0 = fmaf(ta.x, x.x, a0);
+        a1 = fmaf(ta.y, x.y, a1);
+        a2 = fmaf(ta.z, x.z, a2);
+        a3 = fmaf(ta.w, x.w, a3);
+        b0 = fmaf(tb.x, x.x, b0);
+        b1 = fmaf(tb.y, x.y, b1);
+        b2 = fmaf(tb.z, x.z, b2);
+        b3 = fmaf(tb.w, x.w, b3);
+    }
+    oa = (a0 + a1) + (a2 + a3);
+    ob = (b0 + b1) + (b2 + b3);
+}
+
+template <>
+__device__ __forceinline__ void row_dot2<__nv_bfloat16, float>(const __nv_bfloat16* A, const __nv_bfloat16* B,
+                                                               int lane, const float* v, float& oa, float& ob) {
+    const uint4* ra = reinterpret_cast<const uint4*>(A + lane * TILE);
+    const uint4* rb = reinterpret_cast<const uint4*>(B + lane * TILE);
+    const float4* vv = reinterpret_cast<const float4*>(v);
+    float a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    const int sw = (lane >> 1) & 3;
+    auto f2 = [](uint32_t w) { return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w)); };
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 x0 = vv[2 * j], x1 = vv[2 * j + 1];
+        const uint4 ta = ra[j ^ sw], tb = rb[j ^ sw];
+        const float2 p0 = f2(ta.x), p1 = f2(ta.y), p2 = f2(ta.z), p3 = f2(ta.w);
+        const float2 q0 = f2(tb.x), q1 = f2(tb.y), q2 = f2(tb.z), q3 = f2(tb.w);
+        a0 = fmaf(p0.x, x0.x, a0);
+        a1 = fmaf(p0.y, x0.y, a1);
+        a2 = fmaf(p1.x, x0.z, a2);
+        a3 = fmaf(p1.y, x0.w, a3);
+        a0 = fmaf(p2.x, x1.x, a0);
+        a1 = fmaf(p2.y, x1.y, a1);
+        a2 = fmaf(p3.x, x1.z, a2);
+        a3 = fmaf(p3.y, x1.w, a3);
+        b0 = fmaf(q0.x, x0.x, b0);
+        b1 = fmaf(q0.y, x0.y, b1);
+        b2 = fmaf(q1.x, x0.z, b2);
+        b3 = fmaf(q1.y, x0.w, b3);
+        b0 = fmaf(q2.x, x1.x, b0);
+        b1 = fmaf(q2.y, x1.y, b1);
+        b2 = fmaf(q3.x, x1.z, b2);
+        b3 = fmaf(q3.y, x1.w, b3);
+    }
+    oa = (a0 + a1) + (a2 + a3);
+    ob = (b0 + b1) + (b2 + b3);
+}
+
 template <typename TS, typename TA, int G, int RG, int CR, int NW>
 __global__ void __launch_bounds__((NW + 2) * 32) k_chain_solve(SolveArgs a) {
     // Two rings.  The critical ring holds, per step (tile row), the two tiles on the
@@ -898,7 +964,7 @@ __global__ void __launch_bounds__((NW + 2) * 32, (NW == 4 && sizeof(TS) == 2) ? 
     int64_t* issued = reinterpret_cast<int64_t*>(cempty + CR + 1);   // [0] far groups, [1] steps
     volatile int64_t* slot_g = reinterpret_cast<volatile int64_t*>(cempty + CR + 3);   // [RG]
     TA* part = reinterpret_cast<TA*>(full + HDRP);            // [2][NW][2 rows][32]
-    TA* tbuf = part + 4 * NW * TILE;                          // [3][32]: warp 0 t_f, warp 1 t_f t_s
+    TA* tbuf = part + 4 * NW * TILE;                          // [3][32]: t_f (warp 0), t_s (warp 1), u
     uint4* stab = reinterpret_cast<uint4*>(tbuf + 3 * TILE + TILE);   // [nsteps] packed step counts
     int32_t* lo_s = reinterpret_cast<int32_t*>(stab + nsteps);
     int32_t* hi_s = lo_s + T;
@@ -1027,11 +1093,11 @@ __global__ void __launch_bounds__((NW + 2) * 32, (NW == 4 && sizeof(TS) == 2) ? 
             issued[0] = gi;
         }
     } else {
-        // Consumer warps.  Warp 0 owns the step's first row f, warp 1 its second row s:
-        // each applies its row's near tiles (they need the pair solved in the previous
-        // step, exchanged between the two warps at named barrier 2), then, after the
-        // step's named barrier 1, its row's partial sums and diagonal tiles
-        //   warp 0: x_f = D_f t_f,   warp 1: x_s = D_s t_s + K t_f.
+        // Consumer warps.  Warps 0 and 1 take a step's critical path: warp i applies near
+        // slot i of both rows (one vector, two tiles), so both need the pair solved in the
+        // previous step, exchanged at named barrier 2.  After the step's named barrier 1,
+        // warp 0 forms t_f and, in one pass over t_f, x_f = D_f t_f and u = K t_f; warp 1
+        // forms t_s and D_s t_s, and after named barrier 3 (u ready) x_s = D_s t_s + u.
         // Warps 2..NW-1 take the far tiles, dealt round-robin, each read by one warp and
         // released at once.
         auto wait_far = [&](int64_t f) -> const TS* {
@@ -1074,20 +1140,19 @@ __global__ void __launch_bounds__((NW + 2) * 32, (NW == 4 && sizeof(TS) == 2) ? 
             const int Jn0 = (int)(st.z & 0xffffu) - 2, Jf0 = (int)(st.z >> 16), Js0 = (int)st.w;
             TA acc_f = 0, acc_s = 0;
             const TS* cp = nullptr;
-            TA rf = 0;
             if (w < 2) {
                 cp = wait_crit(k);
-                const int nn = w == 0 ? nfn : nsn;
-                const int s0 = w == 0 ? 0 : (fwd ? 3 : 4);   // slot of the row's near tile 0
-                TA acc = 0;
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const bool ok = fwd ? i >= 2 - nn : i < nn;
-                    if (ok) acc += row_dot<TS, TA>(cp + (int64_t)(s0 + i) * TILE2, lane, v + (Jn0 + i) * TILE);
+                const int i = w;                              // near slot of this warp
+                const bool okf = fwd ? i >= 2 - nfn : i < nfn;
+                const bool oks = fwd ? i >= 2 - nsn : i < nsn;
+                const TS* tf = cp + (int64_t)i * TILE2;
+                const TS* ts = cp + (int64_t)((fwd ? 3 : 4) + i) * TILE2;
+                if (okf || oks) {
+                    const TA* xv = v + (Jn0 + i) * TILE;
+                    if (okf && oks) row_dot2<TS, TA>(tf, ts, lane, xv, acc_f, acc_s);
+                    else if (okf) acc_f = row_dot<TS, TA>(tf, lane, xv);
+                    else acc_s = row_dot<TS, TA>(ts, lane, xv);
                 }
-                if (w == 0) acc_f = acc;
-                else acc_s = acc;
-                if (w == 1) rf = v[f * TILE + lane];   // f's right-hand side, before warp 0 overwrites it
             } else {
                 const int nfar = ff + fs;
                 for (int e = w - 2; e < nfar; e += NW - 2) {
@@ -1102,34 +1167,38 @@ __global__ void __launch_bounds__((NW + 2) * 32, (NW == 4 && sizeof(TS) == 2) ? 
             pw[TILE + lane] = acc_s;
             named_barrier(1, NW * 32);
             if (w < 2) {
-                TA sf = 0;
-#pragma unroll
-                for (int u = 0; u < NW; ++u) sf += part[((par * NW + u) * 2) * TILE + lane];
+                TA* ub = tbuf + 2 * TILE;   // u = K t_f, warp 0 -> warp 1
+                TA ys = 0;
                 if (w == 0) {
+                    TA sf = 0;
+#pragma unroll
+                    for (int u = 0; u < NW; ++u) sf += part[((par * NW + u) * 2) * TILE + lane];
                     tbuf[lane] = v[f * TILE + lane] - sf;
                     __syncwarp();
-                    const TA yf = row_dot<TS, TA>(cp + 2 * TILE2, lane, tbuf);
+                    TA yf, uk = 0;
+                    if (sr >= 0 && hasC)
+                        row_dot2<TS, TA>(cp + 2 * TILE2, cp + (int64_t)(fwd ? 5 : 3) * TILE2, lane, tbuf, yf, uk);
+                    else
+                        yf = row_dot<TS, TA>(cp + 2 * TILE2, lane, tbuf);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&cempty[k % CR]));
                     v[f * TILE + lane] = yf;
+                    ub[lane] = uk;
                 } else {
                     if (sr >= 0) {
                         TA ss = 0;
 #pragma unroll
                         for (int u = 0; u < NW; ++u) ss += part[((par * NW + u) * 2 + 1) * TILE + lane];
                         TA* tb = tbuf + TILE;
-                        tb[lane] = rf - sf;
-                        tb[TILE + lane] = v[sr * TILE + lane] - ss;
+                        tb[lane] = v[sr * TILE + lane] - ss;
                         __syncwarp();
-                        TA ys = row_dot<TS, TA>(cp + 6 * TILE2, lane, tb + TILE);
-                        if (hasC) ys += row_dot<TS, TA>(cp + (int64_t)(fwd ? 5 : 3) * TILE2, lane, tb);
+                        ys = row_dot<TS, TA>(cp + 6 * TILE2, lane, tb);
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&cempty[k % CR]));
-                        v[sr * TILE + lane] = ys;
-                    } else if (lane == 0) {
-                        mbar_arrive(smem_u32(&cempty[k % CR]));
                     }
+                    if (lane == 0) mbar_arrive(smem_u32(&cempty[k % CR]));
                 }
+                named_barrier(3, 64);   // u ready
+                if (w == 1 && sr >= 0) v[sr * TILE + lane] = ys + ub[lane];
                 named_barrier(2, 64);   // the pair's solution, for both warps' next near tiles
             }
             fb += ff + fs;
