@@ -92,9 +92,10 @@ typedef struct {
     int32_t nd_depth;              /* interface solve: depth of the nested-dissection split
                                       (2^depth groups from the partition's bisection tree);
                                       -1 (default) picks ~1000-unknown interior blocks    */
-    int32_t l2_prefetch;           /* local triangular solves: factor tiles prefetched into
-                                      L2 ahead of each CTA's shared-memory ring; -1
-                                      (default) = 0 = off                                 */
+    int32_t l2_prefetch;           /* accepted and ignored: L2 prefetch windows ahead of
+                                      the tile rings were measured slower at every depth
+                                      and are not part of the current solves; -1 (default)
+                                      or any value                                        */
     int32_t deep_ring;             /* local triangular solves, shared-memory rings per CTA
                                       (a tuning switch; every value computes the same
                                       solve).  FP32/BF16 factors (tile rows solved in
