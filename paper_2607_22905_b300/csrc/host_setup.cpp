@@ -2,10 +2,14 @@
 #include "host_setup.h"
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <condition_variable>
+#include <mutex>
 #include <numeric>
+#include <thread>
 
 namespace am {
 
@@ -97,6 +101,33 @@ Graph adjacency(const HostCsr& A) {
 // Recursive BFS bisection (the rule stated in oracle/partition.py, implemented anew).
 // ------------------------------------------------------------------------------------
 namespace {
+
+// Runs f(i, t) for every i in [0, n) on up to 16 threads (t = thread index, for per-
+// thread scratch), taking indices in chunks from a shared counter.  Every i must write
+// only its own outputs, so the result does not depend on the schedule.  If threads cannot
+// be started, the calling thread runs everything.
+template <typename F>
+void parallel_for(int64_t n, int64_t chunk, F f) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 16),
+                                                             (n + chunk - 1) / std::max<int64_t>(chunk, 1)));
+    std::atomic<int64_t> next{0};
+    auto run = [&](int64_t t) {
+        for (;;) {
+            const int64_t i0 = next.fetch_add(chunk);
+            if (i0 >= n) return;
+            const int64_t i1 = std::min(n, i0 + chunk);
+            for (int64_t i = i0; i < i1; ++i) f(i, t);
+        }
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int64_t t = 1; t < T; ++t) pool.emplace_back(run, t);
+    } catch (...) {   // fewer threads: the counter hands their indices to the others
+    }
+    run(0);
+    for (auto& th : pool) th.join();
+}
 
 struct SubsetBfs {
     const Graph& G;
@@ -206,46 +237,77 @@ int partition_graph(const Graph& G, int32_t m, const int32_t* sizes_in, std::vec
     std::vector<int64_t> pre(m + 1, 0);
     for (int32_t i = 0; i < m; ++i) pre[i + 1] = pre[i] + sizes[i];
     part.assign(G.n, -1);
-    SubsetBfs sb(G);
+    // The two halves of a bisection are independent, so subsets are split by a pool of
+    // worker threads (each with its own BFS workspace).  A subset's split depends only on
+    // the subset, and leaves label disjoint nodes, so the labels do not depend on the
+    // schedule.
     struct Item {
         std::vector<int32_t> S;
         int32_t lo, hi;
     };
-    std::vector<Item> stack;
+    std::vector<Item> work;
     {
         Item it;
         it.S.resize(G.n);
         std::iota(it.S.begin(), it.S.end(), 0);
         it.lo = 0;
         it.hi = m;
-        stack.push_back(std::move(it));
+        work.push_back(std::move(it));
     }
-    std::vector<int32_t> ord;
-    while (!stack.empty()) {
-        Item it = std::move(stack.back());
-        stack.pop_back();
-        int32_t k = it.hi - it.lo;
-        if (k == 1) {
-            for (int32_t g : it.S) part[g] = it.lo;
-            continue;
+    std::mutex mu;
+    std::condition_variable cv;
+    int64_t pending = 1;   // items queued or in progress
+    auto worker = [&]() {
+        SubsetBfs sb(G);
+        std::vector<int32_t> ord;
+        for (;;) {
+            Item it;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return !work.empty() || pending == 0; });
+                if (work.empty()) return;
+                it = std::move(work.back());
+                work.pop_back();
+            }
+            const int32_t k = it.hi - it.lo;
+            if (k == 1) {
+                for (int32_t g : it.S) part[g] = it.lo;
+            } else {
+                const int32_t k1 = k / 2;
+                const int64_t n1 = pre[it.lo + k1] - pre[it.lo];
+                sb.order(it.S, ord);
+                Item a, b;
+                a.S.reserve(n1);
+                b.S.reserve(it.S.size() - n1);
+                for (size_t t = 0; t < ord.size(); ++t)
+                    (t < (size_t)n1 ? a.S : b.S).push_back(it.S[ord[t]]);
+                std::sort(a.S.begin(), a.S.end());
+                std::sort(b.S.begin(), b.S.end());
+                a.lo = it.lo;
+                a.hi = it.lo + k1;
+                b.lo = it.lo + k1;
+                b.hi = it.hi;
+                std::lock_guard<std::mutex> lk(mu);
+                work.push_back(std::move(b));
+                work.push_back(std::move(a));
+                pending += 2;
+            }
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                --pending;
+            }
+            cv.notify_all();
         }
-        int32_t k1 = k / 2;
-        int64_t n1 = pre[it.lo + k1] - pre[it.lo];
-        sb.order(it.S, ord);
-        Item a, b;
-        a.S.reserve(n1);
-        b.S.reserve(it.S.size() - n1);
-        for (size_t t = 0; t < ord.size(); ++t)
-            (t < (size_t)n1 ? a.S : b.S).push_back(it.S[ord[t]]);
-        std::sort(a.S.begin(), a.S.end());
-        std::sort(b.S.begin(), b.S.end());
-        a.lo = it.lo;
-        a.hi = it.lo + k1;
-        b.lo = it.lo + k1;
-        b.hi = it.hi;
-        stack.push_back(std::move(b));
-        stack.push_back(std::move(a));
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nthreads = (int)std::max(1u, std::min(std::min(hw == 0 ? 1u : hw, 16u), (unsigned)m));
+    std::vector<std::thread> pool;
+    try {
+        for (int i = 1; i < nthreads; ++i) pool.emplace_back(worker);
+    } catch (...) {   // no threads available: the calling thread does all the work
     }
+    worker();
+    for (auto& t : pool) t.join();
     return 0;
 }
 
@@ -401,30 +463,29 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
                 return 3;
             }
         }
-    // per subdomain RCM order -> internal ordering
+    // per subdomain RCM order -> internal ordering, subdomains in parallel (each writes
+    // its own ranges of perm / iperm and its own profile)
     P.perm.resize(n);
     P.iperm.assign(n, -1);
     P.ntiles.resize(m);
     P.trow_off.assign(m + 1, 0);
     P.tile_base.assign(m + 1, 0);
-    std::vector<int32_t> gl(n, -1);   // original -> local index of its subdomain
     std::vector<std::vector<int32_t>> t_lo(m), t_hi(m);
     std::vector<std::vector<int64_t>> t_fwd(m), t_bwd(m);
-    P.max_part = 0;
-    P.min_part = INT32_MAX;
-    for (int32_t s = 0; s < m; ++s) {
-        int64_t a = P.sub_off[s], b = P.sub_off[s + 1];
-        int32_t ns = (int32_t)(b - a);
-        P.max_part = std::max(P.max_part, ns);
-        P.min_part = std::min(P.min_part, ns);
-        for (int32_t t = 0; t < ns; ++t) gl[nodes[a + t]] = t;
+    std::vector<int64_t> tiles_of(m, 0);
+    parallel_for(m, 1, [&](int64_t si, int64_t) {
+        const int32_t s = (int32_t)si;
+        const int64_t a = P.sub_off[s], b = P.sub_off[s + 1];
+        const int32_t ns = (int32_t)(b - a);
+        const int32_t* nb = nodes.data() + a;   // ascending original indices
         std::vector<int64_t> lp(ns + 1, 0);
         std::vector<int32_t> la;
         for (int32_t t = 0; t < ns; ++t) {
-            int32_t g = nodes[a + t];
+            const int32_t g = nb[t];
             for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e) {
-                int32_t c = A.col[e];
-                if (c != g && part[c] == s && A.val[e] != 0.0) la.push_back(gl[c]);
+                const int32_t c = A.col[e];
+                if (c != g && part[c] == s && A.val[e] != 0.0)
+                    la.push_back((int32_t)(std::lower_bound(nb, nb + ns, c) - nb));
             }
             lp[t + 1] = (int64_t)la.size();
         }
@@ -432,8 +493,8 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
         std::vector<int32_t> inv(ns);
         for (int32_t t = 0; t < ns; ++t) {
             inv[ord[t]] = t;
-            P.perm[a + t] = nodes[a + ord[t]];
-            P.iperm[nodes[a + ord[t]]] = (int32_t)(a + t);
+            P.perm[a + t] = nb[ord[t]];
+            P.iperm[nb[ord[t]]] = (int32_t)(a + t);
         }
         // relabel local adjacency into the RCM order for the profile
         std::vector<int64_t> rp(ns + 1, 0);
@@ -443,12 +504,17 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             int64_t o = rp[t];
             for (int64_t e = lp[ord[t]]; e < lp[ord[t] + 1]; ++e) ra[o++] = inv[la[e]];
         }
-        int64_t tiles;
-        tile_profile(ns, rp, ra, P.ntiles[s], t_lo[s], t_hi[s], t_fwd[s], t_bwd[s], tiles);
+        tile_profile(ns, rp, ra, P.ntiles[s], t_lo[s], t_hi[s], t_fwd[s], t_bwd[s], tiles_of[s]);
+    });
+    P.max_part = 0;
+    P.min_part = INT32_MAX;
+    for (int32_t s = 0; s < m; ++s) {
+        const int32_t ns = (int32_t)(P.sub_off[s + 1] - P.sub_off[s]);
+        P.max_part = std::max(P.max_part, ns);
+        P.min_part = std::min(P.min_part, ns);
         P.trow_off[s + 1] = P.trow_off[s] + P.ntiles[s];
-        P.tile_base[s + 1] = P.tile_base[s] + tiles;
+        P.tile_base[s + 1] = P.tile_base[s] + tiles_of[s];
         P.max_tiles = std::max(P.max_tiles, P.ntiles[s]);
-        for (int32_t t = 0; t < ns; ++t) gl[nodes[a + t]] = -1;
     }
     P.total_tiles = P.tile_base[m];
     P.t_lo.reserve(P.trow_off[m]);
@@ -458,30 +524,38 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
         for (auto v : t_fwd[s]) P.t_fwd.push_back(v);
         for (auto v : t_bwd[s]) P.t_bwd.push_back(v);
     }
-    // permuted CSR
+    // permuted CSR: row lengths first, then the rows in parallel (each its own range)
     P.row_sub.resize(n);
     P.p_rowptr.assign(n + 1, 0);
     P.p_col.resize(A.nnz);
     P.p_val.resize(A.nnz);
     P.p_src.resize(A.nnz);
-    {
-        std::vector<std::pair<int32_t, int64_t>> row;
-        int64_t o = 0;
-        for (int64_t k = 0; k < n; ++k) {
-            int32_t g = P.perm[k];
-            P.row_sub[k] = part[g];
-            row.clear();
-            for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e) row.push_back({P.iperm[A.col[e]], e});
-            std::sort(row.begin(), row.end());
-            for (auto& pr : row) {
-                P.p_col[o] = pr.first;
-                P.p_val[o] = A.val[pr.second];
-                P.p_src[o] = pr.second;
-                ++o;
-            }
-            P.p_rowptr[k + 1] = (int32_t)o;
-        }
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t g = P.perm[k];
+        P.p_rowptr[k + 1] = P.p_rowptr[k] + (A.rowptr[g + 1] - A.rowptr[g]);
     }
+    parallel_for(n, 4096, [&](int64_t k, int64_t) {
+        const int32_t g = P.perm[k];
+        P.row_sub[k] = part[g];
+        // (new column, source position), sorted by column: insertion sort of a short row
+        std::pair<int32_t, int64_t> buf[64];
+        std::vector<std::pair<int32_t, int64_t>> big;
+        const int64_t len = A.rowptr[g + 1] - A.rowptr[g];
+        std::pair<int32_t, int64_t>* row = buf;
+        if (len > 64) {
+            big.resize(len);
+            row = big.data();
+        }
+        int64_t c = 0;
+        for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e) row[c++] = {P.iperm[A.col[e]], e};
+        std::sort(row, row + len);
+        int64_t o = P.p_rowptr[k];
+        for (int64_t t = 0; t < len; ++t, ++o) {
+            P.p_col[o] = row[t].first;
+            P.p_val[o] = A.val[row[t].second];
+            P.p_src[o] = row[t].second;
+        }
+    });
     // sliced ELL (32-row slices) of the permuted matrix
     {
         const int64_t ns = (n + 31) / 32;
