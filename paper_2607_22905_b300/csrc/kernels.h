@@ -36,7 +36,7 @@ struct SolveArgs {
     int done_stride;           // int32 stride between columns' stop flags
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
     int l2_ahead;              // carried from opts.l2_prefetch; not read by the current solves
-    int deep_ring;             // 1: twice the default ring depth (64 KB of tiles per CTA)
+    int deep_ring;             // ring / warp configuration of the chain solves (opts.deep_ring)
     int accumulate;            // 1: out += result instead of out = result
     // column-block jobs (launch_tile_solve_cols): up to NW columns of one item per job,
     // column c at job_in[job] + c * job_ld[job] (in and out), the first job_nc[job] valid,
