@@ -19,87 +19,6 @@ static std::string fmt(const char* f, long long a, long long b = 0, long long c 
     return buf;
 }
 
-int validate_csr(const HostCsr& A, std::string& err) {
-    if (A.n <= 0 || !A.rowptr || !A.col || !A.val) {
-        err = "CSR: null pointer or n <= 0";
-        return 1;
-    }
-    if (A.n >= INT32_MAX || A.nnz >= INT32_MAX || A.nnz < A.n) {
-        err = "CSR: n or nnz outside the int32 range, or fewer entries than rows";
-        return 1;
-    }
-    if (A.rowptr[0] != 0 || (int64_t)A.rowptr[A.n] != A.nnz) {
-        err = "CSR: rowptr[0] must be 0 and rowptr[n] must equal nnz";
-        return 1;
-    }
-    for (int64_t i = 0; i < A.n; ++i) {
-        int64_t a = A.rowptr[i], b = A.rowptr[i + 1];
-        if (b < a) {
-            err = fmt("CSR: rowptr decreases at row %lld", i);
-            return 1;
-        }
-        bool diag = false;
-        for (int64_t t = a; t < b; ++t) {
-            int32_t c = A.col[t];
-            if (c < 0 || c >= A.n || (t > a && c <= A.col[t - 1])) {
-                err = fmt("CSR: column out of range or not strictly ascending in row %lld", i);
-                return 1;
-            }
-            if (!std::isfinite(A.val[t])) {
-                err = fmt("CSR: non-finite value in row %lld", i);
-                return 1;
-            }
-            if (c == i) {
-                diag = true;
-                if (!(A.val[t] > 0.0)) {
-                    err = fmt("CSR: non-positive diagonal in row %lld", i);
-                    return 4;
-                }
-            }
-        }
-        if (!diag) {
-            err = fmt("CSR: missing diagonal in row %lld", i);
-            return 1;
-        }
-    }
-    for (int64_t i = 0; i < A.n; ++i) {
-        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t) {
-            int32_t j = A.col[t];
-            if (j == i) continue;
-            const int32_t* first = A.col + A.rowptr[j];
-            const int32_t* last = A.col + A.rowptr[j + 1];
-            const int32_t* f = std::lower_bound(first, last, (int32_t)i);
-            if (f == last || *f != i || A.val[A.rowptr[j] + (f - first)] != A.val[t]) {
-                err = fmt("CSR: a(%lld,%lld) has no equal transposed entry", i, j);
-                return 2;
-            }
-        }
-    }
-    return 0;
-}
-
-Graph adjacency(const HostCsr& A) {
-    Graph G;
-    G.n = (int32_t)A.n;
-    G.ptr.assign(A.n + 1, 0);
-    for (int64_t i = 0; i < A.n; ++i) {
-        int64_t c = 0;
-        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t)
-            if (A.col[t] != i && A.val[t] != 0.0) ++c;
-        G.ptr[i + 1] = G.ptr[i] + c;
-    }
-    G.adj.resize(G.ptr[A.n]);
-    for (int64_t i = 0; i < A.n; ++i) {
-        int64_t o = G.ptr[i];
-        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t)
-            if (A.col[t] != i && A.val[t] != 0.0) G.adj[o++] = A.col[t];
-    }
-    return G;
-}
-
-// ------------------------------------------------------------------------------------
-// Recursive BFS bisection (the rule stated in oracle/partition.py, implemented anew).
-// ------------------------------------------------------------------------------------
 namespace {
 
 // Runs f(i, t) for every i in [0, n) on up to 16 threads (t = thread index, for per-
@@ -128,6 +47,126 @@ void parallel_for(int64_t n, int64_t chunk, F f) {
     run(0);
     for (auto& th : pool) th.join();
 }
+
+}  // namespace
+
+namespace {
+
+// Row checks of validate_csr: 0, or the status code with err set.
+int check_row_structure(const HostCsr& A, int64_t i, std::string& err) {
+    const int64_t a = A.rowptr[i], b = A.rowptr[i + 1];
+    if (b < a || b > A.nnz) {
+        err = fmt("CSR: rowptr decreases or exceeds nnz at row %lld", i);
+        return 1;
+    }
+    bool diag = false;
+    for (int64_t t = a; t < b; ++t) {
+        const int32_t c = A.col[t];
+        if (c < 0 || c >= A.n || (t > a && c <= A.col[t - 1])) {
+            err = fmt("CSR: column out of range or not strictly ascending in row %lld", i);
+            return 1;
+        }
+        if (!std::isfinite(A.val[t])) {
+            err = fmt("CSR: non-finite value in row %lld", i);
+            return 1;
+        }
+        if (c == i) {
+            diag = true;
+            if (!(A.val[t] > 0.0)) {
+                err = fmt("CSR: non-positive diagonal in row %lld", i);
+                return 4;
+            }
+        }
+    }
+    if (!diag) {
+        err = fmt("CSR: missing diagonal in row %lld", i);
+        return 1;
+    }
+    return 0;
+}
+
+// Requires every row to have passed check_row_structure.
+int check_row_symmetry(const HostCsr& A, int64_t i, std::string& err) {
+    for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t) {
+        const int32_t j = A.col[t];
+        if (j == i) continue;
+        const int32_t* first = A.col + A.rowptr[j];
+        const int32_t* last = A.col + A.rowptr[j + 1];
+        const int32_t* f = std::lower_bound(first, last, (int32_t)i);
+        if (f == last || *f != i || A.val[A.rowptr[j] + (f - first)] != A.val[t]) {
+            err = fmt("CSR: a(%lld,%lld) has no equal transposed entry", i, j);
+            return 2;
+        }
+    }
+    return 0;
+}
+
+// First row (lowest index) for which check(row) fails, or -1; rows are checked in
+// parallel blocks, and the reported row is the same as a sequential scan's.
+template <typename Check>
+int64_t first_failing_row(int64_t n, Check check) {
+    constexpr int64_t B = 8192;
+    const int64_t nb = (n + B - 1) / B;
+    std::vector<int64_t> first(nb, -1);
+    parallel_for(nb, 1, [&](int64_t bi, int64_t) {
+        std::string e;
+        for (int64_t i = bi * B; i < std::min(n, bi * B + B); ++i)
+            if (check(i, e)) {
+                first[bi] = i;
+                return;
+            }
+    });
+    for (int64_t bi = 0; bi < nb; ++bi)
+        if (first[bi] >= 0) return first[bi];
+    return -1;
+}
+
+}  // namespace
+
+int validate_csr(const HostCsr& A, std::string& err) {
+    if (A.n <= 0 || !A.rowptr || !A.col || !A.val) {
+        err = "CSR: null pointer or n <= 0";
+        return 1;
+    }
+    if (A.n >= INT32_MAX || A.nnz >= INT32_MAX || A.nnz < A.n) {
+        err = "CSR: n or nnz outside the int32 range, or fewer entries than rows";
+        return 1;
+    }
+    if (A.rowptr[0] != 0 || (int64_t)A.rowptr[A.n] != A.nnz) {
+        err = "CSR: rowptr[0] must be 0 and rowptr[n] must equal nnz";
+        return 1;
+    }
+    int64_t i = first_failing_row(A.n, [&](int64_t r, std::string& e) { return check_row_structure(A, r, e); });
+    if (i >= 0) return check_row_structure(A, i, err);
+    i = first_failing_row(A.n, [&](int64_t r, std::string& e) { return check_row_symmetry(A, r, e); });
+    if (i >= 0) return check_row_symmetry(A, i, err);
+    return 0;
+}
+
+Graph adjacency(const HostCsr& A) {
+    Graph G;
+    G.n = (int32_t)A.n;
+    G.ptr.assign(A.n + 1, 0);
+    parallel_for(A.n, 16384, [&](int64_t i, int64_t) {
+        int64_t c = 0;
+        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t)
+            if (A.col[t] != i && A.val[t] != 0.0) ++c;
+        G.ptr[i + 1] = c;
+    });
+    for (int64_t i = 0; i < A.n; ++i) G.ptr[i + 1] += G.ptr[i];
+    G.adj.resize(G.ptr[A.n]);
+    parallel_for(A.n, 16384, [&](int64_t i, int64_t) {
+        int64_t o = G.ptr[i];
+        for (int64_t t = A.rowptr[i]; t < A.rowptr[i + 1]; ++t)
+            if (A.col[t] != i && A.val[t] != 0.0) G.adj[o++] = A.col[t];
+    });
+    return G;
+}
+
+// ------------------------------------------------------------------------------------
+// Recursive BFS bisection (the rule stated in oracle/partition.py, implemented anew).
+// ------------------------------------------------------------------------------------
+namespace {
 
 struct SubsetBfs {
     const Graph& G;
@@ -556,19 +595,20 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             P.p_src[o] = row[t].second;
         }
     });
-    // sliced ELL (32-row slices) of the permuted matrix
+    // sliced ELL (32-row slices) of the permuted matrix, slices in parallel
     {
         const int64_t ns = (n + 31) / 32;
         P.ell_ptr.assign(ns + 1, 0);
-        for (int64_t sl = 0; sl < ns; ++sl) {
+        parallel_for(ns, 1024, [&](int64_t sl, int64_t) {
             int32_t w = 0;
             for (int64_t k = sl * 32; k < std::min<int64_t>(n, sl * 32 + 32); ++k)
                 w = std::max(w, P.p_rowptr[k + 1] - P.p_rowptr[k]);
-            P.ell_ptr[sl + 1] = P.ell_ptr[sl] + 32 * (int64_t)w;
-        }
+            P.ell_ptr[sl + 1] = 32 * (int64_t)w;
+        });
+        for (int64_t sl = 0; sl < ns; ++sl) P.ell_ptr[sl + 1] += P.ell_ptr[sl];
         P.ell_col.assign(P.ell_ptr[ns], 0);
         P.ell_src.assign(P.ell_ptr[ns], -1);
-        for (int64_t sl = 0; sl < ns; ++sl) {
+        parallel_for(ns, 1024, [&](int64_t sl, int64_t) {
             const int64_t w = (P.ell_ptr[sl + 1] - P.ell_ptr[sl]) / 32;
             for (int r = 0; r < 32; ++r) {
                 const int64_t k = sl * 32 + r;
@@ -582,16 +622,26 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
                     }
                 }
             }
-        }
+        });
     }
     // interfaces: one per subdomain pair (i < j) with a coupling, lexicographic
+    // (rows in parallel blocks; the blocks' outputs are concatenated in row order, so
+    // every list below is the one a sequential scan of the rows produces)
+    constexpr int64_t RB = 16384;
+    const int64_t nrb = (n + RB - 1) / RB;
     std::vector<int64_t> keys;
-    for (int64_t k = 0; k < n; ++k) {
-        int32_t i = P.row_sub[k];
-        for (int32_t e = P.p_rowptr[k]; e < P.p_rowptr[k + 1]; ++e) {
-            int32_t j = P.row_sub[P.p_col[e]];
-            if (i < j && P.p_val[e] != 0.0) keys.push_back((int64_t)i * m + j);
-        }
+    {
+        std::vector<std::vector<int64_t>> kb(nrb);
+        parallel_for(nrb, 1, [&](int64_t bi, int64_t) {
+            for (int64_t k = bi * RB; k < std::min(n, bi * RB + RB); ++k) {
+                const int32_t i = P.row_sub[k];
+                for (int32_t e = P.p_rowptr[k]; e < P.p_rowptr[k + 1]; ++e) {
+                    const int32_t j = P.row_sub[P.p_col[e]];
+                    if (i < j && P.p_val[e] != 0.0) kb[bi].push_back((int64_t)i * m + j);
+                }
+            }
+        });
+        for (auto& v : kb) keys.insert(keys.end(), v.begin(), v.end());
     }
     P.n_edges = (int64_t)keys.size();
     std::sort(keys.begin(), keys.end());
@@ -615,29 +665,44 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
     };
     std::vector<RC> rc;
     std::vector<int32_t> row_pos;     // CSR positions, grouped per (row, interface)
-    std::vector<std::pair<int32_t, std::vector<int32_t>>> acc;
-    for (int64_t k = 0; k < n; ++k) {
-        int32_t i = P.row_sub[k];
-        acc.clear();
-        for (int32_t e = P.p_rowptr[k]; e < P.p_rowptr[k + 1]; ++e) {
-            int32_t l = P.p_col[e];
-            int32_t j = P.row_sub[l];
-            if (j == i || P.p_val[e] == 0.0) continue;
-            int32_t I = iface(i, j);
-            if (i < j) P.T[I] += std::fabs(P.p_val[e]);
-            bool found = false;
-            for (auto& pr : acc)
-                if (pr.first == I) {
-                    pr.second.push_back(e);
-                    found = true;
+    {
+        std::vector<std::vector<RC>> rcb(nrb);
+        std::vector<std::vector<int32_t>> posb(nrb);
+        parallel_for(nrb, 1, [&](int64_t bi, int64_t) {
+            std::vector<std::pair<int32_t, std::vector<int32_t>>> acc;
+            std::vector<RC>& R = rcb[bi];
+            std::vector<int32_t>& Q = posb[bi];
+            for (int64_t k = bi * RB; k < std::min(n, bi * RB + RB); ++k) {
+                const int32_t i = P.row_sub[k];
+                acc.clear();
+                for (int32_t e = P.p_rowptr[k]; e < P.p_rowptr[k + 1]; ++e) {
+                    const int32_t l = P.p_col[e];
+                    const int32_t j = P.row_sub[l];
+                    if (j == i || P.p_val[e] == 0.0) continue;
+                    const int32_t I = iface(i, j);
+                    bool found = false;
+                    for (auto& pr : acc)
+                        if (pr.first == I) {
+                            pr.second.push_back(e);
+                            found = true;
+                        }
+                    if (!found) acc.push_back({I, std::vector<int32_t>{e}});
                 }
-            if (!found) acc.push_back({I, std::vector<int32_t>{e}});
-        }
-        for (auto& pr : acc) {
-            double c = 0.0;
-            for (int32_t e : pr.second) c += P.p_val[e];
-            rc.push_back({pr.first, (int32_t)k, c, (int64_t)row_pos.size(), (int64_t)pr.second.size()});
-            row_pos.insert(row_pos.end(), pr.second.begin(), pr.second.end());
+                for (auto& pr : acc) {
+                    double c = 0.0;
+                    for (int32_t e : pr.second) c += P.p_val[e];
+                    R.push_back({pr.first, (int32_t)k, c, (int64_t)Q.size(), (int64_t)pr.second.size()});
+                    Q.insert(Q.end(), pr.second.begin(), pr.second.end());
+                }
+            }
+        });
+        for (int64_t bi = 0; bi < nrb; ++bi) {
+            const int64_t base = (int64_t)row_pos.size();
+            for (RC x : rcb[bi]) {
+                x.pos0 += base;
+                rc.push_back(x);
+            }
+            row_pos.insert(row_pos.end(), posb[bi].begin(), posb[bi].end());
         }
     }
     // restriction table, interface-major; rp_* lists each entry's CSR positions so that
@@ -645,6 +710,11 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
     std::sort(rc.begin(), rc.end(), [](const RC& a, const RC& b) {
         return a.I != b.I ? a.I < b.I : a.cell < b.cell;
     });
+    // T_I = sum |a_kl| over E_I, accumulated from the rows of the lower-numbered subdomain
+    // of I in ascending row and column order
+    for (const RC& x : rc)
+        if (P.row_sub[x.cell] == P.pairs[2 * x.I])
+            for (int64_t t = x.pos0; t < x.pos0 + x.npos; ++t) P.T[x.I] += std::fabs(P.p_val[row_pos[t]]);
     P.r_ptr.assign(P.n_lambda + 1, 0);
     P.r_cell.resize(rc.size());
     P.r_coef.resize(rc.size());
