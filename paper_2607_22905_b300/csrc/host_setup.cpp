@@ -171,24 +171,26 @@ namespace {
 struct SubsetBfs {
     const Graph& G;
     std::vector<int32_t> loc;     // global -> local index in the current subset, -1 if not
+    std::vector<int64_t> lptr;    // induced subgraph of the current subset, local indices,
+    std::vector<int32_t> ladj;    //   neighbours in the global (ascending) order
     std::vector<int32_t> dist, q, deg;
     explicit SubsetBfs(const Graph& g) : G(g), loc(g.n, -1) {}
 
     // BFS from local `s` over the induced subgraph; q receives the visit order, dist the
     // levels (nodes of other components keep -1).  Returns the eccentricity of s.
-    int32_t bfs(const std::vector<int32_t>& S, int32_t s) {
-        std::fill(dist.begin(), dist.begin() + S.size(), -1);
+    int32_t bfs(size_t n, int32_t s) {
+        std::fill(dist.begin(), dist.begin() + n, -1);
         q.clear();
         q.push_back(s);
         dist[s] = 0;
         size_t h = 0;
         while (h < q.size()) {
-            int32_t u = q[h++];
-            int32_t gu = S[u];
-            for (int64_t e = G.ptr[gu]; e < G.ptr[gu + 1]; ++e) {
-                int32_t v = loc[G.adj[e]];
-                if (v >= 0 && dist[v] < 0) {
-                    dist[v] = dist[u] + 1;
+            const int32_t u = q[h++];
+            const int32_t du = dist[u] + 1;
+            for (int64_t e = lptr[u]; e < lptr[u + 1]; ++e) {
+                const int32_t v = ladj[e];
+                if (dist[v] < 0) {
+                    dist[v] = du;
                     q.push_back(v);
                 }
             }
@@ -197,9 +199,9 @@ struct SubsetBfs {
     }
 
     // George-Liu pseudo-peripheral node of the component of local node 0.
-    int32_t pseudo_peripheral(const std::vector<int32_t>& S) {
+    int32_t pseudo_peripheral(size_t n) {
         int32_t v = 0;
-        int32_t ecc = bfs(S, v);
+        int32_t ecc = bfs(n, v);
         for (;;) {
             int32_t u = -1, best = INT32_MAX;
             for (int32_t x : q)
@@ -207,7 +209,7 @@ struct SubsetBfs {
                     u = x;
                     best = deg[x];
                 }
-            int32_t ecc_u = bfs(S, u);
+            int32_t ecc_u = bfs(n, u);
             if (ecc_u > ecc) {
                 v = u;
                 ecc = ecc_u;
@@ -219,30 +221,37 @@ struct SubsetBfs {
 
     // Full BFS order of the subset (local ids).
     void order(const std::vector<int32_t>& S, std::vector<int32_t>& out) {
-        size_t n = S.size();
+        const size_t n = S.size();
         if (dist.size() < n) {
             dist.resize(n);
             deg.resize(n);
         }
         for (size_t t = 0; t < n; ++t) loc[S[t]] = (int32_t)t;
+        lptr.resize(n + 1);
+        ladj.clear();
+        lptr[0] = 0;
         for (size_t t = 0; t < n; ++t) {
-            int32_t g = S[t], d = 0;
-            for (int64_t e = G.ptr[g]; e < G.ptr[g + 1]; ++e) d += loc[G.adj[e]] >= 0;
-            deg[t] = d;
+            const int32_t g = S[t];
+            for (int64_t e = G.ptr[g]; e < G.ptr[g + 1]; ++e) {
+                const int32_t v = loc[G.adj[e]];
+                if (v >= 0) ladj.push_back(v);
+            }
+            lptr[t + 1] = (int64_t)ladj.size();
+            deg[t] = (int32_t)(lptr[t + 1] - lptr[t]);
         }
+        for (size_t t = 0; t < n; ++t) loc[S[t]] = -1;
         std::vector<char> seen(n, 0);
         out.clear();
-        int32_t start = pseudo_peripheral(S);
+        int32_t start = pseudo_peripheral(n);
         size_t next = 0;
         for (;;) {
-            bfs(S, start);
+            bfs(n, start);
             for (int32_t x : q) seen[x] = 1;
             out.insert(out.end(), q.begin(), q.end());
             while (next < n && seen[next]) ++next;
             if (next == n) break;
             start = (int32_t)next;
         }
-        for (size_t t = 0; t < n; ++t) loc[S[t]] = -1;
     }
 };
 
