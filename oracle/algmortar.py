@@ -266,11 +266,12 @@ class PCGResult:
     history: list
 
 
-def pcg(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000) -> PCGResult:
+def pcg_iterations(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000):
     """Preconditioned CG (Hestenes-Stiefel), x0 = 0, stop when ||r_k||_2 <= tol ||b||_2
     (the Euclidean relative residual of Sec. 7), confirmed on the true residual
     b - A x; if the confirmation fails the iteration continues.  `precond(r)` returns
-    z = M^{-1} r.  `iterations` counts products with A.
+    z = M^{-1} r.  A generator: it yields after every product with A (so that a caller
+    can spread one solve over several timed pieces) and returns the PCGResult.
     """
     A = sp.csr_matrix(A)
     b = np.asarray(b, dtype=np.float64)
@@ -283,6 +284,7 @@ def pcg(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int =
     p = z.copy()
     rz = float(r @ z)
     hist = [1.0]
+    it = 0
     for it in range(1, max_it + 1):
         q = A @ p
         pq = float(p @ q)
@@ -302,5 +304,16 @@ def pcg(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int =
         beta = rz_new / rz
         rz = rz_new
         p = z + beta * p
+        yield it
     true = float(np.linalg.norm(b - A @ x))
     return PCGResult(x, it, true / bn, False, hist)
+
+
+def pcg(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000) -> PCGResult:
+    """PCG of `pcg_iterations` run to its stop (`iterations` counts products with A)."""
+    gen = pcg_iterations(A, b, precond, tol, max_it)
+    while True:
+        try:
+            next(gen)
+        except StopIteration as stop:
+            return stop.value

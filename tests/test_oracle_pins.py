@@ -218,6 +218,63 @@ def test_chain_closed_form():
     np.testing.assert_allclose(oa.apply(pc, r), Ainv @ r, rtol=1e-12, atol=1e-12)
 
 
+def test_interface_groups_all_edges_of_a_pair_by_hand():
+    """Sec. 5.5: one psi per pair i~j, however many edges E_ij holds.  2 x 2 cells,
+    unit transmissibilities, one unit Dirichlet face per cell (a_kk = 3), subdomains
+    {0, 2} | {1, 3}: E_01 = {(0,1), (2,3)}.  By hand from the definitions:
+      D_01 = diag(-1, -1), A_0 = A_1 = [[4, -1], [-1, 4]]             (Eq. A_i)
+      G = B Z = (-2, -2, -2, -2), T = 2, Phi_i = -A_i^{-1} G_i = (2/3, 2/3)
+      S_eta = T + G^T Phi / 4 = 2 - 16/12 = 2/3                      (Cor. cor-schur-eta)
+    and for r = e_0: pbar = (4/15, 1/15 | 0, 0), b_eta = 1/6, eta = 1/4,
+      z = pbar + Phi eta = (13/30, 5/30, 7/30, 5/30) in cells (0, 1, 2, 3),
+    which differs from A^{-1} e_0 = (7/15, 1/5, 1/5, 2/15): the coarse space is one
+    function, not one per edge.  A per-edge (or mis-grouped) Z fails every line."""
+    A = sp.csr_matrix(np.array([[3., -1, -1, 0], [-1, 3, 0, -1], [-1, 0, 3, -1], [0, -1, -1, 3]]))
+    part = np.array([0, 1, 0, 1])
+    pc = oa.setup(A, part)
+    assert pc.sk.nE == 2 and pc.sk.nLam == 1
+    np.testing.assert_allclose(pc.S, [[2.0 / 3.0]], rtol=0, atol=1e-15)
+    z = oa.apply(pc, np.array([1.0, 0, 0, 0]))
+    np.testing.assert_allclose(z, np.array([13, 5, 7, 5]) / 30.0, rtol=0, atol=1e-15)
+    assert np.abs(z - np.array([7 / 15, 1 / 5, 1 / 5, 2 / 15])).max() > 1e-2
+    pbar, b_eta, eta, _ = oa.apply_parts(pc, np.array([1.0, 0, 0, 0]))
+    np.testing.assert_allclose(pbar, [4 / 15, 1 / 15, 0, 0], rtol=0, atol=1e-15)   # (0, 2 | 1, 3)
+    np.testing.assert_allclose(b_eta, [1 / 6], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(eta, [0.25], rtol=0, atol=1e-15)
+    # the per-edge space Lambda = R^E has two unknowns here and recovers A^{-1}
+    pe = oa.setup(A, part, mortar="edge")
+    assert pe.S.shape == (2, 2)
+    np.testing.assert_allclose(oa.apply(pe, np.array([1.0, 0, 0, 0])), [7 / 15, 1 / 5, 1 / 5, 2 / 15], atol=1e-15)
+
+
+def test_multi_edge_interface_is_not_exact():
+    """2D grid split into two halves: the one interface holds many edges, N_Lambda = 1,
+    and z = cal_M^{-1} r differs from A^{-1} r (whereas the per-edge space recovers it)."""
+    A, f, _ = small_problem(shape=(8, 6, 1), m=2)
+    part = (np.arange(A.shape[0]) % 8 >= 4).astype(np.int32)   # x < 4 | x >= 4
+    pc = oa.setup(A, part)
+    assert pc.sk.nLam == 1 and pc.sk.nE == 6
+    r = np.random.default_rng(21).standard_normal(A.shape[0])
+    x = spla.spsolve(A.tocsc(), r)
+    assert np.linalg.norm(oa.apply(pc, r) - x) > 1e-3 * np.linalg.norm(x)
+    np.testing.assert_allclose(oa.apply(oa.setup(A, part, mortar="edge"), r), x, atol=1e-11 * np.abs(x).max())
+
+
+def test_apply_parts_is_algorithm_2(p2d, p3d):
+    """The staged form used by the GPU stage tests: its z equals apply()'s, and its eta
+    solves the interface system S eta = b_eta."""
+    for *_, pc in (p2d, p3d):
+        r = np.random.default_rng(22).standard_normal(pc.sk.n)
+        pbar, b_eta, eta, z = oa.apply_parts(pc, r)
+        np.testing.assert_allclose(z[pc.sk.iperm], oa.apply(pc, r), rtol=0, atol=1e-13 * np.abs(z).max())
+        assert np.linalg.norm(pc.S @ eta - b_eta) <= 1e-12 * np.linalg.norm(b_eta)
+        # pbar solves the local systems A_i pbar_i = r_i (Eq. def-pbar-local)
+        f = r[pc.sk.perm]
+        for i, Ai in enumerate(pc.A_loc):
+            a, b = pc.sk.offsets[i], pc.sk.offsets[i + 1]
+            assert np.linalg.norm(Ai @ pbar[a:b] - f[a:b]) <= 1e-12 * np.linalg.norm(f[a:b])
+
+
 def test_symmetry(p3d):
     """Cor. cor-schur-p: cal_M symmetric -> |r1.M^-1 r2 - r2.M^-1 r1| <= 1e-12 relative."""
     *_, pc = p3d
