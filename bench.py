@@ -50,6 +50,7 @@ def _source_rev(rel):
 # revision of the local-solve kernel source: DRAM traffic taken by ncu on another revision
 # is not reported
 KERNEL_REVISION = _source_rev("paper_2607_22905_b300/csrc/kernels_local.cu")
+LOCAL_KERNEL = "k_chain_solve_pairs (batched local triangular solves, tile rows in pairs)"
 
 
 def load_peaks():
@@ -59,6 +60,23 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+FLOOR = os.path.join(ROOT, "tests", "golden", "factor_floor.json")
+
+
+def factor_floor(config, part):
+    """sum_i nnz(L_i) of Algorithm 1's local factors under a fill-reducing order (stored
+    by tests/golden/make_factor_floor.py from the oracle's symbolic count) for this
+    workload, if the stored partition is the one the handle uses."""
+    import hashlib
+    try:
+        with open(FLOOR) as fh:
+            d = json.load(fh).get(config)
+    except Exception:
+        return None
+    sha = hashlib.sha1(np.ascontiguousarray(part, dtype=np.int32).tobytes()).hexdigest()
+    return d if d and d.get("partition_sha1") == sha else None
 
 
 def workload(name):
@@ -241,14 +259,21 @@ def run_ours(args):
     barrier()
     e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
 
-    # roofline of the dominant kernel: the batched local triangular solves
+    # roofline of the dominant kernel: the batched local triangular solves.  Algorithmic
+    # bytes = 2 s sum_i nnz(L_i) (both sweeps read every factor entry once, s bytes per
+    # entry, nnz under a fill-reducing order) + 16 N (right-hand side in, solution out);
+    # the bytes of the stored factor streams are reported beside them.
     r = res[best]
     isz = {"fp64": 8, "fp32": 4, "bf16": 2}[best]
-    local_bytes = r["factor_bytes"] + 24 * n             # both sweep streams + rhs, out, FP32 scale x2
+    fl = factor_floor(args.config, handles[best].partition())
     local_ms = r["stages_ms"]["local_solve"]
-    achieved = local_bytes / (local_ms * 1e-3) / 1e9
-    spmv_bytes = 12 * nnz + 4 * (n + 1) + 8 * n * 3       # values+cols, rowptr, p gather+p.q read, q write
-    spmv_ms = r["stages_ms"]["spmv"]
+    stored_bytes = r["factor_bytes"] + 24 * n
+    alg_bytes = 2 * isz * fl["sum_nnz_L"] + 16 * n if fl else None
+    achieved = (alg_bytes if fl else stored_bytes) / (local_ms * 1e-3) / 1e9
+    spmv_bytes = 12 * nnz + 4 * (n + 1) + 16 * n          # values+cols, rowptr, p read, q write
+    vec_bytes = 72 * n                                     # p = z + beta p; x, r updates
+    stage_gbs = {"spmv": round(spmv_bytes / (r["stages_ms"]["spmv"] * 1e-3) / 1e9, 1),
+                 "cg_vectors": round(vec_bytes / (r["stages_ms"]["cg_vectors"] * 1e-3) / 1e9, 1)}
     out = {
         "metric": METRIC,
         "value": round(r["ms"], 3),
@@ -269,11 +294,19 @@ def run_ours(args):
                    "host_symbolic_setup_ms": round(host_setup_ms[best], 1)},
         "iterations": r["iterations"],
         "variants": {k: {kk: vv for kk, vv in v.items() if kk != "x_host"} for k, v in res.items()},
-        "roofline": {"bound": "hbm", "kernel": "k_chain_solve_pairs (batched local triangular solves, tile rows in pairs)",
+        "roofline": {"bound": "hbm", "kernel": LOCAL_KERNEL,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "algorithmic_bytes": int(local_bytes), "traffic": None,
-                     "spmv_achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1)},
+                     "traffic": None,
+                     "algorithmic_bytes": int(alg_bytes) if fl else None,
+                     "floor": ("2 s sum_i nnz(L_i) + 16 N; nnz(L_i) = %d (oracle symbolic count, multiple "
+                               "minimum degree), s = %d" % (fl["sum_nnz_L"], isz)) if fl else
+                              "no stored floor for this partition: stored factor bytes used",
+                     "stored_bytes": int(stored_bytes),
+                     "stored_gbs": round(stored_bytes / (local_ms * 1e-3) / 1e9, 1),
+                     "launch_ms": round(local_ms, 5),
+                     "stages_gbs": stage_gbs,
+                     "stages_frac": {k: round(v / peak, 4) for k, v in stage_gbs.items()}},
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(8 * nnz + 8 * n),
                 "d2h_bytes_per_step": int(8 * n)},
         "gpu_launches": int(r["launches_per_step"] * args.steps),
@@ -289,8 +322,9 @@ def run_ours(args):
     if args.extras and rank == 0:
         out["smoothing"] = smoothing_runs(P, best, vals, b, args, local)
         out["multi_rhs"] = multi_rhs_run(best, args, local)
+        out["configs"] = config_runs(args, local)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(P, args)
+        out["cpu_baseline"] = cpu_baseline(P, res.get("fp64", r)["iterations"])
     if rank == 0:
         print(json.dumps(out))
     for am in handles.values():
@@ -371,79 +405,182 @@ def multi_rhs_run(prec, args, local, nrhs=64, nsingle=4):
             "iterations_min_max": [int(min(its)), int(max(its))], "single_iterations": its1}
 
 
-def _oracle_iterations(P, pc, n):
-    """Seconds per PCG iteration of the oracle (SpMV, Algorithm 2, vector updates)."""
+def config_runs(args, local, steps=2):
+    """The other workloads, each timed as a step of the headline (numeric setup + PCG to
+    1e-8 on device-resident inputs, mean of `steps` after one warm-up): C1 (also the
+    device time of one PCG iteration), C2 and C4 (first right-hand side) in every factor
+    precision, and C5's batch of 8 permeability samples (loss and adjoint gradient
+    dL/d ln K of each)."""
+    import torch
+    import synth
+    from paper_2607_22905_b300.solver import AlgMortar
+    dev = torch.device("cuda", local)
+    outs = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, r
+
+    for name, maker, rhs in (("c1", synth.config1, None), ("c2", synth.config2, None),
+                             ("c4", synth.config4, "rhs0")):
+        P = maker()
+        b = torch.as_tensor(P.meta["rhs"][:, 0] if rhs else P.f, dtype=torch.float64, device=dev)
+        vals = torch.as_tensor(P.A.data, dtype=torch.float64, device=dev)
+        rows = {}
+        for prec in ("fp64", "fp32", "bf16"):
+            am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
+                           check_every=args.check_every, device=local)
+
+            def step():
+                am.update_values(vals)
+                return am.solve(b, tol=TOL)[1]
+
+            ms, st = timed(step)
+            row = {"ms": round(ms, 3), "iterations": st["iterations"], "rel_residual": st["rel_residual"]}
+            if name == "c1":
+                row["us_per_iteration"] = round(1e3 * am.time_stages(args.stage_reps)["iteration"], 2)
+            rows[prec] = row
+            am.close()
+        outs[name] = {"workload": P.name, "n": int(P.n), "n_parts": int(P.n_parts), **rows}
+
+    from paper_2607_22905_b300.adjoint import AlgMortarTPFASolve
+    n = 96
+    shape = (n, n, n)
+    lnKs = [synth.gaussian_field(shape, 6.0, 2.0, s) for s in range(50, 58)]
+    A0, f0, _ = synth.tpfa_from_lnK(synth.gaussian_field(shape, 6.0, 2.0, 5999))
+    am = AlgMortar(A0, A0.shape[0] // 1728, precision="bf16", use_graph=True, check_every=args.check_every,
+                   device=local)
+    p_ref, _ = am.solve(f0, tol=TOL)
+    obs, p_obs = synth.observations(A0.shape[0], 200, 5001, p_ref.cpu().numpy())
+    o = torch.as_tensor(obs, device=dev)
+    po = torch.as_tensor(p_obs, device=dev)
+
+    def assemble(t):
+        Ah, fh, fc = synth.tpfa_from_lnK(t.cpu().numpy().reshape(shape, order="F"))
+        tb, tbp = synth.tpfa_cell_bc(Ah.shape[0], fc)
+        return torch.as_tensor(Ah.data, device=dev), fh, tb, tbp
+
+    flats = [torch.tensor(l.ravel(order="F"), device=dev) for l in lnKs]
+
+    def batch():
+        for fl in flats:
+            x = fl.clone().requires_grad_(True)
+            p = AlgMortarTPFASolve.apply(x, am, assemble, TOL)
+            ((p[o] - po) ** 2).sum().backward()
+
+    ms, _ = timed(batch)
+    am.close()
+    outs["c5"] = {"workload": "C5 96^3 TPFA, ln K ~ N(0, 2^2), 8 samples: forward solve + adjoint solve + "
+                              "dL/d ln K each (host assembly of A(ln K) included), bf16 factors",
+                  "n": int(A0.shape[0]), "ms_per_batch_of_8": round(ms, 3)}
+    return outs
+
+
+def cpu_baseline(P, iters, n_iter_sample=8):
+    """The FP64 CPU oracle, as it stands, on the host cores, on a bounded sample of the
+    workload: its Algorithm 1 setup on the full workload, then the first n_iter_sample
+    iterations of its own PCG (oracle.algmortar.pcg_iterations) timed; the time to
+    solution is the setup plus iters times the mean iteration (iters = the FP64 GPU
+    count, which the parity tests hold within one of the oracle's)."""
     from oracle import algmortar as oa
-    r = P.f.copy()
-    z = oa.apply(pc, r)
-    p = z.copy()
-    t0 = time.perf_counter()
-    for _ in range(n):
-        q = P.A @ p
-        a = (r @ z) / (p @ q)
-        r = r - a * q
-        z = oa.apply(pc, r)
-        p = z + 0.5 * p
-    return (time.perf_counter() - t0) / n
-
-
-def _oracle_step(P, part, iters, n_iter_sample):
-    """One step of the CPU oracle on the workload as a bounded sample: its full setup
-    (Algorithm 1) timed, plus n_iter_sample timed PCG iterations extrapolated to iters."""
-    from oracle import algmortar as oa
-    t0 = time.perf_counter()
-    pc = oa.setup(P.A, part)
-    t_setup = time.perf_counter() - t0
-    t_it = _oracle_iterations(P, pc, n_iter_sample)
-    return t_setup + iters * t_it, t_setup, t_it, pc
-
-
-def cpu_baseline(P, args, n_iter_sample=3):
-    """The FP64 CPU oracle, as it stands, on the host cores: its full setup (Algorithm 1)
-    on the workload plus a few timed PCG iterations, extrapolated to the iteration count
-    the oracle needs (equal to the FP64 GPU count)."""
     from oracle import partition as op
     t0 = time.perf_counter()
     part = op.partition(P.A, P.part_sizes)
     t_part = time.perf_counter() - t0
-    iters = args._fp64_iters if getattr(args, "_fp64_iters", None) else 162
-    value, t_setup, t_it, _ = _oracle_step(P, part, iters, n_iter_sample)
+    t0 = time.perf_counter()
+    pc = oa.setup(P.A, part)
+    t_setup = time.perf_counter() - t0
+    gen = oa.pcg_iterations(P.A, P.f, lambda v: oa.apply(pc, v), TOL)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(n_iter_sample):
+        try:
+            next(gen)
+            done += 1
+        except StopIteration:
+            break
+    t_it = (time.perf_counter() - t0) / max(done, 1)
+    value = t_setup + iters * t_it
     return {"value": round(value * 1e3, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle Algorithm 1 setup on the full workload ({t_setup:.1f} s) + {n_iter_sample} timed "
-                      f"PCG iterations ({t_it * 1e3:.0f} ms each) extrapolated to {iters} iterations; "
-                      f"host partition ({t_part:.1f} s) excluded as on the GPU side"}
+            "sample": f"oracle Algorithm 1 setup on the full workload ({t_setup:.1f} s) + the first {done} "
+                      f"iterations of the oracle's PCG ({t_it * 1e3:.0f} ms each, initial preconditioner "
+                      f"application included) scaled to {iters} iterations (the FP64 GPU count); host "
+                      f"partition ({t_part:.1f} s) excluded as on the GPU side"}
 
 
-def run_reference(args, n_iter_sample=3, iters=162):
-    """Reference arm: the FP64 CPU oracle timed on the host (rank 0 only).  W untimed
-    warm-up iterations after one untimed setup, then K timed steps, each a bounded sample
-    of the workload (full setup + n_iter_sample PCG iterations extrapolated to the FP64
-    iteration count)."""
+def run_reference(args, est_iters=200):
+    """Reference arm: the FP64 CPU oracle as it stands, on the host cores (rank 0 only),
+    ONE whole time to solution measured: the host partition untimed (as on the GPU
+    side); the first warm-up step times Algorithm 1 (oracle.algmortar.setup); the K
+    timed steps then run the oracle's own PCG (oracle.algmortar.pcg_iterations) ceil(200
+    / K) iterations each until it stops (steps left after the stop run iterations of a
+    second solve, not counted).  value = setup + the time of the first solve's
+    iterations; ms_per_step = the mean timed step.  If the K steps end before the solve
+    stops, it is run to the end after them and still counted."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import math
     from oracle import algmortar as oa
     from oracle import partition as op
     P, wdesc = workload(args.config)
     part = op.partition(P.A, P.part_sizes)
+    t0 = time.perf_counter()
     pc = oa.setup(P.A, part)
-    for _ in range(args.warmup):
-        _oracle_iterations(P, pc, 1)
-    steps = []
+    t_setup = time.perf_counter() - t0
+    precond = lambda v: oa.apply(pc, v)
+    for _ in range(max(0, args.warmup - 1)):
+        precond(P.f)
+    per_step = max(1, math.ceil(est_iters / max(args.steps, 1)))
+    gen = oa.pcg_iterations(P.A, P.f, precond, TOL)
+    result, t_solve, extra = None, 0.0, None
+    step_s = []
     for _ in range(args.steps):
-        value, t_setup, t_it, _ = _oracle_step(P, part, iters, n_iter_sample)
-        steps.append((value, t_setup, t_it))
-    ms = 1e3 * sum(v for v, _, _ in steps) / len(steps)
-    t_setup = sum(s for _, s, _ in steps) / len(steps)
-    t_it = sum(t for _, _, t in steps) / len(steps)
-    cb = {"value": round(ms, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-          "sample": f"per step: oracle Algorithm 1 setup on the full workload (mean {t_setup:.1f} s) + "
-                    f"{n_iter_sample} timed PCG iterations (mean {t_it * 1e3:.0f} ms each) extrapolated to "
-                    f"{iters} iterations; host partition excluded as on the GPU side"}
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            if result is None:
+                ta = time.perf_counter()
+                try:
+                    next(gen)
+                except StopIteration as stop:
+                    result = stop.value
+                t_solve += time.perf_counter() - ta
+                if result is not None:
+                    break
+            else:                               # keep the step's work: a second solve
+                if extra is None:
+                    extra = oa.pcg_iterations(P.A, P.f, precond, TOL)
+                try:
+                    next(extra)
+                except StopIteration:
+                    extra = None
+        step_s.append(time.perf_counter() - t0)
+    while result is None:                       # K steps were not enough: finish it
+        ta = time.perf_counter()
+        try:
+            next(gen)
+        except StopIteration as stop:
+            result = stop.value
+        t_solve += time.perf_counter() - ta
+    value = 1e3 * (t_setup + t_solve)
+    ms_step = 1e3 * sum(step_s) / max(len(step_s), 1)
+    cb = {"value": round(value, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"one whole oracle time to solution: Algorithm 1 setup ({t_setup * 1e3:.0f} ms) + its PCG to "
+                    f"{TOL:g} ({result.iterations} iterations, {t_solve * 1e3:.0f} ms, true rel. residual "
+                    f"{result.rel_residual:.2e}), spread over the timed steps ({per_step} iterations a step); "
+                    f"host partition excluded as on the GPU side"}
     out = {"metric": METRIC, "value": cb["value"], "unit": "ms", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"], "higher_is_better": False,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 1), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": wdesc, "n": P.n, "nnz": P.A.nnz, "n_parts": P.n_parts, "tol": TOL},
+           "iterations": result.iterations,
            "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

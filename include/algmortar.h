@@ -47,7 +47,9 @@ enum {
     ALGMORTAR_BREAKDOWN = 6,       /* p^T A p <= 0 or a non-finite CG scalar             */
     ALGMORTAR_CUDA = 7,            /* a CUDA runtime call failed                        */
     ALGMORTAR_OOM = 8,             /* device or host allocation failed                  */
-    ALGMORTAR_TOO_LARGE = 9        /* a subdomain above ALGMORTAR_MAX_PART rows          */
+    ALGMORTAR_TOO_LARGE = 9        /* a subdomain above ALGMORTAR_MAX_PART rows, or an
+                                      interface system larger than the static scratch of
+                                      algmortar_interface_solve_noalloc                 */
 };
 
 /* Largest subdomain the batched local kernels accept (rows). */
@@ -248,7 +250,9 @@ int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* t
  * it first); calls whose device work overlaps -- other streams, other threads, other
  * handles on the same GPU -- race on it and must be serialised by the caller.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * no allocation); make that first call before any stream capture on that device. */
+ * no allocation); make that first call before any stream capture on that device.
+ * The call makes the handle's device current for its launches and restores the
+ * caller's current device before it returns. */
 int algmortar_interface_solve_noalloc(const algmortar_t* h, const double* b_dev, double* eta_dev);
 
 /* Labels of the handle's partition (host, n entries). */

@@ -213,7 +213,6 @@ namespace {
 // would round Phi apart from the A_i^{-1} that the interface matrix was built with, and
 // that mismatch makes M^{-1} visibly non-symmetric (~1e-4 relative); FP32 keeps it at
 // rounding level for 32 MB more per iteration at config 3.
-inline int l2_ahead(const algmortar_t* h) { return h->opts.l2_prefetch < 0 ? 0 : h->opts.l2_prefetch; }
 
 template <typename TS>
 using PanelT = typename std::conditional<std::is_same<TS, double>::value, double, float>::type;
@@ -756,7 +755,6 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
-    a.l2_ahead = l2_ahead(h);
     a.deep_ring = h->opts.deep_ring;
     a.err = h->d_kerr;
     if (v.k > 1) {

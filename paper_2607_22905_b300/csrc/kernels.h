@@ -35,7 +35,6 @@ struct SolveArgs {
     int64_t ldin, ldout;       // column strides of in / out (gridDim.y = columns)
     int done_stride;           // int32 stride between columns' stop flags
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
-    int l2_ahead;              // carried from opts.l2_prefetch; not read by the current solves
     int deep_ring;             // ring / warp configuration of the chain solves (opts.deep_ring)
     int accumulate;            // 1: out += result instead of out = result
     // column-block jobs (launch_tile_solve_cols): up to NW columns of one item per job,

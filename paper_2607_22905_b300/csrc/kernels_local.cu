@@ -341,12 +341,6 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
-// Asynchronous prefetch of a global range into L2 (no completion tracking): the chain
-// solves run it ahead of their shared-memory ring, so the ring's bulk copies are served
-// from L2 and the ring depth no longer caps a CTA's bytes in flight at HBM latency.
-__device__ __forceinline__ void l2_prefetch(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(

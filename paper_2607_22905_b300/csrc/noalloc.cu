@@ -55,7 +55,17 @@ int interface_solve_noalloc(int device, cudaStream_t st, int L, const NdSolveArg
               std::to_string(kNoAllocScratchDoubles) + " (n_lambda too large for the allocation-free path)";
         return ALGMORTAR_TOO_LARGE;
     }
-    cudaError_t e = cudaSetDevice(device);
+    // the handle's device is made current for the launches and the caller's current
+    // device is restored before returning (on every path)
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != device) e = cudaSetDevice(device);
+    struct Restore {
+        int prev, dev;
+        ~Restore() {
+            if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+        }
+    } restore{e == cudaSuccess ? prev : -1, device};
     double* scratch = nullptr;
     if (e == cudaSuccess) e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) {
