@@ -1,6 +1,6 @@
 // Host-side symbolic setup of AlgMortar (Algorithm 1, everything before the numeric
 // factorisation): CSR validation, graph partition (Sec. 3.1), permutation, interface
-// edge sets E_ij (Eq. E), tile-profile layout of the local factors, and the index
+// edge sets E_ij (Eq. E), supernodal layout of the local factors, and the index
 // tables the device kernels read.  Pure C++; no CUDA types.
 #pragma once
 
@@ -33,6 +33,22 @@ Graph adjacency(const HostCsr& A);
 int partition_graph(const Graph& G, int32_t m, const int32_t* sizes, std::vector<int32_t>& part,
                     std::string& err);
 
+// Supernodal layout of one subdomain's factor (snode_plan.cpp): nested-dissection order,
+// supernodes J = local rows [c0[J], c0[J] + w[J]) in postorder, row structures R[J]
+// (local rows below the block, ascending), the supernodal elimination tree, levels
+// (height above the leaves) and the numeric updates J <- K (rows [a, b) of R[K] in J).
+struct SnUpd {
+    int32_t K, a, b;
+};
+struct SnLocal {
+    std::vector<int32_t> order;        // local position -> old local id
+    std::vector<int32_t> c0, w, parent, lev;
+    std::vector<std::vector<int32_t>> R;
+    std::vector<std::vector<SnUpd>> upd;
+    int32_t nlev = 0;
+};
+void sn_local_plan(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj, SnLocal& out);
+
 // Everything the device needs, built from A and a partition.
 struct Plan {
     int64_t n = 0;
@@ -51,16 +67,27 @@ struct Plan {
     std::vector<int64_t> ell_ptr;       // nslices + 1 element offsets
     std::vector<int32_t> ell_col;       // column (internal), padding -> the row itself
     std::vector<int32_t> ell_src;       // index into the ORIGINAL CSR values, or -1
-    // tile profile of each local factor
-    std::vector<int32_t> ntiles;        // per subdomain
-    std::vector<int64_t> trow_off;      // m + 1: tile-row descriptors of subdomain i start here
-    std::vector<int32_t> t_lo;          // per tile row (fwd): first tile column
-    std::vector<int64_t> t_fwd;         // per tile row: tile offset of (I, lo) in the fwd stream
-    std::vector<int32_t> t_hi;          // per tile row (bwd, indexed by I): last tile row below
-    std::vector<int64_t> t_bwd;         // per tile row I: tile offset of its bwd step
-    std::vector<int64_t> tile_base;     // m + 1: first tile of subdomain i (both streams)
-    int64_t total_tiles = 0;
-    int32_t max_tiles = 0;
+    // supernodal local factors (global supernode index J over all subdomains)
+    std::vector<int32_t> sn_off;        // m + 1: supernodes of subdomain s
+    std::vector<int32_t> sn_c0, sn_w, sn_nr;   // first local row, width, |R_J|
+    std::vector<int64_t> sn_roff;       // R_J at sn_rows[sn_roff[J] ..)
+    std::vector<uint16_t> sn_rows;      // local rows of the R_J
+    std::vector<int32_t> sn_uoff;       // J's pushed update: U[sn_uoff[J] .. + |R_J|) of its subdomain
+    std::vector<int64_t> sn_poff;       // panel L_{R_J,J}: |R_J| w entries at sn_poff[J]
+    std::vector<int64_t> sn_doff;       // inverse diagonal block: w (w + 1) / 2 entries at sn_doff[J]
+    std::vector<int64_t> sn_foff;       // factorisation front (w + |R_J|) x w at sn_foff[J]
+    std::vector<int64_t> sn_upd_ptr;    // updates J <- K: [sn_upd_ptr[J], sn_upd_ptr[J+1])
+    std::vector<int32_t> sn_upd;        // 3 per update: K (global), a, b
+    int64_t panel_entries = 0, diag_entries = 0, front_entries = 0;
+    std::vector<int32_t> sub_usum;      // per subdomain: sum_J |R_J| (pushed updates)
+    std::vector<int32_t> sub_nlev;      // per subdomain: levels
+    std::vector<int32_t> sub_lev0;      // per subdomain: first global level
+    std::vector<int32_t> lev_du;        // global level + 1 entries: diagonal units [lev_du[l], lev_du[l+1])
+    std::vector<int32_t> lev_pu;        //   push units [lev_pu[l], lev_pu[l+1])
+    std::vector<uint32_t> du_list, pu_list;   // packed (J local << 10) | 32-row chunk
+    std::vector<int64_t> inv_ptr;       // n + 1: pulls of internal row k at inv_idx[inv_ptr[k] ..)
+    std::vector<uint16_t> inv_idx;      // U positions (subdomain-local)
+    int32_t max_usum = 0, max_nlev = 0;
     // interfaces (Sec. 3.1 / 5.5): one mortar unknown per pair i < j, lexicographic
     int32_t n_lambda = 0;
     int64_t n_edges = 0;
@@ -83,13 +110,6 @@ struct Plan {
     std::vector<int32_t> g_row, g_col;
     std::vector<double> g_val;
     std::vector<int32_t> g_from_r;      // G entry -> restriction entry (g_val = -4 r_coef)
-    // interface system layout: RCM order of the interface graph and its tile profile
-    std::vector<int32_t> s_perm;        // s_perm[pos] = interface id
-    std::vector<int32_t> s_iperm;       // interface id -> pos
-    int32_t s_ntiles = 0;
-    std::vector<int32_t> s_lo, s_hi;
-    std::vector<int64_t> s_fwd, s_bwd;
-    int64_t s_tiles = 0;
     int32_t max_part = 0, min_part = 0, max_k = 0;
     // one-level nested dissection of the interface system: interfaces whose two
     // subdomains lie in the same group g (a subtree of the partition's bisection tree)
@@ -112,14 +132,5 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
 // Nested-dissection layout of the interface system (fills the nd_* fields of P).
 // depth < 0 chooses it from the interface count (interior blocks of ~1000 unknowns).
 void plan_interface_nd(Plan& P, int depth);
-
-// Tile-profile descriptors for a symmetric pattern given as local adjacency lists.
-void tile_profile(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
-                  int32_t& ntiles, std::vector<int32_t>& lo, std::vector<int32_t>& hi,
-                  std::vector<int64_t>& fwd, std::vector<int64_t>& bwd, int64_t& tiles);
-
-// Reverse Cuthill-McKee order (local ids) of a graph given by local adjacency lists.
-std::vector<int32_t> rcm_order(int32_t n, const std::vector<int64_t>& ptr,
-                               const std::vector<int32_t>& adj);
 
 }  // namespace am
