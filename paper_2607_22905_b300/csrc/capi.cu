@@ -115,14 +115,19 @@ struct algmortar_handle {
     int64_t* d_sub_off = nullptr;
     int nchunks = 0;                   // prolongation: row chunks (<= VEC_BS rows of one subdomain)
     int32_t *d_chunk_sub = nullptr, *d_chunk_off = nullptr;
-    // supernodal local factors: tables and the four solve streams (panels column- and
-    // row-major, inverse diagonal blocks column- and row-major packed)
+    // supernodal local factors: tables, the per-warp record streams of the solves (their
+    // headers and index lists uploaded at setup, entries filled from each numeric
+    // factorisation) and the fill descriptors
     SnTables sn{};
     int32_t* d_rows = nullptr;
-    void *d_Pf = nullptr, *d_Pb = nullptr, *d_Df = nullptr, *d_Db = nullptr;
+    uint8_t* d_stream = nullptr;
+    int64_t* d_woff = nullptr;
+    int32_t* d_nbar = nullptr;
+    SnFill* d_fill = nullptr;
+    int64_t n_fill = 0, stream_bytes = 0;
     // block-Jacobi smoother (Sec. 5.4): factors of the unmodified blocks A_ii on the same
-    // supernodal layout, and their symmetric scaling
-    void *d_Pf2 = nullptr, *d_Pb2 = nullptr, *d_Df2 = nullptr, *d_Db2 = nullptr;
+    // supernodal layout (a second copy of the streams), and their symmetric scaling
+    uint8_t* d_stream2 = nullptr;
     double *d_dloc2 = nullptr, *d_sc2 = nullptr;
     float* d_sc2_32 = nullptr;
     double *d_dloc = nullptr, *d_sc = nullptr;
@@ -219,19 +224,24 @@ int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
 int upload_sn_tables(algmortar_t* h) {
     const Plan& P = h->P;
     SnTables& t = h->sn;
+    const int32_t nsn = P.sn_off[P.m];
+    std::vector<SnMeta> meta(nsn);
+    for (int32_t J = 0; J < nsn; ++J)
+        meta[J] = SnMeta{P.sn_c0[J], P.sn_w[J], P.sn_nr[J], 0, P.sn_poff[J], P.sn_doff[J], P.sn_roff[J], 0};
     int64_t* sub_off = nullptr;
-    int32_t *sn_off = nullptr, *c0 = nullptr, *w = nullptr, *nr = nullptr, *uoff = nullptr, *upd = nullptr;
+    int32_t *sn_off = nullptr, *c0 = nullptr, *w = nullptr, *nr = nullptr, *upd = nullptr;
     int64_t *roff = nullptr, *poff = nullptr, *doff = nullptr, *foff = nullptr, *updp = nullptr;
-    uint16_t *rows = nullptr, *inv_idx = nullptr;
-    int32_t *nlev = nullptr, *lev0 = nullptr, *lev_du = nullptr, *lev_pu = nullptr, *inv_ptr = nullptr;
-    uint32_t *du = nullptr, *pu = nullptr;
-    std::vector<int32_t> inv32(P.inv_ptr.begin(), P.inv_ptr.end());
+    uint16_t* rows = nullptr;
+    int32_t *nlev = nullptr, *lev0 = nullptr, *lev_du = nullptr, *fwd_ptr = nullptr;
+    uint8_t* lev_multi = nullptr;
+    uint32_t *du = nullptr, *fwd_desc = nullptr;
+    SnMeta* d_meta = nullptr;
     TRY(upload(h, sub_off, P.sub_off));
     TRY(upload(h, sn_off, P.sn_off));
+    TRY(upload(h, d_meta, meta));
     TRY(upload(h, c0, P.sn_c0));
     TRY(upload(h, w, P.sn_w));
     TRY(upload(h, nr, P.sn_nr));
-    TRY(upload(h, uoff, P.sn_uoff));
     TRY(upload(h, roff, P.sn_roff));
     TRY(upload(h, poff, P.sn_poff));
     TRY(upload(h, doff, P.sn_doff));
@@ -242,13 +252,29 @@ int upload_sn_tables(algmortar_t* h) {
     TRY(upload(h, nlev, P.sub_nlev));
     TRY(upload(h, lev0, P.sub_lev0));
     TRY(upload(h, lev_du, P.lev_du));
-    TRY(upload(h, lev_pu, P.lev_pu));
+    TRY(upload(h, lev_multi, P.lev_multi));
     TRY(upload(h, du, P.du_list));
-    TRY(upload(h, pu, P.pu_list));
-    TRY(upload(h, inv_ptr, inv32));
-    TRY(upload(h, inv_idx, P.inv_idx));
-    t = SnTables{sub_off, sn_off, c0, w, nr, uoff, roff, poff, doff, foff, updp, rows, upd,
-                 nlev, lev0, lev_du, lev_pu, du, pu, inv_ptr, inv_idx};
+    TRY(upload(h, fwd_ptr, P.fwd_ptr));
+    TRY(upload(h, fwd_desc, P.fwd_desc));
+    t = SnTables{sub_off, sn_off, d_meta, c0, w, nr, roff, poff, doff, foff, updp, rows, upd,
+                 nlev, lev0, lev_du, lev_multi, du, fwd_ptr, reinterpret_cast<const uint2*>(fwd_desc)};
+    return 0;
+}
+
+// Record streams of the batched local solves for the handle's precision (elem bytes per
+// factor entry): headers and index lists from the host, entries written by each
+// numeric factorisation.
+int upload_sn_stream(algmortar_t* h, int elem) {
+    SnStream S;
+    std::string err;
+    if (build_sn_stream(h->P, sn_solve_warps(), elem, S, err)) return fail(ALGMORTAR_INVALID_ARG, err);
+    if (S.max_record > sn_max_record()) return fail(ALGMORTAR_INVALID_ARG, "local solve stream: record too large");
+    h->stream_bytes = (int64_t)S.bytes.size();
+    h->n_fill = (int64_t)S.fill.size();
+    TRY(upload(h, h->d_stream, S.bytes));
+    TRY(upload(h, h->d_woff, S.woff));
+    TRY(upload(h, h->d_nbar, S.nbar));
+    TRY(upload(h, h->d_fill, S.fill));
     return 0;
 }
 
@@ -256,10 +282,10 @@ int upload_sn_tables(algmortar_t* h) {
 SnSolveArgs local_args(const algmortar_t* h, bool smoother) {
     SnSolveArgs a{};
     a.t = h->sn;
-    a.Pf = smoother ? h->d_Pf2 : h->d_Pf;
-    a.Pb = smoother ? h->d_Pb2 : h->d_Pb;
-    a.Df = smoother ? h->d_Df2 : h->d_Df;
-    a.Db = smoother ? h->d_Db2 : h->d_Db;
+    a.stream = smoother ? h->d_stream2 : h->d_stream;
+    a.woff = h->d_woff;
+    a.nbar = h->d_nbar;
+    a.err = h->d_kerr;
     a.scale = smoother ? h->d_sc2 : h->d_sc;
     a.scale32 = smoother ? h->d_sc2_32 : h->d_sc32;
     return a;
@@ -305,20 +331,13 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     W.d_err = h->alloc<int>(2);
     W.rhs = h->alloc<double>(nphi);
     W.phi64 = h->alloc<double>(nphi);
-    h->d_Pf = h->alloc<TS>((size_t)P.panel_entries);
-    h->d_Pb = h->alloc<TS>((size_t)P.panel_entries);
-    h->d_Df = h->alloc<TS>((size_t)P.diag_entries);
-    h->d_Db = h->alloc<TS>((size_t)P.diag_entries);
     if (h->opts.smooth_steps > 0) {
-        h->d_Pf2 = h->alloc<TS>((size_t)P.panel_entries);
-        h->d_Pb2 = h->alloc<TS>((size_t)P.panel_entries);
-        h->d_Df2 = h->alloc<TS>((size_t)P.diag_entries);
-        h->d_Db2 = h->alloc<TS>((size_t)P.diag_entries);
-        if (!h->d_Pf2 || !h->d_Pb2 || !h->d_Df2 || !h->d_Db2) return fail(ALGMORTAR_OOM, "smoother factor buffers");
+        h->d_stream2 = h->alloc<uint8_t>((size_t)h->stream_bytes);
+        if (!h->d_stream2) return fail(ALGMORTAR_OOM, "smoother factor streams");
+        CU(cudaMemcpyAsync(h->d_stream2, h->d_stream, (size_t)h->stream_bytes, cudaMemcpyDeviceToDevice, h->st));
     }
     h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<PanelT<TS>>(nphi);
-    if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_Pf || !h->d_Pb || !h->d_Df || !h->d_Db ||
-        !h->d_phi)
+    if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
     if (L > 0) {
         TRY(upload(h, W.d_T, P.T));
@@ -559,15 +578,13 @@ int numeric_setup(algmortar_t* h) {
                         W.d_T ? W.d_T : h->d_scalar, (int64_t)P.g_val.size(), h->d_g_from_r, W.d_gval, st);
     // --- local factors (Algorithm 1: extract A_ii, modify its diagonal, factor) ---
     int err_init[2] = {0, -1};
-    const int nsn = P.sn_off[m];
     CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
     launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, 1, h->d_dloc,
                       h->d_sc, h->d_sc32, st);
     CU(launch_sn_factor<TW>(h->sn, m, P.max_part, h->d_job_sub, h->d_rowptr, h->d_col, h->d_val, h->d_dloc, h->d_sc,
                             work, dinv, W.d_err, st));
     TRY(read_err_flag(h, W.d_err, "local"));
-    CU((launch_sn_finalize<TW, TS>(h->sn, nsn, work, dinv, (TS*)h->d_Pf, (TS*)h->d_Pb, (TS*)h->d_Df, (TS*)h->d_Db,
-                                   st)));
+    CU((launch_sn_fill<TW, TS>(h->sn, h->d_fill, h->n_fill, work, dinv, h->d_stream, st)));
     if (h->opts.smooth_steps > 0) {
         // smoother blocks = the subdomains, unmodified A_ii (same sparsity, same layout)
         CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
@@ -576,8 +593,7 @@ int numeric_setup(algmortar_t* h) {
         CU(launch_sn_factor<TW>(h->sn, m, P.max_part, h->d_job_sub, h->d_rowptr, h->d_col, h->d_val, h->d_dloc2,
                                 h->d_sc2, work, dinv, W.d_err, st));
         TRY(read_err_flag(h, W.d_err, "smoother block"));
-        CU((launch_sn_finalize<TW, TS>(h->sn, nsn, work, dinv, (TS*)h->d_Pf2, (TS*)h->d_Pb2, (TS*)h->d_Df2,
-                                       (TS*)h->d_Db2, st)));
+        CU((launch_sn_fill<TW, TS>(h->sn, h->d_fill, h->n_fill, work, dinv, h->d_stream2, st)));
     }
     cudaEventRecord(ev[1], st);
     // --- MBFs (Eq. def-phat-local): Phi_i = A_i^{-1} (-B_i psi_m), one job per (i, m) ---
@@ -590,7 +606,7 @@ int numeric_setup(algmortar_t* h) {
         a.job_out = W.d_jo;
         a.in = W.rhs;
         a.out = W.phi64;
-        CU((launch_sn_solve<TS, TA>(a, W.njobs_mbf, 1, P.max_part, P.max_usum, st)));
+        CU((launch_sn_solve<TS, TA>(a, W.njobs_mbf, 1, P.max_part, st)));
     }
     if (!std::is_same<TS, double>::value) launch_convert<PanelT<TS>>(nphi, W.phi64, (PanelT<TS>*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
@@ -738,7 +754,7 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
-    CU((launch_sn_solve<TS, TA>(a, h->m, v.k, h->P.max_part, h->P.max_usum, h->st)));
+    CU((launch_sn_solve<TS, TA>(a, h->m, v.k, h->P.max_part, h->st)));
     return 0;
 }
 
@@ -1000,10 +1016,10 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     }
     if (o.nd_depth >= 0) plan_interface_nd(h->P, o.nd_depth);
     {
-        // the batched local solve keeps two row vectors and the pushed updates of one
-        // subdomain in shared memory
+        // the batched local solve keeps two vectors over one subdomain's rows in shared
+        // memory
         const size_t ta = o.precision == ALGMORTAR_FP64 ? 8 : 4;
-        const size_t need = sn_solve_smem(h->P.max_part, h->P.max_usum, ta);
+        const size_t need = sn_solve_smem(h->P.max_part, ta);
         if (need > 227 * 1024) {
             delete h;
             return fail(ALGMORTAR_TOO_LARGE, "a subdomain's local solve needs " + std::to_string(need) +
@@ -1062,6 +1078,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     }
     rc = rc ? rc : upload(h, h->d_rows, rows);
     rc = rc ? rc : upload_sn_tables(h);
+    rc = rc ? rc : upload_sn_stream(h, o.precision == ALGMORTAR_FP64 ? 8 : (o.precision == ALGMORTAR_FP32 ? 4 : 2));
     rc = rc ? rc : upload(h, h->d_job_sub, order);
     rc = rc ? rc : upload(h, h->d_job_off, joff);
     rc = rc ? rc : upload(h, h->d_rptr, P.r_ptr);

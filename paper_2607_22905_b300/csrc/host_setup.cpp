@@ -19,36 +19,6 @@ static std::string fmt(const char* f, long long a, long long b = 0, long long c 
     return buf;
 }
 
-namespace {
-
-// Runs f(i, t) for every i in [0, n) on up to 16 threads (t = thread index, for per-
-// thread scratch), taking indices in chunks from a shared counter.  Every i must write
-// only its own outputs, so the result does not depend on the schedule.  If threads cannot
-// be started, the calling thread runs everything.
-template <typename F>
-void parallel_for(int64_t n, int64_t chunk, F f) {
-    const unsigned hw = std::thread::hardware_concurrency();
-    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 16),
-                                                             (n + chunk - 1) / std::max<int64_t>(chunk, 1)));
-    std::atomic<int64_t> next{0};
-    auto run = [&](int64_t t) {
-        for (;;) {
-            const int64_t i0 = next.fetch_add(chunk);
-            if (i0 >= n) return;
-            const int64_t i1 = std::min(n, i0 + chunk);
-            for (int64_t i = i0; i < i1; ++i) f(i, t);
-        }
-    };
-    std::vector<std::thread> pool;
-    try {
-        for (int64_t t = 1; t < T; ++t) pool.emplace_back(run, t);
-    } catch (...) {   // fewer threads: the counter hands their indices to the others
-    }
-    run(0);
-    for (auto& th : pool) th.join();
-}
-
-}  // namespace
 
 namespace {
 
@@ -433,10 +403,9 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
     P.max_part = 0;
     P.min_part = INT32_MAX;
     P.sn_off.assign(m + 1, 0);
-    P.sub_usum.assign(m, 0);
     P.sub_nlev.assign(m, 0);
     P.sub_lev0.assign(m + 1, 0);
-    P.max_usum = P.max_nlev = 0;
+    P.max_nlev = 0;
     for (int32_t s = 0; s < m; ++s) {
         const int32_t ns = (int32_t)(P.sub_off[s + 1] - P.sub_off[s]);
         P.max_part = std::max(P.max_part, ns);
@@ -451,24 +420,21 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
     P.sn_w.resize(nsn);
     P.sn_nr.resize(nsn);
     P.sn_roff.assign(nsn + 1, 0);
-    P.sn_uoff.resize(nsn);
     P.sn_poff.assign(nsn + 1, 0);
     P.sn_doff.assign(nsn + 1, 0);
     P.sn_foff.assign(nsn + 1, 0);
     P.sn_upd_ptr.assign(nsn + 1, 0);
     const int32_t nglev = P.sub_lev0[m];
-    std::vector<std::vector<uint32_t>> du(nglev), pu(nglev);
+    std::vector<std::vector<uint32_t>> du(nglev);
+    P.lev_multi.assign(nglev, 0);
     for (int32_t s = 0; s < m; ++s) {
         const SnLocal& L = sl[s];
-        int32_t usum = 0;
         for (size_t j = 0; j < L.c0.size(); ++j) {
             const int32_t J = P.sn_off[s] + (int32_t)j;
             const int32_t w = L.w[j], nr = (int32_t)L.R[j].size();
             P.sn_c0[J] = L.c0[j];
             P.sn_w[J] = w;
             P.sn_nr[J] = nr;
-            P.sn_uoff[J] = usum;
-            usum += nr;
             P.sn_roff[J + 1] = P.sn_roff[J] + nr;
             P.sn_poff[J + 1] = P.sn_poff[J] + (int64_t)nr * w;
             P.sn_doff[J + 1] = P.sn_doff[J] + (int64_t)w * (w + 1) / 2;
@@ -482,41 +448,38 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             }
             const int32_t gl = P.sub_lev0[s] + L.lev[j];
             for (int32_t q = 0; q * 32 < w; ++q) du[gl].push_back(((uint32_t)j << 10) | (uint32_t)q);
-            for (int32_t q = 0; q * 32 < nr; ++q) pu[gl].push_back(((uint32_t)j << 10) | (uint32_t)q);
+            if (w > 32) P.lev_multi[gl] = 1;
         }
-        P.sub_usum[s] = usum;
-        P.max_usum = std::max(P.max_usum, usum);
     }
     P.panel_entries = P.sn_poff[nsn];
     P.diag_entries = P.sn_doff[nsn];
     P.front_entries = P.sn_foff[nsn];
     P.lev_du.assign(nglev + 1, 0);
-    P.lev_pu.assign(nglev + 1, 0);
     for (int32_t l = 0; l < nglev; ++l) {
         P.lev_du[l + 1] = P.lev_du[l] + (int32_t)du[l].size();
-        P.lev_pu[l + 1] = P.lev_pu[l] + (int32_t)pu[l].size();
         P.du_list.insert(P.du_list.end(), du[l].begin(), du[l].end());
-        P.pu_list.insert(P.pu_list.end(), pu[l].begin(), pu[l].end());
     }
-    // forward pull lists: row r of subdomain s receives U[uoff_K + i] for every K with
-    // R_K[i] = r, in increasing K (a fixed summation order)
-    P.inv_ptr.assign(n + 1, 0);
+    // forward descriptors: row r of subdomain s receives, for every K with R_K[i] = r
+    // (K ascending), L_K's panel row i (offset poff_K + i w_K) times x_K
+    if (P.panel_entries >= ((int64_t)1 << 32)) {
+        err = fmt("the local factors hold %lld panel entries (limit 2^32)", P.panel_entries);
+        return 9;
+    }
+    P.fwd_ptr.assign(n + 1, 0);
     for (int32_t s = 0; s < m; ++s)
         for (int32_t J = P.sn_off[s]; J < P.sn_off[s + 1]; ++J)
-            for (int64_t t = P.sn_roff[J]; t < P.sn_roff[J + 1]; ++t) P.inv_ptr[P.sub_off[s] + P.sn_rows[t] + 1]++;
-    for (int64_t k = 0; k < n; ++k) P.inv_ptr[k + 1] += P.inv_ptr[k];
-    P.inv_idx.assign(P.inv_ptr[n], 0);
+            for (int64_t t = P.sn_roff[J]; t < P.sn_roff[J + 1]; ++t) P.fwd_ptr[P.sub_off[s] + P.sn_rows[t] + 1]++;
+    for (int64_t k = 0; k < n; ++k) P.fwd_ptr[k + 1] += P.fwd_ptr[k];
+    P.fwd_desc.assign(2 * (size_t)P.fwd_ptr[n], 0);
     {
-        std::vector<int64_t> fill(P.inv_ptr.begin(), P.inv_ptr.end() - 1);
+        std::vector<int32_t> fill(P.fwd_ptr.begin(), P.fwd_ptr.end() - 1);
         for (int32_t s = 0; s < m; ++s)
             for (int32_t J = P.sn_off[s]; J < P.sn_off[s + 1]; ++J)
-                for (int64_t t = P.sn_roff[J]; t < P.sn_roff[J + 1]; ++t)
-                    P.inv_idx[fill[P.sub_off[s] + P.sn_rows[t]]++] =
-                        (uint16_t)(P.sn_uoff[J] + (t - P.sn_roff[J]));
-    }
-    if (P.max_usum > 65535) {
-        err = fmt("a subdomain's factor has %lld update rows (limit 65535)", P.max_usum);
-        return 9;
+                for (int64_t t = P.sn_roff[J]; t < P.sn_roff[J + 1]; ++t) {
+                    const int32_t f = fill[P.sub_off[s] + P.sn_rows[t]]++;
+                    P.fwd_desc[2 * (size_t)f] = (uint32_t)(P.sn_poff[J] + (t - P.sn_roff[J]) * P.sn_w[J]);
+                    P.fwd_desc[2 * (size_t)f + 1] = (uint32_t)P.sn_c0[J] | ((uint32_t)P.sn_w[J] << 16);
+                }
     }
     // permuted CSR: row lengths first, then the rows in parallel (each its own range)
     P.row_sub.resize(n);

@@ -4,13 +4,44 @@
 // tables the device kernels read.  Pure C++; no CUDA types.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
+#include "snode_stream.h"
 #include "tile.h"
 
 namespace am {
+
+// Runs f(i, t) for every i in [0, n) on up to 16 threads (t = thread index, for per-
+// thread scratch), taking indices in chunks from a shared counter.  Every i must write
+// only its own outputs, so the result does not depend on the schedule.  If threads cannot
+// be started, the calling thread runs everything.
+template <typename F>
+void parallel_for(int64_t n, int64_t chunk, F f) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 16),
+                                                             (n + chunk - 1) / std::max<int64_t>(chunk, 1)));
+    std::atomic<int64_t> next{0};
+    auto run = [&](int64_t t) {
+        for (;;) {
+            const int64_t i0 = next.fetch_add(chunk);
+            if (i0 >= n) return;
+            const int64_t i1 = std::min(n, i0 + chunk);
+            for (int64_t i = i0; i < i1; ++i) f(i, t);
+        }
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int64_t t = 1; t < T; ++t) pool.emplace_back(run, t);
+    } catch (...) {   // fewer threads: the counter hands their indices to the others
+    }
+    run(0);
+    for (auto& th : pool) th.join();
+}
 
 struct HostCsr {
     int64_t n = 0, nnz = 0;
@@ -72,22 +103,23 @@ struct Plan {
     std::vector<int32_t> sn_c0, sn_w, sn_nr;   // first local row, width, |R_J|
     std::vector<int64_t> sn_roff;       // R_J at sn_rows[sn_roff[J] ..)
     std::vector<uint16_t> sn_rows;      // local rows of the R_J
-    std::vector<int32_t> sn_uoff;       // J's pushed update: U[sn_uoff[J] .. + |R_J|) of its subdomain
     std::vector<int64_t> sn_poff;       // panel L_{R_J,J}: |R_J| w entries at sn_poff[J]
     std::vector<int64_t> sn_doff;       // inverse diagonal block: w (w + 1) / 2 entries at sn_doff[J]
     std::vector<int64_t> sn_foff;       // factorisation front (w + |R_J|) x w at sn_foff[J]
     std::vector<int64_t> sn_upd_ptr;    // updates J <- K: [sn_upd_ptr[J], sn_upd_ptr[J+1])
     std::vector<int32_t> sn_upd;        // 3 per update: K (global), a, b
     int64_t panel_entries = 0, diag_entries = 0, front_entries = 0;
-    std::vector<int32_t> sub_usum;      // per subdomain: sum_J |R_J| (pushed updates)
     std::vector<int32_t> sub_nlev;      // per subdomain: levels
     std::vector<int32_t> sub_lev0;      // per subdomain: first global level
-    std::vector<int32_t> lev_du;        // global level + 1 entries: diagonal units [lev_du[l], lev_du[l+1])
-    std::vector<int32_t> lev_pu;        //   push units [lev_pu[l], lev_pu[l+1])
-    std::vector<uint32_t> du_list, pu_list;   // packed (J local << 10) | 32-row chunk
-    std::vector<int64_t> inv_ptr;       // n + 1: pulls of internal row k at inv_idx[inv_ptr[k] ..)
-    std::vector<uint16_t> inv_idx;      // U positions (subdomain-local)
-    int32_t max_usum = 0, max_nlev = 0;
+    std::vector<int32_t> lev_du;        // global level + 1 entries: units [lev_du[l], lev_du[l+1])
+    std::vector<uint8_t> lev_multi;     // per global level: a supernode of the level is wider than 32
+    std::vector<uint32_t> du_list;      // units: (J local << 10) | 32-row chunk
+    // forward sweep: row k (internal) receives, for every descendant K with k in R_K, the
+    // product of K's panel row for k with x_K; fwd_desc[2 t] = offset of that panel row,
+    // fwd_desc[2 t + 1] = c0_K | w_K << 16, for t in [fwd_ptr[k], fwd_ptr[k+1]), K ascending
+    std::vector<int32_t> fwd_ptr;       // n + 1
+    std::vector<uint32_t> fwd_desc;
+    int32_t max_nlev = 0;
     // interfaces (Sec. 3.1 / 5.5): one mortar unknown per pair i < j, lexicographic
     int32_t n_lambda = 0;
     int64_t n_edges = 0;
@@ -128,6 +160,21 @@ struct Plan {
 
 int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Plan& P,
                std::string& err);
+
+// Record streams of the batched local solves (snode_stream.h) for CTAs of nw warps and
+// factor entries of elem bytes: headers and index lists (entries zero, written on the
+// device from the numeric factor by the fill descriptors).  Warp w of subdomain s reads
+// bytes [woff[s nw + w], woff[s nw + w + 1]); every warp stream of s holds nbar[s]
+// barriers.
+struct SnStream {
+    int nw = 0, elem = 0;
+    std::vector<uint8_t> bytes;
+    std::vector<int64_t> woff;
+    std::vector<int32_t> nbar;
+    std::vector<SnFill> fill;
+    int32_t max_record = 0;             // largest record (bytes)
+};
+int build_sn_stream(const Plan& P, int nw, int elem, SnStream& out, std::string& err);
 
 // Nested-dissection layout of the interface system (fills the nd_* fields of P).
 // depth < 0 chooses it from the interface count (interior blocks of ~1000 unknowns).

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "snode_stream.h"
 
 namespace am {
 
@@ -75,13 +76,18 @@ struct NdSolveArgs {
 };
 
 // Supernodal local factors (layout of snode_plan.cpp, global supernode indices).
+struct SnMeta {                // per supernode, what one solve unit reads first
+    int32_t c0, w, nr, pad;    // first local row, width, |R_J|
+    int64_t poff, doff, roff;  // panel, packed diagonal block and R_J offsets
+    int64_t pad2;
+};
 struct SnTables {
     const int64_t* sub_off;    // m + 1: rows of subdomain s
     const int32_t* sn_off;     // m + 1: supernodes of subdomain s
+    const SnMeta* meta;        // per supernode
     const int32_t* c0;         // per supernode: first local row
     const int32_t* w;          //   width
     const int32_t* nr;         //   |R_J|
-    const int32_t* uoff;       //   pushed update offset in the subdomain's U
     const int64_t* roff;       //   R_J in rows[]
     const int64_t* poff;       //   panel offset (entries)
     const int64_t* doff;       //   packed diagonal-block offset (entries)
@@ -91,20 +97,19 @@ struct SnTables {
     const int32_t* upd;        // (K, a, b) triples
     const int32_t* nlev;       // per subdomain: levels
     const int32_t* lev0;       // per subdomain: first global level
-    const int32_t* lev_du;     // per global level: diagonal units
-    const int32_t* lev_pu;     //   push units
+    const int32_t* lev_du;     // per global level: units [lev_du[l], lev_du[l+1])
+    const uint8_t* lev_multi;  // per global level: some supernode wider than 32
     const uint32_t* du;        // (J local << 10) | chunk
-    const uint32_t* pu;
-    const int32_t* inv_ptr;    // n + 1: pulls of internal row k
-    const uint16_t* inv_idx;   // U positions
+    const int32_t* fwd_ptr;    // n + 1: forward panel rows of internal row k
+    const uint2* fwd_desc;     // (panel-row offset, c0_K | w_K << 16)
 };
 
 struct SnSolveArgs {
     SnTables t;
-    const void* Pf;            // panels, column-major (forward)
-    const void* Pb;            // panels, row-major (backward)
-    const void* Df;            // inverse diagonal blocks, column-major packed (forward)
-    const void* Db;            //   row-major packed (backward)
+    const uint8_t* stream;     // record streams (snode_stream.h)
+    const int64_t* woff;       // m * NW + 1: stream of warp w of subdomain s
+    const int32_t* nbar;       // per subdomain: barriers in each of its warp streams
+    int* err;                  // set to 1 if a bulk copy never completed (bounded wait)
     const double* scale;       // symmetric scaling per internal row (FP64 solves), or null
     const float* scale32;      // the same in FP32 (FP32 / BF16 solves)
     const int32_t* job_sub;    // subdomain of each job
@@ -124,11 +129,13 @@ cudaError_t launch_sn_factor(const SnTables& t, int m, int max_part, const int32
                              const int32_t* col, const double* val, const double* dloc, const double* sc, TW* work,
                              TW* dwork, int* err, cudaStream_t st);
 template <typename TW, typename TS>
-cudaError_t launch_sn_finalize(const SnTables& t, int nsn, const TW* work, const TW* dwork, TS* Pf, TS* Pb, TS* Df,
-                               TS* Db, cudaStream_t st);
-size_t sn_solve_smem(int max_part, int max_usum, size_t ta_bytes);
+cudaError_t launch_sn_fill(const SnTables& t, const SnFill* fill, int64_t nfill, const TW* work, const TW* dwork,
+                           uint8_t* stream, cudaStream_t st);
+int sn_solve_warps();
+int sn_max_record();      // largest record the solve rings accept (bytes)
+size_t sn_solve_smem(int max_part, size_t ta_bytes);
 template <typename TS, typename TA>
-cudaError_t launch_sn_solve(const SnSolveArgs& a, int njobs, int ncols, int max_part, int max_usum, cudaStream_t st);
+cudaError_t launch_sn_solve(const SnSolveArgs& a, int njobs, int ncols, int max_part, cudaStream_t st);
 
 // interface system (kernels_coarse.cu)
 void launch_iface_tables(int L, int64_t nr, const int64_t* rp_ptr, const int32_t* rp_pos, const double* val,

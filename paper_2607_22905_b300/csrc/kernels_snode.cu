@@ -4,17 +4,17 @@
 // solves that apply A_i^{-1} for the particular solutions (Eq. def-pbar-local), the MBFs
 // (Eq. def-phat-local) and the block-Jacobi smoother (Sec. 5.4).
 //
-// Storage per supernode J (w columns, row structure R_J of nr rows):
-//   D_J = L_JJ^{-1}, packed lower triangle, twice: column-major (forward sweep: lane =
-//       row, so a column is read with consecutive lanes) and row-major (backward sweep:
-//       lane = column);
-//   P_J = L_{R_J, J}, nr x w, twice: column-major (forward: lane = row of R_J) and
-//       row-major (backward: lane = column of J).
-// Both copies of an entry are rounded from the same FP32/FP64 value, so the backward
-// sweep applies exactly the transpose of what the forward sweep applies and the local
-// solve stays symmetric after rounding.
+// The solves read the factor as per-warp record streams (snode_stream.h): every entry of
+// L_J (its panel and the inverse D_J of its diagonal block) appears once in the forward
+// records and once in the backward ones, both rounded from the same FP32/FP64 value, so
+// the backward sweep applies exactly the transpose of what the forward sweep applies and
+// the local solve stays symmetric after rounding.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "snode_stream.h"
+#include "tma.cuh"
 
 namespace am {
 
@@ -273,32 +273,50 @@ __global__ void __launch_bounds__(256) k_sn_factor(SnTables t, const int32_t* __
 }
 
 // ---------------------------------------------------------------------------------
-// Solve streams from the factor: per supernode (one CTA), the panel L_{R_J,J} in column-
-// and row-major order and D_J in column- and row-major packed order, in precision TS.
+// Entries of the solve streams from the factor (one warp per record, grid-stride): the
+// fronts in `work` (column-major (w + nr) x w per supernode) and D_J in `dwork` (row-
+// major packed), rounded to TS, at the positions snode_stream.h defines.
 // ---------------------------------------------------------------------------------
 template <typename TW, typename TS>
-__global__ void __launch_bounds__(256) k_sn_finalize(SnTables t, int nsn, const TW* __restrict__ work,
-                                                     const TW* __restrict__ dwork, TS* __restrict__ Pf,
-                                                     TS* __restrict__ Pb, TS* __restrict__ Df, TS* __restrict__ Db) {
-    for (int J = blockIdx.x; J < nsn; J += gridDim.x) {
-        const int w = t.w[J], nr = t.nr[J], h = w + nr;
+__global__ void __launch_bounds__(256) k_sn_fill(SnTables t, const SnFill* __restrict__ fill, int64_t nfill,
+                                                 const TW* __restrict__ work, const TW* __restrict__ dwork,
+                                                 uint8_t* __restrict__ stream) {
+    constexpr int V = 8 / (int)sizeof(TS);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); k < nfill; k += nwarps) {
+        const SnFill f = fill[k];
+        TS* dst = reinterpret_cast<TS*>(stream + f.off);
+        const int J = f.sn, w = t.w[J], h = w + t.nr[J], L = f.lanes;
         const TW* F = work + t.foff[J];
         const TW* D = dwork + t.doff[J];
-        const int64_t po = t.poff[J], dof = t.doff[J];
-        for (int64_t e = threadIdx.x; e < (int64_t)nr * w; e += blockDim.x) {
-            const int i = (int)(e / w), c = (int)(e % w);
-            const TS v = stf<TS>((double)F[(w + i) + (int64_t)c * h]);
-            Pb[po + (int64_t)i * w + c] = v;
-            Pf[po + (int64_t)c * nr + i] = v;
-        }
-        for (int64_t e = threadIdx.x; e < (int64_t)w * (w + 1) / 2; e += blockDim.x) {
-            int r = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-            while (rpack(r + 1, 0) <= e) ++r;
-            while (rpack(r, 0) > e) --r;
-            const int c = (int)(e - rpack(r, 0));
-            const TS v = stf<TS>((double)D[e]);
-            Db[dof + e] = v;
-            Df[dof + cpack(r, c, w)] = v;
+        if (f.kind == SN_FCONTRIB) {
+            for (int e = lane; e < f.n * f.rows; e += 32) {
+                const int c = e / f.rows, i = e - c * f.rows;
+                dst[(int64_t)(c / V) * f.rows * V + i * V + c % V] =
+                    stf<TS>((double)F[(w + f.p0 + i) + (int64_t)(f.p1 + c) * h]);
+            }
+        } else if (f.kind == SN_FDIAG) {
+            const int rel0 = f.p1 - f.p0;
+            for (int j = 0; j < f.n; ++j) {
+                const int c = f.p1 + j, gi = j / V, st = max(0, rel0 + gi * V);
+                const int64_t o = sn_fdiag_off(gi, rel0, L, V) + j % V;
+                for (int l = max(st, c - f.p0) + lane; l < L; l += 32)
+                    dst[o + (int64_t)(l - st) * V] = stf<TS>((double)D[rpack(f.p0 + l, c)]);
+            }
+        } else if (f.kind == SN_BPANEL) {
+            for (int e = lane; e < f.rows * L; e += 32) {
+                const int i = e / L, c = e - i * L;
+                dst[(int64_t)(i / V) * L * V + c * V + i % V] =
+                    stf<TS>((double)F[(w + f.p0 + i) + (int64_t)(f.p1 + c) * h]);
+            }
+        } else if (f.kind == SN_BDIAG) {
+            const int rel0 = f.p1 - f.p0;
+            for (int j = 0; j < f.n; ++j) {
+                const int r = f.p1 + j, gj = j / V, len = min(r - f.p0 + 1, L);
+                const int64_t o = sn_bdiag_off(gj, rel0, L, V) + j % V;
+                for (int c = lane; c < len; c += 32) dst[o + (int64_t)c * V] = stf<TS>((double)D[rpack(r, f.p0 + c)]);
+            }
         }
     }
 }
@@ -306,21 +324,71 @@ __global__ void __launch_bounds__(256) k_sn_finalize(SnTables t, int nsn, const 
 // ---------------------------------------------------------------------------------
 // Batched local solves  out = S L^{-T} L^{-1} S in  (S = diag(scale)), one CTA of NW
 // warps per job (subdomain, input offset, output offset) and column.  Shared memory: v
-// and y (one entry per row of the subdomain) and U (the pushed updates, sum_J |R_J|).
+// and y over the subdomain's rows, and per warp a RING-byte ring with its mbarriers.
 //
-// Forward sweep, levels from the leaves up; at a level, with a CTA barrier after each
-// phase:  pull    v_r -= sum of U entries targeting row r (fixed order)   [rows of J]
-//         diag    y_J = D_J v_J                                           [rows of J]
-//         push    U_J = L_{R_J,J} y_J                                     [rows of R_J]
-// Backward sweep, levels from the top down:
-//         panel   y_J = y_J - L_{R_J,J}^T v_{R_J}   (ancestors' final values in v)
-//         diag    v_J = D_J^T y_J
-// Work units are (supernode, 32-row chunk), dealt round-robin to the warps; lane = row
-// for column-major streams, lane = column for row-major ones, so every stream read is a
-// run of consecutive addresses across the lanes.
+// Each warp interprets its own record stream (snode_stream.h): lane 0 keeps up to RING
+// bytes of it in flight as bulk async copies of kChunk bytes (chunk k lands in slot
+// k % NSLOT once the bytes of chunk k - NSLOT have been consumed), the warp waits for a
+// record's chunks, applies it from shared memory and moves on; across record and level
+// boundaries the copies stay ahead.  Forward records (levels from the leaves up):
+// descendants' panel rows times their solved values subtracted from the unit's rows, then
+// D_J applied (y); backward records (levels from the top down): the panel's transpose
+// times the ancestors' final values subtracted, then D_J^T applied (v).  Barrier records
+// separate the levels (and the two phases of levels holding a supernode wider than 32).
+// Every wait is bounded: on timeout the warp sets the error word, still passes the
+// barriers its stream has left (so no warp of the CTA waits forever), waits (bounded)
+// for its own copies in flight and skips the output.
 // ---------------------------------------------------------------------------------
+constexpr int kRing = 4096;     // bytes of stream in shared memory per warp
+constexpr int kChunk = 1024;    // bytes per bulk copy
+constexpr int kSlots = kRing / kChunk;
+
+// Narrow units use groups of lanes: lanes = (item, group) with RB = next power of two of
+// the unit's items (rows or columns) and G = 32 / RB groups that split the loop; the
+// groups' partial sums are added by xor shuffles at the end.
+__device__ __forceinline__ int pow2_ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+template <typename TA>
+__device__ __forceinline__ TA group_sum(TA x, int rb) {
+    for (int o = rb; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+template <typename TS, typename TA>
+struct G8;
+template <>
+struct G8<__nv_bfloat16, float> {
+    __device__ static void get(uint2 u, float (&e)[4]) {
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        e[0] = a.x;
+        e[1] = a.y;
+        e[2] = b.x;
+        e[3] = b.y;
+    }
+};
+template <>
+struct G8<float, float> {
+    __device__ static void get(uint2 u, float (&e)[2]) {
+        e[0] = __uint_as_float(u.x);
+        e[1] = __uint_as_float(u.y);
+    }
+};
+template <>
+struct G8<double, double> {
+    __device__ static void get(uint2 u, double (&e)[1]) { e[0] = __hiloint2double((int)u.y, (int)u.x); }
+};
+// Operand x[x0 + k] for a group position k, zero past the record's columns (padding).
+template <typename TA>
+__device__ __forceinline__ TA xval(const TA* x, int x0, int k, int n) {
+    return k < n ? x[x0 + k] : (TA)0;
+}
+
 template <typename TS, typename TA, int NW>
-__global__ void __launch_bounds__(NW * 32) k_sn_solve(SnSolveArgs a) {
+__global__ void __launch_bounds__(NW * 32) k_sn_stream(SnSolveArgs a) {
+    constexpr int V = 8 / (int)sizeof(TS);
     const int col = a.col_fast ? blockIdx.x : 0;
     const int job = a.col_fast ? blockIdx.y : blockIdx.x;
     if (a.done && a.done[col * a.done_stride]) return;
@@ -329,127 +397,206 @@ __global__ void __launch_bounds__(NW * 32) k_sn_solve(SnSolveArgs a) {
     const int64_t g0 = t.sub_off[s];
     const int n = (int)(t.sub_off[s + 1] - g0);
     const int npad = (n + 3) & ~3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA* v = reinterpret_cast<TA*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint8_t* rings = smem_raw;                                            // [NW][kRing]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(rings + NW * kRing);     // [NW][kSlots]
+    TA* tmp = reinterpret_cast<TA*>(bars + NW * kSlots);                  // [NW][32]
+    int* flag = reinterpret_cast<int*>(tmp + NW * 32);                    // [4]
+    TA* v = reinterpret_cast<TA*>(flag + 4);
     TA* y = v + npad;
-    TA* U = y + npad;
-    const TS* Pf = (const TS*)a.Pf;
-    const TS* Pb = (const TS*)a.Pb;
-    const TS* Df = (const TS*)a.Df;
-    const TS* Db = (const TS*)a.Db;
-    const double* in = a.in + a.job_in[job] + col * a.ldin;
-    double* out = a.out + a.job_out[job] + col * a.ldout;
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     constexpr int NT = NW * 32;
-    const bool f32 = sizeof(TA) == 4;
+    constexpr bool f32 = sizeof(TA) == 4;
+    constexpr unsigned FULL = 0xffffffffu;
+    uint8_t* ring = rings + wp * kRing;
+    uint64_t* bar = bars + wp * kSlots;
+    TA* tw = tmp + wp * 32;
+    const uint8_t* gs = a.stream + a.woff[(int64_t)s * NW + wp];
+    const int64_t len = a.woff[(int64_t)s * NW + wp + 1] - a.woff[(int64_t)s * NW + wp];
+    const int nbar = a.nbar[s];
+    if (lane == 0) {
+        for (int i = 0; i < kSlots; ++i) mbar_init(smem_u32(&bar[i]), 1);
+        fence_async_smem();
+    }
+    if (tid == 0) flag[0] = 0;
+    const double* in = a.in + a.job_in[job] + col * a.ldin;
+    double* out = a.out + a.job_out[job] + col * a.ldout;
     for (int i = tid; i < n; i += NT) {
         if (f32) v[i] = (TA)((float)in[i] * (a.scale32 ? a.scale32[g0 + i] : 1.0f));
         else v[i] = (TA)(in[i] * (a.scale ? a.scale[g0 + i] : 1.0));
     }
     __syncthreads();
-    const int sn0 = t.sn_off[s], nlev = t.nlev[s], l0 = t.lev0[s];
-    // ----- forward: L y = v -----
-    for (int lv = 0; lv < nlev; ++lv) {
-        const int gl = l0 + lv;
-        const int du0 = t.lev_du[gl], du1 = t.lev_du[gl + 1];
-        for (int u = du0 + wp; u < du1; u += NW) {
-            const uint32_t pk = t.du[u];
-            const int J = sn0 + (int)(pk >> 10), q = (int)(pk & 1023);
-            const int rr = q * TILE + lane;
-            if (rr < t.w[J]) {
-                const int r = t.c0[J] + rr;
-                TA acc = v[r];
-                const int k1 = t.inv_ptr[g0 + r + 1];
-                for (int k = t.inv_ptr[g0 + r]; k < k1; ++k) acc -= U[t.inv_idx[k]];
-                v[r] = acc;
+    int64_t issued = 0, landed = 0, consumed = 0;   // chunks issued / landed, bytes consumed
+    const int64_t nchunks = (len + kChunk - 1) / kChunk;
+    auto refill = [&]() {
+        if (lane == 0) {
+            while (issued < nchunks && (issued + 1) * kChunk <= consumed + kRing) {
+                const int sl = (int)(issued % kSlots);
+                const uint32_t b = (uint32_t)min((int64_t)kChunk, len - issued * kChunk);
+                mbar_expect_tx(smem_u32(&bar[sl]), b);
+                bulk_copy(smem_u32(ring + sl * kChunk), gs + issued * kChunk, b, smem_u32(&bar[sl]));
+                ++issued;
             }
         }
-        __syncthreads();
-        for (int u = du0 + wp; u < du1; u += NW) {
-            const uint32_t pk = t.du[u];
-            const int J = sn0 + (int)(pk >> 10), q = (int)(pk & 1023);
-            const int w = t.w[J], c0 = t.c0[J];
-            const int rr = q * TILE + lane;
-            const TS* Dj = Df + t.doff[J];
-            const int cend = min(w, q * TILE + TILE);
-            TA a0 = 0, a1 = 0;
-            int c = 0;
-            if (rr < w) {
-                for (; c + 1 < cend && c + 1 <= rr; c += 2) {
-                    a0 += ldf<TA, TS>(Dj + cpack(rr, c, w)) * v[c0 + c];
-                    a1 += ldf<TA, TS>(Dj + cpack(rr, c + 1, w)) * v[c0 + c + 1];
+        issued = __shfl_sync(FULL, issued, 0);
+    };
+    // waits until bytes [.., upto) of the stream have landed; false on timeout
+    auto land = [&](int64_t upto) -> bool {
+        while (landed * kChunk < upto) {
+            if (landed >= issued) refill();
+            if (landed >= issued) return false;   // nothing in flight covers it (malformed)
+            const bool ok = mbar_wait(smem_u32(&bar[landed % kSlots]), (uint32_t)((landed / kSlots) & 1));
+            if (!__all_sync(FULL, ok)) return false;
+            ++landed;
+        }
+        return true;
+    };
+    int bars_done = 0;
+    bool ok = true;
+    TA acc = 0, dacc = 0;
+    for (;;) {
+        refill();
+        if (!(ok = land(consumed + 16))) break;
+        SnRec rc;
+        {
+            const uint4 hv = *reinterpret_cast<const uint4*>(ring + (consumed & (kRing - 1)));
+            rc = *reinterpret_cast<const SnRec*>(&hv);
+        }
+        if (!(ok = land(consumed + rc.bytes))) break;
+        if (rc.kind == SN_END) break;
+        if (rc.kind == SN_BARRIER) {
+            __syncthreads();
+            ++bars_done;
+            consumed += rc.bytes;
+            continue;
+        }
+        const int64_t ip = consumed + 16, dp = ip + rc.hdr;
+        // 8-byte entry group q of the record (a group never straddles the ring's end)
+        auto grp = [&](int64_t q, TA(&e)[V]) {
+            G8<TS, TA>::get(*reinterpret_cast<const uint2*>(ring + ((dp + 8 * q) & (kRing - 1))), e);
+        };
+        auto idx8 = [&](int k) -> int { return ring[(ip + k) & (kRing - 1)]; };
+        auto idx16 = [&](int k) -> int {
+            return *reinterpret_cast<const uint16_t*>(ring + ((ip + 2 * k) & (kRing - 1)));
+        };
+        const int L = rc.lanes;
+        if (rc.kind == SN_FCONTRIB) {
+            const int R = rc.rows, RB = pow2_ceil(R), G = 32 / RB;
+            const int i = lane & (RB - 1), g = lane / RB;
+            const int ng = (rc.ncols + V - 1) / V;
+            if (rc.flags & SN_FIRST) acc = lane < L ? v[rc.t0 + lane] : (TA)0;
+            tw[lane] = 0;
+            TA s0 = 0, s1 = 0;
+            if (i < R) {
+                int q = g;
+                for (; q + G < ng; q += 2 * G) {
+                    TA e0[V], e1[V];
+                    grp((int64_t)q * R + i, e0);
+                    grp((int64_t)(q + G) * R + i, e1);
+#pragma unroll
+                    for (int u = 0; u < V; ++u) {
+                        s0 += e0[u] * xval(y, rc.x0, q * V + u, rc.ncols);
+                        s1 += e1[u] * xval(y, rc.x0, (q + G) * V + u, rc.ncols);
+                    }
                 }
-                for (; c <= rr; ++c) a0 += ldf<TA, TS>(Dj + cpack(rr, c, w)) * v[c0 + c];
-                y[c0 + rr] = a0 + a1;
-            }
-        }
-        __syncthreads();
-        const int pu0 = t.lev_pu[gl], pu1 = t.lev_pu[gl + 1];
-        for (int u = pu0 + wp; u < pu1; u += NW) {
-            const uint32_t pk = t.pu[u];
-            const int J = sn0 + (int)(pk >> 10), q = (int)(pk & 1023);
-            const int w = t.w[J], nr = t.nr[J], c0 = t.c0[J];
-            const int i = q * TILE + lane;
-            if (i < nr) {
-                const TS* Pj = Pf + t.poff[J] + i;
-                TA a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-                int c = 0;
-                for (; c + 3 < w; c += 4) {
-                    a0 += ldf<TA, TS>(Pj + (int64_t)c * nr) * y[c0 + c];
-                    a1 += ldf<TA, TS>(Pj + (int64_t)(c + 1) * nr) * y[c0 + c + 1];
-                    a2 += ldf<TA, TS>(Pj + (int64_t)(c + 2) * nr) * y[c0 + c + 2];
-                    a3 += ldf<TA, TS>(Pj + (int64_t)(c + 3) * nr) * y[c0 + c + 3];
+                if (q < ng) {
+                    TA e0[V];
+                    grp((int64_t)q * R + i, e0);
+#pragma unroll
+                    for (int u = 0; u < V; ++u) s0 += e0[u] * xval(y, rc.x0, q * V + u, rc.ncols);
                 }
-                for (; c < w; ++c) a0 += ldf<TA, TS>(Pj + (int64_t)c * nr) * y[c0 + c];
-                U[t.uoff[J] + i] = (a0 + a1) + (a2 + a3);
+            }
+            const TA sdot = group_sum<TA>(s0 + s1, RB);
+            __syncwarp();
+            if (g == 0 && i < R) tw[idx8(i)] = sdot;
+            __syncwarp();
+            acc -= tw[lane];
+            if ((rc.flags & SN_LAST) && lane < L) v[rc.t0 + lane] = acc;
+        } else if (rc.kind == SN_FDIAG) {
+            const int RB = pow2_ceil(L), G = 32 / RB;
+            const int l = lane & (RB - 1), g = lane / RB;
+            const int ng = (rc.ncols + V - 1) / V, rel0 = (int)rc.x0 - (int)rc.t0;
+            if (rc.flags & SN_FIRST) dacc = 0;
+            if (l < L) {
+                for (int q = g; q < ng; q += G) {
+                    const int st = max(0, rel0 + q * V);
+                    if (l >= st) {
+                        TA e0[V];
+                        grp((sn_fdiag_off(q, rel0, L, V) + (int64_t)(l - st) * V) / V, e0);
+#pragma unroll
+                        for (int u = 0; u < V; ++u) dacc += e0[u] * xval(v, rc.x0, q * V + u, rc.ncols);
+                    }
+                }
+            }
+            if (rc.flags & SN_LAST) {
+                const TA sum = group_sum<TA>(dacc, RB);
+                if (g == 0 && l < L) y[rc.t0 + l] = sum;
+            }
+        } else if (rc.kind == SN_BPANEL) {
+            const int RB = pow2_ceil(L), G = 32 / RB;
+            const int c = lane & (RB - 1), g = lane / RB;
+            const int ng = (rc.rows + V - 1) / V;
+            if (rc.flags & SN_FIRST) acc = (g == 0 && c < L) ? y[rc.t0 + c] : (TA)0;
+            if (c < L) {
+                TA s0 = 0, s1 = 0;
+                int q = g;
+                for (; q + G < ng; q += 2 * G) {
+                    TA e0[V], e1[V];
+                    grp((int64_t)q * L + c, e0);
+                    grp((int64_t)(q + G) * L + c, e1);
+#pragma unroll
+                    for (int u = 0; u < V; ++u) {
+                        s0 += e0[u] * v[idx16(q * V + u)];
+                        s1 += e1[u] * v[idx16((q + G) * V + u)];
+                    }
+                }
+                if (q < ng) {
+                    TA e0[V];
+                    grp((int64_t)q * L + c, e0);
+#pragma unroll
+                    for (int u = 0; u < V; ++u) s0 += e0[u] * v[idx16(q * V + u)];
+                }
+                acc -= s0 + s1;
+            }
+            if (rc.flags & SN_LAST) {
+                const TA sum = group_sum<TA>(acc, RB);
+                if (g == 0 && c < L) y[rc.t0 + c] = sum;
+            }
+        } else if (rc.kind == SN_BDIAG) {
+            const int RB = pow2_ceil(L), G = 32 / RB;
+            const int c = lane & (RB - 1), g = lane / RB;
+            const int ng = (rc.ncols + V - 1) / V, rel0 = (int)rc.x0 - (int)rc.t0;
+            if (rc.flags & SN_FIRST) dacc = 0;
+            if (c < L) {
+                for (int q = g; q < ng; q += G) {
+                    const int cnt = min(L, rel0 + q * V + V);
+                    if (c < cnt) {
+                        TA e0[V];
+                        grp((sn_bdiag_off(q, rel0, L, V) + (int64_t)c * V) / V, e0);
+#pragma unroll
+                        for (int u = 0; u < V; ++u) dacc += e0[u] * xval(y, rc.x0, q * V + u, rc.ncols);
+                    }
+                }
+            }
+            if (rc.flags & SN_LAST) {
+                const TA sum = group_sum<TA>(dacc, RB);
+                if (g == 0 && c < L) v[rc.t0 + c] = sum;
             }
         }
-        __syncthreads();
+        __syncwarp();
+        consumed += rc.bytes;
     }
-    // ----- backward: L^T x = y -----
-    for (int lv = nlev - 1; lv >= 0; --lv) {
-        const int gl = l0 + lv;
-        const int du0 = t.lev_du[gl], du1 = t.lev_du[gl + 1];
-        for (int u = du0 + wp; u < du1; u += NW) {
-            const uint32_t pk = t.du[u];
-            const int J = sn0 + (int)(pk >> 10), q = (int)(pk & 1023);
-            const int w = t.w[J], nr = t.nr[J], c0 = t.c0[J];
-            const int c = q * TILE + lane;
-            if (c < w) {
-                const TS* Pj = Pb + t.poff[J] + c;
-                const uint16_t* R = t.rows + t.roff[J];
-                TA a0 = y[c0 + c], a1 = 0, a2 = 0, a3 = 0;
-                int i = 0;
-                for (; i + 3 < nr; i += 4) {
-                    a0 -= ldf<TA, TS>(Pj + (int64_t)i * w) * v[R[i]];
-                    a1 -= ldf<TA, TS>(Pj + (int64_t)(i + 1) * w) * v[R[i + 1]];
-                    a2 -= ldf<TA, TS>(Pj + (int64_t)(i + 2) * w) * v[R[i + 2]];
-                    a3 -= ldf<TA, TS>(Pj + (int64_t)(i + 3) * w) * v[R[i + 3]];
-                }
-                for (; i < nr; ++i) a0 -= ldf<TA, TS>(Pj + (int64_t)i * w) * v[R[i]];
-                y[c0 + c] = (a0 + a1) + (a2 + a3);
-            }
+    if (!ok) {
+        if (lane == 0) {
+            atomicExch(a.err, 1);
+            flag[0] = 1;
         }
-        __syncthreads();
-        for (int u = du0 + wp; u < du1; u += NW) {
-            const uint32_t pk = t.du[u];
-            const int J = sn0 + (int)(pk >> 10), q = (int)(pk & 1023);
-            const int w = t.w[J], c0 = t.c0[J];
-            const int c = q * TILE + lane;
-            if (c < w) {
-                const TS* Dj = Db + t.doff[J];
-                TA a0 = 0, a1 = 0;
-                int r = c;
-                for (; r + 1 < w; r += 2) {
-                    a0 += ldf<TA, TS>(Dj + rpack(r, c)) * y[c0 + r];
-                    a1 += ldf<TA, TS>(Dj + rpack(r + 1, c)) * y[c0 + r + 1];
-                }
-                for (; r < w; ++r) a0 += ldf<TA, TS>(Dj + rpack(r, c)) * y[c0 + r];
-                v[c0 + c] = a0 + a1;
-            }
-        }
-        __syncthreads();
+        for (; bars_done < nbar; ++bars_done) __syncthreads();
+        // copies still in flight land in this warp's ring: wait for them (bounded)
+        for (; landed < issued; ++landed) mbar_wait(smem_u32(&bar[landed % kSlots]), (uint32_t)((landed / kSlots) & 1));
     }
+    __syncthreads();
+    if (flag[0]) return;
     for (int i = tid; i < n; i += NT) {
         double x;
         if (f32) x = (double)((float)v[i] * (a.scale32 ? a.scale32[g0 + i] : 1.0f));
@@ -475,24 +622,31 @@ cudaError_t launch_sn_factor(const SnTables& t, int m, int max_part, const int32
 }
 
 template <typename TW, typename TS>
-cudaError_t launch_sn_finalize(const SnTables& t, int nsn, const TW* work, const TW* dwork, TS* Pf, TS* Pb, TS* Df,
-                               TS* Db, cudaStream_t st) {
-    if (nsn == 0) return cudaSuccess;
-    k_sn_finalize<TW, TS><<<min(nsn, 148 * 16), 256, 0, st>>>(t, nsn, work, dwork, Pf, Pb, Df, Db);
+cudaError_t launch_sn_fill(const SnTables& t, const SnFill* fill, int64_t nfill, const TW* work, const TW* dwork,
+                           uint8_t* stream, cudaStream_t st) {
+    if (nfill == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((nfill + 7) / 8, 148 * 32);
+    k_sn_fill<TW, TS><<<(int)blocks, 256, 0, st>>>(t, fill, nfill, work, dwork, stream);
     count_launch();
     return cudaGetLastError();
 }
 
-size_t sn_solve_smem(int max_part, int max_usum, size_t ta_bytes) {
-    return (2 * (size_t)((max_part + 3) & ~3) + (size_t)max_usum) * ta_bytes;
+constexpr int kSolveWarps = 8;
+int sn_solve_warps() { return kSolveWarps; }
+// a record must land while the next chunk is still free to be issued
+int sn_max_record() { return kRing - kChunk; }
+
+size_t sn_solve_smem(int max_part, size_t ta_bytes) {
+    return (size_t)kSolveWarps * kRing + (size_t)kSolveWarps * kSlots * 8 + (size_t)kSolveWarps * 32 * ta_bytes +
+           16 + 2 * (size_t)((max_part + 3) & ~3) * ta_bytes;
 }
 
 template <typename TS, typename TA>
-cudaError_t launch_sn_solve(const SnSolveArgs& a, int njobs, int ncols, int max_part, int max_usum, cudaStream_t st) {
+cudaError_t launch_sn_solve(const SnSolveArgs& a, int njobs, int ncols, int max_part, cudaStream_t st) {
     if (njobs == 0 || ncols == 0) return cudaSuccess;
-    constexpr int NW = 8;
-    const size_t smem = sn_solve_smem(max_part, max_usum, sizeof(TA));
-    cudaError_t e = cudaFuncSetAttribute(k_sn_solve<TS, TA, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int NW = kSolveWarps;
+    const size_t smem = sn_solve_smem(max_part, sizeof(TA));
+    cudaError_t e = cudaFuncSetAttribute(k_sn_stream<TS, TA, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SnSolveArgs b = a;
     dim3 grid;
@@ -503,7 +657,7 @@ cudaError_t launch_sn_solve(const SnSolveArgs& a, int njobs, int ncols, int max_
         b.col_fast = 0;
         grid = dim3(njobs);
     }
-    k_sn_solve<TS, TA, NW><<<grid, NW * 32, smem, st>>>(b);
+    k_sn_stream<TS, TA, NW><<<grid, NW * 32, smem, st>>>(b);
     count_launch();
     return cudaGetLastError();
 }
@@ -514,15 +668,14 @@ template cudaError_t launch_sn_factor<float>(const SnTables&, int, int, const in
 template cudaError_t launch_sn_factor<double>(const SnTables&, int, int, const int32_t*, const int32_t*, const int32_t*,
                                               const double*, const double*, const double*, double*, double*, int*,
                                               cudaStream_t);
-template cudaError_t launch_sn_finalize<double, double>(const SnTables&, int, const double*, const double*, double*,
-                                                        double*, double*, double*, cudaStream_t);
-template cudaError_t launch_sn_finalize<float, float>(const SnTables&, int, const float*, const float*, float*, float*,
-                                                      float*, float*, cudaStream_t);
-template cudaError_t launch_sn_finalize<float, __nv_bfloat16>(const SnTables&, int, const float*, const float*,
-                                                              __nv_bfloat16*, __nv_bfloat16*, __nv_bfloat16*,
-                                                              __nv_bfloat16*, cudaStream_t);
-template cudaError_t launch_sn_solve<double, double>(const SnSolveArgs&, int, int, int, int, cudaStream_t);
-template cudaError_t launch_sn_solve<float, float>(const SnSolveArgs&, int, int, int, int, cudaStream_t);
-template cudaError_t launch_sn_solve<__nv_bfloat16, float>(const SnSolveArgs&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_sn_fill<double, double>(const SnTables&, const SnFill*, int64_t, const double*,
+                                                    const double*, uint8_t*, cudaStream_t);
+template cudaError_t launch_sn_fill<float, float>(const SnTables&, const SnFill*, int64_t, const float*, const float*,
+                                                  uint8_t*, cudaStream_t);
+template cudaError_t launch_sn_fill<float, __nv_bfloat16>(const SnTables&, const SnFill*, int64_t, const float*,
+                                                          const float*, uint8_t*, cudaStream_t);
+template cudaError_t launch_sn_solve<double, double>(const SnSolveArgs&, int, int, int, cudaStream_t);
+template cudaError_t launch_sn_solve<float, float>(const SnSolveArgs&, int, int, int, cudaStream_t);
+template cudaError_t launch_sn_solve<__nv_bfloat16, float>(const SnSolveArgs&, int, int, int, cudaStream_t);
 
 }  // namespace am
