@@ -46,14 +46,37 @@ double now_ms() {
 
 // Device buffers of Algorithm 1 that survive between numeric setups (value updates
 // reuse them, so captured graphs and pointers stay valid).
+// Column-block jobs of the multi-column chain solve: up to COLS_PER_JOB columns of one
+// item at a constant stride, the smallest start row of the block (identity columns).
+struct BlockJobs {
+    std::vector<int32_t> sub, nc, t0;
+    std::vector<int64_t> in, ld;
+    void add(int32_t item, int64_t base, int64_t stride, int64_t ncols, bool identity_t0) {
+        for (int64_t c = 0; c < ncols; c += COLS_PER_JOB) {
+            sub.push_back(item);
+            in.push_back(base + c * stride);
+            ld.push_back(stride);
+            nc.push_back((int32_t)std::min<int64_t>(COLS_PER_JOB, ncols - c));
+            t0.push_back(identity_t0 ? (int32_t)(c / TILE) : 0);
+        }
+    }
+    int size() const { return (int)sub.size(); }
+};
+struct DevBlockJobs {
+    int n = 0;
+    int32_t *sub = nullptr, *nc = nullptr, *t0 = nullptr;
+    int64_t *in = nullptr, *ld = nullptr;
+};
+
 struct NumWs {
     bool ready = false;
-    int njobs_mbf = 0;                        // MBF solves: one job per (subdomain, column)
+    int njobs_mbf = 0;
+    DevBlockJobs bj_mbf;                      // column-block jobs of the MBF solves
     int32_t *d_js = nullptr, *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
     int64_t *d_jo = nullptr, *d_goff = nullptr, *d_gcptr = nullptr;
     double* d_gval = nullptr;
     double* d_T = nullptr;
-    void *work = nullptr, *dinv = nullptr;   // local factorisation fronts, D_J work
+    void *work = nullptr, *dinv = nullptr;
     int* d_err = nullptr;
     double *rhs = nullptr, *phi64 = nullptr, *diagc = nullptr, *Sd = nullptr;
     // interface groups as factor items (non-empty groups only)
@@ -97,6 +120,9 @@ struct Vecs {
     GridSum gs{};
     cudaGraphExec_t graph = nullptr;
     int graph_k = 0;                   // column count the graph was captured with
+    DevBlockJobs bj;                   // column-block jobs of the batched local solves
+    int32_t* bj_col0 = nullptr;
+    int bj_k = 0;                      // column count bj was built for
     int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
 };
 
@@ -115,19 +141,13 @@ struct algmortar_handle {
     int64_t* d_sub_off = nullptr;
     int nchunks = 0;                   // prolongation: row chunks (<= VEC_BS rows of one subdomain)
     int32_t *d_chunk_sub = nullptr, *d_chunk_off = nullptr;
-    // supernodal local factors: tables, the per-warp record streams of the solves (their
-    // headers and index lists uploaded at setup, entries filled from each numeric
-    // factorisation) and the fill descriptors
-    SnTables sn{};
-    int32_t* d_rows = nullptr;
-    uint8_t* d_stream = nullptr;
-    int64_t* d_woff = nullptr;
-    int32_t* d_nbar = nullptr;
-    SnFill* d_fill = nullptr;
-    int64_t n_fill = 0, stream_bytes = 0;
+    // local factor profile and streams
+    Profile pf{};
+    int32_t *d_rows = nullptr, *d_ntiles = nullptr;
+    void *d_fwdS = nullptr, *d_bwdS = nullptr;
     // block-Jacobi smoother (Sec. 5.4): factors of the unmodified blocks A_ii on the same
-    // supernodal layout (a second copy of the streams), and their symmetric scaling
-    uint8_t* d_stream2 = nullptr;
+    // tile profiles, and their symmetric scaling
+    void *d_fwdS2 = nullptr, *d_bwdS2 = nullptr;
     double *d_dloc2 = nullptr, *d_sc2 = nullptr;
     float* d_sc2_32 = nullptr;
     double *d_dloc = nullptr, *d_sc = nullptr;
@@ -211,6 +231,29 @@ int upload(algmortar_t* h, T*& dst, const std::vector<T>& src) {
         if (rc_) return rc_; \
     } while (0)
 
+int upload_jobs(algmortar_t* h, DevBlockJobs& d, const BlockJobs& b) {
+    d.n = b.size();
+    TRY(upload(h, d.sub, b.sub));
+    TRY(upload(h, d.nc, b.nc));
+    TRY(upload(h, d.t0, b.t0));
+    TRY(upload(h, d.in, b.in));
+    TRY(upload(h, d.ld, b.ld));
+    return 0;
+}
+
+// A solve over column-block jobs (SolveArgs.job_* set from d; in/out offsets shared).
+template <typename TS, typename TA>
+int solve_cols(SolveArgs a, const DevBlockJobs& d, bool identity, int max_tiles, cudaStream_t st) {
+    a.job_sub = d.sub;
+    a.job_in = d.in;
+    a.job_out = d.in;
+    a.job_ld = d.ld;
+    a.job_nc = d.nc;
+    a.job_t0 = identity ? d.t0 : nullptr;
+    CU((launch_tile_solve_cols<TS, TA>(a, d.n, max_tiles, st)));
+    return 0;
+}
+
 int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
     int e[2];
     CU(cudaMemcpyAsync(e, d_err, sizeof(e), cudaMemcpyDeviceToHost, h->st));
@@ -220,84 +263,13 @@ int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
     return 0;
 }
 
-// Device copies of the supernodal tables of the local factors.
-int upload_sn_tables(algmortar_t* h) {
-    const Plan& P = h->P;
-    SnTables& t = h->sn;
-    const int32_t nsn = P.sn_off[P.m];
-    std::vector<SnMeta> meta(nsn);
-    for (int32_t J = 0; J < nsn; ++J)
-        meta[J] = SnMeta{P.sn_c0[J], P.sn_w[J], P.sn_nr[J], 0, P.sn_poff[J], P.sn_doff[J], P.sn_roff[J], 0};
-    int64_t* sub_off = nullptr;
-    int32_t *sn_off = nullptr, *c0 = nullptr, *w = nullptr, *nr = nullptr, *upd = nullptr;
-    int64_t *roff = nullptr, *poff = nullptr, *doff = nullptr, *foff = nullptr, *updp = nullptr;
-    uint16_t* rows = nullptr;
-    int32_t *nlev = nullptr, *lev0 = nullptr, *lev_du = nullptr, *fwd_ptr = nullptr;
-    uint8_t* lev_multi = nullptr;
-    uint32_t *du = nullptr, *fwd_desc = nullptr;
-    SnMeta* d_meta = nullptr;
-    TRY(upload(h, sub_off, P.sub_off));
-    TRY(upload(h, sn_off, P.sn_off));
-    TRY(upload(h, d_meta, meta));
-    TRY(upload(h, c0, P.sn_c0));
-    TRY(upload(h, w, P.sn_w));
-    TRY(upload(h, nr, P.sn_nr));
-    TRY(upload(h, roff, P.sn_roff));
-    TRY(upload(h, poff, P.sn_poff));
-    TRY(upload(h, doff, P.sn_doff));
-    TRY(upload(h, foff, P.sn_foff));
-    TRY(upload(h, updp, P.sn_upd_ptr));
-    TRY(upload(h, rows, P.sn_rows));
-    TRY(upload(h, upd, P.sn_upd));
-    TRY(upload(h, nlev, P.sub_nlev));
-    TRY(upload(h, lev0, P.sub_lev0));
-    TRY(upload(h, lev_du, P.lev_du));
-    TRY(upload(h, lev_multi, P.lev_multi));
-    TRY(upload(h, du, P.du_list));
-    TRY(upload(h, fwd_ptr, P.fwd_ptr));
-    TRY(upload(h, fwd_desc, P.fwd_desc));
-    t = SnTables{sub_off, sn_off, d_meta, c0, w, nr, roff, poff, doff, foff, updp, rows, upd,
-                 nlev, lev0, lev_du, lev_multi, du, fwd_ptr, reinterpret_cast<const uint2*>(fwd_desc)};
-    return 0;
-}
-
-// Record streams of the batched local solves for the handle's precision (elem bytes per
-// factor entry): headers and index lists from the host, entries written by each
-// numeric factorisation.
-int upload_sn_stream(algmortar_t* h, int elem) {
-    SnStream S;
-    std::string err;
-    if (build_sn_stream(h->P, sn_solve_warps(), elem, S, err)) return fail(ALGMORTAR_INVALID_ARG, err);
-    if (S.max_record > sn_max_record()) return fail(ALGMORTAR_INVALID_ARG, "local solve stream: record too large");
-    h->stream_bytes = (int64_t)S.bytes.size();
-    h->n_fill = (int64_t)S.fill.size();
-    TRY(upload(h, h->d_stream, S.bytes));
-    TRY(upload(h, h->d_woff, S.woff));
-    TRY(upload(h, h->d_nbar, S.nbar));
-    TRY(upload(h, h->d_fill, S.fill));
-    return 0;
-}
-
-// Arguments of the batched local solves with the handle's factor (or the smoother's).
-SnSolveArgs local_args(const algmortar_t* h, bool smoother) {
-    SnSolveArgs a{};
-    a.t = h->sn;
-    a.stream = smoother ? h->d_stream2 : h->d_stream;
-    a.woff = h->d_woff;
-    a.nbar = h->d_nbar;
-    a.err = h->d_kerr;
-    a.scale = smoother ? h->d_sc2 : h->d_sc;
-    a.scale32 = smoother ? h->d_sc2_32 : h->d_sc32;
-    return a;
-}
-
 // Symbolic uploads and persistent buffers (first numeric setup only).
 template <typename TW, typename TS>
 int numeric_prepare(algmortar_t* h, NumWs& W) {
     if (W.ready) return 0;
     Plan& P = h->P;
     const int m = h->m, L = h->L;
-    const int64_t nphi = P.phi_off[m];
+    const int64_t tiles = P.total_tiles, trows = P.trow_off[m], nphi = P.phi_off[m];
     std::vector<int32_t> js;
     std::vector<int64_t> jo;
     for (int s = 0; s < m; ++s) {
@@ -308,6 +280,14 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         }
     }
     W.njobs_mbf = (int)js.size();
+    {
+        BlockJobs b;
+        for (int s = 0; s < m; ++s) {
+            const int64_t ns = P.sub_off[s + 1] - P.sub_off[s];
+            b.add(s, P.phi_off[s], ns, P.if_off[s + 1] - P.if_off[s], false);
+        }
+        TRY(upload_jobs(h, W.bj_mbf, b));
+    }
     std::vector<int64_t> gcptr;
     gcptr.reserve(P.if_off[m] + m);
     for (int s = 0; s < m; ++s) {
@@ -326,18 +306,20 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     TRY(upload(h, W.d_gcol, P.g_col));
     TRY(upload(h, W.d_gval, P.g_val));
     TRY(upload(h, W.d_pairs, P.pairs));
-    W.work = h->alloc<TW>((size_t)P.front_entries);
-    W.dinv = h->alloc<TW>((size_t)P.diag_entries);
+    W.work = h->alloc<TW>((size_t)tiles * TILE2);
+    W.dinv = h->alloc<TW>((size_t)trows * TILE2);
     W.d_err = h->alloc<int>(2);
     W.rhs = h->alloc<double>(nphi);
     W.phi64 = h->alloc<double>(nphi);
+    h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
+    h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
     if (h->opts.smooth_steps > 0) {
-        h->d_stream2 = h->alloc<uint8_t>((size_t)h->stream_bytes);
-        if (!h->d_stream2) return fail(ALGMORTAR_OOM, "smoother factor streams");
-        CU(cudaMemcpyAsync(h->d_stream2, h->d_stream, (size_t)h->stream_bytes, cudaMemcpyDeviceToDevice, h->st));
+        h->d_fwdS2 = h->alloc<TS>((size_t)tiles * TILE2);
+        h->d_bwdS2 = h->alloc<TS>((size_t)tiles * TILE2);
+        if (!h->d_fwdS2 || !h->d_bwdS2) return fail(ALGMORTAR_OOM, "smoother factor buffers");
     }
     h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<PanelT<TS>>(nphi);
-    if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_phi)
+    if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
     if (L > 0) {
         TRY(upload(h, W.d_T, P.T));
@@ -570,7 +552,7 @@ int numeric_setup(algmortar_t* h) {
     for (auto& e : ev) cudaEventCreate(&e);
     cudaEventRecord(ev[0], st);
     const int m = h->m, L = h->L;
-    const int64_t nphi = P.phi_off[m];
+    const int64_t tiles = P.total_tiles, nphi = P.phi_off[m];
     TW* work = (TW*)W.work;
     TW* dinv = (TW*)W.dinv;
     // value-dependent interface tables (restriction coefficients, T_I, G entries)
@@ -579,34 +561,47 @@ int numeric_setup(algmortar_t* h) {
     // --- local factors (Algorithm 1: extract A_ii, modify its diagonal, factor) ---
     int err_init[2] = {0, -1};
     CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
     launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, 1, h->d_dloc,
                       h->d_sc, h->d_sc32, st);
-    CU(launch_sn_factor<TW>(h->sn, m, P.max_part, h->d_job_sub, h->d_rowptr, h->d_col, h->d_val, h->d_dloc, h->d_sc,
-                            work, dinv, W.d_err, st));
+    launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
+                             h->d_sc, work, m, st);
+    launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
+    CU(cudaGetLastError());
     TRY(read_err_flag(h, W.d_err, "local"));
-    CU((launch_sn_fill<TW, TS>(h->sn, h->d_fill, h->n_fill, work, dinv, h->d_stream, st)));
+    launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS, (TS*)h->d_bwdS, st);
+    CU(cudaGetLastError());
     if (h->opts.smooth_steps > 0) {
-        // smoother blocks = the subdomains, unmodified A_ii (same sparsity, same layout)
+        // smoother blocks = the subdomains, unmodified A_ii (same sparsity, same profile)
         CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(work, 0, (size_t)tiles * TILE2 * sizeof(TW), st));
         launch_local_diag(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->opts.diag_scale, 0, h->d_dloc2,
                           h->d_sc2, h->d_sc2_32, st);
-        CU(launch_sn_factor<TW>(h->sn, m, P.max_part, h->d_job_sub, h->d_rowptr, h->d_col, h->d_val, h->d_dloc2,
-                                h->d_sc2, work, dinv, W.d_err, st));
+        launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf,
+                                 h->d_dloc2, h->d_sc2, work, m, st);
+        launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
+        CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "smoother block"));
-        CU((launch_sn_fill<TW, TS>(h->sn, h->d_fill, h->n_fill, work, dinv, h->d_stream2, st)));
+        launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS2, (TS*)h->d_bwdS2, st);
+        CU(cudaGetLastError());
     }
     cudaEventRecord(ev[1], st);
     // --- MBFs (Eq. def-phat-local): Phi_i = A_i^{-1} (-B_i psi_m), one job per (i, m) ---
     CU(cudaMemsetAsync(W.rhs, 0, nphi * sizeof(double), st));
     launch_mbf_rhs(m, W.d_goff, W.d_grow, W.d_gcol, W.d_gval, h->d_rows, h->d_phi_off, W.rhs, st);
     {
-        SnSolveArgs a = local_args(h, false);
-        a.job_sub = W.d_js;
-        a.job_in = W.d_jo;
-        a.job_out = W.d_jo;
+        SolveArgs a{};
+        a.pf = h->pf;
+        a.fwdS = h->d_fwdS;
+        a.bwdS = h->d_bwdS;
+        a.scale = h->d_sc;
+        a.scale32 = h->d_sc32;
+        a.scale_off = h->d_sub_off;
         a.in = W.rhs;
         a.out = W.phi64;
-        CU((launch_sn_solve<TS, TA>(a, W.njobs_mbf, 1, P.max_part, st)));
+        a.done = nullptr;
+        a.err = h->d_kerr;
+        TRY((solve_cols<TS, TA>(a, W.bj_mbf, false, P.max_tiles, st)));
     }
     if (!std::is_same<TS, double>::value) launch_convert<PanelT<TS>>(nphi, W.phi64, (PanelT<TS>*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
@@ -744,7 +739,13 @@ ColStrides col_strides(const algmortar_t* h, const Vecs& v, bool pcg) {
 template <typename TS, typename TA>
 int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, bool smoother = false,
                 double* out = nullptr, bool accumulate = false) {
-    SnSolveArgs a = local_args(h, smoother);
+    SolveArgs a{};
+    a.pf = h->pf;
+    a.fwdS = smoother ? h->d_fwdS2 : h->d_fwdS;
+    a.bwdS = smoother ? h->d_bwdS2 : h->d_bwdS;
+    a.scale = smoother ? h->d_sc2 : h->d_sc;
+    a.scale32 = smoother ? h->d_sc2_32 : h->d_sc32;
+    a.scale_off = h->d_sub_off;
     a.job_sub = h->d_job_sub;
     a.job_in = h->d_job_off;
     a.job_out = h->d_job_off;
@@ -754,7 +755,15 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
-    CU((launch_sn_solve<TS, TA>(a, h->m, v.k, h->P.max_part, h->st)));
+    a.deep_ring = h->opts.deep_ring;
+    a.err = h->d_kerr;
+    if (v.k > 1) {
+        // batched columns: one job per (subdomain, block of COLS_PER_JOB columns), each
+        // factor tile read once per block
+        a.job_col0 = v.bj_col0;
+        return solve_cols<TS, TA>(a, v.bj, false, h->P.max_tiles, h->st);
+    }
+    CU((launch_tile_solve<TS, TA>(a, h->m, h->P.max_tiles, h->st, v.k)));
     return 0;
 }
 
@@ -905,6 +914,32 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     return 0;
 }
 
+// Column-block jobs for a batch of k > 1 columns: per subdomain (largest first) blocks of
+// COLS_PER_JOB consecutive columns at stride n.
+int ensure_batch_jobs(algmortar_t* h, Vecs& v) {
+    if (v.k <= 1 || v.bj_k == v.k) return 0;
+    std::vector<int32_t> rows(h->m), order(h->m);
+    for (int s = 0; s < h->m; ++s) {
+        rows[s] = (int32_t)(h->P.sub_off[s + 1] - h->P.sub_off[s]);
+        order[s] = s;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rows[x] > rows[y]; });
+    BlockJobs b;
+    std::vector<int32_t> col0;
+    for (int s : order) {
+        const size_t before = b.sub.size();
+        b.add(s, h->P.sub_off[s], h->n, v.k, false);
+        for (size_t j = before; j < b.sub.size(); ++j) col0.push_back((int32_t)((j - before) * COLS_PER_JOB));
+    }
+    void* old[] = {v.bj.sub, v.bj.nc, v.bj.t0, v.bj.in, v.bj.ld, v.bj_col0};
+    for (void* p : old)
+        if (p) h->release(p);
+    TRY(upload_jobs(h, v.bj, b));
+    TRY(upload(h, v.bj_col0, col0));
+    v.bj_k = v.k;
+    return 0;
+}
+
 // PCG in the internal ordering on v.b -> v.x for the batch's k columns; stats[j] per column.
 // Returns the worst column status.
 int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
@@ -913,6 +948,7 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     if (!(tol > 0.0)) return fail(ALGMORTAR_INVALID_ARG, "tol must be positive");
     const int k = v.k;
     const int64_t n = h->n;
+    TRY(ensure_batch_jobs(h, v));
     if (h->opts.use_graph) TRY(ensure_graph(h, v));
     launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, h->opts.flexible ? 1 : 0, st);
     TRY(apply_internal(h, v, v.r, v.z, true));
@@ -1015,17 +1051,6 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         return fail(rc, err);
     }
     if (o.nd_depth >= 0) plan_interface_nd(h->P, o.nd_depth);
-    {
-        // the batched local solve keeps two vectors over one subdomain's rows in shared
-        // memory
-        const size_t ta = o.precision == ALGMORTAR_FP64 ? 8 : 4;
-        const size_t need = sn_solve_smem(h->P.max_part, ta);
-        if (need > 227 * 1024) {
-            delete h;
-            return fail(ALGMORTAR_TOO_LARGE, "a subdomain's local solve needs " + std::to_string(need) +
-                                                 " bytes of shared memory (limit 232448): use more subdomains");
-        }
-    }
     double t_plan = now_ms();
     auto bail = [&](int code) {
         delete h;
@@ -1058,6 +1083,8 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a] > rows[b]; });
     std::vector<int64_t> joff(h->m);
     for (int t = 0; t < h->m; ++t) joff[t] = P.sub_off[order[t]];
+    int32_t *d_lo = nullptr, *d_hi = nullptr;
+    int64_t *d_row0 = nullptr, *d_base = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
     rc = 0;
     rc = rc ? rc : upload(h, h->d_rowptr, P.p_rowptr);
     rc = rc ? rc : upload(h, h->d_col, P.p_col);
@@ -1077,8 +1104,13 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         rc = rc ? rc : upload(h, h->d_chunk_off, co);
     }
     rc = rc ? rc : upload(h, h->d_rows, rows);
-    rc = rc ? rc : upload_sn_tables(h);
-    rc = rc ? rc : upload_sn_stream(h, o.precision == ALGMORTAR_FP64 ? 8 : (o.precision == ALGMORTAR_FP32 ? 4 : 2));
+    rc = rc ? rc : upload(h, h->d_ntiles, P.ntiles);
+    rc = rc ? rc : upload(h, d_row0, P.trow_off);
+    rc = rc ? rc : upload(h, d_base, P.tile_base);
+    rc = rc ? rc : upload(h, d_lo, P.t_lo);
+    rc = rc ? rc : upload(h, d_hi, P.t_hi);
+    rc = rc ? rc : upload(h, d_fwd, P.t_fwd);
+    rc = rc ? rc : upload(h, d_bwd, P.t_bwd);
     rc = rc ? rc : upload(h, h->d_job_sub, order);
     rc = rc ? rc : upload(h, h->d_job_off, joff);
     rc = rc ? rc : upload(h, h->d_rptr, P.r_ptr);
@@ -1107,6 +1139,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     if (cudaMemcpyAsync(h->d_vtmp, A->val, A->nnz * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
         return bail(fail(ALGMORTAR_CUDA, "upload values"));
     launch_ell_values(h->n_ell, h->d_ell_src, h->d_vtmp, h->d_ell_val, h->st);
+    h->pf = Profile{h->d_rows, h->d_ntiles, d_row0, d_base, d_lo, d_hi, d_fwd, d_bwd};
     const int64_t n = h->n;
     h->d_dloc = h->alloc<double>(n);
     h->d_sc = h->alloc<double>(n);
@@ -1136,18 +1169,18 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     I.min_part = P.min_part;
     I.precision = o.precision;
     I.n_interface_edges = P.n_edges;
-    I.factor_entries = P.panel_entries + P.diag_entries;
+    I.factor_entries = P.total_tiles * TILE2;
     int es = o.precision == ALGMORTAR_FP64 ? 8 : (o.precision == ALGMORTAR_FP32 ? 4 : 2);
-    I.factor_bytes = 2 * I.factor_entries * es;
+    I.factor_bytes = 2 * P.total_tiles * TILE2 * es;
     I.phi_entries = P.phi_off[h->m];
     I.setup_ms[0] = (t_part - t0) + (t_plan - t_part);
     I.setup_ms[1] = t_up - t_plan;
     I.setup_ms[7] = t_end - t0;
     if (o.verbose)
         std::fprintf(stderr,
-                     "[algmortar] n=%lld m=%d nLam=%d parts %d..%d factor entries=%lld | partition %.1f ms plan %.1f ms "
+                     "[algmortar] n=%lld m=%d nLam=%d parts %d..%d tiles=%lld | partition %.1f ms plan %.1f ms "
                      "upload %.1f | factor %.2f mbf %.2f iface-asm %.2f iface-factor %.2f iface-factor+inv %.2f | total %.1f ms\n",
-                     (long long)n, h->m, h->L, P.min_part, P.max_part, (long long)I.factor_entries, t_part - t0,
+                     (long long)n, h->m, h->L, P.min_part, P.max_part, (long long)P.total_tiles, t_part - t0,
                      t_plan - t_part, I.setup_ms[1], I.setup_ms[2], I.setup_ms[3], I.setup_ms[4], I.setup_ms[6], I.setup_ms[5],
                      I.setup_ms[7]);
     *out = h;

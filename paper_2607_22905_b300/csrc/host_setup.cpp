@@ -19,6 +19,36 @@ static std::string fmt(const char* f, long long a, long long b = 0, long long c 
     return buf;
 }
 
+namespace {
+
+// Runs f(i, t) for every i in [0, n) on up to 16 threads (t = thread index, for per-
+// thread scratch), taking indices in chunks from a shared counter.  Every i must write
+// only its own outputs, so the result does not depend on the schedule.  If threads cannot
+// be started, the calling thread runs everything.
+template <typename F>
+void parallel_for(int64_t n, int64_t chunk, F f) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 16),
+                                                             (n + chunk - 1) / std::max<int64_t>(chunk, 1)));
+    std::atomic<int64_t> next{0};
+    auto run = [&](int64_t t) {
+        for (;;) {
+            const int64_t i0 = next.fetch_add(chunk);
+            if (i0 >= n) return;
+            const int64_t i1 = std::min(n, i0 + chunk);
+            for (int64_t i = i0; i < i1; ++i) f(i, t);
+        }
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int64_t t = 1; t < T; ++t) pool.emplace_back(run, t);
+    } catch (...) {   // fewer threads: the counter hands their indices to the others
+    }
+    run(0);
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace
 
 namespace {
 
@@ -330,6 +360,115 @@ int partition_graph(const Graph& G, int32_t m, const int32_t* sizes_in, std::vec
 }
 
 // ------------------------------------------------------------------------------------
+// Reverse Cuthill-McKee on a local graph (CUDA path only: orders rows inside a subdomain
+// so that the Cholesky factor fits a narrow tile profile).
+// ------------------------------------------------------------------------------------
+std::vector<int32_t> rcm_order(int32_t n, const std::vector<int64_t>& ptr,
+                               const std::vector<int32_t>& adj) {
+    std::vector<int32_t> deg(n), dist(n, -1), q, out;
+    for (int32_t i = 0; i < n; ++i) deg[i] = (int32_t)(ptr[i + 1] - ptr[i]);
+    std::vector<char> seen(n, 0);
+    auto bfs_levels = [&](int32_t s) {
+        for (int32_t x : q) dist[x] = -1;
+        q.clear();
+        q.push_back(s);
+        dist[s] = 0;
+        size_t h = 0;
+        while (h < q.size()) {
+            int32_t u = q[h++];
+            for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e) {
+                int32_t v = adj[e];
+                if (dist[v] < 0) {
+                    dist[v] = dist[u] + 1;
+                    q.push_back(v);
+                }
+            }
+        }
+        return dist[q.back()];
+    };
+    std::vector<int32_t> nb;
+    int32_t next = 0;
+    out.reserve(n);
+    while ((int32_t)out.size() < n) {
+        while (seen[next]) ++next;
+        int32_t v = next, ecc = bfs_levels(v);
+        for (;;) {
+            int32_t u = -1, best = INT32_MAX;
+            for (int32_t x : q)
+                if (dist[x] == ecc && (deg[x] < best || (deg[x] == best && x < u))) {
+                    u = x;
+                    best = deg[x];
+                }
+            int32_t e2 = bfs_levels(u);
+            if (e2 > ecc) {
+                v = u;
+                ecc = e2;
+            } else {
+                break;
+            }
+        }
+        for (int32_t x : q) dist[x] = -1;
+        q.clear();
+        size_t h = out.size();
+        out.push_back(v);
+        seen[v] = 1;
+        while (h < out.size()) {
+            int32_t u = out[h++];
+            nb.clear();
+            for (int64_t e = ptr[u]; e < ptr[u + 1]; ++e)
+                if (!seen[adj[e]]) nb.push_back(adj[e]);
+            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+                return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+            });
+            for (int32_t x : nb)
+                if (!seen[x]) {
+                    seen[x] = 1;
+                    out.push_back(x);
+                }
+        }
+    }
+    std::reverse(out.begin(), out.end());
+    return out;
+}
+
+// Tile profile of the lower Cholesky factor for a pattern in its final local order.
+// Row r's envelope starts at f(r) = min(r, min adj(r)); tile row I starts at tile
+// lo(I) = min_{r in I} f(r)/TILE, made non-decreasing by a suffix minimum so that tile
+// column I of the factor occupies the contiguous rows I..hi(I).
+void tile_profile(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
+                  int32_t& ntiles, std::vector<int32_t>& lo, std::vector<int32_t>& hi,
+                  std::vector<int64_t>& fwd, std::vector<int64_t>& bwd, int64_t& tiles) {
+    ntiles = (n + TILE - 1) / TILE;
+    lo.assign(ntiles, 0);
+    hi.assign(ntiles, 0);
+    fwd.assign(ntiles, 0);
+    bwd.assign(ntiles, 0);
+    for (int32_t I = 0; I < ntiles; ++I) lo[I] = I;
+    for (int32_t r = 0; r < n; ++r) {
+        int32_t f = r;
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) f = std::min(f, adj[e]);
+        lo[r / TILE] = std::min(lo[r / TILE], f / TILE);
+    }
+    for (int32_t I = ntiles - 2; I >= 0; --I) lo[I] = std::min(lo[I], lo[I + 1]);
+    int32_t J = ntiles - 1;
+    for (int32_t I = ntiles - 1; I >= 0; --I) {
+        while (J > I && lo[J] > I) --J;
+        hi[I] = std::max(J, I);
+    }
+    int64_t o = 0;
+    for (int32_t I = 0; I < ntiles; ++I) {
+        fwd[I] = o;
+        o += I - lo[I] + 1;
+    }
+    tiles = o;
+    o = 0;
+    for (int32_t I = ntiles - 1; I >= 0; --I) {
+        bwd[I] = o;
+        o += hi[I] - I + 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------
 int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Plan& P,
                std::string& err) {
     const int64_t n = A.n;
@@ -372,12 +511,16 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
                 return 3;
             }
         }
-    // per subdomain nested-dissection order and supernodal layout of L_i -> internal
-    // ordering, subdomains in parallel (each writes its own ranges of perm / iperm and its
-    // own plan)
+    // per subdomain RCM order -> internal ordering, subdomains in parallel (each writes
+    // its own ranges of perm / iperm and its own profile)
     P.perm.resize(n);
     P.iperm.assign(n, -1);
-    std::vector<SnLocal> sl(m);
+    P.ntiles.resize(m);
+    P.trow_off.assign(m + 1, 0);
+    P.tile_base.assign(m + 1, 0);
+    std::vector<std::vector<int32_t>> t_lo(m), t_hi(m);
+    std::vector<std::vector<int64_t>> t_fwd(m), t_bwd(m);
+    std::vector<int64_t> tiles_of(m, 0);
     parallel_for(m, 1, [&](int64_t si, int64_t) {
         const int32_t s = (int32_t)si;
         const int64_t a = P.sub_off[s], b = P.sub_off[s + 1];
@@ -394,92 +537,40 @@ int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Pl
             }
             lp[t + 1] = (int64_t)la.size();
         }
-        sn_local_plan(ns, lp, la, sl[s]);
+        std::vector<int32_t> ord = rcm_order(ns, lp, la);
+        std::vector<int32_t> inv(ns);
         for (int32_t t = 0; t < ns; ++t) {
-            P.perm[a + t] = nb[sl[s].order[t]];
-            P.iperm[nb[sl[s].order[t]]] = (int32_t)(a + t);
+            inv[ord[t]] = t;
+            P.perm[a + t] = nb[ord[t]];
+            P.iperm[nb[ord[t]]] = (int32_t)(a + t);
         }
+        // relabel local adjacency into the RCM order for the profile
+        std::vector<int64_t> rp(ns + 1, 0);
+        std::vector<int32_t> ra(la.size());
+        for (int32_t t = 0; t < ns; ++t) rp[t + 1] = rp[t] + (lp[ord[t] + 1] - lp[ord[t]]);
+        for (int32_t t = 0; t < ns; ++t) {
+            int64_t o = rp[t];
+            for (int64_t e = lp[ord[t]]; e < lp[ord[t] + 1]; ++e) ra[o++] = inv[la[e]];
+        }
+        tile_profile(ns, rp, ra, P.ntiles[s], t_lo[s], t_hi[s], t_fwd[s], t_bwd[s], tiles_of[s]);
     });
     P.max_part = 0;
     P.min_part = INT32_MAX;
-    P.sn_off.assign(m + 1, 0);
-    P.sub_nlev.assign(m, 0);
-    P.sub_lev0.assign(m + 1, 0);
-    P.max_nlev = 0;
     for (int32_t s = 0; s < m; ++s) {
         const int32_t ns = (int32_t)(P.sub_off[s + 1] - P.sub_off[s]);
         P.max_part = std::max(P.max_part, ns);
         P.min_part = std::min(P.min_part, ns);
-        P.sn_off[s + 1] = P.sn_off[s] + (int32_t)sl[s].c0.size();
-        P.sub_nlev[s] = sl[s].nlev;
-        P.sub_lev0[s + 1] = P.sub_lev0[s] + sl[s].nlev;
-        P.max_nlev = std::max(P.max_nlev, sl[s].nlev);
+        P.trow_off[s + 1] = P.trow_off[s] + P.ntiles[s];
+        P.tile_base[s + 1] = P.tile_base[s] + tiles_of[s];
+        P.max_tiles = std::max(P.max_tiles, P.ntiles[s]);
     }
-    const int32_t nsn = P.sn_off[m];
-    P.sn_c0.resize(nsn);
-    P.sn_w.resize(nsn);
-    P.sn_nr.resize(nsn);
-    P.sn_roff.assign(nsn + 1, 0);
-    P.sn_poff.assign(nsn + 1, 0);
-    P.sn_doff.assign(nsn + 1, 0);
-    P.sn_foff.assign(nsn + 1, 0);
-    P.sn_upd_ptr.assign(nsn + 1, 0);
-    const int32_t nglev = P.sub_lev0[m];
-    std::vector<std::vector<uint32_t>> du(nglev);
-    P.lev_multi.assign(nglev, 0);
+    P.total_tiles = P.tile_base[m];
+    P.t_lo.reserve(P.trow_off[m]);
     for (int32_t s = 0; s < m; ++s) {
-        const SnLocal& L = sl[s];
-        for (size_t j = 0; j < L.c0.size(); ++j) {
-            const int32_t J = P.sn_off[s] + (int32_t)j;
-            const int32_t w = L.w[j], nr = (int32_t)L.R[j].size();
-            P.sn_c0[J] = L.c0[j];
-            P.sn_w[J] = w;
-            P.sn_nr[J] = nr;
-            P.sn_roff[J + 1] = P.sn_roff[J] + nr;
-            P.sn_poff[J + 1] = P.sn_poff[J] + (int64_t)nr * w;
-            P.sn_doff[J + 1] = P.sn_doff[J] + (int64_t)w * (w + 1) / 2;
-            P.sn_foff[J + 1] = P.sn_foff[J] + (int64_t)(w + nr) * w;
-            P.sn_upd_ptr[J + 1] = P.sn_upd_ptr[J] + (int64_t)L.upd[j].size();
-            for (int32_t r : L.R[j]) P.sn_rows.push_back((uint16_t)r);
-            for (const SnUpd& u : L.upd[j]) {
-                P.sn_upd.push_back(P.sn_off[s] + u.K);
-                P.sn_upd.push_back(u.a);
-                P.sn_upd.push_back(u.b);
-            }
-            const int32_t gl = P.sub_lev0[s] + L.lev[j];
-            for (int32_t q = 0; q * 32 < w; ++q) du[gl].push_back(((uint32_t)j << 10) | (uint32_t)q);
-            if (w > 32) P.lev_multi[gl] = 1;
-        }
-    }
-    P.panel_entries = P.sn_poff[nsn];
-    P.diag_entries = P.sn_doff[nsn];
-    P.front_entries = P.sn_foff[nsn];
-    P.lev_du.assign(nglev + 1, 0);
-    for (int32_t l = 0; l < nglev; ++l) {
-        P.lev_du[l + 1] = P.lev_du[l] + (int32_t)du[l].size();
-        P.du_list.insert(P.du_list.end(), du[l].begin(), du[l].end());
-    }
-    // forward descriptors: row r of subdomain s receives, for every K with R_K[i] = r
-    // (K ascending), L_K's panel row i (offset poff_K + i w_K) times x_K
-    if (P.panel_entries >= ((int64_t)1 << 32)) {
-        err = fmt("the local factors hold %lld panel entries (limit 2^32)", P.panel_entries);
-        return 9;
-    }
-    P.fwd_ptr.assign(n + 1, 0);
-    for (int32_t s = 0; s < m; ++s)
-        for (int32_t J = P.sn_off[s]; J < P.sn_off[s + 1]; ++J)
-            for (int64_t t = P.sn_roff[J]; t < P.sn_roff[J + 1]; ++t) P.fwd_ptr[P.sub_off[s] + P.sn_rows[t] + 1]++;
-    for (int64_t k = 0; k < n; ++k) P.fwd_ptr[k + 1] += P.fwd_ptr[k];
-    P.fwd_desc.assign(2 * (size_t)P.fwd_ptr[n], 0);
-    {
-        std::vector<int32_t> fill(P.fwd_ptr.begin(), P.fwd_ptr.end() - 1);
-        for (int32_t s = 0; s < m; ++s)
-            for (int32_t J = P.sn_off[s]; J < P.sn_off[s + 1]; ++J)
-                for (int64_t t = P.sn_roff[J]; t < P.sn_roff[J + 1]; ++t) {
-                    const int32_t f = fill[P.sub_off[s] + P.sn_rows[t]]++;
-                    P.fwd_desc[2 * (size_t)f] = (uint32_t)(P.sn_poff[J] + (t - P.sn_roff[J]) * P.sn_w[J]);
-                    P.fwd_desc[2 * (size_t)f + 1] = (uint32_t)P.sn_c0[J] | ((uint32_t)P.sn_w[J] << 16);
-                }
+        P.t_lo.insert(P.t_lo.end(), t_lo[s].begin(), t_lo[s].end());
+        P.t_hi.insert(P.t_hi.end(), t_hi[s].begin(), t_hi[s].end());
+        for (auto v : t_fwd[s]) P.t_fwd.push_back(v);
+        for (auto v : t_bwd[s]) P.t_bwd.push_back(v);
     }
     // permuted CSR: row lengths first, then the rows in parallel (each its own range)
     P.row_sub.resize(n);

@@ -1,47 +1,16 @@
 // Host-side symbolic setup of AlgMortar (Algorithm 1, everything before the numeric
 // factorisation): CSR validation, graph partition (Sec. 3.1), permutation, interface
-// edge sets E_ij (Eq. E), supernodal layout of the local factors, and the index
+// edge sets E_ij (Eq. E), tile-profile layout of the local factors, and the index
 // tables the device kernels read.  Pure C++; no CUDA types.
 #pragma once
 
-#include <algorithm>
-#include <atomic>
 #include <cstdint>
 #include <string>
-#include <thread>
 #include <vector>
 
-#include "snode_stream.h"
 #include "tile.h"
 
 namespace am {
-
-// Runs f(i, t) for every i in [0, n) on up to 16 threads (t = thread index, for per-
-// thread scratch), taking indices in chunks from a shared counter.  Every i must write
-// only its own outputs, so the result does not depend on the schedule.  If threads cannot
-// be started, the calling thread runs everything.
-template <typename F>
-void parallel_for(int64_t n, int64_t chunk, F f) {
-    const unsigned hw = std::thread::hardware_concurrency();
-    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw == 0 ? 1 : hw, 16),
-                                                             (n + chunk - 1) / std::max<int64_t>(chunk, 1)));
-    std::atomic<int64_t> next{0};
-    auto run = [&](int64_t t) {
-        for (;;) {
-            const int64_t i0 = next.fetch_add(chunk);
-            if (i0 >= n) return;
-            const int64_t i1 = std::min(n, i0 + chunk);
-            for (int64_t i = i0; i < i1; ++i) f(i, t);
-        }
-    };
-    std::vector<std::thread> pool;
-    try {
-        for (int64_t t = 1; t < T; ++t) pool.emplace_back(run, t);
-    } catch (...) {   // fewer threads: the counter hands their indices to the others
-    }
-    run(0);
-    for (auto& th : pool) th.join();
-}
 
 struct HostCsr {
     int64_t n = 0, nnz = 0;
@@ -64,22 +33,6 @@ Graph adjacency(const HostCsr& A);
 int partition_graph(const Graph& G, int32_t m, const int32_t* sizes, std::vector<int32_t>& part,
                     std::string& err);
 
-// Supernodal layout of one subdomain's factor (snode_plan.cpp): nested-dissection order,
-// supernodes J = local rows [c0[J], c0[J] + w[J]) in postorder, row structures R[J]
-// (local rows below the block, ascending), the supernodal elimination tree, levels
-// (height above the leaves) and the numeric updates J <- K (rows [a, b) of R[K] in J).
-struct SnUpd {
-    int32_t K, a, b;
-};
-struct SnLocal {
-    std::vector<int32_t> order;        // local position -> old local id
-    std::vector<int32_t> c0, w, parent, lev;
-    std::vector<std::vector<int32_t>> R;
-    std::vector<std::vector<SnUpd>> upd;
-    int32_t nlev = 0;
-};
-void sn_local_plan(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj, SnLocal& out);
-
 // Everything the device needs, built from A and a partition.
 struct Plan {
     int64_t n = 0;
@@ -98,28 +51,16 @@ struct Plan {
     std::vector<int64_t> ell_ptr;       // nslices + 1 element offsets
     std::vector<int32_t> ell_col;       // column (internal), padding -> the row itself
     std::vector<int32_t> ell_src;       // index into the ORIGINAL CSR values, or -1
-    // supernodal local factors (global supernode index J over all subdomains)
-    std::vector<int32_t> sn_off;        // m + 1: supernodes of subdomain s
-    std::vector<int32_t> sn_c0, sn_w, sn_nr;   // first local row, width, |R_J|
-    std::vector<int64_t> sn_roff;       // R_J at sn_rows[sn_roff[J] ..)
-    std::vector<uint16_t> sn_rows;      // local rows of the R_J
-    std::vector<int64_t> sn_poff;       // panel L_{R_J,J}: |R_J| w entries at sn_poff[J]
-    std::vector<int64_t> sn_doff;       // inverse diagonal block: w (w + 1) / 2 entries at sn_doff[J]
-    std::vector<int64_t> sn_foff;       // factorisation front (w + |R_J|) x w at sn_foff[J]
-    std::vector<int64_t> sn_upd_ptr;    // updates J <- K: [sn_upd_ptr[J], sn_upd_ptr[J+1])
-    std::vector<int32_t> sn_upd;        // 3 per update: K (global), a, b
-    int64_t panel_entries = 0, diag_entries = 0, front_entries = 0;
-    std::vector<int32_t> sub_nlev;      // per subdomain: levels
-    std::vector<int32_t> sub_lev0;      // per subdomain: first global level
-    std::vector<int32_t> lev_du;        // global level + 1 entries: units [lev_du[l], lev_du[l+1])
-    std::vector<uint8_t> lev_multi;     // per global level: a supernode of the level is wider than 32
-    std::vector<uint32_t> du_list;      // units: (J local << 10) | 32-row chunk
-    // forward sweep: row k (internal) receives, for every descendant K with k in R_K, the
-    // product of K's panel row for k with x_K; fwd_desc[2 t] = offset of that panel row,
-    // fwd_desc[2 t + 1] = c0_K | w_K << 16, for t in [fwd_ptr[k], fwd_ptr[k+1]), K ascending
-    std::vector<int32_t> fwd_ptr;       // n + 1
-    std::vector<uint32_t> fwd_desc;
-    int32_t max_nlev = 0;
+    // tile profile of each local factor
+    std::vector<int32_t> ntiles;        // per subdomain
+    std::vector<int64_t> trow_off;      // m + 1: tile-row descriptors of subdomain i start here
+    std::vector<int32_t> t_lo;          // per tile row (fwd): first tile column
+    std::vector<int64_t> t_fwd;         // per tile row: tile offset of (I, lo) in the fwd stream
+    std::vector<int32_t> t_hi;          // per tile row (bwd, indexed by I): last tile row below
+    std::vector<int64_t> t_bwd;         // per tile row I: tile offset of its bwd step
+    std::vector<int64_t> tile_base;     // m + 1: first tile of subdomain i (both streams)
+    int64_t total_tiles = 0;
+    int32_t max_tiles = 0;
     // interfaces (Sec. 3.1 / 5.5): one mortar unknown per pair i < j, lexicographic
     int32_t n_lambda = 0;
     int64_t n_edges = 0;
@@ -142,6 +83,13 @@ struct Plan {
     std::vector<int32_t> g_row, g_col;
     std::vector<double> g_val;
     std::vector<int32_t> g_from_r;      // G entry -> restriction entry (g_val = -4 r_coef)
+    // interface system layout: RCM order of the interface graph and its tile profile
+    std::vector<int32_t> s_perm;        // s_perm[pos] = interface id
+    std::vector<int32_t> s_iperm;       // interface id -> pos
+    int32_t s_ntiles = 0;
+    std::vector<int32_t> s_lo, s_hi;
+    std::vector<int64_t> s_fwd, s_bwd;
+    int64_t s_tiles = 0;
     int32_t max_part = 0, min_part = 0, max_k = 0;
     // one-level nested dissection of the interface system: interfaces whose two
     // subdomains lie in the same group g (a subtree of the partition's bisection tree)
@@ -161,23 +109,17 @@ struct Plan {
 int build_plan(const HostCsr& A, const std::vector<int32_t>& part, int32_t m, Plan& P,
                std::string& err);
 
-// Record streams of the batched local solves (snode_stream.h) for CTAs of nw warps and
-// factor entries of elem bytes: headers and index lists (entries zero, written on the
-// device from the numeric factor by the fill descriptors).  Warp w of subdomain s reads
-// bytes [woff[s nw + w], woff[s nw + w + 1]); every warp stream of s holds nbar[s]
-// barriers.
-struct SnStream {
-    int nw = 0, elem = 0;
-    std::vector<uint8_t> bytes;
-    std::vector<int64_t> woff;
-    std::vector<int32_t> nbar;
-    std::vector<SnFill> fill;
-    int32_t max_record = 0;             // largest record (bytes)
-};
-int build_sn_stream(const Plan& P, int nw, int elem, SnStream& out, std::string& err);
-
 // Nested-dissection layout of the interface system (fills the nd_* fields of P).
 // depth < 0 chooses it from the interface count (interior blocks of ~1000 unknowns).
 void plan_interface_nd(Plan& P, int depth);
+
+// Tile-profile descriptors for a symmetric pattern given as local adjacency lists.
+void tile_profile(int32_t n, const std::vector<int64_t>& ptr, const std::vector<int32_t>& adj,
+                  int32_t& ntiles, std::vector<int32_t>& lo, std::vector<int32_t>& hi,
+                  std::vector<int64_t>& fwd, std::vector<int64_t>& bwd, int64_t& tiles);
+
+// Reverse Cuthill-McKee order (local ids) of a graph given by local adjacency lists.
+std::vector<int32_t> rcm_order(int32_t n, const std::vector<int64_t>& ptr,
+                               const std::vector<int32_t>& adj);
 
 }  // namespace am

@@ -8,7 +8,6 @@
 #include <vector>
 
 #include "common.cuh"
-#include "snode_stream.h"
 
 namespace am {
 
@@ -36,7 +35,14 @@ struct SolveArgs {
     int64_t ldin, ldout;       // column strides of in / out (gridDim.y = columns)
     int done_stride;           // int32 stride between columns' stop flags
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
+    int deep_ring;             // ring / warp configuration of the chain solves (opts.deep_ring)
     int accumulate;            // 1: out += result instead of out = result
+    // column-block jobs (launch_tile_solve_cols): up to NW columns of one item per job,
+    // column c at job_in[job] + c * job_ld[job] (in and out), the first job_nc[job] valid,
+    // and for PCG columns the stop flag of column job_col0[job] + c
+    const int64_t* job_ld;
+    const int32_t* job_nc;
+    const int32_t* job_col0;
 };
 
 struct NdAssembleArgs {
@@ -75,68 +81,6 @@ struct NdSolveArgs {
     const double* Cinv;        // nsep x nsep symmetric inverse of the separator Schur complement
 };
 
-// Supernodal local factors (layout of snode_plan.cpp, global supernode indices).
-struct SnMeta {                // per supernode, what one solve unit reads first
-    int32_t c0, w, nr, pad;    // first local row, width, |R_J|
-    int64_t poff, doff, roff;  // panel, packed diagonal block and R_J offsets
-    int64_t pad2;
-};
-struct SnTables {
-    const int64_t* sub_off;    // m + 1: rows of subdomain s
-    const int32_t* sn_off;     // m + 1: supernodes of subdomain s
-    const SnMeta* meta;        // per supernode
-    const int32_t* c0;         // per supernode: first local row
-    const int32_t* w;          //   width
-    const int32_t* nr;         //   |R_J|
-    const int64_t* roff;       //   R_J in rows[]
-    const int64_t* poff;       //   panel offset (entries)
-    const int64_t* doff;       //   packed diagonal-block offset (entries)
-    const int64_t* foff;       //   factorisation front offset (entries)
-    const int64_t* upd_ptr;    //   updates J <- K in upd[3 * .]
-    const uint16_t* rows;      // local rows of the R_J
-    const int32_t* upd;        // (K, a, b) triples
-    const int32_t* nlev;       // per subdomain: levels
-    const int32_t* lev0;       // per subdomain: first global level
-    const int32_t* lev_du;     // per global level: units [lev_du[l], lev_du[l+1])
-    const uint8_t* lev_multi;  // per global level: some supernode wider than 32
-    const uint32_t* du;        // (J local << 10) | chunk
-    const int32_t* fwd_ptr;    // n + 1: forward panel rows of internal row k
-    const uint2* fwd_desc;     // (panel-row offset, c0_K | w_K << 16)
-};
-
-struct SnSolveArgs {
-    SnTables t;
-    const uint8_t* stream;     // record streams (snode_stream.h)
-    const int64_t* woff;       // m * NW + 1: stream of warp w of subdomain s
-    const int32_t* nbar;       // per subdomain: barriers in each of its warp streams
-    int* err;                  // set to 1 if a bulk copy never completed (bounded wait)
-    const double* scale;       // symmetric scaling per internal row (FP64 solves), or null
-    const float* scale32;      // the same in FP32 (FP32 / BF16 solves)
-    const int32_t* job_sub;    // subdomain of each job
-    const int64_t* job_in;     // offset of the job's input vector in `in`
-    const int64_t* job_out;    // offset of the job's output vector in `out`
-    const double* in;
-    double* out;
-    int64_t ldin, ldout;       // column strides (grid columns)
-    const int32_t* done;       // per-column stop flags (PCG) or null
-    int done_stride;
-    int col_fast;              // set by the launcher: grid (columns, jobs)
-    int accumulate;            // 1: out += result
-};
-
-template <typename TW>
-cudaError_t launch_sn_factor(const SnTables& t, int m, int max_part, const int32_t* order, const int32_t* rowptr,
-                             const int32_t* col, const double* val, const double* dloc, const double* sc, TW* work,
-                             TW* dwork, int* err, cudaStream_t st);
-template <typename TW, typename TS>
-cudaError_t launch_sn_fill(const SnTables& t, const SnFill* fill, int64_t nfill, const TW* work, const TW* dwork,
-                           uint8_t* stream, cudaStream_t st);
-int sn_solve_warps();
-int sn_max_record();      // largest record the solve rings accept (bytes)
-size_t sn_solve_smem(int max_part, size_t ta_bytes);
-template <typename TS, typename TA>
-cudaError_t launch_sn_solve(const SnSolveArgs& a, int njobs, int ncols, int max_part, cudaStream_t st);
-
 // interface system (kernels_coarse.cu)
 void launch_iface_tables(int L, int64_t nr, const int64_t* rp_ptr, const int32_t* rp_pos, const double* val,
                          const int64_t* r_ptr, double* rcoef, double* T, int64_t ng, const int32_t* g_from_r,
@@ -171,12 +115,25 @@ cudaError_t prepare_nd_solve(int nsep);
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                        const int32_t* row_sub, int diag_scale, int modified, double* dloc, double* sc, float* sc32,
                        cudaStream_t st);
+template <typename TW>
+void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                          const int32_t* row_sub, const int64_t* sub_off, const Profile& pf,
+                          const double* dloc, const double* sc, TW* work, int nitems, cudaStream_t st);
+template <typename TW>
+void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st);
+template <typename TW>
+void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
+                      cudaStream_t st);
 template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,
                      cudaStream_t st);
-// FP64 tile-profile chain solves (interface blocks; identity right-hand sides via job_t0).
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st, int ncols = 1);
+// Column-block jobs: each of the 4 consumer warps of a CTA solves one column of the job
+// with the same factor tile stream (each tile copied once per job, read by every warp).
+constexpr int COLS_PER_JOB = 4;
+template <typename TS, typename TA>
+cudaError_t launch_tile_solve_cols(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st);
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
                     const double* g_val, const int32_t* rows, const int64_t* phi_off, double* rhs,
                     cudaStream_t st);

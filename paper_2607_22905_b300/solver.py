@@ -28,7 +28,7 @@ class AlgMortar:
 
     def __init__(self, A, n_parts, precision="fp64", part_sizes=None, parts=None, use_graph=False,
                  check_every=1, max_it=10000, diag_scale=True, device=0, verbose=False, stream=None,
-                 nd_depth=-1, flexible=False, smooth_steps=0):
+                 nd_depth=-1, l2_prefetch=-1, deep_ring=False, flexible=False, smooth_steps=0):
         if not torch.cuda.is_available():
             raise RuntimeError("AlgMortar needs a CUDA device")
         L = B.lib()
@@ -43,6 +43,8 @@ class AlgMortar:
         o.verbose = 1 if verbose else 0
         o.device = int(device)
         o.nd_depth = int(nd_depth)
+        o.l2_prefetch = int(l2_prefetch)
+        o.deep_ring = int(deep_ring)
         o.flexible = 1 if flexible else 0
         o.smooth_steps = int(smooth_steps)
         self._sizes = None

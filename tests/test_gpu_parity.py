@@ -335,12 +335,13 @@ def test_tight_tolerance_reports_true_residual():
     assert abs(true - st["rel_residual"]) <= 1e-3 * true + 1e-16
 
 
-def test_large_subdomains_wide_supernodes():
-    """Two subdomains of ~2300 cells: their top separators are wider than 32 rows, so the
-    factorisation runs several 32-column panels per front and the solves split those
-    supernodes over several warps (three CTA barriers per level).  FP64 apply matches the
-    oracle element by element; every precision is deterministic (two applications are
-    bitwise equal); FP32 / BF16 stay close to the oracle and PCG converges."""
+def test_wide_profile_many_tiles_per_row():
+    """Two subdomains of ~2300 cells (73 tile rows, ~3 off-diagonal tiles per row): each
+    chain streams ~8 times its ring's capacity, so ring slots are reused while tiles are
+    released out of order by different warps.  FP64 apply matches the oracle; the
+    alternative ring configuration gives bit-identical results (every tile row has at most
+    two far tiles, so both configurations sum the same partials in the same order);
+    FP32 / BF16 PCG converge."""
     A, f, sizes = small3d(m=2, uneven=False)
     part = op.partition(A, sizes)
     pc = oa.setup(A, part)
@@ -348,11 +349,11 @@ def test_large_subdomains_wide_supernodes():
     z_ref = oa.apply(pc, r)
     for prec in ("fp64", "fp32", "bf16"):
         am = AlgMortar(A, len(sizes), part_sizes=sizes, precision=prec)
+        deep = AlgMortar(A, len(sizes), part_sizes=sizes, precision=prec, deep_ring=True)
         z = am.apply(r)
-        assert torch.equal(z, am.apply(r))
+        assert torch.equal(z, deep.apply(r))
         if prec == "fp64":
             assert rel(z.cpu().numpy(), z_ref) <= 1e-10
-            assert rel_sub(z.cpu().numpy(), z_ref, part) <= 1e-10
         else:
             assert rel(z.cpu().numpy(), z_ref) <= (1e-4 if prec == "fp32" else 3e-2)
         x, st = am.solve(f, tol=1e-9)
@@ -398,17 +399,17 @@ def test_smoothed_low_precision_and_multi_rhs(precision):
         assert np.linalg.norm(Bm[:, j] - A @ x.cpu().numpy()) <= 1e-9 * np.linalg.norm(Bm[:, j])
 
 
-def _local_edge_cases():
+def _pair_edge_cases():
     # checkerboard colouring: no coupling inside a subdomain, so every local block is
-    # diagonal: 800 one-column supernodes per subdomain, all on the first level
+    # diagonal (no off-diagonal tiles at all) and each chain has 25 tile rows (odd)
     A1, f1 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((40, 40, 1), 3.0, 1.0, 3)), bc_axis=0)
     ii, jj = np.meshgrid(np.arange(40), np.arange(40), indexing="ij")
     chk = ((ii + jj) % 2).ravel(order="F").astype(np.int32)
-    # parts of 20, 45, 90 and 150 cells on a 61 x 5 strip (one leaf, then 1-3 levels)
+    # parts of 1, 2, 3 and 5 tile rows (20, 45, 90, 150 cells) on a 61 x 5 strip
     A2, f2 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((61, 5, 1), 3.0, 1.0, 4)), bc_axis=0)
-    # a 1D chain of 700 cells in 2 parts: one-node separators, the deepest trees
+    # a 1D chain of 700 cells in 2 parts (bandwidth-1 factors, 11 tile rows each)
     A3, f3 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((700, 1, 1), 5.0, 1.0, 5)), bc_axis=0)
-    # a part of a single cell next to a large one
+    # a part of a single cell (one tile row holding one row) next to a large one
     A4, f4 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((12, 10, 3), 3.0, 1.0, 6)), bc_axis=0)
     lab4 = np.zeros(A4.shape[0], dtype=np.int32)
     lab4[0] = 1
@@ -417,13 +418,13 @@ def _local_edge_cases():
 
 
 @pytest.mark.parametrize("name", ["checkerboard", "tiny_parts", "chain", "one_cell_part"])
-def test_local_factor_edge_cases(name):
-    """Edge cases of the supernodal local factors: diagonal local blocks (one-column
-    supernodes only), parts of one leaf to three levels, the one-node separators of a 1D
-    chain, and a one-cell part.  FP64 apply matches the oracle; FP32/BF16 applies stay
-    close to it and are symmetric to rounding (the backward sweep reads the exact
-    transpose of what the forward sweep reads); PCG converges for all three."""
-    A, f, labels, sizes = _local_edge_cases()[name]
+def test_pair_chain_edge_profiles(name):
+    """Edge cases of the paired tile rows (FP32/BF16): chains of 1-5 tile rows (odd counts
+    end on a single row), and diagonal local blocks (no near, far or coupling tiles).
+    FP64 apply matches the oracle; FP32/BF16 applies stay close to it and are symmetric
+    to rounding (the backward stream is the exact transpose of the forward one); PCG
+    converges for all three."""
+    A, f, labels, sizes = _pair_edge_cases()[name]
     if labels is None:
         part = op.partition(A, sizes)
         m = len(sizes)
@@ -444,18 +445,15 @@ def test_local_factor_edge_cases(name):
             assert rel(z, z_ref) <= 1e-10
         else:
             # low-precision factors perturb the preconditioner by ~cond(A_i) * unit
-            # roundoff (FP32 2^-24, BF16 2^-9); the FP32 bound is that of
-            # test_pcg_low_precision_factors, and BF16 is compared only where
-            # cond(A_i) * 2^-9 leaves the comparison meaningful
-            if prec == "fp32":
-                assert rel(z, z_ref) <= 2e-3
-            elif kappa * 2.0 ** -9 <= 0.3:
-                assert rel(z, z_ref) <= 0.3
-            # symmetric up to the FP32 rounding of the solve's accumulations, measured
-            # on the Cauchy-Schwarz scale of the bilinear form
-            zs = am.apply(s2).cpu().numpy()
+            # roundoff (FP32 2^-24, BF16 2^-9): compared where that leaves the comparison
+            # meaningful (bounds of test_pcg_low_precision_factors)
+            u, bound = (2.0 ** -24, 2e-3) if prec == "fp32" else (2.0 ** -9, 1e-1)
+            if 4 * kappa * u <= bound:
+                assert rel(z, z_ref) <= bound
+            # symmetric up to the FP32 rounding of the solve's accumulations, measured on
+            # the Cauchy-Schwarz scale of the bilinear form
             a_ = float(s2 @ z)
-            b_ = float(r @ zs)
+            b_ = float(r @ am.apply(s2).cpu().numpy())
             assert abs(a_ - b_) <= 1e-6 * np.linalg.norm(s2) * np.linalg.norm(z)
         x, st = am.solve(f, tol=1e-9)
         assert st["status"] == 0
