@@ -266,12 +266,17 @@ class PCGResult:
     history: list
 
 
-def pcg_iterations(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000):
+def pcg_iterations(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000,
+                   flexible: bool = False):
     """Preconditioned CG (Hestenes-Stiefel), x0 = 0, stop when ||r_k||_2 <= tol ||b||_2
     (the Euclidean relative residual of Sec. 7), confirmed on the true residual
     b - A x; if the confirmation fails the iteration continues.  `precond(r)` returns
-    z = M^{-1} r.  A generator: it yields after every product with A (so that a caller
-    can spread one solve over several timed pieces) and returns the PCGResult.
+    z = M^{-1} r.  beta = rho_{k+1} / rho_k, or with `flexible` the Polak-Ribiere
+    (rho_{k+1} - r_{k+1} . z_k) / rho_k, equal in exact arithmetic for a linear SPD
+    preconditioner and robust to a preconditioner that varies between iterations (the
+    inexact interface solve).  A generator: it yields after every product with A (so
+    that a caller can spread one solve over several timed pieces) and returns the
+    PCGResult.
     """
     A = sp.csr_matrix(A)
     b = np.asarray(b, dtype=np.float64)
@@ -299,9 +304,10 @@ def pcg_iterations(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, ma
             true = float(np.linalg.norm(b - A @ x))
             if true <= tol * bn:
                 return PCGResult(x, it, true / bn, True, hist)
+        rz_mix = float(r @ z) if flexible else 0.0
         z = precond(r)
         rz_new = float(r @ z)
-        beta = rz_new / rz
+        beta = (rz_new - rz_mix) / rz
         rz = rz_new
         p = z + beta * p
         yield it
@@ -309,9 +315,10 @@ def pcg_iterations(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, ma
     return PCGResult(x, it, true / bn, False, hist)
 
 
-def pcg(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000) -> PCGResult:
+def pcg(A: sp.spmatrix, b: np.ndarray, precond, tol: float = 1e-8, max_it: int = 10000,
+        flexible: bool = False) -> PCGResult:
     """PCG of `pcg_iterations` run to its stop (`iterations` counts products with A)."""
-    gen = pcg_iterations(A, b, precond, tol, max_it)
+    gen = pcg_iterations(A, b, precond, tol, max_it, flexible)
     while True:
         try:
             next(gen)
