@@ -183,10 +183,11 @@ def run_ours(args):
     res = {}
     handles = {}
     t0 = time.perf_counter()
-    for prec in variants:
+    for v in variants:
+        prec, iface = parse_variant(v)
         am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
-                       check_every=args.check_every, device=local)
-        handles[prec] = am
+                       check_every=args.check_every, device=local, interface_solve=iface)
+        handles[v] = am
     host_setup_ms = {k: v.info["setup_ms"]["partition_and_tables"] for k, v in handles.items()}
 
     def step(am):
@@ -227,6 +228,9 @@ def run_ours(args):
         stages = am.time_stages(args.stage_reps)
         info = am.info
         res[prec] = {"ms": ms, "iterations": int(np.median(its)), "rel_residual": true_rel,
+                     "interface_solve": parse_variant(prec)[1],
+                     "iface_iterations_per_apply": (round(st["iface_iterations"] / (st["iterations"] + 1), 2)
+                                                    if parse_variant(prec)[1] == "inexact" else None),
                      "setup_ms": {k: round(v, 3) for k, v in info["setup_ms"].items()},
                      "stages_ms": {k: round(v, 5) for k, v in stages.items()},
                      "launches_per_step": (info1.kernel_launches - info0.kernel_launches) / args.steps,
@@ -264,7 +268,8 @@ def run_ours(args):
     # entry, nnz under a fill-reducing order) + 16 N (right-hand side in, solution out);
     # the bytes of the stored factor streams are reported beside them.
     r = res[best]
-    isz = {"fp64": 8, "fp32": 4, "bf16": 2}[best]
+    best_prec, best_iface = parse_variant(best)
+    isz = {"fp64": 8, "fp32": 4, "bf16": 2}[best_prec]
     fl = factor_floor(args.config, handles[best].partition())
     local_ms = r["stages_ms"]["local_solve"]
     stored_bytes = r["factor_bytes"] + 24 * n
@@ -285,7 +290,7 @@ def run_ours(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": f"{best}+f64",
+        "dtype": f"{best_prec}+f64" + ("+f32" if best_iface == "inexact" else ""),
         "data": "synthetic",
         "config": {"workload": wdesc, "n": n, "nnz": nnz, "n_parts": P.n_parts, "n_lambda": r["n_lambda"],
                    "tol": TOL, "variant": best, "step": "numeric setup (Algorithm 1) + PCG to tol",
@@ -312,7 +317,7 @@ def run_ours(args):
         "gpu_launches": int(r["launches_per_step"] * args.steps),
         "clocks": clocks_all.get(best),
     }
-    tr = load_traffic(best)
+    tr = load_traffic(best_prec)
     if tr is not None:
         out["roofline"]["traffic"] = tr["bytes_per_launch"]
         out["roofline"]["traffic_source"] = tr["source"]
@@ -323,6 +328,7 @@ def run_ours(args):
         out["smoothing"] = smoothing_runs(P, best, vals, b, args, local)
         out["multi_rhs"] = multi_rhs_run(best, args, local)
         out["configs"] = config_runs(args, local)
+        out["workloads"] = workload_runs(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(P, res.get("fp64", r)["iterations"])
     if rank == 0:
@@ -331,6 +337,13 @@ def run_ours(args):
         am.close()
     if dist:
         dist.destroy_process_group()
+
+
+def parse_variant(v):
+    """'bf16' -> ('bf16', 'exact'); 'bf16-inexact' -> ('bf16', 'inexact'): local-factor
+    precision and interface solve of Algorithm 2."""
+    prec, _, iface = v.partition("-")
+    return prec, (iface or "exact")
 
 
 def load_traffic(variant):
@@ -403,6 +416,50 @@ def multi_rhs_run(prec, args, local, nrhs=64, nsingle=4):
             "batched_ms_per_rhs": round(batched / nrhs, 3), "single_ms_per_rhs": round(single, 3),
             "batch_speedup": round(single / (batched / nrhs), 3),
             "iterations_min_max": [int(min(its)), int(max(its))], "single_iterations": its1}
+
+
+def workload_runs(args, local, steps=2):
+    """The extra synthetic workloads, each timed as a step of the headline (numeric setup +
+    PCG to 1e-8, mean of `steps` after one warm-up): the cross-shaped kappa = 1e6 field on
+    96^3 cells (864 even parts) in FP64 and BF16, and the K^theta contrast sweep of config
+    3's field, theta = 0.6 ... 1.4, BF16 factors."""
+    import torch
+    import synth
+    from paper_2607_22905_b300.solver import AlgMortar
+    dev = torch.device("cuda", local)
+
+    def run(P, prec):
+        b = torch.as_tensor(P.f, dtype=torch.float64, device=dev)
+        vals = torch.as_tensor(P.A.data, dtype=torch.float64, device=dev)
+        am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
+                       check_every=args.check_every, device=local)
+
+        def step():
+            am.update_values(vals)
+            return am.solve(b, tol=TOL)[1]
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            st = step()
+        e1.record()
+        torch.cuda.synchronize()
+        am.close()
+        return {"ms": round(e0.elapsed_time(e1) / steps, 3), "iterations": st["iterations"],
+                "rel_residual": st["rel_residual"]}
+
+    out = {}
+    P = synth.config_cross(96)
+    out["cross_96"] = {"workload": P.name, "n": int(P.n), "n_parts": int(P.n_parts),
+                       **{prec: run(P, prec) for prec in ("fp64", "bf16")}}
+    sweep = {}
+    for th in (0.6, 0.8, 1.0, 1.2, 1.4):
+        P = synth.config3_theta(th)
+        sweep[f"{th:g}"] = {"contrast": P.meta["contrast"], **run(P, "bf16")}
+    out["c3_theta_bf16"] = sweep
+    return out
 
 
 def config_runs(args, local, steps=2):
@@ -591,8 +648,8 @@ def run_apply(args):
     import torch
     from paper_2607_22905_b300.solver import AlgMortar
     P, wdesc = workload(args.config)
-    prec = args.variants.split(",")[0]
-    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec)
+    prec, iface = parse_variant(args.variants.split(",")[0])
+    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, interface_solve=iface)
     r = torch.as_tensor(np.random.default_rng(0).standard_normal(P.n), device="cuda")
     z = am.apply(r)
     torch.cuda.synchronize()
@@ -607,8 +664,8 @@ def run_solve(args):
     import torch
     from paper_2607_22905_b300.solver import AlgMortar
     P, wdesc = workload(args.config)
-    prec = args.variants.split(",")[0]
-    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec)
+    prec, iface = parse_variant(args.variants.split(",")[0])
+    am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, interface_solve=iface)
     x, st = am.solve(torch.as_tensor(P.f, device="cuda"), tol=TOL)
     torch.cuda.synchronize()
     print(json.dumps({"mode": "solve", "workload": wdesc, "variant": prec, "stats": st}))
@@ -622,7 +679,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c3")
-    ap.add_argument("--variants", default="fp64,fp32,bf16")
+    ap.add_argument("--variants", default="fp64,fp32,bf16,bf16-inexact")
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--stage-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")

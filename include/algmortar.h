@@ -68,6 +68,12 @@ enum {
     ALGMORTAR_BF16 = 2             /* factors stored in BF16, applied with FP32 accumulation */
 };
 
+/* Interface solve of Algorithm 2 (opts.interface_solve). */
+enum {
+    ALGMORTAR_IFACE_EXACT = 0,     /* FP64, exact                                         */
+    ALGMORTAR_IFACE_INEXACT = 1    /* block-Jacobi PCG in FP32 to opts.iface_rtol          */
+};
+
 /* Host CSR matrix, square, full symmetric pattern, columns strictly ascending within
  * each row, explicit diagonal, int32 indices (nnz < 2^31).  Read during setup only. */
 typedef struct {
@@ -94,27 +100,49 @@ typedef struct {
     int32_t nd_depth;              /* interface solve: depth of the nested-dissection split
                                       (2^depth groups from the partition's bisection tree);
                                       -1 (default) picks ~1000-unknown interior blocks    */
-    int32_t l2_prefetch;           /* accepted and ignored: L2 prefetch windows ahead of
-                                      the tile rings were measured slower at every depth
-                                      and are not part of the current solves; -1 (default)
-                                      or any value                                        */
-    int32_t deep_ring;             /* local triangular solves, shared-memory rings per CTA
-                                      (a tuning switch; every value computes the same
-                                      solve).  FP32/BF16 factors (tile rows solved in
-                                      pairs): 0 (default) far-tile ring of 4 (BF16) or 2
-                                      (FP32) groups of 4 tiles, 2 critical slots, 6
-                                      consumer warps; 1 4 consumer warps; 2 3 critical
-                                      slots; 3 one more far-ring group.  FP64 factors: 0
-                                      (default) 4 groups of one tile, 2 critical slots;
-                                      1 2 groups; 2 4 critical slots; 3 2 groups and 4
-                                      critical slots.  Other values act as 0.              */
+    int32_t autotune;              /* 1: during setup, time the launch variants of the hot
+                                      kernels (ring and warp shapes of the batched local
+                                      triangular solves, CTAs per SM of the PCG vector
+                                      kernels) on this handle's own data and keep the
+                                      fastest; results are cached per process by precision
+                                      and factor-profile shape.  0 (default): built-in
+                                      defaults.  Every variant computes the same result.  */
+    int32_t interface_solve;       /* ALGMORTAR_IFACE_EXACT (default): the interface system of
+                                      Algorithm 2 solved exactly in FP64 (one-level nested
+                                      dissection with explicit inverses); ALGMORTAR_IFACE_
+                                      INEXACT: block-Jacobi PCG on S_eta in FP32 to
+                                      iface_rtol (Sec. 7 solver settings), which makes M^{-1}
+                                      non-linear, so the outer PCG then always uses the
+                                      flexible beta                                       */
     int32_t smooth_steps;          /* nu >= 0 block-Jacobi smoothing steps before and after
                                       the AlgMortar correction (Sec. 5.4), composed
                                       multiplicatively; blocks = the subdomains, each
                                       solved with an exact factor of the unmodified
                                       A_ii in the factor precision; default 0            */
+    int32_t iface_block_parts;     /* inexact interface solve: block-Jacobi block of interface
+                                      (i, j), i < j, is i / iface_block_parts (default 1:
+                                      the interfaces each subdomain owns as the smaller
+                                      id; larger groups cut few inner iterations at config
+                                      3 -- 48 at 1, 41 at 4, 32 at 32 -- for 3.5x-25x the
+                                      block-inverse work);
+                                      every block must hold <= 128 interfaces              */
+    int32_t iface_max_it;          /* inexact interface solve: inner iteration cap (200)    */
+    int32_t stage_times;           /* 1: the PCG iteration records CUDA events between its
+                                      stages and algmortar_stats.stage_ms reports them for
+                                      the last iteration; the iterations then run stream-
+                                      ordered even with use_graph (launch gaps included);
+                                      0 (default): no events                              */
+    double iface_rtol;             /* inexact interface solve: stop when ||b - S eta||_2 <=
+                                      iface_rtol ||b||_2 (recurrence residual; 1e-2)       */
+    uint64_t seed;                 /* algmortar_setup with part_sizes == NULL: 0 (default)
+                                      even target sizes; otherwise uneven target sizes
+                                      drawn from this seed (algmortar_part_sizes)          */
 } algmortar_opts;
 
+/* Solver statistics of one right-hand side.  history / history_len are INPUTS (set them,
+ * or leave both 0): when history is a host array of history_len doubles, the solve
+ * writes ||r_k||_2 / ||b||_2 of the CG recurrence for k = 0, 1, ... into it (k = 0 is 1)
+ * and the count written into history_count. */
 typedef struct {
     int32_t status;                /* status of the solve                                 */
     int32_t iterations;            /* products with A in the CG loop                      */
@@ -122,6 +150,15 @@ typedef struct {
     double recursive_residual;     /* CG recurrence ||r_k||_2 / ||b||_2 at exit           */
     double solve_ms;               /* wall time of the solve call, device-synchronised    */
     double host_ms;                /* host-side part of the call (setup: partition etc.)  */
+    double stage_ms[6];            /* opts.stage_times = 1: device ms of the last PCG
+                                      iteration's stages -- [0] SpMV, [1] CG vector
+                                      updates, [2] local solves, [3] restriction,
+                                      [4] interface solve, [5] prolongation; else 0       */
+    int64_t iface_iterations;      /* inexact interface solve: inner iterations summed over
+                                      the solve's preconditioner applications; else 0     */
+    double* history;               /* in: host buffer or NULL                             */
+    int32_t history_len;           /* in: its length                                      */
+    int32_t history_count;         /* out: entries written                                */
 } algmortar_stats;
 
 typedef struct {
@@ -141,12 +178,31 @@ typedef struct {
                                       alone, [7] total of algmortar_setup               */
     int64_t kernel_launches;       /* kernels this library has launched in this process
                                       so far (graph replays counted per kernel)           */
+    int32_t interface_solve;       /* ALGMORTAR_IFACE_EXACT / _INEXACT                    */
+    int32_t iface_blocks;          /* inexact: block-Jacobi blocks                        */
+    int32_t iface_cluster;         /* inexact: CTAs of the inner-PCG cluster               */
+    int32_t iface_staged;          /* inexact: 1 if S_eta rows and block inverses are held
+                                      in shared memory during the inner solve             */
+    int32_t iface_last_iterations; /* inexact: inner iterations of the latest single-right-
+                                      hand-side preconditioner application (read from the
+                                      device when algmortar_get_info is called)           */
+    int32_t tuned_ring;            /* launch variant of the batched local solves in use   */
+    int32_t tuned_vec_ctas;        /* CTAs per SM of the PCG vector kernels in use        */
 } algmortar_info;
 
 typedef struct algmortar_handle algmortar_t;
 
 /* Fill *opts with the defaults listed above. */
 void algmortar_default_opts(algmortar_opts* opts);
+
+/* Host only: the uneven target sizes algmortar_setup uses when opts.part_sizes is NULL and
+ * opts.seed != 0.  With lo = 3n/(10m), hi = 3n/m (integer division) and, for j < m,
+ * a_j, b_j = SplitMix64((seed << 32) ^ 2j), SplitMix64((seed << 32) ^ (2j + 1)) mod 2^20,
+ * weight w_j = lo 2^40 + (hi - lo) a_j b_j (a right-skewed spread with mean near
+ * lo + (hi - lo) / 4); sizes_out[j] = floor(n C_j / W) - floor(n C_{j-1} / W) over the
+ * cumulative weights C_j (C_{-1} = 0, W = C_{m-1}), so the sizes sum to n.  sizes_out:
+ * host, m entries.  INVALID_ARG if m < 1, n < m, or a size would be 0. */
+int algmortar_part_sizes(int64_t n, int32_t m, uint64_t seed, int32_t* sizes_out);
 
 /* Host only (no GPU needed): the deterministic graph partition of Sec. 3.1 used by
  * algmortar_setup.  part_out (host, n entries) receives labels in [0, n_parts).

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libalgmortar.so")
 
 OK, INVALID_ARG, NOT_SYMMETRIC, INTERFACE_SIGN, NOT_SPD, NO_CONVERGENCE, BREAKDOWN, CUDA, OOM, TOO_LARGE = range(10)
 FP64, FP32, BF16 = 0, 1, 2
+IFACE_EXACT, IFACE_INEXACT = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 
 
@@ -27,23 +28,36 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("diag_scale", C.c_int32), ("max_it", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("flexible", C.c_int32),
                 ("verbose", C.c_int32), ("device", C.c_int32), ("part_sizes", C.POINTER(C.c_int32)),
-                ("stream", C.c_void_p), ("nd_depth", C.c_int32), ("l2_prefetch", C.c_int32),
-                ("deep_ring", C.c_int32), ("smooth_steps", C.c_int32)]
+                ("stream", C.c_void_p), ("nd_depth", C.c_int32), ("autotune", C.c_int32),
+                ("interface_solve", C.c_int32), ("smooth_steps", C.c_int32), ("iface_block_parts", C.c_int32),
+                ("iface_max_it", C.c_int32), ("stage_times", C.c_int32), ("iface_rtol", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+STAGE_NAMES = ("spmv", "cg_vectors", "local_solve", "restrict", "coarse", "prolong")
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
-                ("recursive_residual", C.c_double), ("solve_ms", C.c_double), ("host_ms", C.c_double)]
+                ("recursive_residual", C.c_double), ("solve_ms", C.c_double), ("host_ms", C.c_double),
+                ("stage_ms", C.c_double * 6), ("iface_iterations", C.c_int64),
+                ("history", C.POINTER(C.c_double)), ("history_len", C.c_int32), ("history_count", C.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("stage_ms", "history", "history_len")}
+        d["stage_ms"] = dict(zip(STAGE_NAMES, list(self.stage_ms)))
+        if self.history and self.history_count > 0:
+            d["history"] = [self.history[i] for i in range(self.history_count)]
+        return d
 
 
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_parts", C.c_int32), ("n_lambda", C.c_int32), ("max_part", C.c_int32),
                 ("min_part", C.c_int32), ("precision", C.c_int32), ("n_interface_edges", C.c_int64),
                 ("factor_entries", C.c_int64), ("factor_bytes", C.c_int64), ("phi_entries", C.c_int64),
-                ("setup_ms", C.c_double * 8), ("kernel_launches", C.c_int64)]
+                ("setup_ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("interface_solve", C.c_int32),
+                ("iface_blocks", C.c_int32), ("iface_cluster", C.c_int32), ("iface_staged", C.c_int32),
+                ("iface_last_iterations", C.c_int32), ("tuned_ring", C.c_int32), ("tuned_vec_ctas", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "setup_ms"}
@@ -59,6 +73,7 @@ _IP = C.POINTER(C.c_int32)
 SIGNATURES = {
     "algmortar_default_opts": (None, [C.POINTER(Opts)]),
     "algmortar_partition": (C.c_int, [C.POINTER(Csr), C.c_int32, _IP, _IP]),
+    "algmortar_part_sizes": (C.c_int, [C.c_int64, C.c_int32, C.c_uint64, _IP]),
     "algmortar_setup": (C.c_int, [C.POINTER(Csr), C.c_int32, C.POINTER(Opts), C.POINTER(_P)]),
     "algmortar_setup_with_parts": (C.c_int, [C.POINTER(Csr), _IP, C.c_int32, C.POINTER(Opts), C.POINTER(_P)]),
     "algmortar_apply": (C.c_int, [_P, _P, _P]),

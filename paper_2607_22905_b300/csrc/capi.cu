@@ -1,6 +1,8 @@
 // C ABI of libalgmortar (include/algmortar.h): handle lifetime, Algorithm 1 on the device,
 // Algorithm 2 and the PCG loop.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <type_traits>
@@ -89,7 +91,9 @@ struct NumWs {
     int32_t *d_titem = nullptr, *d_tI = nullptr, *d_tJ = nullptr;
     int64_t ntiles_items = 0, trows_items = 0;
     int max_tiles_items = 0;
-    double *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr, *gE = nullptr;
+    void *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr;   // interface arithmetic
+    double* gE = nullptr;
+    DevBlockJobs bj_gid, bj_cid;               // FP32 setup: identity columns in column blocks
     int32_t *d_gjob = nullptr, *d_gjt0 = nullptr, *d_cjt0 = nullptr;
     int64_t* d_gjin = nullptr;
     int njobs_g = 0;
@@ -102,9 +106,16 @@ struct NumWs {
     std::vector<int32_t> c_hi;
     int32_t *d_crows = nullptr, *d_cnt = nullptr, *d_clo = nullptr, *d_chi = nullptr, *d_cjob = nullptr;
     int64_t *d_czero = nullptr, *d_cfwd = nullptr, *d_cbwd = nullptr, *d_cjin = nullptr;
-    double *cwork = nullptr, *cdinv = nullptr, *cf = nullptr, *cb = nullptr, *cE = nullptr;
+    void *cwork = nullptr, *cdinv = nullptr, *cf = nullptr, *cb = nullptr;
+    double* cE = nullptr;
     int32_t* d_crowsq = nullptr;
     int64_t* d_czerooff = nullptr;
+    int64_t n_ginv = 0, n_w = 0;            // entries of the interface inverses Ginv, W
+    // inexact interface solve: per-subdomain blocks of 1/4 G^T Phi, CSR values of S_eta
+    double* pv = nullptr;
+    int64_t* d_pv_off = nullptr;
+    int64_t* d_csr_src = nullptr;
+    double* s_val64 = nullptr;
 };
 
 // PCG / apply vectors of k right-hand sides, column-major: cell vectors with leading
@@ -124,6 +135,12 @@ struct Vecs {
     int32_t* bj_col0 = nullptr;
     int bj_k = 0;                      // column count bj was built for
     int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
+    int32_t* iits = nullptr;           // inexact interface solve: per column, inner iterations
+    int64_t* iits_total = nullptr;     //   of the latest application / summed since reset
+    double* hist = nullptr;            // per column: ||r_k||^2 of iterations 0..hist_len-1
+    int hist_len = 0;
+    cudaEvent_t sev[8] = {};           // stage boundaries of one PCG iteration (stage_times)
+    bool sev_ok = false;
 };
 
 struct algmortar_handle {
@@ -166,6 +183,18 @@ struct algmortar_handle {
     int32_t* nd_grows = nullptr;       // rows of each interface group (symmetrisation)
     int32_t* d_ndpos = nullptr;        // interface id -> ND position
     int32_t* d_ifpos = nullptr;        // if_list entries as ND positions (prolongation)
+    // inexact interface solve (block-Jacobi PCG on S_eta in a thread-block cluster)
+    bool inexact = false;
+    IfaceArgs iface{};
+    int iface_cluster = 0;
+    size_t iface_smem = 0;
+    int iface_nblk = 0, iface_max_nb = 0;
+    // launch variants in use (defaults, or the autotuner's choice)
+    int tuned_ring = 0;
+    int tuned_vec_ctas = 4;
+    int tuned_order = 0;               // local-solve job order: 0 rows, 1 stored tiles, 2 tile rows
+    int32_t* d_job_sub_v[3] = {nullptr, nullptr, nullptr};
+    int64_t* d_job_off_v[3] = {nullptr, nullptr, nullptr};
     // workspace: single right-hand side (v1) and the batched solves' columns (vk)
     Vecs v1, vk;
     double* d_scalar = nullptr;
@@ -200,6 +229,9 @@ struct algmortar_handle {
     ~algmortar_handle() {
         if (v1.graph) cudaGraphExecDestroy(v1.graph);
         if (vk.graph) cudaGraphExecDestroy(vk.graph);
+        for (Vecs* v : {&v1, &vk})
+            for (cudaEvent_t e : v->sev)
+                if (e) cudaEventDestroy(e);
         for (void* p : allocs)
             if (p) cudaFree(p);
         if (own_st) cudaStreamDestroy(own_st);
@@ -263,6 +295,174 @@ int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
     return 0;
 }
 
+// Symbolic part of the inexact interface solve: the CSR pattern of S_eta (I ~ J when the
+// two interfaces share a subdomain; natural interface order, columns ascending), where
+// each off-diagonal value comes from (the per-subdomain block of the one shared
+// subdomain), the block-Jacobi blocks (I = (i, j) -> block i / g, contiguous because
+// interfaces are numbered lexicographically), and a block-aligned split of the rows over
+// the CTAs of one cluster, balanced by S_eta entries plus block-inverse entries.
+int prepare_inexact(algmortar_t* h, NumWs& W) {
+    const Plan& P = h->P;
+    const int L = h->L, m = h->m;
+    const int g = h->opts.iface_block_parts > 0 ? h->opts.iface_block_parts : 1;
+    // per-subdomain block offsets and each interface's position in its subdomains' lists
+    std::vector<int64_t> pv_off(m + 1, 0);
+    for (int sb = 0; sb < m; ++sb) {
+        const int64_t k = P.if_off[sb + 1] - P.if_off[sb];
+        pv_off[sb + 1] = pv_off[sb] + k * k;
+    }
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> rows(L);   // (J, source)
+    for (int sb = 0; sb < m; ++sb) {
+        const int64_t i0 = P.if_off[sb], k = P.if_off[sb + 1] - i0;
+        for (int64_t a = 0; a < k; ++a)
+            for (int64_t b = 0; b < k; ++b) {
+                if (a == b) continue;
+                rows[P.if_list[i0 + a]].push_back({P.if_list[i0 + b], pv_off[sb] + a * k + b});
+            }
+    }
+    std::vector<int32_t> s_ptr(L + 1, 0), s_col;
+    std::vector<int64_t> src;
+    for (int I = 0; I < L; ++I) {
+        auto& r = rows[I];
+        r.push_back({I, -1});
+        std::sort(r.begin(), r.end());
+        for (size_t t = 0; t < r.size(); ++t) {
+            if (t > 0 && r[t].first == r[t - 1].first)
+                return fail(ALGMORTAR_INVALID_ARG, "two interfaces share more than one subdomain");
+            s_col.push_back(r[t].first);
+            src.push_back(r[t].second);
+        }
+        if ((int64_t)s_col.size() > INT32_MAX) return fail(ALGMORTAR_TOO_LARGE, "interface matrix too large");
+        s_ptr[I + 1] = (int32_t)s_col.size();
+        std::vector<std::pair<int32_t, int64_t>>().swap(r);
+    }
+    // blocks
+    std::vector<int32_t> blk_row0{0}, row_blk(L);
+    for (int I = 1; I <= L; ++I)
+        if (I == L || P.pairs[2 * (size_t)I] / g != P.pairs[2 * (size_t)(I - 1)] / g) blk_row0.push_back(I);
+    const int nblk = (int)blk_row0.size() - 1;
+    std::vector<int64_t> blk_off(nblk + 1, 0);
+    int max_nb = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const int nb = blk_row0[b + 1] - blk_row0[b];
+        max_nb = std::max(max_nb, nb);
+        blk_off[b + 1] = blk_off[b] + (int64_t)nb * nb;
+        for (int I = blk_row0[b]; I < blk_row0[b + 1]; ++I) row_blk[I] = b;
+    }
+    if (L >= (1 << 24)) return fail(ALGMORTAR_TOO_LARGE, "inexact interface solve: n_lambda too large");
+    if (max_nb > IFACE_MAX_BLOCK)
+        return fail(ALGMORTAR_INVALID_ARG, "inexact interface solve: a block-Jacobi block has " +
+                                               std::to_string(max_nb) + " interfaces (at most " +
+                                               std::to_string(IFACE_MAX_BLOCK) + "); lower iface_block_parts");
+    // cluster: 16 CTAs where the device runs such clusters, else 8, never more than blocks
+    int cl = std::min(IFACE_MAX_CLUSTER, nblk);
+    std::vector<int32_t> cta_row0, cta_blk0;
+    size_t smem = 0;
+    bool stage = false;
+    int max_rows = 0;
+    int64_t max_nnz = 0, max_inv = 0;
+    auto split = [&](int c) {
+        // greedy block-aligned split: close a CTA once it reaches its share of the work
+        std::vector<int64_t> wblk(nblk);
+        int64_t tot = 0;
+        for (int b = 0; b < nblk; ++b) {
+            wblk[b] = (s_ptr[blk_row0[b + 1]] - s_ptr[blk_row0[b]]) + (blk_off[b + 1] - blk_off[b]);
+            tot += wblk[b];
+        }
+        cta_blk0.assign(1, 0);
+        int64_t acc = 0;
+        for (int b = 0; b < nblk; ++b) {
+            acc += wblk[b];
+            const int done = (int)cta_blk0.size();
+            const int left_blocks = nblk - (b + 1), left_ctas = c - done;
+            if (done < c && (acc * c >= tot * done || left_blocks <= left_ctas)) cta_blk0.push_back(b + 1);
+        }
+        while ((int)cta_blk0.size() < c + 1) cta_blk0.push_back(nblk);
+        cta_blk0.back() = nblk;
+        cta_row0.resize(c + 1);
+        max_rows = 0;
+        max_nnz = max_inv = 0;
+        for (int t = 0; t <= c; ++t) cta_row0[t] = blk_row0[cta_blk0[t]];
+        for (int t = 0; t < c; ++t) {
+            max_rows = std::max(max_rows, cta_row0[t + 1] - cta_row0[t]);
+            max_nnz = std::max<int64_t>(max_nnz, s_ptr[cta_row0[t + 1]] - s_ptr[cta_row0[t]]);
+            max_inv = std::max<int64_t>(max_inv, blk_off[cta_blk0[t + 1]] - blk_off[cta_blk0[t]]);
+        }
+    };
+    int sm_optin = 0;
+    CU(cudaDeviceGetAttribute(&sm_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    for (;;) {
+        split(cl);
+        if (max_rows >= (1 << 16))
+            return fail(ALGMORTAR_TOO_LARGE, "inexact interface solve: too many interfaces for one cluster");
+        stage = iface_smem_bytes(L, max_rows, max_nnz, max_inv, true) <= (size_t)sm_optin;
+        smem = iface_smem_bytes(L, max_rows, max_nnz, max_inv, stage);
+        if (smem > (size_t)sm_optin)
+            return fail(ALGMORTAR_TOO_LARGE, "inexact interface solve: n_lambda too large for one cluster");
+        int active = 0;
+        cudaError_t e = prepare_iface_pcg(cl, smem, &active);
+        if (e == cudaSuccess && active > 0) break;
+        cudaGetLastError();
+        if (cl <= 1) return fail(ALGMORTAR_CUDA, "inexact interface solve: no cluster shape fits the device");
+        cl = cl > 8 ? 8 : cl / 2;
+    }
+    if (h->opts.verbose)
+        std::fprintf(stderr,
+                     "[algmortar] inexact interface solve: n_lambda=%d blocks=%d (max %d) cluster=%d smem=%zu B "
+                     "staged=%d rows/CTA<=%d entries/CTA<=%lld inverse/CTA<=%lld\n",
+                     L, nblk, max_nb, cl, smem, stage ? 1 : 0, max_rows, (long long)max_nnz, (long long)max_inv);
+    std::vector<int2> row_info(L);
+    for (int c = 0; c < cl; ++c)
+        for (int I = cta_row0[c]; I < cta_row0[c + 1]; ++I) {
+            const int bk = row_blk[I], b0 = blk_row0[bk], nb = blk_row0[bk + 1] - b0;
+            row_info[I] = make_int2((b0 - cta_row0[c]) | (nb << 16),
+                                    (int)(blk_off[bk] - blk_off[cta_blk0[c]] + (int64_t)(I - b0) * nb));
+        }
+    IfaceArgs& a = h->iface;
+    a.L = L;
+    a.max_rows = max_rows;
+    a.max_nnz = max_nnz;
+    a.max_inv = max_inv;
+    a.stage = stage ? 1 : 0;
+    a.max_it = h->opts.iface_max_it > 0 ? h->opts.iface_max_it : 200;
+    a.rtol = h->opts.iface_rtol > 0 ? h->opts.iface_rtol : 1e-2;
+    int32_t *d_sptr = nullptr, *d_scol = nullptr, *d_rowblk = nullptr, *d_blk0 = nullptr, *d_crow = nullptr,
+            *d_cblk = nullptr;
+    int64_t* d_boff = nullptr;
+    TRY(upload(h, d_sptr, s_ptr));
+    TRY(upload(h, d_scol, s_col));
+    TRY(upload(h, d_rowblk, row_blk));
+    int2* d_rinfo = nullptr;
+    TRY(upload(h, d_rinfo, row_info));
+    TRY(upload(h, d_blk0, blk_row0));
+    TRY(upload(h, d_boff, blk_off));
+    TRY(upload(h, d_crow, cta_row0));
+    TRY(upload(h, d_cblk, cta_blk0));
+    TRY(upload(h, W.d_csr_src, src));
+    TRY(upload(h, W.d_pv_off, pv_off));
+    W.pv = h->alloc<double>((size_t)std::max<int64_t>(pv_off[m], 1));
+    W.s_val64 = h->alloc<double>(s_col.size());
+    float2* s_ent = h->alloc<float2>(s_col.size());
+    float* binv = h->alloc<float>((size_t)std::max<int64_t>(blk_off[nblk], 1));
+    if (!W.pv || !W.s_val64 || !s_ent || !binv) return fail(ALGMORTAR_OOM, "inexact interface buffers");
+    a.cta_row0 = d_crow;
+    a.cta_blk0 = d_cblk;
+    a.s_ptr = d_sptr;
+    a.s_col = d_scol;
+    a.s_ent = s_ent;
+    a.row_blk = d_rowblk;
+    a.row_info = d_rinfo;
+    a.blk_row0 = d_blk0;
+    a.blk_off = d_boff;
+    a.binv = binv;
+    h->iface_cluster = cl;
+    h->iface_smem = smem;
+    h->iface_nblk = nblk;
+    h->iface_max_nb = max_nb;
+    h->d_ifpos = h->d_if_list;   // interface values in natural order
+    return 0;
+}
+
 // Symbolic uploads and persistent buffers (first numeric setup only).
 template <typename TW, typename TS>
 int numeric_prepare(algmortar_t* h, NumWs& W) {
@@ -321,7 +521,12 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<PanelT<TS>>(nphi);
     if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
-    if (L > 0) {
+    if (L > 0 && h->inexact) {
+        TRY(upload(h, W.d_T, P.T));
+        W.diagc = h->alloc<double>(2 * (size_t)L);
+        if (!W.diagc) return fail(ALGMORTAR_OOM, "interface matrix");
+        TRY(prepare_inexact(h, W));
+    } else if (L > 0) {
         TRY(upload(h, W.d_T, P.T));
         W.diagc = h->alloc<double>(2 * (size_t)L);
         W.Sd = h->alloc<double>((size_t)L * L);
@@ -397,10 +602,24 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         TRY(upload(h, W.d_gjin, gjin));
         TRY(upload(h, W.d_gjt0, gjt0));
         TRY(upload(h, W.d_doff, doff));
-        W.gwork = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
-        W.gdinv = h->alloc<double>((size_t)std::max<int64_t>(trow, 1) * TILE2);
-        W.gf = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
-        W.gb = h->alloc<double>((size_t)std::max<int64_t>(tb, 1) * TILE2);
+        // the interface blocks are factored and inverted in FP64 for FP64 factors and in FP32
+        // for FP32 / BF16 factors (the FP32 pipeline reproduces eta to ~4e-6 relative at
+        // config 3, below those variants' local-solve error; B300's FP32 rate is 64x FP64)
+        const bool lowp = h->opts.precision != ALGMORTAR_FP64;
+        const size_t isz = lowp ? sizeof(float) : sizeof(double);
+        W.gwork = h->alloc<unsigned char>((size_t)std::max<int64_t>(tb, 1) * TILE2 * isz);
+        W.gdinv = h->alloc<unsigned char>((size_t)std::max<int64_t>(trow, 1) * TILE2 * isz);
+        W.gf = h->alloc<unsigned char>((size_t)std::max<int64_t>(tb, 1) * TILE2 * isz);
+        W.gb = h->alloc<unsigned char>((size_t)std::max<int64_t>(tb, 1) * TILE2 * isz);
+        if (lowp) {
+            BlockJobs bg;
+            for (int it = 0; it < (int)W.item_group.size(); ++it) {
+                const int g = W.item_group[it];
+                const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g];
+                bg.add(it, gioff[g], ng, ng, true);
+            }
+            TRY(upload_jobs(h, W.bj_gid, bg));
+        }
         W.gE = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
         W.D = h->alloc<double>((size_t)std::max<int64_t>(dof, 1));
         double* Ginv = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
@@ -408,6 +627,17 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         double* Wrm = h->alloc<double>((size_t)std::max<int64_t>(wo, 1));
         if (!W.gwork || !W.gdinv || !W.gf || !W.gb || !W.gE || !W.D || !Ginv || !Wcm || !Wrm)
             return fail(ALGMORTAR_OOM, "interface group buffers");
+        // FP32 / BF16 factor variants also apply the interface inverses in FP32 (FP32
+        // copies): half the bytes of the solve, and FP32 products
+        float *Ginv32 = nullptr, *Wcm32 = nullptr, *Wrm32 = nullptr;
+        if (lowp) {
+            Ginv32 = h->alloc<float>((size_t)std::max<int64_t>(gi, 1));
+            Wcm32 = h->alloc<float>((size_t)std::max<int64_t>(wo, 1));
+            Wrm32 = h->alloc<float>((size_t)std::max<int64_t>(wo, 1));
+            if (!Ginv32 || !Wcm32 || !Wrm32) return fail(ALGMORTAR_OOM, "interface group buffers");
+        }
+        W.n_ginv = gi;
+        W.n_w = wo;
         // blocks of groups without interior unknowns are never written: keep them zero
         CU(cudaMemsetAsync(W.D, 0, (size_t)std::max<int64_t>(dof, 1) * sizeof(double), h->st));
         // identity right-hand sides of each group (column-major n_g x n_g)
@@ -492,6 +722,9 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         a.Wcm = Wcm;
         a.Wrm = Wrm;
         a.woff = d_woff;
+        a.Ginv32 = Ginv32;
+        a.Wcm32 = Wcm32;
+        a.Wrm32 = Wrm32;
         // ---- separator Schur complement C as one dense item ----
         if (nsep > 0) {
             const int T = (nsep + TILE - 1) / TILE;
@@ -518,14 +751,24 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             TRY(upload(h, W.d_cjin, cjin));
             TRY(upload(h, W.d_cjt0, cjt0));
             const int64_t ct = (int64_t)T * (T + 1) / 2;
-            W.cwork = h->alloc<double>((size_t)ct * TILE2);
-            W.cdinv = h->alloc<double>((size_t)T * TILE2);
-            W.cf = h->alloc<double>((size_t)ct * TILE2);
-            W.cb = h->alloc<double>((size_t)ct * TILE2);
+            W.cwork = h->alloc<unsigned char>((size_t)ct * TILE2 * isz);
+            W.cdinv = h->alloc<unsigned char>((size_t)T * TILE2 * isz);
+            W.cf = h->alloc<unsigned char>((size_t)ct * TILE2 * isz);
+            W.cb = h->alloc<unsigned char>((size_t)ct * TILE2 * isz);
+            if (lowp) {
+                BlockJobs bc;
+                bc.add(0, 0, nsep, nsep, true);
+                TRY(upload_jobs(h, W.bj_cid, bc));
+            }
             W.cE = h->alloc<double>((size_t)nsep * nsep);
             double* Cinv = h->alloc<double>((size_t)nsep * nsep);
             if (!W.cwork || !W.cdinv || !W.cf || !W.cb || !W.cE || !Cinv)
                 return fail(ALGMORTAR_OOM, "separator buffers");
+            if (lowp) {
+                float* Cinv32 = h->alloc<float>((size_t)nsep * nsep);
+                if (!Cinv32) return fail(ALGMORTAR_OOM, "separator buffers");
+                a.Cinv32 = Cinv32;
+            }
             CU(cudaMemsetAsync(W.cE, 0, (size_t)nsep * nsep * sizeof(double), h->st));
             launch_eye(nsep, W.cE, h->st);
             std::vector<int32_t> sq{nsep};
@@ -537,6 +780,86 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         }
     }
     W.ready = true;
+    return 0;
+}
+
+// Interface system by one level of nested dissection, in arithmetic TI (FP64, or FP32 for
+// FP32 / BF16 factors): dense tiles of the group blocks S_gg, their right-looking tile
+// Cholesky and sweep streams, S_gg^{-1} from identity columns, W_g = S_gg^{-1} S_{g,A_g},
+// the separator Schur complement C, its factor and C^{-1}.  Inverses are stored in FP64.
+template <typename TI>
+int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
+    const Plan& P = h->P;
+    const int G = P.nd_G, nsep = P.nd_nsep, L = h->L;
+    const int64_t sep0 = P.nd_goff[G];
+    const int err_init[2] = {0, -1};
+    Profile gpf{W.d_irows, W.d_int, W.d_irow0, W.d_ibase, W.d_ilo, W.d_ihi, W.d_ifwd, W.d_ibwd};
+    launch_dense_to_tiles<TI>(W.ntiles_items, W.Sd, L, W.d_isrc, W.d_irows, W.d_ibase, W.d_titem, W.d_tI, W.d_tJ,
+                              (TI*)W.gwork, st);
+    CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+    {
+        std::vector<int32_t> Th(W.nitems);
+        for (int it = 0; it < W.nitems; ++it) Th[it] = (int32_t)W.item_hi[it].size();
+        launch_dense_cholesky<TI>(W.nitems, Th, W.d_int, W.d_ibase, W.d_irow0, (TI*)W.gwork, (TI*)W.gdinv, W.d_err,
+                                  st);
+    }
+    CU(cudaGetLastError());
+    TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
+    launch_finalize<TI, TI>(W.nitems, gpf, (const TI*)W.gwork, (const TI*)W.gdinv, (TI*)W.gf, (TI*)W.gb, st);
+    // S_gg^{-1} (identity columns), then W_g = S_gg^{-1} S_{g,A_g} from its sparse pattern
+    SolveArgs sa{};
+    sa.pf = gpf;
+    sa.fwdS = W.gf;
+    sa.bwdS = W.gb;
+    sa.err = h->d_kerr;
+    sa.in = W.gE;
+    sa.out = (double*)h->nd.Ginv;
+    if (std::is_same<TI, double>::value) {
+        // one job per column (measured faster than column blocks for FP64: the FP64 work
+        // of a job is spread over four warps and the grids are larger)
+        sa.job_sub = W.d_gjob;
+        sa.job_in = W.d_gjin;
+        sa.job_out = W.d_gjin;
+        sa.job_t0 = W.d_gjt0;   // identity columns: lower triangle of S_gg^{-1} only
+        CU((launch_tile_solve<TI, TI>(sa, W.njobs_g, W.max_tiles_items, st)));
+    } else {
+        TRY((solve_cols<TI, TI>(sa, W.bj_gid, true, W.max_tiles_items, st)));
+    }
+    launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
+    launch_nd_w_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g, W.d_wc_ptr,
+                       W.d_wc_row, h->nd.gioff, h->nd.Ginv, h->nd.woff, (double*)h->nd.Wcm, st);
+    launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
+    if (nsep > 0) {
+        launch_nd_schur_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g,
+                               W.d_wc_ptr, W.d_wc_row, h->nd.woff, h->nd.Wrm, W.d_doff, W.D, st);
+        const int64_t ct = (int64_t)W.cT * (W.cT + 1) / 2;
+        launch_nd_schur_tiles<TI>(ct, L, nsep, sep0, W.Sd, h->nd.sg, h->nd.sidx, h->nd.aoff, W.d_doff, W.D,
+                                  (TI*)W.cwork, st);
+        CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+        launch_dense_cholesky<TI>(1, std::vector<int32_t>{W.cT}, W.d_cnt, W.d_czero, W.d_czero, (TI*)W.cwork,
+                                  (TI*)W.cdinv, W.d_err, st);
+        CU(cudaGetLastError());
+        TRY(read_err_flag(h, W.d_err, "interface (separator)"));
+        Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};
+        launch_finalize<TI, TI>(1, cpf, (const TI*)W.cwork, (const TI*)W.cdinv, (TI*)W.cf, (TI*)W.cb, st);
+        SolveArgs ca{};
+        ca.pf = cpf;
+        ca.fwdS = W.cf;
+        ca.bwdS = W.cb;
+        ca.err = h->d_kerr;
+        ca.in = W.cE;
+        ca.out = (double*)h->nd.Cinv;
+        if (std::is_same<TI, double>::value) {
+            ca.job_sub = W.d_cjob;
+            ca.job_in = W.d_cjin;
+            ca.job_out = W.d_cjin;
+            ca.job_t0 = W.d_cjt0;   // lower triangle of C^{-1} only
+            CU((launch_tile_solve<TI, TI>(ca, nsep, W.cT, st)));
+        } else {
+            TRY((solve_cols<TI, TI>(ca, W.bj_cid, true, W.cT, st)));
+        }
+        launch_mirror_lower(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
+    }
     return 0;
 }
 
@@ -607,7 +930,33 @@ int numeric_setup(algmortar_t* h) {
     cudaEventRecord(ev[2], st);
     // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg),
     //     solved exactly by one level of nested dissection (kernels_coarse.cu) ---
-    if (L > 0) {
+    if (L > 0 && h->inexact) {
+        // S_eta in CSR (the same values as the exact path's dense matrix) and the explicit
+        // FP64 inverses of the block-Jacobi blocks, stored in FP32
+        NdAssembleArgs ia{};
+        ia.rows = h->d_rows;
+        ia.if_off = h->d_if_off;
+        ia.if_list = h->d_if_list;
+        ia.phi_off = h->d_phi_off;
+        ia.phi = W.phi64;
+        ia.g_cptr = W.d_gcptr;
+        ia.g_row = W.d_grow;
+        ia.g_val = W.d_gval;
+        ia.pairs = W.d_pairs;
+        ia.pv = W.pv;
+        ia.pv_off = W.d_pv_off;
+        ia.diagc = W.diagc;
+        ia.L = L;
+        launch_nd_assemble(m, ia, st);
+        launch_iface_csr_values(L, h->iface.s_ptr, h->iface.s_col, W.d_csr_src, W.pv, W.d_T, W.diagc, W.s_val64,
+                                (float2*)h->iface.s_ent, st);
+        cudaEventRecord(ev[3], st);
+        CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
+        CU(launch_iface_block_inv(h->iface_nblk, h->iface_max_nb, h->iface.blk_row0, h->iface.blk_off,
+                                  h->iface.s_ptr, h->iface.s_col, W.s_val64, (float*)h->iface.binv, W.d_err, st));
+        TRY(read_err_flag(h, W.d_err, "interface (block-Jacobi block)"));
+        cudaEventRecord(ev[5], st);
+    } else if (L > 0) {
         const int G = P.nd_G, nsep = P.nd_nsep;
         const int64_t sep0 = P.nd_goff[G];
         CU(cudaMemsetAsync(W.Sd, 0, (size_t)L * L * sizeof(double), st));
@@ -628,64 +977,14 @@ int numeric_setup(algmortar_t* h) {
         launch_nd_assemble(m, ia, st);
         launch_nd_diag(L, W.d_T, W.diagc, h->d_ndpos, W.Sd, st);
         cudaEventRecord(ev[3], st);
-        // interior blocks: dense tiles, right-looking factor per group, sweep streams
-        Profile gpf{W.d_irows, W.d_int, W.d_irow0, W.d_ibase, W.d_ilo, W.d_ihi, W.d_ifwd, W.d_ibwd};
-        launch_dense_to_tiles(W.ntiles_items, W.Sd, L, W.d_isrc, W.d_irows, W.d_ibase, W.d_titem, W.d_tI, W.d_tJ,
-                              W.gwork, st);
-        CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
-        {
-            std::vector<int32_t> Th(W.nitems);
-            for (int it = 0; it < W.nitems; ++it) Th[it] = (int32_t)W.item_hi[it].size();
-            launch_dense_cholesky(W.nitems, Th, W.d_int, W.d_ibase, W.d_irow0, W.gwork, W.gdinv, W.d_err, st);
+        if (h->opts.precision == ALGMORTAR_FP64) TRY(nd_factor_inverse<double>(h, W, st));
+        else TRY(nd_factor_inverse<float>(h, W, st));
+        if (h->nd.Ginv32) {
+            launch_convert<float>(W.n_ginv, h->nd.Ginv, (float*)h->nd.Ginv32, st);
+            launch_convert<float>(W.n_w, h->nd.Wcm, (float*)h->nd.Wcm32, st);
+            launch_convert<float>(W.n_w, h->nd.Wrm, (float*)h->nd.Wrm32, st);
         }
-        CU(cudaGetLastError());
-        TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
-        launch_finalize<double, double>(W.nitems, gpf, W.gwork, W.gdinv, W.gf, W.gb, st);
-        // S_gg^{-1} (identity columns), then W_g = S_gg^{-1} S_{g,A_g} from its sparse pattern
-        SolveArgs sa{};
-        sa.pf = gpf;
-        sa.fwdS = W.gf;
-        sa.bwdS = W.gb;
-        sa.err = h->d_kerr;
-        // one job per column (measured faster than column blocks here: the FP64 work of a
-        // job is spread over four warps and the grids are larger)
-        sa.job_sub = W.d_gjob;
-        sa.job_in = W.d_gjin;
-        sa.job_out = W.d_gjin;
-        sa.job_t0 = W.d_gjt0;          // identity columns: lower triangle of S_gg^{-1} only
-        sa.in = W.gE;
-        sa.out = (double*)h->nd.Ginv;
-        CU((launch_tile_solve<double, double>(sa, W.njobs_g, W.max_tiles_items, st)));
-        launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
-        launch_nd_w_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g, W.d_wc_ptr,
-                           W.d_wc_row, h->nd.gioff, h->nd.Ginv, h->nd.woff, (double*)h->nd.Wcm, st);
-        launch_transpose_blocks(h->nd.goff, h->nd.aoff, h->nd.woff, G, h->nd.Wcm, (double*)h->nd.Wrm, st);
-        if (nsep > 0) {
-            launch_nd_schur_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g,
-                                   W.d_wc_ptr, W.d_wc_row, h->nd.woff, h->nd.Wrm, W.d_doff, W.D, st);
-            const int64_t ct = (int64_t)W.cT * (W.cT + 1) / 2;
-            launch_nd_schur_tiles(ct, L, nsep, sep0, W.Sd, h->nd.sg, h->nd.sidx, h->nd.aoff, W.d_doff, W.D, W.cwork, st);
-            CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
-            launch_dense_cholesky(1, std::vector<int32_t>{W.cT}, W.d_cnt, W.d_czero, W.d_czero, W.cwork, W.cdinv,
-                                  W.d_err, st);
-            CU(cudaGetLastError());
-            TRY(read_err_flag(h, W.d_err, "interface (separator)"));
-            Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};
-            launch_finalize<double, double>(1, cpf, W.cwork, W.cdinv, W.cf, W.cb, st);
-            SolveArgs ca{};
-            ca.pf = cpf;
-            ca.fwdS = W.cf;
-            ca.bwdS = W.cb;
-            ca.err = h->d_kerr;
-            ca.job_sub = W.d_cjob;
-            ca.job_in = W.d_cjin;
-            ca.job_out = W.d_cjin;
-            ca.job_t0 = W.d_cjt0;      // lower triangle of C^{-1} only
-            ca.in = W.cE;
-            ca.out = (double*)h->nd.Cinv;
-            CU((launch_tile_solve<double, double>(ca, nsep, W.cT, st)));
-            launch_mirror_lower(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
-        }
+        if (h->nd.Cinv32) launch_convert<float>((int64_t)nsep * nsep, h->nd.Cinv, (float*)h->nd.Cinv32, st);
         CU(cudaGetLastError());
         cudaEventRecord(ev[5], st);
     } else {
@@ -755,7 +1054,7 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     a.done = cs.done;
     a.done_stride = cs.done_stride;
     a.ldin = a.ldout = h->n;
-    a.deep_ring = h->opts.deep_ring;
+    a.deep_ring = h->tuned_ring;
     a.err = h->d_kerr;
     if (v.k > 1) {
         // batched columns: one job per (subdomain, block of COLS_PER_JOB columns), each
@@ -767,12 +1066,32 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     return 0;
 }
 
+// Stage boundary i of one PCG iteration (opts.stage_times): a stream-ordered event; the
+// solve does not replay the iteration graph while stage times are requested.
+int mark(algmortar_t* h, Vecs& v, int i) {
+    if (!v.sev_ok) return 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(h->st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return 0;   // graph capture: no stage events
+    CU(cudaEventRecord(v.sev[i], h->st));
+    return 0;
+}
+
 // Interface right-hand side and interface solve: b_eta from pbar, eta = S^{-1} b_eta.
 void stage_restrict(algmortar_t* h, Vecs& v, const ColStrides& cs) {
     launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, v.pbar, v.beta, h->d_ndpos, cs, v.k, h->st);
 }
-void stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
-    if (h->L > 0) launch_nd_solve(h->nd, v.beta, v.eta, v.P, cs, v.k, h->st);
+int stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
+    if (h->L <= 0) return 0;
+    if (h->inexact) {
+        IfaceArgs a = h->iface;
+        a.its = v.iits;
+        a.its_total = v.iits_total;
+        CU(launch_iface_pcg(a, h->iface_cluster, h->iface_smem, v.beta, v.eta, cs, v.k, h->st));
+    } else {
+        launch_nd_solve(h->nd, v.beta, v.eta, v.P, cs, v.k, h->st);
+    }
+    return 0;
 }
 
 // z = base + pbar + Phi eta (base may be null); inside PCG (sc given) also r . z and the
@@ -791,8 +1110,11 @@ int apply_t(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
     const int nu = h->opts.smooth_steps;
     if (nu <= 0) {
         TRY((stage_local<TS, TA>(h, v, r, cs)));
+        if (pcg) TRY(mark(h, v, 4));
         stage_restrict(h, v, cs);
-        stage_coarse(h, v, cs);
+        if (pcg) TRY(mark(h, v, 5));
+        TRY(stage_coarse(h, v, cs));
+        if (pcg) TRY(mark(h, v, 6));
         stage_prolong<PanelT<TS>>(h, v, r, z, cs, pcg ? v.sc : nullptr);
         CU(cudaGetLastError());
         return 0;
@@ -811,7 +1133,7 @@ int apply_t(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg) {
     resid();
     TRY((stage_local<TS, TA>(h, v, v.w, cs)));
     stage_restrict(h, v, cs);
-    stage_coarse(h, v, cs);
+    TRY(stage_coarse(h, v, cs));
     stage_prolong<PanelT<TS>>(h, v, nullptr, z, cs, nullptr, z);
     for (int k = 0; k < nu; ++k) {
         resid();
@@ -835,10 +1157,16 @@ int apply_internal(algmortar_t* h, Vecs& v, const double* r, double* z, bool pcg
 int pcg_iteration(algmortar_t* h, Vecs& v) {
     cudaStream_t st = h->st;
     const int64_t n = h->n;
+    set_hot_ctas_per_sm(h->tuned_vec_ctas);
+    TRY(mark(h, v, 0));
     launch_pcg_p(n, v.k, n, v.z, v.p, v.sc, st);
+    TRY(mark(h, v, 1));
     launch_pcg_spmv_ell(n, v.k, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
-    launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, st);
-    return apply_internal(h, v, v.r, v.z, true);
+    TRY(mark(h, v, 2));
+    launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, v.hist, v.hist_len, st);
+    TRY(mark(h, v, 3));
+    TRY(apply_internal(h, v, v.r, v.z, true));
+    return mark(h, v, 7);
 }
 
 int ensure_graph(algmortar_t* h, Vecs& v) {
@@ -872,7 +1200,8 @@ int ensure_graph(algmortar_t* h, Vecs& v) {
 // Workspace of a batch with room for `cap` columns (first use, or growth).
 int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     if (v.cap >= cap) return 0;
-    void* old[] = {v.x, v.r, v.z, v.p, v.q, v.pbar, v.b, v.t, v.w, v.beta, v.eta, v.P, v.sc, v.gs.part, v.gs.ticket};
+    void* old[] = {v.x,  v.r,  v.z,       v.p,         v.q,       v.pbar, v.b,    v.t,          v.w,
+                   v.beta, v.eta, v.P, v.sc, v.gs.part, v.gs.ticket, v.iits, v.iits_total, v.hist};
     for (void* p : old)
         if (p) h->release(p);
     if (v.graph) {
@@ -900,15 +1229,25 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     v.sc = h->alloc<PcgScalars>(cap);
     v.gs.part = h->alloc<double>(nb);
     v.gs.ticket = h->alloc<unsigned int>(cap);
+    v.iits = h->alloc<int32_t>(cap);
+    v.iits_total = h->alloc<int64_t>(cap);
+    // ||r_k||^2 of every iteration (k <= max_it) per column, written by the stop test
+    v.hist_len = std::max(h->opts.max_it, 1) + 1;
+    v.hist = h->alloc<double>((size_t)v.hist_len * cap);
     if (!v.x || !v.r || !v.z || !v.p || !v.q || !v.pbar || !v.b || !v.t || (h->opts.smooth_steps > 0 && !v.w) ||
-        !v.beta || !v.eta || !v.P || !v.sc ||
-        !v.gs.part || !v.gs.ticket) {
+        !v.beta || !v.eta || !v.P || !v.sc || !v.gs.part || !v.gs.ticket || !v.iits || !v.iits_total || !v.hist) {
         v.cap = 0;
         return fail(ALGMORTAR_OOM, "vector workspace");
     }
     CU(cudaMemsetAsync(v.p, 0, n * sizeof(double), h->st));
     CU(cudaMemsetAsync(v.sc, 0, cap * sizeof(PcgScalars), h->st));
     CU(cudaMemsetAsync(v.gs.ticket, 0, cap * sizeof(unsigned int), h->st));
+    CU(cudaMemsetAsync(v.iits, 0, cap * sizeof(int32_t), h->st));
+    CU(cudaMemsetAsync(v.iits_total, 0, cap * sizeof(int64_t), h->st));
+    if (h->opts.stage_times && !v.sev_ok) {
+        for (cudaEvent_t& e : v.sev) CU(cudaEventCreate(&e));
+        v.sev_ok = true;
+    }
     v.cap = cap;
     v.k = cap;
     return 0;
@@ -949,8 +1288,14 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     const int k = v.k;
     const int64_t n = h->n;
     TRY(ensure_batch_jobs(h, v));
-    if (h->opts.use_graph) TRY(ensure_graph(h, v));
-    launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, h->opts.flexible ? 1 : 0, st);
+    // stage timing brackets the kernels with stream-ordered events: no graph replay then
+    // (event nodes inside an instantiated graph do not mark its kernels' boundaries)
+    const bool graph = h->opts.use_graph && !h->opts.stage_times;
+    if (graph) TRY(ensure_graph(h, v));
+    // the inexact interface solve makes M^{-1} non-linear: always the flexible beta then
+    const int flex = (h->opts.flexible || h->inexact) ? 1 : 0;
+    CU(cudaMemsetAsync(v.iits_total, 0, k * sizeof(int64_t), st));
+    launch_pcg_init(n, k, n, v.b, v.x, v.r, v.sc, v.gs, tol, h->opts.max_it, flex, v.hist, v.hist_len, st);
     TRY(apply_internal(h, v, v.r, v.z, true));
     std::vector<PcgScalars> hs(k);
     std::vector<int> restarts(k, 0);
@@ -960,7 +1305,7 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     static const int zero = 0;
     for (;;) {
         for (int c = 0; c < every; ++c) {
-            if (v.graph) {
+            if (graph && v.graph) {
                 CU(cudaGraphLaunch(v.graph, st));
                 add_launches(v.graph_kernels);
             } else {
@@ -995,9 +1340,32 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
         TRY(apply_internal(h, v, v.r, v.z, true));
         CU(cudaStreamSynchronize(st));
     }
+    std::vector<int64_t> iits(k, 0);
+    CU(cudaMemcpyAsync(iits.data(), v.iits_total, k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    float sms[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (v.sev_ok && h->opts.stage_times) {
+        CU(cudaStreamSynchronize(st));
+        for (int i = 0; i < 7; ++i)
+            if (cudaEventElapsedTime(&sms[i], v.sev[i], v.sev[i + 1]) != cudaSuccess) sms[i] = 0.0f;
+        cudaGetLastError();
+    }
     int worst = ALGMORTAR_OK;
     for (int j = 0; j < k; ++j) {
         const PcgScalars& s = hs[j];
+        if (stt) {
+            stt[j].iface_iterations = iits[j];
+            const double st_ms[6] = {sms[1], (double)sms[0] + sms[2], sms[3], sms[4], sms[5], sms[6]};
+            for (int i = 0; i < 6; ++i) stt[j].stage_ms[i] = v.sev_ok && h->opts.stage_times ? st_ms[i] : 0.0;
+            stt[j].history_count = 0;
+            if (stt[j].history && stt[j].history_len > 0) {
+                const int cnt = std::min(std::min(stt[j].history_len, s.iter + 1), v.hist_len);
+                std::vector<double> hb(cnt);
+                CU(cudaMemcpy(hb.data(), v.hist + (size_t)j * v.hist_len, cnt * sizeof(double),
+                              cudaMemcpyDeviceToHost));
+                for (int i = 0; i < cnt; ++i) stt[j].history[i] = s.bb > 0 ? std::sqrt(hb[i] / s.bb) : 0.0;
+                stt[j].history_count = cnt;
+            }
+        }
         int status = s.status == 0 ? (true_rel[j] <= tol || s.bb == 0 ? ALGMORTAR_OK : ALGMORTAR_NO_CONVERGENCE)
                                    : (s.status == 5 ? ALGMORTAR_NO_CONVERGENCE : ALGMORTAR_BREAKDOWN);
         if (stt) {
@@ -1016,6 +1384,197 @@ int pcg_internal(algmortar_t* h, Vecs& v, double tol, algmortar_stats* stt) {
     return worst;
 }
 
+// SplitMix64 (Steele, Lea & Flood 2014): the state advanced by the golden gamma, then the
+// published finaliser.
+uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Uneven target sizes of the partition (see algmortar_part_sizes).
+int uneven_part_sizes(int64_t n, int32_t m, uint64_t seed, int32_t* out, std::string& err) {
+    if (m < 1 || n < m) {
+        err = "part sizes: need 1 <= m <= n";
+        return ALGMORTAR_INVALID_ARG;
+    }
+    const uint64_t K = 1ull << 20;
+    const unsigned __int128 lo = (unsigned __int128)(3 * n / (10 * (int64_t)m)), hi = (unsigned __int128)(3 * n / m);
+    std::vector<unsigned __int128> C(m);
+    unsigned __int128 acc = 0;
+    for (int32_t j = 0; j < m; ++j) {
+        const uint64_t a = splitmix64((seed << 32) ^ (uint64_t)(2 * (int64_t)j)) % K;
+        const uint64_t b = splitmix64((seed << 32) ^ (uint64_t)(2 * (int64_t)j + 1)) % K;
+        acc += lo * K * K + (hi - lo) * a * b;
+        C[j] = acc;
+    }
+    if (acc == 0) {
+        err = "part sizes: zero total weight";
+        return ALGMORTAR_INVALID_ARG;
+    }
+    int64_t prev = 0;
+    for (int32_t j = 0; j < m; ++j) {
+        const int64_t cut = (int64_t)(((unsigned __int128)n * C[j]) / acc);
+        if (cut - prev <= 0) {
+            err = "part sizes: a part would be empty";
+            return ALGMORTAR_INVALID_ARG;
+        }
+        out[j] = (int32_t)(cut - prev);
+        prev = cut;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Launch variants of the hot kernels, measured on the handle's own data with CUDA events:
+// the batched local triangular solves (4 ring / warp shapes x 3 job orders) and the CTAs
+// per SM of the PCG vector kernels.  Every local-solve variant must reproduce the default
+// variant's output to rounding (else ALGMORTAR_CUDA); the choice is cached per process by
+// precision and factor-profile shape, so later setups of the same shape skip the search.
+struct TuneVal {
+    int ring, order, vec_ctas;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, TuneVal> g_tune_cache;
+
+std::vector<int64_t> tune_key(const algmortar_t* h) {
+    const Plan& P = h->P;
+    std::vector<int64_t> key{h->opts.precision, h->n, h->m, P.total_tiles, P.max_tiles, h->device};
+    // histogram of tile rows per subdomain in buckets of 4
+    std::map<int, int64_t> hist;
+    for (int s = 0; s < h->m; ++s) hist[P.ntiles[s] / 4] += 1;
+    for (auto& kv : hist) {
+        key.push_back(kv.first);
+        key.push_back(kv.second);
+    }
+    return key;
+}
+
+template <typename F>
+int time_ms(algmortar_t* h, int reps, F&& body, float* out) {
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (int i = 0; i < 2; ++i) TRY(body());
+    std::vector<float> t;
+    for (int i = 0; i < reps; ++i) {
+        CU(cudaEventRecord(e0, h->st));
+        TRY(body());
+        CU(cudaEventRecord(e1, h->st));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(t.begin(), t.end());
+    *out = t[t.size() / 2];
+    return 0;
+}
+
+int autotune(algmortar_t* h) {
+    CU(cudaSetDevice(h->device));
+    const std::vector<int64_t> key = tune_key(h);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->tuned_ring = it->second.ring;
+            h->tuned_order = it->second.order;
+            h->tuned_vec_ctas = it->second.vec_ctas;
+            h->d_job_sub = h->d_job_sub_v[h->tuned_order];
+            h->d_job_off = h->d_job_off_v[h->tuned_order];
+            return 0;
+        }
+    }
+    Vecs& v = h->v1;
+    const int64_t n = h->n;
+    const ColStrides cs = col_strides(h, v, false);
+    // a fixed, finite right-hand side (SplitMix64 values in [-1, 1))
+    std::vector<double> rhs(n);
+    for (int64_t i = 0; i < n; ++i) rhs[i] = (double)(splitmix64(0xA1u + (uint64_t)i) >> 11) * 0x1.0p-52 - 1.0;
+    CU(cudaMemcpyAsync(v.t, rhs.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    auto local = [&]() -> int {
+        switch (h->opts.precision) {
+            case ALGMORTAR_FP64: return stage_local<double, double>(h, v, v.t, cs);
+            case ALGMORTAR_FP32: return stage_local<float, float>(h, v, v.t, cs);
+            default: return stage_local<__nv_bfloat16, float>(h, v, v.t, cs);
+        }
+    };
+    std::vector<double> ref(n), out(n);
+    const double tol = h->opts.precision == ALGMORTAR_FP64 ? 1e-12 : 1e-5;
+    int best_ring = 0, best_order = 0;
+    float best = 3.4e38f;
+    for (int order = 0; order < 3; ++order)
+        for (int ring = 0; ring < 4; ++ring) {
+            h->tuned_ring = ring;
+            h->d_job_sub = h->d_job_sub_v[order];
+            h->d_job_off = h->d_job_off_v[order];
+            float ms = 0.0f;
+            TRY(time_ms(h, 7, local, &ms));
+            CU(cudaMemcpyAsync(ring == 0 && order == 0 ? ref.data() : out.data(), v.pbar, n * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->st));
+            CU(cudaStreamSynchronize(h->st));
+            if (ring || order) {
+                double dmax = 0.0, rmax = 0.0;
+                for (int64_t i = 0; i < n; ++i) {
+                    dmax = std::max(dmax, std::fabs(out[i] - ref[i]));
+                    rmax = std::max(rmax, std::fabs(ref[i]));
+                }
+                if (!(dmax <= tol * rmax))
+                    return fail(ALGMORTAR_CUDA, "autotune: launch variant " + std::to_string(ring) + "/" +
+                                                    std::to_string(order) + " disagrees with the default");
+            }
+            if (ms < best) {
+                best = ms;
+                best_ring = ring;
+                best_order = order;
+            }
+        }
+    h->tuned_ring = best_ring;
+    h->tuned_order = best_order;
+    h->d_job_sub = h->d_job_sub_v[best_order];
+    h->d_job_off = h->d_job_off_v[best_order];
+    // PCG vector kernels on finite vectors with a live scalar state
+    PcgScalars live{};
+    live.rz = live.rz_next = 1.0;
+    live.beta = 0.5;
+    live.iter = 1;
+    live.max_it = 1 << 30;
+    live.step_ok = 1;
+    for (double* dst : {v.x, v.r, v.p, v.q, v.z})
+        CU(cudaMemcpyAsync(dst, v.t, n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    int best_c = h->tuned_vec_ctas;
+    float best_v = 3.4e38f;
+    for (int c : {2, 3, 4, 6, 8}) {
+        set_hot_ctas_per_sm(c);
+        auto vec = [&]() -> int {
+            CU(cudaMemcpyAsync(v.sc, &live, sizeof(live), cudaMemcpyHostToDevice, h->st));
+            launch_pcg_p(n, 1, n, v.z, v.p, v.sc, h->st);
+            launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, h->st);
+            launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, nullptr, 0, h->st);
+            CU(cudaGetLastError());
+            return 0;
+        };
+        float ms = 0.0f;
+        TRY(time_ms(h, 7, vec, &ms));
+        if (ms < best_v) {
+            best_v = ms;
+            best_c = c;
+        }
+    }
+    h->tuned_vec_ctas = best_c;
+    set_hot_ctas_per_sm(best_c);
+    CU(cudaMemsetAsync(v.sc, 0, sizeof(PcgScalars), h->st));
+    CU(cudaMemsetAsync(v.p, 0, n * sizeof(double), h->st));
+    CU(cudaStreamSynchronize(h->st));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = TuneVal{best_ring, best_order, best_c};
+    return 0;
+}
+
 int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, const algmortar_opts* opts_in,
                algmortar_t** out) {
     if (!out) return fail(ALGMORTAR_INVALID_ARG, "out is NULL");
@@ -1029,6 +1588,11 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     if (o.max_it <= 0) o.max_it = 10000;
     if (o.smooth_steps < 0 || o.smooth_steps > 64) return fail(ALGMORTAR_INVALID_ARG, "smooth_steps out of [0, 64]");
     if (o.check_every <= 0) o.check_every = 1;
+    if (o.interface_solve != ALGMORTAR_IFACE_EXACT && o.interface_solve != ALGMORTAR_IFACE_INEXACT)
+        return fail(ALGMORTAR_INVALID_ARG, "unknown interface_solve");
+    if (o.iface_block_parts <= 0) o.iface_block_parts = 1;
+    if (o.iface_max_it <= 0) o.iface_max_it = 200;
+    if (!(o.iface_rtol > 0.0) || !(o.iface_rtol < 1.0)) o.iface_rtol = 1e-2;
     HostCsr H{A->n, A->nnz, A->rowptr, A->col, A->val};
     std::string err;
     int rc = validate_csr(H, err);
@@ -1038,13 +1602,22 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         part.assign(part_in, part_in + A->n);
     } else {
         Graph G = adjacency(H);
-        rc = partition_graph(G, n_parts, o.part_sizes, part, err);
+        std::vector<int32_t> drawn;
+        const int32_t* sizes = o.part_sizes;
+        if (!sizes && o.seed != 0) {
+            drawn.resize(n_parts > 0 ? n_parts : 1);
+            rc = uneven_part_sizes(A->n, n_parts, o.seed, drawn.data(), err);
+            if (rc) return fail(rc, err);
+            sizes = drawn.data();
+        }
+        rc = partition_graph(G, n_parts, sizes, part, err);
         if (rc) return fail(rc, err);
     }
     double t_part = now_ms();
     algmortar_t* h = new (std::nothrow) algmortar_handle();
     if (!h) return fail(ALGMORTAR_OOM, "host allocation");
     h->opts = o;
+    h->inexact = o.interface_solve == ALGMORTAR_IFACE_INEXACT;
     rc = build_plan(H, part, n_parts, h->P, err);
     if (rc) {
         delete h;
@@ -1077,12 +1650,22 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     h->L = P.n_lambda;
     std::vector<int32_t> rows(h->m);
     for (int s = 0; s < h->m; ++s) rows[s] = (int32_t)(P.sub_off[s + 1] - P.sub_off[s]);
-    // apply jobs: largest subdomains first
-    std::vector<int32_t> order(h->m);
-    for (int s = 0; s < h->m; ++s) order[s] = s;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a] > rows[b]; });
-    std::vector<int64_t> joff(h->m);
-    for (int t = 0; t < h->m; ++t) joff[t] = P.sub_off[order[t]];
+    // apply jobs, longest first by one of three cost proxies (the autotuner picks one):
+    // 0 rows, 1 stored tiles (bytes streamed), 2 tile rows (length of the dependent chain)
+    std::vector<int32_t> orders[3];
+    std::vector<int64_t> joffs[3];
+    for (int v = 0; v < 3; ++v) {
+        std::vector<int64_t> cost(h->m);
+        for (int s = 0; s < h->m; ++s)
+            cost[s] = v == 0 ? rows[s] : (v == 1 ? P.tile_base[s + 1] - P.tile_base[s] : (int64_t)P.ntiles[s]);
+        orders[v].resize(h->m);
+        for (int s = 0; s < h->m; ++s) orders[v][s] = s;
+        std::stable_sort(orders[v].begin(), orders[v].end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        joffs[v].resize(h->m);
+        for (int t = 0; t < h->m; ++t) joffs[v][t] = P.sub_off[orders[v][t]];
+    }
+    const std::vector<int32_t>& order = orders[0];
+    const std::vector<int64_t>& joff = joffs[0];
     int32_t *d_lo = nullptr, *d_hi = nullptr;
     int64_t *d_row0 = nullptr, *d_base = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
     rc = 0;
@@ -1111,8 +1694,12 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     rc = rc ? rc : upload(h, d_hi, P.t_hi);
     rc = rc ? rc : upload(h, d_fwd, P.t_fwd);
     rc = rc ? rc : upload(h, d_bwd, P.t_bwd);
-    rc = rc ? rc : upload(h, h->d_job_sub, order);
-    rc = rc ? rc : upload(h, h->d_job_off, joff);
+    for (int v = 0; v < 3; ++v) {
+        rc = rc ? rc : upload(h, h->d_job_sub_v[v], orders[v]);
+        rc = rc ? rc : upload(h, h->d_job_off_v[v], joffs[v]);
+    }
+    h->d_job_sub = h->d_job_sub_v[0];
+    h->d_job_off = h->d_job_off_v[0];
     rc = rc ? rc : upload(h, h->d_rptr, P.r_ptr);
     rc = rc ? rc : upload(h, h->d_rcell, P.r_cell);
     rc = rc ? rc : upload(h, h->d_rcoef, P.r_coef);
@@ -1160,6 +1747,10 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     rc = numeric_dispatch(h);
     if (rc) return bail(rc);
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return bail(fail(ALGMORTAR_CUDA, "setup synchronize"));
+    if (o.autotune) {
+        rc = autotune(h);
+        if (rc) return bail(rc);
+    }
     double t_end = now_ms();
     algmortar_info& I = h->info;
     I.n = n;
@@ -1176,6 +1767,12 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     I.setup_ms[0] = (t_part - t0) + (t_plan - t_part);
     I.setup_ms[1] = t_up - t_plan;
     I.setup_ms[7] = t_end - t0;
+    I.interface_solve = o.interface_solve;
+    I.iface_blocks = h->inexact ? h->iface_nblk : 0;
+    I.iface_cluster = h->inexact ? h->iface_cluster : 0;
+    I.iface_staged = h->inexact ? h->iface.stage : 0;
+    I.tuned_ring = h->tuned_ring;
+    I.tuned_vec_ctas = h->tuned_vec_ctas;
     if (o.verbose)
         std::fprintf(stderr,
                      "[algmortar] n=%lld m=%d nLam=%d parts %d..%d tiles=%lld | partition %.1f ms plan %.1f ms "
@@ -1205,9 +1802,21 @@ void algmortar_default_opts(algmortar_opts* o) {
     o->part_sizes = nullptr;
     o->stream = nullptr;
     o->nd_depth = -1;
-    o->l2_prefetch = -1;
-    o->deep_ring = 0;
+    o->autotune = 0;
+    o->interface_solve = ALGMORTAR_IFACE_EXACT;
     o->smooth_steps = 0;
+    o->iface_block_parts = 1;
+    o->iface_max_it = 200;
+    o->stage_times = 0;
+    o->iface_rtol = 1e-2;
+    o->seed = 0;
+}
+
+int algmortar_part_sizes(int64_t n, int32_t m, uint64_t seed, int32_t* sizes_out) {
+    if (!sizes_out) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    std::string err;
+    int rc = uneven_part_sizes(n, m, seed, sizes_out, err);
+    return rc ? fail(rc, err) : 0;
 }
 
 int algmortar_partition(const algmortar_csr* A, int32_t n_parts, const int32_t* part_sizes, int32_t* part_out) {
@@ -1254,7 +1863,10 @@ int algmortar_apply_stages(algmortar_t* h, const double* r_dev, double* pbar_dev
     launch_gather(h->n, h->d_perm, r_dev, v.t, h->st);
     TRY(apply_internal(h, v, v.t, v.z, false));
     CU(cudaMemcpyAsync(pbar_dev, v.pbar, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    if (h->L > 0) {
+    if (h->L > 0 && h->inexact) {   // natural interface order inside the handle
+        CU(cudaMemcpyAsync(beta_dev, v.beta, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        CU(cudaMemcpyAsync(eta_dev, v.eta, h->L * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else if (h->L > 0) {
         // ND order inside the handle -> natural interface order
         launch_gather(h->L, h->d_ndpos, v.beta, beta_dev, h->st);
         launch_gather(h->L, h->d_ndpos, v.eta, eta_dev, h->st);
@@ -1357,6 +1969,9 @@ int algmortar_tpfa_grad_lnK(algmortar_t* h, const double* K_dev, const double* t
 int algmortar_interface_solve_noalloc(const algmortar_t* h, const double* b_dev, double* eta_dev) {
     if (!h) return fail(ALGMORTAR_INVALID_ARG, "null handle");
     if (h->L > 0 && (!b_dev || !eta_dev)) return fail(ALGMORTAR_INVALID_ARG, "null argument");
+    if (h->inexact)
+        return fail(ALGMORTAR_INVALID_ARG, "the allocation-free interface solve is the exact one; this handle was set "
+                                           "up with the inexact interface solve");
     std::string err;
     int rc = am::interface_solve_noalloc(h->device, h->st, h->L, h->nd, h->d_ndpos, b_dev, eta_dev, err);
     if (rc) return fail(rc, err);
@@ -1384,6 +1999,7 @@ int algmortar_get_interfaces(const algmortar_t* h, int32_t* pairs_out) {
 int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     if (!h || !ms_out || reps <= 0) return fail(ALGMORTAR_INVALID_ARG, "bad argument");
     CU(cudaSetDevice(h->device));
+    set_hot_ctas_per_sm(h->tuned_vec_ctas);
     cudaStream_t st = h->st;
     Vecs& v = h->v1;
     const int64_t n = h->n;
@@ -1409,7 +2025,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
         launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
         cudaEventRecord(ev[1], st);
         launch_pcg_p(n, 1, n, v.z, v.p, v.sc, st);
-        launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, st);
+        launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, nullptr, 0, st);
         cudaEventRecord(ev[2], st);
         // stages of Algorithm 2 (same launches as apply_internal, timed one by one)
         switch (h->opts.precision) {
@@ -1420,7 +2036,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
         cudaEventRecord(ev[3], st);
         stage_restrict(h, v, cs);
         cudaEventRecord(ev[4], st);
-        stage_coarse(h, v, cs);
+        TRY(stage_coarse(h, v, cs));
         cudaEventRecord(ev[5], st);
         switch (h->opts.precision) {
             case ALGMORTAR_FP64: stage_prolong<double>(h, v, v.r, v.z, cs, rz); break;
@@ -1463,6 +2079,14 @@ int algmortar_get_info(const algmortar_t* h, algmortar_info* info) {
     if (!h || !info) return fail(ALGMORTAR_INVALID_ARG, "null argument");
     *info = h->info;
     info->kernel_launches = launch_count();
+    info->iface_last_iterations = 0;
+    if (h->inexact && h->v1.iits) {
+        CU(cudaSetDevice(h->device));
+        CU(cudaMemcpyAsync(&info->iface_last_iterations, h->v1.iits, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+        CU(cudaStreamSynchronize(h->st));
+    }
+    info->tuned_ring = h->tuned_ring;
+    info->tuned_vec_ctas = h->tuned_vec_ctas;
     return 0;
 }
 

@@ -35,7 +35,8 @@ struct SolveArgs {
     int64_t ldin, ldout;       // column strides of in / out (gridDim.y = columns)
     int done_stride;           // int32 stride between columns' stop flags
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
-    int deep_ring;             // ring / warp configuration of the chain solves (opts.deep_ring)
+    int deep_ring;             // launch variant (ring / warp shape) of the chain solves, 0..3
+                               // (defaults, or the autotuner's choice); all compute the solve
     int accumulate;            // 1: out += result instead of out = result
     // column-block jobs (launch_tile_solve_cols): up to NW columns of one item per job,
     // column c at job_in[job] + c * job_ld[job] (in and out), the first job_nc[job] valid,
@@ -56,10 +57,49 @@ struct NdAssembleArgs {
     const double* g_val;
     const int32_t* pairs;
     const int32_t* nd_pos;     // interface id -> ND position
-    double* Sd;                // dense ND-ordered interface matrix (row-major)
+    double* Sd;                // dense ND-ordered interface matrix (row-major), or null:
+    double* pv;                //   per-subdomain blocks pv[pv_off[s] + a k_s + b] instead
+    const int64_t* pv_off;     //   (off-diagonal entries only; the inexact solve's CSR)
     double* diagc;             // 2 * n_lambda
     int64_t L;
 };
+
+// Inexact interface solve (kernels_iface.cu): one thread-block cluster per right-hand side.
+constexpr int IFACE_BS = 512;           // threads per CTA
+constexpr int IFACE_MAX_CLUSTER = 16;   // CTAs per cluster (non-portable size on sm_10x)
+constexpr int IFACE_MAX_BLOCK = 128;    // largest block-Jacobi block (FP64 inverse in smem)
+struct IfaceArgs {
+    int L;
+    int max_rows;              // most rows of one CTA
+    int64_t max_nnz;           // most S_eta entries of one CTA's rows
+    int64_t max_inv;           // most block-inverse entries of one CTA
+    int stage;                 // 1: the CTA's rows of S_eta and inverses in shared memory
+    int max_it;                // inner iteration cap
+    double rtol;               // inner relative tolerance (Euclidean, recurrence residual)
+    const int32_t* cta_row0;   // cluster + 1 row ranges (block-aligned)
+    const int32_t* cta_blk0;   // cluster + 1 block ranges
+    const int32_t* s_ptr;      // CSR of S_eta (natural interface order)
+    const int32_t* s_col;
+    const float2* s_ent;       // its entries as (FP32 value, column bits)
+    const int32_t* row_blk;    // row -> block
+    const int2* row_info;      // per row: (block start - CTA's first row) | nb << 16, offset of
+                               // the row's inverse row from the CTA's first inverse entry
+    const int32_t* blk_row0;   // nblk + 1
+    const int64_t* blk_off;    // nblk + 1 offsets of the row-major block inverses
+    const float* binv;
+    int32_t* its;              // per column: inner iterations of the latest solve
+    int64_t* its_total;        // per column: running sum
+};
+void launch_iface_csr_values(int L, const int32_t* s_ptr, const int32_t* s_col, const int64_t* csr_src,
+                             const double* pv, const double* T, const double* diagc, double* s_val64, float2* s_ent,
+                             cudaStream_t st);
+cudaError_t launch_iface_block_inv(int nblk, int max_nb, const int32_t* blk_row0, const int64_t* blk_off,
+                                   const int32_t* s_ptr, const int32_t* s_col, const double* s_val64, float* binv,
+                                   int* err, cudaStream_t st);
+size_t iface_smem_bytes(int L, int max_rows, int64_t max_nnz, int64_t max_inv, bool stage);
+cudaError_t prepare_iface_pcg(int cluster, size_t smem, int* active_clusters);
+cudaError_t launch_iface_pcg(const IfaceArgs& a, int cluster, size_t smem, const double* b, double* eta,
+                             ColStrides cs, int ncols, cudaStream_t st);
 
 struct NdSolveArgs {
     int G;                     // groups
@@ -79,6 +119,12 @@ struct NdSolveArgs {
     const double* Wrm;         // same, row-major
     const int64_t* woff;       // G offsets into W
     const double* Cinv;        // nsep x nsep symmetric inverse of the separator Schur complement
+    // FP32 copies of Ginv, Wcm, Wrm, Cinv (rounded once from FP64): when set, the solve
+    // multiplies in FP32 (the FP32 / BF16 factor variants)
+    const float* Ginv32 = nullptr;
+    const float* Wcm32 = nullptr;
+    const float* Wrm32 = nullptr;
+    const float* Cinv32 = nullptr;
 };
 
 // interface system (kernels_coarse.cu)
@@ -87,12 +133,16 @@ void launch_iface_tables(int L, int64_t nr, const int64_t* rp_ptr, const int32_t
                          double* gval, cudaStream_t st);
 void launch_nd_assemble(int m, const NdAssembleArgs& a, cudaStream_t st);
 void launch_nd_diag(int L, const double* T, const double* diagc, const int32_t* nd_pos, double* Sd, cudaStream_t st);
+// dense tiles of the interface blocks in the setup's arithmetic TW (FP64, or FP32 for the
+// FP32 / BF16 factor variants)
+template <typename TW>
 void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const int64_t* src_off, const int32_t* rows,
                            const int64_t* base, const int32_t* tile_item, const int32_t* tile_I,
-                           const int32_t* tile_J, double* work, cudaStream_t st);
+                           const int32_t* tile_J, TW* work, cudaStream_t st);
 // right-looking Cholesky of dense items advancing together (T_host: host copy of T)
+template <typename TW>
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
-                           const int64_t* row0, double* work, double* dinv, int* err, cudaStream_t st);
+                           const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st);
 void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
                              double* Wrm, cudaStream_t st);
@@ -104,9 +154,10 @@ void launch_nd_schur_sparse(int64_t np, int64_t L, const double* Sd, const int64
                             const int32_t* alist, int64_t sep0, const int32_t* prow_g, const int64_t* wc_ptr,
                             const int32_t* wc_row, const int64_t* woff, const double* Wrm, const int64_t* doff,
                             double* D, cudaStream_t st);
+template <typename TW>
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
                            const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
-                           double* work, cudaStream_t st);
+                           TW* work, cudaStream_t st);
 void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
                      cudaStream_t st);
 cudaError_t prepare_nd_solve(int nsep);
@@ -145,6 +196,9 @@ void launch_eye(int L, double* E, cudaStream_t st);
 constexpr int VEC_BS = 256;
 int vec_blocks(int64_t n);                    // CTAs of the grid-strided vector kernels
 void set_vec_sms(int sms);
+void set_hot_ctas_per_sm(int c);              // CTAs per SM of the per-iteration PCG kernels
+int hot_ctas_per_sm();
+int hot_blocks(int64_t work);
 void launch_gather(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t* perm, const double* src, double* dst, cudaStream_t st);
 void launch_gather_cols(int64_t n, int ncols, const int32_t* perm, const double* src, int64_t lds, double* dst,
@@ -165,7 +219,7 @@ void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const 
 void launch_pcg_rho(int64_t n, int ncols, const double* r, const double* z, PcgScalars* sc, GridSum gs,
                     ColStrides cs, cudaStream_t st);
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
-                     GridSum gs, double tol, int max_it, int flexible, cudaStream_t st);
+                     GridSum gs, double tol, int max_it, int flexible, double* hist, int hist_len, cudaStream_t st);
 void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,
                         const double* val, const double* x, const double* b, double* r, PcgScalars* sc, GridSum gs,
                         cudaStream_t st);
@@ -176,7 +230,7 @@ void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_pt
                          cudaStream_t st);
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
-                   const double* z, PcgScalars* sc, GridSum gs, cudaStream_t st);
+                   const double* z, PcgScalars* sc, GridSum gs, double* hist, int hist_len, cudaStream_t st);
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st);
 void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val, const double* K,

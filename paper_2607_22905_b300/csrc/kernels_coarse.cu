@@ -84,6 +84,10 @@ __global__ void k_nd_assemble(NdAssembleArgs a) {
             if (ai == bi) {
                 const int side = (a.pairs[2 * I] == s) ? 0 : 1;
                 a.diagc[2 * I + side] = 0.25 * cab;
+            } else if (!a.Sd) {
+                const double v = 0.125 * (cab + cba);
+                a.pv[a.pv_off[s] + (int64_t)ai * k + bi] = v;
+                a.pv[a.pv_off[s] + (int64_t)bi * k + ai] = v;
             } else {
                 const int64_t p = a.nd_pos[I], q = a.nd_pos[J];
                 const double v = 0.125 * (cab + cba);
@@ -105,21 +109,22 @@ __global__ void k_nd_diag(int L, const double* __restrict__ T, const double* __r
 // Dense lower tile storage of an n x n block (tile (I, J), J <= I, at I(I+1)/2 + J,
 // column-major inside the tile) from a row-major source with leading dimension ld;
 // padding rows get a unit diagonal.  One CTA per tile, items laid out by `base`.
+template <typename T>
 __global__ void k_dense_to_tiles(const double* __restrict__ src, int64_t ld, const int64_t* __restrict__ src_off,
                                  const int32_t* __restrict__ rows, const int64_t* __restrict__ base,
                                  const int32_t* __restrict__ tile_item, const int32_t* __restrict__ tile_I,
-                                 const int32_t* __restrict__ tile_J, double* __restrict__ work) {
+                                 const int32_t* __restrict__ tile_J, T* __restrict__ work) {
     const int64_t t = blockIdx.x;
     const int g = tile_item[t], I = tile_I[t], J = tile_J[t];
     const int n = rows[g];
     const double* S = src + src_off[g];
-    double* dst = work + (base[g] + (int64_t)I * (I + 1) / 2 + J) * TILE2;
+    T* dst = work + (base[g] + (int64_t)I * (I + 1) / 2 + J) * TILE2;
     for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
         const int r = I * TILE + (e & 31), c = J * TILE + (e >> 5);
         double v;
         if (r < n && c < n) v = S[(int64_t)r * ld + c];
         else v = (r == c) ? 1.0 : 0.0;
-        dst[e] = v;
+        dst[e] = (T)v;
     }
 }
 
@@ -224,16 +229,17 @@ __global__ void k_nd_schur_sparse(int64_t L, int64_t np, const double* __restric
 }
 
 // Lower tiles of C = S_sep,sep - sum_g D_g (symmetrised), one CTA per tile.
+template <typename T>
 __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double* __restrict__ Sd,
                                  const int32_t* __restrict__ sg, const int32_t* __restrict__ sidx,
                                  const int64_t* __restrict__ aoff, const int64_t* __restrict__ doff,
-                                 const double* __restrict__ D, double* __restrict__ work) {
+                                 const double* __restrict__ D, T* __restrict__ work) {
     const int64_t t = blockIdx.x;
     int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while ((int64_t)(I + 1) * (I + 2) / 2 <= t) ++I;
     while ((int64_t)I * (I + 1) / 2 > t) --I;
     const int J = (int)(t - (int64_t)I * (I + 1) / 2);
-    double* dst = work + t * TILE2;
+    T* dst = work + t * TILE2;
     for (int e = threadIdx.x; e < TILE2; e += blockDim.x) {
         const int s = I * TILE + (e & 31), u = J * TILE + (e >> 5);
         double v;
@@ -251,9 +257,12 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
         } else {
             v = (s == u) ? 1.0 : 0.0;
         }
-        dst[e] = v;
+        dst[e] = (T)v;
     }
 }
+
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
 // ---------------------------------------------------------------------------------
 // Right-looking Cholesky of a batch of DENSE items (the interface blocks), all items
@@ -272,31 +281,32 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
 //   inverse: with D = diag(L) and the unit lower N = D^{-1} L, L^{-1} = N^{-1} D^{-1};
 //     the columns of N^{-1} are independent, so each warp forward-substitutes its own 8
 //     columns (rows final in order, row r broadcast by shuffle) and scales them.
+template <typename TW>
 __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __restrict__ T,
                                                   const int64_t* __restrict__ base,
-                                                  const int64_t* __restrict__ row0, double* __restrict__ work,
-                                                  double* __restrict__ dinv, int k, int* __restrict__ err) {
-    __shared__ double Ls[TILE][TILE + 1];   // L (column c published at step c - 1)
-    __shared__ double rd_s[TILE];           // 1 / L[c][c]
+                                                  const int64_t* __restrict__ row0, TW* __restrict__ work,
+                                                  TW* __restrict__ dinv, int k, int* __restrict__ err) {
+    __shared__ TW Ls[TILE][TILE + 1];   // L (column c published at step c - 1)
+    __shared__ TW rd_s[TILE];           // 1 / L[c][c]
     __shared__ int bad_s;
     const int g = blockIdx.x;
     if (g >= nitems || k >= T[g]) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double* t = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
-    double a[8];   // a[j]: row `lane` of column w + 4 j
+    TW* t = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
+    TW a[8];   // a[j]: row `lane` of column w + 4 j
 #pragma unroll
     for (int j = 0; j < 8; ++j) a[j] = t[(w + 4 * j) * TILE + lane];
     if (threadIdx.x == 0) bad_s = 0;
     __syncthreads();
     // owner warp of column c = w + 4 j: scale it by 1 / sqrt(pivot) and publish it
-    auto pivot = [&](int c, double& aj) {
-        double piv = __shfl_sync(0xffffffffu, aj, c);
+    auto pivot = [&](int c, TW& aj) {
+        TW piv = __shfl_sync(0xffffffffu, aj, c);
         if (!(piv > 0.0) || !isfinite(piv)) {
             if (lane == 0) bad_s = 1;
-            piv = 1.0;
+            piv = TW(1);
         }
-        const double rs = rsqrt(piv);
-        const double lk = lane > c ? aj * rs : (lane == c ? piv * rs : 0.0);
+        const TW rs = rsq(piv);
+        const TW lk = lane > c ? aj * rs : (lane == c ? piv * rs : TW(0));
         aj = lk;
         Ls[lane][c] = lk;
         if (lane == 0) rd_s[c] = rs;
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __r
     if (w == 0) pivot(0, a[0]);
     for (int kk = 0; kk < TILE; ++kk) {
         __syncthreads();   // column kk published
-        const double lk = Ls[lane][kk];
+        const TW lk = Ls[lane][kk];
         const int nx = kk + 1;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -321,24 +331,24 @@ __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __r
         }
     }
     // every column of L is in Ls now (published before the last step's barrier)
-    double x[8];
+    TW x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = (w + 4 * j == lane) ? 1.0 : 0.0;
-    const double rdl = rd_s[lane];
+    const TW rdl = rd_s[lane];
     for (int r = 0; r < TILE; ++r) {
-        const double nr = lane > r ? Ls[lane][r] * rdl : 0.0;   // N[lane][r]
+        const TW nr = lane > r ? Ls[lane][r] * rdl : TW(0);     // N[lane][r]
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (w + 4 * j > r) continue;                         // N^{-1} is lower triangular
-            const double yrc = __shfl_sync(0xffffffffu, x[j], r);
+            const TW yrc = __shfl_sync(0xffffffffu, x[j], r);
             x[j] -= nr * yrc;
         }
     }
-    double* D = dinv + (row0[g] + k) * TILE2;
+    TW* D = dinv + (row0[g] + k) * TILE2;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = w + 4 * j;
-        t[c * TILE + lane] = c <= lane ? Ls[lane][c] : 0.0;
+        t[c * TILE + lane] = c <= lane ? Ls[lane][c] : TW(0);
         D[c * TILE + lane] = x[j] * rd_s[c];
     }
     if (threadIdx.x == 0 && bad_s) {
@@ -362,19 +372,20 @@ __device__ __forceinline__ int item_of_block(int nitems, const int32_t* T, int k
 }
 
 // L_Ik = A_Ik L_kk^{-T} for I = k+1 .. T_g-1 of every item
+template <typename TW>
 __global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __restrict__ T,
                                                  const int64_t* __restrict__ base,
-                                                 const int64_t* __restrict__ row0, double* __restrict__ work,
-                                                 const double* __restrict__ dinv, int k) {
-    __shared__ double X[TILE][TILE + 1];
-    __shared__ double Bs[TILE][TILE + 1];
+                                                 const int64_t* __restrict__ row0, TW* __restrict__ work,
+                                                 const TW* __restrict__ dinv, int k) {
+    __shared__ TW X[TILE][TILE + 1];
+    __shared__ TW Bs[TILE][TILE + 1];
     int64_t li;
     const int g = item_of_block(nitems, T, k, blockIdx.x, false, &li);
     if (g < 0) return;
     const int I = k + 1 + (int)li;
     const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
-    double* t = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
-    const double* D = dinv + (row0[g] + k) * TILE2;
+    TW* t = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
+    const TW* D = dinv + (row0[g] + k) * TILE2;
     for (int e = tid; e < TILE2; e += 256) {
         X[e & 31][e >> 5] = t[e];
         Bs[e & 31][e >> 5] = D[e];
@@ -382,7 +393,7 @@ __global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __re
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        double v = 0;
+        TW v = 0;
 #pragma unroll 8
         for (int u = 0; u < TILE; ++u) v += X[rb + q][u] * Bs[c][u];
         t[c * TILE + rb + q] = v;
@@ -390,10 +401,11 @@ __global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __re
 }
 
 // A_IJ -= L_Ik L_Jk^T for k < J <= I < T_g of every item
+template <typename TW>
 __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __restrict__ T,
-                                                   const int64_t* __restrict__ base, double* __restrict__ work, int k) {
-    __shared__ double As[TILE][TILE + 1];
-    __shared__ double Bs[TILE][TILE + 1];
+                                                   const int64_t* __restrict__ base, TW* __restrict__ work, int k) {
+    __shared__ TW As[TILE][TILE + 1];
+    __shared__ TW Bs[TILE][TILE + 1];
     int64_t p;
     const int g = item_of_block(nitems, T, k, blockIdx.x, true, &p);
     if (g < 0) return;
@@ -403,9 +415,9 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
     const int b = (int)(p - (int64_t)a * (a + 1) / 2);
     const int I = k + 1 + a, J = k + 1 + b;
     const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
-    const double* LI = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
-    const double* LJ = work + (base[g] + (int64_t)J * (J + 1) / 2 + k) * TILE2;
-    double* t = work + (base[g] + (int64_t)I * (I + 1) / 2 + J) * TILE2;
+    const TW* LI = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
+    const TW* LJ = work + (base[g] + (int64_t)J * (J + 1) / 2 + k) * TILE2;
+    TW* t = work + (base[g] + (int64_t)I * (I + 1) / 2 + J) * TILE2;
     for (int e = tid; e < TILE2; e += 256) {
         As[e & 31][e >> 5] = LI[e];
         Bs[e & 31][e >> 5] = LJ[e];
@@ -413,40 +425,55 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        double v = t[c * TILE + rb + q];
+        TW v = t[c * TILE + rb + q];
 #pragma unroll 8
         for (int u = 0; u < TILE; ++u) v -= As[rb + q][u] * Bs[c][u];
         t[c * TILE + rb + q] = v;
     }
 }
 
-// Warp dot product of a contiguous row with x (len entries), four independent FP64
-// accumulators per lane (the FP64 pipe's latency is long on B300), lanes 0..31 strided.
-__device__ __forceinline__ double warp_row_dot(const double* __restrict__ row, const double* __restrict__ x,
-                                               int64_t len, int lane) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+// Warp dot product of a contiguous row with x (len entries) in the row's arithmetic TM
+// (FP64, or FP32 for the FP32 copies), four independent accumulators per lane (the FP64
+// pipe's latency is long on B300), lanes 0..31 strided.
+template <typename TM>
+__device__ __forceinline__ TM warp_row_dot(const TM* __restrict__ row, const double* __restrict__ x, int64_t len,
+                                           int lane) {
+    TM s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     int64_t j = lane;
     for (; j + 96 < len; j += 128) {
-        s0 += row[j] * x[j];
-        s1 += row[j + 32] * x[j + 32];
-        s2 += row[j + 64] * x[j + 64];
-        s3 += row[j + 96] * x[j + 96];
+        s0 += row[j] * (TM)x[j];
+        s1 += row[j + 32] * (TM)x[j + 32];
+        s2 += row[j + 64] * (TM)x[j + 64];
+        s3 += row[j + 96] * (TM)x[j + 96];
     }
-    for (; j < len; j += 32) s0 += row[j] * x[j];
-    double s = (s0 + s1) + (s2 + s3);
+    for (; j < len; j += 32) s0 += row[j] * (TM)x[j];
+    TM s = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
+template <typename TM>
+struct NdMats {
+    const TM *Ginv, *Wcm, *Wrm, *Cinv;
+};
+__device__ __forceinline__ NdMats<double> nd_mats(const NdSolveArgs& a, double) {
+    return {a.Ginv, a.Wcm, a.Wrm, a.Cinv};
+}
+__device__ __forceinline__ NdMats<float> nd_mats(const NdSolveArgs& a, float) {
+    return {a.Ginv32, a.Wcm32, a.Wrm32, a.Cinv32};
+}
+
 // ---------------------------------------------------------------------------------
-// Per-iteration solve (ND order in and out).
+// Per-iteration solve (ND order in and out), in the arithmetic TM of the matrices used.
 // Stage 1: eta_g = Ginv_g b_g  (rows of the symmetric inverse) and P_g = W_g^T b_g.
 // ---------------------------------------------------------------------------------
+template <typename TM>
 __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
                             double* __restrict__ P, ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
+    const NdMats<TM> M = nd_mats(a, TM(0));
     b += col * cs.l;
     eta += col * cs.l;
     P += col * a.np;
@@ -456,22 +483,24 @@ __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double*
     if (wid < nin) {
         const int g = a.row_g[wid];
         const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
-        const double s = warp_row_dot(a.Ginv + a.gioff[g] + i * ng, b + g0, ng, lane);
-        if (lane == 0) eta[wid] = s;
+        const TM s = warp_row_dot<TM>(M.Ginv + a.gioff[g] + i * ng, b + g0, ng, lane);
+        if (lane == 0) eta[wid] = (double)s;
     } else if (wid < nin + a.aoff[a.G]) {
         const int64_t r = wid - nin;
         const int g = a.prow_g[r];
         const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = r - a.aoff[g];
-        const double s = warp_row_dot(a.Wcm + a.woff[g] + j * ng, b + g0, ng, lane);
-        if (lane == 0) P[r] = s;
+        const TM s = warp_row_dot<TM>(M.Wcm + a.woff[g] + j * ng, b + g0, ng, lane);
+        if (lane == 0) P[r] = (double)s;
     }
 }
 
 // Stage 2: c = b_sep - sum_g P_g (built in shared memory by every CTA), eta_sep = Cinv c.
+template <typename TM>
 __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
                             const double* __restrict__ P, ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
+    const NdMats<TM> M = nd_mats(a, TM(0));
     b += col * cs.l;
     eta += col * cs.l;
     P += col * a.np;
@@ -486,14 +515,16 @@ __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double*
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (wid >= nsep) return;
-    const double s = warp_row_dot(a.Cinv + wid * nsep, cvec, nsep, lane);
-    if (lane == 0) eta[sep0 + wid] = s;
+    const TM s = warp_row_dot<TM>(M.Cinv + wid * nsep, cvec, nsep, lane);
+    if (lane == 0) eta[sep0 + wid] = (double)s;
 }
 
 // Stage 3: eta_g -= W_g eta_{A_g}.
+template <typename TM>
 __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
+    const NdMats<TM> M = nd_mats(a, TM(0));
     eta += col * cs.l;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -501,20 +532,20 @@ __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides 
     if (wid >= nin) return;
     const int g = a.row_g[wid];
     const int64_t g0 = a.goff[g], ag = a.aoff[g + 1] - a.aoff[g], i = wid - g0;
-    const double* row = a.Wrm + a.woff[g] + i * ag;
+    const TM* row = M.Wrm + a.woff[g] + i * ag;
     const int32_t* al = a.alist + a.aoff[g];
     const double* es = eta + nin;
-    double s0 = 0.0, s1 = 0.0;
+    TM s0 = 0, s1 = 0;
     int64_t j = lane;
     for (; j + 32 < ag; j += 64) {
-        s0 += row[j] * es[al[j]];
-        s1 += row[j + 32] * es[al[j + 32]];
+        s0 += row[j] * (TM)es[al[j]];
+        s1 += row[j + 32] * (TM)es[al[j + 32]];
     }
-    for (; j < ag; j += 32) s0 += row[j] * es[al[j]];
-    double s = s0 + s1;
+    for (; j < ag; j += 32) s0 += row[j] * (TM)es[al[j]];
+    TM s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) eta[wid] -= s;
+    if (lane == 0) eta[wid] -= (double)s;
 }
 
 // ------------------------------------------------------------------------ launchers
@@ -543,17 +574,19 @@ void launch_nd_diag(int L, const double* T, const double* diagc, const int32_t* 
         k_nd_diag<<<(L + 127) / 128, 128, 0, st>>>(L, T, diagc, nd_pos, Sd);
     }
 }
+template <typename TW>
 void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const int64_t* src_off, const int32_t* rows,
                            const int64_t* base, const int32_t* tile_item, const int32_t* tile_I,
-                           const int32_t* tile_J, double* work, cudaStream_t st) {
+                           const int32_t* tile_J, TW* work, cudaStream_t st) {
     if (ntiles > 0) {
         count_launch();
-        k_dense_to_tiles<<<(unsigned)ntiles, 256, 0, st>>>(src, ld, src_off, rows, base, tile_item, tile_I, tile_J,
-                                                           work);
+        k_dense_to_tiles<TW><<<(unsigned)ntiles, 256, 0, st>>>(src, ld, src_off, rows, base, tile_item, tile_I, tile_J,
+                                                               work);
     }
 }
+template <typename TW>
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
-                           const int64_t* row0, double* work, double* dinv, int* err, cudaStream_t st) {
+                           const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st) {
     int maxT = 0;
     for (int t : T_host) maxT = std::max(maxT, t);
     for (int k = 0; k < maxT; ++k) {
@@ -566,12 +599,12 @@ void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const
             }
         }
         count_launch();
-        k_dpotrf_b<<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, k, err);
+        k_dpotrf_b<TW><<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, k, err);
         if (nt > 0) {
             count_launch();
-            k_dtrsm_b<<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, k);
+            k_dtrsm_b<TW><<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, k);
             count_launch();
-            k_dupdate_b<<<(unsigned)np, 256, 0, st>>>(nitems, T, base, work, k);
+            k_dupdate_b<TW><<<(unsigned)np, 256, 0, st>>>(nitems, T, base, work, k);
         }
     }
 }
@@ -608,34 +641,57 @@ void launch_nd_schur_sparse(int64_t np, int64_t L, const double* Sd, const int64
                                                                     wc_row, woff, Wrm, doff, D);
     }
 }
+template <typename TW>
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
                            const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
-                           double* work, cudaStream_t st) {
+                           TW* work, cudaStream_t st) {
     if (ntiles > 0) {
         count_launch();
-        k_nd_schur_tiles<<<(unsigned)ntiles, 256, 0, st>>>(L, nsep, sep0, Sd, sg, sidx, aoff, doff, D, work);
+        k_nd_schur_tiles<TW><<<(unsigned)ntiles, 256, 0, st>>>(L, nsep, sep0, Sd, sg, sidx, aoff, doff, D, work);
+    }
+}
+template <typename TM>
+static void nd_solve_t(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
+                       cudaStream_t st) {
+    const int64_t nin = a.nin, np = a.np;
+    if (nin + np > 0) {
+        count_launch();
+        k_nd_stage1<TM><<<dim3((unsigned)((nin + np + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
+    }
+    if (a.nsep > 0) {
+        count_launch();
+        k_nd_stage2<TM><<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, (size_t)a.nsep * sizeof(double), st>>>(
+            a, b, eta, P, cs);
+        count_launch();
+        k_nd_stage3<TM><<<dim3((unsigned)((nin + 7) / 8), ncols), 256, 0, st>>>(a, eta, cs);
     }
 }
 void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
                      cudaStream_t st) {
-    const int64_t nin = a.nin, np = a.np;
-    if (nin + np > 0) {
-        count_launch();
-        k_nd_stage1<<<dim3((unsigned)((nin + np + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
-    }
-    if (a.nsep > 0) {
-        count_launch();
-        k_nd_stage2<<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, (size_t)a.nsep * sizeof(double), st>>>(
-            a, b, eta, P, cs);
-        count_launch();
-        k_nd_stage3<<<dim3((unsigned)((nin + 7) / 8), ncols), 256, 0, st>>>(a, eta, cs);
-    }
+    if (a.Ginv32 || a.Cinv32) nd_solve_t<float>(a, b, eta, P, cs, ncols, st);
+    else nd_solve_t<double>(a, b, eta, P, cs, ncols, st);
 }
 cudaError_t prepare_nd_solve(int nsep) {
     size_t smem = (size_t)nsep * sizeof(double);
-    if (smem > 48 * 1024)
-        return cudaFuncSetAttribute(k_nd_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_nd_stage2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_nd_stage2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
     return cudaSuccess;
 }
+
+#define INST_ND(TW)                                                                                           \
+    template void launch_dense_to_tiles<TW>(int64_t, const double*, int64_t, const int64_t*, const int32_t*,       \
+                                            const int64_t*, const int32_t*, const int32_t*, const int32_t*, TW*,     \
+                                            cudaStream_t);                                                           \
+    template void launch_dense_cholesky<TW>(int, const std::vector<int32_t>&, const int32_t*, const int64_t*,      \
+                                            const int64_t*, TW*, TW*, int*, cudaStream_t);                           \
+    template void launch_nd_schur_tiles<TW>(int64_t, int64_t, int, int64_t, const double*, const int32_t*,         \
+                                            const int32_t*, const int64_t*, const int64_t*, const double*, TW*,      \
+                                            cudaStream_t);
+INST_ND(double)
+INST_ND(float)
 
 }  // namespace am

@@ -8,6 +8,8 @@
 // order (GridSum) and stores the scalar straight into the device-side PCG state, so
 // repeated runs give bit-identical iterates and no partial arrays cross kernels.
 #include <atomic>
+#include <cstdint>
+#include <initializer_list>
 #include <type_traits>
 
 #include "common.cuh"
@@ -23,10 +25,26 @@ int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 // CTAs of the grid-strided vector kernels over n rows (= size of their GridSum partials):
 // at most 8 resident CTAs of 256 threads on each of the device's SMs
 static int g_max_vec_blocks = 8 * 148;
-void set_vec_sms(int sms) { g_max_vec_blocks = 8 * (sms > 0 ? sms : 148); }
+static int g_sms = 148;
+void set_vec_sms(int sms) {
+    g_sms = sms > 0 ? sms : 148;
+    g_max_vec_blocks = 8 * g_sms;
+}
 int vec_blocks(int64_t n) {
     int64_t g = (n + VEC_BS - 1) / VEC_BS;
     return (int)(g < 1 ? 1 : (g > g_max_vec_blocks ? g_max_vec_blocks : g));
+}
+// CTAs of the per-iteration PCG kernels (SpMV, CG updates) over `work` thread items: at
+// most `hot_ctas_per_sm` CTAs on each SM (<= 8, so the GridSum partials sized by
+// vec_blocks suffice).  Fewer, fuller threads keep enough loads in flight and halve the
+// FP64 work of the block reductions relative to one wave of 8 CTAs per SM.
+static thread_local int g_hot_ctas_per_sm = 4;   // set from the handle before its launches
+void set_hot_ctas_per_sm(int c) { g_hot_ctas_per_sm = c < 1 ? 1 : (c > 8 ? 8 : c); }
+int hot_ctas_per_sm() { return g_hot_ctas_per_sm; }
+int hot_blocks(int64_t work) {
+    const int64_t cap = (int64_t)g_hot_ctas_per_sm * g_sms;
+    int64_t g = (work + VEC_BS - 1) / VEC_BS;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 #define GRID_STRIDE(i, n) \
@@ -209,7 +227,7 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_rho(int64_t n, const double* __r
 __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __restrict__ b,
                                                       double* __restrict__ x, double* __restrict__ r, int64_t ld,
                                                       PcgScalars* __restrict__ sc, GridSum gs, double tol,
-                                                      int max_it, int flexible) {
+                                                      int max_it, int flexible, double* hist, int hist_len) {
     __shared__ double sh[32];
     const int col = blockIdx.y;
     b += col * ld;
@@ -240,6 +258,7 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
         sc->alpha = sc->beta = sc->pq = 0.0;
         sc->flexible = flexible;
         sc->restart = 0;
+        if (hist && hist_len > 0) hist[(int64_t)col * hist_len] = bb;
     }
 }
 
@@ -247,7 +266,9 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
 // rho_new / rho (Fletcher-Reeves form of CG) or the flexible (Polak-Ribiere)
 // (rho_new - r_new . z_old) / rho, which tolerates a slightly non-symmetric
 // preconditioner; 0 on the first iteration and right after a residual replacement.
-__global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+// V = 2: rows in 16-byte pairs (n and the column stride even, bases 16-byte aligned).
+template <int V>
+__global__ void __launch_bounds__(VEC_BS, 4) k_pcg_p(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                                                    int64_t ld, const PcgScalars* __restrict__ sc) {
     const int col = blockIdx.y;
     sc += col;
@@ -255,14 +276,36 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_p(int64_t n, const double* __res
     z += col * ld;
     p += col * ld;
     const double beta = sc->beta;
-    GRID_STRIDE(k, n) p[k] = z[k] + beta * p[k];
+    if (V == 2) {
+        const double2* z2 = reinterpret_cast<const double2*>(z);
+        double2* p2 = reinterpret_cast<double2*>(p);
+        GRID_STRIDE(i, n >> 1) {
+            const double2 zz = z2[i];
+            double2 pp = p2[i];
+            pp.x = zz.x + beta * pp.x;
+            pp.y = zz.y + beta * pp.y;
+            p2[i] = pp;
+        }
+    } else {
+        GRID_STRIDE(k, n) p[k] = z[k] + beta * p[k];
+    }
 }
 
-// q = A p on the sliced-ELL copy (one thread per row; a warp is one 32-row slice, so each
-// load of values / columns is one contiguous segment) and p . q -> sc->pq; the CTA that
-// completes p . q sets alpha = rho / p . q once.  CTA 0 moves rho to the new direction's
-// value (read by the following kernels only).
-__global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
+// q = A p on the sliced-ELL copy and p . q -> sc->pq; the CTA that completes p . q sets
+// alpha = rho / p . q once.  CTA 0 moves rho to the new direction's value (read by the
+// following kernels only).
+//
+// A warp takes two 32-row slices at a time (lane = row of each), so each load of values
+// and columns is one contiguous 128/256-byte segment, and the two rows' product chains are
+// independent.  Columns and values of EB entries of both rows are loaded before the
+// gathers of p they index, and those before any product, giving every lane up to 4 EB
+// independent loads in flight.  A slice's width is the same for all its lanes, so entries
+// past it are skipped by a uniform branch (no FP64 work on padding beyond the width; B300
+// issues one FP64 FMA per SM and clock for every two lanes, which bounds this kernel
+// together with HBM).  Padding inside the width and rows past n read column
+// min(row, n - 1) with value 0.
+template <int EB>
+__global__ void __launch_bounds__(VEC_BS, 4) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
                                                           const int32_t* __restrict__ ell_col,
                                                           const double* __restrict__ ell_val,
                                                           const double* __restrict__ p, double* __restrict__ q,
@@ -279,29 +322,68 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_spmv_ell(int64_t n, const int64_
         sc->rz = sc->rz_next;
         sc->restart = 0;
     }
-    double acc = 0.0;
-    GRID_STRIDE(k, n) {
-        const int64_t sl = k >> 5;
-        const int r = (int)(k & 31);
-        const int64_t b = __ldg(ell_ptr + sl), w = (__ldg(ell_ptr + sl + 1) - b) >> 5;
-        const double* v = ell_val + b + r;
-        const int32_t* c = ell_col + b + r;
-        double s = 0.0;
-        int64_t e = 0;
-        for (; e + 4 <= w; e += 4) {
-            const int32_t c0 = __ldg(c + e * 32), c1 = __ldg(c + (e + 1) * 32);
-            const int32_t c2 = __ldg(c + (e + 2) * 32), c3 = __ldg(c + (e + 3) * 32);
-            const double v0 = __ldg(v + e * 32), v1 = __ldg(v + (e + 1) * 32);
-            const double v2 = __ldg(v + (e + 2) * 32), v3 = __ldg(v + (e + 3) * 32);
-            s += v0 * __ldg(p + c0);
-            s += v1 * __ldg(p + c1);
-            s += v2 * __ldg(p + c2);
-            s += v3 * __ldg(p + c3);
+    const int lane = threadIdx.x & 31;
+    const int64_t nsl = (n + 31) >> 5, npair = (nsl + 1) >> 1;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc = 0.0, acc1 = 0.0;
+    for (int64_t sp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sp < npair; sp += nwarp) {
+        const int64_t sa = 2 * sp, sb = sa + 1;
+        const bool hb = sb < nsl;
+        const int64_t ba = __ldg(ell_ptr + sa), bb = __ldg(ell_ptr + sa + 1);
+        const int64_t eb = hb ? __ldg(ell_ptr + sb + 1) : bb;
+        const int wa = (int)((bb - ba) >> 5), wb = (int)((eb - bb) >> 5);
+        const int wm = wa > wb ? wa : wb;
+        const int32_t* ca = ell_col + ba + lane;
+        const int32_t* cb = ell_col + bb + lane;
+        const double* va = ell_val + ba + lane;
+        const double* vb = ell_val + bb + lane;
+        // four independent FP64 chains per lane (even / odd entries of each row): B300
+        // returns FP64 results through a narrow shared unit, so a single dependent chain
+        // per row leaves that unit idle while the lane waits
+        double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+        for (int e0 = 0; e0 < wm; e0 += EB) {
+            int32_t ia[EB], ib[EB];
+            double xa[EB], xb[EB], ga[EB], gb[EB];
+#pragma unroll
+            for (int j = 0; j < EB; ++j) {
+                const int e = e0 + j;
+                ia[j] = e < wa ? __ldg(ca + (int64_t)e * 32) : 0;
+                ib[j] = e < wb ? __ldg(cb + (int64_t)e * 32) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < EB; ++j) {
+                const int e = e0 + j;
+                xa[j] = e < wa ? __ldg(va + (int64_t)e * 32) : 0.0;
+                xb[j] = e < wb ? __ldg(vb + (int64_t)e * 32) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < EB; ++j) {
+                const int e = e0 + j;
+                ga[j] = e < wa ? __ldg(p + ia[j]) : 0.0;
+                gb[j] = e < wb ? __ldg(p + ib[j]) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < EB; j += 2) {
+                const int e = e0 + j;
+                if (e < wa) s0 += xa[j] * ga[j];
+                if (e < wb) s1 += xb[j] * gb[j];
+                if (e + 1 < wa) t0 += xa[j + 1] * ga[j + 1];
+                if (e + 1 < wb) t1 += xb[j + 1] * gb[j + 1];
+            }
         }
-        for (; e < w; ++e) s += __ldg(v + e * 32) * __ldg(p + __ldg(c + e * 32));
-        q[k] = s;
-        acc += p[k] * s;
+        s0 += t0;
+        s1 += t1;
+        const int64_t ka = sa * 32 + lane, kb = sb * 32 + lane;
+        if (ka < n) {
+            q[ka] = s0;
+            acc += p[ka] * s0;
+        }
+        if (hb && kb < n) {
+            q[kb] = s1;
+            acc1 += p[kb] * s1;
+        }
     }
+    acc += acc1;
     if (grid_sum(acc, sh, gs, &sc->pq) && threadIdx.x == 0) {
         const double pq = sc->pq, al = sc->rz_next / pq;
         sc->alpha = al;
@@ -331,11 +413,13 @@ __device__ __forceinline__ void pcg_stop_test(PcgScalars* sc) {
 
 // x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new (and, for
 // the flexible beta, r_new . z_old -> sc->rz_mix, z still holding z_old), then the stop
-// test.
-__global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
+// test.  V = 2: rows in 16-byte pairs, as in k_pcg_p.
+template <int V>
+__global__ void __launch_bounds__(VEC_BS, 4) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ z, int64_t ld,
-                                                    PcgScalars* __restrict__ sc, GridSum gs) {
+                                                    PcgScalars* __restrict__ sc, GridSum gs, double* hist,
+                                                    int hist_len) {
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
@@ -350,20 +434,53 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_xr(int64_t n, double* __restrict
     gs.ticket += col;
     const double al = sc->alpha;
     const bool ok = sc->step_ok != 0;
-    double acc = 0.0, acc2 = 0.0;
-    GRID_STRIDE(k, n) {
-        double rk = r[k];
-        if (ok) {
-            x[k] += al * p[k];
-            rk -= al * q[k];
-            r[k] = rk;
+    double acc = 0.0, acc2 = 0.0, accy = 0.0, acc2y = 0.0;   // independent FP64 chains
+    if (V == 2) {
+        double2* x2 = reinterpret_cast<double2*>(x);
+        double2* r2 = reinterpret_cast<double2*>(r);
+        const double2* p2 = reinterpret_cast<const double2*>(p);
+        const double2* q2 = reinterpret_cast<const double2*>(q);
+        const double2* z2 = reinterpret_cast<const double2*>(z);
+        GRID_STRIDE(i, n >> 1) {
+            double2 rk = r2[i];
+            if (ok) {
+                const double2 pk = p2[i], qk = q2[i];
+                double2 xk = x2[i];
+                xk.x += al * pk.x;
+                xk.y += al * pk.y;
+                rk.x -= al * qk.x;
+                rk.y -= al * qk.y;
+                x2[i] = xk;
+                r2[i] = rk;
+            }
+            acc += rk.x * rk.x;
+            accy += rk.y * rk.y;
+            if (flex) {
+                const double2 zk = z2[i];
+                acc2 += rk.x * zk.x;
+                acc2y += rk.y * zk.y;
+            }
         }
-        acc += rk * rk;
-        if (flex) acc2 += rk * z[k];
+        acc += accy;
+        acc2 += acc2y;
+    } else {
+        GRID_STRIDE(k, n) {
+            double rk = r[k];
+            if (ok) {
+                x[k] += al * p[k];
+                rk -= al * q[k];
+                r[k] = rk;
+            }
+            acc += rk * rk;
+            if (flex) acc2 += rk * z[k];
+        }
     }
     const bool last = flex ? grid_sum2(acc, acc2, sh, gs, &sc->rr_new, &sc->rz_mix)
                            : grid_sum(acc, sh, gs, &sc->rr_new);
-    if (last && threadIdx.x == 0) pcg_stop_test(sc);
+    if (last && threadIdx.x == 0) {
+        pcg_stop_test(sc);
+        if (hist && sc->iter < hist_len) hist[(int64_t)col * hist_len + sc->iter] = sc->rr_new;   // residual history
+    }
 }
 
 // Residual replacement for columns that restart (done == 0): r = b - A x, ||r||^2 ->
@@ -513,9 +630,10 @@ void launch_pcg_rho(int64_t n, int ncols, const double* r, const double* z, PcgS
     k_pcg_rho<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, r, z, sc, gs, cs);
 }
 void launch_pcg_init(int64_t n, int ncols, int64_t ld, const double* b, double* x, double* r, PcgScalars* sc,
-                     GridSum gs, double tol, int max_it, int flexible, cudaStream_t st) {
+                     GridSum gs, double tol, int max_it, int flexible, double* hist, int hist_len, cudaStream_t st) {
     count_launch();
-    k_pcg_init<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, b, x, r, ld, sc, gs, tol, max_it, flexible);
+    k_pcg_init<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, b, x, r, ld, sc, gs, tol, max_it, flexible, hist,
+                                                               hist_len);
 }
 void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col,
                         const double* val, const double* x, const double* b, double* r, PcgScalars* sc, GridSum gs,
@@ -523,25 +641,40 @@ void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr,
     count_launch();
     k_pcg_replace<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, rowptr, col, val, x, b, r, ld, sc, gs);
 }
+// 16-byte row pairs when every column of every operand starts 16-byte aligned
+static bool pairs_ok(int64_t n, int64_t ld, std::initializer_list<const void*> ptrs) {
+    if ((n & 1) || (ld & 1)) return false;
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) & 15) return false;
+    return true;
+}
 void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
                   cudaStream_t st) {
     count_launch();
-    k_pcg_p<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, z, p, ld, sc);
+    if (pairs_ok(n, ld, {z, p}))
+        k_pcg_p<2><<<dim3(hot_blocks(n >> 1), ncols), VEC_BS, 0, st>>>(n, z, p, ld, sc);
+    else
+        k_pcg_p<1><<<dim3(hot_blocks(n), ncols), VEC_BS, 0, st>>>(n, z, p, ld, sc);
 }
 void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
                          const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
                          cudaStream_t st) {
     count_launch();
-    k_pcg_spmv_ell<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, ld, sc, gs);
+    const int64_t warps = (((n + 31) >> 5) + 1) >> 1;   // one warp per pair of slices
+    k_pcg_spmv_ell<4><<<dim3(hot_blocks(warps * 32), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q,
+                                                                               ld, sc, gs);
 }
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st) {
     count_launch();
     k_ell_values<<<grid_for(nell, 256), 256, 0, st>>>(nell, src, val, ell_val);
 }
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
-                   const double* z, PcgScalars* sc, GridSum gs, cudaStream_t st) {
+                   const double* z, PcgScalars* sc, GridSum gs, double* hist, int hist_len, cudaStream_t st) {
     count_launch();
-    k_pcg_xr<<<dim3(vec_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, z, ld, sc, gs);
+    if (pairs_ok(n, ld, {x, r, p, q, z}))
+        k_pcg_xr<2><<<dim3(hot_blocks(n >> 1), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, z, ld, sc, gs, hist, hist_len);
+    else
+        k_pcg_xr<1><<<dim3(hot_blocks(n), ncols), VEC_BS, 0, st>>>(n, x, r, p, q, z, ld, sc, gs, hist, hist_len);
 }
 void launch_residual(int64_t n, int ncols, int64_t ld, const int32_t* rowptr, const int32_t* col, const double* val,
                      const double* x, const double* b, PcgScalars* sc, GridSum gs, cudaStream_t st) {

@@ -24,11 +24,17 @@ class AlgMortar:
     precision: "fp64" | "fp32" | "bf16" for the local factors/solves and MBF panels.
     part_sizes: optional target sizes of the n_parts subdomains (sum = N).
     parts: optional labels replacing the built-in partitioner.
+    interface_solve: "exact" (FP64) or "inexact" (block-Jacobi PCG in FP32 to iface_rtol,
+    blocks of interfaces (i, j) with equal i // iface_block_parts; flexible outer CG).
+    autotune: time the hot kernels' launch variants on this problem during setup.
+    seed: with part_sizes None, nonzero draws uneven target sizes (algmortar_part_sizes).
+    stage_times: per-stage device times of the last PCG iteration in the solve stats.
     """
 
     def __init__(self, A, n_parts, precision="fp64", part_sizes=None, parts=None, use_graph=False,
                  check_every=1, max_it=10000, diag_scale=True, device=0, verbose=False, stream=None,
-                 nd_depth=-1, l2_prefetch=-1, deep_ring=False, flexible=False, smooth_steps=0):
+                 nd_depth=-1, flexible=False, smooth_steps=0, interface_solve="exact", iface_rtol=1e-2,
+                 iface_block_parts=1, iface_max_it=200, autotune=False, seed=0, stage_times=False):
         if not torch.cuda.is_available():
             raise RuntimeError("AlgMortar needs a CUDA device")
         L = B.lib()
@@ -43,10 +49,15 @@ class AlgMortar:
         o.verbose = 1 if verbose else 0
         o.device = int(device)
         o.nd_depth = int(nd_depth)
-        o.l2_prefetch = int(l2_prefetch)
-        o.deep_ring = int(deep_ring)
         o.flexible = 1 if flexible else 0
         o.smooth_steps = int(smooth_steps)
+        o.interface_solve = {"exact": B.IFACE_EXACT, "inexact": B.IFACE_INEXACT}[interface_solve]
+        o.iface_rtol = float(iface_rtol)
+        o.iface_block_parts = int(iface_block_parts)
+        o.iface_max_it = int(iface_max_it)
+        o.autotune = 1 if autotune else 0
+        o.seed = int(seed)
+        o.stage_times = 1 if stage_times else 0
         self._sizes = None
         if part_sizes is not None:
             self._sizes = np.ascontiguousarray(part_sizes, dtype=np.int32)
@@ -107,15 +118,23 @@ class AlgMortar:
         nl = self.info["n_lambda"]
         return pbar, beta[:nl], eta[:nl], z
 
-    def solve(self, b, tol=1e-8, raise_on_fail=True):
-        """PCG with x0 = 0 to ||r|| <= tol ||b||; returns (x, stats dict)."""
+    def solve(self, b, tol=1e-8, raise_on_fail=True, history=0):
+        """PCG with x0 = 0 to ||r|| <= tol ||b||; returns (x, stats dict).  history > 0:
+        stats["history"] holds ||r_k|| / ||b|| for the first `history` iterates."""
         b = self._vec(b)
         x = torch.empty_like(b)
         st = B.Stats()
+        hbuf = None
+        if history > 0:
+            hbuf = (C.c_double * int(history))()
+            st.history = C.cast(hbuf, C.POINTER(C.c_double))
+            st.history_len = int(history)
         rc = B.lib().algmortar_pcg_solve(self._h, _ptr(b), _ptr(x), float(tol), C.byref(st))
         if raise_on_fail and rc != B.OK:
             raise B.AlgMortarError(rc, "algmortar_pcg_solve")
-        return x, st.as_dict()
+        d = st.as_dict()
+        del hbuf
+        return x, d
 
     def solve_host(self, b, tol=1e-8):
         """PCG with HOST numpy b -> host x (copies inside the call)."""
@@ -170,6 +189,12 @@ class AlgMortar:
         out = (C.c_double * 8)()
         B.check(B.lib().algmortar_time_stages(self._h, int(reps), out), "algmortar_time_stages")
         return dict(zip(self.STAGES, list(out)[:7]))
+
+    def get_info(self):
+        """Fresh algmortar_info (device-side counters such as iface_last_iterations)."""
+        info = B.Info()
+        B.check(B.lib().algmortar_get_info(self._h, C.byref(info)))
+        return info.as_dict()
 
     def partition(self):
         out = np.empty(self.n, dtype=np.int32)

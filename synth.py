@@ -32,7 +32,7 @@ import scipy.sparse as sp
 __all__ = [
     "Problem", "gaussian_field", "tpfa_cartesian", "config1", "config2", "config3",
     "config4", "config5", "tpfa_from_lnK", "even_part_sizes", "uneven_part_sizes", "splitmix64",
-    "PAPER_WORKLOADS",
+    "PAPER_WORKLOADS", "EXTRA_WORKLOADS", "cross_field", "config_cross", "config3_theta",
 ]
 
 
@@ -381,6 +381,45 @@ def config5(seed: int = 50, n: int = 96, n_parts: Optional[int] = None) -> Probl
                    {"lnK": lnK})
 
 
+def cross_field(n: int, motif: int = 8, kappa: float = 1e6) -> np.ndarray:
+    """Cross-shaped high-contrast permeability on an n^3 grid (Sec. 7.1 workload shape).
+
+    In every motif^3 block, cell (i, j, k) (block-local indices) has K = kappa when at
+    least two of i, j, k lie in the block's central band {motif/2 - 1, motif/2}: three
+    orthogonal bars of 2 x 2 cells through the block centre.  Periodic replication joins
+    the bars of neighbouring blocks into channels along every axis; K = 1 elsewhere.
+    (The paper gives the motif as a figure only; this is the reading used here.)
+    """
+    idx = np.arange(n) % motif
+    band = (idx == motif // 2 - 1) | (idx == motif // 2)
+    bi, bj, bk = np.meshgrid(band, band, band, indexing="ij")
+    cnt = bi.astype(int) + bj.astype(int) + bk.astype(int)
+    return np.where(cnt >= 2, kappa, 1.0)
+
+
+def config_cross(n: int = 96, motif: int = 8, kappa: float = 1e6, part_cells: int = 1024) -> Problem:
+    """Unit cube, n^3 cells, cross-shaped field with contrast kappa; p = 0 on y = 0 and
+    p = 1 on y = 1, no flow elsewhere, zero source; even parts of ~part_cells cells."""
+    shape = (n, n, n)
+    K = cross_field(n, motif, kappa)
+    A, f = tpfa_cartesian(K, kz_ratio=1.0, bc_axis=1, p_lo=0.0, p_hi=1.0)
+    m = max(1, A.shape[0] // part_cells)
+    return Problem(f"cross_{n}cube_kappa{kappa:.0e}", A, f, shape, m, even_part_sizes(A.shape[0], m),
+                   {"high_fraction": float((K > 1).mean()), "kappa": kappa, "motif": motif})
+
+
+def config3_theta(theta: float, seed: int = 3, n_parts: int = 1122, ny: int = 220) -> Problem:
+    """Contrast sweep (Sec. 7.3): config 3's field K replaced by K^theta, so a contrast c
+    becomes c^theta; everything else as config 3."""
+    shape = (60, ny, 85)
+    K = channel_field(shape, 35, seed) ** float(theta)
+    A, f = tpfa_cartesian(K, kz_ratio=0.1, bc_axis=1)
+    sizes = uneven_part_sizes(A.shape[0], n_parts, 300, 3000, seed)
+    return Problem(f"c3_theta{theta:g}", A, f, shape, n_parts, sizes,
+                   {"theta": float(theta), "contrast": float(K.max() / K.min())})
+
+
 PAPER_WORKLOADS = {
     "c1": config1, "c2": config2, "c3": config3, "c4": config4, "c5": config5,
 }
+EXTRA_WORKLOADS = {"cross": config_cross, "c3_theta": config3_theta}

@@ -35,18 +35,44 @@ def test_exports_every_declared_symbol():
     assert set(names) == set(B.SIGNATURES)
 
 
+def test_library_resolves_every_symbol_at_load():
+    """dlopen with RTLD_NOW: a missing template instantiation or kernel symbol fails here
+    instead of at its first call on the GPU."""
+    import ctypes
+    ctypes.CDLL(B.LIB_PATH, mode=ctypes.RTLD_GLOBAL | os.RTLD_NOW)
+
+
 def test_strerror_and_defaults():
     L = B.lib()
     for s in range(10):
         assert L.algmortar_strerror(s)
     o = B.default_opts()
     assert o.precision == B.FP64 and o.diag_scale == 1 and o.max_it == 10000
+    assert o.interface_solve == B.IFACE_EXACT and o.iface_block_parts == 1 and o.iface_max_it == 200
+    assert o.iface_rtol == 1e-2 and o.autotune == 0 and o.seed == 0 and o.stage_times == 0
 
 
 @pytest.mark.parametrize("cfg", ["config1"])
 def test_partition_bit_identical_to_oracle(cfg):
     P = getattr(synth, cfg)()
     np.testing.assert_array_equal(B.partition(P.A, P.n_parts, P.part_sizes), op.partition(P.A, P.part_sizes))
+
+
+@pytest.mark.parametrize("n,m,seed", [(1122000, 1122, 3), (500000, 500, 4), (5000, 7, 11), (640, 64, 1)])
+def test_uneven_part_sizes_match_the_generator(n, m, seed):
+    """The library's seeded size draw (opts.seed) equals the workload generator's rule with
+    lo = 3n/(10m), hi = 3n/m -- 300..3000 for the 1.122M-cell and 500k-cell cases."""
+    out = np.empty(m, dtype=np.int32)
+    B.check(B.lib().algmortar_part_sizes(n, m, seed, out.ctypes.data_as(B._IP)))
+    ref = synth.uneven_part_sizes(n, m, 3 * n // (10 * m), 3 * n // m, seed)
+    np.testing.assert_array_equal(out, ref)
+    assert out.sum() == n
+
+
+def test_uneven_part_sizes_rejects_bad_arguments():
+    out = np.empty(4, dtype=np.int32)
+    assert B.lib().algmortar_part_sizes(3, 4, 1, out.ctypes.data_as(B._IP)) == B.INVALID_ARG
+    assert B.lib().algmortar_part_sizes(10, 0, 1, out.ctypes.data_as(B._IP)) == B.INVALID_ARG
 
 
 def test_partition_uneven_and_3d():

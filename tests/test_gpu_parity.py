@@ -189,6 +189,25 @@ def test_pcg_low_precision_factors(case, precision):
     assert rel(am.apply(r).cpu().numpy(), oa.apply(pc, r)) <= tol
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("depth", [0, 2])
+def test_low_precision_variants_apply_the_interface_inverses_in_fp32(precision, depth):
+    """FP32 / BF16 factor variants apply the explicit interface inverses in FP32: eta
+    against the oracle's exact solve of S_eta with the GPU's own b_eta.  The handle's S_eta
+    is built from MBFs solved with its own factors, so it matches the exact S_eta to FP32
+    rounding for FP32 factors and only to BF16 rounding (~1e-2) for BF16 factors."""
+    A, f, sizes = small3d(shape=(23, 19, 15), m=16, seed=41)
+    part = op.partition(A, sizes)
+    pc = oa.setup(A, part)
+    am = AlgMortar(A, len(sizes), part_sizes=sizes, nd_depth=depth, precision=precision)
+    r = np.random.default_rng(107).standard_normal(A.shape[0])
+    _, beta, eta, _ = (t.cpu().numpy() for t in am.apply_stages(r))
+    eta_ref = np.linalg.solve(pc.S, beta)
+    assert rel(eta, eta_ref) <= (1e-4 if precision == "fp32" else 5e-2)
+    x, st = am.solve(f, tol=1e-8)
+    assert st["status"] == 0
+
+
 @pytest.mark.parametrize("depth", [0, 1, 2])
 def test_interface_nested_dissection(depth):
     """The interface solve by nested dissection (2^depth groups + separator) gives the
@@ -339,8 +358,7 @@ def test_wide_profile_many_tiles_per_row():
     """Two subdomains of ~2300 cells (73 tile rows, ~3 off-diagonal tiles per row): each
     chain streams ~8 times its ring's capacity, so ring slots are reused while tiles are
     released out of order by different warps.  FP64 apply matches the oracle; the
-    alternative ring configuration gives bit-identical results (every tile row has at most
-    two far tiles, so both configurations sum the same partials in the same order);
+    autotuned launch variant agrees to rounding;
     FP32 / BF16 PCG converge."""
     A, f, sizes = small3d(m=2, uneven=False)
     part = op.partition(A, sizes)
@@ -349,9 +367,9 @@ def test_wide_profile_many_tiles_per_row():
     z_ref = oa.apply(pc, r)
     for prec in ("fp64", "fp32", "bf16"):
         am = AlgMortar(A, len(sizes), part_sizes=sizes, precision=prec)
-        deep = AlgMortar(A, len(sizes), part_sizes=sizes, precision=prec, deep_ring=True)
+        tuned = AlgMortar(A, len(sizes), part_sizes=sizes, precision=prec, autotune=True)
         z = am.apply(r)
-        assert torch.equal(z, deep.apply(r))
+        assert rel(tuned.apply(r).cpu().numpy(), z.cpu().numpy()) <= (1e-13 if prec == "fp64" else 1e-6)
         if prec == "fp64":
             assert rel(z.cpu().numpy(), z_ref) <= 1e-10
         else:
