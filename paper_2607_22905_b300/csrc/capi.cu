@@ -137,6 +137,8 @@ struct Vecs {
     int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
     int32_t* iits = nullptr;           // inexact interface solve: per column, inner iterations
     int64_t* iits_total = nullptr;     //   of the latest application / summed since reset
+    float* f32 = nullptr;              // FP32 interface solve: side vectors per column
+    int64_t fl = 0;                    //   (b: L | P: np | separator eta: nsep), column stride
     double* hist = nullptr;            // per column: ||r_k||^2 of iterations 0..hist_len-1
     int hist_len = 0;
     cudaEvent_t sev[8] = {};           // stage boundaries of one PCG iteration (stage_times)
@@ -725,6 +727,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         a.Ginv32 = Ginv32;
         a.Wcm32 = Wcm32;
         a.Wrm32 = Wrm32;
+
         // ---- separator Schur complement C as one dense item ----
         if (nsep > 0) {
             const int T = (nsep + TILE - 1) / TILE;
@@ -1079,7 +1082,10 @@ int mark(algmortar_t* h, Vecs& v, int i) {
 
 // Interface right-hand side and interface solve: b_eta from pbar, eta = S^{-1} b_eta.
 void stage_restrict(algmortar_t* h, Vecs& v, const ColStrides& cs) {
-    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, v.pbar, v.beta, h->d_ndpos, cs, v.k, h->st);
+    // the FP32 interface solve reads an FP32 copy of b_eta, written here with it
+    const bool f32 = !h->inexact && h->nd.Ginv32;
+    launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, v.pbar, v.beta, h->d_ndpos, cs, v.k,
+                    f32 ? v.f32 : nullptr, v.fl, h->st);
 }
 int stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
     if (h->L <= 0) return 0;
@@ -1089,7 +1095,7 @@ int stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
         a.its_total = v.iits_total;
         CU(launch_iface_pcg(a, h->iface_cluster, h->iface_smem, v.beta, v.eta, cs, v.k, h->st));
     } else {
-        launch_nd_solve(h->nd, v.beta, v.eta, v.P, cs, v.k, h->st);
+        launch_nd_solve(h->nd, v.beta, v.eta, v.P, v.f32, v.fl, true, cs, v.k, h->st);
     }
     return 0;
 }
@@ -1200,8 +1206,9 @@ int ensure_graph(algmortar_t* h, Vecs& v) {
 // Workspace of a batch with room for `cap` columns (first use, or growth).
 int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     if (v.cap >= cap) return 0;
-    void* old[] = {v.x,  v.r,  v.z,       v.p,         v.q,       v.pbar, v.b,    v.t,          v.w,
-                   v.beta, v.eta, v.P, v.sc, v.gs.part, v.gs.ticket, v.iits, v.iits_total, v.hist};
+    void* old[] = {v.x,         v.r,    v.z,    v.p,          v.q,    v.pbar, v.b,  v.t,
+                   v.w,         v.beta, v.eta,  v.P,          v.sc,   v.gs.part,    v.gs.ticket,
+                   v.iits,      v.iits_total,   v.hist,       v.f32};
     for (void* p : old)
         if (p) h->release(p);
     if (v.graph) {
@@ -1229,13 +1236,16 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     v.sc = h->alloc<PcgScalars>(cap);
     v.gs.part = h->alloc<double>(nb);
     v.gs.ticket = h->alloc<unsigned int>(cap);
+    v.fl = (((int64_t)std::max(h->L, 1) + np + h->P.nd_nsep + 3) / 4) * 4;
+    v.f32 = h->alloc<float>((size_t)v.fl * cap);
     v.iits = h->alloc<int32_t>(cap);
     v.iits_total = h->alloc<int64_t>(cap);
     // ||r_k||^2 of every iteration (k <= max_it) per column, written by the stop test
     v.hist_len = std::max(h->opts.max_it, 1) + 1;
     v.hist = h->alloc<double>((size_t)v.hist_len * cap);
     if (!v.x || !v.r || !v.z || !v.p || !v.q || !v.pbar || !v.b || !v.t || (h->opts.smooth_steps > 0 && !v.w) ||
-        !v.beta || !v.eta || !v.P || !v.sc || !v.gs.part || !v.gs.ticket || !v.iits || !v.iits_total || !v.hist) {
+        !v.beta || !v.eta || !v.P || !v.sc || !v.gs.part || !v.gs.ticket || !v.iits || !v.iits_total || !v.hist ||
+        !v.f32) {
         v.cap = 0;
         return fail(ALGMORTAR_OOM, "vector workspace");
     }

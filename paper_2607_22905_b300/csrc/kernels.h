@@ -158,8 +158,11 @@ template <typename TW>
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
                            const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
                            TW* work, cudaStream_t st);
-void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
-                     cudaStream_t st);
+// f32: FP32 side vectors for the FP32 copies ([b: L | c: np | separator eta: nsep] per
+// column, column stride fl; null for FP64); b32_ready: the restriction already wrote the
+// FP32 copy of b (else it is converted here)
+void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, float* f32, int64_t fl,
+                     bool b32_ready, ColStrides cs, int ncols, cudaStream_t st);
 cudaError_t prepare_nd_solve(int nsep);
 
 // local factor
@@ -207,7 +210,8 @@ void launch_scatter_cols(int64_t n, int ncols, const int32_t* perm, const double
                          int64_t ldd, cudaStream_t st);
 void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st);
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
-                     double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st);
+                     double* beta, const int32_t* omap, ColStrides cs, int ncols, float* beta32, int64_t fl,
+                     cudaStream_t st);
 template <typename TP>
 void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
                     const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,

@@ -16,6 +16,7 @@
 // wide warp-per-row GEMV over all SMs (FP64 ALU-bound on B300), with no sequential
 // triangular sweep on the critical path.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -433,24 +434,23 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
 }
 
 // Warp dot product of a contiguous row with x (len entries) in the row's arithmetic TM
-// (FP64, or FP32 for the FP32 copies), four independent accumulators per lane (the FP64
-// pipe's latency is long on B300), lanes 0..31 strided.
+// (FP64, or FP32 for the FP32 copies, x then FP32 too: a double -> float conversion runs
+// on B300's FP64 pipe), eight independent accumulators per lane so that each lane has
+// eight row loads in flight, lanes 0..31 strided.
 template <typename TM>
-__device__ __forceinline__ TM warp_row_dot(const TM* __restrict__ row, const double* __restrict__ x, int64_t len,
+__device__ __forceinline__ TM warp_row_dot(const TM* __restrict__ row, const TM* __restrict__ x, int64_t len,
                                            int lane) {
-    TM s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    TM s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t j = lane;
-    for (; j + 96 < len; j += 128) {
-        s0 += row[j] * (TM)x[j];
-        s1 += row[j + 32] * (TM)x[j + 32];
-        s2 += row[j + 64] * (TM)x[j + 64];
-        s3 += row[j + 96] * (TM)x[j + 96];
-    }
-    for (; j < len; j += 32) s0 += row[j] * (TM)x[j];
-    TM s = (s0 + s1) + (s2 + s3);
+    for (; j + 224 < len; j += 256) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
+        for (int u = 0; u < 8; ++u) s[u] += row[j + 32 * u] * x[j + 32 * u];
+    }
+    for (int u = 0; j < len; j += 32, ++u) s[u & 7] += row[j] * x[j];
+    TM t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
 }
 
 template <typename TM>
@@ -464,68 +464,100 @@ __device__ __forceinline__ NdMats<float> nd_mats(const NdSolveArgs& a, float) {
     return {a.Ginv32, a.Wcm32, a.Wrm32, a.Cinv32};
 }
 
+// Side vectors of one column in the solve's arithmetic TM: the right-hand side b, the
+// separator right-hand side c = b_sep - sum_g S_{sep,g} S_gg^{-1} b_g (in the P buffer,
+// nsep <= np entries) and the separator solution (FP64: b, P and eta themselves; FP32:
+// float copies in `f32`, laid out [b: L | c: np | separator eta: nsep] per column).
+template <typename TM>
+struct NdVecs {
+    const TM* b;
+    TM* c;
+    TM* es;
+};
+__device__ __forceinline__ NdVecs<double> nd_vecs(const NdSolveArgs& a, const double* b, double* eta, double* P,
+                                                  float*, int64_t, double) {
+    return {b, P, eta + a.goff[a.G]};
+}
+__device__ __forceinline__ NdVecs<float> nd_vecs(const NdSolveArgs& a, const double*, double*, double*, float* f32,
+                                                 int64_t L, float) {
+    return {f32, f32 + L, f32 + L + a.np};
+}
+
 // ---------------------------------------------------------------------------------
 // Per-iteration solve (ND order in and out), in the arithmetic TM of the matrices used.
-// Stage 1: eta_g = Ginv_g b_g  (rows of the symmetric inverse) and P_g = W_g^T b_g.
+// Stage 1, one warp per row: eta_g = Ginv_g b_g for the interior rows, and for every
+// separator unknown s (groups g1 < g2) c_s = b_s - (W_g1^T b_g1)_s - (W_g2^T b_g2)_s.
 // ---------------------------------------------------------------------------------
 template <typename TM>
 __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
-                            double* __restrict__ P, ColStrides cs) {
+                            double* __restrict__ P, float* __restrict__ f32, int64_t fl, ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     const NdMats<TM> M = nd_mats(a, TM(0));
-    b += col * cs.l;
+    const NdVecs<TM> V = nd_vecs(a, b + col * cs.l, eta + col * cs.l, P + col * a.np, f32 ? f32 + col * fl : nullptr,
+                                 a.nin + a.nsep, TM(0));
     eta += col * cs.l;
-    P += col * a.np;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t nin = a.goff[a.G];
     if (wid < nin) {
         const int g = a.row_g[wid];
         const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
-        const TM s = warp_row_dot<TM>(M.Ginv + a.gioff[g] + i * ng, b + g0, ng, lane);
+        const TM s = warp_row_dot<TM>(M.Ginv + a.gioff[g] + i * ng, V.b + g0, ng, lane);
         if (lane == 0) eta[wid] = (double)s;
-    } else if (wid < nin + a.aoff[a.G]) {
-        const int64_t r = wid - nin;
-        const int g = a.prow_g[r];
-        const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = r - a.aoff[g];
-        const TM s = warp_row_dot<TM>(M.Wcm + a.woff[g] + j * ng, b + g0, ng, lane);
-        if (lane == 0) P[r] = (double)s;
+    } else if (wid < nin + a.nsep) {
+        const int64_t sp = wid - nin;
+        TM c = V.b[nin + sp];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int g = a.sg[2 * sp + e];
+            const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = a.sidx[2 * sp + e];
+            c -= warp_row_dot<TM>(M.Wcm + a.woff[g] + j * ng, V.b + g0, ng, lane);
+        }
+        if (lane == 0) V.c[sp] = c;
     }
 }
 
-// Stage 2: c = b_sep - sum_g P_g (built in shared memory by every CTA), eta_sep = Cinv c.
+// Stage 2: eta_sep = Cinv c, c staged in shared memory by every CTA.
 template <typename TM>
 __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double* __restrict__ eta,
-                            const double* __restrict__ P, ColStrides cs) {
+                            double* __restrict__ P, float* __restrict__ f32, int64_t fl, ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     const NdMats<TM> M = nd_mats(a, TM(0));
-    b += col * cs.l;
+    const NdVecs<TM> V = nd_vecs(a, b + col * cs.l, eta + col * cs.l, P + col * a.np, f32 ? f32 + col * fl : nullptr,
+                                 a.nin + a.nsep, TM(0));
     eta += col * cs.l;
-    P += col * a.np;
-    extern __shared__ double cvec[];
+    extern __shared__ __align__(16) unsigned char cvec_raw[];
+    TM* cvec = reinterpret_cast<TM*>(cvec_raw);
     const int nsep = a.nsep;
     const int64_t sep0 = a.goff[a.G];
-    for (int s = threadIdx.x; s < nsep; s += blockDim.x) {
-        const int g1 = a.sg[2 * s], g2 = a.sg[2 * s + 1];
-        cvec[s] = b[sep0 + s] - P[a.aoff[g1] + a.sidx[2 * s]] - P[a.aoff[g2] + a.sidx[2 * s + 1]];
-    }
+    for (int s = threadIdx.x; s < nsep; s += blockDim.x) cvec[s] = V.c[s];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (wid >= nsep) return;
     const TM s = warp_row_dot<TM>(M.Cinv + wid * nsep, cvec, nsep, lane);
-    if (lane == 0) eta[sep0 + wid] = (double)s;
+    if (lane == 0) {
+        eta[sep0 + wid] = (double)s;
+        if (!std::is_same<TM, double>::value) V.es[wid] = s;
+    }
 }
 
-// Stage 3: eta_g -= W_g eta_{A_g}.
+// Stage 3: eta_g -= W_g eta_{A_g}; the separator solution staged in shared memory.
 template <typename TM>
-__global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides cs) {
+__global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, float* __restrict__ f32, int64_t fl,
+                            ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     const NdMats<TM> M = nd_mats(a, TM(0));
+    const NdVecs<TM> V =
+        nd_vecs(a, nullptr, eta + col * cs.l, nullptr, f32 ? f32 + col * fl : nullptr, a.nin + a.nsep, TM(0));
     eta += col * cs.l;
+    extern __shared__ __align__(16) unsigned char es_raw[];
+    TM* es = reinterpret_cast<TM*>(es_raw);
+    for (int s = threadIdx.x; s < a.nsep; s += blockDim.x) es[s] = V.es[s];
+    __syncthreads();
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t nin = a.goff[a.G];
@@ -534,18 +566,25 @@ __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, ColStrides 
     const int64_t g0 = a.goff[g], ag = a.aoff[g + 1] - a.aoff[g], i = wid - g0;
     const TM* row = M.Wrm + a.woff[g] + i * ag;
     const int32_t* al = a.alist + a.aoff[g];
-    const double* es = eta + nin;
-    TM s0 = 0, s1 = 0;
+    TM s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     int64_t j = lane;
-    for (; j + 32 < ag; j += 64) {
-        s0 += row[j] * (TM)es[al[j]];
-        s1 += row[j + 32] * (TM)es[al[j + 32]];
+    for (; j + 96 < ag; j += 128) {
+        s0 += row[j] * es[al[j]];
+        s1 += row[j + 32] * es[al[j + 32]];
+        s2 += row[j + 64] * es[al[j + 64]];
+        s3 += row[j + 96] * es[al[j + 96]];
     }
-    for (; j < ag; j += 32) s0 += row[j] * (TM)es[al[j]];
-    TM s = s0 + s1;
+    for (; j < ag; j += 32) s0 += row[j] * es[al[j]];
+    TM s = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) eta[wid] -= (double)s;
+}
+
+// b -> its FP32 copy (callers whose right-hand side does not come from the restriction)
+__global__ void k_nd_b32(int L, const double* __restrict__ b, float* __restrict__ b32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L) b32[i] = (float)b[i];
 }
 
 // ------------------------------------------------------------------------ launchers
@@ -651,33 +690,47 @@ void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, co
     }
 }
 template <typename TM>
-static void nd_solve_t(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
-                       cudaStream_t st) {
-    const int64_t nin = a.nin, np = a.np;
-    if (nin + np > 0) {
+static void nd_solve_t(const NdSolveArgs& a, const double* b, double* eta, double* P, float* f32, int64_t fl,
+                       ColStrides cs, int ncols, cudaStream_t st) {
+    const int64_t nin = a.nin;
+    if (nin + a.nsep > 0) {
         count_launch();
-        k_nd_stage1<TM><<<dim3((unsigned)((nin + np + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, cs);
+        k_nd_stage1<TM><<<dim3((unsigned)((nin + a.nsep + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, f32, fl, cs);
     }
     if (a.nsep > 0) {
+        const size_t smem = (size_t)a.nsep * sizeof(TM);
         count_launch();
-        k_nd_stage2<TM><<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, (size_t)a.nsep * sizeof(double), st>>>(
-            a, b, eta, P, cs);
-        count_launch();
-        k_nd_stage3<TM><<<dim3((unsigned)((nin + 7) / 8), ncols), 256, 0, st>>>(a, eta, cs);
+        k_nd_stage2<TM><<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, smem, st>>>(a, b, eta, P, f32, fl, cs);
+        if (nin > 0) {
+            count_launch();
+            k_nd_stage3<TM><<<dim3((unsigned)((nin + 7) / 8), ncols), 256, smem, st>>>(a, eta, f32, fl, cs);
+        }
     }
 }
-void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, ColStrides cs, int ncols,
-                     cudaStream_t st) {
-    if (a.Ginv32 || a.Cinv32) nd_solve_t<float>(a, b, eta, P, cs, ncols, st);
-    else nd_solve_t<double>(a, b, eta, P, cs, ncols, st);
+void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, float* f32, int64_t fl,
+                     bool b32_ready, ColStrides cs, int ncols, cudaStream_t st) {
+    if (a.Ginv32 || a.Cinv32) {
+        if (!b32_ready) {
+            const int L = (int)(a.nin + a.nsep);
+            for (int c = 0; c < ncols; ++c) {
+                count_launch();
+                k_nd_b32<<<(L + 255) / 256, 256, 0, st>>>(L, b + c * cs.l, f32 + c * fl);
+            }
+        }
+        nd_solve_t<float>(a, b, eta, P, f32, fl, cs, ncols, st);
+    } else {
+        nd_solve_t<double>(a, b, eta, P, nullptr, 0, cs, ncols, st);
+    }
 }
 cudaError_t prepare_nd_solve(int nsep) {
     size_t smem = (size_t)nsep * sizeof(double);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_nd_stage2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_nd_stage2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const void* ks[] = {(const void*)k_nd_stage2<double>, (const void*)k_nd_stage2<float>,
+                            (const void*)k_nd_stage3<double>, (const void*)k_nd_stage3<float>};
+        for (const void* k : ks) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }

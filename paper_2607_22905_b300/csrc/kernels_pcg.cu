@@ -75,11 +75,13 @@ __global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, con
 // written at position omap[I] (the interface solve's ordering) when omap is given.
 __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_t* __restrict__ rcell,
                            const double* __restrict__ rcoef, const double* __restrict__ pbar,
-                           double* __restrict__ beta, const int32_t* __restrict__ omap, ColStrides cs) {
+                           double* __restrict__ beta, const int32_t* __restrict__ omap, ColStrides cs,
+                           float* __restrict__ beta32, int64_t fl) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     pbar += col * cs.v;
     beta += col * cs.l;
+    if (beta32) beta32 += col * fl;
     int I = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (I >= L) return;
@@ -87,7 +89,11 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     for (int64_t t = rptr[I] + lane; t < rptr[I + 1]; t += 32) s += rcoef[t] * pbar[rcell[t]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) beta[omap ? omap[I] : I] = s;
+    if (lane == 0) {
+        const int o = omap ? omap[I] : I;
+        beta[o] = s;
+        if (beta32) beta32[o] = (float)s;   // the FP32 interface solve's copy
+    }
 }
 
 // z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg), one CTA
@@ -601,10 +607,11 @@ void launch_scatter_cols(int64_t n, int ncols, const int32_t* perm, const double
     k_scatter<<<dim3(grid_for(n, 256), ncols), 256, 0, st>>>(n, perm, src, lds, dst, ldd);
 }
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
-                     double* beta, const int32_t* omap, ColStrides cs, int ncols, cudaStream_t st) {
+                     double* beta, const int32_t* omap, ColStrides cs, int ncols, float* beta32, int64_t fl,
+                     cudaStream_t st) {
     if (L > 0) {
         count_launch();
-        k_restrict<<<dim3((L + 7) / 8, ncols), 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, cs);
+        k_restrict<<<dim3((L + 7) / 8, ncols), 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, cs, beta32, fl);
     }
 }
 template <typename TP>

@@ -49,7 +49,10 @@ cudaError_t scratch_for_current_device(double** out) {
 int interface_solve_noalloc(int device, cudaStream_t st, int L, const NdSolveArgs& nd, const int32_t* d_ndpos,
                             const double* b_dev, double* eta_dev, std::string& err) {
     if (L == 0) return ALGMORTAR_OK;
-    const int64_t need = 2 * (int64_t)L + nd.np;
+    // FP64 b, eta and P; with FP32 interface inverses also their FP32 side vectors
+    const bool f32 = nd.Ginv32 || nd.Cinv32;
+    const int64_t fl = f32 ? (((int64_t)L + nd.np + nd.nsep + 3) / 4) * 4 : 0;
+    const int64_t need = 2 * (int64_t)L + nd.np + fl / 2 + 1;
     if (need > kNoAllocScratchDoubles) {
         err = "interface_solve_noalloc: needs " + std::to_string(need) + " doubles of scratch, the static array holds " +
               std::to_string(kNoAllocScratchDoubles) + " (n_lambda too large for the allocation-free path)";
@@ -75,8 +78,10 @@ int interface_solve_noalloc(int device, cudaStream_t st, int L, const NdSolveArg
     double* b_nd = scratch;            // every entry written by the scatter below
     double* eta_nd = scratch + L;      // written by stages 1 (interior) and 2 (separator)
     double* P = scratch + 2 * (int64_t)L;   // written by stage 1 before stage 2 reads it
+    // FP32 side vectors (16-byte aligned; written before they are read, as above)
+    float* fv = f32 ? reinterpret_cast<float*>(scratch + ((2 * (int64_t)L + nd.np + 1) & ~int64_t(1))) : nullptr;
     launch_scatter(L, d_ndpos, b_dev, b_nd, st);
-    launch_nd_solve(nd, b_nd, eta_nd, P, ColStrides{}, 1, st);
+    launch_nd_solve(nd, b_nd, eta_nd, P, fv, fl, false, ColStrides{}, 1, st);
     launch_gather(L, d_ndpos, eta_nd, eta_dev, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
