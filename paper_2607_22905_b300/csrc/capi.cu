@@ -92,6 +92,7 @@ struct NumWs {
     int64_t ntiles_items = 0, trows_items = 0;
     int max_tiles_items = 0;
     void *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr;   // interface arithmetic
+    float *gplanes = nullptr, *cplanes = nullptr;   // FP32: TF32 operand planes of the factor tiles
     double* gE = nullptr;
     DevBlockJobs bj_gid, bj_cid;               // FP32 setup: identity columns in column blocks
     int32_t *d_gjob = nullptr, *d_gjt0 = nullptr, *d_cjt0 = nullptr;
@@ -614,6 +615,8 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         W.gf = h->alloc<unsigned char>((size_t)std::max<int64_t>(tb, 1) * TILE2 * isz);
         W.gb = h->alloc<unsigned char>((size_t)std::max<int64_t>(tb, 1) * TILE2 * isz);
         if (lowp) {
+            W.gplanes = h->alloc<float>((size_t)std::max<int64_t>(tb, 1) * 2 * TILE2);
+            if (!W.gplanes) return fail(ALGMORTAR_OOM, "interface planes");
             BlockJobs bg;
             for (int it = 0; it < (int)W.item_group.size(); ++it) {
                 const int g = W.item_group[it];
@@ -759,6 +762,8 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             W.cf = h->alloc<unsigned char>((size_t)ct * TILE2 * isz);
             W.cb = h->alloc<unsigned char>((size_t)ct * TILE2 * isz);
             if (lowp) {
+                W.cplanes = h->alloc<float>((size_t)ct * 2 * TILE2);
+                if (!W.cplanes) return fail(ALGMORTAR_OOM, "separator planes");
                 BlockJobs bc;
                 bc.add(0, 0, nsep, nsep, true);
                 TRY(upload_jobs(h, W.bj_cid, bc));
@@ -804,7 +809,7 @@ int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
         std::vector<int32_t> Th(W.nitems);
         for (int it = 0; it < W.nitems; ++it) Th[it] = (int32_t)W.item_hi[it].size();
         launch_dense_cholesky<TI>(W.nitems, Th, W.d_int, W.d_ibase, W.d_irow0, (TI*)W.gwork, (TI*)W.gdinv, W.d_err,
-                                  st);
+                                  st, (TI*)W.gplanes, h->d_kerr);
     }
     CU(cudaGetLastError());
     TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
@@ -840,7 +845,7 @@ int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
                                   (TI*)W.cwork, st);
         CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
         launch_dense_cholesky<TI>(1, std::vector<int32_t>{W.cT}, W.d_cnt, W.d_czero, W.d_czero, (TI*)W.cwork,
-                                  (TI*)W.cdinv, W.d_err, st);
+                                  (TI*)W.cdinv, W.d_err, st, (TI*)W.cplanes, h->d_kerr);
         CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "interface (separator)"));
         Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};

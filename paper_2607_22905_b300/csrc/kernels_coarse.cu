@@ -19,6 +19,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "async.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -262,6 +263,22 @@ __global__ void k_nd_schur_tiles(int64_t L, int nsep, int64_t sep0, const double
     }
 }
 
+// TF32 operand planes of a finished 32x32 factor tile for the tensor-core update (FP32
+// interface factorization): plane 0 holds the tile itself (the tensor core reads the top
+// 19 bits of each value, its TF32 rounding toward zero), plane 1 the remainder x - tf32(x);
+// both in the K-major no-swizzle core-matrix layout with the tile's row r as the M/N index
+// and its column c as K: float offset (r/8)*256 + (c/4)*32 + (r%8)*4 + c%4.  The product
+// hi*hi + hi*lo + lo*hi (3xTF32) then carries ~FP32 accuracy.
+__host__ __device__ __forceinline__ int plane_off(int r, int c) {
+    return (r >> 3) * 256 + (c >> 2) * 32 + (r & 7) * 4 + (c & 3);
+}
+__device__ __forceinline__ void put_planes(float* planes, int r, int c, float x) {
+    planes[plane_off(r, c)] = x;
+    planes[TILE2 + plane_off(r, c)] = x - __int_as_float(__float_as_int(x) & 0xffffe000);
+}
+template <typename TW>
+__device__ __forceinline__ void put_planes(TW*, int, int, TW) {}
+
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
@@ -286,7 +303,8 @@ template <typename TW>
 __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __restrict__ T,
                                                   const int64_t* __restrict__ base,
                                                   const int64_t* __restrict__ row0, TW* __restrict__ work,
-                                                  TW* __restrict__ dinv, int k, int* __restrict__ err) {
+                                                  TW* __restrict__ dinv, int k, int* __restrict__ err,
+                                                  TW* __restrict__ planes) {
     __shared__ TW Ls[TILE][TILE + 1];   // L (column c published at step c - 1)
     __shared__ TW rd_s[TILE];           // 1 / L[c][c]
     __shared__ int bad_s;
@@ -351,6 +369,9 @@ __global__ void __launch_bounds__(128) k_dpotrf_b(int nitems, const int32_t* __r
         const int c = w + 4 * j;
         t[c * TILE + lane] = c <= lane ? Ls[lane][c] : TW(0);
         D[c * TILE + lane] = x[j] * rd_s[c];
+        if (planes)
+            put_planes(planes + (base[g] + (int64_t)k * (k + 1) / 2 + k) * 2 * TILE2, lane, c,
+                       c <= lane ? Ls[lane][c] : TW(0));
     }
     if (threadIdx.x == 0 && bad_s) {
         if (atomicCAS(err + 1, -1, g) == -1) atomicExch(err, 1);
@@ -377,7 +398,7 @@ template <typename TW>
 __global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __restrict__ T,
                                                  const int64_t* __restrict__ base,
                                                  const int64_t* __restrict__ row0, TW* __restrict__ work,
-                                                 const TW* __restrict__ dinv, int k) {
+                                                 const TW* __restrict__ dinv, int k, TW* __restrict__ planes) {
     __shared__ TW X[TILE][TILE + 1];
     __shared__ TW Bs[TILE][TILE + 1];
     int64_t li;
@@ -398,6 +419,7 @@ __global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __re
 #pragma unroll 8
         for (int u = 0; u < TILE; ++u) v += X[rb + q][u] * Bs[c][u];
         t[c * TILE + rb + q] = v;
+        if (planes) put_planes(planes + (base[g] + (int64_t)I * (I + 1) / 2 + k) * 2 * TILE2, rb + q, c, v);
     }
 }
 
@@ -431,6 +453,135 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
         for (int u = 0; u < TILE; ++u) v -= As[rb + q][u] * Bs[c][u];
         t[c * TILE + rb + q] = v;
     }
+}
+
+// ---------------------------------------------------------------------------------
+// Left-looking tensor-core update of block column J of the FP32 dense factors:
+//   A_IJ -= sum_{k < J} L_Ik L_Jk^T   for I >= J,
+// for all items, before the column's diagonal tile is factored and its tiles below solved.
+// One CTA per (item, 4 tile rows I0..I0+3): an M = 128, N = 32 product with K = 32 J on
+// tcgen05 (kind::tf32, accumulator in tensor memory), 3xTF32 (hi*hi + hi*lo + lo*hi from
+// the planes written by k_dpotrf_b / k_dtrsm_b), so the update keeps FP32 accuracy.
+// Thread 0 streams the k-th planes of the four row tiles and of tile (J, k) into one of
+// two shared-memory stages by bulk copies (16-byte aligned 4 KB planes, completion on
+// full[s]); thread 32 issues the 12 MMAs of a stage and commits them to empty[s]; at the
+// end four warps read the 128 x 32 product (one tile row each) and subtract it.  Every
+// wait is bounded; a stuck wait sets *err (the bulk-copy error word) and skips the update.
+// ---------------------------------------------------------------------------------
+constexpr int TC_STAGES = 2;
+constexpr int TC_PLANE = TILE2 * 4;                          // bytes of one plane
+constexpr int TC_STAGE = (4 * 2 + 2) * TC_PLANE;             // A hi, A lo (4 tiles), B hi, B lo
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE + 128;
+
+__global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* __restrict__ T,
+                                                    const int64_t* __restrict__ base, float* __restrict__ work,
+                                                    const float* __restrict__ planes, int J, int* __restrict__ err) {
+    // block -> (item, first tile row)
+    int64_t b = blockIdx.x;
+    int g = -1;
+    for (int q = 0; q < nitems; ++q) {
+        const int64_t nb = T[q] > J ? (T[q] - J + 3) / 4 : 0;
+        if (b < nb) {
+            g = q;
+            break;
+        }
+        b -= nb;
+    }
+    if (g < 0) return;
+    const int I0 = J + 4 * (int)b, Tg = T[g];
+    const int nA = min(4, Tg - I0);
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + TC_STAGES * TC_STAGE);
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* done = empty + TC_STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);     // [0] tensor memory, [2] verdict
+    volatile int* bad = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int64_t g0 = base[g];
+    auto tile = [&](int I, int k) { return g0 + (int64_t)I * (I + 1) / 2 + k; };
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
+        }
+        mbar_init(smem_u32(done), 1);
+        *bad = 0;
+        fence_async_smem();
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (w == 0) tc_alloc(smem_u32(tslot), 32);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    int issued = 0;
+    if (tid == 0) {
+        for (int k = 0; k < J; ++k) {
+            const int s = k % TC_STAGES;
+            if (k >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((k / TC_STAGES - 1) & 1))) {
+                *bad = 1;
+                break;
+            }
+            unsigned char* st = sm + s * TC_STAGE;
+            const uint32_t bar = smem_u32(&full[s]);
+            mbar_expect_tx(bar, (uint32_t)((2 * nA + 2) * TC_PLANE));
+            for (int i = 0; i < nA; ++i) {
+                const float* src = planes + tile(I0 + i, k) * 2 * TILE2;
+                bulk_copy(smem_u32(st + i * TC_PLANE), src, TC_PLANE, bar);
+                bulk_copy(smem_u32(st + (4 + i) * TC_PLANE), src + TILE2, TC_PLANE, bar);
+            }
+            const float* srcB = planes + tile(J, k) * 2 * TILE2;
+            bulk_copy(smem_u32(st + 8 * TC_PLANE), srcB, TC_PLANE, bar);
+            bulk_copy(smem_u32(st + 9 * TC_PLANE), srcB + TILE2, TC_PLANE, bar);
+            ++issued;
+        }
+    } else if (tid == 32) {
+        constexpr uint32_t idesc = tc_idesc_tf32(128, 32);
+        for (int k = 0; k < J; ++k) {
+            const int s = k % TC_STAGES;
+            if (*bad || !mbar_wait(smem_u32(&full[s]), (uint32_t)((k / TC_STAGES) & 1))) {
+                *bad = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_u32(sm + s * TC_STAGE);
+            // A: 128 rows (4 tiles, 4 KB each = 4 groups of 8 rows at SBO 1024), K 8 per MMA
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t o = j * 256;   // two core matrices along K
+                const uint64_t aH = tc_smem_desc(st + o, 128, 1024), aL = tc_smem_desc(st + 4 * TC_PLANE + o, 128, 1024);
+                const uint64_t bH = tc_smem_desc(st + 8 * TC_PLANE + o, 128, 1024);
+                const uint64_t bL = tc_smem_desc(st + 9 * TC_PLANE + o, 128, 1024);
+                tc_mma_tf32(tbase, aH, bH, idesc, (k > 0 || j > 0) ? 1u : 0u);
+                tc_mma_tf32(tbase, aH, bL, idesc, 1u);
+                tc_mma_tf32(tbase, aL, bH, idesc, 1u);
+            }
+            tc_commit(smem_u32(&empty[s]));
+        }
+        tc_commit(smem_u32(done));
+    }
+    // everyone: the product is complete (thread 0 decides for the CTA, so that the
+    // warp-wide tensor-memory loads below run in whole warps or not at all)
+    const bool done_ok = mbar_wait(smem_u32(done), 0u);
+    __syncthreads();
+    if (tid == 0) tslot[2] = (done_ok && !*bad) ? 1u : 0u;
+    __syncthreads();
+    const bool ok = tslot[2] != 0;
+    tc_fence_after();
+    if (ok && w < nA) {
+        float v[32];
+        tc_ld32(tbase + ((uint32_t)(32 * w) << 16), v);
+        float* t = work + tile(I0 + w, J) * TILE2;   // column-major: (r, c) at c * 32 + r
+#pragma unroll
+        for (int c = 0; c < 32; ++c) t[c * TILE + lane] -= v[c];
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    // the producer's copies in flight land before the CTA leaves (bounded)
+    if (tid == 0 && !ok)
+        for (int k = max(0, issued - TC_STAGES); k < issued; ++k)
+            mbar_wait(smem_u32(&full[k % TC_STAGES]), (uint32_t)((k / TC_STAGES) & 1));
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) tc_dealloc(tbase, 32);
 }
 
 // Warp dot product of a contiguous row with x (len entries) in the row's arithmetic TM
@@ -625,9 +776,35 @@ void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const 
 }
 template <typename TW>
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
-                           const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st) {
+                           const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st, TW* planes,
+                           int* kerr) {
     int maxT = 0;
     for (int t : T_host) maxT = std::max(maxT, t);
+    if (planes) {
+        // FP32 (planes given): left-looking, column J updated by the tensor cores from the
+        // planes of the finished columns, then its diagonal tile factored, then solved below
+        cudaFuncSetAttribute(k_dupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        for (int J = 0; J < maxT; ++J) {
+            int64_t nblk = 0, nt = 0;
+            for (int t : T_host)
+                if (t > J) {
+                    nblk += (t - J + 3) / 4;
+                    nt += t - 1 - J;
+                }
+            if (J > 0 && nblk > 0) {
+                count_launch();
+                k_dupdate_tc<<<(unsigned)nblk, 128, TC_SMEM, st>>>(nitems, T, base, (float*)work,
+                                                                   (const float*)planes, J, kerr);
+            }
+            count_launch();
+            k_dpotrf_b<TW><<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, J, err, planes);
+            if (nt > 0) {
+                count_launch();
+                k_dtrsm_b<TW><<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, J, planes);
+            }
+        }
+        return;
+    }
     for (int k = 0; k < maxT; ++k) {
         int64_t nt = 0, np = 0;
         for (int t : T_host) {
@@ -638,10 +815,10 @@ void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const
             }
         }
         count_launch();
-        k_dpotrf_b<TW><<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, k, err);
+        k_dpotrf_b<TW><<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, k, err, nullptr);
         if (nt > 0) {
             count_launch();
-            k_dtrsm_b<TW><<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, k);
+            k_dtrsm_b<TW><<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, k, nullptr);
             count_launch();
             k_dupdate_b<TW><<<(unsigned)np, 256, 0, st>>>(nitems, T, base, work, k);
         }
@@ -740,7 +917,7 @@ cudaError_t prepare_nd_solve(int nsep) {
                                             const int64_t*, const int32_t*, const int32_t*, const int32_t*, TW*,     \
                                             cudaStream_t);                                                           \
     template void launch_dense_cholesky<TW>(int, const std::vector<int32_t>&, const int32_t*, const int64_t*,      \
-                                            const int64_t*, TW*, TW*, int*, cudaStream_t);                           \
+                                            const int64_t*, TW*, TW*, int*, cudaStream_t, TW*, int*);                \
     template void launch_nd_schur_tiles<TW>(int64_t, int64_t, int, int64_t, const double*, const int32_t*,         \
                                             const int32_t*, const int64_t*, const int64_t*, const double*, TW*,      \
                                             cudaStream_t);
