@@ -186,7 +186,8 @@ def run_ours(args):
     for v in variants:
         prec, iface = parse_variant(v)
         am = AlgMortar(P.A, P.n_parts, part_sizes=P.part_sizes, precision=prec, use_graph=True,
-                       check_every=args.check_every, device=local, interface_solve=iface)
+                       check_every=args.check_every, device=local, interface_solve=iface,
+                       autotune=not args.no_autotune)
         handles[v] = am
     host_setup_ms = {k: v.info["setup_ms"]["partition_and_tables"] for k, v in handles.items()}
 
@@ -234,6 +235,8 @@ def run_ours(args):
                      "setup_ms": {k: round(v, 3) for k, v in info["setup_ms"].items()},
                      "stages_ms": {k: round(v, 5) for k, v in stages.items()},
                      "launches_per_step": (info1.kernel_launches - info0.kernel_launches) / args.steps,
+                     "tuned": {"local_solve_variant": info1.tuned_ring, "local_job_order": info1.tuned_job_order,
+                               "vector_ctas_per_sm": info1.tuned_vec_ctas},
                      "factor_bytes": info["factor_bytes"], "n_lambda": info["n_lambda"],
                      "x_host": xr}
         clocks_all[prec] = clk.summary()
@@ -683,6 +686,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--stage-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in launch variants instead of the autotuner's (setup-time) choice")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the smoothing and multi-RHS side measurements")
     ap.add_argument("--mode", default="bench", choices=["bench", "apply", "solve"],

@@ -188,6 +188,9 @@ typedef struct {
                                       device when algmortar_get_info is called)           */
     int32_t tuned_ring;            /* launch variant of the batched local solves in use   */
     int32_t tuned_vec_ctas;        /* CTAs per SM of the PCG vector kernels in use        */
+    int32_t tuned_job_order;       /* local-solve job order in use: 0 rows, 1 stored tiles,
+                                      2 tile rows (each longest first)                    */
+    int32_t pad_;
 } algmortar_info;
 
 typedef struct algmortar_handle algmortar_t;

@@ -57,7 +57,8 @@ class Info(C.Structure):
                 ("factor_entries", C.c_int64), ("factor_bytes", C.c_int64), ("phi_entries", C.c_int64),
                 ("setup_ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("interface_solve", C.c_int32),
                 ("iface_blocks", C.c_int32), ("iface_cluster", C.c_int32), ("iface_staged", C.c_int32),
-                ("iface_last_iterations", C.c_int32), ("tuned_ring", C.c_int32), ("tuned_vec_ctas", C.c_int32)]
+                ("iface_last_iterations", C.c_int32), ("tuned_ring", C.c_int32), ("tuned_vec_ctas", C.c_int32),
+                ("tuned_job_order", C.c_int32), ("pad_", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "setup_ms"}

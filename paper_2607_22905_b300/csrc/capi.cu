@@ -2102,6 +2102,7 @@ int algmortar_get_info(const algmortar_t* h, algmortar_info* info) {
     }
     info->tuned_ring = h->tuned_ring;
     info->tuned_vec_ctas = h->tuned_vec_ctas;
+    info->tuned_job_order = h->tuned_order;
     return 0;
 }
 
