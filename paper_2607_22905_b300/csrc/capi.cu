@@ -112,6 +112,7 @@ struct NumWs {
     int32_t* d_crowsq = nullptr;
     int64_t* d_czerooff = nullptr;
     int64_t n_ginv = 0, n_w = 0;            // entries of the interface inverses Ginv, W
+    std::vector<int64_t> h_gioff, h_woff, h_gioff32, h_woff32;   // host copies of their offsets
     // inexact interface solve: per-subdomain blocks of 1/4 G^T Phi, CSR values of S_eta
     double* pv = nullptr;
     int64_t* d_pv_off = nullptr;
@@ -635,14 +636,31 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         // FP32 / BF16 factor variants also apply the interface inverses in FP32 (FP32
         // copies): half the bytes of the solve, and FP32 products
         float *Ginv32 = nullptr, *Wcm32 = nullptr, *Wrm32 = nullptr;
+        std::vector<int64_t> gioff32(G, 0), woff32(G, 0), gpo32(G, 0);
+        int64_t gi32 = 0, wo32 = 0, pos32 = 0;
+        for (int g = 0; g < G; ++g) {
+            const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
+            const int64_t ng4 = (ng + 3) & ~int64_t(3);
+            gioff32[g] = gi32;
+            woff32[g] = wo32;
+            gpo32[g] = pos32;
+            gi32 += ng * ng4;
+            wo32 += ag * ng4;
+            pos32 += ng4;
+        }
+        const int nsep4 = (nsep + 3) & ~3;
         if (lowp) {
-            Ginv32 = h->alloc<float>((size_t)std::max<int64_t>(gi, 1));
-            Wcm32 = h->alloc<float>((size_t)std::max<int64_t>(wo, 1));
+            Ginv32 = h->alloc<float>((size_t)std::max<int64_t>(gi32, 1));
+            Wcm32 = h->alloc<float>((size_t)std::max<int64_t>(wo32, 1));
             Wrm32 = h->alloc<float>((size_t)std::max<int64_t>(wo, 1));
             if (!Ginv32 || !Wcm32 || !Wrm32) return fail(ALGMORTAR_OOM, "interface group buffers");
         }
         W.n_ginv = gi;
         W.n_w = wo;
+        W.h_gioff = gioff;
+        W.h_woff = woff;
+        W.h_gioff32 = gioff32;
+        W.h_woff32 = woff32;
         // blocks of groups without interior unknowns are never written: keep them zero
         CU(cudaMemsetAsync(W.D, 0, (size_t)std::max<int64_t>(dof, 1) * sizeof(double), h->st));
         // identity right-hand sides of each group (column-major n_g x n_g)
@@ -730,6 +748,24 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         a.Ginv32 = Ginv32;
         a.Wcm32 = Wcm32;
         a.Wrm32 = Wrm32;
+        if (lowp) {
+            std::vector<int32_t> p32(std::max<int64_t>(L, 1), 0);
+            for (int64_t q = 0; q < nin; ++q) p32[q] = (int32_t)(gpo32[row_g[q]] + (q - P.nd_goff[row_g[q]]));
+            for (int t = 0; t < nsep; ++t) p32[nin + t] = (int32_t)(pos32 + t);
+            int64_t *d_gio32 = nullptr, *d_wo32 = nullptr, *d_gpo32 = nullptr;
+            int32_t* d_p32 = nullptr;
+            TRY(upload(h, d_gio32, gioff32));
+            TRY(upload(h, d_wo32, woff32));
+            TRY(upload(h, d_gpo32, gpo32));
+            TRY(upload(h, d_p32, p32));
+            a.gioff32 = d_gio32;
+            a.woff32 = d_wo32;
+            a.gpo32 = d_gpo32;
+            a.p32 = d_p32;
+            a.spo32 = pos32;
+            a.L32 = pos32 + nsep4;
+            a.nsep4 = nsep4;
+        }
 
         // ---- separator Schur complement C as one dense item ----
         if (nsep > 0) {
@@ -773,7 +809,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             if (!W.cwork || !W.cdinv || !W.cf || !W.cb || !W.cE || !Cinv)
                 return fail(ALGMORTAR_OOM, "separator buffers");
             if (lowp) {
-                float* Cinv32 = h->alloc<float>((size_t)nsep * nsep);
+                float* Cinv32 = h->alloc<float>((size_t)nsep * ((nsep + 3) & ~3));
                 if (!Cinv32) return fail(ALGMORTAR_OOM, "separator buffers");
                 a.Cinv32 = Cinv32;
             }
@@ -987,12 +1023,17 @@ int numeric_setup(algmortar_t* h) {
         cudaEventRecord(ev[3], st);
         if (h->opts.precision == ALGMORTAR_FP64) TRY(nd_factor_inverse<double>(h, W, st));
         else TRY(nd_factor_inverse<float>(h, W, st));
-        if (h->nd.Ginv32) {
-            launch_convert<float>(W.n_ginv, h->nd.Ginv, (float*)h->nd.Ginv32, st);
-            launch_convert<float>(W.n_w, h->nd.Wcm, (float*)h->nd.Wcm32, st);
+        if (h->nd.Ginv32) {   // FP32 copies, padded rows (see NdSolveArgs)
+            for (int g = 0; g < G; ++g) {
+                const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g], ag = P.nd_aoff[g + 1] - P.nd_aoff[g];
+                const int64_t ng4 = (ng + 3) & ~int64_t(3);
+                launch_pad_convert(ng, ng, h->nd.Ginv + W.h_gioff[g], ng, (float*)h->nd.Ginv32 + W.h_gioff32[g], ng4,
+                                   st);
+                launch_pad_convert(ag, ng, h->nd.Wcm + W.h_woff[g], ng, (float*)h->nd.Wcm32 + W.h_woff32[g], ng4, st);
+            }
             launch_convert<float>(W.n_w, h->nd.Wrm, (float*)h->nd.Wrm32, st);
         }
-        if (h->nd.Cinv32) launch_convert<float>((int64_t)nsep * nsep, h->nd.Cinv, (float*)h->nd.Cinv32, st);
+        if (h->nd.Cinv32) launch_pad_convert(nsep, nsep, h->nd.Cinv, nsep, (float*)h->nd.Cinv32, h->nd.nsep4, st);
         CU(cudaGetLastError());
         cudaEventRecord(ev[5], st);
     } else {
@@ -1090,7 +1131,7 @@ void stage_restrict(algmortar_t* h, Vecs& v, const ColStrides& cs) {
     // the FP32 interface solve reads an FP32 copy of b_eta, written here with it
     const bool f32 = !h->inexact && h->nd.Ginv32;
     launch_restrict(h->L, h->d_rptr, h->d_rcell, h->d_rcoef, v.pbar, v.beta, h->d_ndpos, cs, v.k,
-                    f32 ? v.f32 : nullptr, v.fl, h->st);
+                    f32 ? v.f32 : nullptr, v.fl, h->nd.p32, h->st);
 }
 int stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
     if (h->L <= 0) return 0;
@@ -1241,7 +1282,13 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     v.sc = h->alloc<PcgScalars>(cap);
     v.gs.part = h->alloc<double>(nb);
     v.gs.ticket = h->alloc<unsigned int>(cap);
-    v.fl = (((int64_t)std::max(h->L, 1) + np + h->P.nd_nsep + 3) / 4) * 4;
+    {   // FP32 side vectors of the interface solve: padded b (groups, separator), c, separator eta
+        int64_t l32 = 0;
+        const Plan& Q = h->P;
+        for (size_t g = 0; g + 1 < Q.nd_goff.size(); ++g) l32 += (Q.nd_goff[g + 1] - Q.nd_goff[g] + 3) & ~int64_t(3);
+        const int64_t ns4 = (Q.nd_nsep + 3) & ~3;
+        v.fl = ((std::max<int64_t>(l32 + ns4, 1) + ns4 + Q.nd_nsep + 3) / 4) * 4;
+    }
     v.f32 = h->alloc<float>((size_t)v.fl * cap);
     v.iits = h->alloc<int32_t>(cap);
     v.iits_total = h->alloc<int64_t>(cap);
@@ -1258,6 +1305,7 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     CU(cudaMemsetAsync(v.sc, 0, cap * sizeof(PcgScalars), h->st));
     CU(cudaMemsetAsync(v.gs.ticket, 0, cap * sizeof(unsigned int), h->st));
     CU(cudaMemsetAsync(v.iits, 0, cap * sizeof(int32_t), h->st));
+    CU(cudaMemsetAsync(v.f32, 0, (size_t)v.fl * cap * sizeof(float), h->st));   // padding stays zero
     CU(cudaMemsetAsync(v.iits_total, 0, cap * sizeof(int64_t), h->st));
     if (h->opts.stage_times && !v.sev_ok) {
         for (cudaEvent_t& e : v.sev) CU(cudaEventCreate(&e));

@@ -125,6 +125,16 @@ struct NdSolveArgs {
     const float* Wcm32 = nullptr;
     const float* Wrm32 = nullptr;
     const float* Cinv32 = nullptr;
+    // FP32 layout: rows of Ginv32, columns of Wcm32 and rows of Cinv32 padded with zeros to
+    // a multiple of 4 floats (16-byte loads); the FP32 right-hand side holds each group's
+    // interior unknowns and then the separator's at 16-byte-aligned positions (zeros between)
+    const int64_t* gioff32 = nullptr;   // G offsets into Ginv32 (row stride n_g rounded up to 4)
+    const int64_t* woff32 = nullptr;    // G offsets into Wcm32 (column stride likewise)
+    const int64_t* gpo32 = nullptr;     // G positions of the groups in the FP32 right-hand side
+    const int32_t* p32 = nullptr;       // ND position -> position in the FP32 right-hand side
+    int64_t spo32 = 0;                  // the separator's position there
+    int64_t L32 = 0;                    // its length
+    int nsep4 = 0;                      // nsep rounded up to 4 (row stride of Cinv32)
 };
 
 // interface system (kernels_coarse.cu)
@@ -161,12 +171,16 @@ template <typename TW>
 void launch_nd_schur_tiles(int64_t ntiles, int64_t L, int nsep, int64_t sep0, const double* Sd, const int32_t* sg,
                            const int32_t* sidx, const int64_t* aoff, const int64_t* doff, const double* D,
                            TW* work, cudaStream_t st);
-// f32: FP32 side vectors for the FP32 copies ([b: L | c: np | separator eta: nsep] per
+// f32: FP32 side vectors for the FP32 copies ([b: L32 | c: nsep4 | separator eta: nsep] per
 // column, column stride fl; null for FP64); b32_ready: the restriction already wrote the
 // FP32 copy of b (else it is converted here)
 void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double* P, float* f32, int64_t fl,
                      bool b32_ready, ColStrides cs, int ncols, cudaStream_t st);
 cudaError_t prepare_nd_solve(int nsep);
+// FP32 copy with zero padding: nlines lines of len doubles (source stride ss) to lines of
+// ds >= len floats
+void launch_pad_convert(int64_t nlines, int64_t len, const double* src, int64_t ss, float* dst, int64_t ds,
+                        cudaStream_t st);
 
 // local factor
 void launch_local_diag(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
@@ -214,7 +228,7 @@ void launch_scatter_cols(int64_t n, int ncols, const int32_t* perm, const double
 void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, double* dst, cudaStream_t st);
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* omap, ColStrides cs, int ncols, float* beta32, int64_t fl,
-                     cudaStream_t st);
+                     const int32_t* p32, cudaStream_t st);
 template <typename TP>
 void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
                     const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,

@@ -630,8 +630,30 @@ __device__ __forceinline__ NdVecs<double> nd_vecs(const NdSolveArgs& a, const do
     return {b, P, eta + a.goff[a.G]};
 }
 __device__ __forceinline__ NdVecs<float> nd_vecs(const NdSolveArgs& a, const double*, double*, double*, float* f32,
-                                                 int64_t L, float) {
-    return {f32, f32 + L, f32 + L + a.np};
+                                                 int64_t, float) {
+    return {f32, f32 + a.L32, f32 + a.L32 + a.nsep4};
+}
+
+// 16-byte-load warp dot product of n4 float4 (FP32 rows and vectors of the padded layout)
+__device__ __forceinline__ float warp_row_dot4(const float4* __restrict__ row, const float4* __restrict__ x,
+                                               int64_t n4, int lane) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int64_t j = lane;
+    for (; j + 96 < n4; j += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 a = row[j + 32 * u], b = x[j + 32 * u];
+            s[u] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, s[u]))));
+        }
+    }
+    for (int u = 0; j < n4; j += 32, ++u) {
+        const float4 a = row[j], b = x[j];
+        s[u & 3] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, s[u & 3]))));
+    }
+    float t = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
 }
 
 // ---------------------------------------------------------------------------------
@@ -651,21 +673,42 @@ __global__ void k_nd_stage1(NdSolveArgs a, const double* __restrict__ b, double*
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t nin = a.goff[a.G];
-    if (wid < nin) {
-        const int g = a.row_g[wid];
-        const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
-        const TM s = warp_row_dot<TM>(M.Ginv + a.gioff[g] + i * ng, V.b + g0, ng, lane);
-        if (lane == 0) eta[wid] = (double)s;
-    } else if (wid < nin + a.nsep) {
-        const int64_t sp = wid - nin;
-        TM c = V.b[nin + sp];
+    if constexpr (std::is_same<TM, float>::value) {   // padded FP32 layout, 16-byte loads
+        if (wid < nin) {
+            const int g = a.row_g[wid];
+            const int64_t g0 = a.goff[g], n4 = (a.goff[g + 1] - g0 + 3) >> 2, i = wid - g0;
+            const float s = warp_row_dot4(reinterpret_cast<const float4*>(M.Ginv + a.gioff32[g] + i * 4 * n4),
+                                          reinterpret_cast<const float4*>(V.b + a.gpo32[g]), n4, lane);
+            if (lane == 0) eta[wid] = (double)s;
+        } else if (wid < nin + a.nsep) {
+            const int64_t sp = wid - nin;
+            float c = V.b[a.spo32 + sp];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int g = a.sg[2 * sp + e];
-            const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = a.sidx[2 * sp + e];
-            c -= warp_row_dot<TM>(M.Wcm + a.woff[g] + j * ng, V.b + g0, ng, lane);
+            for (int e = 0; e < 2; ++e) {
+                const int g = a.sg[2 * sp + e];
+                const int64_t n4 = (a.goff[g + 1] - a.goff[g] + 3) >> 2, j = a.sidx[2 * sp + e];
+                c -= warp_row_dot4(reinterpret_cast<const float4*>(M.Wcm + a.woff32[g] + j * 4 * n4),
+                                   reinterpret_cast<const float4*>(V.b + a.gpo32[g]), n4, lane);
+            }
+            if (lane == 0) V.c[sp] = c;
         }
-        if (lane == 0) V.c[sp] = c;
+    } else {
+        if (wid < nin) {
+            const int g = a.row_g[wid];
+            const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, i = wid - g0;
+            const TM s = warp_row_dot<TM>(M.Ginv + a.gioff[g] + i * ng, V.b + g0, ng, lane);
+            if (lane == 0) eta[wid] = (double)s;
+        } else if (wid < nin + a.nsep) {
+            const int64_t sp = wid - nin;
+            TM c = V.b[nin + sp];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int g = a.sg[2 * sp + e];
+                const int64_t g0 = a.goff[g], ng = a.goff[g + 1] - g0, j = a.sidx[2 * sp + e];
+                c -= warp_row_dot<TM>(M.Wcm + a.woff[g] + j * ng, V.b + g0, ng, lane);
+            }
+            if (lane == 0) V.c[sp] = c;
+        }
     }
 }
 
@@ -683,12 +726,18 @@ __global__ void k_nd_stage2(NdSolveArgs a, const double* __restrict__ b, double*
     TM* cvec = reinterpret_cast<TM*>(cvec_raw);
     const int nsep = a.nsep;
     const int64_t sep0 = a.goff[a.G];
-    for (int s = threadIdx.x; s < nsep; s += blockDim.x) cvec[s] = V.c[s];
+    const int nc = std::is_same<TM, float>::value ? a.nsep4 : nsep;   // FP32: zero-padded
+    for (int s = threadIdx.x; s < nc; s += blockDim.x) cvec[s] = V.c[s];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (wid >= nsep) return;
-    const TM s = warp_row_dot<TM>(M.Cinv + wid * nsep, cvec, nsep, lane);
+    TM s;
+    if constexpr (std::is_same<TM, float>::value)
+        s = warp_row_dot4(reinterpret_cast<const float4*>(M.Cinv + wid * nc), reinterpret_cast<const float4*>(cvec),
+                          nc >> 2, lane);
+    else
+        s = warp_row_dot<TM>(M.Cinv + wid * nsep, cvec, nsep, lane);
     if (lane == 0) {
         eta[sep0 + wid] = (double)s;
         if (!std::is_same<TM, double>::value) V.es[wid] = s;
@@ -733,9 +782,18 @@ __global__ void k_nd_stage3(NdSolveArgs a, double* __restrict__ eta, float* __re
 }
 
 // b -> its FP32 copy (callers whose right-hand side does not come from the restriction)
-__global__ void k_nd_b32(int L, const double* __restrict__ b, float* __restrict__ b32) {
+__global__ void k_nd_b32(int L, const double* __restrict__ b, float* __restrict__ b32, const int32_t* __restrict__ p32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < L) b32[i] = (float)b[i];
+    if (i < L) b32[p32[i]] = (float)b[i];
+}
+
+__global__ void k_pad_convert(int64_t nlines, int64_t len, const double* __restrict__ src, int64_t ss,
+                              float* __restrict__ dst, int64_t ds) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nlines * ds;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = e / ds, j = e - l * ds;
+        dst[e] = j < len ? (float)src[l * ss + j] : 0.0f;
+    }
 }
 
 // ------------------------------------------------------------------------ launchers
@@ -875,7 +933,7 @@ static void nd_solve_t(const NdSolveArgs& a, const double* b, double* eta, doubl
         k_nd_stage1<TM><<<dim3((unsigned)((nin + a.nsep + 7) / 8), ncols), 256, 0, st>>>(a, b, eta, P, f32, fl, cs);
     }
     if (a.nsep > 0) {
-        const size_t smem = (size_t)a.nsep * sizeof(TM);
+        const size_t smem = (size_t)(std::is_same<TM, float>::value ? a.nsep4 : a.nsep) * sizeof(TM);
         count_launch();
         k_nd_stage2<TM><<<dim3((unsigned)((a.nsep + 7) / 8), ncols), 256, smem, st>>>(a, b, eta, P, f32, fl, cs);
         if (nin > 0) {
@@ -891,7 +949,7 @@ void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double*
             const int L = (int)(a.nin + a.nsep);
             for (int c = 0; c < ncols; ++c) {
                 count_launch();
-                k_nd_b32<<<(L + 255) / 256, 256, 0, st>>>(L, b + c * cs.l, f32 + c * fl);
+                k_nd_b32<<<(L + 255) / 256, 256, 0, st>>>(L, b + c * cs.l, f32 + c * fl, a.p32);
             }
         }
         nd_solve_t<float>(a, b, eta, P, f32, fl, cs, ncols, st);
@@ -899,8 +957,16 @@ void launch_nd_solve(const NdSolveArgs& a, const double* b, double* eta, double*
         nd_solve_t<double>(a, b, eta, P, nullptr, 0, cs, ncols, st);
     }
 }
+void launch_pad_convert(int64_t nlines, int64_t len, const double* src, int64_t ss, float* dst, int64_t ds,
+                        cudaStream_t st) {
+    if (nlines > 0 && ds > 0) {
+        count_launch();
+        k_pad_convert<<<(unsigned)std::min<int64_t>((nlines * ds + 255) / 256, 4096), 256, 0, st>>>(nlines, len, src,
+                                                                                                   ss, dst, ds);
+    }
+}
 cudaError_t prepare_nd_solve(int nsep) {
-    size_t smem = (size_t)nsep * sizeof(double);
+    size_t smem = (size_t)(nsep + 3) * sizeof(double);
     if (smem > 48 * 1024) {
         const void* ks[] = {(const void*)k_nd_stage2<double>, (const void*)k_nd_stage2<float>,
                             (const void*)k_nd_stage3<double>, (const void*)k_nd_stage3<float>};

@@ -138,9 +138,11 @@ __global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __
     TW* Wb = work + pf.base[s] * TILE2;
     TW* Db = dinv + r0 * TILE2;
     __shared__ TW X[TILE][TILE + 1];
-    __shared__ TW As[TILE][TILE + 1];
-    __shared__ TW Bs[TILE][TILE + 1];
+    __shared__ TW Ab[2][TILE][TILE + 1];   // the K loop's tiles, double-buffered
+    __shared__ TW Bb[2][TILE][TILE + 1];
     __shared__ int bad;
+    TW(*As)[TILE + 1] = Ab[0];
+    TW(*Bs)[TILE + 1] = Bb[0];
     const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 4;
     if (tid == 0) bad = 0;
     auto tile = [&](int I, int J) { return Wb + (fwd[I] + (J - lo[I])) * TILE2; };
@@ -151,25 +153,53 @@ __global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __
             dst[e & 31][e >> 5] = g[e];
         }
     };
+    // asynchronous element copies into the same transposed, padded layout: the tiles of
+    // step K + 1 load while step K multiplies (the chain of a large subdomain otherwise
+    // waits one global round trip per step)
+    auto load_async = [&](TW(*dst)[TILE + 1], const TW* g) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = tid + 256 * q;
+            if constexpr (sizeof(TW) == 8)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&dst[e & 31][e >> 5])),
+                             "l"(g + e) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(&dst[e & 31][e >> 5])),
+                             "l"(g + e) : "memory");
+        }
+    };
     for (int I = 0; I < T; ++I) {
         const int li = lo[I];
         for (int J = li; J <= I; ++J) {
             const TW* Aij = tile(I, J);
             TW acc[4];
+            const int k0 = max(li, lo[J]);
+            if (k0 < J) {
+                load_async(Ab[0], tile(I, k0));
+                load_async(Bb[0], tile(J, k0));
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[q] = Aij[c * TILE + rb + q];
-            const int k0 = max(li, lo[J]);
+            int kb = 0;
             for (int K = k0; K < J; ++K) {
-                load(As, tile(I, K));
-                load(Bs, tile(J, K));
+                if (K + 1 < J) {
+                    load_async(Ab[kb ^ 1], tile(I, K + 1));
+                    load_async(Bb[kb ^ 1], tile(J, K + 1));
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                } else {
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                }
                 __syncthreads();
 #pragma unroll 8
                 for (int t = 0; t < TILE; ++t) {
-                    TW b = Bs[c][t];
+                    TW b = Bb[kb][c][t];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] -= As[rb + q][t] * b;
+                    for (int q = 0; q < 4; ++q) acc[q] -= Ab[kb][rb + q][t] * b;
                 }
-                __syncthreads();
+                __syncthreads();   // before buffer kb is refilled
+                kb ^= 1;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) X[rb + q][c] = acc[q];

@@ -76,7 +76,7 @@ __global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ idx, con
 __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_t* __restrict__ rcell,
                            const double* __restrict__ rcoef, const double* __restrict__ pbar,
                            double* __restrict__ beta, const int32_t* __restrict__ omap, ColStrides cs,
-                           float* __restrict__ beta32, int64_t fl) {
+                           float* __restrict__ beta32, int64_t fl, const int32_t* __restrict__ p32) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     pbar += col * cs.v;
@@ -92,7 +92,7 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     if (lane == 0) {
         const int o = omap ? omap[I] : I;
         beta[o] = s;
-        if (beta32) beta32[o] = (float)s;   // the FP32 interface solve's copy
+        if (beta32) beta32[p32 ? p32[o] : o] = (float)s;   // the FP32 interface solve's copy
     }
 }
 
@@ -608,10 +608,11 @@ void launch_scatter_cols(int64_t n, int ncols, const int32_t* perm, const double
 }
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* omap, ColStrides cs, int ncols, float* beta32, int64_t fl,
-                     cudaStream_t st) {
+                     const int32_t* p32, cudaStream_t st) {
     if (L > 0) {
         count_launch();
-        k_restrict<<<dim3((L + 7) / 8, ncols), 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, cs, beta32, fl);
+        k_restrict<<<dim3((L + 7) / 8, ncols), 256, 0, st>>>(L, rptr, rcell, rcoef, pbar, beta, omap, cs, beta32, fl,
+                                                             p32);
     }
 }
 template <typename TP>

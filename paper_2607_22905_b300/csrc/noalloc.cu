@@ -51,7 +51,7 @@ int interface_solve_noalloc(int device, cudaStream_t st, int L, const NdSolveArg
     if (L == 0) return ALGMORTAR_OK;
     // FP64 b, eta and P; with FP32 interface inverses also their FP32 side vectors
     const bool f32 = nd.Ginv32 || nd.Cinv32;
-    const int64_t fl = f32 ? (((int64_t)L + nd.np + nd.nsep + 3) / 4) * 4 : 0;
+    const int64_t fl = f32 ? ((nd.L32 + nd.nsep4 + nd.nsep + 3) / 4) * 4 : 0;
     const int64_t need = 2 * (int64_t)L + nd.np + fl / 2 + 1;
     if (need > kNoAllocScratchDoubles) {
         err = "interface_solve_noalloc: needs " + std::to_string(need) + " doubles of scratch, the static array holds " +
