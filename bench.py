@@ -105,10 +105,21 @@ class Clocks:
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.n0 = 0
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                       "-lms", "50", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a moment to start: wait for its first sample, so that the
+            # samples taken after it (rows n0 onwards) all fall inside the timed region
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.p.poll() is None:
+                self.f.flush()
+                if os.path.getsize(self.f.name) > 0:
+                    break
+                time.sleep(0.02)
+            with open(self.f.name) as fh:
+                self.n0 = sum(1 for _ in fh)
         except Exception:
             self.p = None
         return self
@@ -132,6 +143,8 @@ class Clocks:
         except Exception:
             pass
         os.unlink(self.f.name)
+        if len(rows) > self.n0:
+            rows = rows[self.n0:]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

@@ -160,8 +160,10 @@ struct algmortar_handle {
     int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_perm = nullptr, *d_row_sub = nullptr;
     double* d_val = nullptr;
     int64_t* d_sub_off = nullptr;
-    int nchunks = 0;                   // prolongation: row chunks (<= VEC_BS rows of one subdomain)
-    int32_t *d_chunk_sub = nullptr, *d_chunk_off = nullptr;
+    int nchunks = 0;                   // prolongation: row chunks (<= 32 rows of one subdomain)
+    ProlongChunk* d_chunks = nullptr;
+    int64_t* d_prm_off = nullptr;      // row-major panels (prolongation): start of subdomain i
+    int64_t nprm = 0;                  // entries of the row-major panels
     // local factor profile and streams
     Profile pf{};
     int32_t *d_rows = nullptr, *d_ntiles = nullptr;
@@ -522,7 +524,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         h->d_bwdS2 = h->alloc<TS>((size_t)tiles * TILE2);
         if (!h->d_fwdS2 || !h->d_bwdS2) return fail(ALGMORTAR_OOM, "smoother factor buffers");
     }
-    h->d_phi = std::is_same<TS, double>::value ? (void*)W.phi64 : (void*)h->alloc<PanelT<TS>>(nphi);
+    h->d_phi = (void*)h->alloc<PanelT<TS>>((size_t)std::max<int64_t>(h->nprm, 1));   // row-major (prolongation)
     if (!W.work || !W.dinv || !W.d_err || !W.rhs || !W.phi64 || !h->d_fwdS || !h->d_bwdS || !h->d_phi)
         return fail(ALGMORTAR_OOM, "factor / MBF buffers");
     if (L > 0 && h->inexact) {
@@ -970,7 +972,8 @@ int numeric_setup(algmortar_t* h) {
         a.err = h->d_kerr;
         TRY((solve_cols<TS, TA>(a, W.bj_mbf, false, P.max_tiles, st)));
     }
-    if (!std::is_same<TS, double>::value) launch_convert<PanelT<TS>>(nphi, W.phi64, (PanelT<TS>*)h->d_phi, st);
+    launch_panel_rows<PanelT<TS>>(m, h->d_sub_off, h->d_phi_off, h->d_if_off, h->d_prm_off, W.phi64,
+                                  (PanelT<TS>*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
     // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg),
     //     solved exactly by one level of nested dissection (kernels_coarse.cu) ---
@@ -1151,9 +1154,8 @@ int stage_coarse(algmortar_t* h, Vecs& v, const ColStrides& cs) {
 template <typename TS>
 void stage_prolong(algmortar_t* h, Vecs& v, const double* r, double* z, const ColStrides& cs, PcgScalars* sc,
                    const double* base = nullptr) {
-    launch_prolong<TS>(h->nchunks, h->d_chunk_sub, h->d_chunk_off, h->P.max_k, h->d_sub_off, h->d_if_off,
-                       h->L > 0 ? h->d_ifpos : h->d_if_list, h->d_phi_off, (const TS*)h->d_phi, v.eta, v.pbar, base,
-                       z, r, v.gs, sc, cs, v.k, h->st);
+    launch_prolong<TS>(h->nchunks, h->d_chunks, h->L > 0 ? h->d_ifpos : h->d_if_list, (const TS*)h->d_phi, v.eta,
+                       v.pbar, base, z, r, v.gs, sc, cs, v.k, h->st);
 }
 
 template <typename TS, typename TA>
@@ -1265,8 +1267,8 @@ int alloc_vecs(algmortar_t* h, Vecs& v, int cap) {
     const size_t l = (size_t)std::max(h->L, 1) * cap;
     const int64_t np = h->P.nd_aoff.empty() ? 1 : std::max<int64_t>(h->P.nd_aoff.back(), 1);
     // grid-sum partials: two per CTA (flexible beta) of the widest grid (vector kernels or
-    // one CTA per row chunk of a subdomain)
-    const size_t nb = 2 * (size_t)std::max(vec_blocks(h->n), h->nchunks) * cap;
+    // the prolongation's warp-per-chunk grid)
+    const size_t nb = 2 * (size_t)std::max(vec_blocks(h->n), prolong_blocks(h->nchunks)) * cap;
     v.x = h->alloc<double>(n);
     v.r = h->alloc<double>(n);
     v.z = h->alloc<double>(n);
@@ -1739,15 +1741,30 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     rc = rc ? rc : upload(h, h->d_row_sub, P.row_sub);
     rc = rc ? rc : upload(h, h->d_sub_off, P.sub_off);
     {
-        std::vector<int32_t> cs, co;
-        for (int s = 0; s < P.m; ++s)
-            for (int64_t o = 0; o < P.sub_off[s + 1] - P.sub_off[s]; o += VEC_BS) {
-                cs.push_back(s);
-                co.push_back((int32_t)o);
+        // row-major panels padded to 16-byte rows (4 FP32 or 2 FP64 entries)
+        const int vw = h->opts.precision == ALGMORTAR_FP64 ? 2 : 4;
+        std::vector<ProlongChunk> ch;
+        std::vector<int64_t> prm(P.m + 1, 0);
+        for (int s = 0; s < P.m; ++s) {
+            const int64_t ns = P.sub_off[s + 1] - P.sub_off[s];
+            const int32_t kk = (int32_t)(P.if_off[s + 1] - P.if_off[s]);
+            const int32_t ld = (kk + vw - 1) / vw * vw;
+            for (int64_t o = 0; o < ns; o += 32) {
+                ProlongChunk c;
+                c.row0 = P.sub_off[s] + o;
+                c.phi0 = prm[s] + o * ld;
+                c.ld = ld;
+                c.nrow = (int32_t)std::min<int64_t>(32, ns - o);
+                c.i0 = (int32_t)P.if_off[s];
+                c.kk = kk;
+                ch.push_back(c);
             }
-        h->nchunks = (int)cs.size();
-        rc = rc ? rc : upload(h, h->d_chunk_sub, cs);
-        rc = rc ? rc : upload(h, h->d_chunk_off, co);
+            prm[s + 1] = prm[s] + ns * ld;
+        }
+        h->nchunks = (int)ch.size();
+        h->nprm = prm[P.m];
+        rc = rc ? rc : upload(h, h->d_chunks, ch);
+        rc = rc ? rc : upload(h, h->d_prm_off, prm);
     }
     rc = rc ? rc : upload(h, h->d_rows, rows);
     rc = rc ? rc : upload(h, h->d_ntiles, P.ntiles);

@@ -229,11 +229,27 @@ void launch_scatter_values(int64_t n, const int64_t* idx, const double* v, doubl
 void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const double* rcoef, const double* pbar,
                      double* beta, const int32_t* omap, ColStrides cs, int ncols, float* beta32, int64_t fl,
                      const int32_t* p32, cudaStream_t st);
+// One prolongation work item: up to 32 consecutive rows of one subdomain i (one warp).
+// The prolongation reads the MBF panels of subdomain i row-major: row k's k_i entries
+// p_hat^(m)_k are contiguous, padded with zeros to ld = k_i rounded up to 16 bytes.
+struct __align__(16) ProlongChunk {
+    int64_t row0;   // first row (subdomain-contiguous numbering)
+    int64_t phi0;   // offset of the first row's panel entries in the row-major panels
+    int32_t ld;     // panel entries per row (k_i padded to a multiple of 16 bytes)
+    int32_t nrow;   // rows in this chunk, 1..32
+    int32_t i0;     // first entry of subdomain i in the interface list
+    int32_t kk;     // interfaces of subdomain i
+};
 template <typename TP>
-void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
-                    const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,
-                    const TP* phi, const double* eta, const double* pbar, const double* base, double* z,
-                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
+void launch_prolong(int nchunks, const ProlongChunk* chunks, const int32_t* if_list, const TP* phi,
+                    const double* eta, const double* pbar, const double* base, double* z, const double* r,
+                    GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
+// Row-major padded copy (layout of ProlongChunk) of the column-major FP64 panels phi
+// (subdomain i's column m at phi_off[i] + m n_i); prm_off[i] = start of subdomain i's rows.
+template <typename TP>
+void launch_panel_rows(int m, const int64_t* sub_off, const int64_t* phi_off, const int64_t* if_off,
+                       const int64_t* prm_off, const double* phi, TP* out, cudaStream_t st);
+int prolong_blocks(int nchunks);   // CTAs of launch_prolong (<= vec_blocks of the widest vector)
 void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
                             const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
                             cudaStream_t st);

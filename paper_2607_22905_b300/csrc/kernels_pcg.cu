@@ -96,34 +96,43 @@ __global__ void k_restrict(int L, const int64_t* __restrict__ rptr, const int32_
     }
 }
 
-// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg), one CTA
-// per chunk of up to VEC_BS rows of one subdomain i (chunk_sub / chunk_off), one row per
-// thread.  The CTA stages the subdomain's k_i interface values eta_m in shared memory;
-// each thread then issues its k_i panel loads (column-major panel: a warp reads 32
-// consecutive rows of one column) with no dependent index loads.  Inside PCG (`psc`
-// given) also rho = r . z and, in the CTA that completes it, the next beta (one thread:
-// scalar FP64 divisions stay off the per-row path, B300's FP64 pipe being ~1/64 of its
-// FP32 rate).
+// z_k = pbar_k + sum_{m in I_i} eta_m p_hat_i^(m)_k  (Eq. p-decomposition-alg).  One warp
+// per chunk of <= 32 rows of one subdomain i, one row per lane, chunks grid-strided over
+// the warps.  The panels are read row-major (ProlongChunk): lane k loads its row's k_i
+// entries as 16-byte vectors, so a warp streams one contiguous block of the panel array.
+// Lane c holds the interface values eta_m of list entries c and c + 32 and passes them
+// to the products by shuffles, so warps never wait on one another; the next chunk's
+// descriptor and interface indices are loaded while the current chunk's loads are in
+// flight.  Inside PCG (`psc` given) also rho = r . z and, in the CTA that completes it,
+// the next beta (one thread: scalar FP64 divisions stay off the per-row path, B300's
+// FP64 pipe being ~1/64 of its FP32 rate).
 template <typename TP>
-__global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ chunk_sub,
-                                                     const int32_t* __restrict__ chunk_off,
-                                                     const int64_t* __restrict__ sub_off,
-                                                     const int64_t* __restrict__ if_off,
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+};
+
+template <typename TP>
+__global__ void __launch_bounds__(VEC_BS) k_prolong(const ProlongChunk* __restrict__ chunks, int nchunks,
                                                      const int32_t* __restrict__ if_list,
-                                                     const int64_t* __restrict__ phi_off,
                                                      const TP* __restrict__ phi, const double* __restrict__ eta,
                                                      const double* __restrict__ pbar,
                                                      const double* base, double* z,   // may alias
                                                      const double* __restrict__ r, GridSum gs,
-                                                     PcgScalars* psc, ColStrides cs, int nchunks) {
+                                                     PcgScalars* psc, ColStrides cs) {
     // the correction sum_m eta_m p_hat^(m) is accumulated in the panel's arithmetic
     // (FP64 panels: FP64; FP32 panels: FP32), then added to pbar in FP64
-    using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
+    using TV = typename Vec16<TP>::T;
+    constexpr int VW = 16 / sizeof(TP);   // entries per vector
+    constexpr int NV = 24 / VW;           // vectors per row loaded before the first product
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
     __shared__ double sh[32];
-    extern __shared__ unsigned char e_raw[];
-    TA* e = reinterpret_cast<TA*>(e_raw);
     eta += col * cs.l;
     pbar += col * cs.v;
     z += col * cs.v;
@@ -132,53 +141,127 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const int32_t* __restrict__ 
     if (psc) psc += col;
     gs.part += col * gridDim.x;
     gs.ticket += col;
-    // CTAs loop over the row chunks: the grid is capped at the vector kernels' size (one
-    // wave), since every CTA's arrival at the grid-wide sum below (partial, fence, atomic)
-    // delays its retirement -- with one CTA per chunk (~5000 at config 3, four waves) the
-    // stage took 53 us instead of 43 us on B300
+    const int lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int ws = gridDim.x * nw;
+    int ch = blockIdx.x * nw + (threadIdx.x >> 5);
     double acc = 0.0;
-    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int s = chunk_sub[ch];
-    const int64_t a0 = sub_off[s];
-    const int ns = (int)(sub_off[s + 1] - a0);
-    const int64_t i0 = if_off[s];
-    const int kk = (int)(if_off[s + 1] - i0);
-    const int i = chunk_off[ch] + threadIdx.x;
-    const bool row = i < ns;
-    // the row's operands and its first KP panel entries are loaded before the CTA waits
-    // for the interface values (gathered through if_list), so both latencies overlap
-    constexpr int KP = 16;
-    const TP* ph = phi + phi_off[s] + i;
-    TA pv[KP];
-#pragma unroll
-    for (int c = 0; c < KP; ++c) pv[c] = (row && c < kk) ? ldf<TA>(ph + (int64_t)c * ns) : (TA)0;
-    const double pb = row ? pbar[a0 + i] : 0.0;
-    const double bs = (row && base) ? base[a0 + i] : 0.0;
-    const double rv = (row && psc) ? r[a0 + i] : 0.0;
-    for (int c = threadIdx.x; c < kk; c += blockDim.x) e[c] = (TA)eta[if_list[i0 + c]];
-    __syncthreads();
-    if (row) {
-        TA c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-#pragma unroll
-        for (int c = 0; c < KP; c += 4) {
-            if (c < kk) c0 += pv[c] * e[c];
-            if (c + 1 < kk) c1 += pv[c + 1] * e[c + 1];
-            if (c + 2 < kk) c2 += pv[c + 2] * e[c + 2];
-            if (c + 3 < kk) c3 += pv[c + 3] * e[c + 3];
-        }
-        for (int c = KP; c < kk; ++c) c0 += ldf<TA>(ph + (int64_t)c * ns) * e[c];
-        double v = pb + (double)((c0 + c1) + (c2 + c3));
-        if (base) v += bs;   // smoothed application: x + M^{-1} (r - A x)
-        z[a0 + i] = v;
-        if (psc) acc += rv * v;
+    ProlongChunk cur{};
+    int ia = -1, ib = -1;   // interface positions of list entries lane, lane + 32
+    if (ch < nchunks) {
+        cur = chunks[ch];
+        if (lane < cur.kk) ia = if_list[cur.i0 + lane];
+        if (lane + 32 < cur.kk) ib = if_list[cur.i0 + lane + 32];
     }
-    __syncthreads();   // e is refilled by the next chunk
+    for (; ch < nchunks; ch += ws) {
+        const int kk = cur.kk;   // warp-uniform, as is every field of cur
+        const int i0 = cur.i0;
+        const int nv = (kk + VW - 1) / VW;
+        const bool row = lane < cur.nrow;
+        const TP* ph = phi + cur.phi0 + (int64_t)lane * cur.ld;
+        TV pv[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            if (row && j < nv) {
+                pv[j] = *reinterpret_cast<const TV*>(ph + j * VW);
+            } else {
+                TP* q = reinterpret_cast<TP*>(&pv[j]);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) q[u] = (TP)0;
+            }
+        }
+        const int64_t g = cur.row0 + lane;
+        const double pb = row ? pbar[g] : 0.0;
+        const double bs = (row && base) ? base[g] : 0.0;
+        const double rv = (row && psc) ? r[g] : 0.0;
+        // entries past k_i: zero panel padding times a zero interface value
+        const TP ea = ia >= 0 ? (TP)eta[ia] : (TP)0;
+        const TP eb = ib >= 0 ? (TP)eta[ib] : (TP)0;
+        // the next chunk's descriptor and indices, overlapping the loads above
+        const int nx = ch + ws;
+        if (nx < nchunks) {
+            cur = chunks[nx];
+            ia = lane < cur.kk ? if_list[cur.i0 + lane] : -1;
+            ib = lane + 32 < cur.kk ? if_list[cur.i0 + lane + 32] : -1;
+        }
+        TP a4[4] = {(TP)0, (TP)0, (TP)0, (TP)0};
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            if (j < nv) {
+                const TP* q = reinterpret_cast<const TP*>(&pv[j]);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) a4[(j * VW + u) & 3] += q[u] * __shfl_sync(0xffffffffu, ea, j * VW + u);
+            }
+        }
+        for (int j = NV; j < nv; ++j) {
+            TV w;
+            if (row) {
+                w = *reinterpret_cast<const TV*>(ph + j * VW);
+            } else {
+                TP* q = reinterpret_cast<TP*>(&w);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) q[u] = (TP)0;
+            }
+            const TP* q = reinterpret_cast<const TP*>(&w);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                const int c = j * VW + u;
+                TP ev;
+                if (c < 64) {
+                    ev = __shfl_sync(0xffffffffu, c < 32 ? ea : eb, c & 31);
+                } else {
+                    // subdomains with more than 64 interfaces: values beyond from global memory
+                    ev = c < kk ? (TP)eta[if_list[i0 + c]] : (TP)0;
+                }
+                a4[u & 3] += q[u] * ev;
+            }
+        }
+        if (row) {
+            double v = pb + (double)((a4[0] + a4[1]) + (a4[2] + a4[3]));
+            if (base) v += bs;   // smoothed application: x + M^{-1} (r - A x)
+            z[g] = v;
+            if (psc) acc += rv * v;
+        }
     }
     if (psc && grid_sum(acc, sh, gs, &psc->rz_next) && threadIdx.x == 0) {
         const double rn = psc->rz_next;
         psc->beta = (psc->iter == 0 || psc->restart)
                         ? 0.0
                         : (psc->flexible ? (rn - psc->rz_mix) / psc->rz : rn / psc->rz);
+    }
+}
+
+// Row-major copy of subdomain blockIdx.x's column-major FP64 panels (layout of
+// ProlongChunk), through a 32-row x 64-column shared-memory tile: column reads and row
+// writes are both coalesced.
+template <typename TP>
+__global__ void __launch_bounds__(256) k_panel_rows(const int64_t* __restrict__ sub_off,
+                                                    const int64_t* __restrict__ phi_off,
+                                                    const int64_t* __restrict__ if_off,
+                                                    const int64_t* __restrict__ prm_off,
+                                                    const double* __restrict__ phi, TP* __restrict__ out) {
+    constexpr int VW = 16 / sizeof(TP);
+    __shared__ TP tile[32][65];
+    const int s = blockIdx.x;
+    const int64_t ns = sub_off[s + 1] - sub_off[s];
+    const int kk = (int)(if_off[s + 1] - if_off[s]);
+    const int ld = (kk + VW - 1) / VW * VW;
+    const double* src = phi + phi_off[s];
+    TP* dst = out + prm_off[s];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int64_t r0 = 0; r0 < ns; r0 += 32) {
+        const int nr = (int)(ns - r0 < 32 ? ns - r0 : 32);
+        for (int c0 = 0; c0 < ld; c0 += 64) {
+            const int nc = ld - c0 < 64 ? ld - c0 : 64;
+            for (int c = w; c < nc; c += nwarp)
+                tile[lane][c] = (lane < nr && c0 + c < kk) ? (TP)src[(int64_t)(c0 + c) * ns + r0 + lane] : (TP)0;
+            __syncthreads();
+            for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) {
+                const int rr = t / nc, c = t - rr * nc;
+                dst[(r0 + rr) * ld + c0 + c] = tile[rr][c];
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -615,16 +698,42 @@ void launch_restrict(int L, const int64_t* rptr, const int32_t* rcell, const dou
                                                              p32);
     }
 }
+// CTAs of the prolongation: one wave at the kernel's occupancy (every CTA's arrival at
+// the grid-wide sum delays its retirement, so extra waves cost), at most one warp per
+// chunk and at most vec_blocks of the widest vector (the GridSum partials).
+static int g_prolong_ctas_per_sm[2] = {0, 0};
 template <typename TP>
-void launch_prolong(int nchunks, const int32_t* chunk_sub, const int32_t* chunk_off, int max_k,
-                    const int64_t* sub_off, const int64_t* if_off, const int32_t* if_list, const int64_t* phi_off,
-                    const TP* phi, const double* eta, const double* pbar, const double* base, double* z,
-                    const double* r, GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
-    using TA = typename std::conditional<sizeof(TP) == 8, double, float>::type;
+static int prolong_ctas_per_sm() {
+    int& c = g_prolong_ctas_per_sm[sizeof(TP) == 8 ? 1 : 0];
+    if (c == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_prolong<TP>, VEC_BS, 0) != cudaSuccess || b < 1)
+            b = 1;
+        c = b;
+    }
+    return c;
+}
+int prolong_blocks(int nchunks) {
+    const int64_t want = ((int64_t)nchunks + (VEC_BS / 32) - 1) / (VEC_BS / 32);
+    return vec_blocks(want * VEC_BS);
+}
+template <typename TP>
+void launch_prolong(int nchunks, const ProlongChunk* chunks, const int32_t* if_list, const TP* phi,
+                    const double* eta, const double* pbar, const double* base, double* z, const double* r,
+                    GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st) {
     count_launch();
-    const int g = nchunks < g_max_vec_blocks ? nchunks : g_max_vec_blocks;
-    k_prolong<TP><<<dim3(g > 0 ? g : 1, ncols), VEC_BS, (size_t)(max_k > 0 ? max_k : 1) * sizeof(TA), st>>>(
-        chunk_sub, chunk_off, sub_off, if_off, if_list, phi_off, phi, eta, pbar, base, z, r, gs, sc, cs, nchunks);
+    int g = prolong_blocks(nchunks);
+    const int cap = prolong_ctas_per_sm<TP>() * g_sms;
+    if (g > cap) g = cap;
+    k_prolong<TP><<<dim3(g > 0 ? g : 1, ncols), VEC_BS, 0, st>>>(chunks, nchunks, if_list, phi, eta, pbar, base, z,
+                                                                  r, gs, sc, cs);
+}
+template <typename TP>
+void launch_panel_rows(int m, const int64_t* sub_off, const int64_t* phi_off, const int64_t* if_off,
+                       const int64_t* prm_off, const double* phi, TP* out, cudaStream_t st) {
+    if (m <= 0) return;
+    count_launch();
+    k_panel_rows<TP><<<m, 256, 0, st>>>(sub_off, phi_off, if_off, prm_off, phi, out);
 }
 void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
                             const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
@@ -697,10 +806,14 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
 }
 
 #define INST_PROLONG(TP)                                                                                     \
-    template void launch_prolong<TP>(int, const int32_t*, const int32_t*, int, const int64_t*, const int64_t*,    \
-                                     const int32_t*, const int64_t*, const TP*, const double*, const double*,     \
-                                     const double*, double*, const double*, GridSum, PcgScalars*, ColStrides,     \
-                                     int, cudaStream_t);
+    template void launch_prolong<TP>(int, const ProlongChunk*, const int32_t*, const TP*, const double*,         \
+                                     const double*, const double*, double*, const double*, GridSum, PcgScalars*, \
+                                     ColStrides, int, cudaStream_t);
+#define INST_PANEL_ROWS(TP)                                                                                  \
+    template void launch_panel_rows<TP>(int, const int64_t*, const int64_t*, const int64_t*, const int64_t*,    \
+                                        const double*, TP*, cudaStream_t);
+INST_PANEL_ROWS(double)
+INST_PANEL_ROWS(float)
 INST_PROLONG(double)
 INST_PROLONG(float)
 

@@ -431,11 +431,21 @@ def _pair_edge_cases():
     A4, f4 = synth.tpfa_cartesian(np.exp(synth.gaussian_field((12, 10, 3), 3.0, 1.0, 6)), bc_axis=0)
     lab4 = np.zeros(A4.shape[0], dtype=np.int32)
     lab4[0] = 1
+    # a hub subdomain (the middle row of a 70 x 21 grid) with 70 neighbours: more
+    # interfaces than the prolongation holds in lane registers (64)
+    K5 = np.exp(synth.gaussian_field((70, 21, 1), 3.0, 1.0, 8))
+    A5, f5 = synth.tpfa_cartesian(K5, bc_axis=0)
+    idx5 = synth.cell_index(K5.shape)
+    lab5 = np.empty(A5.shape[0], dtype=np.int32)
+    for x in range(70):
+        for y in range(21):
+            lab5[idx5[x, y, 0]] = 0 if y == 10 else (1 + x // 2 if y < 10 else 36 + x // 2)
     return {"checkerboard": (A1, f1, chk, None), "tiny_parts": (A2, f2, None, [20, 45, 90, 150]),
-            "chain": (A3, f3, None, [350, 350]), "one_cell_part": (A4, f4, lab4, None)}
+            "chain": (A3, f3, None, [350, 350]), "one_cell_part": (A4, f4, lab4, None),
+            "hub_70_interfaces": (A5, f5, lab5, None)}
 
 
-@pytest.mark.parametrize("name", ["checkerboard", "tiny_parts", "chain", "one_cell_part"])
+@pytest.mark.parametrize("name", ["checkerboard", "tiny_parts", "chain", "one_cell_part", "hub_70_interfaces"])
 def test_pair_chain_edge_profiles(name):
     """Edge cases of the paired tile rows (FP32/BF16): chains of 1-5 tile rows (odd counts
     end on a single row), and diagonal local blocks (no near, far or coupling tiles).
@@ -453,6 +463,11 @@ def test_pair_chain_edge_profiles(name):
     # condition of the diagonally scaled local blocks (the factored matrices)
     kappa = max(np.linalg.cond(Ai.toarray() / np.sqrt(np.outer(Ai.diagonal(), Ai.diagonal())))
                 for Ai in pc.A_loc)
+    # a relative perturbation of S_eta (built from the low-precision MBFs) reaches eta
+    # amplified by the condition of the scaled interface matrix
+    if pc.S.size:
+        d = np.sqrt(np.diag(pc.S))
+        kappa *= max(1.0, float(np.linalg.cond(pc.S / np.outer(d, d))))
     rng = np.random.default_rng(77)
     r, s2 = rng.standard_normal((2, A.shape[0]))
     z_ref = oa.apply(pc, r)
@@ -462,9 +477,9 @@ def test_pair_chain_edge_profiles(name):
         if prec == "fp64":
             assert rel(z, z_ref) <= 1e-10
         else:
-            # low-precision factors perturb the preconditioner by ~cond(A_i) * unit
-            # roundoff (FP32 2^-24, BF16 2^-9): compared where that leaves the comparison
-            # meaningful (bounds of test_pcg_low_precision_factors)
+            # low-precision factors perturb the preconditioner by ~cond(A_i) cond(S_eta) *
+            # unit roundoff (FP32 2^-24, BF16 2^-9): compared where that leaves the
+            # comparison meaningful (bounds of test_pcg_low_precision_factors)
             u, bound = (2.0 ** -24, 2e-3) if prec == "fp32" else (2.0 ** -9, 1e-1)
             if 4 * kappa * u <= bound:
                 assert rel(z, z_ref) <= bound
