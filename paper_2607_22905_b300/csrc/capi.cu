@@ -163,6 +163,7 @@ struct algmortar_handle {
     int nchunks = 0;                   // prolongation: row chunks (<= 32 rows of one subdomain)
     ProlongChunk* d_chunks = nullptr;
     int64_t* d_prm_off = nullptr;      // row-major panels (prolongation): start of subdomain i
+    int tile_wm = 1;                   // widest tile row of the local profiles (tiles)
     int64_t nprm = 0;                  // entries of the row-major panels
     // local factor profile and streams
     Profile pf{};
@@ -935,7 +936,7 @@ int numeric_setup(algmortar_t* h) {
                       h->d_sc, h->d_sc32, st);
     launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf, h->d_dloc,
                              h->d_sc, work, m, st);
-    launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
+    launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, h->tile_wm, st);
     CU(cudaGetLastError());
     TRY(read_err_flag(h, W.d_err, "local"));
     launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS, (TS*)h->d_bwdS, st);
@@ -948,7 +949,7 @@ int numeric_setup(algmortar_t* h) {
                           h->d_sc2, h->d_sc2_32, st);
         launch_scatter_local<TW>(h->n, h->d_rowptr, h->d_col, h->d_val, h->d_row_sub, h->d_sub_off, h->pf,
                                  h->d_dloc2, h->d_sc2, work, m, st);
-        launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, st);
+        launch_tile_chol<TW>(m, h->pf, h->d_job_sub, work, dinv, W.d_err, h->tile_wm, st);
         CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "smoother block"));
         launch_finalize<TW, TS>(m, h->pf, work, dinv, (TS*)h->d_fwdS2, (TS*)h->d_bwdS2, st);
@@ -1763,6 +1764,9 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         }
         h->nchunks = (int)ch.size();
         h->nprm = prm[P.m];
+        for (int s = 0; s < P.m; ++s)
+            for (int I = 0; I < P.ntiles[s]; ++I)
+                h->tile_wm = std::max(h->tile_wm, I - P.t_lo[P.trow_off[s] + I] + 1);
         rc = rc ? rc : upload(h, h->d_chunks, ch);
         rc = rc ? rc : upload(h, h->d_prm_off, prm);
     }

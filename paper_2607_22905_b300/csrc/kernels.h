@@ -192,8 +192,9 @@ void launch_scatter_local(int64_t n, const int32_t* rowptr, const int32_t* col, 
                           const double* dloc, const double* sc, TW* work, int nitems, cudaStream_t st);
 template <typename TW>
 void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st);
+// wm: widest tile row over all items, max_I (I - lo(I) + 1)
 template <typename TW>
-void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
+void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err, int wm,
                       cudaStream_t st);
 template <typename TW, typename TS>
 void launch_finalize(int nitems, const Profile& pf, const TW* work, const TW* dinv, TS* fwdS, TS* bwdS,

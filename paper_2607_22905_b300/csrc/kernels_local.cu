@@ -236,6 +236,190 @@ __global__ void __launch_bounds__(256) k_tile_chol(Profile pf, const int32_t* __
 
 
 // ---------------------------------------------------------------------------------
+// The same factorization with the current tile row resident in shared memory: one CTA
+// (4 warps) per item; thread (lane c, warp w) owns the 8 entries (8w .. 8w+7, c) of every
+// tile it computes.  For tile (I, J) the CTA
+//   1. copies row J's tiles L_J,k0 .. L_J,J-1 (one contiguous block of the work array)
+//      and L_JJ^{-1} into shared memory with 16-byte asynchronous copies (J < I), while
+//      each thread loads its 8 entries of A_IJ;
+//   2. subtracts sum_K L_IK L_JK^T, the L_IK from the resident row (no reloads);
+//   3. J < I: L_IJ = X L_JJ^{-T} (X staged in shared memory), stored to the work array
+//      and to the resident row; J = I: one warp factors X (row `lane` in registers,
+//      pivots by shuffles) and inverts the factor by forward substitution on all 32
+//      right-hand sides at once, then writes L_II and L_II^{-1}.
+// Every tile therefore costs one global round trip, where the per-step version pays one
+// per K step and two more for A_IJ and L_JJ^{-1}; the diagonal tile needs no barriers.
+// Shared memory: wm resident tiles + wm staged tiles + X, wm = widest tile row.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void ld8(const float* p, float (&v)[8]) {
+    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w, v[4] = y.x, v[5] = y.y, v[6] = y.z, v[7] = y.w;
+}
+__device__ __forceinline__ void ld8(const double* p, double (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 x = reinterpret_cast<const double2*>(p)[i];
+        v[2 * i] = x.x, v[2 * i + 1] = x.y;
+    }
+}
+__device__ __forceinline__ void st8(float* p, const float (&v)[8]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void st8(double* p, const double (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
+// Cholesky factor and its inverse of the 32x32 tile X (X(r, c) at c * ldx + r, lower
+// triangle used) by one warp: lane r keeps row r of the factor and of the inverse in
+// registers.  L goes to Lout, L^{-1} to Dout (both column-major, zero above the
+// diagonal).  A non-positive or non-finite pivot sets *bad and is replaced by 1.  Not
+// inlined: its 64 live rows would otherwise raise the register count of the whole
+// factorization kernel.
+template <typename TW>
+__device__ __noinline__ void warp_chol_inv(const TW* X, int ldx, TW* __restrict__ Lout, TW* __restrict__ Dout,
+                                           int lane, int* bad) {
+    TW a[TILE];
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) a[c] = X[c * ldx + lane];
+    TW rd_own = (TW)1;   // 1 / L(lane, lane)
+#pragma unroll
+    for (int k = 0; k < TILE; ++k) {
+        TW d = __shfl_sync(0xffffffffu, a[k], k);
+        if (!(d > (TW)0) || !isfinite((double)d)) {   // warp-uniform
+            if (lane == 0) *bad = 1;
+            d = (TW)1;
+        }
+        d = sqrt(d);
+        const TW rd = (TW)1 / d;
+        if (lane > k) a[k] *= rd;
+        if (lane == k) {
+            a[k] = d;
+            rd_own = rd;
+        }
+#pragma unroll
+        for (int j = k + 1; j < TILE; ++j) {
+            const TW ljk = __shfl_sync(0xffffffffu, a[k], j);
+            if (lane >= j) a[j] -= a[k] * ljk;
+        }
+    }
+    // W = L^{-1}: row t of W is complete (up to its scaling) once rows < t have been
+    // subtracted from it; lane r > t then subtracts L(r, t) W(t, :)
+    TW w[TILE];
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) w[c] = c == lane ? (TW)1 : (TW)0;
+#pragma unroll
+    for (int t = 0; t < TILE; ++t) {
+        if (lane == t) {
+#pragma unroll
+            for (int c = 0; c <= t; ++c) w[c] *= rd_own;
+        }
+#pragma unroll
+        for (int c = 0; c <= t; ++c) {
+            const TW wtc = __shfl_sync(0xffffffffu, w[c], t);
+            if (lane > t) w[c] -= a[t] * wtc;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < TILE; ++c) {
+        Lout[c * TILE + lane] = lane >= c ? a[c] : (TW)0;
+        Dout[c * TILE + lane] = w[c];
+    }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) k_tile_chol_row(Profile pf, const int32_t* __restrict__ order,
+                                                       TW* __restrict__ work, TW* __restrict__ dinv,
+                                                       int* __restrict__ err, int wm) {
+    constexpr int VE = 16 / sizeof(TW);
+    constexpr int LDR = TILE + VE;   // padded column stride of the resident row and X
+    const int s = order ? order[blockIdx.x] : blockIdx.x;
+    const int T = pf.ntiles[s];
+    const int64_t r0 = pf.row0[s];
+    const int32_t* lo = pf.lo + r0;
+    const int64_t* fwd = pf.fwd + r0;
+    TW* Wb = work + pf.base[s] * TILE2;
+    TW* Db = dinv + r0 * TILE2;
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    TW* rowt = reinterpret_cast<TW*>(tc_raw);           // [wm][TILE * LDR]: L_I,lo .. L_I,I-1
+    TW* stg = rowt + (size_t)wm * TILE * LDR;            // [wm - 1][TILE2] L_J,K + [TILE2] L_JJ^{-1}
+    TW* dstg = stg + (size_t)(wm - 1) * TILE2;
+    TW* X = dstg + TILE2;                                // [TILE * LDR]
+    int* bad = reinterpret_cast<int*>(X + TILE * LDR);
+    const int tid = threadIdx.x, c = tid & 31, w = tid >> 5, rb = w * 8;
+    if (tid == 0) *bad = 0;
+    auto tile = [&](int I, int J) { return Wb + (fwd[I] + (J - lo[I])) * TILE2; };
+    for (int I = 0; I < T; ++I) {
+        const int li = lo[I];
+        for (int J = li; J <= I; ++J) {
+            const int k0 = max(li, lo[J]);
+            const int nK = J - k0;
+            if (J < I) {
+                const char* gsrc = reinterpret_cast<const char*>(tile(J, k0));
+                const int nch = nK * (int)(TILE2 * sizeof(TW) / 16);
+                for (int i = tid; i < nch; i += blockDim.x)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(stg) + 16u * i),
+                                 "l"(gsrc + 16 * (int64_t)i) : "memory");
+                const char* dsrc = reinterpret_cast<const char*>(Db + (int64_t)J * TILE2);
+                for (int i = tid; i < (int)(TILE2 * sizeof(TW) / 16); i += blockDim.x)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dstg) + 16u * i),
+                                 "l"(dsrc + 16 * (int64_t)i) : "memory");
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
+            TW acc[8];
+            const TW* Aij = tile(I, J);
+            ld8(Aij + c * TILE + rb, acc);
+            if (J < I) asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            // X = A_IJ - sum_K L_IK L_JK^T
+            for (int K = k0; K < J; ++K) {
+                const TW* Ak = rowt + (size_t)(K - li) * TILE * LDR;
+                const TW* Bk = J < I ? stg + (size_t)(K - k0) * TILE2 : rowt + (size_t)(K - li) * TILE * LDR;
+                const int ldb = J < I ? TILE : LDR;
+#pragma unroll 4
+                for (int t = 0; t < TILE; ++t) {
+                    const TW b = Bk[t * ldb + c];
+                    TW av[8];
+                    ld8(Ak + t * LDR + rb, av);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[q] -= av[q] * b;
+                }
+            }
+            st8(X + c * LDR + rb, acc);
+            __syncthreads();
+            if (J < I) {
+                // L_IJ(r, c) = sum_t X(r, t) L_JJ^{-1}(c, t)
+                TW v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = (TW)0;
+#pragma unroll 4
+                for (int t = 0; t < TILE; ++t) {
+                    const TW d = dstg[t * TILE + c];
+                    TW xv[8];
+                    ld8(X + t * LDR + rb, xv);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] += xv[q] * d;
+                }
+                st8(tile(I, J) + c * TILE + rb, v);
+                st8(rowt + (size_t)(J - li) * TILE * LDR + c * LDR + rb, v);
+            } else if (w == 0) {
+                warp_chol_inv<TW>(X, LDR, tile(I, I), Db + (int64_t)I * TILE2, c, bad);
+            }
+            __syncthreads();   // X, the staged tiles and the resident row are reused
+        }
+    }
+    if (tid == 0 && *bad) {
+        if (atomicCAS(err + 1, -1, s) == -1) atomicExch(err, 1);
+    }
+}
+
+size_t tile_chol_row_smem(int wm, size_t elem) {
+    const size_t ve = 16 / elem, ldr = TILE + ve;
+    return ((size_t)wm * TILE * ldr + (size_t)wm * TILE2 + TILE * ldr) * elem + 16;
+}
+
+// ---------------------------------------------------------------------------------
 // Sweep streams from the factor: forward rows [L_I,lo .. L_I,I-1 | L_II^{-1}], backward
 // rows [(L_I+1,I)^T .. (L_hi,I)^T | L_II^{-T}], in precision TS.  Every 32x32 tile M is
 // stored row-major with its 16-byte chunks XOR-swizzled (swz_index), so that the solve
@@ -1458,11 +1642,24 @@ void launch_pad_diag(int nitems, const Profile& pf, TW* work, cudaStream_t st) {
     k_pad_diag<TW><<<(nitems + 127) / 128, 128, 0, st>>>(nitems, pf, work);
 }
 
+// wm = widest tile row of all items (tiles I - lo(I) + 1).  FP32: the resident-row kernel
+// when its shared memory fits an SM, else the per-step kernel.  FP64 keeps the per-step
+// kernel: measured at config 3 on B300, the resident-row version (178 KB of shared memory,
+// one CTA per SM) took 40.9 ms against 35.5 ms, both bound by the FP64 pipe.
 template <typename TW>
-void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err,
+void launch_tile_chol(int nitems, const Profile& pf, const int32_t* order, TW* work, TW* dinv, int* err, int wm,
                       cudaStream_t st) {
+    if (nitems <= 0) return;
     count_launch();
-    k_tile_chol<TW><<<nitems, 256, 0, st>>>(pf, order, work, dinv, err);
+    const size_t smem = tile_chol_row_smem(wm, sizeof(TW));
+    if (sizeof(TW) == 4 && wm >= 1 && smem <= 227 * 1024 &&
+        cudaFuncSetAttribute(k_tile_chol_row<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+            cudaSuccess) {
+        k_tile_chol_row<TW><<<nitems, 128, smem, st>>>(pf, order, work, dinv, err, wm);
+    } else {
+        (void)cudaGetLastError();
+        k_tile_chol<TW><<<nitems, 256, 0, st>>>(pf, order, work, dinv, err);
+    }
 }
 
 template <typename TW, typename TS>
@@ -1580,8 +1777,10 @@ template void launch_scatter_local<float>(int64_t, const int32_t*, const int32_t
                                           const int32_t*, const int64_t*, const Profile&, const double*,
                                           const double*, float*, int, cudaStream_t);
 template void launch_pad_diag<double>(int, const Profile&, double*, cudaStream_t);
-template void launch_tile_chol<double>(int, const Profile&, const int32_t*, double*, double*, int*, cudaStream_t);
-template void launch_tile_chol<float>(int, const Profile&, const int32_t*, float*, float*, int*, cudaStream_t);
+template void launch_tile_chol<double>(int, const Profile&, const int32_t*, double*, double*, int*, int,
+                                        cudaStream_t);
+template void launch_tile_chol<float>(int, const Profile&, const int32_t*, float*, float*, int*, int,
+                                       cudaStream_t);
 template void launch_finalize<double, double>(int, const Profile&, const double*, const double*, double*,
                                               double*, cudaStream_t);
 template void launch_finalize<float, float>(int, const Profile&, const float*, const float*, float*, float*,
