@@ -22,6 +22,7 @@
 #include "async.cuh"
 #include "common.cuh"
 #include "kernels.h"
+#include "tile_chol.cuh"
 
 namespace am {
 
@@ -420,6 +421,78 @@ __global__ void __launch_bounds__(256) k_dtrsm_b(int nitems, const int32_t* __re
         for (int u = 0; u < TILE; ++u) v += X[rb + q][u] * Bs[c][u];
         t[c * TILE + rb + q] = v;
         if (planes) put_planes(planes + (base[g] + (int64_t)I * (I + 1) / 2 + k) * 2 * TILE2, rb + q, c, v);
+    }
+}
+
+// Tile column k of every item in one launch: CTA (g, 0) factors A_kk and stores
+// L_kk^{-1}; CTA (g, i), i >= 1, factors the same A_kk itself (one warp, registers) and
+// solves L_{k+i,k} = A_{k+i,k} L_kk^{-T} (8 outputs per thread), writing the 3xTF32
+// planes for the tensor-core update.  Repeating the 32x32 factorization in every CTA
+// costs less than a second launch and its serialisation.  FP32 only: one warp of FP64
+// would hold one sub-partition's FP64 pipe for the whole tile (k_dpotrf_b spreads it
+// over four).
+// L_kk itself is not stored: later steps read only the tiles below the diagonal and the
+// inverse diagonal tiles.
+__device__ __forceinline__ int item_of_block_col(int nitems, const int32_t* T, int k, int64_t b, int64_t* local) {
+    for (int g = 0; g < nitems; ++g) {
+        const int64_t c = T[g] - k > 0 ? T[g] - k : 0;
+        if (b < c) {
+            *local = b;
+            return g;
+        }
+        b -= c;
+    }
+    return -1;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) k_dpotrf_trsm(int nitems, const int32_t* __restrict__ T,
+                                                     const int64_t* __restrict__ base,
+                                                     const int64_t* __restrict__ row0, TW* __restrict__ work,
+                                                     TW* __restrict__ dinv, int k, int* __restrict__ err,
+                                                     TW* __restrict__ planes) {
+    __shared__ TW Xd[TILE * (TILE + 1)];   // A_kk, X(r, c) at c * 33 + r
+    __shared__ TW Xo[TILE * (TILE + 1)];   // A_Ik
+    __shared__ TW Dd[TILE2];               // L_kk^{-1}, column-major
+    __shared__ int bad_s;
+    int64_t li;
+    const int g = item_of_block_col(nitems, T, k, blockIdx.x, &li);
+    if (g < 0) return;
+    const int I = k + (int)li;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const TW* tkk = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
+    TW* tik = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
+    if (tid == 0) bad_s = 0;
+    for (int e = tid; e < TILE2; e += blockDim.x) {
+        Xd[(e >> 5) * (TILE + 1) + (e & 31)] = tkk[e];
+        if (li > 0) Xo[(e >> 5) * (TILE + 1) + (e & 31)] = tik[e];
+    }
+    __syncthreads();
+    if (w == 0) warp_chol_inv<TW>(Xd, TILE + 1, nullptr, Dd, lane, &bad_s);
+    __syncthreads();
+    if (li == 0) {
+        TW* D = dinv + (row0[g] + k) * TILE2;
+        for (int e = tid; e < TILE2; e += blockDim.x) D[e] = Dd[e];
+        if (tid == 0 && bad_s) {
+            if (atomicCAS(err + 1, -1, g) == -1) atomicExch(err, 1);
+        }
+        return;
+    }
+    // L_Ik(r, c) = sum_u A_Ik(r, u) D(c, u), D(c, u) at u * 32 + c
+    const int rb = w * 8;
+    TW v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (TW)0;
+#pragma unroll 8
+    for (int u = 0; u < TILE; ++u) {
+        const TW d = Dd[u * TILE + lane];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] += Xo[u * (TILE + 1) + rb + q] * d;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        tik[lane * TILE + rb + q] = v[q];
+        if (planes) put_planes(planes + (base[g] + (int64_t)I * (I + 1) / 2 + k) * 2 * TILE2, rb + q, lane, v[q]);
     }
 }
 
@@ -843,11 +916,12 @@ void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const
         // planes of the finished columns, then its diagonal tile factored, then solved below
         cudaFuncSetAttribute(k_dupdate_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
         for (int J = 0; J < maxT; ++J) {
-            int64_t nblk = 0, nt = 0;
+            int64_t nblk = 0, nt = 0, nd = 0;
             for (int t : T_host)
                 if (t > J) {
                     nblk += (t - J + 3) / 4;
                     nt += t - 1 - J;
+                    nd += 1;
                 }
             if (J > 0 && nblk > 0) {
                 count_launch();
@@ -855,11 +929,7 @@ void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const
                                                                    (const float*)planes, J, kerr);
             }
             count_launch();
-            k_dpotrf_b<TW><<<nitems, 128, 0, st>>>(nitems, T, base, row0, work, dinv, J, err, planes);
-            if (nt > 0) {
-                count_launch();
-                k_dtrsm_b<TW><<<(unsigned)nt, 256, 0, st>>>(nitems, T, base, row0, work, dinv, J, planes);
-            }
+            k_dpotrf_trsm<TW><<<(unsigned)(nt + nd), 128, 0, st>>>(nitems, T, base, row0, work, dinv, J, err, planes);
         }
         return;
     }
