@@ -93,6 +93,7 @@ struct NumWs {
     int max_tiles_items = 0;
     void *gwork = nullptr, *gdinv = nullptr, *gf = nullptr, *gb = nullptr;   // interface arithmetic
     float *gplanes = nullptr, *cplanes = nullptr;   // FP32: TF32 operand planes of the factor tiles
+    TcSplit tcs;                                     // FP32: K-split workspace of the tensor-core update
     double* gE = nullptr;
     DevBlockJobs bj_gid, bj_cid;               // FP32 setup: identity columns in column blocks
     int32_t *d_gjob = nullptr, *d_gjt0 = nullptr, *d_cjt0 = nullptr;
@@ -621,6 +622,20 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         if (lowp) {
             W.gplanes = h->alloc<float>((size_t)std::max<int64_t>(tb, 1) * 2 * TILE2);
             if (!W.gplanes) return fail(ALGMORTAR_OOM, "interface planes");
+            {
+                // two CTAs of the update per SM; row blocks: at most those of column 0
+                int sms = 148;
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+                int64_t nb = 0;
+                for (int it = 0; it < W.nitems; ++it) nb += ((int64_t)W.item_hi[it].size() + 3) / 4;
+                nb = std::max<int64_t>(nb, ((int64_t)P.nd_nsep + TILE - 1) / TILE / 4 + 1);
+                W.tcs.max_ctas = 2 * (int64_t)sms;
+                W.tcs.max_blocks = nb;
+                W.tcs.part = h->alloc<float>((size_t)W.tcs.max_ctas * 4 * TILE2);
+                W.tcs.ticket = h->alloc<unsigned int>((size_t)nb);
+                if (!W.tcs.part || !W.tcs.ticket) return fail(ALGMORTAR_OOM, "interface update workspace");
+                CU(cudaMemsetAsync(W.tcs.ticket, 0, (size_t)nb * sizeof(unsigned int), h->st));
+            }
             BlockJobs bg;
             for (int it = 0; it < (int)W.item_group.size(); ++it) {
                 const int g = W.item_group[it];
@@ -848,7 +863,7 @@ int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
         std::vector<int32_t> Th(W.nitems);
         for (int it = 0; it < W.nitems; ++it) Th[it] = (int32_t)W.item_hi[it].size();
         launch_dense_cholesky<TI>(W.nitems, Th, W.d_int, W.d_ibase, W.d_irow0, (TI*)W.gwork, (TI*)W.gdinv, W.d_err,
-                                  st, (TI*)W.gplanes, h->d_kerr);
+                                  st, (TI*)W.gplanes, h->d_kerr, W.tcs);
     }
     CU(cudaGetLastError());
     TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
@@ -884,7 +899,7 @@ int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
                                   (TI*)W.cwork, st);
         CU(cudaMemcpyAsync(W.d_err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, st));
         launch_dense_cholesky<TI>(1, std::vector<int32_t>{W.cT}, W.d_cnt, W.d_czero, W.d_czero, (TI*)W.cwork,
-                                  (TI*)W.cdinv, W.d_err, st, (TI*)W.cplanes, h->d_kerr);
+                                  (TI*)W.cdinv, W.d_err, st, (TI*)W.cplanes, h->d_kerr, W.tcs);
         CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "interface (separator)"));
         Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};

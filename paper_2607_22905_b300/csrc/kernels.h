@@ -152,10 +152,18 @@ void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const 
 // Cholesky of dense items advancing together (T_host: host copy of T): right-looking
 // tile updates (planes == null), or -- FP32 with `planes` (2 TF32 operand planes per
 // tile, same tile indexing as work) -- left-looking with the column updates on tcgen05
+// Workspace of the K-split tensor-core column update: partial products of up to
+// max_ctas CTAs (4 tiles each) and one zeroed ticket per row block (up to max_blocks).
+struct TcSplit {
+    float* part = nullptr;
+    unsigned int* ticket = nullptr;
+    int64_t max_ctas = 0;
+    int64_t max_blocks = 0;
+};
 template <typename TW>
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
                            const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st,
-                           TW* planes = nullptr, int* kerr = nullptr);
+                           TW* planes = nullptr, int* kerr = nullptr, TcSplit tcs = TcSplit{});
 void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
                              double* Wrm, cudaStream_t st);

@@ -463,16 +463,28 @@ __global__ void __launch_bounds__(128) k_dpotrf_trsm(int nitems, const int32_t* 
     const TW* tkk = work + (base[g] + (int64_t)k * (k + 1) / 2 + k) * TILE2;
     TW* tik = work + (base[g] + (int64_t)I * (I + 1) / 2 + k) * TILE2;
     if (tid == 0) bad_s = 0;
-    for (int e = tid; e < TILE2; e += blockDim.x) {
-        Xd[(e >> 5) * (TILE + 1) + (e & 31)] = tkk[e];
-        if (li > 0) Xo[(e >> 5) * (TILE + 1) + (e & 31)] = tik[e];
+    {
+        // all of a thread's loads issued before the first store (one round trip)
+        TW xd[TILE2 / 128], xo[TILE2 / 128];
+#pragma unroll
+        for (int i = 0; i < TILE2 / 128; ++i) {
+            xd[i] = tkk[tid + 128 * i];
+            xo[i] = li > 0 ? tik[tid + 128 * i] : (TW)0;
+        }
+#pragma unroll
+        for (int i = 0; i < TILE2 / 128; ++i) {
+            const int e = tid + 128 * i;
+            Xd[(e >> 5) * (TILE + 1) + (e & 31)] = xd[i];
+            Xo[(e >> 5) * (TILE + 1) + (e & 31)] = xo[i];
+        }
     }
     __syncthreads();
     if (w == 0) warp_chol_inv<TW>(Xd, TILE + 1, nullptr, Dd, lane, &bad_s);
     __syncthreads();
     if (li == 0) {
         TW* D = dinv + (row0[g] + k) * TILE2;
-        for (int e = tid; e < TILE2; e += blockDim.x) D[e] = Dd[e];
+#pragma unroll
+        for (int i = 0; i < TILE2 / 128; ++i) D[tid + 128 * i] = Dd[tid + 128 * i];
         if (tid == 0 && bad_s) {
             if (atomicCAS(err + 1, -1, g) == -1) atomicExch(err, 1);
         }
@@ -534,7 +546,9 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
 // for all items, before the column's diagonal tile is factored and its tiles below solved.
 // One CTA per (item, 4 tile rows I0..I0+3): an M = 128, N = 32 product with K = 32 J on
 // tcgen05 (kind::tf32, accumulator in tensor memory), 3xTF32 (hi*hi + hi*lo + lo*hi from
-// the planes written by k_dpotrf_b / k_dtrsm_b), so the update keeps FP32 accuracy.
+// the planes written with the finished tiles), so the update keeps FP32 accuracy.  Stage
+// k accumulates into accumulator k % TC_ACC: the MMAs into one accumulator run in order,
+// so one accumulator made the column's update a chain of 12 J dependent MMAs.
 // Thread 0 streams the k-th planes of the four row tiles and of tile (J, k) into one of
 // two shared-memory stages by bulk copies (16-byte aligned 4 KB planes, completion on
 // full[s]); thread 32 issues the 12 MMAs of a stage and commits them to empty[s]; at the
@@ -542,15 +556,20 @@ __global__ void __launch_bounds__(256) k_dupdate_b(int nitems, const int32_t* __
 // wait is bounded; a stuck wait sets *err (the bulk-copy error word) and skips the update.
 // ---------------------------------------------------------------------------------
 constexpr int TC_STAGES = 2;
+constexpr int TC_ACC = 4;   // accumulators in tensor memory: stage k goes to k % TC_ACC
 constexpr int TC_PLANE = TILE2 * 4;                          // bytes of one plane
 constexpr int TC_STAGE = (4 * 2 + 2) * TC_PLANE;             // A hi, A lo (4 tiles), B hi, B lo
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE + 128;
 
 __global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* __restrict__ T,
                                                     const int64_t* __restrict__ base, float* __restrict__ work,
-                                                    const float* __restrict__ planes, int J, int* __restrict__ err) {
-    // block -> (item, first tile row)
-    int64_t b = blockIdx.x;
+                                                    const float* __restrict__ planes, int J, int nsplit,
+                                                    float* __restrict__ part, unsigned int* __restrict__ ticket,
+                                                    int* __restrict__ err) {
+    // block -> (item, first tile row, K split)
+    const int sp = (int)(blockIdx.x % (unsigned)nsplit);
+    const int64_t bq = blockIdx.x / (unsigned)nsplit;   // row block, over all items
+    int64_t b = bq;
     int g = -1;
     for (int q = 0; q < nitems; ++q) {
         const int64_t nb = T[q] > J ? (T[q] - J + 3) / 4 : 0;
@@ -563,11 +582,13 @@ __global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* _
     if (g < 0) return;
     const int I0 = J + 4 * (int)b, Tg = T[g];
     const int nA = min(4, Tg - I0);
+    const int k0 = (int)((int64_t)J * sp / nsplit), k1 = (int)((int64_t)J * (sp + 1) / nsplit);
+    const int nk = k1 - k0;
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + TC_STAGES * TC_STAGE);
     uint64_t* empty = full + TC_STAGES;
     uint64_t* done = empty + TC_STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);     // [0] tensor memory, [2] verdict
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);     // [0] tensor memory, [2] verdict, [3] last
     volatile int* bad = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int64_t g0 = base[g];
@@ -582,26 +603,26 @@ __global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* _
         fence_async_smem();
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (w == 0) tc_alloc(smem_u32(tslot), 32);
+    if (w == 0) tc_alloc(smem_u32(tslot), 32 * TC_ACC);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
     int issued = 0;
     if (tid == 0) {
-        for (int k = 0; k < J; ++k) {
-            const int s = k % TC_STAGES;
-            if (k >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((k / TC_STAGES - 1) & 1))) {
+        for (int i = 0; i < nk; ++i) {
+            const int k = k0 + i, s = i % TC_STAGES;
+            if (i >= TC_STAGES && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((i / TC_STAGES - 1) & 1))) {
                 *bad = 1;
                 break;
             }
             unsigned char* st = sm + s * TC_STAGE;
             const uint32_t bar = smem_u32(&full[s]);
             mbar_expect_tx(bar, (uint32_t)((2 * nA + 2) * TC_PLANE));
-            for (int i = 0; i < nA; ++i) {
-                const float* src = planes + tile(I0 + i, k) * 2 * TILE2;
-                bulk_copy(smem_u32(st + i * TC_PLANE), src, TC_PLANE, bar);
-                bulk_copy(smem_u32(st + (4 + i) * TC_PLANE), src + TILE2, TC_PLANE, bar);
+            for (int r = 0; r < nA; ++r) {
+                const float* src = planes + tile(I0 + r, k) * 2 * TILE2;
+                bulk_copy(smem_u32(st + r * TC_PLANE), src, TC_PLANE, bar);
+                bulk_copy(smem_u32(st + (4 + r) * TC_PLANE), src + TILE2, TC_PLANE, bar);
             }
             const float* srcB = planes + tile(J, k) * 2 * TILE2;
             bulk_copy(smem_u32(st + 8 * TC_PLANE), srcB, TC_PLANE, bar);
@@ -610,23 +631,24 @@ __global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* _
         }
     } else if (tid == 32) {
         constexpr uint32_t idesc = tc_idesc_tf32(128, 32);
-        for (int k = 0; k < J; ++k) {
-            const int s = k % TC_STAGES;
-            if (*bad || !mbar_wait(smem_u32(&full[s]), (uint32_t)((k / TC_STAGES) & 1))) {
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            if (*bad || !mbar_wait(smem_u32(&full[s]), (uint32_t)((i / TC_STAGES) & 1))) {
                 *bad = 1;
                 break;
             }
             tc_fence_after();
             const uint32_t st = smem_u32(sm + s * TC_STAGE);
+            const uint32_t d = tbase + 32u * (uint32_t)(i % TC_ACC);
             // A: 128 rows (4 tiles, 4 KB each = 4 groups of 8 rows at SBO 1024), K 8 per MMA
             for (int j = 0; j < 4; ++j) {
                 const uint32_t o = j * 256;   // two core matrices along K
                 const uint64_t aH = tc_smem_desc(st + o, 128, 1024), aL = tc_smem_desc(st + 4 * TC_PLANE + o, 128, 1024);
                 const uint64_t bH = tc_smem_desc(st + 8 * TC_PLANE + o, 128, 1024);
                 const uint64_t bL = tc_smem_desc(st + 9 * TC_PLANE + o, 128, 1024);
-                tc_mma_tf32(tbase, aH, bH, idesc, (k > 0 || j > 0) ? 1u : 0u);
-                tc_mma_tf32(tbase, aH, bL, idesc, 1u);
-                tc_mma_tf32(tbase, aL, bH, idesc, 1u);
+                tc_mma_tf32(d, aH, bH, idesc, (i >= TC_ACC || j > 0) ? 1u : 0u);
+                tc_mma_tf32(d, aH, bL, idesc, 1u);
+                tc_mma_tf32(d, aL, bH, idesc, 1u);
             }
             tc_commit(smem_u32(&empty[s]));
         }
@@ -640,21 +662,63 @@ __global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* _
     __syncthreads();
     const bool ok = tslot[2] != 0;
     tc_fence_after();
-    if (ok && w < nA) {
-        float v[32];
-        tc_ld32(tbase + ((uint32_t)(32 * w) << 16), v);
-        float* t = work + tile(I0 + w, J) * TILE2;   // column-major: (r, c) at c * 32 + r
+    float v[32];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) t[c * TILE + lane] -= v[c];
+    for (int c = 0; c < 32; ++c) v[c] = 0.0f;
+    if (ok && w < nA) {
+        // the accumulators in use, summed in a fixed order
+        float u[32];
+        for (int a = 0; a < TC_ACC && a < nk; ++a) {
+            tc_ld32(tbase + ((uint32_t)(32 * w) << 16) + 32u * a, u);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] += u[c];
+        }
     }
     if (!ok && tid == 0) atomicExch(err, 1);
+    if (nsplit == 1) {
+        if (ok && w < nA) {
+            float* t = work + tile(I0 + w, J) * TILE2;   // column-major: (r, c) at c * 32 + r
+#pragma unroll
+            for (int c = 0; c < 32; ++c) t[c * TILE + lane] -= v[c];
+        }
+    } else {
+        // K split: every CTA stores its partial product; the CTA that arrives last at the
+        // row block's ticket adds the partials in split order and updates the tiles
+        // (deterministic, as GridSum)
+        float* mine = part + ((bq * nsplit + sp) * 4) * (int64_t)TILE2;
+        if (w < nA) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) mine[w * TILE2 + c * TILE + lane] = v[c];
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) tslot[3] = atomicAdd(&ticket[bq], 1u) == (unsigned)(nsplit - 1) ? 1u : 0u;
+        __syncthreads();
+        if (tslot[3]) {
+            __threadfence();
+            if (w < nA) {
+                float sum[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) sum[c] = 0.0f;
+                for (int q = 0; q < nsplit; ++q) {
+                    const float* pq = part + ((bq * nsplit + q) * 4 + w) * (int64_t)TILE2;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) sum[c] += __ldcg(pq + c * TILE + lane);
+                }
+                float* t = work + tile(I0 + w, J) * TILE2;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) t[c * TILE + lane] -= sum[c];
+            }
+            if (tid == 0) ticket[bq] = 0u;   // re-armed for the next launch
+        }
+    }
     // the producer's copies in flight land before the CTA leaves (bounded)
     if (tid == 0 && !ok)
         for (int k = max(0, issued - TC_STAGES); k < issued; ++k)
             mbar_wait(smem_u32(&full[k % TC_STAGES]), (uint32_t)((k / TC_STAGES) & 1));
     tc_fence_before();
     __syncthreads();
-    if (w == 0) tc_dealloc(tbase, 32);
+    if (w == 0) tc_dealloc(tbase, 32 * TC_ACC);
 }
 
 // Warp dot product of a contiguous row with x (len entries) in the row's arithmetic TM
@@ -908,7 +972,7 @@ void launch_dense_to_tiles(int64_t ntiles, const double* src, int64_t ld, const 
 template <typename TW>
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
                            const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st, TW* planes,
-                           int* kerr) {
+                           int* kerr, TcSplit tcs) {
     int maxT = 0;
     for (int t : T_host) maxT = std::max(maxT, t);
     if (planes) {
@@ -924,9 +988,18 @@ void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const
                     nd += 1;
                 }
             if (J > 0 && nblk > 0) {
+                // K split over CTAs: one CTA streams the 40 KB stage of every k through one SM
+                // (~0.6 us a stage on B300), so the column's update is spread over up to two
+                // CTAs per SM, at least two stages each
+                int nsplit = 1;
+                if (tcs.part) {
+                    nsplit = (int)std::min<int64_t>(tcs.max_ctas / nblk, J / 2);
+                    nsplit = std::max(1, nsplit);
+                    if (nblk > tcs.max_blocks) nsplit = 1;
+                }
                 count_launch();
-                k_dupdate_tc<<<(unsigned)nblk, 128, TC_SMEM, st>>>(nitems, T, base, (float*)work,
-                                                                   (const float*)planes, J, kerr);
+                k_dupdate_tc<<<(unsigned)(nblk * nsplit), 128, TC_SMEM, st>>>(
+                    nitems, T, base, (float*)work, (const float*)planes, J, nsplit, tcs.part, tcs.ticket, kerr);
             }
             count_launch();
             k_dpotrf_trsm<TW><<<(unsigned)(nt + nd), 128, 0, st>>>(nitems, T, base, row0, work, dinv, J, err, planes);
@@ -1053,7 +1126,7 @@ cudaError_t prepare_nd_solve(int nsep) {
                                             const int64_t*, const int32_t*, const int32_t*, const int32_t*, TW*,     \
                                             cudaStream_t);                                                           \
     template void launch_dense_cholesky<TW>(int, const std::vector<int32_t>&, const int32_t*, const int64_t*,      \
-                                            const int64_t*, TW*, TW*, int*, cudaStream_t, TW*, int*);                \
+                                            const int64_t*, TW*, TW*, int*, cudaStream_t, TW*, int*, TcSplit);                \
     template void launch_nd_schur_tiles<TW>(int64_t, int64_t, int, int64_t, const double*, const int32_t*,         \
                                             const int32_t*, const int64_t*, const int64_t*, const double*, TW*,      \
                                             cudaStream_t);

@@ -7,11 +7,9 @@ namespace am {
 // Cholesky factor and its inverse of the 32x32 tile X (X(r, c) at c * ldx + r, lower
 // triangle used) by one warp: lane r keeps row r of the factor and of the inverse in
 // registers.  L goes to Lout (if not null), L^{-1} to Dout (both column-major, zero above
-// the diagonal).  A non-positive or non-finite pivot sets *bad and is replaced by 1.  Not
-// inlined: its 64 live rows would otherwise raise the register count of the whole
-// factorization kernel.
+// the diagonal).  A non-positive or non-finite pivot sets *bad and is replaced by 1.
 template <typename TW>
-__device__ __noinline__ void warp_chol_inv(const TW* X, int ldx, TW* __restrict__ Lout, TW* __restrict__ Dout,
+__device__ __forceinline__ void warp_chol_inv(const TW* X, int ldx, TW* __restrict__ Lout, TW* __restrict__ Dout,
                                            int lane, int* bad) {
     TW a[TILE];
 #pragma unroll
@@ -20,7 +18,7 @@ __device__ __noinline__ void warp_chol_inv(const TW* X, int ldx, TW* __restrict_
 #pragma unroll
     for (int k = 0; k < TILE; ++k) {
         TW d = __shfl_sync(0xffffffffu, a[k], k);
-        if (!(d > (TW)0) || !isfinite((double)d)) {   // warp-uniform
+        if (!(d > (TW)0) || !isfinite(d)) {   // warp-uniform
             if (lane == 0) *bad = 1;
             d = (TW)1;
         }
@@ -31,10 +29,14 @@ __device__ __noinline__ void warp_chol_inv(const TW* X, int ldx, TW* __restrict_
             a[k] = d;
             rd_own = rd;
         }
+        // constant trip counts (a predicate instead of j = k + 1 ..): with a bound that
+        // depends on k the compiler left the row in local memory
 #pragma unroll
-        for (int j = k + 1; j < TILE; ++j) {
-            const TW ljk = __shfl_sync(0xffffffffu, a[k], j);
-            if (lane >= j) a[j] -= a[k] * ljk;
+        for (int j = 0; j < TILE; ++j) {
+            if (j > k) {
+                const TW ljk = __shfl_sync(0xffffffffu, a[k], j);
+                if (lane >= j) a[j] -= a[k] * ljk;
+            }
         }
     }
     // W = L^{-1}: row t of W is complete (up to its scaling) once rows < t have been
@@ -46,12 +48,15 @@ __device__ __noinline__ void warp_chol_inv(const TW* X, int ldx, TW* __restrict_
     for (int t = 0; t < TILE; ++t) {
         if (lane == t) {
 #pragma unroll
-            for (int c = 0; c <= t; ++c) w[c] *= rd_own;
+            for (int c = 0; c < TILE; ++c)
+                if (c <= t) w[c] *= rd_own;
         }
 #pragma unroll
-        for (int c = 0; c <= t; ++c) {
-            const TW wtc = __shfl_sync(0xffffffffu, w[c], t);
-            if (lane > t) w[c] -= a[t] * wtc;
+        for (int c = 0; c < TILE; ++c) {
+            if (c <= t) {
+                const TW wtc = __shfl_sync(0xffffffffu, w[c], t);
+                if (lane > t) w[c] -= a[t] * wtc;
+            }
         }
     }
 #pragma unroll
