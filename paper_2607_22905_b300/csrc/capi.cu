@@ -1,6 +1,8 @@
 // C ABI of libalgmortar (include/algmortar.h): handle lifetime, Algorithm 1 on the device,
 // Algorithm 2 and the PCG loop.
 #include <algorithm>
+#include <array>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <chrono>
@@ -95,7 +97,11 @@ struct NumWs {
     float *gplanes = nullptr, *cplanes = nullptr;   // FP32: TF32 operand planes of the factor tiles
     TcSplit tcs;                                     // FP32: K-split workspace of the tensor-core update
     double* gE = nullptr;
-    DevBlockJobs bj_gid, bj_cid;               // FP32 setup: identity columns in column blocks
+    // FP32 setup: explicit inverses by batched tile products (launch_tile_inv), one job
+    // range per launch, for the group items and for the separator
+    int4 *d_ginv_jobs = nullptr, *d_cinv_jobs = nullptr;
+    std::vector<std::pair<int, int>> ginv_ranges, cinv_ranges;
+    int64_t* d_iout = nullptr;                 // per group item: offset of its inverse in Ginv
     int32_t *d_gjob = nullptr, *d_gjt0 = nullptr, *d_cjt0 = nullptr;
     int64_t* d_gjin = nullptr;
     int njobs_g = 0;
@@ -292,6 +298,50 @@ int solve_cols(SolveArgs a, const DevBlockJobs& d, bool identity, int max_tiles,
     a.job_t0 = identity ? d.t0 : nullptr;
     CU((launch_tile_solve_cols<TS, TA>(a, d.n, max_tiles, st)));
     return 0;
+}
+
+// Jobs of launch_tile_inv for items with T[it] tile rows: the diagonal inverses, then per
+// level of a recursive halving of [0, T) (children first) the products P = L21 W11 and
+// W21 = -W22 P of every node of that height, then the lower tiles of W^T W.  Every range
+// is one launch; its jobs only read tiles finished by earlier launches.
+void build_inv_jobs(const std::vector<int32_t>& T, std::vector<int4>& jobs, std::vector<std::pair<int, int>>& ranges) {
+    jobs.clear();
+    ranges.clear();
+    auto job = [](int it, int I, int J, int k0, int k1, int type) {
+        return make_int4(it, (I << 16) | J, (k0 << 16) | k1, type);
+    };
+    // nodes [a, b) by height, all items
+    std::vector<std::vector<std::array<int, 4>>> byh;   // {item, a, m, b}
+    std::function<int(int, int, int)> walk = [&](int it, int a, int b) -> int {
+        if (b - a <= 1) return 0;
+        const int m = a + (b - a) / 2;
+        const int h = 1 + std::max(walk(it, a, m), walk(it, m, b));
+        if ((int)byh.size() < h) byh.resize(h);
+        byh[h - 1].push_back({it, a, m, b});
+        return h;
+    };
+    int start = 0;
+    for (int it = 0; it < (int)T.size(); ++it)
+        for (int I = 0; I < T[it]; ++I) jobs.push_back(job(it, I, I, 0, 0, 0));
+    ranges.push_back({start, (int)jobs.size() - start});
+    for (int it = 0; it < (int)T.size(); ++it) walk(it, 0, T[it]);
+    for (const auto& lev : byh) {
+        start = (int)jobs.size();
+        for (const auto& nd : lev)
+            for (int I = nd[2]; I < nd[3]; ++I)
+                for (int J = nd[1]; J < nd[2]; ++J) jobs.push_back(job(nd[0], I, J, J, nd[2], 1));
+        ranges.push_back({start, (int)jobs.size() - start});
+        start = (int)jobs.size();
+        for (const auto& nd : lev)
+            for (int I = nd[2]; I < nd[3]; ++I)
+                for (int J = nd[1]; J < nd[2]; ++J) jobs.push_back(job(nd[0], I, J, nd[2], I + 1, 2));
+        ranges.push_back({start, (int)jobs.size() - start});
+    }
+    start = (int)jobs.size();
+    for (int it = 0; it < (int)T.size(); ++it)
+        for (int I = 0; I < T[it]; ++I)
+            for (int J = 0; J <= I; ++J) jobs.push_back(job(it, I, J, I, T[it], 3));
+    ranges.push_back({start, (int)jobs.size() - start});
 }
 
 int read_err_flag(algmortar_t* h, int* d_err, const char* what) {
@@ -636,13 +686,17 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
                 if (!W.tcs.part || !W.tcs.ticket) return fail(ALGMORTAR_OOM, "interface update workspace");
                 CU(cudaMemsetAsync(W.tcs.ticket, 0, (size_t)nb * sizeof(unsigned int), h->st));
             }
-            BlockJobs bg;
+            // explicit S_gg^{-1} by tile products (gf / gb hold W = L^{-1} and P)
+            std::vector<int32_t> Ts;
+            std::vector<int64_t> iout;
             for (int it = 0; it < (int)W.item_group.size(); ++it) {
-                const int g = W.item_group[it];
-                const int64_t ng = P.nd_goff[g + 1] - P.nd_goff[g];
-                bg.add(it, gioff[g], ng, ng, true);
+                Ts.push_back((int32_t)W.item_hi[it].size());
+                iout.push_back(gioff[W.item_group[it]]);
             }
-            TRY(upload_jobs(h, W.bj_gid, bg));
+            std::vector<int4> jobs;
+            build_inv_jobs(Ts, jobs, W.ginv_ranges);
+            TRY(upload(h, W.d_ginv_jobs, jobs));
+            TRY(upload(h, W.d_iout, iout));
         }
         W.gE = h->alloc<double>((size_t)std::max<int64_t>(gi, 1));
         W.D = h->alloc<double>((size_t)std::max<int64_t>(dof, 1));
@@ -818,9 +872,9 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             if (lowp) {
                 W.cplanes = h->alloc<float>((size_t)ct * 2 * TILE2);
                 if (!W.cplanes) return fail(ALGMORTAR_OOM, "separator planes");
-                BlockJobs bc;
-                bc.add(0, 0, nsep, nsep, true);
-                TRY(upload_jobs(h, W.bj_cid, bc));
+                std::vector<int4> jobs;
+                build_inv_jobs(std::vector<int32_t>{T}, jobs, W.cinv_ranges);
+                TRY(upload(h, W.d_cinv_jobs, jobs));
             }
             W.cE = h->alloc<double>((size_t)nsep * nsep);
             double* Cinv = h->alloc<double>((size_t)nsep * nsep);
@@ -867,25 +921,30 @@ int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
     }
     CU(cudaGetLastError());
     TRY(read_err_flag(h, W.d_err, "interface (interior block)"));
-    launch_finalize<TI, TI>(W.nitems, gpf, (const TI*)W.gwork, (const TI*)W.gdinv, (TI*)W.gf, (TI*)W.gb, st);
-    // S_gg^{-1} (identity columns), then W_g = S_gg^{-1} S_{g,A_g} from its sparse pattern
-    SolveArgs sa{};
-    sa.pf = gpf;
-    sa.fwdS = W.gf;
-    sa.bwdS = W.gb;
-    sa.err = h->d_kerr;
-    sa.in = W.gE;
-    sa.out = (double*)h->nd.Ginv;
-    if (std::is_same<TI, double>::value) {
-        // one job per column (measured faster than column blocks for FP64: the FP64 work
-        // of a job is spread over four warps and the grids are larger)
+    // S_gg^{-1}, then W_g = S_gg^{-1} S_{g,A_g} from its sparse pattern
+    if constexpr (std::is_same<TI, double>::value) {
+        // FP64: identity columns through the sweep streams, one job per column (measured
+        // faster than column blocks for FP64: the FP64 work of a job is spread over four
+        // warps and the grids are larger)
+        launch_finalize<TI, TI>(W.nitems, gpf, (const TI*)W.gwork, (const TI*)W.gdinv, (TI*)W.gf, (TI*)W.gb, st);
+        SolveArgs sa{};
+        sa.pf = gpf;
+        sa.fwdS = W.gf;
+        sa.bwdS = W.gb;
+        sa.err = h->d_kerr;
+        sa.in = W.gE;
+        sa.out = (double*)h->nd.Ginv;
         sa.job_sub = W.d_gjob;
         sa.job_in = W.d_gjin;
         sa.job_out = W.d_gjin;
         sa.job_t0 = W.d_gjt0;   // identity columns: lower triangle of S_gg^{-1} only
         CU((launch_tile_solve<TI, TI>(sa, W.njobs_g, W.max_tiles_items, st)));
     } else {
-        TRY((solve_cols<TI, TI>(sa, W.bj_gid, true, W.max_tiles_items, st)));
+        // FP32: lower triangle of W^T W, W = L^{-1}, by batched tile products
+        for (const auto& r : W.ginv_ranges)
+            launch_tile_inv(W.d_ginv_jobs + r.first, r.second, (const float*)W.gwork, (const float*)W.gdinv,
+                            (float*)W.gf, (float*)W.gb, (double*)h->nd.Ginv, W.d_ibase, W.d_irow0, W.d_irows,
+                            W.d_iout, st);
     }
     launch_mirror_lower(h->nd_grows, h->nd.gioff, G, (double*)h->nd.Ginv, st);
     launch_nd_w_sparse(h->nd.np, L, W.Sd, h->nd.goff, h->nd.aoff, h->nd.alist, sep0, h->nd.prow_g, W.d_wc_ptr,
@@ -902,23 +961,26 @@ int nd_factor_inverse(algmortar_t* h, NumWs& W, cudaStream_t st) {
                                   (TI*)W.cdinv, W.d_err, st, (TI*)W.cplanes, h->d_kerr, W.tcs);
         CU(cudaGetLastError());
         TRY(read_err_flag(h, W.d_err, "interface (separator)"));
-        Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};
-        launch_finalize<TI, TI>(1, cpf, (const TI*)W.cwork, (const TI*)W.cdinv, (TI*)W.cf, (TI*)W.cb, st);
-        SolveArgs ca{};
-        ca.pf = cpf;
-        ca.fwdS = W.cf;
-        ca.bwdS = W.cb;
-        ca.err = h->d_kerr;
-        ca.in = W.cE;
-        ca.out = (double*)h->nd.Cinv;
-        if (std::is_same<TI, double>::value) {
+        if constexpr (std::is_same<TI, double>::value) {
+            Profile cpf{W.d_crows, W.d_cnt, W.d_czero, W.d_czero, W.d_clo, W.d_chi, W.d_cfwd, W.d_cbwd};
+            launch_finalize<TI, TI>(1, cpf, (const TI*)W.cwork, (const TI*)W.cdinv, (TI*)W.cf, (TI*)W.cb, st);
+            SolveArgs ca{};
+            ca.pf = cpf;
+            ca.fwdS = W.cf;
+            ca.bwdS = W.cb;
+            ca.err = h->d_kerr;
+            ca.in = W.cE;
+            ca.out = (double*)h->nd.Cinv;
             ca.job_sub = W.d_cjob;
             ca.job_in = W.d_cjin;
             ca.job_out = W.d_cjin;
             ca.job_t0 = W.d_cjt0;   // lower triangle of C^{-1} only
             CU((launch_tile_solve<TI, TI>(ca, nsep, W.cT, st)));
         } else {
-            TRY((solve_cols<TI, TI>(ca, W.bj_cid, true, W.cT, st)));
+            for (const auto& r : W.cinv_ranges)
+                launch_tile_inv(W.d_cinv_jobs + r.first, r.second, (const float*)W.cwork, (const float*)W.cdinv,
+                                (float*)W.cf, (float*)W.cb, (double*)h->nd.Cinv, W.d_czero, W.d_czero, W.d_crows,
+                                W.d_czerooff, st);
         }
         launch_mirror_lower(W.d_crowsq, W.d_czerooff, 1, (double*)h->nd.Cinv, st);
     }

@@ -164,6 +164,13 @@ template <typename TW>
 void launch_dense_cholesky(int nitems, const std::vector<int32_t>& T_host, const int32_t* T, const int64_t* base,
                            const int64_t* row0, TW* work, TW* dinv, int* err, cudaStream_t st,
                            TW* planes = nullptr, int* kerr = nullptr, TcSplit tcs = TcSplit{});
+// Explicit FP32 inverse of dense tile-factored items, S^{-1} = W^T W, W = L^{-1}: each launch
+// runs one batch of int4 jobs {item, I << 16 | J, k0 << 16 | k1, type} (0: W_II = dinv_I,
+// 1: P_IJ = sum L_IK W_KJ, 2: W_IJ = -sum W_IK P_KJ, 3: lower tile of W^T W into the dense
+// FP64 column-major out + out_off[item], leading dimension nrows[item]).
+void launch_tile_inv(const int4* jobs, int njobs, const float* L, const float* dinv, float* Wt, float* Pt,
+                     double* out, const int64_t* base, const int64_t* row0, const int32_t* nrows,
+                     const int64_t* out_off, cudaStream_t st);
 void launch_mirror_lower(const int32_t* rows, const int64_t* off, int nitems, double* M, cudaStream_t st);
 void launch_transpose_blocks(const int64_t* goff, const int64_t* aoff, const int64_t* woff, int G, const double* Wcm,
                              double* Wrm, cudaStream_t st);

@@ -721,6 +721,110 @@ __global__ void __launch_bounds__(128) k_dupdate_tc(int nitems, const int32_t* _
     if (w == 0) tc_dealloc(tbase, 32 * TC_ACC);
 }
 
+// ---------------------------------------------------------------------------------
+// Explicit inverse of a dense FP32 item from its tile factor, S^{-1} = W^T W with
+// W = L^{-1}, by batched 32x32 tile products (one CTA per output tile, 4 warps, thread
+// (lane c, warp w) owns rows 8w .. 8w+7 of column c):
+//   type 0: W_II = L_II^{-1} (copied from dinv);
+//   type 1: P_IJ = sum_{k0 <= K < k1} L_IK W_KJ          (P = L21 W11 of a 2x2 split)
+//   type 2: W_IJ = -sum_{k0 <= K < k1} W_IK P_KJ         (W21 = -W22 P)
+//   type 3: (S^{-1})_IJ = sum_{k0 <= K < k1} W_KI^T W_KJ, I >= J, into the dense FP64
+//           column-major output (rows and columns past the item's n dropped).
+// A job is int4 {item, I << 16 | J, k0 << 16 | k1, type}.  Types 1 and 2 are issued level by
+// level of a recursive halving of the tile range (both halves inverted first), so a level's
+// products only read finished tiles.  Operand tiles are staged in shared memory through
+// registers, the next pair loaded while the current one multiplies.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_tile_inv(const int4* __restrict__ jobs, const float* __restrict__ L,
+                                                  const float* __restrict__ dinv, float* __restrict__ Wt,
+                                                  float* __restrict__ Pt, double* __restrict__ out,
+                                                  const int64_t* __restrict__ base, const int64_t* __restrict__ row0,
+                                                  const int32_t* __restrict__ nrows,
+                                                  const int64_t* __restrict__ out_off) {
+    __shared__ __align__(16) float As[2][TILE * 36];   // A(r, t) at t * 36 + r
+    __shared__ float Bs[2][TILE * 33];                 // B(t, c) at t * 33 + c
+    const int4 jb = jobs[blockIdx.x];
+    const int g = jb.x, I = jb.y >> 16, J = jb.y & 0xffff, k0 = jb.z >> 16, k1 = jb.z & 0xffff, type = jb.w;
+    const int tid = threadIdx.x, c = tid & 31, rb = (tid >> 5) * 8;
+    const int64_t b0 = base[g];
+    auto tile = [&](int a, int b) { return (b0 + (int64_t)a * (a + 1) / 2 + b) * TILE2; };
+    if (type == 0) {
+        const float* D = dinv + (row0[g] + I) * TILE2;
+        float* dst = Wt + tile(I, I);
+#pragma unroll
+        for (int u = 0; u < TILE2 / 128; ++u) dst[tid + 128 * u] = D[tid + 128 * u];
+        return;
+    }
+    const float* Asrc = type == 1 ? L : Wt;
+    const float* Bsrc = type == 1 ? Wt : (type == 2 ? Pt : Wt);
+    float ra[TILE2 / 128], rbv[TILE2 / 128];
+    auto gload = [&](int k) {
+        const float* A = Asrc + (type == 3 ? tile(k, I) : tile(I, k));
+        const float* B = Bsrc + tile(k, J);
+#pragma unroll
+        for (int u = 0; u < TILE2 / 128; ++u) {
+            ra[u] = A[tid + 128 * u];
+            rbv[u] = B[tid + 128 * u];
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < TILE2 / 128; ++u) {
+            const int e = tid + 128 * u, hi = e >> 5, lo = e & 31;   // element (lo, hi) of a column-major tile
+            if (type == 3) As[buf][lo * 36 + hi] = ra[u];             // A = M^T: A(hi, lo) = M(lo, hi)
+            else As[buf][hi * 36 + lo] = ra[u];                      // A(lo, hi)
+            Bs[buf][lo * 33 + hi] = rbv[u];                           // B(lo, hi)
+        }
+    };
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+    if (k0 < k1) {
+        gload(k0);
+        sstore(0);
+    }
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+        const int buf = (k - k0) & 1;
+        if (k + 1 < k1) gload(k + 1);
+#pragma unroll 8
+        for (int t = 0; t < TILE; ++t) {
+            const float b = Bs[buf][t * 33 + c];
+            const float4 x = *reinterpret_cast<const float4*>(&As[buf][t * 36 + rb]);
+            const float4 y = *reinterpret_cast<const float4*>(&As[buf][t * 36 + rb + 4]);
+            acc[0] += x.x * b, acc[1] += x.y * b, acc[2] += x.z * b, acc[3] += x.w * b;
+            acc[4] += y.x * b, acc[5] += y.y * b, acc[6] += y.z * b, acc[7] += y.w * b;
+        }
+        if (k + 1 < k1) sstore(buf ^ 1);
+        __syncthreads();
+    }
+    if (type == 3) {
+        const int64_t n = nrows[g];
+        const int64_t col = (int64_t)J * TILE + c;
+        if (col < n) {
+            double* o = out + out_off[g] + col * n;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t row = (int64_t)I * TILE + rb + q;
+                if (row < n) o[row] = (double)acc[q];
+            }
+        }
+        return;
+    }
+    float* dst = (type == 1 ? Pt : Wt) + tile(I, J) + c * TILE + rb;
+    const float sgn = type == 1 ? 1.0f : -1.0f;
+    *reinterpret_cast<float4*>(dst) = make_float4(sgn * acc[0], sgn * acc[1], sgn * acc[2], sgn * acc[3]);
+    *reinterpret_cast<float4*>(dst + 4) = make_float4(sgn * acc[4], sgn * acc[5], sgn * acc[6], sgn * acc[7]);
+}
+
+void launch_tile_inv(const int4* jobs, int njobs, const float* L, const float* dinv, float* Wt, float* Pt,
+                     double* out, const int64_t* base, const int64_t* row0, const int32_t* nrows,
+                     const int64_t* out_off, cudaStream_t st) {
+    if (njobs <= 0) return;
+    count_launch();
+    k_tile_inv<<<(unsigned)njobs, 128, 0, st>>>(jobs, L, dinv, Wt, Pt, out, base, row0, nrows, out_off);
+}
+
 // Warp dot product of a contiguous row with x (len entries) in the row's arithmetic TM
 // (FP64, or FP32 for the FP32 copies, x then FP32 too: a double -> float conversion runs
 // on B300's FP64 pipe), eight independent accumulators per lane so that each lane has
