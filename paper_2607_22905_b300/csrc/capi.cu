@@ -76,6 +76,8 @@ struct NumWs {
     bool ready = false;
     int njobs_mbf = 0;
     DevBlockJobs bj_mbf;                      // column-block jobs of the MBF solves
+    DevBlockJobs pj_mbf;                      // the same in blocks of PANEL_NC (FP32 / BF16)
+    float* w32 = nullptr;                     // FP32 / BF16: scaled FP32 MBF right-hand sides
     int32_t *d_js = nullptr, *d_grow = nullptr, *d_gcol = nullptr, *d_pairs = nullptr;
     int64_t *d_jo = nullptr, *d_goff = nullptr, *d_gcptr = nullptr;
     double* d_gval = nullptr;
@@ -545,6 +547,22 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             b.add(s, P.phi_off[s], ns, P.if_off[s + 1] - P.if_off[s], false);
         }
         TRY(upload_jobs(h, W.bj_mbf, b));
+        // PANEL_NC columns per job, subdomains with the longest tile chains first
+        std::vector<int32_t> ord(m);
+        for (int s = 0; s < m; ++s) ord[s] = s;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return P.ntiles[x] > P.ntiles[y]; });
+        BlockJobs pb;
+        for (int s : ord) {
+            const int64_t ns = P.sub_off[s + 1] - P.sub_off[s], kk = P.if_off[s + 1] - P.if_off[s];
+            for (int64_t c = 0; c < kk; c += PANEL_NC) {
+                pb.sub.push_back(s);
+                pb.in.push_back(P.phi_off[s] + c * ns);
+                pb.ld.push_back(ns);
+                pb.nc.push_back((int32_t)std::min<int64_t>(PANEL_NC, kk - c));
+                pb.t0.push_back(0);
+            }
+        }
+        TRY(upload_jobs(h, W.pj_mbf, pb));
     }
     std::vector<int64_t> gcptr;
     gcptr.reserve(P.if_off[m] + m);
@@ -569,6 +587,10 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
     W.d_err = h->alloc<int>(2);
     W.rhs = h->alloc<double>(nphi);
     W.phi64 = h->alloc<double>(nphi);
+    if (!std::is_same<TS, double>::value && panel_solve_fits(h->tile_wm, P.max_tiles, sizeof(TS))) {
+        W.w32 = h->alloc<float>((size_t)std::max<int64_t>(nphi, 1));
+        if (!W.w32) return fail(ALGMORTAR_OOM, "MBF right-hand sides");
+    }
     h->d_fwdS = h->alloc<TS>((size_t)tiles * TILE2);
     h->d_bwdS = h->alloc<TS>((size_t)tiles * TILE2);
     if (h->opts.smooth_steps > 0) {
@@ -1034,8 +1056,15 @@ int numeric_setup(algmortar_t* h) {
     }
     cudaEventRecord(ev[1], st);
     // --- MBFs (Eq. def-phat-local): Phi_i = A_i^{-1} (-B_i psi_m), one job per (i, m) ---
-    CU(cudaMemsetAsync(W.rhs, 0, nphi * sizeof(double), st));
-    launch_mbf_rhs(m, W.d_goff, W.d_grow, W.d_gcol, W.d_gval, h->d_rows, h->d_phi_off, W.rhs, st);
+    const bool panel = W.w32 != nullptr && sizeof(TA) == 4;
+    if (panel) {
+        CU(cudaMemsetAsync(W.w32, 0, nphi * sizeof(float), st));
+        launch_mbf_rhs32(m, W.d_goff, W.d_grow, W.d_gcol, W.d_gval, h->d_rows, h->d_phi_off, h->d_sc32, h->d_sub_off,
+                         W.w32, st);
+    } else {
+        CU(cudaMemsetAsync(W.rhs, 0, nphi * sizeof(double), st));
+        launch_mbf_rhs(m, W.d_goff, W.d_grow, W.d_gcol, W.d_gval, h->d_rows, h->d_phi_off, W.rhs, st);
+    }
     {
         SolveArgs a{};
         a.pf = h->pf;
@@ -1048,7 +1077,19 @@ int numeric_setup(algmortar_t* h) {
         a.out = W.phi64;
         a.done = nullptr;
         a.err = h->d_kerr;
-        TRY((solve_cols<TS, TA>(a, W.bj_mbf, false, P.max_tiles, st)));
+        if constexpr (sizeof(TA) == 4) {
+            if (panel) {
+                // all of a subdomain's MBF columns (up to PANEL_NC) against one pass of its factor
+                SolveArgs b = a;
+                b.job_sub = W.pj_mbf.sub;
+                b.job_in = W.pj_mbf.in;
+                b.job_out = W.pj_mbf.in;
+                b.job_ld = W.pj_mbf.ld;
+                b.job_nc = W.pj_mbf.nc;
+                CU(launch_panel_solve<TS>(b, W.w32, W.pj_mbf.n, P.max_tiles, h->tile_wm, st));
+            }
+        }
+        if (!panel) TRY((solve_cols<TS, TA>(a, W.bj_mbf, false, P.max_tiles, st)));
     }
     launch_panel_rows<PanelT<TS>>(m, h->d_sub_off, h->d_phi_off, h->d_if_off, h->d_prm_off, W.phi64,
                                   (PanelT<TS>*)h->d_phi, st);

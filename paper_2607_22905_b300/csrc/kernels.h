@@ -219,6 +219,20 @@ cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cuda
 // Column-block jobs: each of the 4 consumer warps of a CTA solves one column of the job
 // with the same factor tile stream (each tile copied once per job, read by every warp).
 constexpr int COLS_PER_JOB = 4;
+// Multi-column local solves of up to PANEL_NC right-hand sides of one subdomain per CTA
+// (FP32 / BF16 streams; jobs as launch_tile_solve_cols: job_sub, job_in (= offset in w32
+// and in out), job_ld, job_nc); the scaled FP32 right-hand sides in w32 (overwritten),
+// the results in a.out (FP64); wm = widest tile row.  cudaErrorInvalidValue when its
+// shared memory does not fit an SM (the caller then uses launch_tile_solve_cols).
+constexpr int PANEL_NC = 32;
+template <typename TS>
+cudaError_t launch_panel_solve(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm, cudaStream_t st);
+bool panel_solve_fits(int wm, int max_tiles, size_t ts);   // its shared memory fits one SM
+// w32 (zeroed) <- the scaled FP32 MBF right-hand sides -B_i psi_m (as launch_mbf_rhs, times
+// sc32[sc_off[i] + row])
+void launch_mbf_rhs32(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col, const double* g_val,
+                      const int32_t* rows, const int64_t* phi_off, const float* sc32, const int64_t* sc_off,
+                      float* w32, cudaStream_t st);
 template <typename TS, typename TA>
 cudaError_t launch_tile_solve_cols(const SolveArgs& a, int njobs, int max_tiles, cudaStream_t st);
 void launch_mbf_rhs(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col,
