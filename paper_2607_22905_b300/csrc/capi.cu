@@ -145,6 +145,9 @@ struct Vecs {
     DevBlockJobs bj;                   // column-block jobs of the batched local solves
     int32_t* bj_col0 = nullptr;
     int bj_k = 0;                      // column count bj was built for
+    DevBlockJobs pj;                   // the same in blocks of PANEL_NC (FP32 / BF16 panel solves)
+    int32_t* pj_col0 = nullptr;
+    float* w32 = nullptr;              // their forward results (k * n floats), or null
     int64_t graph_kernels = 0;         // kernels in one replay of the iteration graph
     int32_t* iits = nullptr;           // inexact interface solve: per column, inner iterations
     int64_t* iits_total = nullptr;     //   of the latest application / summed since reset
@@ -1228,6 +1231,20 @@ int stage_local(algmortar_t* h, Vecs& v, const double* r, const ColStrides& cs, 
     a.deep_ring = h->tuned_ring;
     a.err = h->d_kerr;
     if (v.k > 1) {
+        if constexpr (sizeof(TA) == 4) {
+            if (v.w32) {
+                // batched FP32 / BF16 columns: one job per (subdomain, block of PANEL_NC
+                // columns), the factor streamed once per block
+                a.job_sub = v.pj.sub;
+                a.job_in = v.pj.in;
+                a.job_out = v.pj.in;
+                a.job_ld = v.pj.ld;
+                a.job_nc = v.pj.nc;
+                a.job_col0 = v.pj_col0;
+                CU(launch_panel_solve_cols<TS>(a, v.w32, v.pj.n, h->P.max_tiles, h->tile_wm, h->st));
+                return 0;
+            }
+        }
         // batched columns: one job per (subdomain, block of COLS_PER_JOB columns), each
         // factor tile read once per block
         a.job_col0 = v.bj_col0;
@@ -1454,11 +1471,37 @@ int ensure_batch_jobs(algmortar_t* h, Vecs& v) {
         b.add(s, h->P.sub_off[s], h->n, v.k, false);
         for (size_t j = before; j < b.sub.size(); ++j) col0.push_back((int32_t)((j - before) * COLS_PER_JOB));
     }
-    void* old[] = {v.bj.sub, v.bj.nc, v.bj.t0, v.bj.in, v.bj.ld, v.bj_col0};
+    void* old[] = {v.bj.sub, v.bj.nc, v.bj.t0, v.bj.in, v.bj.ld, v.bj_col0,
+                   v.pj.sub, v.pj.nc, v.pj.t0, v.pj.in, v.pj.ld, v.pj_col0, v.w32};
     for (void* p : old)
         if (p) h->release(p);
+    v.pj = DevBlockJobs{};
+    v.pj_col0 = nullptr;
+    v.w32 = nullptr;
     TRY(upload_jobs(h, v.bj, b));
     TRY(upload(h, v.bj_col0, col0));
+    if (h->opts.precision != ALGMORTAR_FP64 && panel_solve_fits(h->tile_wm, h->P.max_tiles, h->opts.precision ==
+                                                                                  ALGMORTAR_FP32 ? 4 : 2)) {
+        // PANEL_NC columns per job, subdomains with the longest tile chains first
+        std::vector<int32_t> ord(h->m);
+        for (int s = 0; s < h->m; ++s) ord[s] = s;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return h->P.ntiles[x] > h->P.ntiles[y]; });
+        BlockJobs pb;
+        std::vector<int32_t> pc0;
+        for (int s : ord)
+            for (int c = 0; c < v.k; c += PANEL_NC) {
+                pb.sub.push_back(s);
+                pb.in.push_back(h->P.sub_off[s] + (int64_t)c * h->n);
+                pb.ld.push_back(h->n);
+                pb.nc.push_back(std::min(PANEL_NC, v.k - c));
+                pb.t0.push_back(0);
+                pc0.push_back(c);
+            }
+        TRY(upload_jobs(h, v.pj, pb));
+        TRY(upload(h, v.pj_col0, pc0));
+        v.w32 = h->alloc<float>((size_t)h->n * v.k);
+        if (!v.w32) return fail(ALGMORTAR_OOM, "panel solve scratch");
+    }
     v.bj_k = v.k;
     return 0;
 }

@@ -228,6 +228,12 @@ constexpr int PANEL_NC = 32;
 template <typename TS>
 cudaError_t launch_panel_solve(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm, cudaStream_t st);
 bool panel_solve_fits(int wm, int max_tiles, size_t ts);   // its shared memory fits one SM
+// The same for batched PCG columns: FP64 right-hand sides in a.in (scaled by a.scale32 in the
+// solve), column c of a job being column job_col0[job] + c with its stop flag (a.done); w32
+// (same indexing as in / out, FP32) holds the forward results; a.accumulate adds to a.out.
+template <typename TS>
+cudaError_t launch_panel_solve_cols(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm,
+                                    cudaStream_t st);
 // w32 (zeroed) <- the scaled FP32 MBF right-hand sides -B_i psi_m (as launch_mbf_rhs, times
 // sc32[sc_off[i] + row])
 void launch_mbf_rhs32(int m, const int64_t* g_off, const int32_t* g_row, const int32_t* g_col, const double* g_val,

@@ -119,7 +119,11 @@ void launch_mbf_rhs32(int m, const int64_t* g_off, const int32_t* g_row, const i
     k_mbf_rhs32<<<m, 128, 0, st>>>(m, g_off, g_row, g_col, g_val, rows, phi_off, sc32, sc_off, w32);
 }
 
-template <typename TS>
+// IN64: the right-hand sides come from a.in (FP64, scaled here; batched PCG columns with
+// their stop flags, column c of the job being column job_col0 + c), w32 then only holds
+// the forward results; a.accumulate adds the result to a.out.  Otherwise (the MBFs) w32
+// holds the scaled FP32 right-hand sides.
+template <typename TS, bool IN64>
 __global__ void __launch_bounds__(128) k_panel_solve(SolveArgs a, float* __restrict__ w32, int wm) {
     constexpr int NT = 128;
     constexpr uint32_t TB = TILE2 * sizeof(TS);
@@ -127,6 +131,12 @@ __global__ void __launch_bounds__(128) k_panel_solve(SolveArgs a, float* __restr
     const int s = a.job_sub[job];
     const int nc = a.job_nc[job];
     const int64_t ld = a.job_ld[job];
+    const int col0 = IN64 && a.job_col0 ? a.job_col0[job] : 0;
+    // columns of the job that still run (PCG stop flags); none: nothing to do
+    uint32_t live = 0;
+    for (int c = 0; c < nc; ++c)
+        if (!(IN64 && a.done && a.done[(int64_t)(col0 + c) * a.done_stride])) live |= 1u << c;
+    if (!live) return;
     const Profile pf = a.pf;
     const int n = pf.rows[s], T = pf.ntiles[s];
     const int64_t r0 = pf.row0[s];
@@ -136,6 +146,7 @@ __global__ void __launch_bounds__(128) k_panel_solve(SolveArgs a, float* __restr
     const float* sc32 = a.scale32 ? a.scale32 + a.scale_off[s] : nullptr;
     float* wv = w32 + a.job_in[job];
     double* out = a.out + a.job_in[job];
+    const double* in = IN64 ? a.in + a.job_in[job] : nullptr;
     const int tid = threadIdx.x, r = tid & 31, w = tid >> 5, c0 = 8 * w;
 
     extern __shared__ __align__(16) unsigned char pn_raw[];
@@ -172,19 +183,27 @@ __global__ void __launch_bounds__(128) k_panel_solve(SolveArgs a, float* __restr
                          : "memory");
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
+    auto on = [&](int j) { return ((live >> (c0 + j)) & 1u) != 0; };
     // right-hand side block of step k (row `lane` of its 8 columns): the scaled input
-    // (forward) or the forward result (backward), both in w32
-    auto load_rhs = [&](int k, float (&v)[8]) {
+    // (forward) or the forward result (backward), from w32; FP64 inputs are loaded raw
+    // here and converted when used, so that the load's latency falls in the step before
+    auto load_rhs = [&](int k, float (&v)[8], double (&vd)[8]) {
         int I, nt;
         step_rows(k, I, nt);
         const int row = I * TILE + r;
+        if (IN64 && k < T) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = (row < n && c0 + j < nc) ? wv[(int64_t)(c0 + j) * ld + row] : 0.0f;
+            for (int j = 0; j < 8; ++j) vd[j] = (row < n && on(j)) ? in[(int64_t)(c0 + j) * ld + row] : 0.0;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (row < n && on(j)) ? wv[(int64_t)(c0 + j) * ld + row] : 0.0f;
+        }
     };
     int64_t q = 0;
     issue(0, 0, 0);
     float bvn[8];
-    load_rhs(0, bvn);
+    double bvd[8];
+    load_rhs(0, bvn, bvd);
     int cur = 0;
     for (int k = 0; k < 2 * T; ++k) {
         int I, nt;
@@ -193,13 +212,19 @@ __global__ void __launch_bounds__(128) k_panel_solve(SolveArgs a, float* __restr
         const int64_t qn = q + nt + 1;
         if (k + 1 < 2 * T) issue(k + 1, qn, (k + 1) & 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
+        const int row = I * TILE + r;
         float bv[8];
+        if (IN64 && fwd) {
+            const float f = (row < n && sc32) ? sc32[row] : 1.0f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) bv[j] = bvn[j];
+            for (int j = 0; j < 8; ++j) bv[j] = (float)bvd[j] * f;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) bv[j] = bvn[j];
+        }
         // the next step's block, one step ahead (the first backward step's is the last
         // forward result, still in registers)
-        if (k + 1 < 2 * T && k + 1 != T) load_rhs(k + 1, bvn);
-        const int row = I * TILE + r;
+        if (k + 1 < 2 * T && k + 1 != T) load_rhs(k + 1, bvn, bvd);
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();
         const TS* st = stage + (size_t)(k & 1) * wm * TILE2;
@@ -228,17 +253,22 @@ __global__ void __launch_bounds__(128) k_panel_solve(SolveArgs a, float* __restr
             if (fwd) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
-                    if (c0 + j < nc) wv[(int64_t)(c0 + j) * ld + row] = x[j];
+                    if (on(j)) wv[(int64_t)(c0 + j) * ld + row] = x[j];
             } else {
                 const float f = sc32 ? sc32[row] : 1.0f;
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (c0 + j < nc) out[(int64_t)(c0 + j) * ld + row] = f2d_exact(x[j] * f);
+                for (int j = 0; j < 8; ++j) {
+                    if (!on(j)) continue;
+                    double* o = out + (int64_t)(c0 + j) * ld + row;
+                    const double y = f2d_exact(x[j] * f);
+                    if (IN64 && a.accumulate) *o += y;
+                    else *o = y;
+                }
             }
         }
         if (k + 1 == T) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) bvn[j] = (row < n && c0 + j < nc) ? x[j] : 0.0f;
+            for (int j = 0; j < 8; ++j) bvn[j] = (row < n && on(j)) ? x[j] : 0.0f;
         }
         __syncthreads();
         cur ^= 1;
@@ -253,19 +283,30 @@ size_t panel_solve_smem(int wm, int max_tiles, size_t ts) {
 }
 bool panel_solve_fits(int wm, int max_tiles, size_t ts) { return panel_solve_smem(wm, max_tiles, ts) <= 227 * 1024; }
 
-template <typename TS>
-cudaError_t launch_panel_solve(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm, cudaStream_t st) {
+template <typename TS, bool IN64>
+static cudaError_t launch_panel(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm, cudaStream_t st) {
     if (njobs <= 0) return cudaSuccess;
     const size_t smem = panel_solve_smem(wm, max_tiles, sizeof(TS));
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_panel_solve<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_panel_solve<TS, IN64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_panel_solve<TS><<<njobs, 128, smem, st>>>(a, w32, wm);
+    k_panel_solve<TS, IN64><<<njobs, 128, smem, st>>>(a, w32, wm);
     return cudaGetLastError();
+}
+template <typename TS>
+cudaError_t launch_panel_solve(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm, cudaStream_t st) {
+    return launch_panel<TS, false>(a, w32, njobs, max_tiles, wm, st);
+}
+template <typename TS>
+cudaError_t launch_panel_solve_cols(const SolveArgs& a, float* w32, int njobs, int max_tiles, int wm, cudaStream_t st) {
+    return launch_panel<TS, true>(a, w32, njobs, max_tiles, wm, st);
 }
 
 template cudaError_t launch_panel_solve<float>(const SolveArgs&, float*, int, int, int, cudaStream_t);
 template cudaError_t launch_panel_solve<__nv_bfloat16>(const SolveArgs&, float*, int, int, int, cudaStream_t);
+template cudaError_t launch_panel_solve_cols<float>(const SolveArgs&, float*, int, int, int, cudaStream_t);
+template cudaError_t launch_panel_solve_cols<__nv_bfloat16>(const SolveArgs&, float*, int, int, int, cudaStream_t);
 
 }  // namespace am
