@@ -275,6 +275,22 @@ def test_apply_parts_is_algorithm_2(p2d, p3d):
             assert np.linalg.norm(Ai @ pbar[a:b] - f[a:b]) <= 1e-12 * np.linalg.norm(f[a:b])
 
 
+def test_restriction_from_residual(p2d, p3d):
+    """Algorithm 2's interface right-hand side -1/4 G^T pbar equals 1/4 Phi^T r: the MBFs
+    are Phi = -A_hat^{-1} G (Eq. def-phat-local) and A_hat is symmetric, so the interface
+    right-hand side depends on r alone (pins the oracle's MBFs and restriction together)."""
+    for pc, n in ((p2d[3], p2d[0].shape[0]), (p3d[3], p3d[0].shape[0])):
+        r = np.random.default_rng(21).standard_normal(n)
+        _, rhs, _, _ = oa.apply_parts(pc, r)
+        f = r[pc.sk.perm]
+        alt = np.zeros_like(rhs)
+        for i in range(pc.sk.m):
+            a, b = pc.sk.offsets[i], pc.sk.offsets[i + 1]
+            if pc.I_loc[i].size:
+                np.add.at(alt, pc.I_loc[i], pc.Phat[i].T @ f[a:b])
+        np.testing.assert_allclose(0.25 * alt, rhs, rtol=0, atol=1e-12 * np.abs(rhs).max())
+
+
 def test_symmetry(p3d):
     """Cor. cor-schur-p: cal_M symmetric -> |r1.M^-1 r2 - r2.M^-1 r1| <= 1e-12 relative."""
     *_, pc = p3d
