@@ -174,7 +174,7 @@ struct algmortar_handle {
     int64_t* d_sub_off = nullptr;
     int nchunks = 0;                   // prolongation: row chunks (<= 32 rows of one subdomain)
     ProlongChunk* d_chunks = nullptr;
-    int64_t* d_prm_off = nullptr;      // row-major panels (prolongation): start of subdomain i
+    int32_t* d_chunk_sub = nullptr;    // subdomain of each chunk
     int tile_wm = 1;                   // widest tile row of the local profiles (tiles)
     int64_t nprm = 0;                  // entries of the row-major panels
     // local factor profile and streams
@@ -1094,7 +1094,7 @@ int numeric_setup(algmortar_t* h) {
         }
         if (!panel) TRY((solve_cols<TS, TA>(a, W.bj_mbf, false, P.max_tiles, st)));
     }
-    launch_panel_rows<PanelT<TS>>(m, h->d_sub_off, h->d_phi_off, h->d_if_off, h->d_prm_off, W.phi64,
+    launch_panel_rows<PanelT<TS>>(h->nchunks, h->d_chunks, h->d_chunk_sub, h->d_sub_off, h->d_phi_off, W.phi64,
                                   (PanelT<TS>*)h->d_phi, st);
     cudaEventRecord(ev[2], st);
     // --- interface system S_eta = diag(T) + 1/4 G^T Phi (Eq. interface-problem-alg),
@@ -1925,11 +1925,17 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
         }
         h->nchunks = (int)ch.size();
         h->nprm = prm[P.m];
+        {
+            std::vector<int32_t> csub;
+            csub.reserve(ch.size());
+            for (int s = 0; s < P.m; ++s)
+                for (int64_t o = 0; o < P.sub_off[s + 1] - P.sub_off[s]; o += 32) csub.push_back(s);
+            rc = rc ? rc : upload(h, h->d_chunk_sub, csub);
+        }
         for (int s = 0; s < P.m; ++s)
             for (int I = 0; I < P.ntiles[s]; ++I)
                 h->tile_wm = std::max(h->tile_wm, I - P.t_lo[P.trow_off[s] + I] + 1);
         rc = rc ? rc : upload(h, h->d_chunks, ch);
-        rc = rc ? rc : upload(h, h->d_prm_off, prm);
     }
     rc = rc ? rc : upload(h, h->d_rows, rows);
     rc = rc ? rc : upload(h, h->d_ntiles, P.ntiles);

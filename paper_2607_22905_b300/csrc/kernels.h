@@ -281,10 +281,10 @@ void launch_prolong(int nchunks, const ProlongChunk* chunks, const int32_t* if_l
                     const double* eta, const double* pbar, const double* base, double* z, const double* r,
                     GridSum gs, PcgScalars* sc, ColStrides cs, int ncols, cudaStream_t st);
 // Row-major padded copy (layout of ProlongChunk) of the column-major FP64 panels phi
-// (subdomain i's column m at phi_off[i] + m n_i); prm_off[i] = start of subdomain i's rows.
+// (subdomain i's column m at phi_off[i] + m n_i); chunk_sub = subdomain of each chunk.
 template <typename TP>
-void launch_panel_rows(int m, const int64_t* sub_off, const int64_t* phi_off, const int64_t* if_off,
-                       const int64_t* prm_off, const double* phi, TP* out, cudaStream_t st);
+void launch_panel_rows(int nchunks, const ProlongChunk* chunks, const int32_t* chunk_sub, const int64_t* sub_off,
+                       const int64_t* phi_off, const double* phi, TP* out, cudaStream_t st);
 int prolong_blocks(int nchunks);   // CTAs of launch_prolong (<= vec_blocks of the widest vector)
 void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
                             const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,

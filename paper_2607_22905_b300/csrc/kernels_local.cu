@@ -380,6 +380,18 @@ size_t tile_chol_row_smem(int wm, size_t elem) {
 // transpose of the forward one and L^{-T} L^{-1} stays symmetric after rounding.  FP64
 // streams keep the plain factor.
 // ---------------------------------------------------------------------------------
+// factor entry (FP32 or FP64 work precision) -> stream precision, directly: a conversion
+// through double would run twice on B300's FP64 pipe per entry (float -> double -> float)
+template <typename TS, typename TW>
+__device__ __forceinline__ TS to_stream(TW x) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+        if constexpr (std::is_same<TW, float>::value) return __float2bfloat16_rn(x);
+        else return stf<TS>((double)x);
+    } else {
+        return (TS)x;
+    }
+}
+
 template <typename TW, typename TS>
 __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restrict__ work,
                                                   const TW* __restrict__ dinv,
@@ -387,6 +399,7 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
     constexpr bool kPair = sizeof(TW) == 4;
     __shared__ TW As[kPair ? TILE : 1][TILE + 1];
     __shared__ TW Bs[kPair ? TILE : 1][TILE + 1];
+    __shared__ TW Ms[TILE][TILE + 1];   // a forward tile, read coalesced
     const int s = blockIdx.x;
     const int T = pf.ntiles[s];
     const int64_t r0 = pf.row0[s];
@@ -407,10 +420,13 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
         for (int t = 0; t <= nt; ++t) {
             if (cfw && t == nt - 1) continue;
             const TW* src = t < nt ? Wb + (fwd[I] + t) * TILE2 : Db + (int64_t)I * TILE2;
+            for (int e = tid; e < TILE2; e += blockDim.x) Ms[e >> 5][e & 31] = src[e];   // Ms[c][r] = M[r][c]
+            __syncthreads();
             for (int e = tid; e < TILE2; e += blockDim.x) {
                 const int r = e >> 5, c = e & 31;
-                fwdS[fo + (int64_t)t * TILE2 + swz_index<TS>(r, c)] = stf<TS>((double)src[c * TILE + r]);
+                fwdS[fo + (int64_t)t * TILE2 + swz_index<TS>(r, c)] = to_stream<TS>(Ms[c][r]);
             }
+            __syncthreads();
         }
         if constexpr (kPair) {
             if (cfw) {   // C = -D_b (L_ba D_a), b = I, a = I - 1
@@ -447,7 +463,7 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
                 TS* cb = bwdS + (base + bwd[I - 1]) * TILE2;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const TS cv = stf<TS>((double)acc[q]);
+                    const TS cv = to_stream<TS>(acc[q]);
                     cf[swz_index<TS>(rb + q, cc)] = cv;
                     cb[swz_index<TS>(cc, rb + q)] = cv;
                 }
@@ -465,7 +481,7 @@ __global__ void __launch_bounds__(256) k_finalize(Profile pf, const TW* __restri
             const TW* src = t < nb ? Wb + (fwd[I + 1 + t] + (I - lo[I + 1 + t])) * TILE2 : Db + (int64_t)I * TILE2;
             for (int e = tid; e < TILE2; e += blockDim.x) {
                 const int r = e >> 5, c = e & 31;
-                bwdS[bo + (int64_t)t * TILE2 + swz_index<TS>(r, c)] = stf<TS>((double)src[r * TILE + c]);
+                bwdS[bo + (int64_t)t * TILE2 + swz_index<TS>(r, c)] = to_stream<TS>(src[r * TILE + c]);
             }
         }
     }

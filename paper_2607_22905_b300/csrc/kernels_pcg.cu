@@ -231,36 +231,37 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const ProlongChunk* __restri
     }
 }
 
-// Row-major copy of subdomain blockIdx.x's column-major FP64 panels (layout of
-// ProlongChunk), through a 32-row x 64-column shared-memory tile: column reads and row
-// writes are both coalesced.
+// Row-major copy (layout of ProlongChunk) of the column-major FP64 panels, one warp per
+// 32-row chunk: lane = row, 16 columns at a time read as coalesced column segments and
+// written as 16-byte row segments; the padding columns up to ld are zero.
 template <typename TP>
-__global__ void __launch_bounds__(256) k_panel_rows(const int64_t* __restrict__ sub_off,
+__global__ void __launch_bounds__(256) k_panel_rows(int nchunks, const ProlongChunk* __restrict__ chunks,
+                                                    const int32_t* __restrict__ chunk_sub,
+                                                    const int64_t* __restrict__ sub_off,
                                                     const int64_t* __restrict__ phi_off,
-                                                    const int64_t* __restrict__ if_off,
-                                                    const int64_t* __restrict__ prm_off,
                                                     const double* __restrict__ phi, TP* __restrict__ out) {
     constexpr int VW = 16 / sizeof(TP);
-    __shared__ TP tile[32][65];
-    const int s = blockIdx.x;
-    const int64_t ns = sub_off[s + 1] - sub_off[s];
-    const int kk = (int)(if_off[s + 1] - if_off[s]);
-    const int ld = (kk + VW - 1) / VW * VW;
-    const double* src = phi + phi_off[s];
-    TP* dst = out + prm_off[s];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int64_t r0 = 0; r0 < ns; r0 += 32) {
-        const int nr = (int)(ns - r0 < 32 ? ns - r0 : 32);
-        for (int c0 = 0; c0 < ld; c0 += 64) {
-            const int nc = ld - c0 < 64 ? ld - c0 : 64;
-            for (int c = w; c < nc; c += nwarp)
-                tile[lane][c] = (lane < nr && c0 + c < kk) ? (TP)src[(int64_t)(c0 + c) * ns + r0 + lane] : (TP)0;
-            __syncthreads();
-            for (int t = threadIdx.x; t < nr * nc; t += blockDim.x) {
-                const int rr = t / nc, c = t - rr * nc;
-                dst[(r0 + rr) * ld + c0 + c] = tile[rr][c];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int ch = blockIdx.x * nw + (threadIdx.x >> 5); ch < nchunks; ch += gridDim.x * nw) {
+        const ProlongChunk cu = chunks[ch];
+        if (lane >= cu.nrow) continue;
+        const int s = chunk_sub[ch];
+        const int64_t ns = sub_off[s + 1] - sub_off[s], o = cu.row0 - sub_off[s] + lane;
+        const double* src = phi + phi_off[s] + o;
+        TP* dst = out + cu.phi0 + (int64_t)lane * cu.ld;
+        for (int cb = 0; cb < cu.ld; cb += 16) {
+            TP v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = cb + j < cu.kk ? (TP)src[(int64_t)(cb + j) * ns] : (TP)0;
+#pragma unroll
+            for (int j = 0; j < 16; j += VW) {
+                if (cb + j < cu.ld) {
+                    if constexpr (VW == 4)
+                        *reinterpret_cast<float4*>(dst + cb + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    else
+                        *reinterpret_cast<double2*>(dst + cb + j) = make_double2(v[j], v[j + 1]);
+                }
             }
-            __syncthreads();
         }
     }
 }
@@ -729,11 +730,11 @@ void launch_prolong(int nchunks, const ProlongChunk* chunks, const int32_t* if_l
                                                                   r, gs, sc, cs);
 }
 template <typename TP>
-void launch_panel_rows(int m, const int64_t* sub_off, const int64_t* phi_off, const int64_t* if_off,
-                       const int64_t* prm_off, const double* phi, TP* out, cudaStream_t st) {
-    if (m <= 0) return;
+void launch_panel_rows(int nchunks, const ProlongChunk* chunks, const int32_t* chunk_sub, const int64_t* sub_off,
+                       const int64_t* phi_off, const double* phi, TP* out, cudaStream_t st) {
+    if (nchunks <= 0) return;
     count_launch();
-    k_panel_rows<TP><<<m, 256, 0, st>>>(sub_off, phi_off, if_off, prm_off, phi, out);
+    k_panel_rows<TP><<<prolong_blocks(nchunks), 256, 0, st>>>(nchunks, chunks, chunk_sub, sub_off, phi_off, phi, out);
 }
 void launch_smooth_residual(int64_t n, int ncols, const int64_t* ell_ptr, const int32_t* ell_col,
                             const double* ell_val, const double* x, const double* r, double* s, ColStrides cs,
@@ -810,7 +811,7 @@ void launch_tpfa_grad(int64_t n, const int32_t* rowptr, const int32_t* col, cons
                                      const double*, const double*, double*, const double*, GridSum, PcgScalars*, \
                                      ColStrides, int, cudaStream_t);
 #define INST_PANEL_ROWS(TP)                                                                                  \
-    template void launch_panel_rows<TP>(int, const int64_t*, const int64_t*, const int64_t*, const int64_t*,    \
+    template void launch_panel_rows<TP>(int, const ProlongChunk*, const int32_t*, const int64_t*, const int64_t*, \
                                         const double*, TP*, cudaStream_t);
 INST_PANEL_ROWS(double)
 INST_PANEL_ROWS(float)
