@@ -1655,7 +1655,7 @@ int uneven_part_sizes(int64_t n, int32_t m, uint64_t seed, int32_t* out, std::st
 
 // ------------------------------------------------------------------ autotuner
 // Launch variants of the hot kernels, measured on the handle's own data with CUDA events:
-// the batched local triangular solves (4 ring / warp shapes x 3 job orders) and the CTAs
+// the batched local triangular solves (5 ring / warp shapes x 3 job orders) and the CTAs
 // per SM of the PCG vector kernels.  Every local-solve variant must reproduce the default
 // variant's output to rounding (else ALGMORTAR_CUDA); the choice is cached per process by
 // precision and factor-profile shape, so later setups of the same shape skip the search.
@@ -1735,7 +1735,7 @@ int autotune(algmortar_t* h) {
     int best_ring = 0, best_order = 0;
     float best = 3.4e38f;
     for (int order = 0; order < 3; ++order)
-        for (int ring = 0; ring < 4; ++ring) {
+        for (int ring = 0; ring < 5; ++ring) {
             h->tuned_ring = ring;
             h->d_job_sub = h->d_job_sub_v[order];
             h->d_job_off = h->d_job_off_v[order];

@@ -35,7 +35,7 @@ struct SolveArgs {
     int64_t ldin, ldout;       // column strides of in / out (gridDim.y = columns)
     int done_stride;           // int32 stride between columns' stop flags
     int col_fast;              // set by the launcher: grid (columns, jobs) instead of (jobs)
-    int deep_ring;             // launch variant (ring / warp shape) of the chain solves, 0..3
+    int deep_ring;             // launch variant (ring / warp shape) of the chain solves, 0..4
                                // (defaults, or the autotuner's choice); all compute the solve
     int accumulate;            // 1: out += result instead of out = result
     // column-block jobs (launch_tile_solve_cols): up to NW columns of one item per job,

@@ -1029,9 +1029,9 @@ __device__ __forceinline__ PairStep pair_step(int k, int NP, int T, const int32_
 }
 
 template <typename TS, typename TA, int G, int RG, int CR, int NW>
-// BF16 with 4 consumer warps: 3 CTAs per SM (<= 112 registers a thread; its shared memory
-// fits 3 as well).  FP32 tiles fill shared memory at 2 CTAs per SM.
-__global__ void __launch_bounds__((NW + 2) * 32, (NW == 4 && sizeof(TS) == 2) ? 3 : 2)
+// BF16 with 4 consumer warps, or with a 3-group far ring: 3 CTAs per SM (their shared
+// memory fits 3 as well).  FP32 tiles fill shared memory at 2 CTAs per SM.
+__global__ void __launch_bounds__((NW + 2) * 32, (sizeof(TS) == 2 && (NW == 4 || RG <= 3)) ? 3 : 2)
     k_chain_solve_pairs(SolveArgs a) {
     // Critical slot of a step (7 tiles): forward [nf0 nf1 D_f | ns0 ns1 C D_s], backward
     // [nf0 nf1 D_f | C^T ns0 ns1 D_s]; near slot i multiplies row Jnear0 + i.
@@ -1693,6 +1693,8 @@ cudaError_t launch_tile_solve(const SolveArgs& a, int njobs, int max_tiles, cuda
             case 1: return launch_pairs<TS, TA, G, RG, 2, 4>(a, njobs, max_tiles, st, ncols);      // 4 consumer warps
             case 2: return launch_pairs<TS, TA, G, RG, 3, 6>(a, njobs, max_tiles, st, ncols);      // 3 critical slots
             case 3: return launch_pairs<TS, TA, G, RG + 1, 2, 6>(a, njobs, max_tiles, st, ncols);  // deeper far ring
+            // BF16: a 3-group far ring, so that 3 CTAs fit an SM's shared memory
+            case 4: return launch_pairs<TS, TA, G, (sizeof(TS) == 2 ? 3 : RG), 2, 6>(a, njobs, max_tiles, st, ncols);
             default: return launch_pairs<TS, TA, G, RG, 2, 6>(a, njobs, max_tiles, st, ncols);
         }
     } else {
