@@ -227,6 +227,7 @@ struct algmortar_handle {
     int32_t *d_ell_col = nullptr, *d_ell_src = nullptr;
     double* d_ell_val = nullptr;
     int64_t n_ell = 0;
+    int ell_wf = 0;                    // slice width of the SpMV's unrolled path (0: none)
     double* d_vtmp = nullptr;          // staging for value updates (original CSR order)
     algmortar_info info{};
 
@@ -1351,7 +1352,7 @@ int pcg_iteration(algmortar_t* h, Vecs& v) {
     TRY(mark(h, v, 0));
     launch_pcg_p(n, v.k, n, v.z, v.p, v.sc, st);
     TRY(mark(h, v, 1));
-    launch_pcg_spmv_ell(n, v.k, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
+    launch_pcg_spmv_ell(n, v.k, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, h->ell_wf, st);
     TRY(mark(h, v, 2));
     launch_pcg_xr(n, v.k, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, v.hist, v.hist_len, st);
     TRY(mark(h, v, 3));
@@ -1780,7 +1781,7 @@ int autotune(algmortar_t* h) {
         auto vec = [&]() -> int {
             CU(cudaMemcpyAsync(v.sc, &live, sizeof(live), cudaMemcpyHostToDevice, h->st));
             launch_pcg_p(n, 1, n, v.z, v.p, v.sc, h->st);
-            launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, h->st);
+            launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, h->ell_wf, h->st);
             launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, nullptr, 0, h->st);
             CU(cudaGetLastError());
             return 0;
@@ -1970,6 +1971,7 @@ int setup_impl(const algmortar_csr* A, const int32_t* part_in, int32_t n_parts, 
     rc = rc ? rc : upload(h, h->d_ell_src, P.ell_src);
     if (rc) return bail(rc);
     h->n_ell = (int64_t)P.ell_col.size();
+    h->ell_wf = spmv_fast_width(P.ell_ptr.data(), (int64_t)P.ell_ptr.size() - 1);
     h->ws = new (std::nothrow) NumWs();
     h->d_vtmp = h->alloc<double>((size_t)A->nnz);
     h->d_ell_val = h->alloc<double>((size_t)h->n_ell);
@@ -2273,7 +2275,7 @@ int algmortar_time_stages(algmortar_t* h, int32_t reps, double* ms_out) {
     for (int it = 0; it <= reps; ++it) {
         CU(cudaMemcpyAsync(v.sc, &live, sizeof(live), cudaMemcpyHostToDevice, st));
         cudaEventRecord(ev[0], st);
-        launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, st);
+        launch_pcg_spmv_ell(n, 1, n, h->d_ell_ptr, h->d_ell_col, h->d_ell_val, v.p, v.q, v.sc, v.gs, h->ell_wf, st);
         cudaEventRecord(ev[1], st);
         launch_pcg_p(n, 1, n, v.z, v.p, v.sc, st);
         launch_pcg_xr(n, 1, n, v.x, v.r, v.p, v.q, v.z, v.sc, v.gs, nullptr, 0, st);

@@ -119,17 +119,19 @@ __device__ __forceinline__ double warp_sum_partials_cg(const double* part, int n
     return s;
 }
 
-// Block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+// Block-wide sum (blockDim.x a multiple of 32); result valid in thread 0.  `sh` holds
+// blockDim.x doubles: every thread stores its value and warp 0 alone adds them (a
+// fixed strided assignment, then a shuffle tree).  One warp doing the additions costs
+// blockDim.x / 32 + 5 warp-wide FP64 adds, against 5 per warp plus 5 for a shuffle tree
+// in every warp; B300 runs FP64 at 1/64 of its FP32 rate, so at several CTAs per SM
+// the shorter form is visible in the dot-product kernels.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    sh[threadIdx.x] = v;
     __syncthreads();
     double s = 0.0;
     if (w == 0) {
-        int nw = blockDim.x >> 5;
-        s = lane < nw ? sh[lane] : 0.0;
+        for (int i = lane; i < (int)blockDim.x; i += 32) s += sh[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }

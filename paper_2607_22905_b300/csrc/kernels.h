@@ -298,9 +298,11 @@ void launch_pcg_replace(int64_t n, int ncols, int64_t ld, const int32_t* rowptr,
                         cudaStream_t st);
 void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, const PcgScalars* sc,
                   cudaStream_t st);
+// wf: the slice width of the unrolled path (spmv_fast_width), 0 for none
 void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
-                         const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
+                         const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs, int wf,
                          cudaStream_t st);
+int spmv_fast_width(const int64_t* ell_ptr_host, int64_t nslices);
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st);
 void launch_pcg_xr(int64_t n, int ncols, int64_t ld, double* x, double* r, const double* p, const double* q,
                    const double* z, PcgScalars* sc, GridSum gs, double* hist, int hist_len, cudaStream_t st);

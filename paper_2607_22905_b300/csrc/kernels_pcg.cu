@@ -7,6 +7,7 @@
 // writes its block sum, and the CTA that finishes last adds the partials in a fixed
 // order (GridSum) and stores the scalar straight into the device-side PCG state, so
 // repeated runs give bit-identical iterates and no partial arrays cross kernels.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <initializer_list>
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(VEC_BS) k_prolong(const ProlongChunk* __restri
     constexpr int NV = 24 / VW;           // vectors per row loaded before the first product
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     eta += col * cs.l;
     pbar += col * cs.v;
     z += col * cs.v;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_rho(int64_t n, const double* __r
                                                      ColStrides cs) {
     const int col = blockIdx.y;
     if (cs.done && cs.done[col * cs.done_stride]) return;
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     r += col * cs.v;
     z += col * cs.v;
     psc += col;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_init(int64_t n, const double* __
                                                       double* __restrict__ x, double* __restrict__ r, int64_t ld,
                                                       PcgScalars* __restrict__ sc, GridSum gs, double tol,
                                                       int max_it, int flexible, double* hist, int hist_len) {
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     const int col = blockIdx.y;
     b += col * ld;
     x += col * ld;
@@ -390,12 +391,16 @@ __global__ void __launch_bounds__(VEC_BS, 4) k_pcg_p(int64_t n, const double* __
 // independent.  Columns and values of EB entries of both rows are loaded before the
 // gathers of p they index, and those before any product, giving every lane up to 4 EB
 // independent loads in flight.  A slice's width is the same for all its lanes, so entries
-// past it are skipped by a uniform branch (no FP64 work on padding beyond the width; B300
-// issues one FP64 FMA per SM and clock for every two lanes, which bounds this kernel
-// together with HBM).  Padding inside the width and rows past n read column
-// min(row, n - 1) with value 0.
-template <int EB>
-__global__ void __launch_bounds__(VEC_BS, 4) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
+// past it are skipped by a uniform branch (no FP64 work on padding beyond the width;
+// B300's FP64 rate, about two lanes per SM and clock, bounds this kernel more than HBM
+// does).  Padding inside the width and rows past n read column min(row, n - 1) with
+// value 0.  WF > 0: a pair of slices that are both WF entries wide (the common width of
+// a stencil matrix, e.g. 7 for a 3D seven-point stencil) takes a fully unrolled path
+// with the fewest FP64 instructions: 2 WF loads of each kind in flight per lane, one FMA
+// chain per row, no predicated slot past the width (WF = 7 in steps of EB = 4 spends
+// one) and no add joining split chains.
+template <int EB, int WF>
+__global__ void __launch_bounds__(VEC_BS, WF > 0 ? 3 : 4) k_pcg_spmv_ell(int64_t n, const int64_t* __restrict__ ell_ptr,
                                                           const int32_t* __restrict__ ell_col,
                                                           const double* __restrict__ ell_val,
                                                           const double* __restrict__ p, double* __restrict__ q,
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(VEC_BS, 4) k_pcg_spmv_ell(int64_t n, const int
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     p += col * ld;
     q += col * ld;
     gs.part += col * gridDim.x;
@@ -427,42 +432,73 @@ __global__ void __launch_bounds__(VEC_BS, 4) k_pcg_spmv_ell(int64_t n, const int
         const int32_t* cb = ell_col + bb + lane;
         const double* va = ell_val + ba + lane;
         const double* vb = ell_val + bb + lane;
-        // four independent FP64 chains per lane (even / odd entries of each row): B300
-        // returns FP64 results through a narrow shared unit, so a single dependent chain
-        // per row leaves that unit idle while the lane waits
-        double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
-        for (int e0 = 0; e0 < wm; e0 += EB) {
-            int32_t ia[EB], ib[EB];
-            double xa[EB], xb[EB], ga[EB], gb[EB];
+        double s0, s1;
+        constexpr int WA = WF > 0 ? WF : 1;
+        if (WF > 0 && wa == WF && wb == WF) {
+            // one FMA chain per row: 2 per lane, and the many resident warps, keep the
+            // FP64 unit fed, and no add joins split chains (the SpMV is FP64-bound)
+            int32_t ia[WA], ib[WA];
+            double xa[WA], xb[WA], ga[WA], gb[WA];
 #pragma unroll
-            for (int j = 0; j < EB; ++j) {
-                const int e = e0 + j;
-                ia[j] = e < wa ? __ldg(ca + (int64_t)e * 32) : 0;
-                ib[j] = e < wb ? __ldg(cb + (int64_t)e * 32) : 0;
+            for (int j = 0; j < WF; ++j) {
+                ia[j] = __ldg(ca + j * 32);
+                ib[j] = __ldg(cb + j * 32);
             }
 #pragma unroll
-            for (int j = 0; j < EB; ++j) {
-                const int e = e0 + j;
-                xa[j] = e < wa ? __ldg(va + (int64_t)e * 32) : 0.0;
-                xb[j] = e < wb ? __ldg(vb + (int64_t)e * 32) : 0.0;
+            for (int j = 0; j < WF; ++j) {
+                xa[j] = __ldg(va + j * 32);
+                xb[j] = __ldg(vb + j * 32);
             }
 #pragma unroll
-            for (int j = 0; j < EB; ++j) {
-                const int e = e0 + j;
-                ga[j] = e < wa ? __ldg(p + ia[j]) : 0.0;
-                gb[j] = e < wb ? __ldg(p + ib[j]) : 0.0;
+            for (int j = 0; j < WF; ++j) {
+                ga[j] = __ldg(p + ia[j]);
+                gb[j] = __ldg(p + ib[j]);
             }
+            s0 = xa[0] * ga[0];
+            s1 = xb[0] * gb[0];
 #pragma unroll
-            for (int j = 0; j < EB; j += 2) {
-                const int e = e0 + j;
-                if (e < wa) s0 += xa[j] * ga[j];
-                if (e < wb) s1 += xb[j] * gb[j];
-                if (e + 1 < wa) t0 += xa[j + 1] * ga[j + 1];
-                if (e + 1 < wb) t1 += xb[j + 1] * gb[j + 1];
+            for (int j = 1; j < WF; ++j) {
+                s0 = fma(xa[j], ga[j], s0);
+                s1 = fma(xb[j], gb[j], s1);
             }
+        } else {
+            // four independent FP64 chains per lane (even / odd entries of each row)
+            double t0 = 0.0, t1 = 0.0;
+            s0 = 0.0;
+            s1 = 0.0;
+            for (int e0 = 0; e0 < wm; e0 += EB) {
+                int32_t ia[EB], ib[EB];
+                double xa[EB], xb[EB], ga[EB], gb[EB];
+#pragma unroll
+                for (int j = 0; j < EB; ++j) {
+                    const int e = e0 + j;
+                    ia[j] = e < wa ? __ldg(ca + (int64_t)e * 32) : 0;
+                    ib[j] = e < wb ? __ldg(cb + (int64_t)e * 32) : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < EB; ++j) {
+                    const int e = e0 + j;
+                    xa[j] = e < wa ? __ldg(va + (int64_t)e * 32) : 0.0;
+                    xb[j] = e < wb ? __ldg(vb + (int64_t)e * 32) : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < EB; ++j) {
+                    const int e = e0 + j;
+                    ga[j] = e < wa ? __ldg(p + ia[j]) : 0.0;
+                    gb[j] = e < wb ? __ldg(p + ib[j]) : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < EB; j += 2) {
+                    const int e = e0 + j;
+                    if (e < wa) s0 += xa[j] * ga[j];
+                    if (e < wb) s1 += xb[j] * gb[j];
+                    if (e + 1 < wa) t0 += xa[j + 1] * ga[j + 1];
+                    if (e + 1 < wb) t1 += xb[j + 1] * gb[j + 1];
+                }
+            }
+            s0 += t0;
+            s1 += t1;
         }
-        s0 += t0;
-        s1 += t1;
         const int64_t ka = sa * 32 + lane, kb = sb * 32 + lane;
         if (ka < n) {
             q[ka] = s0;
@@ -501,9 +537,58 @@ __device__ __forceinline__ void pcg_stop_test(PcgScalars* sc) {
     }
 }
 
-// x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new (and, for
-// the flexible beta, r_new . z_old -> sc->rz_mix, z still holding z_old), then the stop
-// test.  V = 2: rows in 16-byte pairs, as in k_pcg_p.
+// Rows of k_pcg_xr in 16-byte pairs: with UPD, x += alpha p and r -= alpha q; then
+// ||r||^2 (and with FLEX r . z) into two independent FP64 chains each.  Separate loop
+// bodies per case keep the per-row path free of branches.
+template <bool FLEX, bool UPD>
+__device__ __forceinline__ void xr_pairs(int64_t np, double2* __restrict__ x2, double2* __restrict__ r2,
+                                         const double2* __restrict__ p2, const double2* __restrict__ q2,
+                                         const double2* __restrict__ z2, double al, double& acc, double& acc2) {
+    double ay = 0.0, a2y = 0.0;
+#pragma unroll 1   // unrolled, the loop spills at the 64 registers of 4 CTAs per SM
+    GRID_STRIDE(i, np) {
+        double2 rk = r2[i];
+        if (UPD) {
+            const double2 pk = p2[i], qk = q2[i];
+            double2 xk = x2[i];
+            xk.x += al * pk.x;
+            xk.y += al * pk.y;
+            rk.x -= al * qk.x;
+            rk.y -= al * qk.y;
+            x2[i] = xk;
+            r2[i] = rk;
+        }
+        acc += rk.x * rk.x;
+        ay += rk.y * rk.y;
+        if (FLEX) {
+            const double2 zk = z2[i];
+            acc2 += rk.x * zk.x;
+            a2y += rk.y * zk.y;
+        }
+    }
+    acc += ay;
+    acc2 += a2y;
+}
+template <bool FLEX, bool UPD>
+__device__ __forceinline__ void xr_rows(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                        const double* __restrict__ p, const double* __restrict__ q,
+                                        const double* __restrict__ z, double al, double& acc, double& acc2) {
+    GRID_STRIDE(k, n) {
+        double rk = r[k];
+        if (UPD) {
+            x[k] += al * p[k];
+            rk -= al * q[k];
+            r[k] = rk;
+        }
+        acc += rk * rk;
+        if (FLEX) acc2 += rk * z[k];
+    }
+}
+
+// x += alpha p;  r -= alpha q;  ||r||^2 -> sc->rr_new (and, for the flexible beta,
+// r_new . z_old -> sc->rz_mix, z still holding z_old), then the stop test.  After a
+// breakdown (step_ok == 0) x and r stay as they are.  V = 2: rows in 16-byte pairs, as
+// in k_pcg_p.
 template <int V>
 __global__ void __launch_bounds__(VEC_BS, 4) k_pcg_xr(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p, const double* __restrict__ q,
@@ -513,7 +598,7 @@ __global__ void __launch_bounds__(VEC_BS, 4) k_pcg_xr(int64_t n, double* __restr
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     x += col * ld;
     r += col * ld;
     p += col * ld;
@@ -524,45 +609,28 @@ __global__ void __launch_bounds__(VEC_BS, 4) k_pcg_xr(int64_t n, double* __restr
     gs.ticket += col;
     const double al = sc->alpha;
     const bool ok = sc->step_ok != 0;
-    double acc = 0.0, acc2 = 0.0, accy = 0.0, acc2y = 0.0;   // independent FP64 chains
+    double acc = 0.0, acc2 = 0.0;
     if (V == 2) {
         double2* x2 = reinterpret_cast<double2*>(x);
         double2* r2 = reinterpret_cast<double2*>(r);
         const double2* p2 = reinterpret_cast<const double2*>(p);
         const double2* q2 = reinterpret_cast<const double2*>(q);
         const double2* z2 = reinterpret_cast<const double2*>(z);
-        GRID_STRIDE(i, n >> 1) {
-            double2 rk = r2[i];
-            if (ok) {
-                const double2 pk = p2[i], qk = q2[i];
-                double2 xk = x2[i];
-                xk.x += al * pk.x;
-                xk.y += al * pk.y;
-                rk.x -= al * qk.x;
-                rk.y -= al * qk.y;
-                x2[i] = xk;
-                r2[i] = rk;
-            }
-            acc += rk.x * rk.x;
-            accy += rk.y * rk.y;
-            if (flex) {
-                const double2 zk = z2[i];
-                acc2 += rk.x * zk.x;
-                acc2y += rk.y * zk.y;
-            }
+        const int64_t np = n >> 1;
+        if (ok) {
+            if (flex) xr_pairs<true, true>(np, x2, r2, p2, q2, z2, al, acc, acc2);
+            else xr_pairs<false, true>(np, x2, r2, p2, q2, z2, al, acc, acc2);
+        } else {
+            if (flex) xr_pairs<true, false>(np, x2, r2, p2, q2, z2, al, acc, acc2);
+            else xr_pairs<false, false>(np, x2, r2, p2, q2, z2, al, acc, acc2);
         }
-        acc += accy;
-        acc2 += acc2y;
     } else {
-        GRID_STRIDE(k, n) {
-            double rk = r[k];
-            if (ok) {
-                x[k] += al * p[k];
-                rk -= al * q[k];
-                r[k] = rk;
-            }
-            acc += rk * rk;
-            if (flex) acc2 += rk * z[k];
+        if (ok) {
+            if (flex) xr_rows<true, true>(n, x, r, p, q, z, al, acc, acc2);
+            else xr_rows<false, true>(n, x, r, p, q, z, al, acc, acc2);
+        } else {
+            if (flex) xr_rows<true, false>(n, x, r, p, q, z, al, acc, acc2);
+            else xr_rows<false, false>(n, x, r, p, q, z, al, acc, acc2);
         }
     }
     const bool last = flex ? grid_sum2(acc, acc2, sh, gs, &sc->rr_new, &sc->rz_mix)
@@ -584,7 +652,7 @@ __global__ void __launch_bounds__(VEC_BS) k_pcg_replace(int64_t n, const int32_t
     const int col = blockIdx.y;
     sc += col;
     if (sc->done) return;
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     x += col * ld;
     b += col * ld;
     r += col * ld;
@@ -609,7 +677,7 @@ __global__ void __launch_bounds__(VEC_BS) k_residual(int64_t n, const int32_t* _
                                                       const double* __restrict__ val,
                                                       const double* __restrict__ x, const double* __restrict__ b,
                                                       int64_t ld, PcgScalars* __restrict__ sc, GridSum gs) {
-    __shared__ double sh[32];
+    __shared__ double sh[VEC_BS];
     const int col = blockIdx.y;
     x += col * ld;
     b += col * ld;
@@ -774,13 +842,50 @@ void launch_pcg_p(int64_t n, int ncols, int64_t ld, const double* z, double* p, 
     else
         k_pcg_p<1><<<dim3(hot_blocks(n), ncols), VEC_BS, 0, st>>>(n, z, p, ld, sc);
 }
+// resident CTAs per SM of an SpMV instantiation (its register budget), cached
+template <int WF>
+static int spmv_ctas_per_sm() {
+    static int c = 0;
+    if (c == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_spmv_ell<4, WF>, VEC_BS, 0) != cudaSuccess || b < 1)
+            b = 1;
+        c = b;
+    }
+    return c;
+}
+template <int WF>
+static void spmv_launch(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
+                        const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
+                        cudaStream_t st) {
+    const int64_t warps = (((n + 31) >> 5) + 1) >> 1;   // one warp per pair of slices
+    int g = hot_blocks(warps * 32);
+    g = std::min(g, spmv_ctas_per_sm<WF>() * g_sms);   // one wave: no CTA waits for a slot
+    k_pcg_spmv_ell<4, WF><<<dim3(g, ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q, ld, sc, gs);
+}
 void launch_pcg_spmv_ell(int64_t n, int ncols, int64_t ld, const int64_t* ell_ptr, const int32_t* ell_col,
-                         const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs,
+                         const double* ell_val, const double* p, double* q, PcgScalars* sc, GridSum gs, int wf,
                          cudaStream_t st) {
     count_launch();
-    const int64_t warps = (((n + 31) >> 5) + 1) >> 1;   // one warp per pair of slices
-    k_pcg_spmv_ell<4><<<dim3(hot_blocks(warps * 32), ncols), VEC_BS, 0, st>>>(n, ell_ptr, ell_col, ell_val, p, q,
-                                                                               ld, sc, gs);
+    if (wf == 7)
+        spmv_launch<7>(n, ncols, ld, ell_ptr, ell_col, ell_val, p, q, sc, gs, st);
+    else if (wf == 5)
+        spmv_launch<5>(n, ncols, ld, ell_ptr, ell_col, ell_val, p, q, sc, gs, st);
+    else
+        spmv_launch<0>(n, ncols, ld, ell_ptr, ell_col, ell_val, p, q, sc, gs, st);
+}
+// the slice width that takes the SpMV's unrolled path: 7 or 5 when at least half of the
+// 32-row slices have it, else 0
+int spmv_fast_width(const int64_t* ell_ptr_host, int64_t nslices) {
+    int64_t c5 = 0, c7 = 0;
+    for (int64_t s = 0; s < nslices; ++s) {
+        const int64_t w = (ell_ptr_host[s + 1] - ell_ptr_host[s]) >> 5;
+        c5 += w == 5;
+        c7 += w == 7;
+    }
+    if (2 * c7 >= nslices && nslices > 0) return 7;
+    if (2 * c5 >= nslices && nslices > 0) return 5;
+    return 0;
 }
 void launch_ell_values(int64_t nell, const int32_t* src, const double* val, double* ell_val, cudaStream_t st) {
     count_launch();
