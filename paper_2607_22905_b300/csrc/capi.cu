@@ -229,6 +229,11 @@ struct algmortar_handle {
     int64_t n_ell = 0;
     int ell_wf = 0;                    // slice width of the SpMV's unrolled path (0: none)
     double* d_vtmp = nullptr;          // staging for value updates (original CSR order)
+    // FP32 interface inverses (G_g^-1, W_g in both layouts, C^-1) in one block, kept in L2
+    // across PCG iterations by an access-policy window on the iteration graph's kernels
+    float* ifw32 = nullptr;
+    size_t ifw32_bytes = 0;
+    cudaAccessPolicyWindow l2w{};
     algmortar_info info{};
 
     template <typename T>
@@ -252,6 +257,7 @@ struct algmortar_handle {
         for (Vecs* v : {&v1, &vk})
             for (cudaEvent_t e : v->sev)
                 if (e) cudaEventDestroy(e);
+        if (l2w.num_bytes) cudaCtxResetPersistingL2Cache();   // its lines back to normal
         for (void* p : allocs)
             if (p) cudaFree(p);
         if (own_st) cudaStreamDestroy(own_st);
@@ -748,10 +754,15 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         }
         const int nsep4 = (nsep + 3) & ~3;
         if (lowp) {
-            Ginv32 = h->alloc<float>((size_t)std::max<int64_t>(gi32, 1));
-            Wcm32 = h->alloc<float>((size_t)std::max<int64_t>(wo32, 1));
-            Wrm32 = h->alloc<float>((size_t)std::max<int64_t>(wo, 1));
-            if (!Ginv32 || !Wcm32 || !Wrm32) return fail(ALGMORTAR_OOM, "interface group buffers");
+            // one block: G^-1 | W (column-major) | W (row-major) | C^-1, 256-byte aligned parts
+            auto up = [](int64_t x) { return (std::max<int64_t>(x, 1) + 63) & ~int64_t(63); };
+            const int64_t o1 = up(gi32), o2 = o1 + up(wo32), o3 = o2 + up(wo), tot = o3 + up((int64_t)nsep * nsep4);
+            h->ifw32 = h->alloc<float>((size_t)tot);
+            if (!h->ifw32) return fail(ALGMORTAR_OOM, "interface group buffers");
+            h->ifw32_bytes = (size_t)tot * sizeof(float);
+            Ginv32 = h->ifw32;
+            Wcm32 = h->ifw32 + o1;
+            Wrm32 = h->ifw32 + o2;
         }
         W.n_ginv = gi;
         W.n_w = wo;
@@ -907,9 +918,9 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             if (!W.cwork || !W.cdinv || !W.cf || !W.cb || !W.cE || !Cinv)
                 return fail(ALGMORTAR_OOM, "separator buffers");
             if (lowp) {
-                float* Cinv32 = h->alloc<float>((size_t)nsep * ((nsep + 3) & ~3));
-                if (!Cinv32) return fail(ALGMORTAR_OOM, "separator buffers");
-                a.Cinv32 = Cinv32;
+                // last part of the interface block (allocated with the group inverses)
+                const size_t nC = (size_t)nsep * ((nsep + 3) & ~3);
+                a.Cinv32 = h->ifw32 + (h->ifw32_bytes / sizeof(float) - ((nC + 63) & ~size_t(63)));
             }
             CU(cudaMemsetAsync(W.cE, 0, (size_t)nsep * nsep * sizeof(double), h->st));
             launch_eye(nsep, W.cE, h->st);
@@ -1360,6 +1371,55 @@ int pcg_iteration(algmortar_t* h, Vecs& v) {
     return mark(h, v, 7);
 }
 
+// The FP32 interface inverses are re-read every iteration, while the local solves stream
+// ~0.5 GB of factor tiles between two reads and would evict them: where the device offers
+// persisting L2 lines, the iteration graph's kernels carry an access-policy window over
+// the interface block (hit ratio = the persisting set-aside / the window), so the three
+// interface stages read L2.  The set-aside belongs to this process's context; it is only
+// ever raised.  A hint: failures are ignored.
+void set_l2_window(algmortar_t* h, cudaGraph_t g) {
+    if (!h->ifw32 || h->ifw32_bytes == 0) return;
+    if (h->l2w.num_bytes == 0) {
+        int maxp = 0, maxw = 0;
+        if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, h->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, h->device) != cudaSuccess ||
+            maxp <= 0 || maxw <= 0) {
+            cudaGetLastError();
+            return;
+        }
+        const size_t win = std::min(h->ifw32_bytes, (size_t)maxw);
+        size_t lim = 0;
+        if (cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize) != cudaSuccess) lim = 0;
+        const size_t want = std::min(win, (size_t)maxp);
+        if (lim < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) lim = want;
+        cudaGetLastError();
+        if (lim == 0) return;
+        h->l2w.base_ptr = h->ifw32;
+        h->l2w.num_bytes = win;
+        h->l2w.hitRatio = (float)std::min(1.0, (double)lim / (double)win);
+        h->l2w.hitProp = cudaAccessPropertyPersisting;
+        h->l2w.missProp = cudaAccessPropertyStreaming;
+    }
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn == 0) {
+        cudaGetLastError();
+        return;
+    }
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaKernelNodeAttrValue av{};
+    av.accessPolicyWindow = h->l2w;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributeAccessPolicyWindow, &av);
+    }
+    cudaGetLastError();
+}
+
 int ensure_graph(algmortar_t* h, Vecs& v) {
     if (v.graph && v.graph_k == v.k) return 0;
     if (v.graph) {
@@ -1378,6 +1438,7 @@ int ensure_graph(algmortar_t* h, Vecs& v) {
         return rc;
     }
     if (e != cudaSuccess) return fail(ALGMORTAR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    set_l2_window(h, g);
     e = cudaGraphInstantiate(&v.graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
