@@ -229,10 +229,12 @@ struct algmortar_handle {
     int64_t n_ell = 0;
     int ell_wf = 0;                    // slice width of the SpMV's unrolled path (0: none)
     double* d_vtmp = nullptr;          // staging for value updates (original CSR order)
-    // FP32 interface inverses (G_g^-1, W_g in both layouts, C^-1) in one block, kept in L2
-    // across PCG iterations by an access-policy window on the iteration graph's kernels
+    // FP32 interface inverses (G_g^-1, W_g in both layouts, C^-1) and the restriction
+    // tables in one block, kept in L2 across PCG iterations by an access-policy window on
+    // the iteration graph's kernels
     float* ifw32 = nullptr;
     size_t ifw32_bytes = 0;
+    int64_t ifw_cinv = 0;   // offset (floats) of C^-1 in the block
     cudaAccessPolicyWindow l2w{};
     algmortar_info info{};
 
@@ -754,15 +756,33 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         }
         const int nsep4 = (nsep + 3) & ~3;
         if (lowp) {
-            // one block: G^-1 | W (column-major) | W (row-major) | C^-1, 256-byte aligned parts
+            // one block: G^-1 | W (column-major) | W (row-major) | C^-1 | restriction pointers,
+            // cells and coefficients (moved here from their own allocations), 256-byte
+            // aligned parts (sizes in floats)
             auto up = [](int64_t x) { return (std::max<int64_t>(x, 1) + 63) & ~int64_t(63); };
-            const int64_t o1 = up(gi32), o2 = o1 + up(wo32), o3 = o2 + up(wo), tot = o3 + up((int64_t)nsep * nsep4);
+            const int64_t R = (int64_t)P.r_cell.size();
+            const int64_t o1 = up(gi32), o2 = o1 + up(wo32), o3 = o2 + up(wo), o4 = o3 + up((int64_t)nsep * nsep4);
+            const int64_t o5 = o4 + up(2 * ((int64_t)L + 1)), o6 = o5 + up(R), tot = o6 + up(2 * R);
             h->ifw32 = h->alloc<float>((size_t)tot);
             if (!h->ifw32) return fail(ALGMORTAR_OOM, "interface group buffers");
             h->ifw32_bytes = (size_t)tot * sizeof(float);
+            h->ifw_cinv = o3;
             Ginv32 = h->ifw32;
             Wcm32 = h->ifw32 + o1;
             Wrm32 = h->ifw32 + o2;
+            int64_t* rptr = reinterpret_cast<int64_t*>(h->ifw32 + o4);
+            int32_t* rcell = reinterpret_cast<int32_t*>(h->ifw32 + o5);
+            double* rcoef = reinterpret_cast<double*>(h->ifw32 + o6);
+            CU(cudaMemcpyAsync(rptr, h->d_rptr, ((size_t)L + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, h->st));
+            CU(cudaMemcpyAsync(rcell, h->d_rcell, (size_t)R * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st));
+            CU(cudaMemcpyAsync(rcoef, h->d_rcoef, (size_t)R * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+            CU(cudaStreamSynchronize(h->st));
+            h->release(h->d_rptr);
+            h->release(h->d_rcell);
+            h->release(h->d_rcoef);
+            h->d_rptr = rptr;
+            h->d_rcell = rcell;
+            h->d_rcoef = rcoef;
         }
         W.n_ginv = gi;
         W.n_w = wo;
@@ -918,9 +938,7 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             if (!W.cwork || !W.cdinv || !W.cf || !W.cb || !W.cE || !Cinv)
                 return fail(ALGMORTAR_OOM, "separator buffers");
             if (lowp) {
-                // last part of the interface block (allocated with the group inverses)
-                const size_t nC = (size_t)nsep * ((nsep + 3) & ~3);
-                a.Cinv32 = h->ifw32 + (h->ifw32_bytes / sizeof(float) - ((nC + 63) & ~size_t(63)));
+                a.Cinv32 = h->ifw32 + h->ifw_cinv;   // part of the interface block
             }
             CU(cudaMemsetAsync(W.cE, 0, (size_t)nsep * nsep * sizeof(double), h->st));
             launch_eye(nsep, W.cE, h->st);
