@@ -235,6 +235,7 @@ struct algmortar_handle {
     float* ifw32 = nullptr;
     size_t ifw32_bytes = 0;
     int64_t ifw_cinv = 0;   // offset (floats) of C^-1 in the block
+    int64_t ifw_ifpos = 0;  // offset (floats) of the ND interface positions
     cudaAccessPolicyWindow l2w{};
     algmortar_info info{};
 
@@ -756,13 +757,21 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         }
         const int nsep4 = (nsep + 3) & ~3;
         if (lowp) {
-            // one block: G^-1 | W (column-major) | W (row-major) | C^-1 | restriction pointers,
-            // cells and coefficients (moved here from their own allocations), 256-byte
-            // aligned parts (sizes in floats)
-            auto up = [](int64_t x) { return (std::max<int64_t>(x, 1) + 63) & ~int64_t(63); };
-            const int64_t R = (int64_t)P.r_cell.size();
-            const int64_t o1 = up(gi32), o2 = o1 + up(wo32), o3 = o2 + up(wo), o4 = o3 + up((int64_t)nsep * nsep4);
-            const int64_t o5 = o4 + up(2 * ((int64_t)L + 1)), o6 = o5 + up(R), tot = o6 + up(2 * R);
+            // One block, 256-byte aligned parts: G^-1 | W (column-major) | W (row-major) |
+            // C^-1, then tables every iteration re-reads, moved here from their own
+            // allocations: restriction pointers, cells and coefficients, the local solves'
+            // FP32 row scales, tile-profile descriptors and job lists (sizes in floats).
+            auto up = [](int64_t bytes) { return ((std::max<int64_t>(bytes, 1) + 3) / 4 + 63) & ~int64_t(63); };
+            const int64_t R = (int64_t)P.r_cell.size(), trw = P.trow_off[m];
+            const int64_t o1 = up(4 * gi32), o2 = o1 + up(4 * wo32), o3 = o2 + up(4 * wo);
+            const int64_t o4 = o3 + up(4 * (int64_t)nsep * nsep4);
+            // the moved tables, in the order of the move_in calls below
+            const int64_t moved = up(8 * ((int64_t)L + 1)) + up(4 * R) + up(8 * R) + up(4 * h->n) + 2 * up(4 * m) +
+                                  2 * up(8 * ((int64_t)m + 1)) + 2 * up(4 * trw) + 2 * up(8 * trw) +
+                                  3 * (up(4 * (int64_t)m) + up(8 * (int64_t)m)) +
+                                  up((int64_t)sizeof(ProlongChunk) * h->nchunks) + up(8 * (int64_t)P.ell_ptr.size()) +
+                                  up(4 * (int64_t)P.if_list.size());
+            const int64_t tot = o4 + moved;
             h->ifw32 = h->alloc<float>((size_t)tot);
             if (!h->ifw32) return fail(ALGMORTAR_OOM, "interface group buffers");
             h->ifw32_bytes = (size_t)tot * sizeof(float);
@@ -770,19 +779,48 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
             Ginv32 = h->ifw32;
             Wcm32 = h->ifw32 + o1;
             Wrm32 = h->ifw32 + o2;
-            int64_t* rptr = reinterpret_cast<int64_t*>(h->ifw32 + o4);
-            int32_t* rcell = reinterpret_cast<int32_t*>(h->ifw32 + o5);
-            double* rcoef = reinterpret_cast<double*>(h->ifw32 + o6);
-            CU(cudaMemcpyAsync(rptr, h->d_rptr, ((size_t)L + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, h->st));
-            CU(cudaMemcpyAsync(rcell, h->d_rcell, (size_t)R * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st));
-            CU(cudaMemcpyAsync(rcoef, h->d_rcoef, (size_t)R * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-            CU(cudaStreamSynchronize(h->st));
-            h->release(h->d_rptr);
-            h->release(h->d_rcell);
-            h->release(h->d_rcoef);
-            h->d_rptr = rptr;
-            h->d_rcell = rcell;
-            h->d_rcoef = rcoef;
+            int64_t off = o4;
+            bool moved_ok = true;
+            // copy a table into the block, free its old allocation, return the new address
+            auto move_in = [&](auto* src, int64_t count) -> decltype(src) {
+                using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
+                T* dst = reinterpret_cast<T*>(h->ifw32 + off);
+                off += up((int64_t)sizeof(T) * count);
+                if (count > 0 && cudaMemcpyAsync(dst, src, (size_t)count * sizeof(T), cudaMemcpyDeviceToDevice,
+                                                 h->st) != cudaSuccess)
+                    moved_ok = false;
+                if (cudaStreamSynchronize(h->st) != cudaSuccess) moved_ok = false;
+                h->release(const_cast<T*>(src));
+                return dst;
+            };
+            h->d_rptr = move_in(h->d_rptr, (int64_t)L + 1);
+            h->d_rcell = move_in(h->d_rcell, R);
+            h->d_rcoef = move_in(h->d_rcoef, R);
+            h->d_sc32 = move_in(h->d_sc32, h->n);
+            h->d_rows = move_in(h->d_rows, m);
+            h->d_ntiles = move_in(h->d_ntiles, m);
+            h->pf.rows = h->d_rows;
+            h->pf.ntiles = h->d_ntiles;
+            h->pf.row0 = move_in(h->pf.row0, (int64_t)m + 1);
+            h->pf.base = move_in(h->pf.base, (int64_t)m + 1);
+            h->pf.lo = move_in(h->pf.lo, trw);
+            h->pf.hi = move_in(h->pf.hi, trw);
+            h->pf.fwd = move_in(h->pf.fwd, trw);
+            h->pf.bwd = move_in(h->pf.bwd, trw);
+            for (int v = 0; v < 3; ++v) {
+                const bool cur = h->d_job_sub == h->d_job_sub_v[v];
+                h->d_job_sub_v[v] = move_in(h->d_job_sub_v[v], m);
+                h->d_job_off_v[v] = move_in(h->d_job_off_v[v], (int64_t)m);
+                if (cur) {
+                    h->d_job_sub = h->d_job_sub_v[v];
+                    h->d_job_off = h->d_job_off_v[v];
+                }
+            }
+            h->d_chunks = move_in(h->d_chunks, h->nchunks);
+            h->d_ell_ptr = move_in(h->d_ell_ptr, (int64_t)P.ell_ptr.size());
+            h->ifw_ifpos = off;   // filled below, with the interface positions in ND order
+            off += up(4 * (int64_t)P.if_list.size());
+            if (!moved_ok) return fail(ALGMORTAR_CUDA, "moving tables into the interface block");
         }
         W.n_ginv = gi;
         W.n_w = wo;
@@ -855,7 +893,15 @@ int numeric_prepare(algmortar_t* h, NumWs& W) {
         {
             std::vector<int32_t> ifpos(P.if_list.size());
             for (size_t t = 0; t < ifpos.size(); ++t) ifpos[t] = P.nd_pos[P.if_list[t]];
-            TRY(upload(h, h->d_ifpos, ifpos));
+            if (h->ifw32) {
+                h->d_ifpos = reinterpret_cast<int32_t*>(h->ifw32 + h->ifw_ifpos);
+                if (!ifpos.empty())
+                    CU(cudaMemcpyAsync(h->d_ifpos, ifpos.data(), ifpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                       h->st));
+                CU(cudaStreamSynchronize(h->st));
+            } else {
+                TRY(upload(h, h->d_ifpos, ifpos));
+            }
         }
         NdSolveArgs& a = h->nd;
         a.G = G;
